@@ -1,0 +1,358 @@
+"""Benchmark of the coupled phase-field step on GB300.
+
+Workload (default): 2D core-shell, 512 x 512 cells, radius 160, iron shell 32,
+J2 plasticity (sigma_Y = 0.01 E, H = 0.001 E), CG warm-started from the
+previous step.  One "step" is the whole hot path: mechanics right-hand side,
+PCG solve, J2 return, field update.  The chosen form (FP32 fields and
+operator, FP64-grade reductions) gives ``value``; the plain FP64 method is
+measured beside it on the same GPU.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the workload
+(the single-grid step does not shard; see the design notes) and ``value`` is
+the sum over ranks.  Rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s, coupled PF+diffusion+mechanics, at stated FP64 error; % HBM peak"
+L2_BYTES = 129 * 1024 * 1024
+
+# Algorithmic bytes per node per PCG iteration (x, r, p read and written once,
+# diag and the two Lame parameters read once) and per node of the solve's
+# set-up (eigenstress, Lame, warm start read; residual and diagonal written).
+CG_ITER_WORDS = {2: 16, 3: 24}
+CG_INIT_WORDS = {2: 10, 3: 15}
+
+
+def _load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_fields():
+    from paper_2111_11538_gb300 import workloads
+    return workloads.build_fields("coreshell512")
+
+
+def workload_params(precision):
+    from paper_2111_11538_gb300 import workloads
+    prm = dict(workloads.WORKLOADS["coreshell512"]["params"])
+    # the mixed form stops the FP32 CG at a residual FP32 can represent
+    prm["cg_rtol"] = 1e-10 if precision == "fp64" else 1e-6
+    return prm
+
+
+def run_gpu(precision, steps, warmup, fields, profile=True):
+    import torch
+    from paper_2111_11538_gb300 import Simulation
+    shape = fields["phi_f"].shape
+    prm = workload_params(precision)
+    sim = Simulation(shape, prm, precision=precision)
+    sim.set_fields(fields)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    for _ in range(warmup):
+        sim.step(1, stream=sh)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    sim.profile(profile)
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    for _ in range(steps):
+        flush.zero_()                       # evict the working set from L2
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(1, stream=sh)
+        b.record(stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+    prof = sim.profile_read() if profile else None
+    diag = sim.diagnostics()
+    out = sim.get_fields(keys=("phi_f", "phi_w", "xO", "xH", "xW", "sigma"))
+    sim.close()
+    return total_ms, prof, diag, out
+
+
+def run_e2e(precision, steps, fields):
+    """Same metric through the public API with host buffers: every step copies
+    the full state in from pinned host memory and the fields back out."""
+    import torch
+    from paper_2111_11538_gb300 import Simulation
+    shape = fields["phi_f"].shape
+    sim = Simulation(shape, workload_params(precision), precision=precision)
+
+    def pinned(a, dtype=np.float64):
+        t = torch.empty(a.shape, dtype=torch.float64 if dtype == np.float64 else torch.uint8, pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+    state = {k: pinned(v, np.uint8 if k == "mask" else np.float64) for k, v in fields.items()}
+    sim.set_fields(state)
+    sim.step(2)
+    keys = ("phi_f", "phi_w", "xO", "xH", "xW", "u", "Ebar", "eps_p", "alpha")
+    cur = sim.get_fields(keys=keys)
+    state.update({k: pinned(v) for k, v in cur.items()})
+    h2d = sum(v.nbytes for v in state.values())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.set_fields(state)
+        sim.step(1)
+        cur = sim.get_fields(keys=keys)
+        for k in keys:
+            state[k][...] = cur[k]
+    dt = time.perf_counter() - t0
+    d2h = sum(cur[k].nbytes for k in keys)
+    sim.close()
+    return dt, h2d, d2h
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle on the host (single thread) over a bounded sample of the
+    workload: the same core-shell geometry and parameters on a 128 x 128 grid
+    (radius and shell scaled by 1/4), two untimed steps, then timed steps
+    until about `seconds` have passed."""
+    import oracle
+    from paper_2111_11538_gb300 import workloads
+    f = workloads.build_fields("coreshell512", shape=(128, 128))
+    s = oracle.Sim(f, workloads.WORKLOADS["coreshell512"]["params"])
+    s.step(2)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        s.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": 128 * 128 * n / dt, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "128x128 core-shell (workload geometry scaled 1/4, same parameters), %d timed "
+                      "steps after 2 untimed, single-threaded FP64 C" % n}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def reduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    ws, rank, local = dist_setup()
+    cfg = {"workload": "coreshell512_j2: 2D core-shell 512x512, radius 160, shell 32, J2 plasticity "
+                       "sigma_Y=0.01E H=0.001E, CG warm start from previous step",
+           "cells": 512 * 512, "l2": "flushed before every timed step (512 MB write)",
+           "parallelism": "replicas" if ws > 1 else "single"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        f = None
+        from paper_2111_11538_gb300 import workloads
+        f = workloads.build_fields("coreshell512", shape=(128, 128))
+        s = oracle.Sim(f, workloads.WORKLOADS["coreshell512"]["params"])
+        for _ in range(args.warmup):
+            s.step(1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.step(1)
+        dt = time.perf_counter() - t0
+        v = 128 * 128 * args.steps / dt
+        sample = ("each step: one oracle step of the workload geometry scaled to 128x128 "
+                  "(radius 40, shell 8, same parameters), single-threaded FP64 C")
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-steps/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": cfg,
+                          "cpu_baseline": {"value": v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                                           "sample": sample},
+                          "e2e": {"value": v, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    from paper_2111_11538_gb300 import native
+    native.build_library()
+    fields = workload_fields()
+    N = fields["phi_f"].size
+
+    # plain FP64 method (reported beside the chosen form)
+    barrier(ws)
+    ms64, prof64, diag64, out64 = run_gpu("fp64", max(3, args.steps // 4), args.warmup, fields)
+    steps64 = max(3, args.steps // 4)
+
+    barrier(ws)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ms, prof, diag, out = run_gpu("mixed", args.steps, args.warmup, fields)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = clk.stop()
+    ms_max = reduce_max(ms, ws)
+    value = N * args.steps * ws / (ms_max / 1e3)
+
+    # per-field error of the chosen form against the plain FP64 method after
+    # the same steps (the FP64 path is held to the oracle by the parity tests)
+    def relerr(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    err = {}
+    # rerun FP64 for exactly the mixed step count so the states line up
+    ms64b, _, _, ref = run_gpu("fp64", args.steps, args.warmup, fields, profile=False)
+    for k in ("phi_f", "phi_w", "xO", "xH", "xW", "sigma"):
+        err[k] = relerr(out[k], ref[k])
+
+    hbm, peak_kind = _load_peaks()
+    nd = 2
+    b_iter = CG_ITER_WORDS[nd] * 4 * N
+    b_init = CG_INIT_WORDS[nd] * 4 * N
+    cg_launches = prof["count"]["cg"]
+    cg_ms = prof["ms"]["cg"]
+    iters_timed = prof["cg_iters"]          # CG iterations of the timed solves
+    achieved = None
+    cg_bytes_per_launch = None
+    if cg_launches and cg_ms > 0:
+        bytes_total = b_iter * iters_timed + b_init * cg_launches
+        cg_bytes_per_launch = bytes_total / cg_launches
+        achieved = cg_bytes_per_launch / (cg_ms / cg_launches / 1e3) / 1e9
+
+    e2e_dt, h2d, d2h = run_e2e("mixed", args.e2e_steps, fields)
+    e2e_val = N * args.e2e_steps * ws / reduce_max(e2e_dt, ws)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        try:
+            cpu = cpu_baseline()
+        except Exception as e:  # noqa: BLE001
+            cpu = {"value": None, "error": str(e)[:200]}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 fields+operator, f64 reductions", "data": "synthetic", "config": cfg,
+        "fp64_plain": {"value": N * steps64 * ws / (reduce_max(ms64, ws) / 1e3), "unit": "cell-steps/s",
+                       "ms_per_step": ms64 / steps64, "cg_iters_per_step": prof64["cg_iters"] / steps64,
+                       "kernel_ms": prof64["ms"]},
+        "speedup_vs_fp64_plain": None,
+        "error_vs_fp64": err,
+        "cg": {"rtol_mixed": 1e-6, "rtol_fp64": 1e-10, "iters_timed": iters_timed,
+               "iters_per_step": iters_timed / args.steps if args.steps else None},
+        "kernel_ms": prof["ms"], "kernel_count": prof["count"],
+        "roofline": {"kernel": "k_cg (persistent PCG)", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
+                     "algorithmic_bytes_per_launch": cg_bytes_per_launch},
+        "e2e": {"value": e2e_val, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": prof["launches"],
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    line["speedup_vs_fp64_plain"] = value / line["fp64_plain"]["value"] if line["fp64_plain"]["value"] else None
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

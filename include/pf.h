@@ -1,0 +1,181 @@
+/*
+ * pf.h -- C ABI of the GB300 (sm_103a) library that advances the
+ * chemo-mechanical phase-field model of wuestite-to-iron reduction by
+ * hydrogen (Bai, Mianroodi et al., arXiv 2111.11538).
+ *
+ * One call of pf_step advances every field by one explicit time step per
+ * requested step:
+ *   1. mechanics: small-strain elasticity with the transformation eigenstrain
+ *      (Sec. 2.2, eq. RulFloDefLocAlt, linearised) and the plastic strain,
+ *      solved for the periodic displacement and the mean strain by a
+ *      Jacobi-preconditioned CG on Q1 voxel elements (Sec. 2.4, div P = 0);
+ *   2. per-cell stress and J2 radial return (Sec. 2.3, eq. PlaTwoJ;
+ *      Sec. 2.4, eq. RulFloPla);
+ *   3. explicit Euler update of the solid order parameter and of the oxygen,
+ *      hydrogen and water fractions with the reaction source terms
+ *      (Sec. 2.4, eq. FieRelDRI; Sec. 2.3.1, eqs. EmpModRea, forward-k),
+ *      then the reset of the supply (Dirichlet) cells (Sec. 4.3).
+ * Gas fraction phi_g = 1 - phi_f - phi_w is held fixed; the solid is split by
+ * theta = phi_f / (phi_f + phi_w) (the library's reading of Sec. 2.2 and
+ * Sec. 2.4, see the repository's design notes).
+ *
+ * Conventions
+ *   - Grids are periodic, dx = 1, row-major with x fastest: index
+ *     i + nx*(j + ny*k).  2D: nz is ignored (treated as 1).
+ *   - Host arrays are always FP64.  PF_MIXED stores fields in FP32 on the
+ *     device and converts on the way in and out.
+ *   - Every function returns an int status (PF_OK on success) and never
+ *     throws; pf_last_error(h) gives a text for the last failure.
+ *   - The library owns all device memory it allocates; it never keeps a
+ *     caller pointer after a call returns.
+ *   - Calls on one handle must not overlap; different handles are
+ *     independent.
+ */
+#ifndef PF_H
+#define PF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PF_OK = 0,
+    PF_EINVAL = 1,      /* bad argument or configuration                       */
+    PF_ENOMEM = 2,      /* device allocation failed                            */
+    PF_ECUDA = 3,       /* a CUDA call failed                                  */
+    PF_ENOTCONV = 4,    /* a CG solve hit cg_maxit; the step was still taken   */
+    PF_ENONFINITE = 5,  /* a non-finite value appeared in the fields           */
+    PF_ETIMEOUT = 6,    /* a bounded device-side wait gave up (no hang)        */
+    PF_ESTATE = 7       /* call out of order (e.g. pf_step before set_fields)  */
+};
+
+enum { PF_FP64 = 0, PF_MIXED = 1 };            /* device storage / arithmetic */
+enum { PF_WS_ZERO = 0, PF_WS_PREV = 1 };       /* CG initial guess            */
+enum { PF_HOST = 0, PF_DEVICE = 1 };           /* where caller arrays live    */
+
+/* Nondimensional model parameters (energy in units of the solid Young's
+ * modulus, length in cells, time in 1/(L E_s)); see Sec. 3 / Table 1. */
+typedef struct {
+    double c_chem;      /* R theta / (V_mol E_s): scale of the CALPHAD energies (Sec. 3.1) */
+    double w;           /* double-well height w_alpha                                   */
+    double eps_phi;     /* gradient-energy coefficient epsilon_alpha                    */
+    double kappa_O;     /* oxygen gradient-energy coefficient kappa_O                  */
+    double L;           /* phase mobility L_alpha                                       */
+    double D_O_s, D_O_g, D_H_s, D_H_g, D_W_s, D_W_g;   /* solid / gas diffusivities     */
+    double k_for;       /* reaction constant k_for                                      */
+    double xH_bc;       /* hydrogen fraction held on supply cells                       */
+    double E_s, nu;     /* solid Young's modulus and Poisson ratio                      */
+    double E_g_ratio;   /* gas / solid stiffness ratio                                  */
+    double eig0;        /* linearised transformation strain of ferrite (e.g. -0.05)     */
+    double sigma_Y;     /* initial yield stress                                         */
+    double H_hard;      /* isotropic hardening modulus                                  */
+    double prestress;   /* prescribed mean stress = -prestress * I                      */
+} pf_params;
+
+typedef struct {
+    int ndim;           /* 2 (plane strain) or 3                                        */
+    int nx, ny, nz;     /* grid size, each >= 2                                         */
+    int precision;      /* PF_FP64 or PF_MIXED                                          */
+    int mechanics;      /* 0: skip the solve (coupling terms zero)                      */
+    int plasticity;     /* 0: elastic, 1: J2 radial return                              */
+    int warm_start;     /* PF_WS_ZERO or PF_WS_PREV                                     */
+    int cg_maxit;       /* CG iteration cap per step (> 0)                              */
+    double cg_rtol;     /* stop when ||r||_2 <= cg_rtol ||b||_2                         */
+    double dt;          /* time step; <= 0 selects 0.2 x the stable limit               */
+    pf_params p;
+} pf_config;
+
+/* Field arrays, FP64, cell-major.  Any pointer may be NULL (skipped).
+ *   phi_f, phi_w, x_O, x_H, x_H2O : N each
+ *   u       : N*ndim, nodal periodic displacement, u[n*ndim + c]; node n is the
+ *             lower corner of cell n
+ *   Ebar    : 3 (2D: xx, yy, 2xy) or 6 (3D: xx, yy, zz, 2yz, 2xz, 2xy) mean strain
+ *   eps_p   : N*4 (2D: xx, yy, zz, xy) or N*6 (3D: xx, yy, zz, yz, xz, xy)
+ *   alpha   : N accumulated plastic strain
+ *   sigma   : output only, N*4 / N*6 like eps_p (from the last step's return map)
+ *   mobility: input only, N factor on L (grain scatter)
+ *   dirichlet: input only, N bytes, 1 = supply cell
+ * With PF_DEVICE every pointer is device memory holding the same FP64 layout. */
+typedef struct {
+    double *phi_f, *phi_w, *x_O, *x_H, *x_H2O;
+    double *u, *Ebar, *eps_p, *alpha, *sigma;
+    double *mobility;
+    unsigned char *dirichlet;
+} pf_fields;
+
+typedef struct {
+    double sum_O, sum_H, sum_H2O;   /* FP64 sums over cells of x_O, x_H, x_H2O    */
+    double removed_H2O;             /* water removed on supply cells, cumulative   */
+    double supplied_H;              /* hydrogen added on supply cells, cumulative  */
+    double sum_O_init;              /* sum of x_O at pf_set_fields                 */
+    double reduction_degree;        /* 1 - sum_O / sum_O_init (Sec. 4.2.1)         */
+    double cg_rel_residual;         /* last solve: ||r|| / ||b||                   */
+    int cg_iters_last, cg_iters_max;/* last solve / max over the last pf_step call */
+    long long cg_iters_total;       /* all solves since pf_set_fields              */
+    long long steps;                /* steps taken since pf_set_fields             */
+    double dt;                      /* time step in use                            */
+    int status;                     /* sticky status of the last pf_step call      */
+} pf_diag;
+
+typedef struct pf_handle pf_handle;
+
+/* Allocate device state for one grid.  Validates cfg (PF_EINVAL), chooses dt
+ * (pf_dt_stable x 0.2 when cfg->dt <= 0), allocates (PF_ENOMEM).  *out is set
+ * to NULL on failure. */
+int pf_create(const pf_config *cfg, pf_handle **out);
+
+/* Copy fields in.  phi_f, phi_w, x_O, x_H, x_H2O are required; the rest
+ * default to: u = 0, Ebar = 0, eps_p = 0, alpha = 0, mobility = 1,
+ * dirichlet = 0.  Resets the step counter and the diagnostics. */
+int pf_set_fields(pf_handle *h, const pf_fields *f, int where);
+
+/* Advance nsteps >= 0 steps on cudaStream (NULL: the handle's own stream),
+ * blocking until they are done.  Returns PF_ENOTCONV if any CG solve stopped
+ * at cg_maxit (the steps are still taken), PF_ENONFINITE if a non-finite
+ * value appeared, PF_ETIMEOUT if a bounded device wait gave up. */
+int pf_step(pf_handle *h, int nsteps, void *cudaStream);
+
+/* Copy fields out into caller arrays (FP64).  sigma is the stress of the last
+ * return map.  mobility / dirichlet are ignored. */
+int pf_get_fields(pf_handle *h, pf_fields *out, int where);
+
+int pf_get_diagnostics(pf_handle *h, pf_diag *out);
+
+/* Discrete free energy of the current state (FP64; cell bulk + well +
+ * elastic energy, face gradient energies), Sec. 2.2. */
+int pf_free_energy(pf_handle *h, double *out);
+
+/* Stable explicit time step for cfg (host only, no GPU needed). */
+double pf_dt_stable(const pf_config *cfg);
+
+/* Per-kernel device timing (CUDA events on the launch stream) and launch
+ * counts, for profiling.  Kernel classes of one step: */
+enum { PF_K_SETUP = 0,    /* moduli and eigenstress per cell              */
+       PF_K_CG = 1,       /* persistent PCG solve (one launch per step)   */
+       PF_K_RETURN = 2,   /* stress and J2 return per cell                */
+       PF_K_MU = 3,       /* oxygen chemical potential and mobility       */
+       PF_K_UPDATE = 4,   /* explicit Euler update of the fields          */
+       PF_K_NCLASS = 5 };
+
+typedef struct {
+    int enabled;
+    long long launches;            /* all kernels launched by pf_step since reset */
+    long long count[PF_K_NCLASS];  /* launches per class (timed only if enabled)  */
+    double ms[PF_K_NCLASS];        /* summed device time per class, ms            */
+    long long cg_iters;            /* CG iterations of the timed solves           */
+} pf_profile;
+
+/* Enable (on != 0) or disable event timing; either way the counters reset. */
+int pf_profile_enable(pf_handle *h, int on);
+int pf_profile_read(pf_handle *h, pf_profile *out);
+
+/* Device memory held by the handle, bytes. */
+long long pf_device_bytes(const pf_handle *h);
+
+const char *pf_last_error(const pf_handle *h);
+void pf_destroy(pf_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

@@ -1,0 +1,191 @@
+"""GB300-native coupled phase-field step for wuestite-to-iron reduction by
+hydrogen (arXiv 2111.11538): Python front end of the C ABI in include/pf.h.
+
+    from paper_2111_11538_gb300 import Simulation, workloads, inputs
+    fields = inputs.core_shell((64, 64), 20.0, 4.0)
+    sim = Simulation((64, 64), workloads.params(), precision="fp64")
+    sim.set_fields(fields)
+    sim.step(500)
+    out = sim.get_fields()
+
+All arithmetic of the step runs in the CUDA library; this module only moves
+arrays across the boundary.
+"""
+import ctypes
+
+import numpy as np
+
+from . import native
+from .native import (PF_DEVICE, PF_FP64, PF_HOST, PF_MIXED, PF_OK, PF_WS_PREV, PF_WS_ZERO,
+                     STATUS_NAMES, pf_config, pf_diag, pf_fields, pf_params)
+
+__all__ = ["Simulation", "PFError", "make_config", "native"]
+
+PARAM_NAMES = [f[0] for f in pf_params._fields_]
+
+
+class PFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+def make_config(shape, prm, precision="fp64", mechanics=None, plasticity=None, warm_start=None,
+                cg_rtol=None, cg_maxit=None, dt=None):
+    """Build a pf_config from a grid shape ((ny, nx) or (nz, ny, nx)) and a
+    parameter dict (see workloads.params)."""
+    c = pf_config()
+    c.ndim = len(shape)
+    if c.ndim == 2:
+        c.ny, c.nx = shape
+        c.nz = 1
+    elif c.ndim == 3:
+        c.nz, c.ny, c.nx = shape
+    else:
+        raise ValueError("shape must have 2 or 3 entries")
+    c.precision = {"fp64": PF_FP64, "mixed": PF_MIXED}[precision]
+    c.mechanics = int(prm.get("mechanics", 1) if mechanics is None else mechanics)
+    c.plasticity = int(prm.get("plasticity", 0) if plasticity is None else plasticity)
+    ws = prm.get("warm_start", 1) if warm_start is None else warm_start
+    c.warm_start = {"zero": PF_WS_ZERO, "prev": PF_WS_PREV}.get(ws, ws)
+    c.cg_rtol = float(prm.get("cg_rtol", 1e-10) if cg_rtol is None else cg_rtol)
+    c.cg_maxit = int(prm.get("cg_maxit", 20000) if cg_maxit is None else cg_maxit)
+    c.dt = float(prm.get("dt", 0.0) if dt is None else dt)
+    for k in PARAM_NAMES:
+        setattr(c.p, k, float(prm[k]))
+    return c
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+class Simulation:
+    """One grid advanced by the CUDA library.
+
+    Host arrays are numpy float64 (cell-major, x fastest).  ``set_fields`` and
+    ``get_fields`` also accept / fill torch CUDA float64 tensors when
+    ``where="device"``.
+    """
+
+    def __init__(self, shape, prm, precision="fp64", **kw):
+        self.shape = tuple(shape)
+        self.ndim = len(self.shape)
+        self.N = int(np.prod(self.shape))
+        self.cfg = make_config(self.shape, prm, precision=precision, **kw)
+        rc, h = native.pf_create(self.cfg)
+        if rc != PF_OK:
+            raise PFError(rc, native.pf_last_error(None))
+        self.h = h
+        self.np_ = 4 if self.ndim == 2 else 6
+        self.nv = 3 if self.ndim == 2 else 6
+
+    # ------------------------------------------------------------------
+    def _check(self, rc):
+        if rc != PF_OK:
+            raise PFError(rc, native.pf_last_error(self.h))
+        return rc
+
+    def set_fields(self, fields, where="host"):
+        f = pf_fields()
+        keep = []
+        if where == "host":
+            def put(name, key, dtype=np.float64, shape=None):
+                v = fields.get(key)
+                if v is None:
+                    return
+                a = np.ascontiguousarray(v, dtype=dtype)
+                if shape is not None and a.size != int(np.prod(shape)):
+                    raise ValueError("%s has %d values, expected %d" % (key, a.size, int(np.prod(shape))))
+                keep.append(a)
+                if dtype == np.uint8:
+                    setattr(f, name, a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+                else:
+                    setattr(f, name, _dptr(a))
+            for name, key in (("phi_f", "phi_f"), ("phi_w", "phi_w"), ("x_O", "xO"), ("x_H", "xH"),
+                              ("x_H2O", "xW"), ("alpha", "alpha"), ("mobility", "mob")):
+                put(name, key, shape=(self.N,))
+            put("u", "u", shape=(self.N, self.ndim))
+            put("eps_p", "eps_p", shape=(self.N, self.np_))
+            put("Ebar", "Ebar", shape=(self.nv,))
+            put("dirichlet", "mask", dtype=np.uint8, shape=(self.N,))
+            rc = native.pf_set_fields(self.h, f, PF_HOST)
+        else:
+            for name, key in (("phi_f", "phi_f"), ("phi_w", "phi_w"), ("x_O", "xO"), ("x_H", "xH"),
+                              ("x_H2O", "xW"), ("alpha", "alpha"), ("mobility", "mob"), ("u", "u"),
+                              ("eps_p", "eps_p"), ("Ebar", "Ebar")):
+                t = fields.get(key)
+                if t is not None:
+                    t = t.contiguous()
+                    keep.append(t)
+                    setattr(f, name, ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_double)))
+            t = fields.get("mask")
+            if t is not None:
+                t = t.contiguous()
+                keep.append(t)
+                f.dirichlet = ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_ubyte))
+            rc = native.pf_set_fields(self.h, f, PF_DEVICE)
+        return self._check(rc)
+
+    def step(self, n=1, stream=None, check=True):
+        rc = native.pf_step(self.h, n, stream)
+        if check:
+            self._check(rc)
+        return rc
+
+    def get_fields(self, keys=("phi_f", "phi_w", "xO", "xH", "xW", "u", "Ebar", "eps_p", "alpha", "sigma")):
+        f = pf_fields()
+        out = {}
+        shp = {"u": self.shape + (self.ndim,), "eps_p": self.shape + (self.np_,),
+               "sigma": self.shape + (self.np_,), "Ebar": (self.nv,)}
+        names = {"phi_f": "phi_f", "phi_w": "phi_w", "xO": "x_O", "xH": "x_H", "xW": "x_H2O",
+                 "u": "u", "Ebar": "Ebar", "eps_p": "eps_p", "alpha": "alpha", "sigma": "sigma"}
+        for k in keys:
+            out[k] = np.zeros(shp.get(k, self.shape))
+            setattr(f, names[k], _dptr(out[k]))
+        self._check(native.pf_get_fields(self.h, f, PF_HOST))
+        return out
+
+    def diagnostics(self):
+        rc, d = native.pf_get_diagnostics(self.h)
+        self._check(rc)
+        return {k: getattr(d, k) for k, _ in pf_diag._fields_}
+
+    def free_energy(self):
+        rc, v = native.pf_free_energy(self.h)
+        self._check(rc)
+        return v
+
+    @property
+    def dt(self):
+        return self.diagnostics()["dt"]
+
+    def profile(self, on=True):
+        self._check(native.pf_profile_enable(self.h, on))
+
+    def profile_read(self):
+        rc, p = native.pf_profile_read(self.h)
+        self._check(rc)
+        return {"launches": p.launches, "cg_iters": p.cg_iters,
+                "count": {k: p.count[i] for i, k in enumerate(native.KERNEL_CLASSES)},
+                "ms": {k: p.ms[i] for i, k in enumerate(native.KERNEL_CLASSES)}}
+
+    def device_bytes(self):
+        return native.pf_device_bytes(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            native.pf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

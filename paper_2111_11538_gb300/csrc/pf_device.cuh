@@ -1,0 +1,298 @@
+// Device code of the coupled phase-field step (sm_103a).
+//
+// Storage: structure of arrays, row-major with x fastest (cell / node index
+// i + nx*(j + ny*k)); node n is the lower corner of cell n.  T is the storage
+// and arithmetic type of the fields (double for the plain FP64 method, float
+// for the mixed method); reductions are carried in FP64 (per thread with
+// compensated FP32 sums in the mixed method, then FP64 across threads).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pfdev {
+
+constexpr int PSTRIDE = 24;       // doubles per block in a partials array
+
+// ---------------------------------------------------------------------------
+// Parameters (by value to every kernel)
+// ---------------------------------------------------------------------------
+struct Params {
+    int ndim, nx, ny, nz;
+    long long N;
+    double dt, c, w, eps, kappa, L;
+    double DOs, DOg, DHs, DHg, DWs, DWg;
+    double kfor, xHbc;
+    double Ks, Gs, Kg, Gg;          // solid / gas bulk and shear moduli
+    double eig0, sY, Hh, prestress;
+    int plasticity;
+};
+
+// Element tables (Q1 unit square / cube, exact 2^d-point Gauss integration),
+// written once per device by the host.
+//   K?2: 8x8 (2D), K?3: 24x24 (3D), dof index = node*d + comp
+//   Bb?: average shape-function gradient over the element, [node][axis]
+//   Kdiag: the (equal) diagonal entries of K_lambda and K_mu
+// Each table exists in double and float so that no FP64 -> FP32 conversion
+// sits in the FP32 inner loops.
+template <typename T> struct Tab {
+    T Kl2[64], Km2[64], Kl3[576], Km3[576];
+    T Bb2[8], Bb3[24];
+    T Kdiag[4];   // [0],[1]: 2D lambda, mu; [2],[3]: 3D lambda, mu
+};
+__constant__ Tab<double> cTabD;
+__constant__ Tab<float> cTabF;
+
+template <typename T> __device__ __forceinline__ const Tab<T> &tab();
+template <> __device__ __forceinline__ const Tab<double> &tab<double>() { return cTabD; }
+template <> __device__ __forceinline__ const Tab<float> &tab<float>() { return cTabF; }
+
+template <typename T, int D> __device__ __forceinline__ T Kl(int r, int c) { return D == 2 ? tab<T>().Kl2[r * 8 + c] : tab<T>().Kl3[r * 24 + c]; }
+template <typename T, int D> __device__ __forceinline__ T Km(int r, int c) { return D == 2 ? tab<T>().Km2[r * 8 + c] : tab<T>().Km3[r * 24 + c]; }
+template <typename T, int D> __device__ __forceinline__ T Bb(int a, int k) { return D == 2 ? tab<T>().Bb2[a * 2 + k] : tab<T>().Bb3[a * 3 + k]; }
+template <typename T, int D> __device__ __forceinline__ T KdL() { return D == 2 ? tab<T>().Kdiag[0] : tab<T>().Kdiag[2]; }
+template <typename T, int D> __device__ __forceinline__ T KdM() { return D == 2 ? tab<T>().Kdiag[1] : tab<T>().Kdiag[3]; }
+
+template <int D> struct Dims { static constexpr int NV = D == 2 ? 3 : 6; static constexpr int NP = D == 2 ? 4 : 6; static constexpr int NN = 1 << D; };
+
+// ---------------------------------------------------------------------------
+// Scalars of one mechanics solve, in device memory
+// ---------------------------------------------------------------------------
+struct Scalars {
+    double E[6];          // mean strain (Voigt, engineering shears) = Ebar
+    double relres;        // final ||r|| / ||b||
+    double bnorm;
+    int iters;
+    int status;           // PF_* code set by device code (0 = ok)
+    int pad[2];
+};
+
+struct Diag {
+    double sumO, sumH, sumW;
+    double removedW, suppliedH;
+    long long cg_total;
+    int cg_last, cg_max;
+    int status;
+    int pad;
+};
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T ldg_(const T *p) { return __ldg(p); }
+template <typename T> __device__ __forceinline__ T ldcg_(const T *p) { return __ldcg(p); }
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Per-thread accumulator: plain FP64 for double, compensated FP32 (sum and
+// error term kept separately, product errors from fma) for float.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ void addprod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        float t = s + x;
+        float bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
+        s = t;
+    }
+    __device__ __forceinline__ void addprod(float a, float b)
+    {
+        float p = a * b;
+        float e = fmaf(a, b, -p);
+        add(p);
+        c += e;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Block-wide sum of K values; thread 0 writes them to dst[0..K).
+template <int K>
+__device__ void block_sum_store(double (&v)[K], double *dst)
+{
+    __shared__ double sh[K][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = warp_sum(v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) sh[k][wid] = v[k];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double s = lane < nw ? sh[k][lane] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) dst[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Sum of partials[b*PSTRIDE + k] over b < nb in a fixed order; every block
+// that calls it gets bit-identical results.
+template <int K>
+__device__ void grid_sum(const double *partials, int nb, int off, double (&out)[K])
+{
+    __shared__ double res[K];
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double s = 0.0;
+            for (int b = lane; b < nb; b += 32) s += __ldcg(partials + (size_t)b * PSTRIDE + off + k);
+            s = warp_sum(s);
+            if (lane == 0) res[k] = s;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) out[k] = res[k];
+    __syncthreads();
+}
+
+// Grid barrier for a cooperative launch.  The wait is bounded: after
+// SPIN_LIMIT polls the block records PF_ETIMEOUT (6) in *err and the caller
+// returns.  Returns false on timeout.
+constexpr long long SPIN_LIMIT = 1LL << 24;
+
+__device__ bool grid_barrier(unsigned int *count, unsigned int *gen, int *err)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int *vgen = gen;
+        unsigned int g = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g) {
+                if (++spins > SPIN_LIMIT) { atomicExch(err, 6); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Model functions (Sec. 3.1 energies, R1 double well)
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T hfun(T x) { return x * x * x * (x * (T(6) * x - T(15)) + T(10)); }
+template <typename T> __device__ __forceinline__ T hder(T x) { T y = x * (T(1) - x); return T(30) * y * y; }
+template <typename T> __device__ __forceinline__ T mfun(T x) { T y = x * (T(1) - x); return y * y; }
+template <typename T> __device__ __forceinline__ T mder(T x) { return T(2) * x * (T(1) - x) * (T(1) - T(2) * x); }
+
+// CALPHAD polynomials and derivatives (scaled by V_mol / R theta).
+template <typename T> __device__ __forceinline__ T f_fe(T x) { return (((T(163.708) * x - T(182.510)) * x + T(90.573)) * x - T(36.031)) * x - T(4.372); }
+template <typename T> __device__ __forceinline__ T f_fe1(T x) { return ((T(654.832) * x - T(547.530)) * x + T(181.146)) * x - T(36.031); }
+template <typename T> __device__ __forceinline__ T f_fe2(T x) { return (T(1964.496) * x - T(1095.060)) * x + T(181.146); }
+template <typename T> __device__ __forceinline__ T f_wu(T x) { return (T(173.263) * x - T(213.460)) * x + T(41.953); }
+template <typename T> __device__ __forceinline__ T f_wu1(T x) { return T(346.526) * x - T(213.460); }
+template <typename T> __device__ __forceinline__ T f_wu2(T) { return T(346.526); }
+template <typename T> __device__ __forceinline__ T f_ga(T x) { return T(1000) * x * x; }
+template <typename T> __device__ __forceinline__ T f_ga1(T x) { return T(2000) * x; }
+template <typename T> __device__ __forceinline__ T f_ga2(T) { return T(2000); }
+
+// Phase weights W_f, W_w, W_g from theta and the fixed gas fraction.
+template <typename T>
+__device__ __forceinline__ void phase_weights(T th, T pg, T &Wf, T &Ww, T &Wg)
+{
+    T hg = hfun(pg), ht = hfun(th);
+    T sol = T(1) - hg;
+    Wf = sol * ht;
+    Ww = sol - Wf;
+    Wg = hg;
+}
+
+template <int D> __device__ __forceinline__ void cell_coords(const Params &P, long long n, int &i, int &j, int &k)
+{
+    i = (int)(n % P.nx);
+    long long r = n / P.nx;
+    j = (int)(r % P.ny);
+    k = D == 3 ? (int)(r / P.ny) : 0;
+}
+__device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+template <int D> __device__ __forceinline__ long long lin(const Params &P, int i, int j, int k)
+{
+    return (long long)wrap(i, P.nx) + (long long)P.nx * ((long long)wrap(j, P.ny) + (D == 3 ? (long long)P.ny * wrap(k, P.nz) : 0LL));
+}
+
+// Isotropic stiffness in Voigt form (plane strain in-plane block in 2D).
+template <typename T, int D>
+__device__ __forceinline__ void voigt_stress(T lam, T mu, const T *e, T *s)
+{
+    if constexpr (D == 2) {
+        T tr = e[0] + e[1];
+        s[0] = lam * tr + T(2) * mu * e[0];
+        s[1] = lam * tr + T(2) * mu * e[1];
+        s[2] = mu * e[2];
+    } else {
+        T tr = e[0] + e[1] + e[2];
+        s[0] = lam * tr + T(2) * mu * e[0];
+        s[1] = lam * tr + T(2) * mu * e[1];
+        s[2] = lam * tr + T(2) * mu * e[2];
+        s[3] = mu * e[3]; s[4] = mu * e[4]; s[5] = mu * e[5];
+    }
+}
+
+// Average (= centre) strain of an element from nodal values u[b][comp].
+template <typename T, int D>
+__device__ __forceinline__ void avg_strain(const T (*u)[D], T *e)
+{
+    T g[D][D];
+#pragma unroll
+    for (int i = 0; i < D; i++)
+#pragma unroll
+        for (int k = 0; k < D; k++) g[i][k] = T(0);
+#pragma unroll
+    for (int b = 0; b < (1 << D); b++)
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            T bb = Bb<T, D>(b, k);
+#pragma unroll
+            for (int i = 0; i < D; i++) g[i][k] += bb * u[b][i];
+        }
+    if constexpr (D == 2) {
+        e[0] = g[0][0]; e[1] = g[1][1]; e[2] = g[0][1] + g[1][0];
+    } else {
+        e[0] = g[0][0]; e[1] = g[1][1]; e[2] = g[2][2];
+        e[3] = g[1][2] + g[2][1]; e[4] = g[0][2] + g[2][0]; e[5] = g[0][1] + g[1][0];
+    }
+}
+
+// (Bbar_a^T s) for node a of an element with Voigt stress s.
+template <typename T, int D>
+__device__ __forceinline__ void bbar_t(int a, const T *s, T *out)
+{
+    T bx = Bb<T, D>(a, 0), by = Bb<T, D>(a, 1);
+    if constexpr (D == 2) {
+        out[0] = bx * s[0] + by * s[2];
+        out[1] = by * s[1] + bx * s[2];
+    } else {
+        T bz = Bb<T, D>(a, 2);
+        out[0] = bx * s[0] + by * s[5] + bz * s[4];
+        out[1] = by * s[1] + bx * s[5] + bz * s[3];
+        out[2] = bz * s[2] + by * s[3] + bx * s[4];
+    }
+}
+
+} // namespace pfdev

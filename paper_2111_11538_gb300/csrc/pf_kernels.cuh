@@ -1,0 +1,682 @@
+// Kernels of the coupled step.  See pf_device.cuh for layout and helpers.
+#pragma once
+#include "pf_device.cuh"
+
+namespace pfdev {
+
+// ---------------------------------------------------------------------------
+// K2: per-cell Lame parameters and eigenstress C : eps* (Voigt) for the
+// mechanics right-hand side.  eps* = eig0 W_f I + eps_p (linearised
+// transformation strain of Sec. 2.2, plus the plastic strain).
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+struct FieldPtrs {
+    const T *theta, *phig, *xO, *xH, *xW, *mob;
+    const unsigned char *mask;
+    T *theta_o, *xO_o, *xH_o, *xW_o;
+    T *muO, *MO;
+    T *trE, *devE2;
+    T *lam, *mu;
+    T *sig[6];
+    T *ep[6];
+    T *alpha;
+    T *sigma_out[6];
+    T *u[3];
+};
+
+template <typename T, int D>
+__global__ void k_setup(Params P, FieldPtrs<T, D> F)
+{
+    constexpr int NV = Dims<D>::NV;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.N; c += (long long)gridDim.x * blockDim.x) {
+        T Wf, Ww, Wg;
+        phase_weights(F.theta[c], F.phig[c], Wf, Ww, Wg);
+        T K = (Wf + Ww) * T(P.Ks) + Wg * T(P.Kg);
+        T G = (Wf + Ww) * T(P.Gs) + Wg * T(P.Gg);
+        T lam = K - T(2.0 / 3.0) * G;
+        F.lam[c] = lam;
+        F.mu[c] = G;
+        T e0 = T(P.eig0) * Wf;
+        // eigenstrain tensor components xx, yy, zz, yz, xz, xy
+        T es[6];
+        if constexpr (D == 2) {
+            es[0] = e0 + F.ep[0][c]; es[1] = e0 + F.ep[1][c]; es[2] = e0 + F.ep[2][c];
+            es[3] = T(0); es[4] = T(0); es[5] = F.ep[3][c];
+        } else {
+#pragma unroll
+            for (int v = 0; v < 6; v++) es[v] = (v < 3 ? e0 : T(0)) + F.ep[v][c];
+        }
+        T tr = es[0] + es[1] + es[2];
+        if constexpr (D == 2) {
+            F.sig[0][c] = lam * tr + T(2) * G * es[0];
+            F.sig[1][c] = lam * tr + T(2) * G * es[1];
+            F.sig[2][c] = T(2) * G * es[5];
+        } else {
+#pragma unroll
+            for (int v = 0; v < 3; v++) F.sig[v][c] = lam * tr + T(2) * G * es[v];
+#pragma unroll
+            for (int v = 3; v < 6; v++) F.sig[v][c] = T(2) * G * es[v];
+        }
+        (void)NV;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K3/K4: persistent cooperative Jacobi-PCG for the periodic fluctuation u and
+// the mean strain E (Voigt), with the operator
+//     A = sum_e int [B | I]^T D_e [B | I]
+// applied matrix-free, node by node, from the element tables.  Convergence is
+// decided on the device; the host launches once per solve.
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+struct CGArgs {
+    Params P;
+    const T *lam, *mu;
+    const T *sig[6];
+    T *x[3], *r[3], *p[3], *q[3];
+    T *diag;
+    double *partials;
+    unsigned int *bar_count, *bar_gen;
+    Scalars *sc;
+    Diag *dg;
+    double rtol;
+    int maxit;
+    int warm;
+};
+
+// Voigt stiffness D(lam, mu) times e (double, used for the few mean-strain dofs)
+template <int D>
+__device__ __forceinline__ void dmat_mul(double lam, double mu, const double *e, double *s)
+{
+    if constexpr (D == 2) {
+        double tr = e[0] + e[1];
+        s[0] = lam * tr + 2 * mu * e[0]; s[1] = lam * tr + 2 * mu * e[1]; s[2] = mu * e[2];
+    } else {
+        double tr = e[0] + e[1] + e[2];
+        for (int v = 0; v < 3; v++) s[v] = lam * tr + 2 * mu * e[v];
+        for (int v = 3; v < 6; v++) s[v] = mu * e[v];
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void node_of(int a, int &ox, int &oy, int &oz)
+{
+    ox = a & 1; oy = (a >> 1) & 1; oz = D == 3 ? (a >> 2) & 1 : 0;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_cg(CGArgs<T, D> A)
+{
+    constexpr int NV = Dims<D>::NV, NN = Dims<D>::NN;
+    const Params &P = A.P;
+    const long long N = P.N;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long st = (long long)gridDim.x * blockDim.x;
+    const int nb = gridDim.x;
+    double *myp = A.partials + (size_t)blockIdx.x * PSTRIDE;
+    int *err = &A.sc->status;
+
+    // ---------------- init: b, diag, r = b - A x0, sums over cells ----------
+    double XE[6] = {0, 0, 0, 0, 0, 0};
+    if (A.warm) {
+        for (int v = 0; v < NV; v++) XE[v] = A.sc->E[v];
+    }
+    {
+        Acc<T> bb, rz, rr, sl, sm, ss[NV], de[NV];
+        for (long long n = t0; n < N; n += st) {
+            int i, j, k;
+            cell_coords<D>(P, n, i, j, k);
+            T b[D], ax[D];
+#pragma unroll
+            for (int d = 0; d < D; d++) { b[d] = T(0); ax[d] = T(0); }
+            T dgn = T(0);
+#pragma unroll
+            for (int a = 0; a < NN; a++) {
+                int ox, oy, oz;
+                node_of<D>(a, ox, oy, oz);
+                const int ci = i - ox, cj = j - oy, ck = k - oz;
+                const long long c = lin<D>(P, ci, cj, ck);
+                const T l = A.lam[c], m = A.mu[c];
+                dgn += l * KdL<T, D>() + m * KdM<T, D>();
+                T s[NV], bt[D];
+#pragma unroll
+                for (int v = 0; v < NV; v++) s[v] = A.sig[v][c];
+                bbar_t<T, D>(a, s, bt);
+#pragma unroll
+                for (int d = 0; d < D; d++) b[d] += bt[d];
+                if (A.warm) {
+                    T ue[NN][D];
+#pragma unroll
+                    for (int bn = 0; bn < NN; bn++) {
+                        int px, py, pz;
+                        node_of<D>(bn, px, py, pz);
+                        const long long mm = lin<D>(P, ci + px, cj + py, ck + pz);
+#pragma unroll
+                        for (int d = 0; d < D; d++) ue[bn][d] = A.x[d][mm];
+                    }
+#pragma unroll
+                    for (int co = 0; co < D; co++) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int bn = 0; bn < NN; bn++)
+#pragma unroll
+                            for (int cc = 0; cc < D; cc++)
+                                acc += (l * Kl<T, D>(a * D + co, bn * D + cc) + m * Km<T, D>(a * D + co, bn * D + cc)) * ue[bn][cc];
+                        ax[co] += acc;
+                    }
+                    T e[NV], se[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; v++) e[v] = (T)XE[v];
+                    voigt_stress<T, D>(l, m, e, se);
+                    bbar_t<T, D>(a, se, bt);
+#pragma unroll
+                    for (int d = 0; d < D; d++) ax[d] += bt[d];
+                    if (a == 0) {      // own cell: mean-strain row of A x0
+                        T eb[NV];
+                        avg_strain<T, D>(ue, eb);
+                        voigt_stress<T, D>(l, m, eb, se);
+#pragma unroll
+                        for (int v = 0; v < NV; v++) de[v].add(se[v]);
+                    }
+                }
+                if (a == 0) {
+                    sl.add(l);
+                    sm.add(m);
+#pragma unroll
+                    for (int v = 0; v < NV; v++) ss[v].add(s[v]);
+                }
+            }
+            A.diag[n] = dgn;
+#pragma unroll
+            for (int d = 0; d < D; d++) {
+                if (!A.warm) A.x[d][n] = T(0);
+                const T rv = b[d] - ax[d];
+                A.r[d][n] = rv;
+                bb.addprod(b[d], b[d]);
+                rr.addprod(rv, rv);
+                rz.addprod(rv, rv / dgn);
+            }
+        }
+        double v[17];
+        v[0] = bb.value(); v[1] = rz.value(); v[2] = rr.value(); v[3] = sl.value(); v[4] = sm.value();
+#pragma unroll
+        for (int q = 0; q < 6; q++) { v[5 + q] = q < NV ? ss[q].value() : 0.0; v[11 + q] = q < NV ? de[q].value() : 0.0; }
+        block_sum_store<17>(v, myp);
+    }
+    if (!grid_barrier(A.bar_count, A.bar_gen, err)) return;
+    double tot[17];
+    grid_sum<17>(A.partials, nb, 0, tot);
+    const double Sl = tot[3], Sm = tot[4];
+    double DiagE[6], BE[6], RE[6], ZE[6], PE[6], QE[6], AXE[6];
+    {
+        double unit[6];
+        for (int v = 0; v < NV; v++) {
+            for (int w = 0; w < NV; w++) unit[w] = (w == v) ? 1.0 : 0.0;
+            double s[6];
+            dmat_mul<D>(Sl, Sm, unit, s);
+            DiagE[v] = s[v];
+        }
+        dmat_mul<D>(Sl, Sm, XE, AXE);
+    }
+    double bb = tot[0], rz = tot[1], rr = tot[2];
+    for (int v = 0; v < NV; v++) {
+        BE[v] = tot[5 + v] + (v < D ? (double)N * (-P.prestress) : 0.0);
+        RE[v] = BE[v] - (tot[11 + v] + AXE[v]);
+        ZE[v] = RE[v] / DiagE[v];
+        bb += BE[v] * BE[v];
+        rz += RE[v] * ZE[v];
+        rr += RE[v] * RE[v];
+        PE[v] = 0.0;
+    }
+    const double bnorm = sqrt(bb);
+    int it = 0;
+    bool conv = false;
+    if (bnorm == 0.0) {
+        for (long long n = t0; n < N; n += st)
+            for (int d = 0; d < D; d++) A.x[d][n] = T(0);
+        for (int v = 0; v < NV; v++) XE[v] = 0.0;
+        rr = 0.0;
+        conv = true;
+    } else if (sqrt(rr) <= A.rtol * bnorm) {
+        conv = true;
+    }
+    double beta = 0.0;
+    while (!conv && it < A.maxit) {
+        // ---- phase A: p = z + beta p -------------------------------------
+        const T tb = (T)beta;
+        for (long long n = t0; n < N; n += st) {
+            const T inv = T(1) / A.diag[n];
+#pragma unroll
+            for (int d = 0; d < D; d++) {
+                const T z = A.r[d][n] * inv;
+                A.p[d][n] = it == 0 ? z : z + tb * A.p[d][n];
+            }
+        }
+        for (int v = 0; v < NV; v++) PE[v] = (it == 0) ? ZE[v] : ZE[v] + beta * PE[v];
+        if (!grid_barrier(A.bar_count, A.bar_gen, err)) return;
+        // ---- phase B: q = A p, p.q, mean-strain row ------------------------
+        {
+            Acc<T> pq, de[NV];
+            T pe[6];
+#pragma unroll
+            for (int v = 0; v < NV; v++) pe[v] = (T)PE[v];
+            for (long long n = t0; n < N; n += st) {
+                int i, j, k;
+                cell_coords<D>(P, n, i, j, k);
+                T qv[D];
+#pragma unroll
+                for (int d = 0; d < D; d++) qv[d] = T(0);
+#pragma unroll
+                for (int a = 0; a < NN; a++) {
+                    int ox, oy, oz;
+                    node_of<D>(a, ox, oy, oz);
+                    const int ci = i - ox, cj = j - oy, ck = k - oz;
+                    const long long c = lin<D>(P, ci, cj, ck);
+                    const T l = A.lam[c], m = A.mu[c];
+                    T ue[NN][D];
+#pragma unroll
+                    for (int bn = 0; bn < NN; bn++) {
+                        int px, py, pz;
+                        node_of<D>(bn, px, py, pz);
+                        const long long mm = lin<D>(P, ci + px, cj + py, ck + pz);
+#pragma unroll
+                        for (int d = 0; d < D; d++) ue[bn][d] = __ldcg(A.p[d] + mm);
+                    }
+#pragma unroll
+                    for (int co = 0; co < D; co++) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int bn = 0; bn < NN; bn++)
+#pragma unroll
+                            for (int cc = 0; cc < D; cc++)
+                                acc += (l * Kl<T, D>(a * D + co, bn * D + cc) + m * Km<T, D>(a * D + co, bn * D + cc)) * ue[bn][cc];
+                        qv[co] += acc;
+                    }
+                    T se[NV], bt[D];
+                    voigt_stress<T, D>(l, m, pe, se);
+                    bbar_t<T, D>(a, se, bt);
+#pragma unroll
+                    for (int d = 0; d < D; d++) qv[d] += bt[d];
+                    if (a == 0) {
+                        T eb[NV];
+                        avg_strain<T, D>(ue, eb);
+                        voigt_stress<T, D>(l, m, eb, se);
+#pragma unroll
+                        for (int v = 0; v < NV; v++) de[v].add(se[v]);
+                    }
+                }
+#pragma unroll
+                for (int d = 0; d < D; d++) {
+                    A.q[d][n] = qv[d];
+                    pq.addprod(A.p[d][n], qv[d]);
+                }
+            }
+            double v[7];
+            v[0] = pq.value();
+#pragma unroll
+            for (int q = 0; q < 6; q++) v[1 + q] = q < NV ? de[q].value() : 0.0;
+            block_sum_store<7>(v, myp);
+        }
+        if (!grid_barrier(A.bar_count, A.bar_gen, err)) return;
+        double tb7[7];
+        grid_sum<7>(A.partials, nb, 0, tb7);
+        double pqt = tb7[0];
+        {
+            double s[6];
+            dmat_mul<D>(Sl, Sm, PE, s);
+            for (int v = 0; v < NV; v++) {
+                QE[v] = tb7[1 + v] + s[v];
+                pqt += PE[v] * QE[v];
+            }
+        }
+        const double alpha = rz / pqt;
+        // ---- phase C: x += alpha p, r -= alpha q, r.z, r.r ----------------
+        {
+            const T ta = (T)alpha;
+            Acc<T> rzA, rrA;
+            for (long long n = t0; n < N; n += st) {
+                const T inv = T(1) / A.diag[n];
+#pragma unroll
+                for (int d = 0; d < D; d++) {
+                    const T pv = A.p[d][n];
+                    A.x[d][n] += ta * pv;
+                    const T rv = A.r[d][n] - ta * A.q[d][n];
+                    A.r[d][n] = rv;
+                    rzA.addprod(rv, rv * inv);
+                    rrA.addprod(rv, rv);
+                }
+            }
+            double v[2] = {rzA.value(), rrA.value()};
+            block_sum_store<2>(v, myp + 8);
+        }
+        for (int v = 0; v < NV; v++) {
+            XE[v] += alpha * PE[v];
+            RE[v] -= alpha * QE[v];
+            ZE[v] = RE[v] / DiagE[v];
+        }
+        if (!grid_barrier(A.bar_count, A.bar_gen, err)) return;
+        double t2[2];
+        grid_sum<2>(A.partials, nb, 8, t2);
+        double rzn = t2[0], rrn = t2[1];
+        for (int v = 0; v < NV; v++) { rzn += RE[v] * ZE[v]; rrn += RE[v] * RE[v]; }
+        it++;
+        rr = rrn;
+        if (sqrt(rrn) <= A.rtol * bnorm) { conv = true; break; }
+        beta = rzn / rz;
+        rz = rzn;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int v = 0; v < NV; v++) A.sc->E[v] = XE[v];
+        A.sc->iters = it;
+        A.sc->bnorm = bnorm;
+        A.sc->relres = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+        if (!conv) atomicMax(err, 4);
+        A.dg->cg_last = it;
+        if (it > A.dg->cg_max) A.dg->cg_max = it;
+        A.dg->cg_total += it;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: per-cell stress and J2 radial return (Sec. 2.3 PlaTwoJ, small-strain
+// form): yield |dev sigma| - sqrt(2/3)(sigma_Y + H a) <= 0, flow along
+// dev sigma / |dev sigma|, da = dlambda = f / (2G + sqrt(2/3) H).
+// Outputs eps_p, alpha, the coupling scalars t = tr eps_e and s = |dev eps_e|^2
+// and (on request) the stress.
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__global__ void k_return(Params P, FieldPtrs<T, D> F, const Scalars *sc, int want_sigma)
+{
+    constexpr int NN = Dims<D>::NN, NV = Dims<D>::NV;
+    double Ed[6];
+    for (int v = 0; v < NV; v++) Ed[v] = sc->E[v];
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.N; c += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_coords<D>(P, c, i, j, k);
+        T ue[NN][D];
+#pragma unroll
+        for (int b = 0; b < NN; b++) {
+            int px, py, pz;
+            node_of<D>(b, px, py, pz);
+            const long long m = lin<D>(P, i + px, j + py, k + pz);
+#pragma unroll
+            for (int d = 0; d < D; d++) ue[b][d] = F.u[d][m];
+        }
+        T ev[NV];
+        avg_strain<T, D>(ue, ev);
+#pragma unroll
+        for (int v = 0; v < NV; v++) ev[v] += (T)Ed[v];
+        // total strain tensor xx, yy, zz, yz, xz, xy
+        T et[6];
+        if constexpr (D == 2) {
+            et[0] = ev[0]; et[1] = ev[1]; et[2] = T(0); et[3] = T(0); et[4] = T(0); et[5] = T(0.5) * ev[2];
+        } else {
+            et[0] = ev[0]; et[1] = ev[1]; et[2] = ev[2];
+            et[3] = T(0.5) * ev[3]; et[4] = T(0.5) * ev[4]; et[5] = T(0.5) * ev[5];
+        }
+        T Wf, Ww, Wg;
+        phase_weights(F.theta[c], F.phig[c], Wf, Ww, Wg);
+        const T K = (Wf + Ww) * T(P.Ks) + Wg * T(P.Kg);
+        const T G = (Wf + Ww) * T(P.Gs) + Wg * T(P.Gg);
+        const T e0 = T(P.eig0) * Wf;
+        T ep[6];
+        if constexpr (D == 2) {
+            ep[0] = F.ep[0][c]; ep[1] = F.ep[1][c]; ep[2] = F.ep[2][c]; ep[3] = T(0); ep[4] = T(0); ep[5] = F.ep[3][c];
+        } else {
+#pragma unroll
+            for (int v = 0; v < 6; v++) ep[v] = F.ep[v][c];
+        }
+        T ee[6];
+#pragma unroll
+        for (int v = 0; v < 6; v++) ee[v] = et[v] - ep[v] - (v < 3 ? e0 : T(0));
+        T tr = ee[0] + ee[1] + ee[2];
+        T dev[6];
+#pragma unroll
+        for (int v = 0; v < 6; v++) dev[v] = ee[v] - (v < 3 ? tr / T(3) : T(0));
+        T n2 = dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2] + T(2) * (dev[3] * dev[3] + dev[4] * dev[4] + dev[5] * dev[5]);
+        if (P.plasticity) {
+            T a = F.alpha[c];
+            const T nrm = sqrt(n2);
+            const T f = T(2) * G * nrm - T(0.816496580927726) * (T(P.sY) + T(P.Hh) * a);
+            if (f > T(0)) {
+                const T dl = f / (T(2) * G + T(0.816496580927726) * T(P.Hh));
+                const T sc_ = dl / nrm;
+#pragma unroll
+                for (int v = 0; v < 6; v++) { T dep = sc_ * dev[v]; ep[v] += dep; dev[v] -= dep; ee[v] -= dep; }
+                a += dl;
+                F.alpha[c] = a;
+                if constexpr (D == 2) {
+                    F.ep[0][c] = ep[0]; F.ep[1][c] = ep[1]; F.ep[2][c] = ep[2]; F.ep[3][c] = ep[5];
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 6; v++) F.ep[v][c] = ep[v];
+                }
+                tr = ee[0] + ee[1] + ee[2];
+                n2 = dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2] + T(2) * (dev[3] * dev[3] + dev[4] * dev[4] + dev[5] * dev[5]);
+            }
+        }
+        F.trE[c] = tr;
+        F.devE2[c] = n2;
+        if (want_sigma) {
+            T sg[6];
+#pragma unroll
+            for (int v = 0; v < 6; v++) sg[v] = T(2) * G * dev[v] + (v < 3 ? K * tr : T(0));
+            if constexpr (D == 2) {
+                F.sigma_out[0][c] = sg[0]; F.sigma_out[1][c] = sg[1]; F.sigma_out[2][c] = sg[2]; F.sigma_out[3][c] = sg[5];
+            } else {
+#pragma unroll
+                for (int v = 0; v < 6; v++) F.sigma_out[v][c] = sg[v];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1a: oxygen chemical potential mu_O = sum_a W_a c f_a'(x_O) - kappa Lap x_O
+// and mobility M_O = D_O(phi_g) / (c sum_a W_a f_a''(x_O))   (Sec. 2.2, 3.2)
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__global__ void k_mu(Params P, FieldPtrs<T, D> F)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.N; c += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_coords<D>(P, c, i, j, k);
+        const T x = F.xO[c];
+        T lap = F.xO[lin<D>(P, i - 1, j, k)] + F.xO[lin<D>(P, i + 1, j, k)]
+              + F.xO[lin<D>(P, i, j - 1, k)] + F.xO[lin<D>(P, i, j + 1, k)] - T(2 * D) * x;
+        if constexpr (D == 3) lap += F.xO[lin<D>(P, i, j, k - 1)] + F.xO[lin<D>(P, i, j, k + 1)];
+        T Wf, Ww, Wg;
+        phase_weights(F.theta[c], F.phig[c], Wf, Ww, Wg);
+        const T cc = T(P.c);
+        const T m1 = Wf * f_fe1(x) + Ww * f_wu1(x) + Wg * f_ga1(x);
+        const T m2 = Wf * f_fe2(x) + Ww * f_wu2(x) + Wg * f_ga2(x);
+        F.muO[c] = cc * m1 - T(P.kappa) * lap;
+        const T DO = (T(1) - Wg) * T(P.DOs) + Wg * T(P.DOg);
+        const T den = cc * m2;
+        F.MO[c] = den != T(0) ? DO / den : T(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1b: explicit Euler update (Sec. 2.4 field relations, R2 order parameter)
+//   theta' = -(L g / 2) [force(theta) - 2 eps Lap theta]
+//   x_O'   = div(M_O grad mu_O) - r
+//   x_H'   = div(D_H grad x_H) - 2 r
+//   x_W'   = div(D_W grad x_W) + r,     r = m(phi_g) k x_O x_H (0 if x_W >= 1)
+// face values are arithmetic means; then the supply reset.  Per-block sums
+// of the new fields and of the supply exchange are reduced by the last block.
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_update(Params P, FieldPtrs<T, D> F, double *partials, unsigned int *counter, Diag *dg)
+{
+    Acc<T> sO, sH, sW, rem, sup;
+    int bad = 0;
+    const T cc = T(P.c), eps2 = T(2 * P.eps), dt = T(P.dt);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.N; c += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_coords<D>(P, c, i, j, k);
+        long long nbr[2 * D];
+        nbr[0] = lin<D>(P, i - 1, j, k); nbr[1] = lin<D>(P, i + 1, j, k);
+        nbr[2] = lin<D>(P, i, j - 1, k); nbr[3] = lin<D>(P, i, j + 1, k);
+        if constexpr (D == 3) { nbr[4] = lin<D>(P, i, j, k - 1); nbr[5] = lin<D>(P, i, j, k + 1); }
+        const T th = F.theta[c], pg = F.phig[c];
+        const T xo = F.xO[c], xh = F.xH[c], xw = F.xW[c];
+        const T mu0 = F.muO[c], M0 = F.MO[c];
+        const T hg0 = hfun(pg);
+        const T DH0 = (T(1) - hg0) * T(P.DHs) + hg0 * T(P.DHg);
+        const T DW0 = (T(1) - hg0) * T(P.DWs) + hg0 * T(P.DWg);
+        T lapt = T(0), dO = T(0), dH = T(0), dW = T(0);
+#pragma unroll
+        for (int q = 0; q < 2 * D; q++) {
+            const long long m = nbr[q];
+            lapt += F.theta[m] - th;
+            dO += T(0.5) * (M0 + F.MO[m]) * (F.muO[m] - mu0);
+            const T hg = hfun(F.phig[m]);
+            const T DHm = (T(1) - hg) * T(P.DHs) + hg * T(P.DHg);
+            const T DWm = (T(1) - hg) * T(P.DWs) + hg * T(P.DWg);
+            dH += T(0.5) * (DH0 + DHm) * (F.xH[m] - xh);
+            dW += T(0.5) * (DW0 + DWm) * (F.xW[m] - xw);
+        }
+        // local force of the theta equation
+        const T t = F.trE[c], s2 = F.devE2[c];
+        const T ht = hfun(th), hpt = hder(th);
+        const T sol = T(1) - hg0;
+        const T Af = cc * f_fe(xo) + T(0.5) * T(P.Ks) * t * t + T(P.Gs) * s2;
+        const T Aw = cc * f_wu(xo) + T(0.5) * T(P.Ks) * t * t + T(P.Gs) * s2;
+        const T Kmix = sol * T(P.Ks) + hg0 * T(P.Kg);
+        const T force = sol * hpt * (Af - Aw) + T(2 * P.w) * mder(th) - T(P.eig0) * sol * hpt * T(3) * Kmix * t;
+        (void)ht;
+        const T rate = T(-0.5 * P.L) * F.mob[c] * (force - eps2 * lapt);
+        T r = mfun(pg) * T(P.kfor) * xo * xh;
+        if (xw >= T(1)) r = T(0);
+        const T nth = th + dt * rate;
+        const T nxo = xo + dt * (dO - r);
+        T nxh = xh + dt * (dH - T(2) * r);
+        T nxw = xw + dt * (dW + r);
+        if (F.mask[c]) {
+            rem.add(nxw);
+            sup.add(T(P.xHbc) - nxh);
+            nxh = T(P.xHbc);
+            nxw = T(0);
+        }
+        F.theta_o[c] = nth;
+        F.xO_o[c] = nxo;
+        F.xH_o[c] = nxh;
+        F.xW_o[c] = nxw;
+        sO.add(nxo); sH.add(nxh); sW.add(nxw);
+        if (!(isfinite(nth) && isfinite(nxo) && isfinite(nxh) && isfinite(nxw))) bad = 1;
+    }
+    double v[6] = {sO.value(), sH.value(), sW.value(), rem.value(), sup.value(), (double)bad};
+    block_sum_store<6>(v, partials + (size_t)blockIdx.x * PSTRIDE);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int tk = atomicAdd(counter, 1u);
+        last = (tk == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        double tot[6];
+        grid_sum<6>(partials, gridDim.x, 0, tot);
+        if (threadIdx.x == 0) {
+            dg->sumO = tot[0]; dg->sumH = tot[1]; dg->sumW = tot[2];
+            dg->removedW += tot[3];
+            dg->suppliedH += tot[4];
+            if (tot[5] > 0.0 && dg->status == 0) dg->status = 5;
+            *counter = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Conversions between the caller's FP64 cell-major arrays and device storage
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_in_scalar(long long N, const double *src, T *dst, double dflt)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        dst[c] = (T)(src ? src[c] : dflt);
+}
+
+template <typename T>
+__global__ void k_in_comp(long long N, int ncomp, const double *src, T *const *dst)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        for (int k = 0; k < ncomp; k++) dst[k][c] = (T)(src ? src[c * ncomp + k] : 0.0);
+}
+
+// (phi_f, phi_w) -> theta = phi_f / (phi_f + phi_w) (0 where no solid), phi_g
+template <typename T>
+__global__ void k_in_phase(long long N, const double *pf, const double *pw, T *theta, T *phig)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const double s = pf[c] + pw[c];
+        theta[c] = (T)(s > 0.0 ? pf[c] / s : 0.0);
+        phig[c] = (T)(1.0 - s);
+    }
+}
+
+template <typename T>
+__global__ void k_out_scalar(long long N, const T *src, double *dst)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        dst[c] = (double)src[c];
+}
+
+template <typename T>
+__global__ void k_out_comp(long long N, int ncomp, T *const *src, double *dst)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        for (int k = 0; k < ncomp; k++) dst[c * ncomp + k] = (double)src[k][c];
+}
+
+template <typename T>
+__global__ void k_out_phase(long long N, const T *theta, const T *phig, double *pf, double *pw)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const double s = 1.0 - (double)phig[c];
+        if (pf) pf[c] = s * (double)theta[c];
+        if (pw) pw[c] = s * (1.0 - (double)theta[c]);
+    }
+}
+
+// sum of x_O (for the initial reference of the reduction degree)
+template <typename T>
+__global__ void k_sum(long long N, const T *a, double *partials)
+{
+    Acc<T> s;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) s.add(a[c]);
+    double v[1] = {s.value()};
+    block_sum_store<1>(v, partials + (size_t)blockIdx.x * PSTRIDE);
+}
+
+// Discrete free energy (per-block partials): cell bulk + well + elastic
+// energy and forward-face gradient energies.
+template <typename T, int D>
+__global__ void k_free_energy(Params P, FieldPtrs<T, D> F, double *partials)
+{
+    Acc<double> e;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.N; c += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_coords<D>(P, c, i, j, k);
+        const double th = F.theta[c], pg = F.phig[c], x = F.xO[c];
+        const double t = F.trE[c], s2 = F.devE2[c];
+        double Wf, Ww, Wg;
+        phase_weights<double>(th, pg, Wf, Ww, Wg);
+        double v = Wf * (P.c * f_fe(x) + 0.5 * P.Ks * t * t + P.Gs * s2)
+                 + Ww * (P.c * f_wu(x) + 0.5 * P.Ks * t * t + P.Gs * s2)
+                 + Wg * (P.c * f_ga(x) + 0.5 * P.Kg * t * t + P.Gg * s2)
+                 + 2.0 * P.w * mfun(th);
+        long long nb[3] = {lin<D>(P, i + 1, j, k), lin<D>(P, i, j + 1, k), D == 3 ? lin<D>(P, i, j, k + 1) : 0};
+        for (int q = 0; q < D; q++) {
+            const double gt = (double)F.theta[nb[q]] - th, gx = (double)F.xO[nb[q]] - x;
+            v += P.eps * gt * gt + 0.5 * P.kappa * gx * gx;
+        }
+        e.add(v);
+    }
+    double vv[1] = {e.value()};
+    block_sum_store<1>(vv, partials + (size_t)blockIdx.x * PSTRIDE);
+}
+
+} // namespace pfdev

@@ -1,0 +1,729 @@
+// Host side of the C ABI declared in include/pf.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pf.h"
+#include "pf_kernels.cuh"
+
+using namespace pfdev;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ---------------------------------------------------------------------------
+// Element tables: Q1 unit square / cube, stiffness split into the lambda and
+// mu parts, integrated exactly with 2^d Gauss points.
+// ---------------------------------------------------------------------------
+void element_tables(int d, std::vector<double> &Kl, std::vector<double> &Km, std::vector<double> &Bb)
+{
+    const int nn = 1 << d, ne = nn * d, nv = d == 2 ? 3 : 6;
+    Kl.assign(ne * ne, 0.0);
+    Km.assign(ne * ne, 0.0);
+    Bb.assign(nn * d, 0.0);
+    const double g0 = 0.5 - 0.5 / std::sqrt(3.0), g1 = 0.5 + 0.5 / std::sqrt(3.0);
+    const double wgt = 1.0 / nn;
+    for (int g = 0; g < nn; g++) {
+        double xi[3];
+        for (int l = 0; l < d; l++) xi[l] = ((g >> l) & 1) ? g1 : g0;
+        double dn[8][3];
+        for (int a = 0; a < nn; a++)
+            for (int k = 0; k < d; k++) {
+                double v = 1.0;
+                for (int l = 0; l < d; l++) {
+                    const int bit = (a >> l) & 1;
+                    if (l == k) v *= bit ? 1.0 : -1.0;
+                    else v *= bit ? xi[l] : 1.0 - xi[l];
+                }
+                dn[a][k] = v;
+                Bb[a * d + k] += wgt * v;
+            }
+        // strain-displacement matrix B (nv x ne), engineering shears
+        std::vector<double> B(nv * ne, 0.0);
+        for (int a = 0; a < nn; a++) {
+            auto at = [&](int row, int comp, double v) { B[row * ne + a * d + comp] = v; };
+            if (d == 2) {
+                at(0, 0, dn[a][0]); at(1, 1, dn[a][1]);
+                at(2, 0, dn[a][1]); at(2, 1, dn[a][0]);
+            } else {
+                at(0, 0, dn[a][0]); at(1, 1, dn[a][1]); at(2, 2, dn[a][2]);
+                at(3, 1, dn[a][2]); at(3, 2, dn[a][1]);
+                at(4, 0, dn[a][2]); at(4, 2, dn[a][0]);
+                at(5, 0, dn[a][1]); at(5, 1, dn[a][0]);
+            }
+        }
+        // D_lambda = m m^T (normal rows), D_mu = diag(2 on normals, 1 on shears)
+        for (int r = 0; r < ne; r++)
+            for (int c = 0; c < ne; c++) {
+                double trr = 0.0, trc = 0.0, mu = 0.0;
+                for (int v = 0; v < d; v++) { trr += B[v * ne + r]; trc += B[v * ne + c]; }
+                for (int v = 0; v < nv; v++) mu += (v < d ? 2.0 : 1.0) * B[v * ne + r] * B[v * ne + c];
+                Kl[r * ne + c] += wgt * trr * trc;
+                Km[r * ne + c] += wgt * mu;
+            }
+    }
+}
+
+template <typename T>
+void fill_tab(Tab<T> &t)
+{
+    std::vector<double> Kl, Km, Bb;
+    element_tables(2, Kl, Km, Bb);
+    for (int i = 0; i < 64; i++) { t.Kl2[i] = (T)Kl[i]; t.Km2[i] = (T)Km[i]; }
+    for (int i = 0; i < 8; i++) t.Bb2[i] = (T)Bb[i];
+    t.Kdiag[0] = (T)Kl[0]; t.Kdiag[1] = (T)Km[0];
+    element_tables(3, Kl, Km, Bb);
+    for (int i = 0; i < 576; i++) { t.Kl3[i] = (T)Kl[i]; t.Km3[i] = (T)Km[i]; }
+    for (int i = 0; i < 24; i++) t.Bb3[i] = (T)Bb[i];
+    t.Kdiag[2] = (T)Kl[0]; t.Kdiag[3] = (T)Km[0];
+}
+
+bool upload_tables(int dev)
+{
+    static bool done[64] = {false};
+    if (dev >= 0 && dev < 64 && done[dev]) return true;
+    Tab<double> td;
+    Tab<float> tf;
+    fill_tab(td);
+    fill_tab(tf);
+    if (cudaMemcpyToSymbol(cTabD, &td, sizeof(td)) != cudaSuccess) return false;
+    if (cudaMemcpyToSymbol(cTabF, &tf, sizeof(tf)) != cudaSuccess) return false;
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return true;
+}
+
+double dt_stable_impl(const pf_config *c)
+{
+    const int d = c->ndim;
+    const pf_params &p = c->p;
+    const double Ds[6] = {p.D_O_s, p.D_O_g, p.D_H_s, p.D_H_g, p.D_W_s, p.D_W_g};
+    double Dmax = 0.0;
+    for (double v : Ds) Dmax = std::fmax(Dmax, v);
+    double dt = 1.0e300;
+    if (Dmax > 0.0) dt = std::fmin(dt, 1.0 / (2.0 * d * Dmax));
+    // smallest curvature of the phase energies: the ferrite quartic's minimum
+    // second derivative (at x = 6 * 182.510 / (24 * 163.708)) or wuestite's
+    const double xm = 6.0 * 182.510 / (24.0 * 163.708);
+    double fmin = 12.0 * 163.708 * xm * xm - 6.0 * 182.510 * xm + 2.0 * 90.573;
+    fmin = std::fmin(fmin, 2.0 * 173.263);
+    if (p.kappa_O > 0.0 && p.c_chem > 0.0 && Dmax > 0.0) {
+        const double Mmax = Dmax / (p.c_chem * fmin);
+        dt = std::fmin(dt, 2.0 / (Mmax * p.kappa_O * (4.0 * d) * (4.0 * d)));
+    }
+    if (p.L > 0.0) dt = std::fmin(dt, 1.0 / (1.2 * p.L * (2.0 * d * p.eps_phi + 2.0 * p.w)));
+    if (p.k_for > 0.0) dt = std::fmin(dt, 1.0 / (p.k_for * (1.0 / 16.0) * (0.571 + 2.0 * p.xH_bc)));
+    return dt;
+}
+
+} // namespace
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+struct pf_handle {
+    pf_config cfg;
+    Params P;
+    int dev = 0, sms = 0;
+    bool fp64 = true;
+    size_t tsz = 8;
+    cudaStream_t own = nullptr;
+    std::string err;
+    bool have_fields = false;
+    long long steps = 0;
+    double sumO0 = 0.0;
+    long long bytes = 0;
+    std::vector<void *> allocs;
+
+    // device arrays (void* so one handle type serves both precisions)
+    void *theta[2] = {nullptr, nullptr}, *xO[2] = {}, *xH[2] = {}, *xW[2] = {};
+    int cur = 0;
+    void *phig = nullptr, *mob = nullptr, *muO = nullptr, *MO = nullptr, *trE = nullptr, *devE2 = nullptr;
+    void *lam = nullptr, *mu = nullptr, *sig[6] = {}, *ep[6] = {}, *alpha = nullptr, *sigma[6] = {};
+    void *u[3] = {}, *r[3] = {}, *p[3] = {}, *q[3] = {}, *diag = nullptr;
+    unsigned char *mask = nullptr;
+    double *partials = nullptr;
+    int npart = 0;
+    unsigned int *sync = nullptr;      // [0] barrier count, [1] barrier generation, [2] last-block counter
+    Scalars *sc = nullptr;
+    Diag *dg = nullptr;
+    double *stage = nullptr, *stage2 = nullptr;
+    void **ptrtab = nullptr;           // device table of component pointers (6 entries)
+    int cg_grid = 0, cg_block = 256;
+    bool sigma_valid = false;
+
+    // profiling: event pairs around each launch while enabled
+    bool prof_on = false;
+    pf_profile prof;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_class;   // class of each recorded pair
+    size_t ev_used = 0;          // events recorded since the last harvest
+    long long cg_total_seen = 0; // CG iteration total at the end of the last pf_step
+
+    cudaEvent_t next_event()
+    {
+        if (ev_used == ev_pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            ev_pool.push_back(e);
+        }
+        return ev_pool[ev_used++];
+    }
+    void mark_begin(int cls, cudaStream_t s)
+    {
+        prof.launches++;
+        prof.count[cls]++;
+        if (!prof_on) return;
+        cudaEvent_t e = next_event();
+        if (e) cudaEventRecord(e, s);
+        ev_class.push_back(cls);
+    }
+    void mark_end(cudaStream_t s)
+    {
+        if (!prof_on) return;
+        cudaEvent_t e = next_event();
+        if (e) cudaEventRecord(e, s);
+    }
+    void harvest()
+    {
+        for (size_t k = 0; k + 1 < ev_used && k / 2 < ev_class.size(); k += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev_pool[k], ev_pool[k + 1]) == cudaSuccess) prof.ms[ev_class[k / 2]] += ms;
+        }
+        ev_used = 0;
+        ev_class.clear();
+    }
+
+    int fail(int code, const char *fmt, ...)
+    {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+    int cuda(cudaError_t e, const char *what)
+    {
+        if (e == cudaSuccess) return PF_OK;
+        return fail(e == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    }
+    template <typename X>
+    int alloc(X **ptr, size_t bytes_)
+    {
+        void *v = nullptr;
+        cudaError_t e = cudaMalloc(&v, bytes_ ? bytes_ : 16);
+        if (e != cudaSuccess) return fail(PF_ENOMEM, "cudaMalloc(%zu): %s", bytes_, cudaGetErrorString(e));
+        allocs.push_back(v);
+        bytes += (long long)bytes_;
+        *ptr = (X *)v;
+        return PF_OK;
+    }
+};
+
+#define PF_TRY(x) do { int _rc = (x); if (_rc != PF_OK) return _rc; } while (0)
+
+namespace {
+
+int grid_for(const pf_handle *h, long long n, int block = 256)
+{
+    long long g = (n + block - 1) / block;
+    long long cap = (long long)h->sms * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <typename T, int D>
+FieldPtrs<T, D> field_ptrs(pf_handle *h)
+{
+    FieldPtrs<T, D> F;
+    const int c = h->cur, o = 1 - h->cur;
+    F.theta = (const T *)h->theta[c]; F.xO = (const T *)h->xO[c]; F.xH = (const T *)h->xH[c]; F.xW = (const T *)h->xW[c];
+    F.theta_o = (T *)h->theta[o]; F.xO_o = (T *)h->xO[o]; F.xH_o = (T *)h->xH[o]; F.xW_o = (T *)h->xW[o];
+    F.phig = (const T *)h->phig; F.mob = (const T *)h->mob; F.mask = h->mask;
+    F.muO = (T *)h->muO; F.MO = (T *)h->MO; F.trE = (T *)h->trE; F.devE2 = (T *)h->devE2;
+    F.lam = (T *)h->lam; F.mu = (T *)h->mu;
+    for (int v = 0; v < 6; v++) { F.sig[v] = (T *)h->sig[v]; F.ep[v] = (T *)h->ep[v]; F.sigma_out[v] = (T *)h->sigma[v]; }
+    F.alpha = (T *)h->alpha;
+    for (int d = 0; d < 3; d++) F.u[d] = (T *)h->u[d];
+    return F;
+}
+
+template <typename T, int D>
+int setup_cg_launch(pf_handle *h)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<T, D>, h->cg_block, 0);
+    if (e != cudaSuccess) return h->cuda(e, "occupancy query");
+    if (per_sm < 1) return h->fail(PF_ECUDA, "CG kernel cannot be resident");
+    if (per_sm > 2) per_sm = 2;
+    long long want = (h->P.N + h->cg_block - 1) / h->cg_block;
+    long long g = (long long)per_sm * h->sms;
+    if (want < g) g = want;
+    if (g < 1) g = 1;
+    h->cg_grid = (int)g;
+    return PF_OK;
+}
+
+template <typename T, int D>
+int run_steps(pf_handle *h, int nsteps, cudaStream_t s)
+{
+    const Params &P = h->P;
+    const int ge = grid_for(h, P.N);
+    for (int step = 0; step < nsteps; step++) {
+        FieldPtrs<T, D> F = field_ptrs<T, D>(h);
+        if (h->cfg.mechanics) {
+            h->mark_begin(PF_K_SETUP, s);
+            k_setup<T, D><<<ge, 256, 0, s>>>(P, F);
+            h->mark_end(s);
+            CGArgs<T, D> A;
+            A.P = P;
+            A.lam = (const T *)h->lam; A.mu = (const T *)h->mu;
+            for (int v = 0; v < 6; v++) A.sig[v] = (const T *)h->sig[v];
+            for (int d = 0; d < 3; d++) { A.x[d] = (T *)h->u[d]; A.r[d] = (T *)h->r[d]; A.p[d] = (T *)h->p[d]; A.q[d] = (T *)h->q[d]; }
+            A.diag = (T *)h->diag;
+            A.partials = h->partials;
+            A.bar_count = h->sync; A.bar_gen = h->sync + 1;
+            A.sc = h->sc; A.dg = h->dg;
+            A.rtol = h->cfg.cg_rtol; A.maxit = h->cfg.cg_maxit;
+            A.warm = h->cfg.warm_start == PF_WS_PREV ? 1 : 0;
+            void *args[] = {&A};
+            h->mark_begin(PF_K_CG, s);
+            cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_cg<T, D>, dim3(h->cg_grid), dim3(h->cg_block), args, 0, s);
+            h->mark_end(s);
+            if (e != cudaSuccess) return h->cuda(e, "cooperative CG launch");
+            const int want_sigma = (step == nsteps - 1) ? 1 : 0;
+            h->mark_begin(PF_K_RETURN, s);
+            k_return<T, D><<<ge, 256, 0, s>>>(P, F, h->sc, want_sigma);
+            h->mark_end(s);
+            if (want_sigma) h->sigma_valid = true;
+        }
+        h->mark_begin(PF_K_MU, s);
+        k_mu<T, D><<<ge, 256, 0, s>>>(P, F);
+        h->mark_end(s);
+        h->mark_begin(PF_K_UPDATE, s);
+        k_update<T, D><<<ge, 256, 0, s>>>(P, F, h->partials, h->sync + 2, h->dg);
+        h->mark_end(s);
+        h->cur = 1 - h->cur;
+        h->steps++;
+    }
+    return h->cuda(cudaGetLastError(), "kernel launch");
+}
+
+template <typename T>
+int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
+{
+    const long long N = h->P.N;
+    const int D = h->cfg.ndim, NP = D == 2 ? 4 : 6, NV = D == 2 ? 3 : 6;
+    const int g = grid_for(h, N);
+    const size_t nb = sizeof(double) * (size_t)N;
+    auto src = [&](const double *ptr, size_t bytes_, double *stage) -> const double * {
+        if (!ptr) return nullptr;
+        if (where == PF_DEVICE) return ptr;
+        if (cudaMemcpyAsync(stage, ptr, bytes_, cudaMemcpyHostToDevice, s) != cudaSuccess) return (const double *)-1;
+        return stage;
+    };
+#define PF_SRC(var, ptr, bytes_, stg) const double *var = src(ptr, bytes_, stg); if (var == (const double *)-1) return h->fail(PF_ECUDA, "host-to-device copy failed");
+    {
+        PF_SRC(pf, f->phi_f, nb, h->stage);
+        PF_SRC(pw, f->phi_w, nb, h->stage2);
+        k_in_phase<T><<<g, 256, 0, s>>>(N, pf, pw, (T *)h->theta[0], (T *)h->phig);
+    }
+    {
+        PF_SRC(a, f->x_O, nb, h->stage);
+        k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->xO[0], 0.0);
+        PF_SRC(b, f->x_H, nb, h->stage2);
+        k_in_scalar<T><<<g, 256, 0, s>>>(N, b, (T *)h->xH[0], 0.0);
+    }
+    {
+        PF_SRC(a, f->x_H2O, nb, h->stage);
+        k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->xW[0], 0.0);
+        PF_SRC(b, f->mobility, nb, h->stage2);
+        k_in_scalar<T><<<g, 256, 0, s>>>(N, b, (T *)h->mob, 1.0);
+    }
+    {
+        PF_SRC(a, f->alpha, nb, h->stage);
+        k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->alpha, 0.0);
+    }
+    // component arrays through the device pointer table
+    void *tab[6];
+    {
+        for (int d = 0; d < 3; d++) tab[d] = h->u[d];
+        PF_TRY(h->cuda(cudaMemcpyAsync(h->ptrtab, tab, sizeof(tab), cudaMemcpyHostToDevice, s), "pointer table"));
+        PF_SRC(a, f->u, nb * D, h->stage);
+        k_in_comp<T><<<g, 256, 0, s>>>(N, D, a, (T *const *)h->ptrtab);
+        PF_TRY(h->cuda(cudaStreamSynchronize(s), "set_fields sync"));
+    }
+    {
+        for (int v = 0; v < 6; v++) tab[v] = h->ep[v];
+        PF_TRY(h->cuda(cudaMemcpyAsync(h->ptrtab, tab, sizeof(tab), cudaMemcpyHostToDevice, s), "pointer table"));
+        PF_SRC(a, f->eps_p, nb * NP, h->stage);
+        k_in_comp<T><<<g, 256, 0, s>>>(N, NP, a, (T *const *)h->ptrtab);
+    }
+    if (f->dirichlet) {
+        PF_TRY(h->cuda(cudaMemcpyAsync(h->mask, f->dirichlet, (size_t)N, where == PF_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s), "mask copy"));
+    } else {
+        PF_TRY(h->cuda(cudaMemsetAsync(h->mask, 0, (size_t)N, s), "mask clear"));
+    }
+    // scalars: mean strain, diagnostics
+    Scalars sc;
+    memset(&sc, 0, sizeof(sc));
+    if (f->Ebar) {
+        if (where == PF_DEVICE) {
+            PF_TRY(h->cuda(cudaMemcpyAsync(sc.E, f->Ebar, sizeof(double) * NV, cudaMemcpyDeviceToHost, s), "Ebar copy"));
+            PF_TRY(h->cuda(cudaStreamSynchronize(s), "Ebar sync"));
+        } else {
+            memcpy(sc.E, f->Ebar, sizeof(double) * NV);
+        }
+    }
+    PF_TRY(h->cuda(cudaMemcpyAsync(h->sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, s), "scalars"));
+    Diag dg;
+    memset(&dg, 0, sizeof(dg));
+    PF_TRY(h->cuda(cudaMemcpyAsync(h->dg, &dg, sizeof(dg), cudaMemcpyHostToDevice, s), "diag"));
+    PF_TRY(h->cuda(cudaMemsetAsync(h->sync, 0, sizeof(unsigned int) * 4, s), "sync words"));
+    PF_TRY(h->cuda(cudaMemsetAsync(h->trE, 0, h->tsz * (size_t)N, s), "coupling"));
+    PF_TRY(h->cuda(cudaMemsetAsync(h->devE2, 0, h->tsz * (size_t)N, s), "coupling"));
+    // reference oxygen content
+    const int gs = grid_for(h, N);
+    k_sum<T><<<gs, 256, 0, s>>>(N, (const T *)h->xO[0], h->partials);
+    std::vector<double> part((size_t)gs * PSTRIDE);
+    PF_TRY(h->cuda(cudaMemcpyAsync(part.data(), h->partials, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s), "partials"));
+    PF_TRY(h->cuda(cudaStreamSynchronize(s), "set_fields sync"));
+    double s0 = 0.0;
+    for (int b = 0; b < gs; b++) s0 += part[(size_t)b * PSTRIDE];
+    h->sumO0 = s0;
+    h->cur = 0;
+    h->steps = 0;
+    h->cg_total_seen = 0;
+    h->have_fields = true;
+    h->sigma_valid = false;
+    return h->cuda(cudaGetLastError(), "set_fields kernels");
+#undef PF_SRC
+}
+
+template <typename T>
+int get_fields_t(pf_handle *h, pf_fields *f, int where, cudaStream_t s)
+{
+    const long long N = h->P.N;
+    const int D = h->cfg.ndim, NP = D == 2 ? 4 : 6, NV = D == 2 ? 3 : 6;
+    const int g = grid_for(h, N);
+    const size_t nb = sizeof(double) * (size_t)N;
+    const int c = h->cur;
+    auto finish = [&](double *dst, double *stage, size_t bytes_) -> int {
+        if (where == PF_DEVICE) return PF_OK;
+        return h->cuda(cudaMemcpyAsync(dst, stage, bytes_, cudaMemcpyDeviceToHost, s), "device-to-host copy");
+    };
+    auto out = [&](double *dst, double *stage) -> double * { return where == PF_DEVICE ? dst : stage; };
+    if (f->phi_f || f->phi_w) {
+        double *a = f->phi_f ? out(f->phi_f, h->stage) : nullptr;
+        double *b = f->phi_w ? out(f->phi_w, h->stage2) : nullptr;
+        k_out_phase<T><<<g, 256, 0, s>>>(N, (const T *)h->theta[c], (const T *)h->phig, a, b);
+        if (f->phi_f) PF_TRY(finish(f->phi_f, h->stage, nb));
+        if (f->phi_w) PF_TRY(finish(f->phi_w, h->stage2, nb));
+        PF_TRY(h->cuda(cudaStreamSynchronize(s), "get sync"));
+    }
+    struct One { double *dst; const void *src; };
+    One ones[4] = {{f->x_O, h->xO[c]}, {f->x_H, h->xH[c]}, {f->x_H2O, h->xW[c]}, {f->alpha, h->alpha}};
+    for (auto &o : ones) {
+        if (!o.dst) continue;
+        k_out_scalar<T><<<g, 256, 0, s>>>(N, (const T *)o.src, out(o.dst, h->stage));
+        PF_TRY(finish(o.dst, h->stage, nb));
+        PF_TRY(h->cuda(cudaStreamSynchronize(s), "get sync"));
+    }
+    struct Comp { double *dst; void *const *src; int n; };
+    Comp comps[3] = {{f->u, h->u, D}, {f->eps_p, h->ep, NP}, {f->sigma, h->sigma, NP}};
+    for (auto &o : comps) {
+        if (!o.dst) continue;
+        void *tab[6] = {};
+        for (int k = 0; k < o.n; k++) tab[k] = o.src[k];
+        PF_TRY(h->cuda(cudaMemcpyAsync(h->ptrtab, tab, sizeof(tab), cudaMemcpyHostToDevice, s), "pointer table"));
+        k_out_comp<T><<<g, 256, 0, s>>>(N, o.n, (T *const *)h->ptrtab, out(o.dst, h->stage));
+        PF_TRY(finish(o.dst, h->stage, nb * o.n));
+        PF_TRY(h->cuda(cudaStreamSynchronize(s), "get sync"));
+    }
+    if (f->Ebar) {
+        Scalars sc;
+        PF_TRY(h->cuda(cudaMemcpyAsync(&sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost, s), "scalars"));
+        PF_TRY(h->cuda(cudaStreamSynchronize(s), "get sync"));
+        if (where == PF_DEVICE) {
+            PF_TRY(h->cuda(cudaMemcpy(f->Ebar, sc.E, sizeof(double) * NV, cudaMemcpyHostToDevice), "Ebar"));
+        } else {
+            memcpy(f->Ebar, sc.E, sizeof(double) * NV);
+        }
+    }
+    return h->cuda(cudaGetLastError(), "get_fields kernels");
+}
+
+template <typename T>
+int alloc_fields(pf_handle *h)
+{
+    const long long N = h->P.N;
+    const int D = h->cfg.ndim, NP = D == 2 ? 4 : 6, NV = D == 2 ? 3 : 6;
+    const size_t b = sizeof(T) * (size_t)N;
+    for (int k = 0; k < 2; k++) {
+        PF_TRY(h->alloc(&h->theta[k], b)); PF_TRY(h->alloc(&h->xO[k], b));
+        PF_TRY(h->alloc(&h->xH[k], b)); PF_TRY(h->alloc(&h->xW[k], b));
+    }
+    PF_TRY(h->alloc(&h->phig, b)); PF_TRY(h->alloc(&h->mob, b));
+    PF_TRY(h->alloc(&h->muO, b)); PF_TRY(h->alloc(&h->MO, b));
+    PF_TRY(h->alloc(&h->trE, b)); PF_TRY(h->alloc(&h->devE2, b));
+    PF_TRY(h->alloc(&h->mask, (size_t)N));
+    if (h->cfg.mechanics) {
+        PF_TRY(h->alloc(&h->lam, b)); PF_TRY(h->alloc(&h->mu, b));
+        for (int v = 0; v < NV; v++) PF_TRY(h->alloc(&h->sig[v], b));
+        for (int d = 0; d < D; d++) {
+            PF_TRY(h->alloc(&h->r[d], b)); PF_TRY(h->alloc(&h->p[d], b)); PF_TRY(h->alloc(&h->q[d], b));
+        }
+        PF_TRY(h->alloc(&h->diag, b));
+    }
+    for (int d = 0; d < D; d++) PF_TRY(h->alloc(&h->u[d], b));
+    for (int v = 0; v < NP; v++) { PF_TRY(h->alloc(&h->ep[v], b)); PF_TRY(h->alloc(&h->sigma[v], b)); }
+    PF_TRY(h->alloc(&h->alpha, b));
+    const size_t stage = sizeof(double) * (size_t)N * (size_t)(NP > D ? NP : D);
+    PF_TRY(h->alloc(&h->stage, stage));
+    PF_TRY(h->alloc(&h->stage2, sizeof(double) * (size_t)N));
+    h->npart = h->sms * 16 > 4096 ? h->sms * 16 : 4096;
+    PF_TRY(h->alloc(&h->partials, sizeof(double) * PSTRIDE * (size_t)h->npart));
+    PF_TRY(h->alloc(&h->sync, sizeof(unsigned int) * 4));
+    PF_TRY(h->alloc(&h->sc, sizeof(Scalars)));
+    PF_TRY(h->alloc(&h->dg, sizeof(Diag)));
+    PF_TRY(h->alloc(&h->ptrtab, sizeof(void *) * 6));
+    PF_TRY(h->cuda(cudaMemset(h->sync, 0, sizeof(unsigned int) * 4), "sync init"));
+    for (int v = 0; v < NP; v++) PF_TRY(h->cuda(cudaMemset(h->sigma[v], 0, b), "sigma init"));
+    return PF_OK;
+}
+
+void free_all(pf_handle *h)
+{
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    h->ev_pool.clear();
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->own) cudaStreamDestroy(h->own);
+    h->own = nullptr;
+}
+
+} // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+double pf_dt_stable(const pf_config *cfg)
+{
+    if (!cfg || (cfg->ndim != 2 && cfg->ndim != 3)) return -1.0;
+    return dt_stable_impl(cfg);
+}
+
+int pf_create(const pf_config *cfg, pf_handle **out)
+{
+    if (!out) return PF_EINVAL;
+    *out = nullptr;
+    g_create_error.clear();
+    if (!cfg) { g_create_error = "cfg is NULL"; return PF_EINVAL; }
+    const pf_config &c = *cfg;
+    if (c.ndim != 2 && c.ndim != 3) { g_create_error = "ndim must be 2 or 3"; return PF_EINVAL; }
+    if (c.nx < 2 || c.ny < 2 || (c.ndim == 3 && c.nz < 2)) { g_create_error = "grid sizes must be >= 2"; return PF_EINVAL; }
+    if (c.precision != PF_FP64 && c.precision != PF_MIXED) { g_create_error = "precision must be PF_FP64 or PF_MIXED"; return PF_EINVAL; }
+    if (c.warm_start != PF_WS_ZERO && c.warm_start != PF_WS_PREV) { g_create_error = "warm_start must be PF_WS_ZERO or PF_WS_PREV"; return PF_EINVAL; }
+    if (c.mechanics && (c.cg_maxit <= 0 || !(c.cg_rtol > 0.0))) { g_create_error = "cg_maxit must be > 0 and cg_rtol > 0"; return PF_EINVAL; }
+    if (!(c.p.nu > -1.0 && c.p.nu < 0.5) || !(c.p.E_s > 0.0) || !(c.p.E_g_ratio > 0.0)) { g_create_error = "elastic constants out of range"; return PF_EINVAL; }
+    const long long N = (long long)c.nx * c.ny * (c.ndim == 3 ? c.nz : 1);
+    if (N > (1LL << 31)) { g_create_error = "grid too large (more than 2^31 cells)"; return PF_EINVAL; }
+
+    pf_handle *h = new (std::nothrow) pf_handle();
+    if (!h) { g_create_error = "host allocation failed"; return PF_ENOMEM; }
+    h->cfg = c;
+    memset(&h->prof, 0, sizeof(h->prof));
+    if (c.ndim == 2) h->cfg.nz = 1;
+    h->fp64 = c.precision == PF_FP64;
+    h->tsz = h->fp64 ? sizeof(double) : sizeof(float);
+    cudaError_t e = cudaGetDevice(&h->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("CUDA unavailable: ") + cudaGetErrorString(e);
+        delete h;
+        return PF_ECUDA;
+    }
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev);
+    if (!coop) { g_create_error = "device lacks cooperative launch"; free_all(h); delete h; return PF_ECUDA; }
+    if (!upload_tables(h->dev)) { g_create_error = "constant table upload failed"; free_all(h); delete h; return PF_ECUDA; }
+
+    Params &P = h->P;
+    memset(&P, 0, sizeof(P));
+    P.ndim = c.ndim; P.nx = c.nx; P.ny = c.ny; P.nz = h->cfg.nz; P.N = N;
+    P.dt = c.dt > 0.0 ? c.dt : 0.2 * dt_stable_impl(&h->cfg);
+    P.c = c.p.c_chem; P.w = c.p.w; P.eps = c.p.eps_phi; P.kappa = c.p.kappa_O; P.L = c.p.L;
+    P.DOs = c.p.D_O_s; P.DOg = c.p.D_O_g; P.DHs = c.p.D_H_s; P.DHg = c.p.D_H_g; P.DWs = c.p.D_W_s; P.DWg = c.p.D_W_g;
+    P.kfor = c.p.k_for; P.xHbc = c.p.xH_bc;
+    const double Es = c.p.E_s, Eg = c.p.E_s * c.p.E_g_ratio, nu = c.p.nu;
+    P.Ks = Es / (3.0 * (1.0 - 2.0 * nu)); P.Gs = Es / (2.0 * (1.0 + nu));
+    P.Kg = Eg / (3.0 * (1.0 - 2.0 * nu)); P.Gg = Eg / (2.0 * (1.0 + nu));
+    P.eig0 = c.p.eig0; P.sY = c.p.sigma_Y; P.Hh = c.p.H_hard; P.prestress = c.p.prestress;
+    P.plasticity = c.plasticity;
+
+    int rc = h->fp64 ? alloc_fields<double>(h) : alloc_fields<float>(h);
+    if (rc == PF_OK && c.mechanics) {
+        if (c.ndim == 2) rc = h->fp64 ? setup_cg_launch<double, 2>(h) : setup_cg_launch<float, 2>(h);
+        else rc = h->fp64 ? setup_cg_launch<double, 3>(h) : setup_cg_launch<float, 3>(h);
+    }
+    if (rc != PF_OK) {
+        g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return PF_OK;
+}
+
+int pf_set_fields(pf_handle *h, const pf_fields *f, int where)
+{
+    if (!h) return PF_EINVAL;
+    if (!f || !f->phi_f || !f->phi_w || !f->x_O || !f->x_H || !f->x_H2O)
+        return h->fail(PF_EINVAL, "phi_f, phi_w, x_O, x_H and x_H2O are required");
+    if (where != PF_HOST && where != PF_DEVICE) return h->fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    cudaStream_t s = h->own;
+    return h->fp64 ? set_fields_t<double>(h, f, where, s) : set_fields_t<float>(h, f, where, s);
+}
+
+int pf_step(pf_handle *h, int nsteps, void *stream)
+{
+    if (!h) return PF_EINVAL;
+    if (nsteps < 0) return h->fail(PF_EINVAL, "nsteps < 0");
+    if (!h->have_fields) return h->fail(PF_ESTATE, "pf_step before pf_set_fields");
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->own;
+    if (s != h->own) {
+        // order the caller's stream after anything queued on the library stream
+        cudaEvent_t ev;
+        PF_TRY(h->cuda(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event"));
+        cudaEventRecord(ev, h->own);
+        cudaStreamWaitEvent(s, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    // clear the sticky device status words of this call
+    PF_TRY(h->cuda(cudaMemsetAsync(&h->sc->status, 0, sizeof(int), s), "status clear"));
+    PF_TRY(h->cuda(cudaMemsetAsync(&h->dg->status, 0, sizeof(int), s), "status clear"));
+    PF_TRY(h->cuda(cudaMemsetAsync(&h->dg->cg_max, 0, sizeof(int), s), "status clear"));
+    int rc;
+    if (h->cfg.ndim == 2) rc = h->fp64 ? run_steps<double, 2>(h, nsteps, s) : run_steps<float, 2>(h, nsteps, s);
+    else rc = h->fp64 ? run_steps<double, 3>(h, nsteps, s) : run_steps<float, 3>(h, nsteps, s);
+    if (rc != PF_OK) return rc;
+    Scalars sc;
+    Diag dg;
+    PF_TRY(h->cuda(cudaMemcpyAsync(&sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost, s), "status read"));
+    PF_TRY(h->cuda(cudaMemcpyAsync(&dg, h->dg, sizeof(dg), cudaMemcpyDeviceToHost, s), "status read"));
+    PF_TRY(h->cuda(cudaStreamSynchronize(s), "pf_step"));
+    if (h->prof_on) {
+        h->harvest();
+        h->prof.cg_iters += dg.cg_total - h->cg_total_seen;
+    }
+    h->cg_total_seen = dg.cg_total;
+    int st = PF_OK;
+    if (sc.status == 6 || dg.status == 6) st = PF_ETIMEOUT;
+    else if (dg.status == 5) st = PF_ENONFINITE;
+    else if (sc.status == 4) st = PF_ENOTCONV;
+    if (st == PF_ETIMEOUT) return h->fail(st, "a bounded device-side wait gave up");
+    if (st == PF_ENONFINITE) return h->fail(st, "non-finite value in the fields");
+    if (st == PF_ENOTCONV) return h->fail(st, "CG reached cg_maxit without meeting cg_rtol");
+    return PF_OK;
+}
+
+int pf_get_fields(pf_handle *h, pf_fields *out, int where)
+{
+    if (!h || !out) return PF_EINVAL;
+    if (!h->have_fields) return h->fail(PF_ESTATE, "pf_get_fields before pf_set_fields");
+    if (where != PF_HOST && where != PF_DEVICE) return h->fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    return h->fp64 ? get_fields_t<double>(h, out, where, h->own) : get_fields_t<float>(h, out, where, h->own);
+}
+
+int pf_get_diagnostics(pf_handle *h, pf_diag *out)
+{
+    if (!h || !out) return PF_EINVAL;
+    Scalars sc;
+    Diag dg;
+    PF_TRY(h->cuda(cudaMemcpy(&sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost), "scalars"));
+    PF_TRY(h->cuda(cudaMemcpy(&dg, h->dg, sizeof(dg), cudaMemcpyDeviceToHost), "diag"));
+    memset(out, 0, sizeof(*out));
+    out->sum_O = dg.sumO; out->sum_H = dg.sumH; out->sum_H2O = dg.sumW;
+    out->removed_H2O = dg.removedW; out->supplied_H = dg.suppliedH;
+    out->sum_O_init = h->sumO0;
+    out->reduction_degree = h->sumO0 != 0.0 && h->steps > 0 ? 1.0 - dg.sumO / h->sumO0 : 0.0;
+    out->cg_rel_residual = sc.relres;
+    out->cg_iters_last = dg.cg_last;
+    out->cg_iters_max = dg.cg_max;
+    out->cg_iters_total = dg.cg_total;
+    out->steps = h->steps;
+    out->dt = h->P.dt;
+    out->status = dg.status ? dg.status : sc.status;
+    return PF_OK;
+}
+
+int pf_free_energy(pf_handle *h, double *out)
+{
+    if (!h || !out) return PF_EINVAL;
+    if (!h->have_fields) return h->fail(PF_ESTATE, "no fields");
+    const int g = grid_for(h, h->P.N);
+    if (h->cfg.ndim == 2) {
+        if (h->fp64) k_free_energy<double, 2><<<g, 256, 0, h->own>>>(h->P, field_ptrs<double, 2>(h), h->partials);
+        else k_free_energy<float, 2><<<g, 256, 0, h->own>>>(h->P, field_ptrs<float, 2>(h), h->partials);
+    } else {
+        if (h->fp64) k_free_energy<double, 3><<<g, 256, 0, h->own>>>(h->P, field_ptrs<double, 3>(h), h->partials);
+        else k_free_energy<float, 3><<<g, 256, 0, h->own>>>(h->P, field_ptrs<float, 3>(h), h->partials);
+    }
+    std::vector<double> part((size_t)g * PSTRIDE);
+    PF_TRY(h->cuda(cudaMemcpyAsync(part.data(), h->partials, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, h->own), "partials"));
+    PF_TRY(h->cuda(cudaStreamSynchronize(h->own), "free energy"));
+    double s = 0.0;
+    for (int b = 0; b < g; b++) s += part[(size_t)b * PSTRIDE];
+    *out = s;
+    return PF_OK;
+}
+
+int pf_profile_enable(pf_handle *h, int on)
+{
+    if (!h) return PF_EINVAL;
+    cudaStreamSynchronize(h->own);
+    h->ev_used = 0;
+    h->ev_class.clear();
+    memset(&h->prof, 0, sizeof(h->prof));
+    h->prof_on = on != 0;
+    h->prof.enabled = h->prof_on ? 1 : 0;
+    return PF_OK;
+}
+
+int pf_profile_read(pf_handle *h, pf_profile *out)
+{
+    if (!h || !out) return PF_EINVAL;
+    *out = h->prof;
+    return PF_OK;
+}
+
+long long pf_device_bytes(const pf_handle *h) { return h ? h->bytes : 0; }
+
+const char *pf_last_error(const pf_handle *h)
+{
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+void pf_destroy(pf_handle *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->own);
+    free_all(h);
+    delete h;
+}
+
+} // extern "C"

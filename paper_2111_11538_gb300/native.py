@@ -1,0 +1,192 @@
+"""ctypes binding of the C ABI in include/pf.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``libpf.so`` built from
+``csrc/``; there is no Python or CPU fallback.  If the library is missing the
+functions raise ``RuntimeError``.
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(_HERE)
+LIB_PATH = os.path.join(_HERE, "libpf.so")
+SOURCES = [os.path.join(_HERE, "csrc", n) for n in ("pf_lib.cu", "pf_kernels.cuh", "pf_device.cuh")]
+INCLUDE = os.path.join(ROOT, "include")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOTCONV, PF_ENONFINITE, PF_ETIMEOUT, PF_ESTATE = range(8)
+PF_FP64, PF_MIXED = 0, 1
+PF_WS_ZERO, PF_WS_PREV = 0, 1
+PF_HOST, PF_DEVICE = 0, 1
+
+STATUS_NAMES = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_ENOTCONV",
+                5: "PF_ENONFINITE", 6: "PF_ETIMEOUT", 7: "PF_ESTATE"}
+
+
+class pf_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "c_chem", "w", "eps_phi", "kappa_O", "L", "D_O_s", "D_O_g", "D_H_s", "D_H_g", "D_W_s", "D_W_g",
+        "k_for", "xH_bc", "E_s", "nu", "E_g_ratio", "eig0", "sigma_Y", "H_hard", "prestress")]
+
+
+class pf_config(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("precision", ctypes.c_int), ("mechanics", ctypes.c_int), ("plasticity", ctypes.c_int),
+                ("warm_start", ctypes.c_int), ("cg_maxit", ctypes.c_int), ("cg_rtol", ctypes.c_double),
+                ("dt", ctypes.c_double), ("p", pf_params)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class pf_fields(ctypes.Structure):
+    _fields_ = [("phi_f", _DP), ("phi_w", _DP), ("x_O", _DP), ("x_H", _DP), ("x_H2O", _DP),
+                ("u", _DP), ("Ebar", _DP), ("eps_p", _DP), ("alpha", _DP), ("sigma", _DP),
+                ("mobility", _DP), ("dirichlet", ctypes.POINTER(ctypes.c_ubyte))]
+
+
+class pf_diag(ctypes.Structure):
+    _fields_ = [("sum_O", ctypes.c_double), ("sum_H", ctypes.c_double), ("sum_H2O", ctypes.c_double),
+                ("removed_H2O", ctypes.c_double), ("supplied_H", ctypes.c_double),
+                ("sum_O_init", ctypes.c_double), ("reduction_degree", ctypes.c_double),
+                ("cg_rel_residual", ctypes.c_double), ("cg_iters_last", ctypes.c_int),
+                ("cg_iters_max", ctypes.c_int), ("cg_iters_total", ctypes.c_longlong),
+                ("steps", ctypes.c_longlong), ("dt", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+PF_K_SETUP, PF_K_CG, PF_K_RETURN, PF_K_MU, PF_K_UPDATE, PF_K_NCLASS = range(6)
+KERNEL_CLASSES = ["setup", "cg", "return", "mu", "update"]
+
+
+class pf_profile(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int), ("launches", ctypes.c_longlong),
+                ("count", ctypes.c_longlong * PF_K_NCLASS), ("ms", ctypes.c_double * PF_K_NCLASS),
+                ("cg_iters", ctypes.c_longlong)]
+
+
+# exported symbols, in the order of include/pf.h
+SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_diagnostics",
+           "pf_free_energy", "pf_dt_stable", "pf_profile_enable", "pf_profile_read",
+           "pf_device_bytes", "pf_last_error", "pf_destroy"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _stale():
+    if not os.path.exists(LIB_PATH):
+        return True
+    t = os.path.getmtime(LIB_PATH)
+    return any(os.path.getmtime(s) > t for s in SOURCES + [os.path.join(INCLUDE, "pf.h")])
+
+
+def build_library(force=False, verbose=False):
+    """Compile csrc/ into libpf.so for sm_103a with nvcc (in-tree)."""
+    if not force and not _stale():
+        return LIB_PATH
+    tmp = LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["nvcc", "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+           "-I" + INCLUDE, "-o", tmp, SOURCES[0]]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+def lib():
+    """Load libpf.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpf.so is not built: run __graft_entry__.build() or "
+                               "paper_2111_11538_gb300.native.build_library()")
+        l = ctypes.CDLL(LIB_PATH)
+        l.pf_create.argtypes = [ctypes.POINTER(pf_config), ctypes.POINTER(ctypes.c_void_p)]
+        l.pf_create.restype = ctypes.c_int
+        l.pf_set_fields.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_fields), ctypes.c_int]
+        l.pf_set_fields.restype = ctypes.c_int
+        l.pf_step.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        l.pf_step.restype = ctypes.c_int
+        l.pf_get_fields.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_fields), ctypes.c_int]
+        l.pf_get_fields.restype = ctypes.c_int
+        l.pf_get_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_diag)]
+        l.pf_get_diagnostics.restype = ctypes.c_int
+        l.pf_free_energy.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+        l.pf_free_energy.restype = ctypes.c_int
+        l.pf_dt_stable.argtypes = [ctypes.POINTER(pf_config)]
+        l.pf_dt_stable.restype = ctypes.c_double
+        l.pf_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        l.pf_profile_enable.restype = ctypes.c_int
+        l.pf_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_profile)]
+        l.pf_profile_read.restype = ctypes.c_int
+        l.pf_device_bytes.argtypes = [ctypes.c_void_p]
+        l.pf_device_bytes.restype = ctypes.c_longlong
+        l.pf_last_error.argtypes = [ctypes.c_void_p]
+        l.pf_last_error.restype = ctypes.c_char_p
+        l.pf_destroy.argtypes = [ctypes.c_void_p]
+        l.pf_destroy.restype = None
+        _lib = l
+        return l
+
+
+# ---- thin same-name wrappers ------------------------------------------------
+def pf_create(cfg):
+    h = ctypes.c_void_p()
+    rc = lib().pf_create(ctypes.byref(cfg), ctypes.byref(h))
+    return rc, h
+
+
+def pf_set_fields(h, fields, where=PF_HOST):
+    return lib().pf_set_fields(h, ctypes.byref(fields), where)
+
+
+def pf_step(h, nsteps, stream=None):
+    return lib().pf_step(h, int(nsteps), ctypes.c_void_p(stream) if stream else None)
+
+
+def pf_get_fields(h, fields, where=PF_HOST):
+    return lib().pf_get_fields(h, ctypes.byref(fields), where)
+
+
+def pf_get_diagnostics(h):
+    d = pf_diag()
+    rc = lib().pf_get_diagnostics(h, ctypes.byref(d))
+    return rc, d
+
+
+def pf_free_energy(h):
+    v = ctypes.c_double()
+    rc = lib().pf_free_energy(h, ctypes.byref(v))
+    return rc, v.value
+
+
+def pf_dt_stable(cfg):
+    return lib().pf_dt_stable(ctypes.byref(cfg))
+
+
+def pf_profile_enable(h, on=True):
+    return lib().pf_profile_enable(h, 1 if on else 0)
+
+
+def pf_profile_read(h):
+    p = pf_profile()
+    rc = lib().pf_profile_read(h, ctypes.byref(p))
+    return rc, p
+
+
+def pf_device_bytes(h):
+    return lib().pf_device_bytes(h)
+
+
+def pf_last_error(h=None):
+    s = lib().pf_last_error(h)
+    return s.decode() if s else ""
+
+
+def pf_destroy(h):
+    lib().pf_destroy(h)

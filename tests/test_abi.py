@@ -1,0 +1,67 @@
+"""C-ABI library: builds, loads without a GPU, exports every symbol of
+include/pf.h, and its host-only functions agree with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2111_11538_gb300 import make_config, native, workloads
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "pf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    native.build_library()
+    return native.lib()
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(pf_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_binding_symbols():
+    assert _declared() == sorted(native.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (8, 8, 8), (40, 24)])
+@pytest.mark.parametrize("over", [{}, {"D_O_g": 0.0, "D_H_g": 0.3, "D_W_g": 0.0}, {"eps_phi": 3.0}, {"k_for": 50.0}])
+def test_dt_stable_matches_oracle(lib, orc, shape, over):
+    prm = workloads.params(**over)
+    cfg = make_config(shape, prm)
+    assert abs(native.pf_dt_stable(cfg) - orc.dt_stable(shape, prm)) <= 1e-15 * orc.dt_stable(shape, prm)
+
+
+def test_create_rejects_bad_config(lib):
+    prm = workloads.params()
+    cfg = make_config((16, 16), prm)
+    cfg.ndim = 4
+    rc, h = native.pf_create(cfg)
+    assert rc == native.PF_EINVAL and not h.value
+    assert "ndim" in native.pf_last_error(None)
+    cfg = make_config((16, 16), prm)
+    cfg.nx = 1
+    rc, h = native.pf_create(cfg)
+    assert rc == native.PF_EINVAL
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    rc, h = native.pf_create(make_config((16, 16), workloads.params()))
+    assert rc == native.PF_ECUDA and not h.value
+    assert native.pf_last_error(None)
+
+
+def test_null_handle_calls(lib):
+    assert lib.pf_step(None, 1, None) == native.PF_EINVAL
+    assert lib.pf_set_fields(None, None, 0) == native.PF_EINVAL
+    lib.pf_destroy(None)
