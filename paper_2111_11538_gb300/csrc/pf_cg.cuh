@@ -1,0 +1,421 @@
+// Persistent Jacobi-PCG for the mechanics (K3/K4), one grid barrier per
+// iteration.
+//
+// The iteration is the Chronopoulos-Gear form of preconditioned CG: with
+// u = M^-1 r, w = A u, gamma = r.u, delta = w.u,
+//     beta_i  = gamma_i / gamma_{i-1}
+//     alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1})
+//     p_i = u_i + beta_i p_{i-1},  s_i = w_i + beta_i s_{i-1}
+//     x_{i+1} = x_i + alpha_i p_i,  r_{i+1} = r_i - alpha_i s_i
+// which produces the iterates of standard PCG but needs all its inner
+// products at one point per iteration.  One sweep over node tiles does the
+// vector updates, rebuilds u_{i+1} on the tile and its halo in shared memory
+// from r_i, w_i, s_{i-1} (double-buffered in global memory), applies the Q1
+// operator to it and accumulates gamma, delta and ||r||^2; the grid barrier
+// then reduces those in a fixed order (the last block to arrive reduces) and
+// every block continues with identical scalars.
+#pragma once
+#include "pf_kernels.cuh"
+
+namespace pfdev {
+
+template <int D> struct Tile;
+template <> struct Tile<2> { static constexpr int X = 32, Y = 8, Z = 1; };
+template <> struct Tile<3> { static constexpr int X = 16, Y = 4, Z = 4; };
+
+template <typename T, int D>
+struct PCGArgs {
+    Params P;
+    const T *lam, *mu;
+    const T *sig[6];
+    T *x[3], *p[3];
+    T *r[2][3], *w[2][3], *s[2][3];
+    T *diag;
+    double *partials;
+    double *result;                // >= 16 doubles
+    unsigned int *bar_count, *bar_gen;
+    Scalars *sc;
+    Diag *dg;
+    double rtol;
+    int maxit;
+    int warm;
+};
+
+// Grid barrier that also reduces K per-block values in a fixed order: the
+// last block to arrive sums the partials (block-strided, then a block tree)
+// and publishes them before releasing the others.  Waits are bounded
+// (SPIN_LIMIT polls, then PF_ETIMEOUT in *err and false is returned).
+template <int K>
+__device__ bool reduce_barrier(double (&v)[K], double *partials, double *result, unsigned int *count,
+                               unsigned int *gen, int *err, double (&out)[K])
+{
+    __shared__ int s_last, s_ok;
+    __shared__ unsigned int s_gen;
+    block_sum_store<K>(v, partials + (size_t)blockIdx.x * PSTRIDE);
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        volatile unsigned int *vgen = gen;
+        s_gen = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(count, 1u);
+        s_last = (arrived == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        double acc[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) acc[k] = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+            for (int k = 0; k < K; k++) acc[k] += __ldcg(partials + (size_t)b * PSTRIDE + k);
+        }
+        block_sum_store<K>(acc, result);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = gen;
+        long long spins = 0;
+        while (*vgen == s_gen) {
+            if (++spins > SPIN_LIMIT) { atomicExch(err, 6); s_ok = 0; break; }
+            __nanosleep(20);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) out[k] = __ldcg(result + k);
+    const int ok = s_ok;
+    __syncthreads();
+    return ok != 0;
+}
+
+// q = sum over the 2^d cells around a node of (lam K_lam + mu K_mu) u_e, plus
+// the mean-strain coupling B_a^T D_c UE, from shared-memory tiles.
+// su: [D][HN] halo nodes, sl/sm: [HC] halo cells.  (lx, ly, lz): the node's
+// halo-local coordinates.
+template <typename T, int D, int HX, int HY, int CX, int CY>
+__device__ __forceinline__ void apply_tile(const T *su, const T *sl, const T *sm, int HN, int lx, int ly, int lz,
+                                           const T *ue, T (&q)[D], T (&eown)[Dims<D>::NV], T &lown, T &mown)
+{
+    constexpr int NN = Dims<D>::NN, NV = Dims<D>::NV;
+#pragma unroll
+    for (int d = 0; d < D; d++) q[d] = T(0);
+#pragma unroll
+    for (int a = 0; a < NN; a++) {
+        const int ax = a & 1, ay = (a >> 1) & 1, az = D == 3 ? (a >> 2) & 1 : 0;
+        // Halo nodes and halo cells both start one before the tile, so the
+        // cell whose lower corner is halo node (cx, cy, cz) has cell-local
+        // coordinates (cx, cy, cz); cell a of this node has its lower corner
+        // at the node minus bits(a).
+        const int cx = lx - ax, cy = ly - ay, cz = lz - az;
+        const int cl = cx + CX * (cy + CY * (D == 3 ? cz : 0));
+        const T l = sl[cl], m = sm[cl];
+        T ul[NN][D];
+#pragma unroll
+        for (int b = 0; b < NN; b++) {
+            const int bx = b & 1, by = (b >> 1) & 1, bz = D == 3 ? (b >> 2) & 1 : 0;
+            const int hn = (cx + bx) + HX * ((cy + by) + HY * (D == 3 ? cz + bz : 0));
+#pragma unroll
+            for (int d = 0; d < D; d++) ul[b][d] = su[d * HN + hn];
+        }
+#pragma unroll
+        for (int co = 0; co < D; co++) {
+            T acc = T(0);
+#pragma unroll
+            for (int b = 0; b < NN; b++)
+#pragma unroll
+                for (int cc = 0; cc < D; cc++)
+                    acc += (l * Kl<T, D>(a * D + co, b * D + cc) + m * Km<T, D>(a * D + co, b * D + cc)) * ul[b][cc];
+            q[co] += acc;
+        }
+        T se[NV], bt[D];
+        voigt_stress<T, D>(l, m, ue, se);
+        bbar_t<T, D>(a, se, bt);
+#pragma unroll
+        for (int d = 0; d < D; d++) q[d] += bt[d];
+        if (a == 0) {
+            avg_strain<T, D>(ul, eown);
+            lown = l;
+            mown = m;
+        }
+    }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_pcg(PCGArgs<T, D> A)
+{
+    constexpr int NV = Dims<D>::NV, NN = Dims<D>::NN;
+    constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+    constexpr int HX = TX + 2, HY = TY + 2, HZ = D == 3 ? TZ + 2 : 1;
+    constexpr int CX = TX + 1, CY = TY + 1, CZ = D == 3 ? TZ + 1 : 1;
+    constexpr int HN = HX * HY * HZ, HC = CX * CY * CZ;
+    __shared__ T su[D * HN];
+    __shared__ T sl[HC], sm[HC];
+
+    const Params &P = A.P;
+    const long long N = P.N;
+    int *err = &A.sc->status;
+    const int ntx = (P.nx + TX - 1) / TX, nty = (P.ny + TY - 1) / TY, ntz = D == 3 ? (P.nz + TZ - 1) / TZ : 1;
+    const int ntiles = ntx * nty * ntz;
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = D == 3 ? threadIdx.x / (TX * TY) : 0;
+
+    // ---------------- I1: b, diag, r0 = b - A x0 and cell sums ---------------
+    double XE[6] = {0, 0, 0, 0, 0, 0};
+    if (A.warm)
+        for (int v = 0; v < NV; v++) XE[v] = A.sc->E[v];
+    {
+        const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        const long long st = (long long)gridDim.x * blockDim.x;
+        Acc<T> bb, rr, sl_, sm_, ss[NV], de[NV];
+        for (long long n = t0; n < N; n += st) {
+            int i, j, k;
+            cell_coords<D>(P, n, i, j, k);
+            T b[D], ax[D];
+#pragma unroll
+            for (int d = 0; d < D; d++) { b[d] = T(0); ax[d] = T(0); }
+            T dgn = T(0);
+#pragma unroll
+            for (int a = 0; a < NN; a++) {
+                const int ox = a & 1, oy = (a >> 1) & 1, oz = D == 3 ? (a >> 2) & 1 : 0;
+                const int ci = i - ox, cj = j - oy, ck = k - oz;
+                const long long c = lin<D>(P, ci, cj, ck);
+                const T l = A.lam[c], m = A.mu[c];
+                dgn += l * KdL<T, D>() + m * KdM<T, D>();
+                T s[NV], bt[D];
+#pragma unroll
+                for (int v = 0; v < NV; v++) s[v] = A.sig[v][c];
+                bbar_t<T, D>(a, s, bt);
+#pragma unroll
+                for (int d = 0; d < D; d++) b[d] += bt[d];
+                if (A.warm) {
+                    T ue[NN][D];
+#pragma unroll
+                    for (int bn = 0; bn < NN; bn++) {
+                        const int px = bn & 1, py = (bn >> 1) & 1, pz = D == 3 ? (bn >> 2) & 1 : 0;
+                        const long long mm = lin<D>(P, ci + px, cj + py, ck + pz);
+#pragma unroll
+                        for (int d = 0; d < D; d++) ue[bn][d] = A.x[d][mm];
+                    }
+#pragma unroll
+                    for (int co = 0; co < D; co++) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int bn = 0; bn < NN; bn++)
+#pragma unroll
+                            for (int cc = 0; cc < D; cc++)
+                                acc += (l * Kl<T, D>(a * D + co, bn * D + cc) + m * Km<T, D>(a * D + co, bn * D + cc)) * ue[bn][cc];
+                        ax[co] += acc;
+                    }
+                    T e[NV], se[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; v++) e[v] = (T)XE[v];
+                    voigt_stress<T, D>(l, m, e, se);
+                    bbar_t<T, D>(a, se, bt);
+#pragma unroll
+                    for (int d = 0; d < D; d++) ax[d] += bt[d];
+                    if (a == 0) {
+                        T eb[NV];
+                        avg_strain<T, D>(ue, eb);
+                        voigt_stress<T, D>(l, m, eb, se);
+#pragma unroll
+                        for (int v = 0; v < NV; v++) de[v].add(se[v]);
+                    }
+                }
+                if (a == 0) {
+                    sl_.add(l);
+                    sm_.add(m);
+#pragma unroll
+                    for (int v = 0; v < NV; v++) ss[v].add(s[v]);
+                }
+            }
+            A.diag[n] = dgn;
+#pragma unroll
+            for (int d = 0; d < D; d++) {
+                if (!A.warm) A.x[d][n] = T(0);
+                A.p[d][n] = T(0);
+                A.s[0][d][n] = T(0);
+                const T rv = b[d] - ax[d];
+                A.r[0][d][n] = rv;
+                bb.addprod(b[d], b[d]);
+                rr.addprod(rv, rv);
+            }
+        }
+        double v[16];
+        v[0] = bb.value(); v[1] = rr.value(); v[2] = sl_.value(); v[3] = sm_.value();
+#pragma unroll
+        for (int q = 0; q < 6; q++) { v[4 + q] = q < NV ? ss[q].value() : 0.0; v[10 + q] = q < NV ? de[q].value() : 0.0; }
+        double tot[16];
+        if (!reduce_barrier<16>(v, A.partials, A.result, A.bar_count, A.bar_gen, err, tot)) return;
+        // scalars of the mean-strain dofs (computed identically by every block)
+        const double Sl = tot[2], Sm = tot[3];
+        double DiagE[6], BE[6], RE[6], UE[6], PE[6], SE[6], WE[6], AXE[6];
+        {
+            double unit[6], s6[6];
+            for (int vv = 0; vv < NV; vv++) {
+                for (int w = 0; w < NV; w++) unit[w] = (w == vv) ? 1.0 : 0.0;
+                dmat_mul<D>(Sl, Sm, unit, s6);
+                DiagE[vv] = s6[vv];
+            }
+            dmat_mul<D>(Sl, Sm, XE, AXE);
+        }
+        double bbt = tot[0], rho = tot[1];
+        for (int vv = 0; vv < NV; vv++) {
+            BE[vv] = tot[4 + vv] + (vv < D ? (double)N * (-P.prestress) : 0.0);
+            RE[vv] = BE[vv] - (tot[10 + vv] + AXE[vv]);
+            UE[vv] = RE[vv] / DiagE[vv];
+            bbt += BE[vv] * BE[vv];
+            rho += RE[vv] * RE[vv];
+            PE[vv] = 0.0;
+            SE[vv] = 0.0;
+        }
+        const double bnorm = sqrt(bbt);
+        int it = 0;
+        bool conv = false;
+        int cur = 0;
+        if (bnorm == 0.0) {
+            for (long long n = t0; n < N; n += st)
+                for (int d = 0; d < D; d++) A.x[d][n] = T(0);
+            for (int vv = 0; vv < NV; vv++) XE[vv] = 0.0;
+            rho = 0.0;
+            conv = true;
+        } else if (sqrt(rho) <= A.rtol * bnorm) {
+            conv = true;
+        }
+        double gamma = 0.0, delta = 0.0, gamma_prev = 1.0, alpha_prev = 1.0;
+        double alpha = 0.0, beta = 0.0;
+        // ---------------- sweeps: I2 (first = true) then iterations ---------
+        bool first = true;
+        while (!conv) {
+            if (!first) {
+                beta = (it == 0) ? 0.0 : gamma / gamma_prev;
+                alpha = (it == 0) ? gamma / delta : gamma / (delta - beta * gamma / alpha_prev);
+                for (int vv = 0; vv < NV; vv++) {
+                    PE[vv] = UE[vv] + beta * PE[vv];
+                    SE[vv] = WE[vv] + beta * SE[vv];
+                    XE[vv] += alpha * PE[vv];
+                    RE[vv] -= alpha * SE[vv];
+                    UE[vv] = RE[vv] / DiagE[vv];
+                }
+            }
+            const T ta = (T)alpha, tb = (T)beta;
+            const int nxt = first ? cur : 1 - cur;
+            T ue[NV];
+#pragma unroll
+            for (int vv = 0; vv < NV; vv++) ue[vv] = (T)UE[vv];
+            Acc<T> ga, de_, rh, dsum[NV];
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
+                const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+                // halo nodes: u_{i+1} = (r_i - alpha (w_i + beta s_{i-1})) / diag
+                for (int h = threadIdx.x; h < HN; h += blockDim.x) {
+                    const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
+                    const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
+                    const T inv = T(1) / __ldcg(A.diag + g);
+#pragma unroll
+                    for (int d = 0; d < D; d++) {
+                        T rv = __ldcg(A.r[cur][d] + g);
+                        if (!first) rv -= ta * (__ldcg(A.w[cur][d] + g) + tb * __ldcg(A.s[cur][d] + g));
+                        su[d * HN + h] = rv * inv;
+                    }
+                }
+                for (int h = threadIdx.x; h < HC; h += blockDim.x) {
+                    const int lx = h % CX, ly = (h / CX) % CY, lz = D == 3 ? h / (CX * CY) : 0;
+                    const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
+                    sl[h] = A.lam[g];
+                    sm[h] = A.mu[g];
+                }
+                __syncthreads();
+                const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+                const bool active = gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz);
+                if (active) {
+                    const long long n = (long long)gx + (long long)P.nx * ((long long)gy + (D == 3 ? (long long)P.ny * gz : 0LL));
+                    const int lx = tx + 1, ly = ty + 1, lz = D == 3 ? tz + 1 : 0;
+                    const int hn = lx + HX * (ly + HY * lz);
+                    T un[D];
+#pragma unroll
+                    for (int d = 0; d < D; d++) un[d] = su[d * HN + hn];
+                    T rn[D];
+                    if (!first) {
+                        const T inv = T(1) / __ldcg(A.diag + n);
+#pragma unroll
+                        for (int d = 0; d < D; d++) {
+                            const T ri = __ldcg(A.r[cur][d] + n);
+                            const T si = __ldcg(A.w[cur][d] + n) + tb * __ldcg(A.s[cur][d] + n);
+                            const T pi = ri * inv + tb * A.p[d][n];
+                            A.p[d][n] = pi;
+                            A.x[d][n] += ta * pi;
+                            A.s[nxt][d][n] = si;
+                            rn[d] = ri - ta * si;
+                            A.r[nxt][d][n] = rn[d];
+                        }
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < D; d++) rn[d] = __ldcg(A.r[cur][d] + n);
+                    }
+                    T q[D], eo[NV], lo, mo;
+                    apply_tile<T, D, HX, HY, CX, CY>(su, sl, sm, HN, lx, ly, lz, ue, q, eo, lo, mo);
+#pragma unroll
+                    for (int d = 0; d < D; d++) {
+                        A.w[nxt][d][n] = q[d];
+                        ga.addprod(rn[d], un[d]);
+                        de_.addprod(q[d], un[d]);
+                        rh.addprod(rn[d], rn[d]);
+                    }
+                    T se[NV];
+                    voigt_stress<T, D>(lo, mo, eo, se);
+#pragma unroll
+                    for (int vv = 0; vv < NV; vv++) dsum[vv].add(se[vv]);
+                }
+                __syncthreads();
+            }
+            double v9[9], t9[9];
+            v9[0] = ga.value(); v9[1] = de_.value(); v9[2] = rh.value();
+#pragma unroll
+            for (int q = 0; q < 6; q++) v9[3 + q] = q < NV ? dsum[q].value() : 0.0;
+            if (!reduce_barrier<9>(v9, A.partials, A.result, A.bar_count, A.bar_gen, err, t9)) return;
+            {
+                double s6[6];
+                dmat_mul<D>(Sl, Sm, UE, s6);
+                for (int vv = 0; vv < NV; vv++) WE[vv] = t9[3 + vv] + s6[vv];
+            }
+            double gnew = t9[0], dnew = t9[1], rnew = t9[2];
+            for (int vv = 0; vv < NV; vv++) {
+                gnew += RE[vv] * UE[vv];
+                dnew += WE[vv] * UE[vv];
+                rnew += RE[vv] * RE[vv];
+            }
+            if (first) {
+                first = false;
+                gamma = gnew;
+                delta = dnew;
+                continue;
+            }
+            cur = nxt;
+            it++;
+            rho = rnew;
+            if (sqrt(rnew) <= A.rtol * bnorm) { conv = true; break; }
+            if (it >= A.maxit) break;
+            gamma_prev = gamma;
+            alpha_prev = alpha;
+            gamma = gnew;
+            delta = dnew;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            for (int vv = 0; vv < NV; vv++) A.sc->E[vv] = XE[vv];
+            A.sc->iters = it;
+            A.sc->bnorm = bnorm;
+            A.sc->relres = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;
+            if (!conv) atomicMax(err, 4);
+            A.dg->cg_last = it;
+            if (it > A.dg->cg_max) A.dg->cg_max = it;
+            A.dg->cg_total += it;
+        }
+    }
+}
+
+} // namespace pfdev

@@ -231,6 +231,12 @@ template <int D> __device__ __forceinline__ void cell_coords(const Params &P, lo
     k = D == 3 ? (int)(r / P.ny) : 0;
 }
 __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+// periodic index for any a (tile halos of grids smaller than a tile)
+__device__ __forceinline__ int wrapm(int a, int n) { int m = a % n; return m < 0 ? m + n : m; }
+template <int D> __device__ __forceinline__ long long linm(const Params &P, int i, int j, int k)
+{
+    return (long long)wrapm(i, P.nx) + (long long)P.nx * ((long long)wrapm(j, P.ny) + (D == 3 ? (long long)P.ny * wrapm(k, P.nz) : 0LL));
+}
 template <int D> __device__ __forceinline__ long long lin(const Params &P, int i, int j, int k)
 {
     return (long long)wrap(i, P.nx) + (long long)P.nx * ((long long)wrap(j, P.ny) + (D == 3 ? (long long)P.ny * wrap(k, P.nz) : 0LL));

@@ -61,29 +61,6 @@ __global__ void k_setup(Params P, FieldPtrs<T, D> F)
     }
 }
 
-// ---------------------------------------------------------------------------
-// K3/K4: persistent cooperative Jacobi-PCG for the periodic fluctuation u and
-// the mean strain E (Voigt), with the operator
-//     A = sum_e int [B | I]^T D_e [B | I]
-// applied matrix-free, node by node, from the element tables.  Convergence is
-// decided on the device; the host launches once per solve.
-// ---------------------------------------------------------------------------
-template <typename T, int D>
-struct CGArgs {
-    Params P;
-    const T *lam, *mu;
-    const T *sig[6];
-    T *x[3], *r[3], *p[3], *q[3];
-    T *diag;
-    double *partials;
-    unsigned int *bar_count, *bar_gen;
-    Scalars *sc;
-    Diag *dg;
-    double rtol;
-    int maxit;
-    int warm;
-};
-
 // Voigt stiffness D(lam, mu) times e (double, used for the few mean-strain dofs)
 template <int D>
 __device__ __forceinline__ void dmat_mul(double lam, double mu, const double *e, double *s)
@@ -102,279 +79,6 @@ template <int D>
 __device__ __forceinline__ void node_of(int a, int &ox, int &oy, int &oz)
 {
     ox = a & 1; oy = (a >> 1) & 1; oz = D == 3 ? (a >> 2) & 1 : 0;
-}
-
-template <typename T, int D>
-__global__ void __launch_bounds__(256) k_cg(CGArgs<T, D> A)
-{
-    constexpr int NV = Dims<D>::NV, NN = Dims<D>::NN;
-    const Params &P = A.P;
-    const long long N = P.N;
-    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long st = (long long)gridDim.x * blockDim.x;
-    const int nb = gridDim.x;
-    double *myp = A.partials + (size_t)blockIdx.x * PSTRIDE;
-    int *err = &A.sc->status;
-
-    // ---------------- init: b, diag, r = b - A x0, sums over cells ----------
-    double XE[6] = {0, 0, 0, 0, 0, 0};
-    if (A.warm) {
-        for (int v = 0; v < NV; v++) XE[v] = A.sc->E[v];
-    }
-    {
-        Acc<T> bb, rz, rr, sl, sm, ss[NV], de[NV];
-        for (long long n = t0; n < N; n += st) {
-            int i, j, k;
-            cell_coords<D>(P, n, i, j, k);
-            T b[D], ax[D];
-#pragma unroll
-            for (int d = 0; d < D; d++) { b[d] = T(0); ax[d] = T(0); }
-            T dgn = T(0);
-#pragma unroll
-            for (int a = 0; a < NN; a++) {
-                int ox, oy, oz;
-                node_of<D>(a, ox, oy, oz);
-                const int ci = i - ox, cj = j - oy, ck = k - oz;
-                const long long c = lin<D>(P, ci, cj, ck);
-                const T l = A.lam[c], m = A.mu[c];
-                dgn += l * KdL<T, D>() + m * KdM<T, D>();
-                T s[NV], bt[D];
-#pragma unroll
-                for (int v = 0; v < NV; v++) s[v] = A.sig[v][c];
-                bbar_t<T, D>(a, s, bt);
-#pragma unroll
-                for (int d = 0; d < D; d++) b[d] += bt[d];
-                if (A.warm) {
-                    T ue[NN][D];
-#pragma unroll
-                    for (int bn = 0; bn < NN; bn++) {
-                        int px, py, pz;
-                        node_of<D>(bn, px, py, pz);
-                        const long long mm = lin<D>(P, ci + px, cj + py, ck + pz);
-#pragma unroll
-                        for (int d = 0; d < D; d++) ue[bn][d] = A.x[d][mm];
-                    }
-#pragma unroll
-                    for (int co = 0; co < D; co++) {
-                        T acc = T(0);
-#pragma unroll
-                        for (int bn = 0; bn < NN; bn++)
-#pragma unroll
-                            for (int cc = 0; cc < D; cc++)
-                                acc += (l * Kl<T, D>(a * D + co, bn * D + cc) + m * Km<T, D>(a * D + co, bn * D + cc)) * ue[bn][cc];
-                        ax[co] += acc;
-                    }
-                    T e[NV], se[NV];
-#pragma unroll
-                    for (int v = 0; v < NV; v++) e[v] = (T)XE[v];
-                    voigt_stress<T, D>(l, m, e, se);
-                    bbar_t<T, D>(a, se, bt);
-#pragma unroll
-                    for (int d = 0; d < D; d++) ax[d] += bt[d];
-                    if (a == 0) {      // own cell: mean-strain row of A x0
-                        T eb[NV];
-                        avg_strain<T, D>(ue, eb);
-                        voigt_stress<T, D>(l, m, eb, se);
-#pragma unroll
-                        for (int v = 0; v < NV; v++) de[v].add(se[v]);
-                    }
-                }
-                if (a == 0) {
-                    sl.add(l);
-                    sm.add(m);
-#pragma unroll
-                    for (int v = 0; v < NV; v++) ss[v].add(s[v]);
-                }
-            }
-            A.diag[n] = dgn;
-#pragma unroll
-            for (int d = 0; d < D; d++) {
-                if (!A.warm) A.x[d][n] = T(0);
-                const T rv = b[d] - ax[d];
-                A.r[d][n] = rv;
-                bb.addprod(b[d], b[d]);
-                rr.addprod(rv, rv);
-                rz.addprod(rv, rv / dgn);
-            }
-        }
-        double v[17];
-        v[0] = bb.value(); v[1] = rz.value(); v[2] = rr.value(); v[3] = sl.value(); v[4] = sm.value();
-#pragma unroll
-        for (int q = 0; q < 6; q++) { v[5 + q] = q < NV ? ss[q].value() : 0.0; v[11 + q] = q < NV ? de[q].value() : 0.0; }
-        block_sum_store<17>(v, myp);
-    }
-    if (!grid_barrier(A.bar_count, A.bar_gen, err)) return;
-    double tot[17];
-    grid_sum<17>(A.partials, nb, 0, tot);
-    const double Sl = tot[3], Sm = tot[4];
-    double DiagE[6], BE[6], RE[6], ZE[6], PE[6], QE[6], AXE[6];
-    {
-        double unit[6];
-        for (int v = 0; v < NV; v++) {
-            for (int w = 0; w < NV; w++) unit[w] = (w == v) ? 1.0 : 0.0;
-            double s[6];
-            dmat_mul<D>(Sl, Sm, unit, s);
-            DiagE[v] = s[v];
-        }
-        dmat_mul<D>(Sl, Sm, XE, AXE);
-    }
-    double bb = tot[0], rz = tot[1], rr = tot[2];
-    for (int v = 0; v < NV; v++) {
-        BE[v] = tot[5 + v] + (v < D ? (double)N * (-P.prestress) : 0.0);
-        RE[v] = BE[v] - (tot[11 + v] + AXE[v]);
-        ZE[v] = RE[v] / DiagE[v];
-        bb += BE[v] * BE[v];
-        rz += RE[v] * ZE[v];
-        rr += RE[v] * RE[v];
-        PE[v] = 0.0;
-    }
-    const double bnorm = sqrt(bb);
-    int it = 0;
-    bool conv = false;
-    if (bnorm == 0.0) {
-        for (long long n = t0; n < N; n += st)
-            for (int d = 0; d < D; d++) A.x[d][n] = T(0);
-        for (int v = 0; v < NV; v++) XE[v] = 0.0;
-        rr = 0.0;
-        conv = true;
-    } else if (sqrt(rr) <= A.rtol * bnorm) {
-        conv = true;
-    }
-    double beta = 0.0;
-    while (!conv && it < A.maxit) {
-        // ---- phase A: p = z + beta p -------------------------------------
-        const T tb = (T)beta;
-        for (long long n = t0; n < N; n += st) {
-            const T inv = T(1) / A.diag[n];
-#pragma unroll
-            for (int d = 0; d < D; d++) {
-                const T z = A.r[d][n] * inv;
-                A.p[d][n] = it == 0 ? z : z + tb * A.p[d][n];
-            }
-        }
-        for (int v = 0; v < NV; v++) PE[v] = (it == 0) ? ZE[v] : ZE[v] + beta * PE[v];
-        if (!grid_barrier(A.bar_count, A.bar_gen, err)) return;
-        // ---- phase B: q = A p, p.q, mean-strain row ------------------------
-        {
-            Acc<T> pq, de[NV];
-            T pe[6];
-#pragma unroll
-            for (int v = 0; v < NV; v++) pe[v] = (T)PE[v];
-            for (long long n = t0; n < N; n += st) {
-                int i, j, k;
-                cell_coords<D>(P, n, i, j, k);
-                T qv[D];
-#pragma unroll
-                for (int d = 0; d < D; d++) qv[d] = T(0);
-#pragma unroll
-                for (int a = 0; a < NN; a++) {
-                    int ox, oy, oz;
-                    node_of<D>(a, ox, oy, oz);
-                    const int ci = i - ox, cj = j - oy, ck = k - oz;
-                    const long long c = lin<D>(P, ci, cj, ck);
-                    const T l = A.lam[c], m = A.mu[c];
-                    T ue[NN][D];
-#pragma unroll
-                    for (int bn = 0; bn < NN; bn++) {
-                        int px, py, pz;
-                        node_of<D>(bn, px, py, pz);
-                        const long long mm = lin<D>(P, ci + px, cj + py, ck + pz);
-#pragma unroll
-                        for (int d = 0; d < D; d++) ue[bn][d] = __ldcg(A.p[d] + mm);
-                    }
-#pragma unroll
-                    for (int co = 0; co < D; co++) {
-                        T acc = T(0);
-#pragma unroll
-                        for (int bn = 0; bn < NN; bn++)
-#pragma unroll
-                            for (int cc = 0; cc < D; cc++)
-                                acc += (l * Kl<T, D>(a * D + co, bn * D + cc) + m * Km<T, D>(a * D + co, bn * D + cc)) * ue[bn][cc];
-                        qv[co] += acc;
-                    }
-                    T se[NV], bt[D];
-                    voigt_stress<T, D>(l, m, pe, se);
-                    bbar_t<T, D>(a, se, bt);
-#pragma unroll
-                    for (int d = 0; d < D; d++) qv[d] += bt[d];
-                    if (a == 0) {
-                        T eb[NV];
-                        avg_strain<T, D>(ue, eb);
-                        voigt_stress<T, D>(l, m, eb, se);
-#pragma unroll
-                        for (int v = 0; v < NV; v++) de[v].add(se[v]);
-                    }
-                }
-#pragma unroll
-                for (int d = 0; d < D; d++) {
-                    A.q[d][n] = qv[d];
-                    pq.addprod(A.p[d][n], qv[d]);
-                }
-            }
-            double v[7];
-            v[0] = pq.value();
-#pragma unroll
-            for (int q = 0; q < 6; q++) v[1 + q] = q < NV ? de[q].value() : 0.0;
-            block_sum_store<7>(v, myp);
-        }
-        if (!grid_barrier(A.bar_count, A.bar_gen, err)) return;
-        double tb7[7];
-        grid_sum<7>(A.partials, nb, 0, tb7);
-        double pqt = tb7[0];
-        {
-            double s[6];
-            dmat_mul<D>(Sl, Sm, PE, s);
-            for (int v = 0; v < NV; v++) {
-                QE[v] = tb7[1 + v] + s[v];
-                pqt += PE[v] * QE[v];
-            }
-        }
-        const double alpha = rz / pqt;
-        // ---- phase C: x += alpha p, r -= alpha q, r.z, r.r ----------------
-        {
-            const T ta = (T)alpha;
-            Acc<T> rzA, rrA;
-            for (long long n = t0; n < N; n += st) {
-                const T inv = T(1) / A.diag[n];
-#pragma unroll
-                for (int d = 0; d < D; d++) {
-                    const T pv = A.p[d][n];
-                    A.x[d][n] += ta * pv;
-                    const T rv = A.r[d][n] - ta * A.q[d][n];
-                    A.r[d][n] = rv;
-                    rzA.addprod(rv, rv * inv);
-                    rrA.addprod(rv, rv);
-                }
-            }
-            double v[2] = {rzA.value(), rrA.value()};
-            block_sum_store<2>(v, myp + 8);
-        }
-        for (int v = 0; v < NV; v++) {
-            XE[v] += alpha * PE[v];
-            RE[v] -= alpha * QE[v];
-            ZE[v] = RE[v] / DiagE[v];
-        }
-        if (!grid_barrier(A.bar_count, A.bar_gen, err)) return;
-        double t2[2];
-        grid_sum<2>(A.partials, nb, 8, t2);
-        double rzn = t2[0], rrn = t2[1];
-        for (int v = 0; v < NV; v++) { rzn += RE[v] * ZE[v]; rrn += RE[v] * RE[v]; }
-        it++;
-        rr = rrn;
-        if (sqrt(rrn) <= A.rtol * bnorm) { conv = true; break; }
-        beta = rzn / rz;
-        rz = rzn;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int v = 0; v < NV; v++) A.sc->E[v] = XE[v];
-        A.sc->iters = it;
-        A.sc->bnorm = bnorm;
-        A.sc->relres = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
-        if (!conv) atomicMax(err, 4);
-        A.dg->cg_last = it;
-        if (it > A.dg->cg_max) A.dg->cg_max = it;
-        A.dg->cg_total += it;
-    }
 }
 
 // ---------------------------------------------------------------------------

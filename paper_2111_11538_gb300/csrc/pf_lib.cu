@@ -10,7 +10,7 @@
 #include <vector>
 
 #include "pf.h"
-#include "pf_kernels.cuh"
+#include "pf_cg.cuh"
 
 using namespace pfdev;
 
@@ -146,7 +146,8 @@ struct pf_handle {
     int cur = 0;
     void *phig = nullptr, *mob = nullptr, *muO = nullptr, *MO = nullptr, *trE = nullptr, *devE2 = nullptr;
     void *lam = nullptr, *mu = nullptr, *sig[6] = {}, *ep[6] = {}, *alpha = nullptr, *sigma[6] = {};
-    void *u[3] = {}, *r[3] = {}, *p[3] = {}, *q[3] = {}, *diag = nullptr;
+    void *u[3] = {}, *p[3] = {}, *r[2][3] = {}, *w[2][3] = {}, *s[2][3] = {}, *diag = nullptr;
+    double *result = nullptr;
     unsigned char *mask = nullptr;
     double *partials = nullptr;
     int npart = 0;
@@ -261,10 +262,10 @@ template <typename T, int D>
 int setup_cg_launch(pf_handle *h)
 {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<T, D>, h->cg_block, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<T, D>, h->cg_block, 0);
     if (e != cudaSuccess) return h->cuda(e, "occupancy query");
     if (per_sm < 1) return h->fail(PF_ECUDA, "CG kernel cannot be resident");
-    if (per_sm > 2) per_sm = 2;
+    if (per_sm > 4) per_sm = 4;
     long long want = (h->P.N + h->cg_block - 1) / h->cg_block;
     long long g = (long long)per_sm * h->sms;
     if (want < g) g = want;
@@ -284,20 +285,24 @@ int run_steps(pf_handle *h, int nsteps, cudaStream_t s)
             h->mark_begin(PF_K_SETUP, s);
             k_setup<T, D><<<ge, 256, 0, s>>>(P, F);
             h->mark_end(s);
-            CGArgs<T, D> A;
+            PCGArgs<T, D> A;
             A.P = P;
             A.lam = (const T *)h->lam; A.mu = (const T *)h->mu;
             for (int v = 0; v < 6; v++) A.sig[v] = (const T *)h->sig[v];
-            for (int d = 0; d < 3; d++) { A.x[d] = (T *)h->u[d]; A.r[d] = (T *)h->r[d]; A.p[d] = (T *)h->p[d]; A.q[d] = (T *)h->q[d]; }
+            for (int d = 0; d < 3; d++) {
+                A.x[d] = (T *)h->u[d]; A.p[d] = (T *)h->p[d];
+                for (int k = 0; k < 2; k++) { A.r[k][d] = (T *)h->r[k][d]; A.w[k][d] = (T *)h->w[k][d]; A.s[k][d] = (T *)h->s[k][d]; }
+            }
             A.diag = (T *)h->diag;
             A.partials = h->partials;
+            A.result = h->result;
             A.bar_count = h->sync; A.bar_gen = h->sync + 1;
             A.sc = h->sc; A.dg = h->dg;
             A.rtol = h->cfg.cg_rtol; A.maxit = h->cfg.cg_maxit;
             A.warm = h->cfg.warm_start == PF_WS_PREV ? 1 : 0;
             void *args[] = {&A};
             h->mark_begin(PF_K_CG, s);
-            cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_cg<T, D>, dim3(h->cg_grid), dim3(h->cg_block), args, 0, s);
+            cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_pcg<T, D>, dim3(h->cg_grid), dim3(h->cg_block), args, 0, s);
             h->mark_end(s);
             if (e != cudaSuccess) return h->cuda(e, "cooperative CG launch");
             const int want_sigma = (step == nsteps - 1) ? 1 : 0;
@@ -480,8 +485,12 @@ int alloc_fields(pf_handle *h)
         PF_TRY(h->alloc(&h->lam, b)); PF_TRY(h->alloc(&h->mu, b));
         for (int v = 0; v < NV; v++) PF_TRY(h->alloc(&h->sig[v], b));
         for (int d = 0; d < D; d++) {
-            PF_TRY(h->alloc(&h->r[d], b)); PF_TRY(h->alloc(&h->p[d], b)); PF_TRY(h->alloc(&h->q[d], b));
+            PF_TRY(h->alloc(&h->p[d], b));
+            for (int k = 0; k < 2; k++) {
+                PF_TRY(h->alloc(&h->r[k][d], b)); PF_TRY(h->alloc(&h->w[k][d], b)); PF_TRY(h->alloc(&h->s[k][d], b));
+            }
         }
+        PF_TRY(h->alloc(&h->result, sizeof(double) * 32));
         PF_TRY(h->alloc(&h->diag, b));
     }
     for (int d = 0; d < D; d++) PF_TRY(h->alloc(&h->u[d], b));

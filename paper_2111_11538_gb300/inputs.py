@@ -73,7 +73,7 @@ def _periodic_nearest(points, shape):
 
 
 def porous(shape, n_grains, pore_fraction, pore_median, pore_sigma, seed,
-           delta=3.0, supply_layers=2, mob_range=(0.8, 1.2)):
+           delta=3.0, supply_layers=2, mob_range=(0.8, 1.2), rim=3.0):
     """Voronoi wuestite grains with lognormal gas pores (periodic box).
 
     * n_grains seed points uniform in the box; every grain gets a mobility
@@ -81,6 +81,7 @@ def porous(shape, n_grains, pore_fraction, pore_median, pore_sigma, seed,
     * pores: balls with radii ~ lognormal(ln(pore_median), pore_sigma) at
       uniform centres, added until the gas volume fraction reaches
       pore_fraction; their edges are smoothed with the tanh profile.
+    * a ferrite rim of width `rim` cells lines every pore.
     * the outermost supply_layers cell layers of the box are gas and form the
       hydrogen supply (mask), as an open channel to the surroundings.
     """
@@ -122,11 +123,16 @@ def porous(shape, n_grains, pore_fraction, pore_median, pore_sigma, seed,
         idx[ax] = slice(shape[ax] - supply_layers, shape[ax])
         mask[tuple(idx)] = 1
     phi_g = np.where(mask == 1, 1.0, phi_g)
-    phi_w = 1.0 - phi_g
+    # the oxide next to every pore starts as a thin iron rim (the reduced
+    # surface layer, as the shell of the core-shell geometry)
+    theta = 1.0 - _tanh_step(dist - rim, delta)
+    solid = 1.0 - phi_g
+    phi_f = solid * theta
+    phi_w = solid * (1.0 - theta)
     return {
-        "phi_f": np.zeros(shape),
+        "phi_f": phi_f,
         "phi_w": phi_w,
-        "xO": X_W_INIT * phi_w,
+        "xO": X_W_INIT * phi_w + X_F_INIT * phi_f,
         "xH": XH_GAS * phi_g,
         "xW": np.zeros(shape),
         "mob": mob,
