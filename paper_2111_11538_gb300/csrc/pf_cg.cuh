@@ -31,6 +31,10 @@ struct PCGArgs {
     T *x[3], *p[3];
     T *r[2][3], *w[2][3], *s[2][3];
     T *diag;
+    T *u[3];                       // refinement mode: FP32 displacement written at the end
+    double *x64[3];                // refinement mode: FP64 solution
+    int refine;                    // 1: FP64 outer residual around the FP32 iteration
+    double eta;                    // refinement mode: relative target of one FP32 pass
     double *partials;
     double *result;                // >= 16 doubles
     unsigned int *bar_count, *bar_gen;
@@ -146,14 +150,91 @@ __device__ __forceinline__ void apply_tile(const T *su, const T *sl, const T *sm
     }
 }
 
+// Per-node part of the solve's set-up: right-hand side b = sum_e Bbar^T sig*,
+// Jacobi diagonal, A x (element tables + mean-strain coupling XE) and the own
+// cell's quantities.  TC is the arithmetic type, TV the type of x.
+template <typename T, typename TC, typename TV, int D>
+__device__ __forceinline__ void node_setup(const Params &P, long long n, const T *lam, const T *mu, const T *const *sig,
+                                           TV *const *x, const double *XE, bool use_x, TC (&b)[D], TC (&ax)[D], TC &dgn,
+                                           TC (&sig_own)[Dims<D>::NV], TC (&de_own)[Dims<D>::NV], TC &l_own, TC &m_own)
+{
+    constexpr int NN = Dims<D>::NN, NV = Dims<D>::NV;
+    int i, j, k;
+    cell_coords<D>(P, n, i, j, k);
+#pragma unroll
+    for (int d = 0; d < D; d++) { b[d] = TC(0); ax[d] = TC(0); }
+#pragma unroll
+    for (int v = 0; v < NV; v++) de_own[v] = TC(0);
+    dgn = TC(0);
+#pragma unroll
+    for (int a = 0; a < NN; a++) {
+        const int ox = a & 1, oy = (a >> 1) & 1, oz = D == 3 ? (a >> 2) & 1 : 0;
+        const int ci = i - ox, cj = j - oy, ck = k - oz;
+        const long long c = lin<D>(P, ci, cj, ck);
+        const TC l = (TC)lam[c], m = (TC)mu[c];
+        dgn += l * KdL<TC, D>() + m * KdM<TC, D>();
+        TC s[NV], bt[D];
+#pragma unroll
+        for (int v = 0; v < NV; v++) s[v] = (TC)sig[v][c];
+        bbar_t<TC, D>(a, s, bt);
+#pragma unroll
+        for (int d = 0; d < D; d++) b[d] += bt[d];
+        if (a == 0) {
+#pragma unroll
+            for (int v = 0; v < NV; v++) sig_own[v] = s[v];
+            l_own = l;
+            m_own = m;
+        }
+        if (use_x) {
+            TC ue[NN][D];
+#pragma unroll
+            for (int bn = 0; bn < NN; bn++) {
+                const int px = bn & 1, py = (bn >> 1) & 1, pz = D == 3 ? (bn >> 2) & 1 : 0;
+                const long long mm = lin<D>(P, ci + px, cj + py, ck + pz);
+#pragma unroll
+                for (int d = 0; d < D; d++) ue[bn][d] = (TC)__ldcg(x[d] + mm);
+            }
+#pragma unroll
+            for (int co = 0; co < D; co++) {
+                TC acc = TC(0);
+#pragma unroll
+                for (int bn = 0; bn < NN; bn++)
+#pragma unroll
+                    for (int cc = 0; cc < D; cc++)
+                        acc += (l * Kl<TC, D>(a * D + co, bn * D + cc) + m * Km<TC, D>(a * D + co, bn * D + cc)) * ue[bn][cc];
+                ax[co] += acc;
+            }
+            TC e[NV], se[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) e[v] = (TC)XE[v];
+            voigt_stress<TC, D>(l, m, e, se);
+            bbar_t<TC, D>(a, se, bt);
+#pragma unroll
+            for (int d = 0; d < D; d++) ax[d] += bt[d];
+            if (a == 0) {
+                TC eb[NV];
+                avg_strain<TC, D>(ue, eb);
+                voigt_stress<TC, D>(l, m, eb, de_own);
+            }
+        }
+    }
+}
+
+// The solve.  Plain mode (refine = 0): x = A.x (the displacement itself).
+// Refinement mode (FP32 storage): the solution is kept in FP64 (A.x64 and the
+// FP64 mean strain); every outer pass forms the true residual b - A x64 in
+// FP64, solves for a correction with the FP32 iteration above (A.x holds the
+// correction), adds it in FP64, and stops when the FP64 residual meets rtol;
+// the FP32 displacement A.u is written from x64 at the end.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_pcg(PCGArgs<T, D> A)
 {
-    constexpr int NV = Dims<D>::NV, NN = Dims<D>::NN;
+    constexpr int NV = Dims<D>::NV;
     constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
     constexpr int HX = TX + 2, HY = TY + 2, HZ = D == 3 ? TZ + 2 : 1;
     constexpr int CX = TX + 1, CY = TY + 1, CZ = D == 3 ? TZ + 1 : 1;
     constexpr int HN = HX * HY * HZ, HC = CX * CY * CZ;
+    constexpr int MAX_OUTER = 12;
     __shared__ T su[D * HN];
     __shared__ T sl[HC], sm[HC];
 
@@ -163,258 +244,251 @@ __global__ void __launch_bounds__(256) k_pcg(PCGArgs<T, D> A)
     const int ntx = (P.nx + TX - 1) / TX, nty = (P.ny + TY - 1) / TY, ntz = D == 3 ? (P.nz + TZ - 1) / TZ : 1;
     const int ntiles = ntx * nty * ntz;
     const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = D == 3 ? threadIdx.x / (TX * TY) : 0;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long st = (long long)gridDim.x * blockDim.x;
+    const bool refine = A.refine != 0;
 
-    // ---------------- I1: b, diag, r0 = b - A x0 and cell sums ---------------
-    double XE[6] = {0, 0, 0, 0, 0, 0};
+    double XE[6] = {0, 0, 0, 0, 0, 0};     // mean strain of x (plain) / of the correction (refine)
+    double E64[6] = {0, 0, 0, 0, 0, 0};    // FP64 mean strain of the solution (refine)
     if (A.warm)
-        for (int v = 0; v < NV; v++) XE[v] = A.sc->E[v];
-    {
-        const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-        const long long st = (long long)gridDim.x * blockDim.x;
-        Acc<T> bb, rr, sl_, sm_, ss[NV], de[NV];
-        for (long long n = t0; n < N; n += st) {
-            int i, j, k;
-            cell_coords<D>(P, n, i, j, k);
-            T b[D], ax[D];
-#pragma unroll
-            for (int d = 0; d < D; d++) { b[d] = T(0); ax[d] = T(0); }
-            T dgn = T(0);
-#pragma unroll
-            for (int a = 0; a < NN; a++) {
-                const int ox = a & 1, oy = (a >> 1) & 1, oz = D == 3 ? (a >> 2) & 1 : 0;
-                const int ci = i - ox, cj = j - oy, ck = k - oz;
-                const long long c = lin<D>(P, ci, cj, ck);
-                const T l = A.lam[c], m = A.mu[c];
-                dgn += l * KdL<T, D>() + m * KdM<T, D>();
-                T s[NV], bt[D];
-#pragma unroll
-                for (int v = 0; v < NV; v++) s[v] = A.sig[v][c];
-                bbar_t<T, D>(a, s, bt);
-#pragma unroll
-                for (int d = 0; d < D; d++) b[d] += bt[d];
-                if (A.warm) {
-                    T ue[NN][D];
-#pragma unroll
-                    for (int bn = 0; bn < NN; bn++) {
-                        const int px = bn & 1, py = (bn >> 1) & 1, pz = D == 3 ? (bn >> 2) & 1 : 0;
-                        const long long mm = lin<D>(P, ci + px, cj + py, ck + pz);
-#pragma unroll
-                        for (int d = 0; d < D; d++) ue[bn][d] = A.x[d][mm];
-                    }
-#pragma unroll
-                    for (int co = 0; co < D; co++) {
-                        T acc = T(0);
-#pragma unroll
-                        for (int bn = 0; bn < NN; bn++)
-#pragma unroll
-                            for (int cc = 0; cc < D; cc++)
-                                acc += (l * Kl<T, D>(a * D + co, bn * D + cc) + m * Km<T, D>(a * D + co, bn * D + cc)) * ue[bn][cc];
-                        ax[co] += acc;
-                    }
-                    T e[NV], se[NV];
-#pragma unroll
-                    for (int v = 0; v < NV; v++) e[v] = (T)XE[v];
-                    voigt_stress<T, D>(l, m, e, se);
-                    bbar_t<T, D>(a, se, bt);
-#pragma unroll
-                    for (int d = 0; d < D; d++) ax[d] += bt[d];
-                    if (a == 0) {
-                        T eb[NV];
-                        avg_strain<T, D>(ue, eb);
-                        voigt_stress<T, D>(l, m, eb, se);
-#pragma unroll
-                        for (int v = 0; v < NV; v++) de[v].add(se[v]);
-                    }
-                }
-                if (a == 0) {
-                    sl_.add(l);
-                    sm_.add(m);
-#pragma unroll
-                    for (int v = 0; v < NV; v++) ss[v].add(s[v]);
-                }
-            }
-            A.diag[n] = dgn;
-#pragma unroll
-            for (int d = 0; d < D; d++) {
-                if (!A.warm) A.x[d][n] = T(0);
-                A.p[d][n] = T(0);
-                A.s[0][d][n] = T(0);
-                const T rv = b[d] - ax[d];
-                A.r[0][d][n] = rv;
-                bb.addprod(b[d], b[d]);
-                rr.addprod(rv, rv);
-            }
-        }
-        double v[16];
-        v[0] = bb.value(); v[1] = rr.value(); v[2] = sl_.value(); v[3] = sm_.value();
-#pragma unroll
-        for (int q = 0; q < 6; q++) { v[4 + q] = q < NV ? ss[q].value() : 0.0; v[10 + q] = q < NV ? de[q].value() : 0.0; }
-        double tot[16];
-        if (!reduce_barrier<16>(v, A.partials, A.result, A.bar_count, A.bar_gen, err, tot)) return;
-        // scalars of the mean-strain dofs (computed identically by every block)
-        const double Sl = tot[2], Sm = tot[3];
-        double DiagE[6], BE[6], RE[6], UE[6], PE[6], SE[6], WE[6], AXE[6];
+        for (int v = 0; v < NV; v++) (refine ? E64 : XE)[v] = A.sc->E[v];
+    int it_total = 0;
+    bool conv = false;
+    double bnorm = 0.0, rho_final = 0.0;
+    for (int outer = 0; outer < (refine ? MAX_OUTER : 1); outer++) {
+        // ---------------- set-up: r0 = b - A x0, diagonal, cell sums --------
+        const bool use_x = refine ? (A.warm || outer > 0) : (A.warm != 0);
         {
-            double unit[6], s6[6];
-            for (int vv = 0; vv < NV; vv++) {
-                for (int w = 0; w < NV; w++) unit[w] = (w == vv) ? 1.0 : 0.0;
-                dmat_mul<D>(Sl, Sm, unit, s6);
-                DiagE[vv] = s6[vv];
-            }
-            dmat_mul<D>(Sl, Sm, XE, AXE);
-        }
-        double bbt = tot[0], rho = tot[1];
-        for (int vv = 0; vv < NV; vv++) {
-            BE[vv] = tot[4 + vv] + (vv < D ? (double)N * (-P.prestress) : 0.0);
-            RE[vv] = BE[vv] - (tot[10 + vv] + AXE[vv]);
-            UE[vv] = RE[vv] / DiagE[vv];
-            bbt += BE[vv] * BE[vv];
-            rho += RE[vv] * RE[vv];
-            PE[vv] = 0.0;
-            SE[vv] = 0.0;
-        }
-        const double bnorm = sqrt(bbt);
-        int it = 0;
-        bool conv = false;
-        int cur = 0;
-        if (bnorm == 0.0) {
-            for (long long n = t0; n < N; n += st)
-                for (int d = 0; d < D; d++) A.x[d][n] = T(0);
-            for (int vv = 0; vv < NV; vv++) XE[vv] = 0.0;
-            rho = 0.0;
-            conv = true;
-        } else if (sqrt(rho) <= A.rtol * bnorm) {
-            conv = true;
-        }
-        double gamma = 0.0, delta = 0.0, gamma_prev = 1.0, alpha_prev = 1.0;
-        double alpha = 0.0, beta = 0.0;
-        // ---------------- sweeps: I2 (first = true) then iterations ---------
-        bool first = true;
-        while (!conv) {
-            if (!first) {
-                beta = (it == 0) ? 0.0 : gamma / gamma_prev;
-                alpha = (it == 0) ? gamma / delta : gamma / (delta - beta * gamma / alpha_prev);
-                for (int vv = 0; vv < NV; vv++) {
-                    PE[vv] = UE[vv] + beta * PE[vv];
-                    SE[vv] = WE[vv] + beta * SE[vv];
-                    XE[vv] += alpha * PE[vv];
-                    RE[vv] -= alpha * SE[vv];
-                    UE[vv] = RE[vv] / DiagE[vv];
+            Acc<double> bb, rr, sl_, sm_, ss[NV], de[NV];
+            for (long long n = t0; n < N; n += st) {
+                double bv[D], rv[D];
+                if (refine) {
+                    double b[D], ax[D], dgn, so[NV], deo[NV], lo, mo;
+                    node_setup<T, double, double, D>(P, n, A.lam, A.mu, A.sig, A.x64, E64, use_x, b, ax, dgn, so, deo, lo, mo);
+                    A.diag[n] = (T)dgn;
+#pragma unroll
+                    for (int d = 0; d < D; d++) { bv[d] = b[d]; rv[d] = b[d] - ax[d]; }
+                    sl_.add(lo); sm_.add(mo);
+#pragma unroll
+                    for (int v = 0; v < NV; v++) { ss[v].add(so[v]); de[v].add(deo[v]); }
+                    if (!use_x)
+#pragma unroll
+                        for (int d = 0; d < D; d++) A.x64[d][n] = 0.0;
+                } else {
+                    T b[D], ax[D], dgn, so[NV], deo[NV], lo, mo;
+                    node_setup<T, T, T, D>(P, n, A.lam, A.mu, A.sig, A.x, XE, use_x, b, ax, dgn, so, deo, lo, mo);
+                    A.diag[n] = dgn;
+#pragma unroll
+                    for (int d = 0; d < D; d++) { bv[d] = (double)b[d]; rv[d] = (double)(b[d] - ax[d]); }
+                    sl_.add((double)lo); sm_.add((double)mo);
+#pragma unroll
+                    for (int v = 0; v < NV; v++) { ss[v].add((double)so[v]); de[v].add((double)deo[v]); }
+                }
+#pragma unroll
+                for (int d = 0; d < D; d++) {
+                    if (refine || !use_x) A.x[d][n] = T(0);
+                    A.p[d][n] = T(0);
+                    A.s[0][d][n] = T(0);
+                    A.r[0][d][n] = (T)rv[d];
+                    bb.addprod(bv[d], bv[d]);
+                    rr.addprod(rv[d], rv[d]);
                 }
             }
-            const T ta = (T)alpha, tb = (T)beta;
-            const int nxt = first ? cur : 1 - cur;
-            T ue[NV];
+            double v[16];
+            v[0] = bb.value(); v[1] = rr.value(); v[2] = sl_.value(); v[3] = sm_.value();
 #pragma unroll
-            for (int vv = 0; vv < NV; vv++) ue[vv] = (T)UE[vv];
-            Acc<T> ga, de_, rh, dsum[NV];
-            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-                const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
-                const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
-                // halo nodes: u_{i+1} = (r_i - alpha (w_i + beta s_{i-1})) / diag
-                for (int h = threadIdx.x; h < HN; h += blockDim.x) {
-                    const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
-                    const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
-                    const T inv = T(1) / __ldcg(A.diag + g);
-#pragma unroll
+            for (int q = 0; q < 6; q++) { v[4 + q] = q < NV ? ss[q].value() : 0.0; v[10 + q] = q < NV ? de[q].value() : 0.0; }
+            double tot[16];
+            if (!reduce_barrier<16>(v, A.partials, A.result, A.bar_count, A.bar_gen, err, tot)) return;
+            // scalars of the mean-strain dofs (computed identically by every block)
+            const double Sl = tot[2], Sm = tot[3];
+            double DiagE[6], BE[6], RE[6], UE[6], PE[6], SE[6], WE[6], AXE[6];
+            {
+                double unit[6], s6[6];
+                for (int vv = 0; vv < NV; vv++) {
+                    for (int w = 0; w < NV; w++) unit[w] = (w == vv) ? 1.0 : 0.0;
+                    dmat_mul<D>(Sl, Sm, unit, s6);
+                    DiagE[vv] = s6[vv];
+                }
+                dmat_mul<D>(Sl, Sm, refine ? E64 : XE, AXE);
+            }
+            double bbt = tot[0], rho = tot[1];
+            for (int vv = 0; vv < NV; vv++) {
+                BE[vv] = tot[4 + vv] + (vv < D ? (double)N * (-P.prestress) : 0.0);
+                RE[vv] = BE[vv] - (use_x ? tot[10 + vv] + AXE[vv] : 0.0);
+                UE[vv] = RE[vv] / DiagE[vv];
+                bbt += BE[vv] * BE[vv];
+                rho += RE[vv] * RE[vv];
+                PE[vv] = 0.0;
+                SE[vv] = 0.0;
+                if (refine) XE[vv] = 0.0;
+            }
+            bnorm = sqrt(bbt);
+            rho_final = rho;
+            if (bnorm == 0.0) {
+                for (long long n = t0; n < N; n += st)
                     for (int d = 0; d < D; d++) {
-                        T rv = __ldcg(A.r[cur][d] + g);
-                        if (!first) rv -= ta * (__ldcg(A.w[cur][d] + g) + tb * __ldcg(A.s[cur][d] + g));
-                        su[d * HN + h] = rv * inv;
+                        A.x[d][n] = T(0);
+                        if (refine) A.x64[d][n] = 0.0;
+                    }
+                for (int vv = 0; vv < NV; vv++) { XE[vv] = 0.0; E64[vv] = 0.0; }
+                rho_final = 0.0;
+                conv = true;
+                break;
+            }
+            if (sqrt(rho) <= A.rtol * bnorm) { conv = true; break; }
+            // target of this pass: the requested tolerance, or in refinement
+            // mode what an FP32 iteration can deliver on this correction
+            const double target = refine ? fmax(0.5 * A.rtol * bnorm, A.eta * sqrt(rho)) : A.rtol * bnorm;
+            double gamma = 0.0, delta = 0.0, gamma_prev = 1.0, alpha_prev = 1.0;
+            double alpha = 0.0, beta = 0.0;
+            bool first = true, inner_conv = false;
+            int it = 0, cur = 0;
+            while (true) {
+                if (!first) {
+                    beta = (it == 0) ? 0.0 : gamma / gamma_prev;
+                    alpha = (it == 0) ? gamma / delta : gamma / (delta - beta * gamma / alpha_prev);
+                    for (int vv = 0; vv < NV; vv++) {
+                        PE[vv] = UE[vv] + beta * PE[vv];
+                        SE[vv] = WE[vv] + beta * SE[vv];
+                        XE[vv] += alpha * PE[vv];
+                        RE[vv] -= alpha * SE[vv];
+                        UE[vv] = RE[vv] / DiagE[vv];
                     }
                 }
-                for (int h = threadIdx.x; h < HC; h += blockDim.x) {
-                    const int lx = h % CX, ly = (h / CX) % CY, lz = D == 3 ? h / (CX * CY) : 0;
-                    const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
-                    sl[h] = A.lam[g];
-                    sm[h] = A.mu[g];
-                }
-                __syncthreads();
-                const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-                const bool active = gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz);
-                if (active) {
-                    const long long n = (long long)gx + (long long)P.nx * ((long long)gy + (D == 3 ? (long long)P.ny * gz : 0LL));
-                    const int lx = tx + 1, ly = ty + 1, lz = D == 3 ? tz + 1 : 0;
-                    const int hn = lx + HX * (ly + HY * lz);
-                    T un[D];
+                const T ta = (T)alpha, tb = (T)beta;
+                const int nxt = first ? cur : 1 - cur;
+                T ue[NV];
 #pragma unroll
-                    for (int d = 0; d < D; d++) un[d] = su[d * HN + hn];
-                    T rn[D];
-                    if (!first) {
-                        const T inv = T(1) / __ldcg(A.diag + n);
+                for (int vv = 0; vv < NV; vv++) ue[vv] = (T)UE[vv];
+                Acc<T> ga, de_, rh, dsum[NV];
+                for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                    const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
+                    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+                    // halo nodes: u_{i+1} = (r_i - alpha (w_i + beta s_{i-1})) / diag
+                    for (int h = threadIdx.x; h < HN; h += blockDim.x) {
+                        const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
+                        const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
+                        const T inv = T(1) / __ldcg(A.diag + g);
 #pragma unroll
                         for (int d = 0; d < D; d++) {
-                            const T ri = __ldcg(A.r[cur][d] + n);
-                            const T si = __ldcg(A.w[cur][d] + n) + tb * __ldcg(A.s[cur][d] + n);
-                            const T pi = ri * inv + tb * A.p[d][n];
-                            A.p[d][n] = pi;
-                            A.x[d][n] += ta * pi;
-                            A.s[nxt][d][n] = si;
-                            rn[d] = ri - ta * si;
-                            A.r[nxt][d][n] = rn[d];
+                            T rv = __ldcg(A.r[cur][d] + g);
+                            if (!first) rv -= ta * (__ldcg(A.w[cur][d] + g) + tb * __ldcg(A.s[cur][d] + g));
+                            su[d * HN + h] = rv * inv;
                         }
-                    } else {
-#pragma unroll
-                        for (int d = 0; d < D; d++) rn[d] = __ldcg(A.r[cur][d] + n);
                     }
-                    T q[D], eo[NV], lo, mo;
-                    apply_tile<T, D, HX, HY, CX, CY>(su, sl, sm, HN, lx, ly, lz, ue, q, eo, lo, mo);
-#pragma unroll
-                    for (int d = 0; d < D; d++) {
-                        A.w[nxt][d][n] = q[d];
-                        ga.addprod(rn[d], un[d]);
-                        de_.addprod(q[d], un[d]);
-                        rh.addprod(rn[d], rn[d]);
+                    for (int h = threadIdx.x; h < HC; h += blockDim.x) {
+                        const int lx = h % CX, ly = (h / CX) % CY, lz = D == 3 ? h / (CX * CY) : 0;
+                        const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
+                        sl[h] = A.lam[g];
+                        sm[h] = A.mu[g];
                     }
-                    T se[NV];
-                    voigt_stress<T, D>(lo, mo, eo, se);
+                    __syncthreads();
+                    const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+                    const bool active = gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz);
+                    if (active) {
+                        const long long n = (long long)gx + (long long)P.nx * ((long long)gy + (D == 3 ? (long long)P.ny * gz : 0LL));
+                        const int lx = tx + 1, ly = ty + 1, lz = D == 3 ? tz + 1 : 0;
+                        const int hn = lx + HX * (ly + HY * lz);
+                        T un[D];
 #pragma unroll
-                    for (int vv = 0; vv < NV; vv++) dsum[vv].add(se[vv]);
+                        for (int d = 0; d < D; d++) un[d] = su[d * HN + hn];
+                        T rn[D];
+                        if (!first) {
+                            const T inv = T(1) / __ldcg(A.diag + n);
+#pragma unroll
+                            for (int d = 0; d < D; d++) {
+                                const T ri = __ldcg(A.r[cur][d] + n);
+                                const T si = __ldcg(A.w[cur][d] + n) + tb * __ldcg(A.s[cur][d] + n);
+                                const T pi = ri * inv + tb * A.p[d][n];
+                                A.p[d][n] = pi;
+                                A.x[d][n] += ta * pi;
+                                A.s[nxt][d][n] = si;
+                                rn[d] = ri - ta * si;
+                                A.r[nxt][d][n] = rn[d];
+                            }
+                        } else {
+#pragma unroll
+                            for (int d = 0; d < D; d++) rn[d] = __ldcg(A.r[cur][d] + n);
+                        }
+                        T q[D], eo[NV], lo, mo;
+                        apply_tile<T, D, HX, HY, CX, CY>(su, sl, sm, HN, lx, ly, lz, ue, q, eo, lo, mo);
+#pragma unroll
+                        for (int d = 0; d < D; d++) {
+                            A.w[nxt][d][n] = q[d];
+                            ga.addprod(rn[d], un[d]);
+                            de_.addprod(q[d], un[d]);
+                            rh.addprod(rn[d], rn[d]);
+                        }
+                        T se[NV];
+                        voigt_stress<T, D>(lo, mo, eo, se);
+#pragma unroll
+                        for (int vv = 0; vv < NV; vv++) dsum[vv].add(se[vv]);
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
-            }
-            double v9[9], t9[9];
-            v9[0] = ga.value(); v9[1] = de_.value(); v9[2] = rh.value();
+                double v9[9], t9[9];
+                v9[0] = ga.value(); v9[1] = de_.value(); v9[2] = rh.value();
 #pragma unroll
-            for (int q = 0; q < 6; q++) v9[3 + q] = q < NV ? dsum[q].value() : 0.0;
-            if (!reduce_barrier<9>(v9, A.partials, A.result, A.bar_count, A.bar_gen, err, t9)) return;
-            {
-                double s6[6];
-                dmat_mul<D>(Sl, Sm, UE, s6);
-                for (int vv = 0; vv < NV; vv++) WE[vv] = t9[3 + vv] + s6[vv];
-            }
-            double gnew = t9[0], dnew = t9[1], rnew = t9[2];
-            for (int vv = 0; vv < NV; vv++) {
-                gnew += RE[vv] * UE[vv];
-                dnew += WE[vv] * UE[vv];
-                rnew += RE[vv] * RE[vv];
-            }
-            if (first) {
-                first = false;
+                for (int q = 0; q < 6; q++) v9[3 + q] = q < NV ? dsum[q].value() : 0.0;
+                if (!reduce_barrier<9>(v9, A.partials, A.result, A.bar_count, A.bar_gen, err, t9)) return;
+                {
+                    double s6[6];
+                    dmat_mul<D>(Sl, Sm, UE, s6);
+                    for (int vv = 0; vv < NV; vv++) WE[vv] = t9[3 + vv] + s6[vv];
+                }
+                double gnew = t9[0], dnew = t9[1], rnew = t9[2];
+                for (int vv = 0; vv < NV; vv++) {
+                    gnew += RE[vv] * UE[vv];
+                    dnew += WE[vv] * UE[vv];
+                    rnew += RE[vv] * RE[vv];
+                }
+                if (first) {
+                    first = false;
+                    gamma = gnew;
+                    delta = dnew;
+                    continue;
+                }
+                cur = nxt;
+                it++;
+                rho_final = rnew;
+                if (sqrt(rnew) <= target) { inner_conv = true; break; }
+                if (it_total + it >= A.maxit) break;
+                gamma_prev = gamma;
+                alpha_prev = alpha;
                 gamma = gnew;
                 delta = dnew;
-                continue;
             }
-            cur = nxt;
-            it++;
-            rho = rnew;
-            if (sqrt(rnew) <= A.rtol * bnorm) { conv = true; break; }
-            if (it >= A.maxit) break;
-            gamma_prev = gamma;
-            alpha_prev = alpha;
-            gamma = gnew;
-            delta = dnew;
+            it_total += it;
+            if (!refine) {
+                conv = inner_conv;
+                break;
+            }
+            // refinement: x64 += correction, then a grid-wide sync before the
+            // next pass reads x64 around every node
+            for (long long n = t0; n < N; n += st)
+#pragma unroll
+                for (int d = 0; d < D; d++) A.x64[d][n] += (double)A.x[d][n];
+            for (int vv = 0; vv < NV; vv++) E64[vv] += XE[vv];
+            if (it_total >= A.maxit) break;
+            double dummy[1] = {0.0}, dres[1];
+            if (!reduce_barrier<1>(dummy, A.partials, A.result, A.bar_count, A.bar_gen, err, dres)) return;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            for (int vv = 0; vv < NV; vv++) A.sc->E[vv] = XE[vv];
-            A.sc->iters = it;
-            A.sc->bnorm = bnorm;
-            A.sc->relres = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;
-            if (!conv) atomicMax(err, 4);
-            A.dg->cg_last = it;
-            if (it > A.dg->cg_max) A.dg->cg_max = it;
-            A.dg->cg_total += it;
-        }
+    }
+    if (refine) {
+        for (long long n = t0; n < N; n += st)
+#pragma unroll
+            for (int d = 0; d < D; d++) A.u[d][n] = (T)A.x64[d][n];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int vv = 0; vv < NV; vv++) A.sc->E[vv] = refine ? E64[vv] : XE[vv];
+        A.sc->iters = it_total;
+        A.sc->bnorm = bnorm;
+        A.sc->relres = bnorm > 0.0 ? sqrt(rho_final) / bnorm : 0.0;
+        if (!conv) atomicMax(err, 4);
+        A.dg->cg_last = it_total;
+        if (it_total > A.dg->cg_max) A.dg->cg_max = it_total;
+        A.dg->cg_total += it_total;
     }
 }
 

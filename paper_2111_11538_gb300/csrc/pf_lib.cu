@@ -147,6 +147,9 @@ struct pf_handle {
     void *phig = nullptr, *mob = nullptr, *muO = nullptr, *MO = nullptr, *trE = nullptr, *devE2 = nullptr;
     void *lam = nullptr, *mu = nullptr, *sig[6] = {}, *ep[6] = {}, *alpha = nullptr, *sigma[6] = {};
     void *u[3] = {}, *p[3] = {}, *r[2][3] = {}, *w[2][3] = {}, *s[2][3] = {}, *diag = nullptr;
+    void *corr[3] = {};                // mixed mode: FP32 correction of one refinement pass
+    double *x64[3] = {};               // mixed mode: FP64 displacement
+    bool refine = false;
     double *result = nullptr;
     unsigned char *mask = nullptr;
     double *partials = nullptr;
@@ -290,9 +293,12 @@ int run_steps(pf_handle *h, int nsteps, cudaStream_t s)
             A.lam = (const T *)h->lam; A.mu = (const T *)h->mu;
             for (int v = 0; v < 6; v++) A.sig[v] = (const T *)h->sig[v];
             for (int d = 0; d < 3; d++) {
-                A.x[d] = (T *)h->u[d]; A.p[d] = (T *)h->p[d];
+                A.x[d] = (T *)(h->refine ? h->corr[d] : h->u[d]); A.p[d] = (T *)h->p[d];
+                A.u[d] = (T *)h->u[d]; A.x64[d] = h->x64[d];
                 for (int k = 0; k < 2; k++) { A.r[k][d] = (T *)h->r[k][d]; A.w[k][d] = (T *)h->w[k][d]; A.s[k][d] = (T *)h->s[k][d]; }
             }
+            A.refine = h->refine ? 1 : 0;
+            A.eta = 1e-4;
             A.diag = (T *)h->diag;
             A.partials = h->partials;
             A.result = h->result;
@@ -366,6 +372,12 @@ int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
         PF_SRC(a, f->u, nb * D, h->stage);
         k_in_comp<T><<<g, 256, 0, s>>>(N, D, a, (T *const *)h->ptrtab);
         PF_TRY(h->cuda(cudaStreamSynchronize(s), "set_fields sync"));
+        if (h->refine) {
+            for (int d = 0; d < 3; d++) tab[d] = h->x64[d];
+            PF_TRY(h->cuda(cudaMemcpyAsync(h->ptrtab, tab, sizeof(tab), cudaMemcpyHostToDevice, s), "pointer table"));
+            k_in_comp<double><<<g, 256, 0, s>>>(N, D, a, (double *const *)h->ptrtab);
+            PF_TRY(h->cuda(cudaStreamSynchronize(s), "set_fields sync"));
+        }
     }
     {
         for (int v = 0; v < 6; v++) tab[v] = h->ep[v];
@@ -445,6 +457,16 @@ int get_fields_t(pf_handle *h, pf_fields *f, int where, cudaStream_t s)
     }
     struct Comp { double *dst; void *const *src; int n; };
     Comp comps[3] = {{f->u, h->u, D}, {f->eps_p, h->ep, NP}, {f->sigma, h->sigma, NP}};
+    if (f->u && h->refine) {
+        // mixed mode keeps the displacement in FP64
+        void *tab[6] = {};
+        for (int k = 0; k < D; k++) tab[k] = h->x64[k];
+        PF_TRY(h->cuda(cudaMemcpyAsync(h->ptrtab, tab, sizeof(tab), cudaMemcpyHostToDevice, s), "pointer table"));
+        k_out_comp<double><<<g, 256, 0, s>>>(N, D, (double *const *)h->ptrtab, out(f->u, h->stage));
+        PF_TRY(finish(f->u, h->stage, nb * D));
+        PF_TRY(h->cuda(cudaStreamSynchronize(s), "get sync"));
+        comps[0].dst = nullptr;
+    }
     for (auto &o : comps) {
         if (!o.dst) continue;
         void *tab[6] = {};
@@ -492,6 +514,13 @@ int alloc_fields(pf_handle *h)
         }
         PF_TRY(h->alloc(&h->result, sizeof(double) * 32));
         PF_TRY(h->alloc(&h->diag, b));
+        if (!h->fp64) {
+            h->refine = true;
+            for (int d = 0; d < D; d++) {
+                PF_TRY(h->alloc(&h->corr[d], b));
+                PF_TRY(h->alloc(&h->x64[d], sizeof(double) * (size_t)N));
+            }
+        }
     }
     for (int d = 0; d < D; d++) PF_TRY(h->alloc(&h->u[d], b));
     for (int v = 0; v < NP; v++) { PF_TRY(h->alloc(&h->ep[v], b)); PF_TRY(h->alloc(&h->sigma[v], b)); }
