@@ -227,14 +227,14 @@ __device__ __forceinline__ void node_setup(const Params &P, long long n, const T
 // correction), adds it in FP64, and stops when the FP64 residual meets rtol;
 // the FP32 displacement A.u is written from x64 at the end.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_pcg(PCGArgs<T, D> A)
+__global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
 {
     constexpr int NV = Dims<D>::NV;
     constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
     constexpr int HX = TX + 2, HY = TY + 2, HZ = D == 3 ? TZ + 2 : 1;
     constexpr int CX = TX + 1, CY = TY + 1, CZ = D == 3 ? TZ + 1 : 1;
     constexpr int HN = HX * HY * HZ, HC = CX * CY * CZ;
-    constexpr int MAX_OUTER = 12;
+    constexpr int MAX_OUTER = 24;
     __shared__ T su[D * HN];
     __shared__ T sl[HC], sm[HC];
 
@@ -362,27 +362,96 @@ __global__ void __launch_bounds__(256) k_pcg(PCGArgs<T, D> A)
 #pragma unroll
                 for (int vv = 0; vv < NV; vv++) ue[vv] = (T)UE[vv];
                 Acc<T> ga, de_, rh, dsum[NV];
+                // Register double buffering across tiles: the loads of the
+                // next tile's halo (r, w, s, diag), cells (lam, mu) and own
+                // node are issued before the current tile is staged and
+                // computed, so their latency overlaps that work.
+                constexpr int HS = (HN + 255) / 256, CS = (HC + 255) / 256;
+                struct Raw {
+                    T r[HS][D], w[HS][D], s[HS][D], dg[HS];
+                    T l[CS], m[CS];
+                    T ro[D], wo[D], so[D], xo[D], po[D], dgo;
+                };
+                auto load_raw = [&](int tile, Raw &R) {
+                    const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
+                    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+#pragma unroll
+                    for (int k = 0; k < HS; k++) {
+                        const int h = threadIdx.x + 256 * k;
+                        if (h < HN) {
+                            const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
+                            const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
+                            R.dg[k] = __ldcg(A.diag + g);
+#pragma unroll
+                            for (int d = 0; d < D; d++) {
+                                R.r[k][d] = __ldcg(A.r[cur][d] + g);
+                                if (!first) {
+                                    R.w[k][d] = __ldcg(A.w[cur][d] + g);
+                                    R.s[k][d] = __ldcg(A.s[cur][d] + g);
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < CS; k++) {
+                        const int h = threadIdx.x + 256 * k;
+                        if (h < HC) {
+                            const int lx = h % CX, ly = (h / CX) % CY, lz = D == 3 ? h / (CX * CY) : 0;
+                            const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
+                            R.l[k] = __ldg(A.lam + g);
+                            R.m[k] = __ldg(A.mu + g);
+                        }
+                    }
+                    const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+                    if (gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz)) {
+                        const long long n = (long long)gx + (long long)P.nx * ((long long)gy + (D == 3 ? (long long)P.ny * gz : 0LL));
+                        R.dgo = __ldcg(A.diag + n);
+#pragma unroll
+                        for (int d = 0; d < D; d++) {
+                            R.ro[d] = __ldcg(A.r[cur][d] + n);
+                            if (!first) {
+                                R.wo[d] = __ldcg(A.w[cur][d] + n);
+                                R.so[d] = __ldcg(A.s[cur][d] + n);
+                                R.xo[d] = A.x[d][n];
+                                R.po[d] = A.p[d][n];
+                            }
+                        }
+                    }
+                };
+                Raw R;
+                if ((int)blockIdx.x < ntiles) load_raw(blockIdx.x, R);
                 for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
                     const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
                     const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
-                    // halo nodes: u_{i+1} = (r_i - alpha (w_i + beta s_{i-1})) / diag
-                    for (int h = threadIdx.x; h < HN; h += blockDim.x) {
-                        const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
-                        const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
-                        const T inv = T(1) / __ldcg(A.diag + g);
+                    // stage this tile: u_{i+1} = (r_i - alpha (w_i + beta s_{i-1})) / diag
+                    // on the halo nodes, lam / mu on the halo cells
 #pragma unroll
-                        for (int d = 0; d < D; d++) {
-                            T rv = __ldcg(A.r[cur][d] + g);
-                            if (!first) rv -= ta * (__ldcg(A.w[cur][d] + g) + tb * __ldcg(A.s[cur][d] + g));
-                            su[d * HN + h] = rv * inv;
+                    for (int k = 0; k < HS; k++) {
+                        const int h = threadIdx.x + 256 * k;
+                        if (h < HN) {
+                            const T inv = T(1) / R.dg[k];
+#pragma unroll
+                            for (int d = 0; d < D; d++) {
+                                T rv = R.r[k][d];
+                                if (!first) rv -= ta * (R.w[k][d] + tb * R.s[k][d]);
+                                su[d * HN + h] = rv * inv;
+                            }
                         }
                     }
-                    for (int h = threadIdx.x; h < HC; h += blockDim.x) {
-                        const int lx = h % CX, ly = (h / CX) % CY, lz = D == 3 ? h / (CX * CY) : 0;
-                        const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
-                        sl[h] = A.lam[g];
-                        sm[h] = A.mu[g];
+#pragma unroll
+                    for (int k = 0; k < CS; k++) {
+                        const int h = threadIdx.x + 256 * k;
+                        if (h < HC) {
+                            sl[h] = R.l[k];
+                            sm[h] = R.m[k];
+                        }
                     }
+                    T ro[D], wo[D], so[D], xo[D], po[D];
+                    const T dgo = R.dgo;
+#pragma unroll
+                    for (int d = 0; d < D; d++) { ro[d] = R.ro[d]; wo[d] = R.wo[d]; so[d] = R.so[d]; xo[d] = R.xo[d]; po[d] = R.po[d]; }
+                    // issue the next tile's loads; they complete while this one computes
+                    if (tile + (int)gridDim.x < ntiles) load_raw(tile + gridDim.x, R);
                     __syncthreads();
                     const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
                     const bool active = gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz);
@@ -395,21 +464,21 @@ __global__ void __launch_bounds__(256) k_pcg(PCGArgs<T, D> A)
                         for (int d = 0; d < D; d++) un[d] = su[d * HN + hn];
                         T rn[D];
                         if (!first) {
-                            const T inv = T(1) / __ldcg(A.diag + n);
+                            const T inv = T(1) / dgo;
 #pragma unroll
                             for (int d = 0; d < D; d++) {
-                                const T ri = __ldcg(A.r[cur][d] + n);
-                                const T si = __ldcg(A.w[cur][d] + n) + tb * __ldcg(A.s[cur][d] + n);
-                                const T pi = ri * inv + tb * A.p[d][n];
+                                const T ri = ro[d];
+                                const T si = wo[d] + tb * so[d];
+                                const T pi = ri * inv + tb * po[d];
                                 A.p[d][n] = pi;
-                                A.x[d][n] += ta * pi;
+                                A.x[d][n] = xo[d] + ta * pi;
                                 A.s[nxt][d][n] = si;
                                 rn[d] = ri - ta * si;
                                 A.r[nxt][d][n] = rn[d];
                             }
                         } else {
 #pragma unroll
-                            for (int d = 0; d < D; d++) rn[d] = __ldcg(A.r[cur][d] + n);
+                            for (int d = 0; d < D; d++) rn[d] = ro[d];
                         }
                         T q[D], eo[NV], lo, mo;
                         apply_tile<T, D, HX, HY, CX, CY>(su, sl, sm, HN, lx, ly, lz, ue, q, eo, lo, mo);

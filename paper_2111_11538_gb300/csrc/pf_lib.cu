@@ -298,7 +298,7 @@ int run_steps(pf_handle *h, int nsteps, cudaStream_t s)
                 for (int k = 0; k < 2; k++) { A.r[k][d] = (T *)h->r[k][d]; A.w[k][d] = (T *)h->w[k][d]; A.s[k][d] = (T *)h->s[k][d]; }
             }
             A.refine = h->refine ? 1 : 0;
-            A.eta = 1e-4;
+            A.eta = 1e-3;
             A.diag = (T *)h->diag;
             A.partials = h->partials;
             A.result = h->result;
