@@ -12,8 +12,12 @@
 // vector updates, rebuilds u_{i+1} on the tile and its halo in shared memory
 // from r_i, w_i, s_{i-1} (double-buffered in global memory), applies the Q1
 // operator to it and accumulates gamma, delta and ||r||^2; the grid barrier
-// then reduces those in a fixed order (the last block to arrive reduces) and
-// every block continues with identical scalars.
+// then reduces those in a fixed order (the last block to arrive reduces).
+//
+// The few FP64 scalars of the iteration (alpha, beta, the mean-strain dofs)
+// are computed by thread 0 of every block (identically, from the same
+// reduced values) and broadcast through shared memory: FP64 runs at a small
+// fraction of the FP32 rate on this GPU, so no other thread touches them.
 #pragma once
 #include "pf_kernels.cuh"
 
@@ -36,7 +40,7 @@ struct PCGArgs {
     int refine;                    // 1: FP64 outer residual around the FP32 iteration
     double eta;                    // refinement mode: relative target of one FP32 pass
     double *partials;
-    double *result;                // >= 16 doubles
+    double *result;                // 32 doubles: [0,16) reductions, [24,30) FP64 mean strain
     unsigned int *bar_count, *bar_gen;
     Scalars *sc;
     Diag *dg;
@@ -45,17 +49,71 @@ struct PCGArgs {
     int warm;
 };
 
-// Grid barrier that also reduces K per-block values in a fixed order: the
-// last block to arrive sums the partials (block-strided, then a block tree)
-// and publishes them before releasing the others.  Waits are bounded
-// (SPIN_LIMIT polls, then PF_ETIMEOUT in *err and false is returned).
+// ---------------------------------------------------------------------------
+// Block reduction of per-thread accumulators to one FP64 value per entry,
+// written by thread 0 to dst.  FP32 accumulators are reduced as (sum, error)
+// pairs with error-free additions, so no FP64 arithmetic runs per thread.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pair_add(float &h, float &l, float h2, float l2)
+{
+    const float s = h + h2;
+    const float bp = s - h;
+    const float e = (h - (s - bp)) + (h2 - bp);
+    l = l + l2 + e;
+    h = s + l;
+    l = l - (h - s);
+}
+
 template <int K>
-__device__ bool reduce_barrier(double (&v)[K], double *partials, double *result, unsigned int *count,
+__device__ void block_reduce_store(Acc<float> (&a)[K], double *dst)
+{
+    __shared__ float sh[K][32], sl[K][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        float h = a[k].s, l = a[k].c;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+            pair_add(h, l, h2, l2);
+        }
+        if (lane == 0) { sh[k][wid] = h; sl[k][wid] = l; }
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            float h = lane < nw ? sh[k][lane] : 0.f, l = lane < nw ? sl[k][lane] : 0.f;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+                pair_add(h, l, h2, l2);
+            }
+            if (lane == 0) dst[k] = (double)h + (double)l;
+        }
+    }
+    __syncthreads();
+}
+
+template <int K>
+__device__ void block_reduce_store(Acc<double> (&a)[K], double *dst)
+{
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = a[k].value();
+    block_sum_store<K>(v, dst);
+}
+
+// Grid barrier that also reduces K per-block values in a fixed order: the
+// last block to arrive sums the partials (warp 0, lane-strided over blocks,
+// then a butterfly) and publishes them before releasing the others.  After
+// the call thread 0 holds the totals in out[].  Waits are bounded
+// (SPIN_LIMIT polls, then PF_ETIMEOUT in *err and false is returned).
+template <typename AccT, int K>
+__device__ bool reduce_barrier(AccT (&acc)[K], double *partials, double *result, unsigned int *count,
                                unsigned int *gen, int *err, double (&out)[K])
 {
     __shared__ int s_last, s_ok;
     __shared__ unsigned int s_gen;
-    block_sum_store<K>(v, partials + (size_t)blockIdx.x * PSTRIDE);
+    block_reduce_store<K>(acc, partials + (size_t)blockIdx.x * PSTRIDE);
     if (threadIdx.x == 0) {
         s_ok = 1;
         volatile unsigned int *vgen = gen;
@@ -66,36 +124,38 @@ __device__ bool reduce_barrier(double (&v)[K], double *partials, double *result,
     }
     __syncthreads();
     if (s_last) {
-        __threadfence();
-        double acc[K];
-#pragma unroll
-        for (int k = 0; k < K; k++) acc[k] = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-#pragma unroll
-            for (int k = 0; k < K; k++) acc[k] += __ldcg(partials + (size_t)b * PSTRIDE + k);
-        }
-        block_sum_store<K>(acc, result);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             __threadfence();
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
+            const int lane = threadIdx.x;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                double sacc = 0.0;
+                for (int b = lane; b < (int)gridDim.x; b += 32) sacc += __ldcg(partials + (size_t)b * PSTRIDE + k);
+                sacc = warp_sum(sacc);
+                if (lane == 0) result[k] = sacc;
+            }
+            if (lane == 0) {
+                __threadfence();
+                atomicExch(count, 0u);
+                __threadfence();
+                atomicAdd(gen, 1u);
+            }
         }
     } else if (threadIdx.x == 0) {
         volatile unsigned int *vgen = gen;
         long long spins = 0;
         while (*vgen == s_gen) {
             if (++spins > SPIN_LIMIT) { atomicExch(err, 6); s_ok = 0; break; }
-            __nanosleep(20);
+            __nanosleep(100);
         }
         __threadfence();
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; k++) out[k] = __ldcg(result + k);
-    const int ok = s_ok;
-    __syncthreads();
-    return ok != 0;
+        for (int k = 0; k < K; k++) out[k] = __ldcg(result + k);
+    }
+    return s_ok != 0;
 }
 
 // q = sum over the 2^d cells around a node of (lam K_lam + mu K_mu) u_e, plus
@@ -155,7 +215,7 @@ __device__ __forceinline__ void apply_tile(const T *su, const T *sl, const T *sm
 // cell's quantities.  TC is the arithmetic type, TV the type of x.
 template <typename T, typename TC, typename TV, int D>
 __device__ __forceinline__ void node_setup(const Params &P, long long n, const T *lam, const T *mu, const T *const *sig,
-                                           TV *const *x, const double *XE, bool use_x, TC (&b)[D], TC (&ax)[D], TC &dgn,
+                                           TV *const *x, const TC *XE, bool use_x, TC (&b)[D], TC (&ax)[D], TC &dgn,
                                            TC (&sig_own)[Dims<D>::NV], TC (&de_own)[Dims<D>::NV], TC &l_own, TC &m_own)
 {
     constexpr int NN = Dims<D>::NN, NV = Dims<D>::NV;
@@ -204,10 +264,8 @@ __device__ __forceinline__ void node_setup(const Params &P, long long n, const T
                         acc += (l * Kl<TC, D>(a * D + co, bn * D + cc) + m * Km<TC, D>(a * D + co, bn * D + cc)) * ue[bn][cc];
                 ax[co] += acc;
             }
-            TC e[NV], se[NV];
-#pragma unroll
-            for (int v = 0; v < NV; v++) e[v] = (TC)XE[v];
-            voigt_stress<TC, D>(l, m, e, se);
+            TC se[NV];
+            voigt_stress<TC, D>(l, m, XE, se);
             bbar_t<TC, D>(a, se, bt);
 #pragma unroll
             for (int d = 0; d < D; d++) ax[d] += bt[d];
@@ -220,10 +278,13 @@ __device__ __forceinline__ void node_setup(const Params &P, long long n, const T
     }
 }
 
+// Control words broadcast by thread 0.
+enum { CTL_RUN = 0, CTL_DONE = 1, CTL_ZERO = 2, CTL_STOP = 3 };
+
 // The solve.  Plain mode (refine = 0): x = A.x (the displacement itself).
 // Refinement mode (FP32 storage): the solution is kept in FP64 (A.x64 and the
 // FP64 mean strain); every outer pass forms the true residual b - A x64 in
-// FP64, solves for a correction with the FP32 iteration above (A.x holds the
+// FP64, solves for a correction with the FP32 iteration (A.x holds the
 // correction), adds it in FP64, and stops when the FP64 residual meets rtol;
 // the FP32 displacement A.u is written from x64 at the end.
 template <typename T, int D>
@@ -237,6 +298,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
     constexpr int MAX_OUTER = 24;
     __shared__ T su[D * HN];
     __shared__ T sl[HC], sm[HC];
+    __shared__ T s_ta, s_tb, s_ue[6], s_xe[6];
+    __shared__ int s_ctl;
 
     const Params &P = A.P;
     const long long N = P.N;
@@ -247,42 +310,75 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long st = (long long)gridDim.x * blockDim.x;
     const bool refine = A.refine != 0;
+    const bool lead = threadIdx.x == 0;
 
-    double XE[6] = {0, 0, 0, 0, 0, 0};     // mean strain of x (plain) / of the correction (refine)
-    double E64[6] = {0, 0, 0, 0, 0, 0};    // FP64 mean strain of the solution (refine)
-    if (A.warm)
-        for (int v = 0; v < NV; v++) (refine ? E64 : XE)[v] = A.sc->E[v];
-    int it_total = 0;
+    // FP64 state of the iteration, in shared memory and touched only by
+    // thread 0 (so it costs the other threads no registers).
+    struct State {
+        double XE[6];      // mean strain of x (plain) / of the correction (refine)
+        double E64[6];     // FP64 mean strain of the solution (refine)
+        double DiagE[6], RE[6], UE[6], PE[6], SE[6], WE[6];
+        double Sl, Sm, bnorm, rho_final, target;
+        double gamma, delta, gamma_prev, alpha_prev, alpha, beta;
+        int it, it_total, conv;
+    };
+    __shared__ State S;
+    double *XE = S.XE, *E64 = S.E64, *DiagE = S.DiagE, *RE = S.RE, *UE = S.UE, *PE = S.PE, *SE = S.SE, *WE = S.WE;
+    double &Sl = S.Sl, &Sm = S.Sm, &bnorm = S.bnorm, &rho_final = S.rho_final, &target = S.target;
+    double &gamma = S.gamma, &delta = S.delta, &gamma_prev = S.gamma_prev, &alpha_prev = S.alpha_prev;
+    double &alpha = S.alpha, &beta = S.beta;
+    int &it = S.it, &it_total = S.it_total;
     bool conv = false;
-    double bnorm = 0.0, rho_final = 0.0;
+    if (lead) {
+        for (int v = 0; v < 6; v++) { XE[v] = 0.0; E64[v] = 0.0; }
+        Sl = Sm = bnorm = rho_final = target = 0.0;
+        gamma = delta = alpha = beta = 0.0;
+        gamma_prev = alpha_prev = 1.0;
+        it = 0;
+        it_total = 0;
+        if (A.warm)
+            for (int v = 0; v < NV; v++) (refine ? E64 : XE)[v] = A.sc->E[v];
+    }
+
     for (int outer = 0; outer < (refine ? MAX_OUTER : 1); outer++) {
         // ---------------- set-up: r0 = b - A x0, diagonal, cell sums --------
         const bool use_x = refine ? (A.warm || outer > 0) : (A.warm != 0);
+        if (lead)
+            for (int v = 0; v < NV; v++) s_xe[v] = (T)(refine ? 0.0 : XE[v]);
+        __syncthreads();
         {
-            Acc<double> bb, rr, sl_, sm_, ss[NV], de[NV];
+            // every thread needs the mean strain of x for A x: FP64 from the
+            // previous pass (refine) or the FP32 copy broadcast above
+            double xe64[6];
+            T xeT[6];
+            for (int v = 0; v < NV; v++) {
+                xe64[v] = outer == 0 ? (A.warm ? A.sc->E[v] : 0.0) : __ldcg(A.result + 24 + v);
+                xeT[v] = s_xe[v];
+            }
+            Acc<double> acc[16];
             for (long long n = t0; n < N; n += st) {
                 double bv[D], rv[D];
                 if (refine) {
                     double b[D], ax[D], dgn, so[NV], deo[NV], lo, mo;
-                    node_setup<T, double, double, D>(P, n, A.lam, A.mu, A.sig, A.x64, E64, use_x, b, ax, dgn, so, deo, lo, mo);
+                    node_setup<T, double, double, D>(P, n, A.lam, A.mu, A.sig, A.x64, xe64, use_x, b, ax, dgn, so, deo, lo, mo);
                     A.diag[n] = (T)dgn;
 #pragma unroll
                     for (int d = 0; d < D; d++) { bv[d] = b[d]; rv[d] = b[d] - ax[d]; }
-                    sl_.add(lo); sm_.add(mo);
+                    acc[2].add(lo); acc[3].add(mo);
 #pragma unroll
-                    for (int v = 0; v < NV; v++) { ss[v].add(so[v]); de[v].add(deo[v]); }
+                    for (int v = 0; v < NV; v++) { acc[4 + v].add(so[v]); acc[10 + v].add(deo[v]); }
                     if (!use_x)
 #pragma unroll
                         for (int d = 0; d < D; d++) A.x64[d][n] = 0.0;
                 } else {
                     T b[D], ax[D], dgn, so[NV], deo[NV], lo, mo;
-                    node_setup<T, T, T, D>(P, n, A.lam, A.mu, A.sig, A.x, XE, use_x, b, ax, dgn, so, deo, lo, mo);
+                    node_setup<T, T, T, D>(P, n, A.lam, A.mu, A.sig, A.x, xeT, use_x, b, ax, dgn, so, deo, lo, mo);
                     A.diag[n] = dgn;
 #pragma unroll
                     for (int d = 0; d < D; d++) { bv[d] = (double)b[d]; rv[d] = (double)(b[d] - ax[d]); }
-                    sl_.add((double)lo); sm_.add((double)mo);
+                    acc[2].add((double)lo); acc[3].add((double)mo);
 #pragma unroll
-                    for (int v = 0; v < NV; v++) { ss[v].add((double)so[v]); de[v].add((double)deo[v]); }
+                    for (int v = 0; v < NV; v++) { acc[4 + v].add((double)so[v]); acc[10 + v].add((double)deo[v]); }
                 }
 #pragma unroll
                 for (int d = 0; d < D; d++) {
@@ -290,61 +386,69 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
                     A.p[d][n] = T(0);
                     A.s[0][d][n] = T(0);
                     A.r[0][d][n] = (T)rv[d];
-                    bb.addprod(bv[d], bv[d]);
-                    rr.addprod(rv[d], rv[d]);
+                    acc[0].addprod(bv[d], bv[d]);
+                    acc[1].addprod(rv[d], rv[d]);
                 }
             }
-            double v[16];
-            v[0] = bb.value(); v[1] = rr.value(); v[2] = sl_.value(); v[3] = sm_.value();
-#pragma unroll
-            for (int q = 0; q < 6; q++) { v[4 + q] = q < NV ? ss[q].value() : 0.0; v[10 + q] = q < NV ? de[q].value() : 0.0; }
             double tot[16];
-            if (!reduce_barrier<16>(v, A.partials, A.result, A.bar_count, A.bar_gen, err, tot)) return;
-            // scalars of the mean-strain dofs (computed identically by every block)
-            const double Sl = tot[2], Sm = tot[3];
-            double DiagE[6], BE[6], RE[6], UE[6], PE[6], SE[6], WE[6], AXE[6];
-            {
-                double unit[6], s6[6];
+            if (!reduce_barrier<Acc<double>, 16>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tot)) return;
+            if (lead) {
+                // scalars of the mean-strain dofs
+                Sl = tot[2];
+                Sm = tot[3];
+                double AXE[6], unit[6], s6[6];
                 for (int vv = 0; vv < NV; vv++) {
                     for (int w = 0; w < NV; w++) unit[w] = (w == vv) ? 1.0 : 0.0;
                     dmat_mul<D>(Sl, Sm, unit, s6);
                     DiagE[vv] = s6[vv];
                 }
                 dmat_mul<D>(Sl, Sm, refine ? E64 : XE, AXE);
+                double bbt = tot[0], rho = tot[1];
+                for (int vv = 0; vv < NV; vv++) {
+                    const double BE = tot[4 + vv] + (vv < D ? (double)N * (-P.prestress) : 0.0);
+                    RE[vv] = BE - (use_x ? tot[10 + vv] + AXE[vv] : 0.0);
+                    UE[vv] = RE[vv] / DiagE[vv];
+                    bbt += BE * BE;
+                    rho += RE[vv] * RE[vv];
+                    PE[vv] = 0.0;
+                    SE[vv] = 0.0;
+                    if (refine) XE[vv] = 0.0;
+                }
+                bnorm = sqrt(bbt);
+                rho_final = rho;
+                int ctl = CTL_RUN;
+                if (bnorm == 0.0) ctl = CTL_ZERO;
+                else if (sqrt(rho) <= A.rtol * bnorm) ctl = CTL_DONE;
+                // target of this pass: the requested tolerance, or in refinement
+                // mode what an FP32 iteration can deliver on this correction
+                target = refine ? fmax(0.5 * A.rtol * bnorm, A.eta * sqrt(rho)) : A.rtol * bnorm;
+                gamma = 0.0; delta = 0.0; gamma_prev = 1.0; alpha_prev = 1.0; alpha = 0.0; beta = 0.0;
+                it = 0;
+                s_ctl = ctl;
             }
-            double bbt = tot[0], rho = tot[1];
-            for (int vv = 0; vv < NV; vv++) {
-                BE[vv] = tot[4 + vv] + (vv < D ? (double)N * (-P.prestress) : 0.0);
-                RE[vv] = BE[vv] - (use_x ? tot[10 + vv] + AXE[vv] : 0.0);
-                UE[vv] = RE[vv] / DiagE[vv];
-                bbt += BE[vv] * BE[vv];
-                rho += RE[vv] * RE[vv];
-                PE[vv] = 0.0;
-                SE[vv] = 0.0;
-                if (refine) XE[vv] = 0.0;
-            }
-            bnorm = sqrt(bbt);
-            rho_final = rho;
-            if (bnorm == 0.0) {
-                for (long long n = t0; n < N; n += st)
-                    for (int d = 0; d < D; d++) {
-                        A.x[d][n] = T(0);
-                        if (refine) A.x64[d][n] = 0.0;
-                    }
+            __syncthreads();
+        }
+        const int ctl0 = s_ctl;
+        if (ctl0 == CTL_ZERO) {
+            for (long long n = t0; n < N; n += st)
+                for (int d = 0; d < D; d++) {
+                    A.x[d][n] = T(0);
+                    if (refine) A.x64[d][n] = 0.0;
+                }
+            if (lead) {
                 for (int vv = 0; vv < NV; vv++) { XE[vv] = 0.0; E64[vv] = 0.0; }
                 rho_final = 0.0;
-                conv = true;
-                break;
             }
-            if (sqrt(rho) <= A.rtol * bnorm) { conv = true; break; }
-            // target of this pass: the requested tolerance, or in refinement
-            // mode what an FP32 iteration can deliver on this correction
-            const double target = refine ? fmax(0.5 * A.rtol * bnorm, A.eta * sqrt(rho)) : A.rtol * bnorm;
-            double gamma = 0.0, delta = 0.0, gamma_prev = 1.0, alpha_prev = 1.0;
-            double alpha = 0.0, beta = 0.0;
-            bool first = true, inner_conv = false;
-            int it = 0, cur = 0;
-            while (true) {
+            conv = true;
+            break;
+        }
+        if (ctl0 == CTL_DONE) { conv = true; break; }
+
+        // ---------------- sweeps: the first builds w_0, then iterations -----
+        bool first = true;
+        int cur = 0;
+        while (true) {
+            if (lead) {
                 if (!first) {
                     beta = (it == 0) ? 0.0 : gamma / gamma_prev;
                     alpha = (it == 0) ? gamma / delta : gamma / (delta - beta * gamma / alpha_prev);
@@ -356,200 +460,215 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
                         UE[vv] = RE[vv] / DiagE[vv];
                     }
                 }
-                const T ta = (T)alpha, tb = (T)beta;
-                const int nxt = first ? cur : 1 - cur;
-                T ue[NV];
+                s_ta = (T)alpha;
+                s_tb = (T)beta;
+                for (int vv = 0; vv < NV; vv++) s_ue[vv] = (T)UE[vv];
+            }
+            __syncthreads();
+            const T ta = s_ta, tb = s_tb;
+            T ue[NV];
 #pragma unroll
-                for (int vv = 0; vv < NV; vv++) ue[vv] = (T)UE[vv];
-                Acc<T> ga, de_, rh, dsum[NV];
-                // Register double buffering across tiles: the loads of the
-                // next tile's halo (r, w, s, diag), cells (lam, mu) and own
-                // node are issued before the current tile is staged and
-                // computed, so their latency overlaps that work.
-                constexpr int HS = (HN + 255) / 256, CS = (HC + 255) / 256;
-                struct Raw {
-                    T r[HS][D], w[HS][D], s[HS][D], dg[HS];
-                    T l[CS], m[CS];
-                    T ro[D], wo[D], so[D], xo[D], po[D], dgo;
-                };
-                auto load_raw = [&](int tile, Raw &R) {
-                    const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
-                    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+            for (int vv = 0; vv < NV; vv++) ue[vv] = s_ue[vv];
+            const int nxt = first ? cur : 1 - cur;
+            Acc<T> acc[3 + NV];      // gamma, delta, ||r||^2, mean-strain row
+            // Register double buffering across tiles: the loads of the next
+            // tile's halo (r, w, s, diag), cells (lam, mu) and own node are
+            // issued before the current tile is staged and computed, so their
+            // latency overlaps that work.
+            constexpr int HS = (HN + 255) / 256, CS = (HC + 255) / 256;
+            struct Raw {
+                T r[HS][D], w[HS][D], s[HS][D], dg[HS];
+                T l[CS], m[CS];
+                T ro[D], wo[D], so[D], xo[D], po[D], dgo;
+            };
+            auto load_raw = [&](int tile, Raw &R) {
+                const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
+                const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
 #pragma unroll
-                    for (int k = 0; k < HS; k++) {
-                        const int h = threadIdx.x + 256 * k;
-                        if (h < HN) {
-                            const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
-                            const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
-                            R.dg[k] = __ldcg(A.diag + g);
-#pragma unroll
-                            for (int d = 0; d < D; d++) {
-                                R.r[k][d] = __ldcg(A.r[cur][d] + g);
-                                if (!first) {
-                                    R.w[k][d] = __ldcg(A.w[cur][d] + g);
-                                    R.s[k][d] = __ldcg(A.s[cur][d] + g);
-                                }
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < CS; k++) {
-                        const int h = threadIdx.x + 256 * k;
-                        if (h < HC) {
-                            const int lx = h % CX, ly = (h / CX) % CY, lz = D == 3 ? h / (CX * CY) : 0;
-                            const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
-                            R.l[k] = __ldg(A.lam + g);
-                            R.m[k] = __ldg(A.mu + g);
-                        }
-                    }
-                    const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-                    if (gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz)) {
-                        const long long n = (long long)gx + (long long)P.nx * ((long long)gy + (D == 3 ? (long long)P.ny * gz : 0LL));
-                        R.dgo = __ldcg(A.diag + n);
+                for (int k = 0; k < HS; k++) {
+                    const int h = threadIdx.x + 256 * k;
+                    if (h < HN) {
+                        const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
+                        const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
+                        R.dg[k] = __ldcg(A.diag + g);
 #pragma unroll
                         for (int d = 0; d < D; d++) {
-                            R.ro[d] = __ldcg(A.r[cur][d] + n);
+                            R.r[k][d] = __ldcg(A.r[cur][d] + g);
                             if (!first) {
-                                R.wo[d] = __ldcg(A.w[cur][d] + n);
-                                R.so[d] = __ldcg(A.s[cur][d] + n);
-                                R.xo[d] = A.x[d][n];
-                                R.po[d] = A.p[d][n];
+                                R.w[k][d] = __ldcg(A.w[cur][d] + g);
+                                R.s[k][d] = __ldcg(A.s[cur][d] + g);
                             }
                         }
                     }
-                };
-                Raw R;
-                if ((int)blockIdx.x < ntiles) load_raw(blockIdx.x, R);
-                for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-                    const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
-                    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
-                    // stage this tile: u_{i+1} = (r_i - alpha (w_i + beta s_{i-1})) / diag
-                    // on the halo nodes, lam / mu on the halo cells
+                }
 #pragma unroll
-                    for (int k = 0; k < HS; k++) {
-                        const int h = threadIdx.x + 256 * k;
-                        if (h < HN) {
-                            const T inv = T(1) / R.dg[k];
-#pragma unroll
-                            for (int d = 0; d < D; d++) {
-                                T rv = R.r[k][d];
-                                if (!first) rv -= ta * (R.w[k][d] + tb * R.s[k][d]);
-                                su[d * HN + h] = rv * inv;
-                            }
-                        }
+                for (int k = 0; k < CS; k++) {
+                    const int h = threadIdx.x + 256 * k;
+                    if (h < HC) {
+                        const int lx = h % CX, ly = (h / CX) % CY, lz = D == 3 ? h / (CX * CY) : 0;
+                        const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
+                        R.l[k] = __ldg(A.lam + g);
+                        R.m[k] = __ldg(A.mu + g);
                     }
+                }
+                const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+                if (gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz)) {
+                    const long long n = (long long)gx + (long long)P.nx * ((long long)gy + (D == 3 ? (long long)P.ny * gz : 0LL));
+                    R.dgo = __ldcg(A.diag + n);
 #pragma unroll
-                    for (int k = 0; k < CS; k++) {
-                        const int h = threadIdx.x + 256 * k;
-                        if (h < HC) {
-                            sl[h] = R.l[k];
-                            sm[h] = R.m[k];
-                        }
-                    }
-                    T ro[D], wo[D], so[D], xo[D], po[D];
-                    const T dgo = R.dgo;
-#pragma unroll
-                    for (int d = 0; d < D; d++) { ro[d] = R.ro[d]; wo[d] = R.wo[d]; so[d] = R.so[d]; xo[d] = R.xo[d]; po[d] = R.po[d]; }
-                    // issue the next tile's loads; they complete while this one computes
-                    if (tile + (int)gridDim.x < ntiles) load_raw(tile + gridDim.x, R);
-                    __syncthreads();
-                    const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-                    const bool active = gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz);
-                    if (active) {
-                        const long long n = (long long)gx + (long long)P.nx * ((long long)gy + (D == 3 ? (long long)P.ny * gz : 0LL));
-                        const int lx = tx + 1, ly = ty + 1, lz = D == 3 ? tz + 1 : 0;
-                        const int hn = lx + HX * (ly + HY * lz);
-                        T un[D];
-#pragma unroll
-                        for (int d = 0; d < D; d++) un[d] = su[d * HN + hn];
-                        T rn[D];
+                    for (int d = 0; d < D; d++) {
+                        R.ro[d] = __ldcg(A.r[cur][d] + n);
                         if (!first) {
-                            const T inv = T(1) / dgo;
-#pragma unroll
-                            for (int d = 0; d < D; d++) {
-                                const T ri = ro[d];
-                                const T si = wo[d] + tb * so[d];
-                                const T pi = ri * inv + tb * po[d];
-                                A.p[d][n] = pi;
-                                A.x[d][n] = xo[d] + ta * pi;
-                                A.s[nxt][d][n] = si;
-                                rn[d] = ri - ta * si;
-                                A.r[nxt][d][n] = rn[d];
-                            }
-                        } else {
-#pragma unroll
-                            for (int d = 0; d < D; d++) rn[d] = ro[d];
+                            R.wo[d] = __ldcg(A.w[cur][d] + n);
+                            R.so[d] = __ldcg(A.s[cur][d] + n);
+                            R.xo[d] = A.x[d][n];
+                            R.po[d] = A.p[d][n];
                         }
-                        T q[D], eo[NV], lo, mo;
-                        apply_tile<T, D, HX, HY, CX, CY>(su, sl, sm, HN, lx, ly, lz, ue, q, eo, lo, mo);
+                    }
+                }
+            };
+            Raw R;
+            if ((int)blockIdx.x < ntiles) load_raw(blockIdx.x, R);
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
+                const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+                // stage this tile: u_{i+1} = (r_i - alpha (w_i + beta s_{i-1})) / diag
+                // on the halo nodes, lam / mu on the halo cells
+#pragma unroll
+                for (int k = 0; k < HS; k++) {
+                    const int h = threadIdx.x + 256 * k;
+                    if (h < HN) {
+                        const T inv = T(1) / R.dg[k];
 #pragma unroll
                         for (int d = 0; d < D; d++) {
-                            A.w[nxt][d][n] = q[d];
-                            ga.addprod(rn[d], un[d]);
-                            de_.addprod(q[d], un[d]);
-                            rh.addprod(rn[d], rn[d]);
+                            T rv = R.r[k][d];
+                            if (!first) rv -= ta * (R.w[k][d] + tb * R.s[k][d]);
+                            su[d * HN + h] = rv * inv;
                         }
-                        T se[NV];
-                        voigt_stress<T, D>(lo, mo, eo, se);
-#pragma unroll
-                        for (int vv = 0; vv < NV; vv++) dsum[vv].add(se[vv]);
                     }
-                    __syncthreads();
                 }
-                double v9[9], t9[9];
-                v9[0] = ga.value(); v9[1] = de_.value(); v9[2] = rh.value();
 #pragma unroll
-                for (int q = 0; q < 6; q++) v9[3 + q] = q < NV ? dsum[q].value() : 0.0;
-                if (!reduce_barrier<9>(v9, A.partials, A.result, A.bar_count, A.bar_gen, err, t9)) return;
-                {
-                    double s6[6];
-                    dmat_mul<D>(Sl, Sm, UE, s6);
-                    for (int vv = 0; vv < NV; vv++) WE[vv] = t9[3 + vv] + s6[vv];
+                for (int k = 0; k < CS; k++) {
+                    const int h = threadIdx.x + 256 * k;
+                    if (h < HC) {
+                        sl[h] = R.l[k];
+                        sm[h] = R.m[k];
+                    }
                 }
-                double gnew = t9[0], dnew = t9[1], rnew = t9[2];
+                T ro[D], wo[D], so[D], xo[D], po[D];
+                const T dgo = R.dgo;
+#pragma unroll
+                for (int d = 0; d < D; d++) { ro[d] = R.ro[d]; wo[d] = R.wo[d]; so[d] = R.so[d]; xo[d] = R.xo[d]; po[d] = R.po[d]; }
+                // issue the next tile's loads; they complete while this one computes
+                if (tile + (int)gridDim.x < ntiles) load_raw(tile + gridDim.x, R);
+                __syncthreads();
+                const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+                const bool active = gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz);
+                if (active) {
+                    const long long n = (long long)gx + (long long)P.nx * ((long long)gy + (D == 3 ? (long long)P.ny * gz : 0LL));
+                    const int lx = tx + 1, ly = ty + 1, lz = D == 3 ? tz + 1 : 0;
+                    const int hn = lx + HX * (ly + HY * lz);
+                    T un[D];
+#pragma unroll
+                    for (int d = 0; d < D; d++) un[d] = su[d * HN + hn];
+                    T rn[D];
+                    if (!first) {
+                        const T inv = T(1) / dgo;
+#pragma unroll
+                        for (int d = 0; d < D; d++) {
+                            const T ri = ro[d];
+                            const T si = wo[d] + tb * so[d];
+                            const T pi = ri * inv + tb * po[d];
+                            A.p[d][n] = pi;
+                            A.x[d][n] = xo[d] + ta * pi;
+                            A.s[nxt][d][n] = si;
+                            rn[d] = ri - ta * si;
+                            A.r[nxt][d][n] = rn[d];
+                        }
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < D; d++) rn[d] = ro[d];
+                    }
+                    T q[D], eo[NV], lo, mo;
+                    apply_tile<T, D, HX, HY, CX, CY>(su, sl, sm, HN, lx, ly, lz, ue, q, eo, lo, mo);
+#pragma unroll
+                    for (int d = 0; d < D; d++) {
+                        A.w[nxt][d][n] = q[d];
+                        acc[0].addprod(rn[d], un[d]);
+                        acc[1].addprod(q[d], un[d]);
+                        acc[2].addprod(rn[d], rn[d]);
+                    }
+                    T se[NV];
+                    voigt_stress<T, D>(lo, mo, eo, se);
+#pragma unroll
+                    for (int vv = 0; vv < NV; vv++) acc[3 + vv].add(se[vv]);
+                }
+                __syncthreads();
+            }
+            double tt[3 + NV];
+            if (!reduce_barrier<Acc<T>, 3 + NV>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tt)) return;
+            const bool was_first = first;
+            if (lead) {
+                double s6[6];
+                dmat_mul<D>(Sl, Sm, UE, s6);
+                for (int vv = 0; vv < NV; vv++) WE[vv] = tt[3 + vv] + s6[vv];
+                double gnew = tt[0], dnew = tt[1], rnew = tt[2];
                 for (int vv = 0; vv < NV; vv++) {
                     gnew += RE[vv] * UE[vv];
                     dnew += WE[vv] * UE[vv];
                     rnew += RE[vv] * RE[vv];
                 }
-                if (first) {
-                    first = false;
+                int ctl = CTL_RUN;
+                if (was_first) {
                     gamma = gnew;
                     delta = dnew;
-                    continue;
+                } else {
+                    it++;
+                    rho_final = rnew;
+                    if (sqrt(rnew) <= target) ctl = CTL_DONE;
+                    else if (it_total + it >= A.maxit) ctl = CTL_STOP;
+                    gamma_prev = gamma;
+                    alpha_prev = alpha;
+                    gamma = gnew;
+                    delta = dnew;
                 }
-                cur = nxt;
-                it++;
-                rho_final = rnew;
-                if (sqrt(rnew) <= target) { inner_conv = true; break; }
-                if (it_total + it >= A.maxit) break;
-                gamma_prev = gamma;
-                alpha_prev = alpha;
-                gamma = gnew;
-                delta = dnew;
+                s_ctl = ctl;
             }
-            it_total += it;
-            if (!refine) {
-                conv = inner_conv;
+            __syncthreads();
+            const int ctl = s_ctl;
+            first = false;
+            if (!was_first) cur = nxt;
+            if (ctl == CTL_DONE || ctl == CTL_STOP) {
+                if (lead) conv = (ctl == CTL_DONE);
                 break;
             }
-            // refinement: x64 += correction, then a grid-wide sync before the
-            // next pass reads x64 around every node
-            for (long long n = t0; n < N; n += st)
-#pragma unroll
-                for (int d = 0; d < D; d++) A.x64[d][n] += (double)A.x[d][n];
-            for (int vv = 0; vv < NV; vv++) E64[vv] += XE[vv];
-            if (it_total >= A.maxit) break;
-            double dummy[1] = {0.0}, dres[1];
-            if (!reduce_barrier<1>(dummy, A.partials, A.result, A.bar_count, A.bar_gen, err, dres)) return;
         }
+        if (lead) it_total += it;
+        if (!refine) break;
+        // refinement: x64 += correction, then a grid-wide sync before the
+        // next pass reads x64 around every node
+        for (long long n = t0; n < N; n += st)
+#pragma unroll
+            for (int d = 0; d < D; d++) A.x64[d][n] += (double)A.x[d][n];
+        if (lead) {
+            for (int vv = 0; vv < NV; vv++) E64[vv] += XE[vv];
+            s_ctl = (it_total >= A.maxit) ? CTL_STOP : CTL_RUN;
+            if (blockIdx.x == 0)
+                for (int vv = 0; vv < NV; vv++) A.result[24 + vv] = E64[vv];
+        }
+        __syncthreads();
+        const int stop = s_ctl;
+        Acc<T> dummy[1];
+        double dres[1];
+        if (!reduce_barrier<Acc<T>, 1>(dummy, A.partials, A.result, A.bar_count, A.bar_gen, err, dres)) return;
+        if (stop == CTL_STOP) { if (lead) conv = false; break; }
     }
     if (refine) {
         for (long long n = t0; n < N; n += st)
 #pragma unroll
             for (int d = 0; d < D; d++) A.u[d][n] = (T)A.x64[d][n];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && lead) {
         for (int vv = 0; vv < NV; vv++) A.sc->E[vv] = refine ? E64[vv] : XE[vv];
         A.sc->iters = it_total;
         A.sc->bnorm = bnorm;

@@ -12,6 +12,9 @@
 namespace pfdev {
 
 constexpr int PSTRIDE = 24;       // doubles per block in a partials array
+// Sync words, each on its own 128-byte line so that blocks polling the
+// barrier generation do not contend with the arrival counter.
+constexpr int SYNC_GEN = 32, SYNC_LAST = 64, SYNC_WORDS = 96;
 
 // ---------------------------------------------------------------------------
 // Parameters (by value to every kernel)
