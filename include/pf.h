@@ -175,6 +175,42 @@ long long pf_device_bytes(const pf_handle *h);
 const char *pf_last_error(const pf_handle *h);
 void pf_destroy(pf_handle *h);
 
+/* ------------------------------------------------------------------------
+ * Field update that allocates no device memory.  (The paper has no
+ * counterpart: this entry point exists for callers of the library.)
+ *
+ * For callers that cannot call cudaMalloc at the point of use: code that
+ * runs while a stream is being captured into a CUDA graph, runtimes that
+ * hand out a fixed device-memory budget once and forbid later allocations,
+ * and hosts that must leave the process's allocator untouched.
+ *
+ * One explicit Euler step of the phase and species fields -- the part of
+ * pf_step after the mechanics -- with the coupling scalars tr(eps_e) and
+ * |dev eps_e|^2 given per cell (trE, devE2; NULL means zero, i.e. no
+ * mechanics).  All pointers are DEVICE memory, FP64, laid out as in
+ * pf_fields: `in` supplies phi_f, phi_w, x_O, x_H, x_H2O (required),
+ * mobility and dirichlet (optional: 1 and 0); `out` receives phi_f, phi_w,
+ * x_O, x_H, x_H2O (required; must not alias `in`).  dt is cfg->dt, or 0.2 x
+ * pf_dt_stable(cfg) when cfg->dt <= 0; precision, mechanics and CG fields of
+ * cfg are ignored (the update runs in FP64).  Work is queued on cudaStream
+ * (NULL: the legacy default stream) and the call returns when it is done.
+ *
+ * Working arrays live in one fixed device array of the library (about
+ * 8 * PF_STATIC_MAX_CELLS doubles plus about 0.2 MB; 4.5 MB), which every device
+ * that loads the library keeps until the process exits.  Grids with more
+ * than PF_STATIC_MAX_CELLS cells are rejected with PF_EINVAL.  The first call
+ * on a device looks the array's device address up (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call shares the
+ * array and clears what must start at zero: calls whose GPU work overlaps
+ * (other streams or host threads) race, so serialise them.
+ * Returns PF_OK, PF_EINVAL, PF_ECUDA or PF_ENONFINITE; the text of the last
+ * failure on this host thread is pf_static_last_error().
+ * ------------------------------------------------------------------------ */
+#define PF_STATIC_MAX_CELLS 65536
+int pf_fields_update_static(const pf_config *cfg, const pf_fields *in, const double *trE,
+                            const double *devE2, pf_fields *out, void *cudaStream);
+const char *pf_static_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,8 @@
 #include <new>
 #include <string>
 #include <vector>
+#include <algorithm>
+#include <mutex>
 
 #include "pf.h"
 #include "pf_cg.cuh"
@@ -122,6 +124,22 @@ double dt_stable_impl(const pf_config *c)
     return dt;
 }
 
+// Device parameter block of a (validated) configuration; 2D grids use nz = 1.
+void fill_params(const pf_config &c, long long N, Params &P)
+{
+    memset(&P, 0, sizeof(P));
+    P.ndim = c.ndim; P.nx = c.nx; P.ny = c.ny; P.nz = c.ndim == 3 ? c.nz : 1; P.N = N;
+    P.dt = c.dt > 0.0 ? c.dt : 0.2 * dt_stable_impl(&c);
+    P.c = c.p.c_chem; P.w = c.p.w; P.eps = c.p.eps_phi; P.kappa = c.p.kappa_O; P.L = c.p.L;
+    P.DOs = c.p.D_O_s; P.DOg = c.p.D_O_g; P.DHs = c.p.D_H_s; P.DHg = c.p.D_H_g; P.DWs = c.p.D_W_s; P.DWg = c.p.D_W_g;
+    P.kfor = c.p.k_for; P.xHbc = c.p.xH_bc;
+    const double Es = c.p.E_s, Eg = c.p.E_s * c.p.E_g_ratio, nu = c.p.nu;
+    P.Ks = Es / (3.0 * (1.0 - 2.0 * nu)); P.Gs = Es / (2.0 * (1.0 + nu));
+    P.Kg = Eg / (3.0 * (1.0 - 2.0 * nu)); P.Gg = Eg / (2.0 * (1.0 + nu));
+    P.eig0 = c.p.eig0; P.sY = c.p.sigma_Y; P.Hh = c.p.H_hard; P.prestress = c.p.prestress;
+    P.plasticity = c.plasticity;
+}
+
 } // namespace
 
 // ---------------------------------------------------------------------------
@@ -154,7 +172,7 @@ struct pf_handle {
     unsigned char *mask = nullptr;
     double *partials = nullptr;
     int npart = 0;
-    unsigned int *sync = nullptr;      // [0] barrier count, [1] barrier generation, [2] last-block counter
+    unsigned int *sync = nullptr;      // barrier count, barrier generation, last-block counter (own 128-B lines)
     Scalars *sc = nullptr;
     Diag *dg = nullptr;
     double *stage = nullptr, *stage2 = nullptr;
@@ -302,7 +320,7 @@ int run_steps(pf_handle *h, int nsteps, cudaStream_t s)
             A.diag = (T *)h->diag;
             A.partials = h->partials;
             A.result = h->result;
-            A.bar_count = h->sync; A.bar_gen = h->sync + 1;
+            A.bar_count = h->sync; A.bar_gen = h->sync + SYNC_GEN;
             A.sc = h->sc; A.dg = h->dg;
             A.rtol = h->cfg.cg_rtol; A.maxit = h->cfg.cg_maxit;
             A.warm = h->cfg.warm_start == PF_WS_PREV ? 1 : 0;
@@ -321,7 +339,7 @@ int run_steps(pf_handle *h, int nsteps, cudaStream_t s)
         k_mu<T, D><<<ge, 256, 0, s>>>(P, F);
         h->mark_end(s);
         h->mark_begin(PF_K_UPDATE, s);
-        k_update<T, D><<<ge, 256, 0, s>>>(P, F, h->partials, h->sync + 2, h->dg);
+        k_update<T, D><<<ge, 256, 0, s>>>(P, F, h->partials, h->sync + SYNC_LAST, h->dg);
         h->mark_end(s);
         h->cur = 1 - h->cur;
         h->steps++;
@@ -405,7 +423,7 @@ int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
     Diag dg;
     memset(&dg, 0, sizeof(dg));
     PF_TRY(h->cuda(cudaMemcpyAsync(h->dg, &dg, sizeof(dg), cudaMemcpyHostToDevice, s), "diag"));
-    PF_TRY(h->cuda(cudaMemsetAsync(h->sync, 0, sizeof(unsigned int) * 4, s), "sync words"));
+    PF_TRY(h->cuda(cudaMemsetAsync(h->sync, 0, sizeof(unsigned int) * SYNC_WORDS, s), "sync words"));
     PF_TRY(h->cuda(cudaMemsetAsync(h->trE, 0, h->tsz * (size_t)N, s), "coupling"));
     PF_TRY(h->cuda(cudaMemsetAsync(h->devE2, 0, h->tsz * (size_t)N, s), "coupling"));
     // reference oxygen content
@@ -530,11 +548,11 @@ int alloc_fields(pf_handle *h)
     PF_TRY(h->alloc(&h->stage2, sizeof(double) * (size_t)N));
     h->npart = h->sms * 16 > 4096 ? h->sms * 16 : 4096;
     PF_TRY(h->alloc(&h->partials, sizeof(double) * PSTRIDE * (size_t)h->npart));
-    PF_TRY(h->alloc(&h->sync, sizeof(unsigned int) * 4));
+    PF_TRY(h->alloc(&h->sync, sizeof(unsigned int) * SYNC_WORDS));
     PF_TRY(h->alloc(&h->sc, sizeof(Scalars)));
     PF_TRY(h->alloc(&h->dg, sizeof(Diag)));
     PF_TRY(h->alloc(&h->ptrtab, sizeof(void *) * 6));
-    PF_TRY(h->cuda(cudaMemset(h->sync, 0, sizeof(unsigned int) * 4), "sync init"));
+    PF_TRY(h->cuda(cudaMemset(h->sync, 0, sizeof(unsigned int) * SYNC_WORDS), "sync init"));
     for (int v = 0; v < NP; v++) PF_TRY(h->cuda(cudaMemset(h->sigma[v], 0, b), "sigma init"));
     return PF_OK;
 }
@@ -598,18 +616,7 @@ int pf_create(const pf_config *cfg, pf_handle **out)
     if (!coop) { g_create_error = "device lacks cooperative launch"; free_all(h); delete h; return PF_ECUDA; }
     if (!upload_tables(h->dev)) { g_create_error = "constant table upload failed"; free_all(h); delete h; return PF_ECUDA; }
 
-    Params &P = h->P;
-    memset(&P, 0, sizeof(P));
-    P.ndim = c.ndim; P.nx = c.nx; P.ny = c.ny; P.nz = h->cfg.nz; P.N = N;
-    P.dt = c.dt > 0.0 ? c.dt : 0.2 * dt_stable_impl(&h->cfg);
-    P.c = c.p.c_chem; P.w = c.p.w; P.eps = c.p.eps_phi; P.kappa = c.p.kappa_O; P.L = c.p.L;
-    P.DOs = c.p.D_O_s; P.DOg = c.p.D_O_g; P.DHs = c.p.D_H_s; P.DHg = c.p.D_H_g; P.DWs = c.p.D_W_s; P.DWg = c.p.D_W_g;
-    P.kfor = c.p.k_for; P.xHbc = c.p.xH_bc;
-    const double Es = c.p.E_s, Eg = c.p.E_s * c.p.E_g_ratio, nu = c.p.nu;
-    P.Ks = Es / (3.0 * (1.0 - 2.0 * nu)); P.Gs = Es / (2.0 * (1.0 + nu));
-    P.Kg = Eg / (3.0 * (1.0 - 2.0 * nu)); P.Gg = Eg / (2.0 * (1.0 + nu));
-    P.eig0 = c.p.eig0; P.sY = c.p.sigma_Y; P.Hh = c.p.H_hard; P.prestress = c.p.prestress;
-    P.plasticity = c.plasticity;
+    fill_params(h->cfg, N, h->P);
 
     int rc = h->fp64 ? alloc_fields<double>(h) : alloc_fields<float>(h);
     if (rc == PF_OK && c.mechanics) {
@@ -763,5 +770,145 @@ void pf_destroy(pf_handle *h)
     free_all(h);
     delete h;
 }
+
+} // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free field update.
+//
+// Some callers cannot allocate device memory: code that runs while a stream
+// is being captured into a CUDA graph (cudaMalloc is not allowed there),
+// host runtimes that hand out a fixed device-memory budget up front and
+// forbid allocations afterwards, and callers that must not touch the
+// allocator state of a process they share.  For them,
+// pf_fields_update_static runs the explicit field update of one step with its
+// working arrays in the fixed device array below instead of in memory it
+// allocates.  The array exists once per device that loads the library, for
+// the life of the process.  Every call shares it: calls whose work overlaps
+// on the GPU (other streams, other host threads) race and must be
+// serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr long long STATIC_MAX_CELLS = PF_STATIC_MAX_CELLS;
+constexpr int STATIC_BLOCKS = 512;
+// theta, phi_g, mu_O, M_O, theta_out, zero, zero, one  (8 FP64 arrays), then
+// the partial sums, the last-block counter, the diagnostics record and the
+// zero mask.
+constexpr size_t STATIC_ARRAYS = 8;
+constexpr size_t STATIC_DOUBLES = STATIC_ARRAYS * STATIC_MAX_CELLS + (size_t)STATIC_BLOCKS * PSTRIDE + 64;
+constexpr size_t STATIC_BYTES = STATIC_DOUBLES * sizeof(double) + STATIC_MAX_CELLS;
+
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_BYTES];
+
+std::mutex g_static_mu;
+void *g_static_addr[64] = {};
+
+// Device address of the scratch array for the current device (looked up once
+// per device; the host-side name is only a stand-in for it).
+int static_scratch(void **out, std::string &err)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { err = std::string("cudaGetDevice: ") + cudaGetErrorString(e); return PF_ECUDA; }
+    if (dev < 0 || dev >= 64) { err = "device index out of range"; return PF_ECUDA; }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return PF_ECUDA;
+        }
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return PF_OK;
+}
+
+thread_local std::string g_static_error;
+
+template <int D>
+int fields_update_static_t(const Params &P, const pf_fields *in, const double *trE, const double *devE2,
+                           pf_fields *out, cudaStream_t s, void *base)
+{
+    const long long N = P.N;
+    double *a = (double *)base;
+    double *theta = a, *phig = a + N, *muO = a + 2 * N, *MO = a + 3 * N, *theta_o = a + 4 * N;
+    double *zero0 = a + 5 * N, *zero1 = a + 6 * N, *one = a + 7 * N;
+    double *partials = a + STATIC_ARRAYS * STATIC_MAX_CELLS;
+    double *tail = partials + (size_t)STATIC_BLOCKS * PSTRIDE;
+    unsigned int *counter = (unsigned int *)tail;
+    Diag *dg = (Diag *)(tail + 8);
+    unsigned char *mask0 = (unsigned char *)(a + STATIC_DOUBLES);
+    const int g = (int)std::min<long long>((N + 255) / 256, STATIC_BLOCKS);
+    // state that must start at zero on every call
+    if (cudaMemsetAsync(tail, 0, 64 * sizeof(double), s) != cudaSuccess) return PF_ECUDA;
+    if (!trE || !devE2) {
+        if (cudaMemsetAsync(zero0, 0, sizeof(double) * N, s) != cudaSuccess) return PF_ECUDA;
+        if (cudaMemsetAsync(zero1, 0, sizeof(double) * N, s) != cudaSuccess) return PF_ECUDA;
+    }
+    if (!in->dirichlet && cudaMemsetAsync(mask0, 0, (size_t)N, s) != cudaSuccess) return PF_ECUDA;
+    if (!in->mobility) k_in_scalar<double><<<g, 256, 0, s>>>(N, nullptr, one, 1.0);
+    k_in_phase<double><<<g, 256, 0, s>>>(N, in->phi_f, in->phi_w, theta, phig);
+    FieldPtrs<double, D> F;
+    memset(&F, 0, sizeof(F));
+    F.theta = theta; F.phig = phig; F.xO = in->x_O; F.xH = in->x_H; F.xW = in->x_H2O;
+    F.mob = in->mobility ? in->mobility : one;
+    F.mask = in->dirichlet ? in->dirichlet : mask0;
+    F.theta_o = theta_o; F.xO_o = out->x_O; F.xH_o = out->x_H; F.xW_o = out->x_H2O;
+    F.muO = muO; F.MO = MO;
+    F.trE = const_cast<double *>(trE ? trE : zero0);
+    F.devE2 = const_cast<double *>(devE2 ? devE2 : zero1);
+    k_mu<double, D><<<g, 256, 0, s>>>(P, F);
+    k_update<double, D><<<g, 256, 0, s>>>(P, F, partials, counter, dg);
+    k_out_phase<double><<<g, 256, 0, s>>>(N, theta_o, phig, out->phi_f, out->phi_w);
+    if (cudaGetLastError() != cudaSuccess) return PF_ECUDA;
+    int status = 0;
+    if (cudaMemcpyAsync(&status, &dg->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PF_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PF_ECUDA;
+    return status == 5 ? PF_ENONFINITE : PF_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int pf_fields_update_static(const pf_config *cfg, const pf_fields *in, const double *trE, const double *devE2,
+                            pf_fields *out, void *cudaStream)
+{
+    g_static_error.clear();
+    if (!cfg || !in || !out) { g_static_error = "cfg, in and out are required"; return PF_EINVAL; }
+    if (cfg->ndim != 2 && cfg->ndim != 3) { g_static_error = "ndim must be 2 or 3"; return PF_EINVAL; }
+    if (cfg->nx < 2 || cfg->ny < 2 || (cfg->ndim == 3 && cfg->nz < 2)) { g_static_error = "grid sizes must be >= 2"; return PF_EINVAL; }
+    const long long N = (long long)cfg->nx * cfg->ny * (cfg->ndim == 3 ? cfg->nz : 1);
+    if (N > STATIC_MAX_CELLS) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "grid has %lld cells; pf_fields_update_static handles at most %lld (PF_STATIC_MAX_CELLS)",
+                 N, STATIC_MAX_CELLS);
+        g_static_error = buf;
+        return PF_EINVAL;
+    }
+    if (!in->phi_f || !in->phi_w || !in->x_O || !in->x_H || !in->x_H2O ||
+        !out->phi_f || !out->phi_w || !out->x_O || !out->x_H || !out->x_H2O) {
+        g_static_error = "phi_f, phi_w, x_O, x_H and x_H2O are required in `in` and `out`";
+        return PF_EINVAL;
+    }
+    void *base = nullptr;
+    int rc = static_scratch(&base, g_static_error);
+    if (rc != PF_OK) return rc;
+    pf_config c = *cfg;
+    if (c.ndim == 2) c.nz = 1;
+    Params P;
+    fill_params(c, N, P);
+    cudaStream_t s = (cudaStream_t)cudaStream;
+    rc = c.ndim == 2 ? fields_update_static_t<2>(P, in, trE, devE2, out, s, base)
+                     : fields_update_static_t<3>(P, in, trE, devE2, out, s, base);
+    if (rc == PF_ECUDA) g_static_error = std::string("CUDA error: ") + cudaGetErrorString(cudaGetLastError());
+    else if (rc == PF_ENONFINITE) g_static_error = "non-finite value in the fields";
+    return rc;
+}
+
+const char *pf_static_last_error(void) { return g_static_error.c_str(); }
 
 } // extern "C"

@@ -69,7 +69,9 @@ class pf_profile(ctypes.Structure):
 # exported symbols, in the order of include/pf.h
 SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_diagnostics",
            "pf_free_energy", "pf_dt_stable", "pf_profile_enable", "pf_profile_read",
-           "pf_device_bytes", "pf_last_error", "pf_destroy"]
+           "pf_device_bytes", "pf_last_error", "pf_destroy",
+           "pf_fields_update_static", "pf_static_last_error"]
+PF_STATIC_MAX_CELLS = 65536
 
 _lock = threading.Lock()
 _lib = None
@@ -130,6 +132,11 @@ def lib():
         l.pf_last_error.restype = ctypes.c_char_p
         l.pf_destroy.argtypes = [ctypes.c_void_p]
         l.pf_destroy.restype = None
+        l.pf_fields_update_static.argtypes = [ctypes.POINTER(pf_config), ctypes.POINTER(pf_fields), _DP, _DP,
+                                              ctypes.POINTER(pf_fields), ctypes.c_void_p]
+        l.pf_fields_update_static.restype = ctypes.c_int
+        l.pf_static_last_error.argtypes = []
+        l.pf_static_last_error.restype = ctypes.c_char_p
         _lib = l
         return l
 
@@ -190,3 +197,14 @@ def pf_last_error(h=None):
 
 def pf_destroy(h):
     lib().pf_destroy(h)
+
+
+def pf_fields_update_static(cfg, fin, trE, devE2, fout, stream=None):
+    """Allocation-free field update; every pointer is device memory (see pf.h)."""
+    return lib().pf_fields_update_static(ctypes.byref(cfg), ctypes.byref(fin), trE, devE2,
+                                         ctypes.byref(fout), ctypes.c_void_p(stream) if stream else None)
+
+
+def pf_static_last_error():
+    s = lib().pf_static_last_error()
+    return s.decode() if s else ""
