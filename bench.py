@@ -176,6 +176,42 @@ def run_e2e(precision, steps, fields):
     return dt, h2d, d2h
 
 
+def run_batch(precision, steps, warmup, count=64, seed=4, profile=True):
+    """The batched workload: `count` independent 2D porous instances of uneven
+    sizes (128^2 .. 1024^2), seeded pore fractions and prestresses, advanced
+    together by one launch per kernel class and step."""
+    import torch
+    from paper_2111_11538_gb300 import Batch, inputs, workloads
+    desc = inputs.batch_instances(count, seed)
+    base = workloads.WORKLOADS["batch64"]["params"]
+    shapes = [(d["n"], d["n"]) for d in desc]
+    prms = [dict(base, prestress=d["prestress"]) for d in desc]
+    b = Batch(shapes, prms, precision=precision)
+    for i, d in enumerate(desc):
+        b.set_fields(i, inputs.batch_fields(d))
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    b.step(warmup, stream=sh)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    b.profile(profile)
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(1, stream=sh)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    prof = b.profile_read()
+    cells = sum(n[0] * n[1] for n in shapes)
+    iters = [b.diagnostics(i)["cg_iters_last"] for i in range(count)]
+    b.close()
+    return total_ms, prof, cells, iters
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle on the host (single thread) over a bounded sample of the
     workload: the same core-shell geometry and parameters on a 128 x 128 grid
@@ -234,7 +270,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="coreshell512",
-                    help="coreshell512 (default, the headline), porous2048 or coreshell64")
+                    help="coreshell512 (default, the headline); porous2048, coreshell64 or batch64 "
+                         "print a short line")
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"],
                     help="profiling aid: run one method only and print a short line")
     args = ap.parse_args()
@@ -281,6 +318,18 @@ def main():
     import torch
     from paper_2111_11538_gb300 import native
     native.build_library()
+    if WORKLOAD == "batch64":
+        meth = "mixed" if args.only == "both" else args.only
+        for prof_on in (False, True):
+            msb, profb, cells, iters = run_batch(meth, args.steps, args.warmup, profile=prof_on)
+            if rank == 0:
+                print(json.dumps({"workload": WORKLOAD, "method": meth, "cells": cells, "steps": args.steps,
+                                  "timing": "per-kernel events" if prof_on else "graph replay",
+                                  "ms_per_step": msb / args.steps, "value": cells * args.steps / (msb / 1e3),
+                                  "kernel_ms": profb["ms"], "cg_iters": profb["cg_iters"],
+                                  "graph_steps": profb["graph_steps"],
+                                  "cg_iters_last_min_max": [min(iters), max(iters)]}))
+        return
     fields = workload_fields()
     N = fields["phi_f"].size
     if args.only != "both":

@@ -132,7 +132,10 @@ int pf_set_fields(pf_handle *h, const pf_fields *f, int where);
 /* Advance nsteps >= 0 steps on cudaStream (NULL: the handle's own stream),
  * blocking until they are done.  Returns PF_ENOTCONV if any CG solve stopped
  * at cg_maxit (the steps are still taken), PF_ENONFINITE if a non-finite
- * value appeared, PF_ETIMEOUT if a bounded device wait gave up. */
+ * value appeared, PF_ETIMEOUT if a bounded device wait gave up.  With
+ * per-kernel timing off, each step is replayed from a CUDA graph captured at
+ * the first step after pf_create / pf_set_fields (direct launches if the
+ * capture fails); the results are the same either way. */
 int pf_step(pf_handle *h, int nsteps, void *cudaStream);
 
 /* Copy fields out into caller arrays (FP64).  sigma is the stress of the last
@@ -163,11 +166,41 @@ typedef struct {
     long long count[PF_K_NCLASS];  /* launches per class (timed only if enabled)  */
     double ms[PF_K_NCLASS];        /* summed device time per class, ms            */
     long long cg_iters;            /* CG iterations of the timed solves           */
+    long long graph_steps;         /* steps replayed from a captured CUDA graph   */
 } pf_profile;
 
 /* Enable (on != 0) or disable event timing; either way the counters reset. */
 int pf_profile_enable(pf_handle *h, int on);
 int pf_profile_read(pf_handle *h, pf_profile *out);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent instances advanced by the same launches.
+ *
+ * Each instance is one simulation of the model above (the paper's
+ * micrographs are independent particles and pores, Sec. 4.3); a batch steps
+ * all of them with one launch per kernel class and step, the blocks of every
+ * launch split between the instances.  Instances may differ in grid size,
+ * parameters, CG tolerance and fields; they must share ndim, precision and
+ * whether mechanics is on (PF_EINVAL otherwise).
+ *
+ * pf_batch_create: cfgs[0..n-1] as for pf_create; *out is a batch handle
+ *   (NULL on failure; pf_last_error(NULL) names the failing instance).
+ *   PF_EINVAL at the first pf_step if the instances need more co-resident CG
+ *   blocks than the device holds (one per instance at least).
+ * On a batch handle, pf_step advances every instance (all must have fields,
+ *   else PF_ESTATE) and returns the worst status over the instances
+ *   (PF_ETIMEOUT > PF_ENONFINITE > PF_ENOTCONV); pf_profile_*,
+ *   pf_device_bytes (sum over instances), pf_last_error and pf_destroy work
+ *   as for one instance.  pf_set_fields, pf_get_fields, pf_get_diagnostics
+ *   and pf_free_energy return PF_EINVAL: use the pf_batch_ calls with the
+ *   instance index i (0 <= i < n, PF_EINVAL otherwise), which have the
+ *   semantics of their single-instance counterparts.
+ * pf_batch_size: n for a batch handle, 1 for a single handle, 0 for NULL. */
+int pf_batch_create(const pf_config *cfgs, int n, pf_handle **out);
+int pf_batch_size(const pf_handle *h);
+int pf_batch_set_fields(pf_handle *h, int i, const pf_fields *f, int where);
+int pf_batch_get_fields(pf_handle *h, int i, pf_fields *out, int where);
+int pf_batch_get_diagnostics(pf_handle *h, int i, pf_diag *out);
 
 /* Device memory held by the handle, bytes. */
 long long pf_device_bytes(const pf_handle *h);

@@ -19,7 +19,7 @@ from . import native
 from .native import (PF_DEVICE, PF_FP64, PF_HOST, PF_MIXED, PF_OK, PF_WS_PREV, PF_WS_ZERO,
                      STATUS_NAMES, pf_config, pf_diag, pf_fields, pf_params)
 
-__all__ = ["Simulation", "PFError", "make_config", "native"]
+__all__ = ["Simulation", "Batch", "PFError", "make_config", "native"]
 
 PARAM_NAMES = [f[0] for f in pf_params._fields_]
 
@@ -60,6 +60,69 @@ def _dptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
 
 
+FIELD_KEYS = ("phi_f", "phi_w", "xO", "xH", "xW", "u", "Ebar", "eps_p", "alpha", "sigma")
+_NAMES = {"phi_f": "phi_f", "phi_w": "phi_w", "xO": "x_O", "xH": "x_H", "xW": "x_H2O",
+          "u": "u", "Ebar": "Ebar", "eps_p": "eps_p", "alpha": "alpha", "sigma": "sigma",
+          "mob": "mobility"}
+
+
+def _in_fields(fields, where, N, ndim):
+    """pf_fields pointing at the caller's arrays (numpy on the host, torch
+    CUDA tensors on the device) and the list of objects that must stay alive
+    until the call returns."""
+    f = pf_fields()
+    keep = []
+    npl = 4 if ndim == 2 else 6
+    nv = 3 if ndim == 2 else 6
+    if where == "host":
+        sizes = {"u": N * ndim, "eps_p": N * npl, "Ebar": nv}
+        for key in ("phi_f", "phi_w", "xO", "xH", "xW", "alpha", "mob", "u", "eps_p", "Ebar"):
+            v = fields.get(key)
+            if v is None:
+                continue
+            a = np.ascontiguousarray(v, dtype=np.float64)
+            if a.size != sizes.get(key, N):
+                raise ValueError("%s has %d values, expected %d" % (key, a.size, sizes.get(key, N)))
+            keep.append(a)
+            setattr(f, _NAMES[key], _dptr(a))
+        v = fields.get("mask")
+        if v is not None:
+            a = np.ascontiguousarray(v, dtype=np.uint8)
+            if a.size != N:
+                raise ValueError("mask has %d values, expected %d" % (a.size, N))
+            keep.append(a)
+            f.dirichlet = a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+    elif where == "device":
+        for key in ("phi_f", "phi_w", "xO", "xH", "xW", "alpha", "mob", "u", "eps_p", "Ebar"):
+            t = fields.get(key)
+            if t is not None:
+                t = t.contiguous()
+                keep.append(t)
+                setattr(f, _NAMES[key], ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_double)))
+        t = fields.get("mask")
+        if t is not None:
+            t = t.contiguous()
+            keep.append(t)
+            f.dirichlet = ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_ubyte))
+    else:
+        raise ValueError("where must be 'host' or 'device'")
+    return f, keep
+
+
+def _out_fields(keys, shape):
+    """pf_fields pointing at fresh numpy arrays for the requested keys."""
+    ndim = len(shape)
+    npl = 4 if ndim == 2 else 6
+    nv = 3 if ndim == 2 else 6
+    shp = {"u": shape + (ndim,), "eps_p": shape + (npl,), "sigma": shape + (npl,), "Ebar": (nv,)}
+    f = pf_fields()
+    out = {}
+    for k in keys:
+        out[k] = np.zeros(shp.get(k, shape))
+        setattr(f, _NAMES[k], _dptr(out[k]))
+    return f, out
+
+
 class Simulation:
     """One grid advanced by the CUDA library.
 
@@ -87,44 +150,9 @@ class Simulation:
         return rc
 
     def set_fields(self, fields, where="host"):
-        f = pf_fields()
-        keep = []
-        if where == "host":
-            def put(name, key, dtype=np.float64, shape=None):
-                v = fields.get(key)
-                if v is None:
-                    return
-                a = np.ascontiguousarray(v, dtype=dtype)
-                if shape is not None and a.size != int(np.prod(shape)):
-                    raise ValueError("%s has %d values, expected %d" % (key, a.size, int(np.prod(shape))))
-                keep.append(a)
-                if dtype == np.uint8:
-                    setattr(f, name, a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
-                else:
-                    setattr(f, name, _dptr(a))
-            for name, key in (("phi_f", "phi_f"), ("phi_w", "phi_w"), ("x_O", "xO"), ("x_H", "xH"),
-                              ("x_H2O", "xW"), ("alpha", "alpha"), ("mobility", "mob")):
-                put(name, key, shape=(self.N,))
-            put("u", "u", shape=(self.N, self.ndim))
-            put("eps_p", "eps_p", shape=(self.N, self.np_))
-            put("Ebar", "Ebar", shape=(self.nv,))
-            put("dirichlet", "mask", dtype=np.uint8, shape=(self.N,))
-            rc = native.pf_set_fields(self.h, f, PF_HOST)
-        else:
-            for name, key in (("phi_f", "phi_f"), ("phi_w", "phi_w"), ("x_O", "xO"), ("x_H", "xH"),
-                              ("x_H2O", "xW"), ("alpha", "alpha"), ("mobility", "mob"), ("u", "u"),
-                              ("eps_p", "eps_p"), ("Ebar", "Ebar")):
-                t = fields.get(key)
-                if t is not None:
-                    t = t.contiguous()
-                    keep.append(t)
-                    setattr(f, name, ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_double)))
-            t = fields.get("mask")
-            if t is not None:
-                t = t.contiguous()
-                keep.append(t)
-                f.dirichlet = ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_ubyte))
-            rc = native.pf_set_fields(self.h, f, PF_DEVICE)
+        f, keep = _in_fields(fields, where, self.N, self.ndim)
+        rc = native.pf_set_fields(self.h, f, PF_HOST if where == "host" else PF_DEVICE)
+        del keep
         return self._check(rc)
 
     def step(self, n=1, stream=None, check=True):
@@ -133,16 +161,8 @@ class Simulation:
             self._check(rc)
         return rc
 
-    def get_fields(self, keys=("phi_f", "phi_w", "xO", "xH", "xW", "u", "Ebar", "eps_p", "alpha", "sigma")):
-        f = pf_fields()
-        out = {}
-        shp = {"u": self.shape + (self.ndim,), "eps_p": self.shape + (self.np_,),
-               "sigma": self.shape + (self.np_,), "Ebar": (self.nv,)}
-        names = {"phi_f": "phi_f", "phi_w": "phi_w", "xO": "x_O", "xH": "x_H", "xW": "x_H2O",
-                 "u": "u", "Ebar": "Ebar", "eps_p": "eps_p", "alpha": "alpha", "sigma": "sigma"}
-        for k in keys:
-            out[k] = np.zeros(shp.get(k, self.shape))
-            setattr(f, names[k], _dptr(out[k]))
+    def get_fields(self, keys=FIELD_KEYS):
+        f, out = _out_fields(keys, self.shape)
         self._check(native.pf_get_fields(self.h, f, PF_HOST))
         return out
 
@@ -166,7 +186,88 @@ class Simulation:
     def profile_read(self):
         rc, p = native.pf_profile_read(self.h)
         self._check(rc)
-        return {"launches": p.launches, "cg_iters": p.cg_iters,
+        return {"launches": p.launches, "cg_iters": p.cg_iters, "graph_steps": p.graph_steps,
+                "count": {k: p.count[i] for i, k in enumerate(native.KERNEL_CLASSES)},
+                "ms": {k: p.ms[i] for i, k in enumerate(native.KERNEL_CLASSES)}}
+
+    def device_bytes(self):
+        return native.pf_device_bytes(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            native.pf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Many independent instances stepped by the same launches.
+
+    ``shapes`` and ``prms`` give one grid shape and parameter dict per
+    instance; the instances share ndim, precision and whether mechanics is
+    on.  Fields go in and out per instance (index ``i``); ``step`` advances
+    all of them.
+    """
+
+    def __init__(self, shapes, prms, precision="fp64", **kw):
+        if isinstance(prms, dict):
+            prms = [prms] * len(shapes)
+        self.shapes = [tuple(s) for s in shapes]
+        self.cfgs = [make_config(s, p, precision=precision, **kw) for s, p in zip(self.shapes, prms)]
+        rc, h = native.pf_batch_create(self.cfgs)
+        if rc != PF_OK:
+            raise PFError(rc, native.pf_last_error(None))
+        self.h = h
+
+    def __len__(self):
+        return native.pf_batch_size(self.h)
+
+    def _check(self, rc):
+        if rc != PF_OK:
+            raise PFError(rc, native.pf_last_error(self.h))
+        return rc
+
+    def set_fields(self, i, fields, where="host"):
+        shape = self.shapes[i]
+        f, keep = _in_fields(fields, where, int(np.prod(shape)), len(shape))
+        rc = native.pf_batch_set_fields(self.h, i, f, PF_HOST if where == "host" else PF_DEVICE)
+        del keep
+        return self._check(rc)
+
+    def step(self, n=1, stream=None, check=True):
+        rc = native.pf_step(self.h, n, stream)
+        if check:
+            self._check(rc)
+        return rc
+
+    def get_fields(self, i, keys=FIELD_KEYS):
+        f, out = _out_fields(keys, self.shapes[i])
+        self._check(native.pf_batch_get_fields(self.h, i, f, PF_HOST))
+        return out
+
+    def diagnostics(self, i):
+        rc, d = native.pf_batch_get_diagnostics(self.h, i)
+        self._check(rc)
+        return {k: getattr(d, k) for k, _ in pf_diag._fields_}
+
+    def profile(self, on=True):
+        self._check(native.pf_profile_enable(self.h, on))
+
+    def profile_read(self):
+        rc, p = native.pf_profile_read(self.h)
+        self._check(rc)
+        return {"launches": p.launches, "cg_iters": p.cg_iters, "graph_steps": p.graph_steps,
                 "count": {k: p.count[i] for i, k in enumerate(native.KERNEL_CLASSES)},
                 "ms": {k: p.ms[i] for i, k in enumerate(native.KERNEL_CLASSES)}}
 

@@ -19,6 +19,8 @@
 // reduced values) and broadcast through shared memory: FP64 runs at a small
 // fraction of the FP32 rate on this GPU, so no other thread touches them.
 #pragma once
+#include <type_traits>
+
 #include "pf_kernels.cuh"
 
 namespace pfdev {
@@ -47,60 +49,8 @@ struct PCGArgs {
     double rtol;
     int maxit;
     int warm;
+    int block0, nblocks;           // this job's blocks in the launch
 };
-
-// ---------------------------------------------------------------------------
-// Block reduction of per-thread accumulators to one FP64 value per entry,
-// written by thread 0 to dst.  FP32 accumulators are reduced as (sum, error)
-// pairs with error-free additions, so no FP64 arithmetic runs per thread.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void pair_add(float &h, float &l, float h2, float l2)
-{
-    const float s = h + h2;
-    const float bp = s - h;
-    const float e = (h - (s - bp)) + (h2 - bp);
-    l = l + l2 + e;
-    h = s + l;
-    l = l - (h - s);
-}
-
-template <int K>
-__device__ void block_reduce_store(Acc<float> (&a)[K], double *dst)
-{
-    __shared__ float sh[K][32], sl[K][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-        float h = a[k].s, l = a[k].c;
-        for (int o = 16; o > 0; o >>= 1) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
-            pair_add(h, l, h2, l2);
-        }
-        if (lane == 0) { sh[k][wid] = h; sl[k][wid] = l; }
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            float h = lane < nw ? sh[k][lane] : 0.f, l = lane < nw ? sl[k][lane] : 0.f;
-            for (int o = 16; o > 0; o >>= 1) {
-                const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
-                pair_add(h, l, h2, l2);
-            }
-            if (lane == 0) dst[k] = (double)h + (double)l;
-        }
-    }
-    __syncthreads();
-}
-
-template <int K>
-__device__ void block_reduce_store(Acc<double> (&a)[K], double *dst)
-{
-    double v[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) v[k] = a[k].value();
-    block_sum_store<K>(v, dst);
-}
 
 // Grid barrier that also reduces K per-block values in a fixed order: the
 // last block to arrive sums the partials (warp 0, lane-strided over blocks,
@@ -109,28 +59,39 @@ __device__ void block_reduce_store(Acc<double> (&a)[K], double *dst)
 // (SPIN_LIMIT polls, then PF_ETIMEOUT in *err and false is returned).
 template <typename AccT, int K>
 __device__ bool reduce_barrier(AccT (&acc)[K], double *partials, double *result, unsigned int *count,
-                               unsigned int *gen, int *err, double (&out)[K])
+                               unsigned int *gen, int *err, double (&out)[K], int bid, int nbk)
 {
+    constexpr bool pairs = std::is_same<AccT, Acc<float>>::value;
     __shared__ int s_last, s_ok;
     __shared__ unsigned int s_gen;
-    block_reduce_store<K>(acc, partials + (size_t)blockIdx.x * PSTRIDE);
+    if constexpr (pairs) block_reduce_pairs<K>(acc, reinterpret_cast<float2 *>(partials + (size_t)bid * PSTRIDE));
+    else block_reduce_store<K>(acc, partials + (size_t)bid * PSTRIDE);
     if (threadIdx.x == 0) {
         s_ok = 1;
         volatile unsigned int *vgen = gen;
         s_gen = *vgen;
         __threadfence();
         const unsigned int arrived = atomicAdd(count, 1u);
-        s_last = (arrived == gridDim.x - 1) ? 1 : 0;
+        s_last = (arrived == (unsigned int)nbk - 1) ? 1 : 0;
     }
     __syncthreads();
-    if (s_last) {
+    if (s_last && pairs) {
+        __threadfence();
+        last_block_pairs<K>(partials, nbk, result);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        }
+    } else if (s_last) {
         if (threadIdx.x < 32) {
             __threadfence();
             const int lane = threadIdx.x;
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 double sacc = 0.0;
-                for (int b = lane; b < (int)gridDim.x; b += 32) sacc += __ldcg(partials + (size_t)b * PSTRIDE + k);
+                for (int b = lane; b < nbk; b += 32) sacc += __ldcg(partials + (size_t)b * PSTRIDE + k);
                 sacc = warp_sum(sacc);
                 if (lane == 0) result[k] = sacc;
             }
@@ -210,6 +171,42 @@ __device__ __forceinline__ void apply_tile(const T *su, const T *sl, const T *sm
     }
 }
 
+// 2D Q1 element with constant moduli, exact form of its stiffness: writing
+// the bilinear displacement of a unit cell as its average gradient G plus
+// the hourglass mode h = u00 - u10 - u01 + u11 (per component), the strain is
+// G + h * (eta - 1/2, xi - 1/2) terms whose cross products with G integrate
+// to zero, so  K_e u = Bbar^T D eps(G) + (lam + 3 mu)/12 * gamma h  with
+// gamma = (+1, -1, -1, +1) over the cell's nodes.  cell_force2 returns the
+// average stress (without any mean strain) and the two hourglass forces.
+template <typename TC>
+__device__ __forceinline__ void cell_force2(TC l, TC m, const TC (&ue)[4][2], TC (&s)[3], TC (&fh)[2])
+{
+    const TC Gxu = TC(0.5) * ((ue[1][0] - ue[0][0]) + (ue[3][0] - ue[2][0]));
+    const TC Gyu = TC(0.5) * ((ue[2][0] - ue[0][0]) + (ue[3][0] - ue[1][0]));
+    const TC Gxv = TC(0.5) * ((ue[1][1] - ue[0][1]) + (ue[3][1] - ue[2][1]));
+    const TC Gyv = TC(0.5) * ((ue[2][1] - ue[0][1]) + (ue[3][1] - ue[1][1]));
+    const TC hu = (ue[0][0] - ue[1][0]) - (ue[2][0] - ue[3][0]);
+    const TC hv = (ue[0][1] - ue[1][1]) - (ue[2][1] - ue[3][1]);
+    const TC tr = Gxu + Gyv;
+    s[0] = l * tr + TC(2) * m * Gxu;
+    s[1] = l * tr + TC(2) * m * Gyv;
+    s[2] = m * (Gyu + Gxv);
+    const TC c = (l + TC(3) * m) * TC(1.0 / 12.0);
+    fh[0] = c * hu;
+    fh[1] = c * hv;
+}
+
+// force on the node with local index a of a 2D cell from its average stress
+// s (mean strain included) and hourglass forces fh
+template <typename TC>
+__device__ __forceinline__ void node_force2(int a, const TC *s, const TC *fh, TC (&f)[2])
+{
+    const TC bx = (a & 1) ? TC(0.5) : TC(-0.5), by = (a >> 1) ? TC(0.5) : TC(-0.5);
+    const TC g = (a == 0 || a == 3) ? TC(1) : TC(-1);
+    f[0] = bx * s[0] + by * s[2] + g * fh[0];
+    f[1] = by * s[1] + bx * s[2] + g * fh[1];
+}
+
 // Per-node part of the solve's set-up: right-hand side b = sum_e Bbar^T sig*,
 // Jacobi diagonal, A x (element tables + mean-strain coupling XE) and the own
 // cell's quantities.  TC is the arithmetic type, TV the type of x.
@@ -254,28 +251,61 @@ __device__ __forceinline__ void node_setup(const Params &P, long long n, const T
 #pragma unroll
                 for (int d = 0; d < D; d++) ue[bn][d] = (TC)__ldcg(x[d] + mm);
             }
+            if constexpr (D == 2) {
+                TC s3[3], fh[2], sx[3], f[2];
+                cell_force2<TC>(l, m, ue, s3, fh);
+                if (a == 0)
 #pragma unroll
-            for (int co = 0; co < D; co++) {
-                TC acc = TC(0);
+                    for (int v = 0; v < 3; v++) de_own[v] = s3[v];
+                voigt_stress<TC, 2>(l, m, XE, sx);
 #pragma unroll
-                for (int bn = 0; bn < NN; bn++)
+                for (int v = 0; v < 3; v++) s3[v] += sx[v];
+                node_force2<TC>(a, s3, fh, f);
+                ax[0] += f[0];
+                ax[1] += f[1];
+            } else {
 #pragma unroll
-                    for (int cc = 0; cc < D; cc++)
-                        acc += (l * Kl<TC, D>(a * D + co, bn * D + cc) + m * Km<TC, D>(a * D + co, bn * D + cc)) * ue[bn][cc];
-                ax[co] += acc;
-            }
-            TC se[NV];
-            voigt_stress<TC, D>(l, m, XE, se);
-            bbar_t<TC, D>(a, se, bt);
+                for (int co = 0; co < D; co++) {
+                    TC acc = TC(0);
 #pragma unroll
-            for (int d = 0; d < D; d++) ax[d] += bt[d];
-            if (a == 0) {
-                TC eb[NV];
-                avg_strain<TC, D>(ue, eb);
-                voigt_stress<TC, D>(l, m, eb, de_own);
+                    for (int bn = 0; bn < NN; bn++)
+#pragma unroll
+                        for (int cc = 0; cc < D; cc++)
+                            acc += (l * Kl<TC, D>(a * D + co, bn * D + cc) + m * Km<TC, D>(a * D + co, bn * D + cc)) * ue[bn][cc];
+                    ax[co] += acc;
+                }
+                TC se[NV];
+                voigt_stress<TC, D>(l, m, XE, se);
+                bbar_t<TC, D>(a, se, bt);
+#pragma unroll
+                for (int d = 0; d < D; d++) ax[d] += bt[d];
+                if (a == 0) {
+                    TC eb[NV];
+                    avg_strain<TC, D>(ue, eb);
+                    voigt_stress<TC, D>(l, m, eb, de_own);
+                }
             }
         }
     }
+}
+
+// Periodic 32-bit index of a tile-halo position.  Halo coordinates lie in
+// [-1, n - 1 + tile], so one conditional wrap per axis suffices unless the
+// grid is not larger than a tile (small), where a modulo is used.
+template <int D>
+__device__ __forceinline__ int hidx(const Params &P, int x, int y, int z, bool small)
+{
+    if (small) return (int)linm<D>(P, x, y, z);
+    x += (x < 0) ? P.nx : 0;
+    x -= (x >= P.nx) ? P.nx : 0;
+    y += (y < 0) ? P.ny : 0;
+    y -= (y >= P.ny) ? P.ny : 0;
+    if constexpr (D == 3) {
+        z += (z < 0) ? P.nz : 0;
+        z -= (z >= P.nz) ? P.nz : 0;
+        return x + P.nx * (y + P.ny * z);
+    }
+    return x + P.nx * y;
 }
 
 // Control words broadcast by thread 0.
@@ -288,8 +318,19 @@ enum { CTL_RUN = 0, CTL_DONE = 1, CTL_ZERO = 2, CTL_STOP = 3 };
 // correction), adds it in FP64, and stops when the FP64 residual meets rtol;
 // the FP32 displacement A.u is written from x64 at the end.
 template <typename T, int D>
-__global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
+__global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int njobs)
 {
+    // this block's job, copied to shared memory
+    __shared__ PCGArgs<T, D> sA;
+    {
+        const PCGArgs<T, D> *J = my_job(jobs, njobs);
+        const int *src = reinterpret_cast<const int *>(J);
+        int *dst = reinterpret_cast<int *>(&sA);
+        for (int i = threadIdx.x; i < (int)(sizeof(PCGArgs<T, D>) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    }
+    const PCGArgs<T, D> &A = sA;
+    const int bid = (int)blockIdx.x - A.block0, nbk = A.nblocks;
     constexpr int NV = Dims<D>::NV;
     constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
     constexpr int HX = TX + 2, HY = TY + 2, HZ = D == 3 ? TZ + 2 : 1;
@@ -298,6 +339,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
     constexpr int MAX_OUTER = 24;
     __shared__ T su[D * HN];
     __shared__ T sl[HC], sm[HC];
+    __shared__ T scell[D == 2 ? 5 * HC : 1];     // 2D: per-cell stress and hourglass forces
     __shared__ T s_ta, s_tb, s_ue[6], s_xe[6];
     __shared__ int s_ctl;
 
@@ -307,10 +349,11 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
     const int ntx = (P.nx + TX - 1) / TX, nty = (P.ny + TY - 1) / TY, ntz = D == 3 ? (P.nz + TZ - 1) / TZ : 1;
     const int ntiles = ntx * nty * ntz;
     const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = D == 3 ? threadIdx.x / (TX * TY) : 0;
-    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long st = (long long)gridDim.x * blockDim.x;
+    const long long t0 = bid * (long long)blockDim.x + threadIdx.x;
+    const long long st = (long long)nbk * blockDim.x;
     const bool refine = A.refine != 0;
     const bool lead = threadIdx.x == 0;
+    const bool small = P.nx < TX + 2 || P.ny < TY + 2 || (D == 3 && P.nz < TZ + 2);
 
     // FP64 state of the iteration, in shared memory and touched only by
     // thread 0 (so it costs the other threads no registers).
@@ -318,7 +361,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
         double XE[6];      // mean strain of x (plain) / of the correction (refine)
         double E64[6];     // FP64 mean strain of the solution (refine)
         double DiagE[6], RE[6], UE[6], PE[6], SE[6], WE[6];
-        double Sl, Sm, bnorm, rho_final, target;
+        double Sl, Sm, bnorm, rho_final, target, prev_res;
         double gamma, delta, gamma_prev, alpha_prev, alpha, beta;
         int it, it_total, conv;
     };
@@ -391,7 +434,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
                 }
             }
             double tot[16];
-            if (!reduce_barrier<Acc<double>, 16>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tot)) return;
+            if (!reduce_barrier<Acc<double>, 16>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tot, bid, nbk)) return;
             if (lead) {
                 // scalars of the mean-strain dofs
                 Sl = tot[2];
@@ -419,6 +462,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
                 int ctl = CTL_RUN;
                 if (bnorm == 0.0) ctl = CTL_ZERO;
                 else if (sqrt(rho) <= A.rtol * bnorm) ctl = CTL_DONE;
+                // refinement that no longer halves the FP64 residual has
+                // reached what the FP32 passes can resolve: stop (not converged)
+                else if (refine && outer > 0 && sqrt(rho) > 0.5 * S.prev_res) ctl = CTL_STOP;
+                S.prev_res = sqrt(rho);
                 // target of this pass: the requested tolerance, or in refinement
                 // mode what an FP32 iteration can deliver on this correction
                 target = refine ? fmax(0.5 * A.rtol * bnorm, A.eta * sqrt(rho)) : A.rtol * bnorm;
@@ -443,6 +490,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
             break;
         }
         if (ctl0 == CTL_DONE) { conv = true; break; }
+        if (ctl0 == CTL_STOP) { conv = false; break; }
 
         // ---------------- sweeps: the first builds w_0, then iterations -----
         bool first = true;
@@ -489,7 +537,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
                     const int h = threadIdx.x + 256 * k;
                     if (h < HN) {
                         const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
-                        const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
+                        const int g = hidx<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz, small);
                         R.dg[k] = __ldcg(A.diag + g);
 #pragma unroll
                         for (int d = 0; d < D; d++) {
@@ -506,14 +554,14 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
                     const int h = threadIdx.x + 256 * k;
                     if (h < HC) {
                         const int lx = h % CX, ly = (h / CX) % CY, lz = D == 3 ? h / (CX * CY) : 0;
-                        const long long g = linm<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz);
+                        const int g = hidx<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz, small);
                         R.l[k] = __ldg(A.lam + g);
                         R.m[k] = __ldg(A.mu + g);
                     }
                 }
                 const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
                 if (gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz)) {
-                    const long long n = (long long)gx + (long long)P.nx * ((long long)gy + (D == 3 ? (long long)P.ny * gz : 0LL));
+                    const int n = gx + P.nx * (gy + (D == 3 ? P.ny * gz : 0));
                     R.dgo = __ldcg(A.diag + n);
 #pragma unroll
                     for (int d = 0; d < D; d++) {
@@ -528,8 +576,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
                 }
             };
             Raw R;
-            if ((int)blockIdx.x < ntiles) load_raw(blockIdx.x, R);
-            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            if (bid < ntiles) load_raw(bid, R);
+            for (int tile = bid; tile < ntiles; tile += nbk) {
                 const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
                 const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
                 // stage this tile: u_{i+1} = (r_i - alpha (w_i + beta s_{i-1})) / diag
@@ -560,12 +608,36 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
 #pragma unroll
                 for (int d = 0; d < D; d++) { ro[d] = R.ro[d]; wo[d] = R.wo[d]; so[d] = R.so[d]; xo[d] = R.xo[d]; po[d] = R.po[d]; }
                 // issue the next tile's loads; they complete while this one computes
-                if (tile + (int)gridDim.x < ntiles) load_raw(tile + gridDim.x, R);
+                if (tile + nbk < ntiles) load_raw(tile + nbk, R);
                 __syncthreads();
+                if constexpr (D == 2) {
+                    // per halo cell: average stress (mean strain UE included)
+                    // and hourglass forces, shared by the cell's four nodes
+                    for (int h = threadIdx.x; h < HC; h += blockDim.x) {
+                        const int cx = h % CX, cy = h / CX;
+                        T uc[4][2];
+#pragma unroll
+                        for (int b = 0; b < 4; b++) {
+                            const int hn = (cx + (b & 1)) + HX * (cy + (b >> 1));
+                            uc[b][0] = su[hn];
+                            uc[b][1] = su[HN + hn];
+                        }
+                        const T l = sl[h], m = sm[h];
+                        T s3[3], fh[2], sx[3];
+                        cell_force2<T>(l, m, uc, s3, fh);
+                        voigt_stress<T, 2>(l, m, ue, sx);
+                        scell[h] = s3[0] + sx[0];
+                        scell[HC + h] = s3[1] + sx[1];
+                        scell[2 * HC + h] = s3[2] + sx[2];
+                        scell[3 * HC + h] = fh[0];
+                        scell[4 * HC + h] = fh[1];
+                    }
+                    __syncthreads();
+                }
                 const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
                 const bool active = gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz);
                 if (active) {
-                    const long long n = (long long)gx + (long long)P.nx * ((long long)gy + (D == 3 ? (long long)P.ny * gz : 0LL));
+                    const int n = gx + P.nx * (gy + (D == 3 ? P.ny * gz : 0));
                     const int lx = tx + 1, ly = ty + 1, lz = D == 3 ? tz + 1 : 0;
                     const int hn = lx + HX * (ly + HY * lz);
                     T un[D];
@@ -589,8 +661,32 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
 #pragma unroll
                         for (int d = 0; d < D; d++) rn[d] = ro[d];
                     }
-                    T q[D], eo[NV], lo, mo;
-                    apply_tile<T, D, HX, HY, CX, CY>(su, sl, sm, HN, lx, ly, lz, ue, q, eo, lo, mo);
+                    T q[D], se[NV];
+                    if constexpr (D == 2) {
+                        q[0] = T(0);
+                        q[1] = T(0);
+#pragma unroll
+                        for (int a = 0; a < 4; a++) {
+                            const int cl = (lx - (a & 1)) + CX * (ly - (a >> 1));
+                            const T s3[3] = {scell[cl], scell[HC + cl], scell[2 * HC + cl]};
+                            const T fh[2] = {scell[3 * HC + cl], scell[4 * HC + cl]};
+                            T f[2];
+                            node_force2<T>(a, s3, fh, f);
+                            q[0] += f[0];
+                            q[1] += f[1];
+                        }
+                        // own cell's average stress without the mean strain
+                        const int c0 = lx + CX * ly;
+                        T sx[3];
+                        voigt_stress<T, 2>(sl[c0], sm[c0], ue, sx);
+                        se[0] = scell[c0] - sx[0];
+                        se[1] = scell[HC + c0] - sx[1];
+                        se[2] = scell[2 * HC + c0] - sx[2];
+                    } else {
+                        T eo[NV], lo, mo;
+                        apply_tile<T, D, HX, HY, CX, CY>(su, sl, sm, HN, lx, ly, lz, ue, q, eo, lo, mo);
+                        voigt_stress<T, D>(lo, mo, eo, se);
+                    }
 #pragma unroll
                     for (int d = 0; d < D; d++) {
                         A.w[nxt][d][n] = q[d];
@@ -598,15 +694,13 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
                         acc[1].addprod(q[d], un[d]);
                         acc[2].addprod(rn[d], rn[d]);
                     }
-                    T se[NV];
-                    voigt_stress<T, D>(lo, mo, eo, se);
 #pragma unroll
                     for (int vv = 0; vv < NV; vv++) acc[3 + vv].add(se[vv]);
                 }
                 __syncthreads();
             }
             double tt[3 + NV];
-            if (!reduce_barrier<Acc<T>, 3 + NV>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tt)) return;
+            if (!reduce_barrier<Acc<T>, 3 + NV>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tt, bid, nbk)) return;
             const bool was_first = first;
             if (lead) {
                 double s6[6];
@@ -653,14 +747,14 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
         if (lead) {
             for (int vv = 0; vv < NV; vv++) E64[vv] += XE[vv];
             s_ctl = (it_total >= A.maxit) ? CTL_STOP : CTL_RUN;
-            if (blockIdx.x == 0)
+            if (bid == 0)
                 for (int vv = 0; vv < NV; vv++) A.result[24 + vv] = E64[vv];
         }
         __syncthreads();
         const int stop = s_ctl;
         Acc<T> dummy[1];
         double dres[1];
-        if (!reduce_barrier<Acc<T>, 1>(dummy, A.partials, A.result, A.bar_count, A.bar_gen, err, dres)) return;
+        if (!reduce_barrier<Acc<T>, 1>(dummy, A.partials, A.result, A.bar_count, A.bar_gen, err, dres, bid, nbk)) return;
         if (stop == CTL_STOP) { if (lead) conv = false; break; }
     }
     if (refine) {
@@ -668,7 +762,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(PCGArgs<T, D> A)
 #pragma unroll
             for (int d = 0; d < D; d++) A.u[d][n] = (T)A.x64[d][n];
     }
-    if (blockIdx.x == 0 && lead) {
+    if (bid == 0 && lead) {
         for (int vv = 0; vv < NV; vv++) A.sc->E[vv] = refine ? E64[vv] : XE[vv];
         A.sc->iters = it_total;
         A.sc->bnorm = bnorm;

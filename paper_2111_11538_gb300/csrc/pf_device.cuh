@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace pfdev {
 
 constexpr int PSTRIDE = 24;       // doubles per block in a partials array
@@ -162,6 +164,128 @@ __device__ void grid_sum(const double *partials, int nb, int off, double (&out)[
 #pragma unroll
     for (int k = 0; k < K; k++) out[k] = res[k];
     __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Block reduction of per-thread accumulators to one FP64 value per entry,
+// written by thread 0 to dst.  FP32 accumulators are reduced as (sum, error)
+// pairs with error-free additions, so no FP64 arithmetic runs per thread.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pair_add(float &h, float &l, float h2, float l2)
+{
+    const float s = h + h2;
+    const float bp = s - h;
+    const float e = (h - (s - bp)) + (h2 - bp);
+    l = l + l2 + e;
+    h = s + l;
+    l = l - (h - s);
+}
+
+template <int K>
+__device__ void block_reduce_store(Acc<float> (&a)[K], double *dst)
+{
+    __shared__ float sh[K][32], sl[K][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        float h = a[k].s, l = a[k].c;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+            pair_add(h, l, h2, l2);
+        }
+        if (lane == 0) { sh[k][wid] = h; sl[k][wid] = l; }
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            float h = lane < nw ? sh[k][lane] : 0.f, l = lane < nw ? sl[k][lane] : 0.f;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+                pair_add(h, l, h2, l2);
+            }
+            if (lane == 0) dst[k] = (double)h + (double)l;
+        }
+    }
+    __syncthreads();
+}
+
+template <int K>
+__device__ void block_reduce_store(Acc<double> (&a)[K], double *dst)
+{
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = a[k].value();
+    block_sum_store<K>(v, dst);
+}
+
+// FP32 path: the block's K sums as (hi, lo) float pairs, written by thread 0
+// into the block's partials slot.
+template <int K>
+__device__ void block_reduce_pairs(Acc<float> (&a)[K], float2 *dst)
+{
+    __shared__ float sh[K][32], sl[K][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        float h = a[k].s, l = a[k].c;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+            pair_add(h, l, h2, l2);
+        }
+        if (lane == 0) { sh[k][wid] = h; sl[k][wid] = l; }
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            float h = lane < nw ? sh[k][lane] : 0.f, l = lane < nw ? sl[k][lane] : 0.f;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+                pair_add(h, l, h2, l2);
+            }
+            if (lane == 0) dst[k] = make_float2(h, l);
+        }
+    }
+    __syncthreads();
+}
+
+// Last block: every thread loads the pairs of a fixed set of blocks (all
+// loads independent), then a pair-arithmetic block tree; thread 0 publishes
+// hi + lo in FP64.  The order depends only on indices.
+template <int K>
+__device__ void last_block_pairs(const double *partials, int nb, double *result)
+{
+    Acc<float> acc[K];
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const float2 *src = reinterpret_cast<const float2 *>(partials + (size_t)b * PSTRIDE);
+        float2 v[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) v[k] = __ldcg(src + k);
+#pragma unroll
+        for (int k = 0; k < K; k++) pair_add(acc[k].s, acc[k].c, v[k].x, v[k].y);
+    }
+    __shared__ float2 tmp[K];
+    block_reduce_pairs<K>(acc, tmp);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) result[k] = (double)tmp[k].x + (double)tmp[k].y;
+    }
+}
+
+// FP64 path of the same: every thread sums a fixed set of blocks, then the
+// block tree; thread 0 writes the totals to result.
+template <int K>
+__device__ void last_block_sums(const double *partials, int nb, double *result)
+{
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < K; k++) v[k] += __ldcg(partials + (size_t)b * PSTRIDE + k);
+    }
+    block_sum_store<K>(v, result);
 }
 
 // Grid barrier for a cooperative launch.  The wait is bounded: after

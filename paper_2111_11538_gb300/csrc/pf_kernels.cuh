@@ -24,11 +24,63 @@ struct FieldPtrs {
     T *u[3];
 };
 
+// One grid (instance) of a launch.  A launch serves one or many instances:
+// its blocks are split into consecutive ranges, one per job, and every block
+// works on its job's grid only (block bid of nbk within the job).
 template <typename T, int D>
-__global__ void k_setup(Params P, FieldPtrs<T, D> F)
+struct CellJob {
+    Params P;
+    FieldPtrs<T, D> F;
+    const Scalars *sc;       // mean strain for the return map
+    double *partials;        // per-block sums of the update
+    unsigned int *counter;   // last-block counter of the update
+    Diag *dg;
+    int block0, nblocks;
+};
+
+// Job of this block: the last job whose first block is <= blockIdx.x (jobs
+// are sorted by block0).
+template <typename Job>
+__device__ __forceinline__ const Job *my_job(const Job *jobs, int njobs)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].block0 <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    return jobs + lo;
+}
+
+// The jobs of a cell launch: a device table (sorted by block0), or, when the
+// table is null, the single job carried in the launch parameters (used by
+// callers that must not copy anything to the device before the launch).
+template <typename Job>
+struct JobSet {
+    const Job *table;
+    int njobs;
+    Job one;
+};
+
+template <typename Job>
+__device__ __forceinline__ const Job *my_job(const JobSet<Job> &js)
+{
+    return js.table ? my_job(js.table, js.njobs) : &js.one;
+}
+
+#define PF_CELL_JOB_PROLOGUE                                   \
+    const CellJob<T, D> *J_ = my_job(js);                      \
+    const Params P = J_->P;                                    \
+    const FieldPtrs<T, D> F = J_->F;                           \
+    const long long bid = (long long)blockIdx.x - J_->block0;  \
+    const long long nbk = J_->nblocks;
+
+template <typename T, int D>
+__global__ void k_setup(const __grid_constant__ JobSet<CellJob<T, D>> js)
 {
     constexpr int NV = Dims<D>::NV;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.N; c += (long long)gridDim.x * blockDim.x) {
+    PF_CELL_JOB_PROLOGUE
+    for (long long c = bid * blockDim.x + threadIdx.x; c < P.N; c += nbk * blockDim.x) {
         T Wf, Ww, Wg;
         phase_weights(F.theta[c], F.phig[c], Wf, Ww, Wg);
         T K = (Wf + Ww) * T(P.Ks) + Wg * T(P.Kg);
@@ -86,15 +138,18 @@ __device__ __forceinline__ void node_of(int a, int &ox, int &oy, int &oz)
 // form): yield |dev sigma| - sqrt(2/3)(sigma_Y + H a) <= 0, flow along
 // dev sigma / |dev sigma|, da = dlambda = f / (2G + sqrt(2/3) H).
 // Outputs eps_p, alpha, the coupling scalars t = tr eps_e and s = |dev eps_e|^2
-// and (on request) the stress.
+// and the stress.
 // ---------------------------------------------------------------------------
 template <typename T, int D>
-__global__ void k_return(Params P, FieldPtrs<T, D> F, const Scalars *sc, int want_sigma)
+__global__ void k_return(const __grid_constant__ JobSet<CellJob<T, D>> js)
 {
     constexpr int NN = Dims<D>::NN, NV = Dims<D>::NV;
+    PF_CELL_JOB_PROLOGUE
+    const Scalars *sc = J_->sc;
+    const int want_sigma = 1;
     double Ed[6];
     for (int v = 0; v < NV; v++) Ed[v] = sc->E[v];
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.N; c += (long long)gridDim.x * blockDim.x) {
+    for (long long c = bid * blockDim.x + threadIdx.x; c < P.N; c += nbk * blockDim.x) {
         int i, j, k;
         cell_coords<D>(P, c, i, j, k);
         T ue[NN][D];
@@ -180,9 +235,10 @@ __global__ void k_return(Params P, FieldPtrs<T, D> F, const Scalars *sc, int wan
 // and mobility M_O = D_O(phi_g) / (c sum_a W_a f_a''(x_O))   (Sec. 2.2, 3.2)
 // ---------------------------------------------------------------------------
 template <typename T, int D>
-__global__ void k_mu(Params P, FieldPtrs<T, D> F)
+__global__ void k_mu(const __grid_constant__ JobSet<CellJob<T, D>> js)
 {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.N; c += (long long)gridDim.x * blockDim.x) {
+    PF_CELL_JOB_PROLOGUE
+    for (long long c = bid * blockDim.x + threadIdx.x; c < P.N; c += nbk * blockDim.x) {
         int i, j, k;
         cell_coords<D>(P, c, i, j, k);
         const T x = F.xO[c];
@@ -211,12 +267,17 @@ __global__ void k_mu(Params P, FieldPtrs<T, D> F)
 // of the new fields and of the supply exchange are reduced by the last block.
 // ---------------------------------------------------------------------------
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_update(Params P, FieldPtrs<T, D> F, double *partials, unsigned int *counter, Diag *dg)
+__global__ void __launch_bounds__(256) k_update(const __grid_constant__ JobSet<CellJob<T, D>> js)
 {
-    Acc<T> sO, sH, sW, rem, sup;
+    PF_CELL_JOB_PROLOGUE
+    double *partials = J_->partials;
+    unsigned int *counter = J_->counter;
+    Diag *dg = J_->dg;
+    Acc<T> acc[6];           // sum x_O, x_H, x_H2O, removed water, supplied H, non-finite count
+    Acc<T> &sO = acc[0], &sH = acc[1], &sW = acc[2], &rem = acc[3], &sup = acc[4];
     int bad = 0;
     const T cc = T(P.c), eps2 = T(2 * P.eps), dt = T(P.dt);
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.N; c += (long long)gridDim.x * blockDim.x) {
+    for (long long c = bid * blockDim.x + threadIdx.x; c < P.N; c += nbk * blockDim.x) {
         int i, j, k;
         cell_coords<D>(P, c, i, j, k);
         long long nbr[2 * D];
@@ -270,19 +331,20 @@ __global__ void __launch_bounds__(256) k_update(Params P, FieldPtrs<T, D> F, dou
         sO.add(nxo); sH.add(nxh); sW.add(nxw);
         if (!(isfinite(nth) && isfinite(nxo) && isfinite(nxh) && isfinite(nxw))) bad = 1;
     }
-    double v[6] = {sO.value(), sH.value(), sW.value(), rem.value(), sup.value(), (double)bad};
-    block_sum_store<6>(v, partials + (size_t)blockIdx.x * PSTRIDE);
+    acc[5].add(T(bad));
+    // per-block sums (FP32 pairs in the mixed method: no FP64 per thread)
+    block_reduce_store<6>(acc, partials + (size_t)bid * PSTRIDE);
     __shared__ bool last;
     if (threadIdx.x == 0) {
         __threadfence();
         unsigned int tk = atomicAdd(counter, 1u);
-        last = (tk == gridDim.x - 1);
+        last = (tk == (unsigned int)nbk - 1);
     }
     __syncthreads();
     if (last) {
         __threadfence();
-        double tot[6];
-        grid_sum<6>(partials, gridDim.x, 0, tot);
+        __shared__ double tot[6];
+        last_block_sums<6>(partials, (int)nbk, tot);
         if (threadIdx.x == 0) {
             dg->sumO = tot[0]; dg->sumH = tot[1]; dg->sumW = tot[2];
             dg->removedW += tot[3];

@@ -177,8 +177,23 @@ struct pf_handle {
     Diag *dg = nullptr;
     double *stage = nullptr, *stage2 = nullptr;
     void **ptrtab = nullptr;           // device table of component pointers (6 entries)
-    int cg_grid = 0, cg_block = 256;
+    int cg_block = 256;
     bool sigma_valid = false;
+
+    // Launch plan.  Every kernel of a step serves all instances of the handle
+    // (one for pf_create, several for pf_batch_create) through job tables in
+    // device memory; tables [k] describe the state k steps from now.
+    bool is_batch = false;
+    std::vector<pf_handle *> members;   // batch members (owned by the batch)
+    void *d_cell_jobs[2] = {nullptr, nullptr};
+    void *d_pcg_jobs = nullptr;
+    int cell_grid = 0, pcg_grid = 0, njobs = 0;
+    int cg_per_sm = 0;
+    bool plan_ready = false;
+    int plan_par = 0;                   // which table describes the current state
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step from job tables [k]
+    bool graph_failed = false;
+    bool use_graph = true;
 
     // profiling: event pairs around each launch while enabled
     bool prof_on = false;
@@ -279,6 +294,11 @@ FieldPtrs<T, D> field_ptrs(pf_handle *h)
     return F;
 }
 
+std::vector<pf_handle *> instances(pf_handle *h)
+{
+    return h->is_batch ? h->members : std::vector<pf_handle *>{h};
+}
+
 template <typename T, int D>
 int setup_cg_launch(pf_handle *h)
 {
@@ -287,64 +307,208 @@ int setup_cg_launch(pf_handle *h)
     if (e != cudaSuccess) return h->cuda(e, "occupancy query");
     if (per_sm < 1) return h->fail(PF_ECUDA, "CG kernel cannot be resident");
     if (per_sm > 4) per_sm = 4;
-    long long want = (h->P.N + h->cg_block - 1) / h->cg_block;
-    long long g = (long long)per_sm * h->sms;
-    if (want < g) g = want;
-    if (g < 1) g = 1;
-    h->cg_grid = (int)g;
+    h->cg_per_sm = per_sm;
     return PF_OK;
 }
 
 template <typename T, int D>
+PCGArgs<T, D> pcg_args(pf_handle *m)
+{
+    PCGArgs<T, D> A;
+    memset(&A, 0, sizeof(A));
+    A.P = m->P;
+    A.lam = (const T *)m->lam; A.mu = (const T *)m->mu;
+    for (int v = 0; v < 6; v++) A.sig[v] = (const T *)m->sig[v];
+    for (int d = 0; d < 3; d++) {
+        A.x[d] = (T *)(m->refine ? m->corr[d] : m->u[d]); A.p[d] = (T *)m->p[d];
+        A.u[d] = (T *)m->u[d]; A.x64[d] = m->x64[d];
+        for (int k = 0; k < 2; k++) { A.r[k][d] = (T *)m->r[k][d]; A.w[k][d] = (T *)m->w[k][d]; A.s[k][d] = (T *)m->s[k][d]; }
+    }
+    A.refine = m->refine ? 1 : 0;
+    A.eta = 1e-3;
+    A.diag = (T *)m->diag;
+    A.partials = m->partials;
+    A.result = m->result;
+    A.bar_count = m->sync; A.bar_gen = m->sync + SYNC_GEN;
+    A.sc = m->sc; A.dg = m->dg;
+    A.rtol = m->cfg.cg_rtol; A.maxit = m->cfg.cg_maxit;
+    A.warm = m->cfg.warm_start == PF_WS_PREV ? 1 : 0;
+    return A;
+}
+
+// Build the job tables of every instance: cell kernels get ~N/256 blocks per
+// instance; the cooperative PCG launch splits the co-resident block capacity
+// over the instances in proportion to their tile counts (at least one each).
+template <typename T, int D>
+int build_plan(pf_handle *h)
+{
+    std::vector<pf_handle *> I = instances(h);
+    const int n = (int)I.size();
+    std::vector<CellJob<T, D>> cj[2];
+    cj[0].resize(n);
+    cj[1].resize(n);
+    int b0 = 0;
+    for (int i = 0; i < n; i++) {
+        pf_handle *m = I[i];
+        const int nb = grid_for(m, m->P.N);
+        for (int k = 0; k < 2; k++) {
+            const int saved = m->cur;
+            m->cur = saved ^ k;
+            CellJob<T, D> &j = cj[k][i];
+            memset(&j, 0, sizeof(j));
+            j.P = m->P;
+            j.F = field_ptrs<T, D>(m);
+            m->cur = saved;
+            j.sc = m->sc;
+            j.partials = m->partials;
+            j.counter = m->sync + SYNC_LAST;
+            j.dg = m->dg;
+            j.block0 = b0;
+            j.nblocks = nb;
+        }
+        b0 += nb;
+    }
+    h->cell_grid = b0;
+    h->njobs = n;
+    const size_t cbytes = sizeof(CellJob<T, D>) * (size_t)n;
+    if (!h->d_cell_jobs[0]) {
+        PF_TRY(h->alloc(&h->d_cell_jobs[0], cbytes));
+        PF_TRY(h->alloc(&h->d_cell_jobs[1], cbytes));
+    }
+    PF_TRY(h->cuda(cudaMemcpy(h->d_cell_jobs[0], cj[0].data(), cbytes, cudaMemcpyHostToDevice), "job table"));
+    PF_TRY(h->cuda(cudaMemcpy(h->d_cell_jobs[1], cj[1].data(), cbytes, cudaMemcpyHostToDevice), "job table"));
+    if (h->cfg.mechanics) {
+        constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+        // Jacobi-PCG iteration counts grow with the grid's linear size, so
+        // an instance's work per solve is ~ tiles x linear size: blocks are
+        // shared out in proportion to that, so that instances finish together
+        std::vector<long long> tiles(n);
+        std::vector<double> work(n);
+        double wtot = 0.0;
+        for (int i = 0; i < n; i++) {
+            const Params &P = I[i]->P;
+            tiles[i] = (long long)((P.nx + TX - 1) / TX) * ((P.ny + TY - 1) / TY) * (D == 3 ? (P.nz + TZ - 1) / TZ : 1);
+            const double lin = (double)std::max(P.nx, std::max(P.ny, D == 3 ? P.nz : 1));
+            work[i] = (double)tiles[i] * lin;
+            wtot += work[i];
+        }
+        const long long cap = (long long)h->cg_per_sm * h->sms;
+        if (cap < n) return h->fail(PF_EINVAL, "batch of %d instances exceeds the %lld co-resident CG blocks", n, cap);
+        std::vector<PCGArgs<T, D>> pj(n);
+        int g0 = 0;
+        for (int i = 0; i < n; i++) {
+            long long nb = 1 + (long long)((double)(cap - n) * work[i] / wtot);
+            if (nb > tiles[i]) nb = tiles[i] > 0 ? tiles[i] : 1;
+            pj[i] = pcg_args<T, D>(I[i]);
+            pj[i].block0 = g0;
+            pj[i].nblocks = (int)nb;
+            g0 += (int)nb;
+        }
+        h->pcg_grid = g0;
+        const size_t pbytes = sizeof(PCGArgs<T, D>) * (size_t)n;
+        if (!h->d_pcg_jobs) PF_TRY(h->alloc(&h->d_pcg_jobs, pbytes));
+        PF_TRY(h->cuda(cudaMemcpy(h->d_pcg_jobs, pj.data(), pbytes, cudaMemcpyHostToDevice), "job table"));
+    }
+    for (int k = 0; k < 2; k++) {
+        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+        h->graph[k] = nullptr;
+    }
+    h->plan_par = 0;
+    h->plan_ready = true;
+    return PF_OK;
+}
+
+// Queue one step of every instance; k selects the job tables (0: current
+// state, 1: one step later).
+template <typename T, int D>
+int launch_step(pf_handle *h, cudaStream_t s, int k)
+{
+    JobSet<CellJob<T, D>> cj;
+    memset(&cj, 0, sizeof(cj));
+    cj.table = (const CellJob<T, D> *)h->d_cell_jobs[k];
+    cj.njobs = h->njobs;
+    const int n = h->njobs;
+    if (h->cfg.mechanics) {
+        h->mark_begin(PF_K_SETUP, s);
+        k_setup<T, D><<<h->cell_grid, 256, 0, s>>>(cj);
+        h->mark_end(s);
+        const PCGArgs<T, D> *pj = (const PCGArgs<T, D> *)h->d_pcg_jobs;
+        int nj = n;
+        void *args[] = {(void *)&pj, (void *)&nj};
+        h->mark_begin(PF_K_CG, s);
+        cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_pcg<T, D>, dim3(h->pcg_grid), dim3(h->cg_block), args, 0, s);
+        h->mark_end(s);
+        if (e != cudaSuccess) return h->cuda(e, "cooperative CG launch");
+        h->mark_begin(PF_K_RETURN, s);
+        k_return<T, D><<<h->cell_grid, 256, 0, s>>>(cj);
+        h->mark_end(s);
+    }
+    h->mark_begin(PF_K_MU, s);
+    k_mu<T, D><<<h->cell_grid, 256, 0, s>>>(cj);
+    h->mark_end(s);
+    h->mark_begin(PF_K_UPDATE, s);
+    k_update<T, D><<<h->cell_grid, 256, 0, s>>>(cj);
+    h->mark_end(s);
+    return h->cuda(cudaGetLastError(), "kernel launch");
+}
+
+void advance(pf_handle *h, int nsteps)
+{
+    for (pf_handle *m : instances(h)) {
+        m->cur ^= (nsteps & 1);
+        m->steps += nsteps;
+        m->sigma_valid = true;
+    }
+    if (h->is_batch) h->steps += nsteps;
+    h->plan_par ^= (nsteps & 1);
+}
+
+// Steps are replayed from CUDA graphs of one step, one per job-table parity
+// (captured once per plan on the handle's stream), unless per-kernel timing
+// is on; a graph that cannot be captured falls back to direct launches.
+template <typename T, int D>
 int run_steps(pf_handle *h, int nsteps, cudaStream_t s)
 {
-    const Params &P = h->P;
-    const int ge = grid_for(h, P.N);
-    for (int step = 0; step < nsteps; step++) {
-        FieldPtrs<T, D> F = field_ptrs<T, D>(h);
-        if (h->cfg.mechanics) {
-            h->mark_begin(PF_K_SETUP, s);
-            k_setup<T, D><<<ge, 256, 0, s>>>(P, F);
-            h->mark_end(s);
-            PCGArgs<T, D> A;
-            A.P = P;
-            A.lam = (const T *)h->lam; A.mu = (const T *)h->mu;
-            for (int v = 0; v < 6; v++) A.sig[v] = (const T *)h->sig[v];
-            for (int d = 0; d < 3; d++) {
-                A.x[d] = (T *)(h->refine ? h->corr[d] : h->u[d]); A.p[d] = (T *)h->p[d];
-                A.u[d] = (T *)h->u[d]; A.x64[d] = h->x64[d];
-                for (int k = 0; k < 2; k++) { A.r[k][d] = (T *)h->r[k][d]; A.w[k][d] = (T *)h->w[k][d]; A.s[k][d] = (T *)h->s[k][d]; }
+    if (!h->plan_ready) PF_TRY((build_plan<T, D>(h)));
+    while (nsteps > 0) {
+        const int k = h->plan_par;
+        const bool graphable = h->use_graph && !h->prof_on && !h->graph_failed;
+        if (graphable && !h->graph[k]) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(h->own, cudaStreamCaptureModeThreadLocal);
+            int rc = PF_OK;
+            pf_profile saved = h->prof;
+            if (e == cudaSuccess) {
+                rc = launch_step<T, D>(h, h->own, k);
+                e = cudaStreamEndCapture(h->own, &g);
             }
-            A.refine = h->refine ? 1 : 0;
-            A.eta = 1e-3;
-            A.diag = (T *)h->diag;
-            A.partials = h->partials;
-            A.result = h->result;
-            A.bar_count = h->sync; A.bar_gen = h->sync + SYNC_GEN;
-            A.sc = h->sc; A.dg = h->dg;
-            A.rtol = h->cfg.cg_rtol; A.maxit = h->cfg.cg_maxit;
-            A.warm = h->cfg.warm_start == PF_WS_PREV ? 1 : 0;
-            void *args[] = {&A};
-            h->mark_begin(PF_K_CG, s);
-            cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_pcg<T, D>, dim3(h->cg_grid), dim3(h->cg_block), args, 0, s);
-            h->mark_end(s);
-            if (e != cudaSuccess) return h->cuda(e, "cooperative CG launch");
-            const int want_sigma = (step == nsteps - 1) ? 1 : 0;
-            h->mark_begin(PF_K_RETURN, s);
-            k_return<T, D><<<ge, 256, 0, s>>>(P, F, h->sc, want_sigma);
-            h->mark_end(s);
-            if (want_sigma) h->sigma_valid = true;
+            // launches recorded during capture are not executions
+            h->prof = saved;
+            if (e == cudaSuccess && rc == PF_OK && g) e = cudaGraphInstantiate(&h->graph[k], g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess || rc != PF_OK || !h->graph[k]) {
+                h->graph_failed = true;
+                h->graph[k] = nullptr;
+                cudaGetLastError();
+                h->err.clear();
+                continue;
+            }
         }
-        h->mark_begin(PF_K_MU, s);
-        k_mu<T, D><<<ge, 256, 0, s>>>(P, F);
-        h->mark_end(s);
-        h->mark_begin(PF_K_UPDATE, s);
-        k_update<T, D><<<ge, 256, 0, s>>>(P, F, h->partials, h->sync + SYNC_LAST, h->dg);
-        h->mark_end(s);
-        h->cur = 1 - h->cur;
-        h->steps++;
+        if (graphable && h->graph[k]) {
+            PF_TRY(h->cuda(cudaGraphLaunch(h->graph[k], s), "graph launch"));
+            // one launch per kernel class of the step, whatever the batch size
+            const int cls[5] = {PF_K_MU, PF_K_UPDATE, PF_K_SETUP, PF_K_CG, PF_K_RETURN};
+            const int per = h->cfg.mechanics ? 5 : 2;
+            h->prof.launches += per;
+            for (int c = 0; c < per; c++) h->prof.count[cls[c]] += 1;
+            h->prof.graph_steps += 1;
+        } else {
+            PF_TRY((launch_step<T, D>(h, s, k)));
+        }
+        advance(h, 1);
+        nsteps -= 1;
     }
-    return h->cuda(cudaGetLastError(), "kernel launch");
+    return PF_OK;
 }
 
 template <typename T>
@@ -440,6 +604,7 @@ int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
     h->cg_total_seen = 0;
     h->have_fields = true;
     h->sigma_valid = false;
+    h->plan_ready = false;          // the field buffers' roles changed
     return h->cuda(cudaGetLastError(), "set_fields kernels");
 #undef PF_SRC
 }
@@ -559,12 +724,73 @@ int alloc_fields(pf_handle *h)
 
 void free_all(pf_handle *h)
 {
+    for (int k = 0; k < 2; k++) {
+        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+        h->graph[k] = nullptr;
+    }
+    for (pf_handle *m : h->members) {
+        free_all(m);
+        delete m;
+    }
+    h->members.clear();
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
     for (void *p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->own) cudaStreamDestroy(h->own);
     h->own = nullptr;
+}
+
+// Validate a configuration and create one instance (device arrays, stream,
+// CG launch shape).  On failure *out stays null and err says why.
+int create_one(const pf_config *cfg, pf_handle **out, std::string &err)
+{
+    if (!cfg) { err = "cfg is NULL"; return PF_EINVAL; }
+    const pf_config &c = *cfg;
+    if (c.ndim != 2 && c.ndim != 3) { err = "ndim must be 2 or 3"; return PF_EINVAL; }
+    if (c.nx < 2 || c.ny < 2 || (c.ndim == 3 && c.nz < 2)) { err = "grid sizes must be >= 2"; return PF_EINVAL; }
+    if (c.precision != PF_FP64 && c.precision != PF_MIXED) { err = "precision must be PF_FP64 or PF_MIXED"; return PF_EINVAL; }
+    if (c.warm_start != PF_WS_ZERO && c.warm_start != PF_WS_PREV) { err = "warm_start must be PF_WS_ZERO or PF_WS_PREV"; return PF_EINVAL; }
+    if (c.mechanics && (c.cg_maxit <= 0 || !(c.cg_rtol > 0.0))) { err = "cg_maxit must be > 0 and cg_rtol > 0"; return PF_EINVAL; }
+    if (!(c.p.nu > -1.0 && c.p.nu < 0.5) || !(c.p.E_s > 0.0) || !(c.p.E_g_ratio > 0.0)) { err = "elastic constants out of range"; return PF_EINVAL; }
+    const long long N = (long long)c.nx * c.ny * (c.ndim == 3 ? c.nz : 1);
+    if (N > (1LL << 31)) { err = "grid too large (more than 2^31 cells)"; return PF_EINVAL; }
+
+    pf_handle *h = new (std::nothrow) pf_handle();
+    if (!h) { err = "host allocation failed"; return PF_ENOMEM; }
+    h->cfg = c;
+    memset(&h->prof, 0, sizeof(h->prof));
+    if (c.ndim == 2) h->cfg.nz = 1;
+    h->fp64 = c.precision == PF_FP64;
+    h->tsz = h->fp64 ? sizeof(double) : sizeof(float);
+    cudaError_t e = cudaGetDevice(&h->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        err = std::string("CUDA unavailable: ") + cudaGetErrorString(e);
+        delete h;
+        return PF_ECUDA;
+    }
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev);
+    if (!coop) { err = "device lacks cooperative launch"; free_all(h); delete h; return PF_ECUDA; }
+    if (!upload_tables(h->dev)) { err = "constant table upload failed"; free_all(h); delete h; return PF_ECUDA; }
+
+    fill_params(h->cfg, N, h->P);
+
+    int rc = h->fp64 ? alloc_fields<double>(h) : alloc_fields<float>(h);
+    if (rc == PF_OK && c.mechanics) {
+        if (c.ndim == 2) rc = h->fp64 ? setup_cg_launch<double, 2>(h) : setup_cg_launch<float, 2>(h);
+        else rc = h->fp64 ? setup_cg_launch<double, 3>(h) : setup_cg_launch<float, 3>(h);
+    }
+    if (rc != PF_OK) {
+        err = h->err;
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return PF_OK;
 }
 
 } // namespace
@@ -585,57 +811,103 @@ int pf_create(const pf_config *cfg, pf_handle **out)
     if (!out) return PF_EINVAL;
     *out = nullptr;
     g_create_error.clear();
-    if (!cfg) { g_create_error = "cfg is NULL"; return PF_EINVAL; }
-    const pf_config &c = *cfg;
-    if (c.ndim != 2 && c.ndim != 3) { g_create_error = "ndim must be 2 or 3"; return PF_EINVAL; }
-    if (c.nx < 2 || c.ny < 2 || (c.ndim == 3 && c.nz < 2)) { g_create_error = "grid sizes must be >= 2"; return PF_EINVAL; }
-    if (c.precision != PF_FP64 && c.precision != PF_MIXED) { g_create_error = "precision must be PF_FP64 or PF_MIXED"; return PF_EINVAL; }
-    if (c.warm_start != PF_WS_ZERO && c.warm_start != PF_WS_PREV) { g_create_error = "warm_start must be PF_WS_ZERO or PF_WS_PREV"; return PF_EINVAL; }
-    if (c.mechanics && (c.cg_maxit <= 0 || !(c.cg_rtol > 0.0))) { g_create_error = "cg_maxit must be > 0 and cg_rtol > 0"; return PF_EINVAL; }
-    if (!(c.p.nu > -1.0 && c.p.nu < 0.5) || !(c.p.E_s > 0.0) || !(c.p.E_g_ratio > 0.0)) { g_create_error = "elastic constants out of range"; return PF_EINVAL; }
-    const long long N = (long long)c.nx * c.ny * (c.ndim == 3 ? c.nz : 1);
-    if (N > (1LL << 31)) { g_create_error = "grid too large (more than 2^31 cells)"; return PF_EINVAL; }
+    return create_one(cfg, out, g_create_error);
+}
 
-    pf_handle *h = new (std::nothrow) pf_handle();
-    if (!h) { g_create_error = "host allocation failed"; return PF_ENOMEM; }
-    h->cfg = c;
-    memset(&h->prof, 0, sizeof(h->prof));
-    if (c.ndim == 2) h->cfg.nz = 1;
-    h->fp64 = c.precision == PF_FP64;
-    h->tsz = h->fp64 ? sizeof(double) : sizeof(float);
-    cudaError_t e = cudaGetDevice(&h->dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
+int pf_batch_create(const pf_config *cfgs, int n, pf_handle **out)
+{
+    if (!out) return PF_EINVAL;
+    *out = nullptr;
+    g_create_error.clear();
+    if (!cfgs || n < 1) { g_create_error = "cfgs is NULL or n < 1"; return PF_EINVAL; }
+    for (int i = 1; i < n; i++) {
+        if (cfgs[i].ndim != cfgs[0].ndim || cfgs[i].precision != cfgs[0].precision
+            || (cfgs[i].mechanics != 0) != (cfgs[0].mechanics != 0)) {
+            g_create_error = "batch instances must share ndim, precision and mechanics";
+            return PF_EINVAL;
+        }
+    }
+    pf_handle *b = new (std::nothrow) pf_handle();
+    if (!b) { g_create_error = "host allocation failed"; return PF_ENOMEM; }
+    b->is_batch = true;
+    memset(&b->prof, 0, sizeof(b->prof));
+    for (int i = 0; i < n; i++) {
+        pf_handle *m = nullptr;
+        std::string err;
+        int rc = create_one(&cfgs[i], &m, err);
+        if (rc != PF_OK) {
+            char buf[64];
+            snprintf(buf, sizeof(buf), "instance %d: ", i);
+            g_create_error = buf + err;
+            free_all(b);
+            delete b;
+            return rc;
+        }
+        b->members.push_back(m);
+    }
+    pf_handle *m0 = b->members[0];
+    b->cfg = m0->cfg;
+    b->P = m0->P;
+    b->fp64 = m0->fp64;
+    b->tsz = m0->tsz;
+    b->dev = m0->dev;
+    b->sms = m0->sms;
+    b->cg_block = m0->cg_block;
+    b->cg_per_sm = m0->cg_per_sm;
+    for (pf_handle *m : b->members) b->bytes += m->bytes;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
-        g_create_error = std::string("CUDA unavailable: ") + cudaGetErrorString(e);
-        delete h;
+        g_create_error = std::string("stream: ") + cudaGetErrorString(e);
+        free_all(b);
+        delete b;
         return PF_ECUDA;
     }
-    int coop = 0;
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev);
-    if (!coop) { g_create_error = "device lacks cooperative launch"; free_all(h); delete h; return PF_ECUDA; }
-    if (!upload_tables(h->dev)) { g_create_error = "constant table upload failed"; free_all(h); delete h; return PF_ECUDA; }
+    *out = b;
+    return PF_OK;
+}
 
-    fill_params(h->cfg, N, h->P);
+int pf_batch_size(const pf_handle *h)
+{
+    if (!h) return 0;
+    return h->is_batch ? (int)h->members.size() : 1;
+}
 
-    int rc = h->fp64 ? alloc_fields<double>(h) : alloc_fields<float>(h);
-    if (rc == PF_OK && c.mechanics) {
-        if (c.ndim == 2) rc = h->fp64 ? setup_cg_launch<double, 2>(h) : setup_cg_launch<float, 2>(h);
-        else rc = h->fp64 ? setup_cg_launch<double, 3>(h) : setup_cg_launch<float, 3>(h);
-    }
-    if (rc != PF_OK) {
-        g_create_error = h->err;
-        free_all(h);
-        delete h;
-        return rc;
-    }
-    *out = h;
+int pf_batch_set_fields(pf_handle *b, int i, const pf_fields *f, int where)
+{
+    if (!b) return PF_EINVAL;
+    if (!b->is_batch) return b->fail(PF_EINVAL, "not a batch handle");
+    if (i < 0 || i >= (int)b->members.size()) return b->fail(PF_EINVAL, "instance %d out of range", i);
+    cudaStreamSynchronize(b->own);
+    int rc = pf_set_fields(b->members[i], f, where);
+    if (rc != PF_OK) return b->fail(rc, "instance %d: %s", i, b->members[i]->err.c_str());
+    b->plan_ready = false;
+    return PF_OK;
+}
+
+int pf_batch_get_fields(pf_handle *b, int i, pf_fields *out, int where)
+{
+    if (!b) return PF_EINVAL;
+    if (!b->is_batch) return b->fail(PF_EINVAL, "not a batch handle");
+    if (i < 0 || i >= (int)b->members.size()) return b->fail(PF_EINVAL, "instance %d out of range", i);
+    int rc = pf_get_fields(b->members[i], out, where);
+    if (rc != PF_OK) return b->fail(rc, "instance %d: %s", i, b->members[i]->err.c_str());
+    return PF_OK;
+}
+
+int pf_batch_get_diagnostics(pf_handle *b, int i, pf_diag *out)
+{
+    if (!b) return PF_EINVAL;
+    if (!b->is_batch) return b->fail(PF_EINVAL, "not a batch handle");
+    if (i < 0 || i >= (int)b->members.size()) return b->fail(PF_EINVAL, "instance %d out of range", i);
+    int rc = pf_get_diagnostics(b->members[i], out);
+    if (rc != PF_OK) return b->fail(rc, "instance %d: %s", i, b->members[i]->err.c_str());
     return PF_OK;
 }
 
 int pf_set_fields(pf_handle *h, const pf_fields *f, int where)
 {
     if (!h) return PF_EINVAL;
+    if (h->is_batch) return h->fail(PF_EINVAL, "batch handle: use the pf_batch_ call for one instance");
     if (!f || !f->phi_f || !f->phi_w || !f->x_O || !f->x_H || !f->x_H2O)
         return h->fail(PF_EINVAL, "phi_f, phi_w, x_O, x_H and x_H2O are required");
     if (where != PF_HOST && where != PF_DEVICE) return h->fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
@@ -647,38 +919,58 @@ int pf_step(pf_handle *h, int nsteps, void *stream)
 {
     if (!h) return PF_EINVAL;
     if (nsteps < 0) return h->fail(PF_EINVAL, "nsteps < 0");
-    if (!h->have_fields) return h->fail(PF_ESTATE, "pf_step before pf_set_fields");
+    for (pf_handle *m : instances(h))
+        if (!m->have_fields) return h->fail(PF_ESTATE, "pf_step before the fields were set");
     cudaStream_t s = stream ? (cudaStream_t)stream : h->own;
-    if (s != h->own) {
-        // order the caller's stream after anything queued on the library stream
+    {
+        // order the caller's stream after anything queued on the library
+        // streams (the handle's and, in a batch, its members')
         cudaEvent_t ev;
         PF_TRY(h->cuda(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event"));
-        cudaEventRecord(ev, h->own);
-        cudaStreamWaitEvent(s, ev, 0);
+        for (pf_handle *m : instances(h)) {
+            if (m->own == s) continue;
+            cudaEventRecord(ev, m->own);
+            cudaStreamWaitEvent(s, ev, 0);
+        }
+        if (h->is_batch && h->own != s) {
+            cudaEventRecord(ev, h->own);
+            cudaStreamWaitEvent(s, ev, 0);
+        }
         cudaEventDestroy(ev);
     }
     // clear the sticky device status words of this call
-    PF_TRY(h->cuda(cudaMemsetAsync(&h->sc->status, 0, sizeof(int), s), "status clear"));
-    PF_TRY(h->cuda(cudaMemsetAsync(&h->dg->status, 0, sizeof(int), s), "status clear"));
-    PF_TRY(h->cuda(cudaMemsetAsync(&h->dg->cg_max, 0, sizeof(int), s), "status clear"));
+    for (pf_handle *m : instances(h)) {
+        PF_TRY(h->cuda(cudaMemsetAsync(&m->sc->status, 0, sizeof(int), s), "status clear"));
+        PF_TRY(h->cuda(cudaMemsetAsync(&m->dg->status, 0, sizeof(int), s), "status clear"));
+        PF_TRY(h->cuda(cudaMemsetAsync(&m->dg->cg_max, 0, sizeof(int), s), "status clear"));
+    }
     int rc;
     if (h->cfg.ndim == 2) rc = h->fp64 ? run_steps<double, 2>(h, nsteps, s) : run_steps<float, 2>(h, nsteps, s);
     else rc = h->fp64 ? run_steps<double, 3>(h, nsteps, s) : run_steps<float, 3>(h, nsteps, s);
     if (rc != PF_OK) return rc;
-    Scalars sc;
-    Diag dg;
-    PF_TRY(h->cuda(cudaMemcpyAsync(&sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost, s), "status read"));
-    PF_TRY(h->cuda(cudaMemcpyAsync(&dg, h->dg, sizeof(dg), cudaMemcpyDeviceToHost, s), "status read"));
+    std::vector<pf_handle *> I = instances(h);
+    std::vector<Scalars> scs(I.size());
+    std::vector<Diag> dgs(I.size());
+    for (size_t i = 0; i < I.size(); i++) {
+        PF_TRY(h->cuda(cudaMemcpyAsync(&scs[i], I[i]->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s), "status read"));
+        PF_TRY(h->cuda(cudaMemcpyAsync(&dgs[i], I[i]->dg, sizeof(Diag), cudaMemcpyDeviceToHost, s), "status read"));
+    }
     PF_TRY(h->cuda(cudaStreamSynchronize(s), "pf_step"));
+    long long cg_new = 0;
+    int st = PF_OK;
+    for (size_t i = 0; i < I.size(); i++) {
+        cg_new += dgs[i].cg_total - I[i]->cg_total_seen;
+        I[i]->cg_total_seen = dgs[i].cg_total;
+        int sti = PF_OK;
+        if (scs[i].status == 6 || dgs[i].status == 6) sti = PF_ETIMEOUT;
+        else if (dgs[i].status == 5) sti = PF_ENONFINITE;
+        else if (scs[i].status == 4) sti = PF_ENOTCONV;
+        if (sti == PF_ETIMEOUT || (sti == PF_ENONFINITE && st != PF_ETIMEOUT) || (sti == PF_ENOTCONV && st == PF_OK)) st = sti;
+    }
     if (h->prof_on) {
         h->harvest();
-        h->prof.cg_iters += dg.cg_total - h->cg_total_seen;
+        h->prof.cg_iters += cg_new;
     }
-    h->cg_total_seen = dg.cg_total;
-    int st = PF_OK;
-    if (sc.status == 6 || dg.status == 6) st = PF_ETIMEOUT;
-    else if (dg.status == 5) st = PF_ENONFINITE;
-    else if (sc.status == 4) st = PF_ENOTCONV;
     if (st == PF_ETIMEOUT) return h->fail(st, "a bounded device-side wait gave up");
     if (st == PF_ENONFINITE) return h->fail(st, "non-finite value in the fields");
     if (st == PF_ENOTCONV) return h->fail(st, "CG reached cg_maxit without meeting cg_rtol");
@@ -688,6 +980,7 @@ int pf_step(pf_handle *h, int nsteps, void *stream)
 int pf_get_fields(pf_handle *h, pf_fields *out, int where)
 {
     if (!h || !out) return PF_EINVAL;
+    if (h->is_batch) return h->fail(PF_EINVAL, "batch handle: use the pf_batch_ call for one instance");
     if (!h->have_fields) return h->fail(PF_ESTATE, "pf_get_fields before pf_set_fields");
     if (where != PF_HOST && where != PF_DEVICE) return h->fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
     return h->fp64 ? get_fields_t<double>(h, out, where, h->own) : get_fields_t<float>(h, out, where, h->own);
@@ -696,6 +989,7 @@ int pf_get_fields(pf_handle *h, pf_fields *out, int where)
 int pf_get_diagnostics(pf_handle *h, pf_diag *out)
 {
     if (!h || !out) return PF_EINVAL;
+    if (h->is_batch) return h->fail(PF_EINVAL, "batch handle: use the pf_batch_ call for one instance");
     Scalars sc;
     Diag dg;
     PF_TRY(h->cuda(cudaMemcpy(&sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost), "scalars"));
@@ -718,6 +1012,7 @@ int pf_get_diagnostics(pf_handle *h, pf_diag *out)
 int pf_free_energy(pf_handle *h, double *out)
 {
     if (!h || !out) return PF_EINVAL;
+    if (h->is_batch) return h->fail(PF_EINVAL, "batch handle: use the pf_batch_ call for one instance");
     if (!h->have_fields) return h->fail(PF_ESTATE, "no fields");
     const int g = grid_for(h, h->P.N);
     if (h->cfg.ndim == 2) {
@@ -860,8 +1155,19 @@ int fields_update_static_t(const Params &P, const pf_fields *in, const double *t
     F.muO = muO; F.MO = MO;
     F.trE = const_cast<double *>(trE ? trE : zero0);
     F.devE2 = const_cast<double *>(devE2 ? devE2 : zero1);
-    k_mu<double, D><<<g, 256, 0, s>>>(P, F);
-    k_update<double, D><<<g, 256, 0, s>>>(P, F, partials, counter, dg);
+    // the job travels in the launch parameters: nothing is copied to the
+    // device before the launches, so the call can be captured into a graph
+    JobSet<CellJob<double, D>> js;
+    memset(&js, 0, sizeof(js));
+    js.one.P = P;
+    js.one.F = F;
+    js.one.partials = partials;
+    js.one.counter = counter;
+    js.one.dg = dg;
+    js.one.block0 = 0;
+    js.one.nblocks = g;
+    k_mu<double, D><<<g, 256, 0, s>>>(js);
+    k_update<double, D><<<g, 256, 0, s>>>(js);
     k_out_phase<double><<<g, 256, 0, s>>>(N, theta_o, phig, out->phi_f, out->phi_w);
     if (cudaGetLastError() != cudaSuccess) return PF_ECUDA;
     int status = 0;

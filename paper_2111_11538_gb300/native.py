@@ -63,12 +63,14 @@ KERNEL_CLASSES = ["setup", "cg", "return", "mu", "update"]
 class pf_profile(ctypes.Structure):
     _fields_ = [("enabled", ctypes.c_int), ("launches", ctypes.c_longlong),
                 ("count", ctypes.c_longlong * PF_K_NCLASS), ("ms", ctypes.c_double * PF_K_NCLASS),
-                ("cg_iters", ctypes.c_longlong)]
+                ("cg_iters", ctypes.c_longlong), ("graph_steps", ctypes.c_longlong)]
 
 
 # exported symbols, in the order of include/pf.h
 SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_diagnostics",
            "pf_free_energy", "pf_dt_stable", "pf_profile_enable", "pf_profile_read",
+           "pf_batch_create", "pf_batch_size", "pf_batch_set_fields", "pf_batch_get_fields",
+           "pf_batch_get_diagnostics",
            "pf_device_bytes", "pf_last_error", "pf_destroy",
            "pf_fields_update_static", "pf_static_last_error"]
 PF_STATIC_MAX_CELLS = 65536
@@ -126,6 +128,16 @@ def lib():
         l.pf_profile_enable.restype = ctypes.c_int
         l.pf_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_profile)]
         l.pf_profile_read.restype = ctypes.c_int
+        l.pf_batch_create.argtypes = [ctypes.POINTER(pf_config), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+        l.pf_batch_create.restype = ctypes.c_int
+        l.pf_batch_size.argtypes = [ctypes.c_void_p]
+        l.pf_batch_size.restype = ctypes.c_int
+        l.pf_batch_set_fields.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(pf_fields), ctypes.c_int]
+        l.pf_batch_set_fields.restype = ctypes.c_int
+        l.pf_batch_get_fields.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(pf_fields), ctypes.c_int]
+        l.pf_batch_get_fields.restype = ctypes.c_int
+        l.pf_batch_get_diagnostics.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(pf_diag)]
+        l.pf_batch_get_diagnostics.restype = ctypes.c_int
         l.pf_device_bytes.argtypes = [ctypes.c_void_p]
         l.pf_device_bytes.restype = ctypes.c_longlong
         l.pf_last_error.argtypes = [ctypes.c_void_p]
@@ -184,6 +196,31 @@ def pf_profile_read(h):
     p = pf_profile()
     rc = lib().pf_profile_read(h, ctypes.byref(p))
     return rc, p
+
+
+def pf_batch_create(cfgs):
+    arr = (pf_config * len(cfgs))(*cfgs)
+    h = ctypes.c_void_p()
+    rc = lib().pf_batch_create(arr, len(cfgs), ctypes.byref(h))
+    return rc, h
+
+
+def pf_batch_size(h):
+    return lib().pf_batch_size(h)
+
+
+def pf_batch_set_fields(h, i, fields, where=PF_HOST):
+    return lib().pf_batch_set_fields(h, int(i), ctypes.byref(fields), where)
+
+
+def pf_batch_get_fields(h, i, fields, where=PF_HOST):
+    return lib().pf_batch_get_fields(h, int(i), ctypes.byref(fields), where)
+
+
+def pf_batch_get_diagnostics(h, i):
+    d = pf_diag()
+    rc = lib().pf_batch_get_diagnostics(h, int(i), ctypes.byref(d))
+    return rc, d
 
 
 def pf_device_bytes(h):

@@ -61,7 +61,10 @@ WORKLOADS = {
     "coreshell512": {
         "shape": (512, 512), "steps": 20000, "precision": "fp64|mixed",
         "geometry": ("core_shell", {"radius": 160.0, "shell": 32.0}),
-        "params": params(plasticity=1, sigma_Y=0.01, H_hard=0.001, cg_rtol=1e-10),
+        # both methods solve to 1e-8: with Jacobi preconditioning this grid's
+        # cond(A) times the FP32 unit roundoff is near 1, so the FP32 passes of
+        # the mixed method cannot resolve residuals much below 1e-9
+        "params": params(plasticity=1, sigma_Y=0.01, H_hard=0.001, cg_rtol=1e-8),
     },
     "porous2048": {
         "shape": (2048, 2048), "steps": 10000, "precision": "mixed",

@@ -1,5 +1,6 @@
 """C-ABI library: builds, loads without a GPU, exports every symbol of
 include/pf.h, and its host-only functions agree with the oracle."""
+import ctypes
 import os
 import re
 
@@ -65,3 +66,21 @@ def test_null_handle_calls(lib):
     assert lib.pf_step(None, 1, None) == native.PF_EINVAL
     assert lib.pf_set_fields(None, None, 0) == native.PF_EINVAL
     lib.pf_destroy(None)
+
+
+def test_batch_create_validates_before_touching_the_gpu(lib):
+    prm = workloads.params()
+    two = make_config((16, 16), prm)
+    three = make_config((8, 8, 8), prm)
+    rc, h = native.pf_batch_create([two, three])
+    assert rc == native.PF_EINVAL and not h.value
+    assert "share ndim" in native.pf_last_error(None)
+    mixed = make_config((16, 16), prm, precision="mixed")
+    rc, h = native.pf_batch_create([two, mixed])
+    assert rc == native.PF_EINVAL
+    bad = make_config((16, 16), prm)
+    bad.nx = 1
+    rc, h = native.pf_batch_create([two, bad])
+    assert rc in (native.PF_EINVAL, native.PF_ECUDA) and not h.value
+    assert lib.pf_batch_create(None, 0, ctypes.byref(ctypes.c_void_p())) == native.PF_EINVAL
+    assert native.pf_batch_size(None) == 0
