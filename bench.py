@@ -34,6 +34,10 @@ L2_BYTES = 129 * 1024 * 1024
 # set-up (eigenstress, Lame, warm start read; residual and diagonal written).
 CG_ITER_WORDS = {2: 16, 3: 24}
 CG_INIT_WORDS = {2: 10, 3: 15}
+# Algorithmic bytes per cell of the fused explicit update (k_fused): theta,
+# phi_g, x_O, x_H, x_H2O, tr eps_e, |dev eps_e|^2, mobility read, the 1-byte
+# supply mask read, theta, x_O, x_H, x_H2O written.
+FUSED_BYTES = {"mixed": 8 * 4 + 1 + 4 * 4, "fp64": 8 * 8 + 1 + 4 * 8}
 
 
 def _load_peaks():
@@ -212,6 +216,31 @@ def run_batch(precision, steps, warmup, count=64, seed=4, profile=True):
     return total_ms, prof, cells, iters
 
 
+def stencil_roofline(steps=20, warmup=3, n=2048):
+    """Achieved HBM bandwidth of the fused explicit update alone: the
+    2048 x 2048 porous microstructure (inputs 4x larger than L2) stepped with
+    the mechanics off, so that every launch is k_fused; per-launch CUDA
+    events on the launch stream."""
+    from paper_2111_11538_gb300 import Simulation, workloads
+    f = workloads.build_fields("porous2048", shape=(n, n))
+    sim = Simulation((n, n), workloads.params(mechanics=0), precision="mixed")
+    sim.set_fields(f)
+    sim.step(warmup)
+    sim.profile(True)
+    sim.step(steps)
+    prof = sim.profile_read()
+    sim.close()
+    launches = prof["count"]["update"]
+    ms = prof["ms"]["update"] / launches
+    hbm, kind = _load_peaks()
+    algo = FUSED_BYTES["mixed"] * n * n
+    gbs = algo / (ms / 1e3) / 1e9
+    return {"kernel": "k_fused (mu_O + explicit update)", "workload": "porous 2048x2048, mechanics off",
+            "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+            "traffic": None, "peak_kind": kind, "algorithmic_bytes_per_launch": algo,
+            "us_per_launch": ms * 1e3, "launches": launches}
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle on the host (single thread) over a bounded sample of the
     workload: the same core-shell geometry and parameters on a 128 x 128 grid
@@ -318,6 +347,9 @@ def main():
     import torch
     from paper_2111_11538_gb300 import native
     native.build_library()
+    if WORKLOAD == "stencil":
+        print(json.dumps(stencil_roofline(steps=args.steps, warmup=args.warmup)))
+        return
     if WORKLOAD == "batch64":
         meth = "mixed" if args.only == "both" else args.only
         for prof_on in (False, True):
@@ -380,6 +412,7 @@ def main():
         cg_bytes_per_launch = bytes_total / cg_launches
         achieved = cg_bytes_per_launch / (cg_ms / cg_launches / 1e3) / 1e9
 
+    stencil = stencil_roofline()
     e2e_dt, h2d, d2h = run_e2e("mixed", args.e2e_steps, fields)
     e2e_val = N * args.e2e_steps * ws / reduce_max(e2e_dt, ws)
 
@@ -409,6 +442,7 @@ def main():
                      "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "traffic": None,
                      "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
                      "algorithmic_bytes_per_launch": cg_bytes_per_launch},
+        "roofline_stencil": stencil,
         "e2e": {"value": e2e_val, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": prof["launches"],
         "clocks": clocks,

@@ -156,9 +156,8 @@ double pf_dt_stable(const pf_config *cfg);
 enum { PF_K_SETUP = 0,    /* moduli and eigenstress per cell              */
        PF_K_CG = 1,       /* persistent PCG solve (one launch per step)   */
        PF_K_RETURN = 2,   /* stress and J2 return per cell                */
-       PF_K_MU = 3,       /* oxygen chemical potential and mobility       */
-       PF_K_UPDATE = 4,   /* explicit Euler update of the fields          */
-       PF_K_NCLASS = 5 };
+       PF_K_UPDATE = 3,   /* fused mu_O, M_O and explicit Euler update    */
+       PF_K_NCLASS = 4 };
 
 typedef struct {
     int enabled;

@@ -27,9 +27,30 @@ struct FieldPtrs {
 // One grid (instance) of a launch.  A launch serves one or many instances:
 // its blocks are split into consecutive ranges, one per job, and every block
 // works on its job's grid only (block bid of nbk within the job).
+// Model constants in the storage type, converted once on the host: GB300's
+// FP64 pipe is narrow, and per-tile double->float conversions alone can
+// saturate it in a kernel that otherwise runs in FP32.
+template <typename T>
+struct CellConst {
+    T c, kappa, DOs, DOg, DHs, DHg, DWs, DWg;      // mu_O, M_O, D_H, D_H2O
+    T eps2, dt, Ks, Gs, Kg, w2, eig3, Lh, kf, xHbc; // update
+};
+
+template <typename T>
+inline CellConst<T> cell_const(const Params &P)
+{
+    CellConst<T> k;
+    k.c = T(P.c); k.kappa = T(P.kappa);
+    k.DOs = T(P.DOs); k.DOg = T(P.DOg); k.DHs = T(P.DHs); k.DHg = T(P.DHg); k.DWs = T(P.DWs); k.DWg = T(P.DWg);
+    k.eps2 = T(2 * P.eps); k.dt = T(P.dt); k.Ks = T(P.Ks); k.Gs = T(P.Gs); k.Kg = T(P.Kg);
+    k.w2 = T(2 * P.w); k.eig3 = T(P.eig0) * T(3); k.Lh = T(-0.5 * P.L); k.kf = T(P.kfor); k.xHbc = T(P.xHbc);
+    return k;
+}
+
 template <typename T, int D>
 struct CellJob {
     Params P;
+    CellConst<T> K;
     FieldPtrs<T, D> F;
     const Scalars *sc;       // mean strain for the return map
     double *partials;        // per-block sums of the update
@@ -346,6 +367,281 @@ __global__ void __launch_bounds__(256) k_update(const __grid_constant__ JobSet<C
         __shared__ double tot[6];
         last_block_sums<6>(partials, (int)nbk, tot);
         if (threadIdx.x == 0) {
+            dg->sumO = tot[0]; dg->sumH = tot[1]; dg->sumW = tot[2];
+            dg->removedW += tot[3];
+            dg->suppliedH += tot[4];
+            if (tot[5] > 0.0 && dg->status == 0) dg->status = 5;
+            *counter = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1: the fused explicit step -- oxygen chemical potential and mobility
+// (K1a) and the explicit Euler update (K1b) in one pass over the grid.
+//
+// Each block walks tiles of TX x TY (x TZ) cells.  Per tile it stages in
+// shared memory x_O with a halo of two cells and theta, phi_g, x_H, x_H2O
+// with a halo of one, evaluates mu_O and M_O on the tile plus one halo
+// cell, then updates the tile's cells from shared memory.  HBM sees each
+// field once per step (the halo re-reads hit L2); mu_O and M_O never leave
+// the SM.  Arithmetic and operand order per cell are those of k_mu and
+// k_update.
+// ---------------------------------------------------------------------------
+template <int D, int TX, int TY, int TZ>
+struct FusedTile {
+    static constexpr int EX = TX + 2, EY = TY + 2, EZ = D == 3 ? TZ + 2 : 1;   // halo 1
+    static constexpr int GX = TX + 4, GY = TY + 4, GZ = D == 3 ? TZ + 4 : 1;   // halo 2
+    static constexpr int E = EX * EY * EZ, G = GX * GY * GZ, C = TX * TY * (D == 3 ? TZ : 1);
+    // shared words: x_O (G); theta, phi_g, x_H, x_H2O, mu_O, M_O, D_H, D_H2O (E each)
+    static constexpr int WORDS = G + 8 * E;
+    static constexpr int NT = 256;                       // threads per block
+    static constexpr int CPT = (C + NT - 1) / NT;        // tile cells per thread
+};
+
+// Quotient for the mobility M_O = D_O / psi'': the FP32 method takes the
+// hardware approximate divide (2 ulp; its fields are held to 1e-4), FP64 the
+// IEEE divide.
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+
+// periodic coordinate; any a (grids smaller than a tile wrap several times)
+__device__ __forceinline__ int pwrap(int a, int n)
+{
+    if (a < 0) a += n;
+    if (a >= n) a -= n;
+    if ((unsigned)a >= (unsigned)n) a = wrapm(a, n);
+    return a;
+}
+
+template <typename T, int D, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && D == 2) ? 3 : 2) k_fused(const __grid_constant__ JobSet<CellJob<T, D>> js)
+{
+    using FT = FusedTile<D, TX, TY, TZ>;
+    static_assert(TX == 32, "the staging maps one warp lane to one tile column");
+    constexpr int EX = FT::EX, EY = FT::EY, GX = FT::GX, GY = FT::GY, NT = FT::NT, CPT = FT::CPT;
+    constexpr int TZe = D == 3 ? TZ : 1;
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
+    T *sXO = (T *)fsm_raw;
+    T *sTh = sXO + FT::G, *sPg = sTh + FT::E, *sXH = sPg + FT::E, *sXW = sXH + FT::E;
+    T *sMu = sXW + FT::E, *sM = sMu + FT::E, *sDH = sM + FT::E, *sDW = sDH + FT::E;
+
+    // the job lives in shared memory: its parameters are read where they
+    // are used instead of occupying registers for the whole kernel
+    __shared__ __align__(16) CellJob<T, D> sJ;
+    {
+        const CellJob<T, D> *J_ = my_job(js);
+        const int *src = (const int *)J_;
+        int *dst = (int *)&sJ;
+        for (int w = threadIdx.x; w < (int)(sizeof(CellJob<T, D>) / sizeof(int)); w += NT) dst[w] = src[w];
+    }
+    __syncthreads();
+    const Params &P = sJ.P;
+    const FieldPtrs<T, D> &F = sJ.F;
+    const long long bid = (long long)blockIdx.x - sJ.block0;
+    const long long nbk = sJ.nblocks;
+    const int nx = P.nx, ny = P.ny, nz = D == 3 ? P.nz : 1;
+    const int tiles_x = (nx + TX - 1) / TX, tiles_y = (ny + TY - 1) / TY, tiles_z = (nz + TZe - 1) / TZe;
+    const long long ntiles = (long long)tiles_x * tiles_y * tiles_z;
+    const unsigned sxy = (unsigned)nx * (unsigned)ny;   // grids hold < 2^31 cells
+
+    Acc<T> acc[5];           // sum x_O, x_H, x_H2O, removed water, supplied H
+    bool bad = false;
+
+    for (long long t = bid; t < ntiles; t += nbk) {
+        const int tx = (int)(t % tiles_x);
+        const long long tr = t / tiles_x;
+        const int ty = (int)(tr % tiles_y), tz = (int)(tr / tiles_y);
+        const int x0 = tx * TX, y0 = ty * TY, z0 = tz * TZe;
+
+        // per-cell inputs of this thread's cells, requested first so that
+        // they arrive while the tile is staged
+        int gc[CPT];
+        T pre_tE[CPT], pre_s2[CPT], pre_mob[CPT];
+        unsigned char pre_mask[CPT];
+#pragma unroll
+        for (int u = 0; u < CPT; u++) {
+            const int l = threadIdx.x + u * NT;
+            const int a = l % TX, r = l / TX, b = r % TY, c = r / TY;
+            const int i = x0 + a, j = y0 + b, k = z0 + c;
+            const bool in = l < FT::C && i < nx && j < ny && (D == 2 || k < nz);
+            gc[u] = in ? (int)((unsigned)i + (unsigned)nx * (unsigned)j + sxy * (unsigned)k) : -1;
+            if (in) {
+                pre_tE[u] = F.trE[gc[u]];
+                pre_s2[u] = F.devE2[gc[u]];
+                pre_mob[u] = F.mob[gc[u]];
+                pre_mask[u] = F.mask[gc[u]];
+            }
+        }
+        // Stage x_O (halo 2) and theta, phi_g, x_H, x_H2O (halo 1).  Warps take
+        // whole rows: lane L loads column L, lanes 0..(extra-1) the columns
+        // past 32; the periodic wrap is computed once per row and column, and
+        // every load of a thread is issued before its shared-memory stores.
+        {
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            constexpr int NW = NT / 32;
+            constexpr int RG = FT::GY * FT::GZ, RE = EY * FT::EZ;
+            constexpr int NRG = (RG + NW - 1) / NW, NRE = (RE + NW - 1) / NW;
+            const int ci2 = pwrap(x0 + lane - 2, nx), ci2x = pwrap(x0 + 32 + lane - 2, nx);
+            const int ci1 = pwrap(x0 + lane - 1, nx), ci1x = pwrap(x0 + 32 + lane - 1, nx);
+            const bool xg = lane < GX - 32, xe = lane < EX - 32;
+            T v[NRG], vx[NRG];
+#pragma unroll
+            for (int u = 0; u < NRG; u++) {
+                const int row = warp + u * NW;
+                if (row < RG) {
+                    const int b = row % GY, c = row / GY;
+                    const int gj = pwrap(y0 + b - 2, ny), gk = D == 3 ? pwrap(z0 + c - 2, nz) : 0;
+                    const T *src = F.xO + ((unsigned)nx * (unsigned)gj + sxy * (unsigned)gk);
+                    v[u] = src[ci2];
+                    if (xg) vx[u] = src[ci2x];
+                }
+            }
+            T e0[NRE], e1[NRE], e2[NRE], e3[NRE], x0v[NRE], x1v[NRE], x2v[NRE], x3v[NRE];
+#pragma unroll
+            for (int u = 0; u < NRE; u++) {
+                const int row = warp + u * NW;
+                if (row < RE) {
+                    const int b = row % EY, c = row / EY;
+                    const int gj = pwrap(y0 + b - 1, ny), gk = D == 3 ? pwrap(z0 + c - 1, nz) : 0;
+                    const unsigned rb = (unsigned)nx * (unsigned)gj + sxy * (unsigned)gk;
+                    e0[u] = F.theta[rb + ci1]; e1[u] = F.phig[rb + ci1]; e2[u] = F.xH[rb + ci1]; e3[u] = F.xW[rb + ci1];
+                    if (xe) {
+                        x0v[u] = F.theta[rb + ci1x]; x1v[u] = F.phig[rb + ci1x];
+                        x2v[u] = F.xH[rb + ci1x]; x3v[u] = F.xW[rb + ci1x];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < NRG; u++) {
+                const int row = warp + u * NW;
+                if (row < RG) {
+                    sXO[row * GX + lane] = v[u];
+                    if (xg) sXO[row * GX + 32 + lane] = vx[u];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < NRE; u++) {
+                const int row = warp + u * NW;
+                if (row < RE) {
+                    const int q = row * EX + lane;
+                    sTh[q] = e0[u]; sPg[q] = e1[u]; sXH[q] = e2[u]; sXW[q] = e3[u];
+                    if (xe) { sTh[q + 32] = x0v[u]; sPg[q + 32] = x1v[u]; sXH[q + 32] = x2v[u]; sXW[q + 32] = x3v[u]; }
+                }
+            }
+        }
+        __syncthreads();
+        // mu_O, M_O (Sec. 2.2, 3.2) and the species diffusivities (R4) on the
+        // tile plus one halo cell
+        {
+            const CellConst<T> &K = sJ.K;
+            const T cc = K.c, kap = K.kappa;
+            const T DOs = K.DOs, DOg = K.DOg, DHs = K.DHs, DHg = K.DHg, DWs = K.DWs, DWg = K.DWg;
+            constexpr int NI = (FT::E + NT - 1) / NT;
+#pragma unroll
+            for (int u = 0; u < NI; u++) {
+                const int l = threadIdx.x + u * NT;
+                if (l < FT::E) {
+                    const int a = l % EX, r = l / EX, b = r % EY, c = r / EY;
+                    const int q = (a + 1) + GX * ((b + 1) + GY * (D == 3 ? c + 1 : 0));
+                    const T x = sXO[q];
+                    T lap = sXO[q - 1] + sXO[q + 1] + sXO[q - GX] + sXO[q + GX] - T(2 * D) * x;
+                    if constexpr (D == 3) lap += sXO[q - GX * GY] + sXO[q + GX * GY];
+                    T Wf, Ww, Wg;
+                    phase_weights(sTh[l], sPg[l], Wf, Ww, Wg);
+                    const T m1 = Wf * f_fe1(x) + Ww * f_wu1(x) + Wg * f_ga1(x);
+                    const T m2 = Wf * f_fe2(x) + Ww * f_wu2(x) + Wg * f_ga2(x);
+                    sMu[l] = cc * m1 - kap * lap;
+                    const T DO = (T(1) - Wg) * DOs + Wg * DOg;
+                    const T den = cc * m2;
+                    sM[l] = den != T(0) ? fast_div(DO, den) : T(0);
+                    sDH[l] = (T(1) - Wg) * DHs + Wg * DHg;
+                    sDW[l] = (T(1) - Wg) * DWs + Wg * DWg;
+                }
+            }
+        }
+        __syncthreads();
+        // explicit Euler update of the tile's cells (Sec. 2.4, R2)
+        {
+            const CellConst<T> &K = sJ.K;
+            const T cc = K.c, eps2 = K.eps2, dt = K.dt;
+            const T Ks = K.Ks, Gs = K.Gs, Kg = K.Kg, w2 = K.w2, eig3 = K.eig3;
+            const T Lh = K.Lh, kf = K.kf, xHbc = K.xHbc;
+#pragma unroll
+            for (int u = 0; u < CPT; u++) {
+                if (gc[u] < 0) continue;
+                const int l = threadIdx.x + u * NT;
+                const int a = l % TX, r = l / TX, b = r % TY, c = r / TY;
+                const int e = (a + 1) + EX * ((b + 1) + EY * (D == 3 ? c + 1 : 0));
+                int nb[2 * D];
+                nb[0] = e - 1; nb[1] = e + 1; nb[2] = e - EX; nb[3] = e + EX;
+                if constexpr (D == 3) { nb[4] = e - EX * EY; nb[5] = e + EX * EY; }
+                const T th = sTh[e], pg = sPg[e];
+                const T xo = sXO[(a + 2) + GX * ((b + 2) + GY * (D == 3 ? c + 2 : 0))];
+                const T xh = sXH[e], xw = sXW[e];
+                const T mu0 = sMu[e], M0 = sM[e], DH0 = sDH[e], DW0 = sDW[e];
+                T lapt = T(0), dO = T(0), dH = T(0), dW = T(0);
+#pragma unroll
+                for (int q = 0; q < 2 * D; q++) {
+                    const int m = nb[q];
+                    lapt += sTh[m] - th;
+                    dO += T(0.5) * (M0 + sM[m]) * (sMu[m] - mu0);
+                    dH += T(0.5) * (DH0 + sDH[m]) * (sXH[m] - xh);
+                    dW += T(0.5) * (DW0 + sDW[m]) * (sXW[m] - xw);
+                }
+                const T tE = pre_tE[u], s2 = pre_s2[u];
+                const T hg0 = hfun(pg);
+                const T hpt = hder(th);
+                const T sol = T(1) - hg0;
+                const T Af = cc * f_fe(xo) + T(0.5) * Ks * tE * tE + Gs * s2;
+                const T Aw = cc * f_wu(xo) + T(0.5) * Ks * tE * tE + Gs * s2;
+                const T Kmix = sol * Ks + hg0 * Kg;
+                const T force = sol * hpt * (Af - Aw) + w2 * mder(th) - eig3 * sol * hpt * Kmix * tE;
+                const T rate = Lh * pre_mob[u] * (force - eps2 * lapt);
+                T rr = mfun(pg) * kf * xo * xh;
+                if (xw >= T(1)) rr = T(0);
+                const T nth = th + dt * rate;
+                const T nxo = xo + dt * (dO - rr);
+                T nxh = xh + dt * (dH - T(2) * rr);
+                T nxw = xw + dt * (dW + rr);
+                if (pre_mask[u]) {
+                    acc[3].add(nxw);
+                    acc[4].add(xHbc - nxh);
+                    nxh = xHbc;
+                    nxw = T(0);
+                }
+                const unsigned g = (unsigned)gc[u];
+                F.theta_o[g] = nth;
+                F.xO_o[g] = nxo;
+                F.xH_o[g] = nxh;
+                F.xW_o[g] = nxw;
+                acc[0].add(nxo); acc[1].add(nxh); acc[2].add(nxw);
+                // a non-finite value anywhere makes the sum non-finite
+                bad |= !isfinite(nth + nxo + nxh + nxw);
+            }
+        }
+        __syncthreads();
+    }
+    Acc<T> acc6[6];
+#pragma unroll
+    for (int q = 0; q < 5; q++) acc6[q] = acc[q];
+    acc6[5].add(T(bad ? 1 : 0));
+    double *partials = sJ.partials;
+    unsigned int *counter = sJ.counter;
+    block_reduce_store<6>(acc6, partials + (size_t)bid * PSTRIDE);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int tk = atomicAdd(counter, 1u);
+        last = (tk == (unsigned int)nbk - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        __shared__ double tot[6];
+        last_block_sums<6>(partials, (int)nbk, tot);
+        if (threadIdx.x == 0) {
+            Diag *dg = sJ.dg;
             dg->sumO = tot[0]; dg->sumH = tot[1]; dg->sumW = tot[2];
             dg->removedW += tot[3];
             dg->suppliedH += tot[4];

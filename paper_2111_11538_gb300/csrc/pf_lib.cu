@@ -186,8 +186,9 @@ struct pf_handle {
     bool is_batch = false;
     std::vector<pf_handle *> members;   // batch members (owned by the batch)
     void *d_cell_jobs[2] = {nullptr, nullptr};
+    void *d_fused_jobs[2] = {nullptr, nullptr};
     void *d_pcg_jobs = nullptr;
-    int cell_grid = 0, pcg_grid = 0, njobs = 0;
+    int cell_grid = 0, fused_grid = 0, pcg_grid = 0, njobs = 0;
     int cg_per_sm = 0;
     bool plan_ready = false;
     int plan_par = 0;                   // which table describes the current state
@@ -336,12 +337,42 @@ PCGArgs<T, D> pcg_args(pf_handle *m)
     return A;
 }
 
+// Tile of the fused update (k_fused): 2D 32 x 16 cells, 3D 32 x 4 x 4.
+template <int D> struct FusedShape;
+template <> struct FusedShape<2> { static constexpr int X = 32, Y = 16, Z = 1; };
+template <> struct FusedShape<3> { static constexpr int X = 32, Y = 4, Z = 4; };
+
+template <typename T, int D>
+size_t fused_smem()
+{
+    using S = FusedShape<D>;
+    return sizeof(T) * FusedTile<D, S::X, S::Y, S::Z>::WORDS;
+}
+
+template <typename T, int D>
+int prepare_fused(pf_handle *h)
+{
+    using S = FusedShape<D>;
+    cudaError_t e = cudaFuncSetAttribute(k_fused<T, D, S::X, S::Y, S::Z>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fused_smem<T, D>());
+    return h->cuda(e, "fused kernel shared memory");
+}
+
+template <typename T, int D>
+void launch_fused(int grid, const JobSet<CellJob<T, D>> &js, cudaStream_t s)
+{
+    using S = FusedShape<D>;
+    k_fused<T, D, S::X, S::Y, S::Z><<<grid, 256, fused_smem<T, D>(), s>>>(js);
+}
+
 // Build the job tables of every instance: cell kernels get ~N/256 blocks per
 // instance; the cooperative PCG launch splits the co-resident block capacity
 // over the instances in proportion to their tile counts (at least one each).
 template <typename T, int D>
 int build_plan(pf_handle *h)
 {
+    constexpr int FX = FusedShape<D>::X, FY = FusedShape<D>::Y, FZ = FusedShape<D>::Z;
+    PF_TRY((prepare_fused<T, D>(h)));
     std::vector<pf_handle *> I = instances(h);
     const int n = (int)I.size();
     std::vector<CellJob<T, D>> cj[2];
@@ -357,6 +388,7 @@ int build_plan(pf_handle *h)
             CellJob<T, D> &j = cj[k][i];
             memset(&j, 0, sizeof(j));
             j.P = m->P;
+            j.K = cell_const<T>(m->P);
             j.F = field_ptrs<T, D>(m);
             m->cur = saved;
             j.sc = m->sc;
@@ -370,13 +402,28 @@ int build_plan(pf_handle *h)
     }
     h->cell_grid = b0;
     h->njobs = n;
+    // the fused update walks tiles: up to 8 blocks per SM per instance
+    std::vector<CellJob<T, D>> fj[2] = {cj[0], cj[1]};
+    int f0 = 0;
+    for (int i = 0; i < n; i++) {
+        const Params &P = I[i]->P;
+        const long long nt = (long long)((P.nx + FX - 1) / FX) * ((P.ny + FY - 1) / FY) * (D == 3 ? (P.nz + FZ - 1) / FZ : 1);
+        const int nb = (int)std::min<long long>(nt, (long long)h->sms * 8);
+        for (int k = 0; k < 2; k++) { fj[k][i].block0 = f0; fj[k][i].nblocks = nb; }
+        f0 += nb;
+    }
+    h->fused_grid = f0;
     const size_t cbytes = sizeof(CellJob<T, D>) * (size_t)n;
     if (!h->d_cell_jobs[0]) {
-        PF_TRY(h->alloc(&h->d_cell_jobs[0], cbytes));
-        PF_TRY(h->alloc(&h->d_cell_jobs[1], cbytes));
+        for (int k = 0; k < 2; k++) {
+            PF_TRY(h->alloc(&h->d_cell_jobs[k], cbytes));
+            PF_TRY(h->alloc(&h->d_fused_jobs[k], cbytes));
+        }
     }
-    PF_TRY(h->cuda(cudaMemcpy(h->d_cell_jobs[0], cj[0].data(), cbytes, cudaMemcpyHostToDevice), "job table"));
-    PF_TRY(h->cuda(cudaMemcpy(h->d_cell_jobs[1], cj[1].data(), cbytes, cudaMemcpyHostToDevice), "job table"));
+    for (int k = 0; k < 2; k++) {
+        PF_TRY(h->cuda(cudaMemcpy(h->d_cell_jobs[k], cj[k].data(), cbytes, cudaMemcpyHostToDevice), "job table"));
+        PF_TRY(h->cuda(cudaMemcpy(h->d_fused_jobs[k], fj[k].data(), cbytes, cudaMemcpyHostToDevice), "job table"));
+    }
     if (h->cfg.mechanics) {
         constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
         // Jacobi-PCG iteration counts grow with the grid's linear size, so
@@ -443,11 +490,10 @@ int launch_step(pf_handle *h, cudaStream_t s, int k)
         k_return<T, D><<<h->cell_grid, 256, 0, s>>>(cj);
         h->mark_end(s);
     }
-    h->mark_begin(PF_K_MU, s);
-    k_mu<T, D><<<h->cell_grid, 256, 0, s>>>(cj);
-    h->mark_end(s);
+    JobSet<CellJob<T, D>> fj = cj;
+    fj.table = (const CellJob<T, D> *)h->d_fused_jobs[k];
     h->mark_begin(PF_K_UPDATE, s);
-    k_update<T, D><<<h->cell_grid, 256, 0, s>>>(cj);
+    launch_fused<T, D>(h->fused_grid, fj, s);
     h->mark_end(s);
     return h->cuda(cudaGetLastError(), "kernel launch");
 }
@@ -497,8 +543,8 @@ int run_steps(pf_handle *h, int nsteps, cudaStream_t s)
         if (graphable && h->graph[k]) {
             PF_TRY(h->cuda(cudaGraphLaunch(h->graph[k], s), "graph launch"));
             // one launch per kernel class of the step, whatever the batch size
-            const int cls[5] = {PF_K_MU, PF_K_UPDATE, PF_K_SETUP, PF_K_CG, PF_K_RETURN};
-            const int per = h->cfg.mechanics ? 5 : 2;
+            const int cls[4] = {PF_K_UPDATE, PF_K_SETUP, PF_K_CG, PF_K_RETURN};
+            const int per = h->cfg.mechanics ? 4 : 1;
             h->prof.launches += per;
             for (int c = 0; c < per; c++) h->prof.count[cls[c]] += 1;
             h->prof.graph_steps += 1;
@@ -1160,6 +1206,7 @@ int fields_update_static_t(const Params &P, const pf_fields *in, const double *t
     JobSet<CellJob<double, D>> js;
     memset(&js, 0, sizeof(js));
     js.one.P = P;
+    js.one.K = cell_const<double>(P);
     js.one.F = F;
     js.one.partials = partials;
     js.one.counter = counter;

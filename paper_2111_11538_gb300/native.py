@@ -12,7 +12,9 @@ import threading
 _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libpf.so")
-SOURCES = [os.path.join(_HERE, "csrc", n) for n in ("pf_lib.cu", "pf_kernels.cuh", "pf_device.cuh")]
+CSRC = os.path.join(_HERE, "csrc")
+UNITS = [os.path.join(CSRC, n) for n in ("pf_lib.cu", "unet.cu")]       # translation units
+BUILD_DIR = os.path.join(_HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -56,8 +58,8 @@ class pf_diag(ctypes.Structure):
                 ("steps", ctypes.c_longlong), ("dt", ctypes.c_double), ("status", ctypes.c_int)]
 
 
-PF_K_SETUP, PF_K_CG, PF_K_RETURN, PF_K_MU, PF_K_UPDATE, PF_K_NCLASS = range(6)
-KERNEL_CLASSES = ["setup", "cg", "return", "mu", "update"]
+PF_K_SETUP, PF_K_CG, PF_K_RETURN, PF_K_UPDATE, PF_K_NCLASS = range(5)
+KERNEL_CLASSES = ["setup", "cg", "return", "update"]
 
 
 class pf_profile(ctypes.Structure):
@@ -66,13 +68,21 @@ class pf_profile(ctypes.Structure):
                 ("cg_iters", ctypes.c_longlong), ("graph_steps", ctypes.c_longlong)]
 
 
-# exported symbols, in the order of include/pf.h
+class pf_unet_config(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("cin", ctypes.c_int), ("levels", ctypes.c_int),
+                ("channels", ctypes.c_int * 5)]
+
+
+# exported symbols, in the order of include/pf.h then include/pf_unet.h
 SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_diagnostics",
            "pf_free_energy", "pf_dt_stable", "pf_profile_enable", "pf_profile_read",
            "pf_batch_create", "pf_batch_size", "pf_batch_set_fields", "pf_batch_get_fields",
            "pf_batch_get_diagnostics",
            "pf_device_bytes", "pf_last_error", "pf_destroy",
-           "pf_fields_update_static", "pf_static_last_error"]
+           "pf_fields_update_static", "pf_static_last_error",
+           "pf_unet_create", "pf_unet_param_count", "pf_unet_set_params", "pf_unet_get_params",
+           "pf_unet_forward", "pf_unet_loss_grad", "pf_unet_adam_step", "pf_unet_last_error",
+           "pf_unet_destroy"]
 PF_STATIC_MAX_CELLS = 65536
 
 _lock = threading.Lock()
@@ -83,19 +93,37 @@ def _stale():
     if not os.path.exists(LIB_PATH):
         return True
     t = os.path.getmtime(LIB_PATH)
-    return any(os.path.getmtime(s) > t for s in SOURCES + [os.path.join(INCLUDE, "pf.h")])
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + \
+        [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+    return any(os.path.getmtime(s) > t for s in deps)
 
 
 def build_library(force=False, verbose=False):
-    """Compile csrc/ into libpf.so for sm_103a with nvcc (in-tree)."""
+    """Compile csrc/ into libpf.so for sm_103a with nvcc (in-tree): each
+    translation unit in parallel, then one link."""
     if not force and not _stale():
         return LIB_PATH
-    tmp = LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = ["nvcc", "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-I" + INCLUDE, "-o", tmp, SOURCES[0]]
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    tag = "%d" % os.getpid()
+    objs, procs = [], []
+    for u in UNITS:
+        o = os.path.join(BUILD_DIR, os.path.basename(u) + "." + tag + ".o")
+        cmd = ["nvcc", "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+               "-I" + INCLUDE, "-c", "-o", o, u]
+        if verbose:
+            print(" ".join(cmd))
+        procs.append((subprocess.Popen(cmd), cmd))
+        objs.append(o)
+    for p, cmd in procs:
+        if p.wait() != 0:
+            raise subprocess.CalledProcessError(p.returncode, cmd)
+    tmp = LIB_PATH + ".tmp" + tag
+    cmd = ["nvcc", *ARCH, "-shared", "-o", tmp, *objs]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 
@@ -147,6 +175,28 @@ def lib():
         l.pf_fields_update_static.argtypes = [ctypes.POINTER(pf_config), ctypes.POINTER(pf_fields), _DP, _DP,
                                               ctypes.POINTER(pf_fields), ctypes.c_void_p]
         l.pf_fields_update_static.restype = ctypes.c_int
+        _FP = ctypes.POINTER(ctypes.c_float)
+        l.pf_unet_create.argtypes = [ctypes.POINTER(pf_unet_config), ctypes.POINTER(ctypes.c_void_p)]
+        l.pf_unet_create.restype = ctypes.c_int
+        l.pf_unet_param_count.argtypes = [ctypes.c_void_p]
+        l.pf_unet_param_count.restype = ctypes.c_longlong
+        l.pf_unet_set_params.argtypes = [ctypes.c_void_p, _FP]
+        l.pf_unet_set_params.restype = ctypes.c_int
+        l.pf_unet_get_params.argtypes = [ctypes.c_void_p, _FP]
+        l.pf_unet_get_params.restype = ctypes.c_int
+        l.pf_unet_forward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        l.pf_unet_forward.restype = ctypes.c_int
+        l.pf_unet_loss_grad.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_double), _FP, ctypes.c_void_p]
+        l.pf_unet_loss_grad.restype = ctypes.c_int
+        l.pf_unet_adam_step.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+        l.pf_unet_adam_step.restype = ctypes.c_int
+        l.pf_unet_last_error.argtypes = [ctypes.c_void_p]
+        l.pf_unet_last_error.restype = ctypes.c_char_p
+        l.pf_unet_destroy.argtypes = [ctypes.c_void_p]
+        l.pf_unet_destroy.restype = None
         l.pf_static_last_error.argtypes = []
         l.pf_static_last_error.restype = ctypes.c_char_p
         _lib = l
@@ -245,3 +295,48 @@ def pf_fields_update_static(cfg, fin, trE, devE2, fout, stream=None):
 def pf_static_last_error():
     s = lib().pf_static_last_error()
     return s.decode() if s else ""
+
+
+def pf_unet_create(cfg):
+    h = ctypes.c_void_p()
+    rc = lib().pf_unet_create(ctypes.byref(cfg), ctypes.byref(h))
+    return rc, h
+
+
+def pf_unet_param_count(h):
+    return lib().pf_unet_param_count(h)
+
+
+def pf_unet_set_params(h, host):
+    return lib().pf_unet_set_params(h, host.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+
+
+def pf_unet_get_params(h, host):
+    return lib().pf_unet_get_params(h, host.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+
+
+def pf_unet_forward(h, inp, out, nb, nx, ny, nz, stream=None):
+    """inp / out: device addresses (int) of FP32 channels-last arrays."""
+    return lib().pf_unet_forward(h, ctypes.c_void_p(inp), ctypes.c_void_p(out), nb, nx, ny, nz,
+                                 ctypes.c_void_p(stream) if stream else None)
+
+
+def pf_unet_loss_grad(h, inp, target, nb, nx, ny, nz, grad_host=None, stream=None):
+    loss = ctypes.c_double()
+    g = grad_host.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if grad_host is not None else None
+    rc = lib().pf_unet_loss_grad(h, ctypes.c_void_p(inp), ctypes.c_void_p(target), nb, nx, ny, nz,
+                                 ctypes.byref(loss), g, ctypes.c_void_p(stream) if stream else None)
+    return rc, loss.value
+
+
+def pf_unet_adam_step(h, lr, stream=None):
+    return lib().pf_unet_adam_step(h, float(lr), ctypes.c_void_p(stream) if stream else None)
+
+
+def pf_unet_last_error(h=None):
+    s = lib().pf_unet_last_error(h)
+    return s.decode() if s else ""
+
+
+def pf_unet_destroy(h):
+    lib().pf_unet_destroy(h)

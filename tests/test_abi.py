@@ -9,7 +9,7 @@ import pytest
 
 from paper_2111_11538_gb300 import make_config, native, workloads
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "pf.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
 
 
 @pytest.fixture(scope="module")
@@ -19,7 +19,7 @@ def lib():
 
 
 def _declared():
-    txt = open(HEADER).read()
+    txt = "".join(open(os.path.join(INCLUDE, f)).read() for f in sorted(os.listdir(INCLUDE)) if f.endswith(".h"))
     return sorted(set(re.findall(r"\b(pf_[a-z_]+)\s*\(", txt)))
 
 
