@@ -116,12 +116,16 @@ def workload_params(precision):
     return dict(workloads.WORKLOADS[WORKLOAD]["params"])
 
 
-def run_gpu(precision, steps, warmup, fields, profile=True):
+def run_gpu(precision, steps, warmup, fields, profile=True, warm=None, net=None):
     import torch
     from paper_2111_11538_gb300 import Simulation
     shape = fields["phi_f"].shape
     prm = workload_params(precision)
+    if warm is not None:
+        prm["warm_start"] = warm
     sim = Simulation(shape, prm, precision=precision)
+    if net is not None:
+        sim.attach_unet(net)
     sim.set_fields(fields)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
@@ -180,13 +184,17 @@ def run_e2e(precision, steps, fields):
     return dt, h2d, d2h
 
 
-def run_batch(precision, steps, warmup, count=64, seed=4, profile=True):
+def run_batch(precision, steps, warmup, count=64, seed=4, profile=True, rank=0, world=1):
     """The batched workload: `count` independent 2D porous instances of uneven
     sizes (128^2 .. 1024^2), seeded pore fractions and prestresses, advanced
-    together by one launch per kernel class and step."""
+    together by one launch per kernel class and step.  With several ranks
+    each advances its cost-balanced share of the instances."""
     import torch
-    from paper_2111_11538_gb300 import Batch, inputs, workloads
+    from paper_2111_11538_gb300 import Batch, inputs, sharding, workloads
     desc = inputs.batch_instances(count, seed)
+    mine = sharding.shard([sharding.instance_cost((d["n"], d["n"])) for d in desc], world)[rank]
+    desc = [desc[i] for i in mine]
+    count = len(desc)
     base = workloads.WORKLOADS["batch64"]["params"]
     shapes = [(d["n"], d["n"]) for d in desc]
     prms = [dict(base, prestress=d["prestress"]) for d in desc]
@@ -214,6 +222,29 @@ def run_batch(precision, steps, warmup, count=64, seed=4, profile=True):
     iters = [b.diagnostics(i)["cg_iters_last"] for i in range(count)]
     b.close()
     return total_ms, prof, cells, iters
+
+
+WARMSTART_WEIGHTS = os.path.join(ROOT, "paper_2111_11538_gb300", "data", "warmstart2d.npz")
+
+
+def learned_warm_start(steps, warmup, fields, prev_ms, prev_iters):
+    """The chosen form with the learned warm start (the trained 2D network
+    shipped with the package) beside the previous-step guess, same steps."""
+    if not os.path.exists(WARMSTART_WEIGHTS):
+        return {"status": "no trained network at paper_2111_11538_gb300/data/warmstart2d.npz"}
+    import json as _json
+    from paper_2111_11538_gb300 import warmstart
+    net = warmstart.load(WARMSTART_WEIGHTS)
+    ms, prof, diag, _ = run_gpu("mixed", steps, warmup, fields, warm="learned", net=net)
+    info = {}
+    if os.path.exists(WARMSTART_WEIGHTS + ".json"):
+        info = _json.load(open(WARMSTART_WEIGHTS + ".json"))
+    N = fields["phi_f"].size
+    net.close()
+    return {"value": N * steps / (ms / 1e3), "unit": "cell-steps/s", "ms_per_step": ms / steps,
+            "cg_iters_per_step": prof["cg_iters"] / steps, "prev_guess_cg_iters_per_step": prev_iters / steps,
+            "prev_guess_ms_per_step": prev_ms / steps, "network_ms": prof["ms"]["warm"] / max(1, prof["count"]["warm"]),
+            "training": info}
 
 
 def stencil_roofline(steps=20, warmup=3, n=2048):
@@ -281,6 +312,16 @@ def reduce_max(x, ws):
     import torch.distributed as dist
     t = torch.tensor([x], dtype=torch.float64, device="cuda")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -353,9 +394,12 @@ def main():
     if WORKLOAD == "batch64":
         meth = "mixed" if args.only == "both" else args.only
         for prof_on in (False, True):
-            msb, profb, cells, iters = run_batch(meth, args.steps, args.warmup, profile=prof_on)
+            msb, profb, cells, iters = run_batch(meth, args.steps, args.warmup, profile=prof_on, rank=rank, world=ws)
+            msb = reduce_max(msb, ws)
+            cells = int(reduce_sum(cells, ws))
             if rank == 0:
                 print(json.dumps({"workload": WORKLOAD, "method": meth, "cells": cells, "steps": args.steps,
+                                  "n_gpus": ws, "scaling": "strong (the 64 instances split over ranks, no collective)",
                                   "timing": "per-kernel events" if prof_on else "graph replay",
                                   "ms_per_step": msb / args.steps, "value": cells * args.steps / (msb / 1e3),
                                   "kernel_ms": profb["ms"], "cg_iters": profb["cg_iters"],
@@ -413,6 +457,7 @@ def main():
         achieved = cg_bytes_per_launch / (cg_ms / cg_launches / 1e3) / 1e9
 
     stencil = stencil_roofline()
+    learned = learned_warm_start(args.steps, args.warmup, fields, ms, prof["cg_iters"])
     e2e_dt, h2d, d2h = run_e2e("mixed", args.e2e_steps, fields)
     e2e_val = N * args.e2e_steps * ws / reduce_max(e2e_dt, ws)
 
@@ -443,6 +488,7 @@ def main():
                      "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
                      "algorithmic_bytes_per_launch": cg_bytes_per_launch},
         "roofline_stencil": stencil,
+        "learned_warm_start": learned,
         "e2e": {"value": e2e_val, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": prof["launches"],
         "clocks": clocks,

@@ -50,7 +50,7 @@ enum {
 };
 
 enum { PF_FP64 = 0, PF_MIXED = 1 };            /* device storage / arithmetic */
-enum { PF_WS_ZERO = 0, PF_WS_PREV = 1 };       /* CG initial guess            */
+enum { PF_WS_ZERO = 0, PF_WS_PREV = 1, PF_WS_LEARNED = 2 };   /* CG initial guess */
 enum { PF_HOST = 0, PF_DEVICE = 1 };           /* where caller arrays live    */
 
 /* Nondimensional model parameters (energy in units of the solid Young's
@@ -78,7 +78,7 @@ typedef struct {
     int precision;      /* PF_FP64 or PF_MIXED                                          */
     int mechanics;      /* 0: skip the solve (coupling terms zero)                      */
     int plasticity;     /* 0: elastic, 1: J2 radial return                              */
-    int warm_start;     /* PF_WS_ZERO or PF_WS_PREV                                     */
+    int warm_start;     /* PF_WS_ZERO, PF_WS_PREV or PF_WS_LEARNED (see pf_attach_unet) */
     int cg_maxit;       /* CG iteration cap per step (> 0)                              */
     double cg_rtol;     /* stop when ||r||_2 <= cg_rtol ||b||_2                         */
     double dt;          /* time step; <= 0 selects 0.2 x the stable limit               */
@@ -157,7 +157,8 @@ enum { PF_K_SETUP = 0,    /* moduli and eigenstress per cell              */
        PF_K_CG = 1,       /* persistent PCG solve (one launch per step)   */
        PF_K_RETURN = 2,   /* stress and J2 return per cell                */
        PF_K_UPDATE = 3,   /* fused mu_O, M_O and explicit Euler update    */
-       PF_K_NCLASS = 4 };
+       PF_K_WARM = 4,     /* learned warm start: inference and guess      */
+       PF_K_NCLASS = 5 };
 
 typedef struct {
     int enabled;
@@ -200,6 +201,31 @@ int pf_batch_size(const pf_handle *h);
 int pf_batch_set_fields(pf_handle *h, int i, const pf_fields *f, int where);
 int pf_batch_get_fields(pf_handle *h, int i, pf_fields *out, int where);
 int pf_batch_get_diagnostics(pf_handle *h, int i, pf_diag *out);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (PF_WS_LEARNED).  Attach a network (include/pf_unet.h;
+ * 4 input channels, the grid's ndim outputs, each grid size divisible as
+ * that header states, else PF_EINVAL) to a handle (every instance of a
+ * batch).  Before each solve the network maps the cells' ferrite weight W_f,
+ * gas weight W_g, prestress / |eig0| and ferrite-weight rate
+ * (W_f - W_f,prev) / dt to y ~ (du/dt) / |eig0|, and the solve starts from
+ *   u_prev + |eig0| dt y
+ * (on the first step after pf_set_fields, which has no W_f,prev, from
+ * u_prev).  The PCG still runs to cg_rtol, so results do not depend on the
+ * network's accuracy.  Without a network PF_WS_LEARNED behaves as
+ * PF_WS_PREV.  The network must stay alive while attached; net = NULL
+ * detaches.  The inference runs inside pf_step (kernel class PF_K_WARM). */
+struct pf_unet;
+int pf_attach_unet(pf_handle *h, struct pf_unet *net);
+
+/* Self-test of the bounded device-side wait that every PCG grid barrier
+ * uses: one thread waits for a word that nothing updates, at most
+ * spin_limit polls (1 .. 2^24, ~100 ns apart), and the kernel then returns
+ * with PF_ETIMEOUT recorded -- the path a barrier takes when a peer block
+ * never arrives.  Returns PF_ETIMEOUT when the wait timed out as designed
+ * (the CUDA context stays usable), PF_EINVAL for a bad limit, PF_ECUDA /
+ * PF_ENOMEM on CUDA failures. */
+int pf_selftest_wait(long long spin_limit);
 
 /* Device memory held by the handle, bytes. */
 long long pf_device_bytes(const pf_handle *h);

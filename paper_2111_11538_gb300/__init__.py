@@ -16,7 +16,7 @@ import ctypes
 import numpy as np
 
 from . import native
-from .native import (PF_DEVICE, PF_FP64, PF_HOST, PF_MIXED, PF_OK, PF_WS_PREV, PF_WS_ZERO,
+from .native import (PF_DEVICE, PF_FP64, PF_HOST, PF_MIXED, PF_OK, PF_WS_LEARNED, PF_WS_PREV, PF_WS_ZERO,
                      STATUS_NAMES, pf_config, pf_diag, pf_fields, pf_params)
 
 __all__ = ["Simulation", "Batch", "PFError", "make_config", "native"]
@@ -47,7 +47,7 @@ def make_config(shape, prm, precision="fp64", mechanics=None, plasticity=None, w
     c.mechanics = int(prm.get("mechanics", 1) if mechanics is None else mechanics)
     c.plasticity = int(prm.get("plasticity", 0) if plasticity is None else plasticity)
     ws = prm.get("warm_start", 1) if warm_start is None else warm_start
-    c.warm_start = {"zero": PF_WS_ZERO, "prev": PF_WS_PREV}.get(ws, ws)
+    c.warm_start = {"zero": PF_WS_ZERO, "prev": PF_WS_PREV, "learned": PF_WS_LEARNED}.get(ws, ws)
     c.cg_rtol = float(prm.get("cg_rtol", 1e-10) if cg_rtol is None else cg_rtol)
     c.cg_maxit = int(prm.get("cg_maxit", 20000) if cg_maxit is None else cg_maxit)
     c.dt = float(prm.get("dt", 0.0) if dt is None else dt)
@@ -190,6 +190,13 @@ class Simulation:
                 "count": {k: p.count[i] for i, k in enumerate(native.KERNEL_CLASSES)},
                 "ms": {k: p.ms[i] for i, k in enumerate(native.KERNEL_CLASSES)}}
 
+    def attach_unet(self, net):
+        """Use a trained warm-start network (warmstart.WarmStartNet) for the
+        initial guess of every solve (config warm_start="learned"); None
+        detaches."""
+        self._check(native.pf_attach_unet(self.h, net.h if net is not None else None))
+        self._net = net            # keep it alive while attached
+
     def device_bytes(self):
         return native.pf_device_bytes(self.h)
 
@@ -270,6 +277,13 @@ class Batch:
         return {"launches": p.launches, "cg_iters": p.cg_iters, "graph_steps": p.graph_steps,
                 "count": {k: p.count[i] for i, k in enumerate(native.KERNEL_CLASSES)},
                 "ms": {k: p.ms[i] for i, k in enumerate(native.KERNEL_CLASSES)}}
+
+    def attach_unet(self, net):
+        """Use a trained warm-start network (warmstart.WarmStartNet) for the
+        initial guess of every solve (config warm_start="learned"); None
+        detaches."""
+        self._check(native.pf_attach_unet(self.h, net.h if net is not None else None))
+        self._net = net            # keep it alive while attached
 
     def device_bytes(self):
         return native.pf_device_bytes(self.h)

@@ -103,12 +103,7 @@ __device__ bool reduce_barrier(AccT (&acc)[K], double *partials, double *result,
             }
         }
     } else if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = gen;
-        long long spins = 0;
-        while (*vgen == s_gen) {
-            if (++spins > SPIN_LIMIT) { atomicExch(err, 6); s_ok = 0; break; }
-            __nanosleep(100);
-        }
+        if (!wait_generation(gen, s_gen, err, SPIN_LIMIT)) s_ok = 0;
         __threadfence();
     }
     __syncthreads();

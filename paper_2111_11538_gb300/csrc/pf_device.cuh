@@ -288,36 +288,24 @@ __device__ void last_block_sums(const double *partials, int nb, double *result)
     block_sum_store<K>(v, result);
 }
 
-// Grid barrier for a cooperative launch.  The wait is bounded: after
-// SPIN_LIMIT polls the block records PF_ETIMEOUT (6) in *err and the caller
-// returns.  Returns false on timeout.
+// Bounded wait of one thread for a generation word to move past g: at most
+// `limit` polls ~100 ns apart; on expiry PF_ETIMEOUT (6) goes to *err and
+// false is returned, so the kernel can leave with the context intact.  The
+// grid barrier of the PCG and its self-test (pf_selftest_wait) use it.
 constexpr long long SPIN_LIMIT = 1LL << 24;
 
-__device__ bool grid_barrier(unsigned int *count, unsigned int *gen, int *err)
+__device__ __forceinline__ bool wait_generation(const unsigned int *gen, unsigned int g, int *err, long long limit)
 {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        volatile unsigned int *vgen = gen;
-        unsigned int g = *vgen;
-        __threadfence();
-        unsigned int arrived = atomicAdd(count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == g) {
-                if (++spins > SPIN_LIMIT) { atomicExch(err, 6); ok = 0; break; }
-                __nanosleep(64);
-            }
+    const volatile unsigned int *vgen = gen;
+    long long spins = 0;
+    while (*vgen == g) {
+        if (++spins > limit) {
+            atomicExch(err, 6);
+            return false;
         }
-        __threadfence();
+        __nanosleep(100);
     }
-    __syncthreads();
-    return ok != 0;
+    return true;
 }
 
 // ---------------------------------------------------------------------------

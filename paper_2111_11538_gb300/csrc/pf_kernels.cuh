@@ -652,6 +652,64 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && D == 2) ? 3 : 2) k_fus
 }
 
 // ---------------------------------------------------------------------------
+// Learned warm start: network inputs and the guess update.  The network
+// predicts the rate of the displacement, du/dt / |eig0|, from the phase
+// weights, the prestress and the rate of the ferrite weight, dW_f/dt.
+// ---------------------------------------------------------------------------
+// in[4c..4c+3] = W_f, W_g, p/|eig0|, (W_f - W_f,prev) / dt (0 on the first
+// step after pf_set_fields, mode != 0); W_f,prev = W_f.
+template <typename T>
+__global__ void k_net_input(long long N, const T *theta, const T *phig, float pscaled, float inv_dt,
+                            const int *mode, float *wf_prev, float *in)
+{
+    const int md = *mode;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        T Wf, Ww, Wg;
+        phase_weights(theta[c], phig[c], Wf, Ww, Wg);
+        const float wf = (float)Wf;
+        in[4 * c] = wf;
+        in[4 * c + 1] = (float)Wg;
+        in[4 * c + 2] = pscaled;
+        in[4 * c + 3] = md == 0 ? (wf - wf_prev[c]) * inv_dt : 0.f;
+        wf_prev[c] = wf;
+    }
+}
+
+// u += s y (s = |eig0| dt) unless this is the first step after
+// pf_set_fields (mode != 0).  In the mixed method the FP64 copy x64 is the
+// solve's initial guess and u follows it.
+template <typename T, int D>
+__global__ void k_net_guess(long long N, const float *y, const int *mode, double s,
+                            T *u0, T *u1, T *u2, double *x0, double *x1, double *x2)
+{
+    if (*mode != 0) return;
+    T *u[3] = {u0, u1, u2};
+    double *x[3] = {x0, x1, x2};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < D; d++) {
+            const double delta = s * (double)y[D * c + d];
+            if (x[d]) {
+                const double v = x[d][c] + delta;
+                x[d][c] = v;
+                u[d][c] = (T)v;
+            } else {
+                u[d][c] = (T)((double)u[d][c] + delta);
+            }
+        }
+    }
+}
+
+__global__ void k_net_mode_clear(int *mode) { *mode = 0; }
+
+// Self-test of the bounded wait: one thread waits on a generation word that
+// nothing advances.
+__global__ void k_wait_selftest(const unsigned int *gen, int *err, long long limit)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) wait_generation(gen, 0u, err, limit);
+}
+
+// ---------------------------------------------------------------------------
 // Conversions between the caller's FP64 cell-major arrays and device storage
 // ---------------------------------------------------------------------------
 template <typename T>

@@ -12,6 +12,8 @@
 #include <mutex>
 
 #include "pf.h"
+#include "pf_unet.h"
+#include "unet_net.h"
 #include "pf_cg.cuh"
 
 using namespace pfdev;
@@ -196,6 +198,14 @@ struct pf_handle {
     bool graph_failed = false;
     bool use_graph = true;
 
+    // learned warm start (pf_attach_unet)
+    pf_unet *net = nullptr;
+    UWork *net_work = nullptr;
+    float *net_in = nullptr;            // N x 4 network inputs
+    float *net_prev = nullptr;          // N previous ferrite weight
+    int *net_mode = nullptr;            // 1: first step after pf_set_fields (no guess), 0: guess
+    std::vector<void *> net_allocs;
+
     // profiling: event pairs around each launch while enabled
     bool prof_on = false;
     pf_profile prof;
@@ -333,7 +343,7 @@ PCGArgs<T, D> pcg_args(pf_handle *m)
     A.bar_count = m->sync; A.bar_gen = m->sync + SYNC_GEN;
     A.sc = m->sc; A.dg = m->dg;
     A.rtol = m->cfg.cg_rtol; A.maxit = m->cfg.cg_maxit;
-    A.warm = m->cfg.warm_start == PF_WS_PREV ? 1 : 0;
+    A.warm = m->cfg.warm_start != PF_WS_ZERO ? 1 : 0;
     return A;
 }
 
@@ -465,6 +475,32 @@ int build_plan(pf_handle *h)
     return PF_OK;
 }
 
+// Learned warm start of one instance: network inputs from the current state
+// (W_f, W_g, prestress / |eig0|, dW_f/dt since the previous step), one
+// inference y ~ du/dt / |eig0|, then the guess u += |eig0| dt y (not on the
+// first step after pf_set_fields, which has no previous W_f).  The current
+// state is theta[cur]: cur advances with the job-table parity, so a graph
+// captured for one parity always replays with that parity's buffer.
+template <typename T, int D>
+int learned_guess(pf_handle *m, cudaStream_t s)
+{
+    const long long N = m->P.N;
+    const int c = m->cur;
+    const int g = grid_for(m, N);
+    const double ae = std::fabs(m->P.eig0) > 0.0 ? std::fabs(m->P.eig0) : 1.0;
+    k_net_input<T><<<g, 256, 0, s>>>(N, (const T *)m->theta[c], (const T *)m->phig, (float)(m->cfg.p.prestress / ae),
+                                     (float)(1.0 / m->P.dt), m->net_mode, m->net_prev, m->net_in);
+    const float *y = nullptr;
+    const int rc = unet_forward_work(m->net, m->net_work, m->net_in, &y, s);
+    if (rc != PF_OK) return m->fail(rc, "warm-start network: %s", unet_error(m->net));
+    T *u[3] = {(T *)m->u[0], (T *)m->u[1], (T *)m->u[2]};
+    k_net_guess<T, D><<<g, 256, 0, s>>>(N, y, m->net_mode, ae * m->P.dt, u[0], u[1], u[2],
+                                        m->refine ? m->x64[0] : nullptr, m->refine ? m->x64[1] : nullptr,
+                                        m->refine ? m->x64[2] : nullptr);
+    k_net_mode_clear<<<1, 1, 0, s>>>(m->net_mode);
+    return PF_OK;
+}
+
 // Queue one step of every instance; k selects the job tables (0: current
 // state, 1: one step later).
 template <typename T, int D>
@@ -479,6 +515,14 @@ int launch_step(pf_handle *h, cudaStream_t s, int k)
         h->mark_begin(PF_K_SETUP, s);
         k_setup<T, D><<<h->cell_grid, 256, 0, s>>>(cj);
         h->mark_end(s);
+        if (h->cfg.warm_start == PF_WS_LEARNED) {
+            h->mark_begin(PF_K_WARM, s);
+            for (pf_handle *m : instances(h)) {
+                if (!m->net) continue;
+                PF_TRY((learned_guess<T, D>(m, s)));
+            }
+            h->mark_end(s);
+        }
         const PCGArgs<T, D> *pj = (const PCGArgs<T, D> *)h->d_pcg_jobs;
         int nj = n;
         void *args[] = {(void *)&pj, (void *)&nj};
@@ -545,6 +589,7 @@ int run_steps(pf_handle *h, int nsteps, cudaStream_t s)
             // one launch per kernel class of the step, whatever the batch size
             const int cls[4] = {PF_K_UPDATE, PF_K_SETUP, PF_K_CG, PF_K_RETURN};
             const int per = h->cfg.mechanics ? 4 : 1;
+            if (h->cfg.mechanics && h->cfg.warm_start == PF_WS_LEARNED) h->prof.count[PF_K_WARM] += 1;
             h->prof.launches += per;
             for (int c = 0; c < per; c++) h->prof.count[cls[c]] += 1;
             h->prof.graph_steps += 1;
@@ -651,6 +696,10 @@ int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
     h->have_fields = true;
     h->sigma_valid = false;
     h->plan_ready = false;          // the field buffers' roles changed
+    if (h->net_mode) {
+        static const int first = 1;
+        PF_TRY(h->cuda(cudaMemcpyAsync(h->net_mode, &first, sizeof(int), cudaMemcpyHostToDevice, s), "net mode"));
+    }
     return h->cuda(cudaGetLastError(), "set_fields kernels");
 #undef PF_SRC
 }
@@ -779,6 +828,10 @@ void free_all(pf_handle *h)
         delete m;
     }
     h->members.clear();
+    unet_work_destroy(h->net_work);
+    h->net_work = nullptr;
+    for (void *p : h->net_allocs) cudaFree(p);
+    h->net_allocs.clear();
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
     for (void *p : h->allocs) cudaFree(p);
@@ -796,7 +849,10 @@ int create_one(const pf_config *cfg, pf_handle **out, std::string &err)
     if (c.ndim != 2 && c.ndim != 3) { err = "ndim must be 2 or 3"; return PF_EINVAL; }
     if (c.nx < 2 || c.ny < 2 || (c.ndim == 3 && c.nz < 2)) { err = "grid sizes must be >= 2"; return PF_EINVAL; }
     if (c.precision != PF_FP64 && c.precision != PF_MIXED) { err = "precision must be PF_FP64 or PF_MIXED"; return PF_EINVAL; }
-    if (c.warm_start != PF_WS_ZERO && c.warm_start != PF_WS_PREV) { err = "warm_start must be PF_WS_ZERO or PF_WS_PREV"; return PF_EINVAL; }
+    if (c.warm_start != PF_WS_ZERO && c.warm_start != PF_WS_PREV && c.warm_start != PF_WS_LEARNED) {
+        err = "warm_start must be PF_WS_ZERO, PF_WS_PREV or PF_WS_LEARNED";
+        return PF_EINVAL;
+    }
     if (c.mechanics && (c.cg_maxit <= 0 || !(c.cg_rtol > 0.0))) { err = "cg_maxit must be > 0 and cg_rtol > 0"; return PF_EINVAL; }
     if (!(c.p.nu > -1.0 && c.p.nu < 0.5) || !(c.p.E_s > 0.0) || !(c.p.E_g_ratio > 0.0)) { err = "elastic constants out of range"; return PF_EINVAL; }
     const long long N = (long long)c.nx * c.ny * (c.ndim == 3 ? c.nz : 1);
@@ -1094,6 +1150,70 @@ int pf_profile_read(pf_handle *h, pf_profile *out)
     if (!h || !out) return PF_EINVAL;
     *out = h->prof;
     return PF_OK;
+}
+
+int pf_attach_unet(pf_handle *h, pf_unet *net)
+{
+    if (!h) return PF_EINVAL;
+    for (pf_handle *m : instances(h)) {
+        cudaStreamSynchronize(m->own);
+        unet_work_destroy(m->net_work);
+        m->net_work = nullptr;
+        for (void *p : m->net_allocs) cudaFree(p);
+        m->net_allocs.clear();
+        m->net = nullptr;
+        m->net_in = m->net_prev = nullptr;
+        m->net_mode = nullptr;
+    }
+    h->plan_ready = false;
+    if (!net) return PF_OK;
+    if (unet_ndim(net) != h->cfg.ndim) return h->fail(PF_EINVAL, "network is %dD, grid is %dD", unet_ndim(net), h->cfg.ndim);
+    if (unet_cin(net) != 4) return h->fail(PF_EINVAL, "warm-start network needs 4 input channels");
+    for (pf_handle *m : instances(h)) {
+        const int nz = m->cfg.ndim == 3 ? m->cfg.nz : 1;
+        m->net_work = unet_work_create(net, 1, m->cfg.nx, m->cfg.ny, nz);
+        if (!m->net_work) {
+            std::string why = unet_error(net);
+            pf_attach_unet(h, nullptr);
+            return h->fail(PF_EINVAL, "grid %dx%dx%d does not suit the network: %s", m->cfg.nx, m->cfg.ny, nz, why.c_str());
+        }
+        const size_t N = (size_t)m->P.N;
+        void *a = nullptr, *b = nullptr, *c = nullptr;
+        if (cudaMalloc(&a, sizeof(float) * N * 4) != cudaSuccess || cudaMalloc(&b, sizeof(float) * N) != cudaSuccess
+            || cudaMalloc(&c, sizeof(int)) != cudaSuccess) {
+            if (a) cudaFree(a);
+            if (b) cudaFree(b);
+            pf_attach_unet(h, nullptr);
+            return h->fail(PF_ENOMEM, "warm-start buffers");
+        }
+        m->net_allocs = {a, b, c};
+        m->net_in = (float *)a;
+        m->net_prev = (float *)b;
+        m->net_mode = (int *)c;
+        cudaMemset(m->net_prev, 0, sizeof(float) * N);
+        const int first = 1;
+        cudaMemcpy(m->net_mode, &first, sizeof(int), cudaMemcpyHostToDevice);
+        m->net = net;
+    }
+    return h->cuda(cudaDeviceSynchronize(), "attach");
+}
+
+int pf_selftest_wait(long long spin_limit)
+{
+    if (spin_limit < 1 || spin_limit > SPIN_LIMIT) return PF_EINVAL;
+    void *buf = nullptr;
+    if (cudaMalloc(&buf, 2 * sizeof(int)) != cudaSuccess) return PF_ENOMEM;
+    int rc = PF_OK;
+    int err = 0;
+    if (cudaMemset(buf, 0, 2 * sizeof(int)) != cudaSuccess) rc = PF_ECUDA;
+    if (rc == PF_OK) {
+        k_wait_selftest<<<1, 32>>>((const unsigned int *)buf, (int *)buf + 1, spin_limit);
+        if (cudaDeviceSynchronize() != cudaSuccess) rc = PF_ECUDA;
+    }
+    if (rc == PF_OK && cudaMemcpy(&err, (int *)buf + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = PF_ECUDA;
+    cudaFree(buf);
+    if (rc != PF_OK) return rc;
+    return err == 6 ? PF_ETIMEOUT : PF_ECUDA;
 }
 
 long long pf_device_bytes(const pf_handle *h) { return h ? h->bytes : 0; }

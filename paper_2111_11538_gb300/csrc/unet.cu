@@ -252,6 +252,27 @@ struct ConvLayer {
     float *gk = nullptr;            // weight gradient in the kernel layout
 };
 
+// Activations (and, for training, gradients) of one (nb, nx, ny, nz).  The
+// network's own calls use the network's workspace; a field handle that
+// replays the inference inside a CUDA graph owns a separate one, so that no
+// call on the network can move buffers the graph points at.
+struct UWork {
+    int wnb = -1, wnx = -1, wny = -1, wnz = -1;
+    bool grads = false;
+    std::vector<void *> work;
+    __nv_bfloat16 *x0 = nullptr;
+    std::vector<__nv_bfloat16 *> enc1, enc2, pool, dec1, dec2;     // per level
+    std::vector<float *> g_a, g_d, g_p;                            // FP32 gradients per level
+    __nv_bfloat16 *gz = nullptr, *gin = nullptr;                   // scratch (largest level)
+    float *y = nullptr, *gy = nullptr, *gd0 = nullptr;
+    void release()
+    {
+        for (void *p : work) cudaFree(p);
+        work.clear();
+        wnb = wnx = wny = wnz = -1;
+    }
+};
+
 struct pf_unet {
     pf_unet_config cfg;
     std::string err;
@@ -261,14 +282,7 @@ struct pf_unet {
     long long adam_t = 0;
     double *part = nullptr;         // loss partials
     std::vector<void *> allocs;
-    // activation workspace for one (nb, nx, ny, nz)
-    int wnb = -1, wnx = -1, wny = -1, wnz = -1;
-    std::vector<void *> work;
-    __nv_bfloat16 *x0 = nullptr;
-    std::vector<__nv_bfloat16 *> enc1, enc2, pool, dec1, dec2;     // per level
-    std::vector<float *> g_a, g_d, g_p;                            // FP32 gradients per level
-    __nv_bfloat16 *gz = nullptr, *gin = nullptr;                   // scratch (largest level)
-    float *y = nullptr, *gy = nullptr, *gd0 = nullptr;
+    UWork train;                    // workspace of pf_unet_forward / pf_unet_loss_grad
 
     int fail(int code, const char *fmt, ...)
     {
@@ -366,26 +380,26 @@ int launch_wgrad(int cout, const WGradArgs &a, int cin, cudaStream_t s)
     return PF_OK;
 }
 
-long long level_cells(const pf_unet *n, int l)
+long long level_cells(const pf_unet *n, const UWork *w, int l)
 {
-    long long c = (long long)(n->wnx >> l) * (n->wny >> l);
-    if (n->cfg.ndim == 3) c *= (n->wnz >> l);
+    long long c = (long long)(w->wnx >> l) * (w->wny >> l);
+    if (n->cfg.ndim == 3) c *= (w->wnz >> l);
     return c;
 }
 
-Dims level_dims(const pf_unet *n, int l)
+Dims level_dims(const pf_unet *n, const UWork *w, int l)
 {
     Dims d;
-    d.nx = n->wnx >> l;
-    d.ny = n->wny >> l;
-    d.nz = n->cfg.ndim == 3 ? n->wnz >> l : 1;
-    d.nb = n->wnb;
+    d.nx = w->wnx >> l;
+    d.ny = w->wny >> l;
+    d.nz = n->cfg.ndim == 3 ? w->wnz >> l : 1;
+    d.nb = w->wnb;
     return d;
 }
 
-long long level_tiles(const pf_unet *n, int l)
+long long level_tiles(const pf_unet *n, const UWork *w, int l)
 {
-    const Dims d = level_dims(n, l);
+    const Dims d = level_dims(n, w, l);
     if (n->cfg.ndim == 2) return (long long)(d.nx / 16) * (d.ny / 8) * d.nb;
     return (long long)(d.nx / 16) * (d.ny / 4) * (d.nz / 2) * d.nb;
 }
@@ -403,34 +417,36 @@ int check_dims(pf_unet *n, int nb, int nx, int ny, int nz)
     return PF_OK;
 }
 
-int ensure_work(pf_unet *n, int nb, int nx, int ny, int nz)
+int ensure_work(pf_unet *n, UWork *w, int nb, int nx, int ny, int nz, bool grads)
 {
     if (n->cfg.ndim == 2) nz = 1;
-    if (n->wnb == nb && n->wnx == nx && n->wny == ny && n->wnz == nz) return PF_OK;
-    for (void *p : n->work) cudaFree(p);
-    n->work.clear();
-    n->wnb = nb; n->wnx = nx; n->wny = ny; n->wnz = nz;
+    if (w->wnb == nb && w->wnx == nx && w->wny == ny && w->wnz == nz && (w->grads || !grads)) return PF_OK;
+    w->release();
+    w->grads = grads;
+    w->wnb = nb; w->wnx = nx; w->wny = ny; w->wnz = nz;
     const int L = n->cfg.levels;
     const int D = n->cfg.ndim;
-    n->enc1.assign(L, nullptr); n->enc2.assign(L, nullptr); n->pool.assign(L, nullptr);
-    n->dec1.assign(L, nullptr); n->dec2.assign(L, nullptr);
-    n->g_a.assign(L, nullptr); n->g_d.assign(L, nullptr); n->g_p.assign(L, nullptr);
-    const long long c0 = level_cells(n, 0) * nb;
-    UN_TRY(n->alloc(&n->x0, sizeof(__nv_bfloat16) * c0 * 16, n->work));
+    w->enc1.assign(L, nullptr); w->enc2.assign(L, nullptr); w->pool.assign(L, nullptr);
+    w->dec1.assign(L, nullptr); w->dec2.assign(L, nullptr);
+    w->g_a.assign(L, nullptr); w->g_d.assign(L, nullptr); w->g_p.assign(L, nullptr);
+    const long long c0 = level_cells(n, w, 0) * nb;
+    UN_TRY(n->alloc(&w->x0, sizeof(__nv_bfloat16) * c0 * 16, w->work));
     size_t big = 0;
     for (int l = 0; l < L; l++) {
-        const long long c = level_cells(n, l) * nb;
+        const long long c = level_cells(n, w, l) * nb;
         const int C = n->cfg.channels[l];
-        UN_TRY(n->alloc(&n->enc1[l], sizeof(__nv_bfloat16) * c * C, n->work));
-        UN_TRY(n->alloc(&n->enc2[l], sizeof(__nv_bfloat16) * c * C, n->work));
-        if (l > 0) UN_TRY(n->alloc(&n->pool[l], sizeof(__nv_bfloat16) * c * n->cfg.channels[l - 1], n->work));
+        UN_TRY(n->alloc(&w->enc1[l], sizeof(__nv_bfloat16) * c * C, w->work));
+        UN_TRY(n->alloc(&w->enc2[l], sizeof(__nv_bfloat16) * c * C, w->work));
+        if (l > 0) UN_TRY(n->alloc(&w->pool[l], sizeof(__nv_bfloat16) * c * n->cfg.channels[l - 1], w->work));
         if (l < L - 1) {
-            UN_TRY(n->alloc(&n->dec1[l], sizeof(__nv_bfloat16) * c * C, n->work));
-            UN_TRY(n->alloc(&n->dec2[l], sizeof(__nv_bfloat16) * c * C, n->work));
+            UN_TRY(n->alloc(&w->dec1[l], sizeof(__nv_bfloat16) * c * C, w->work));
+            UN_TRY(n->alloc(&w->dec2[l], sizeof(__nv_bfloat16) * c * C, w->work));
         }
-        UN_TRY(n->alloc(&n->g_a[l], sizeof(float) * c * C, n->work));
-        UN_TRY(n->alloc(&n->g_d[l], sizeof(float) * c * C, n->work));
-        if (l > 0) UN_TRY(n->alloc(&n->g_p[l], sizeof(float) * c * n->cfg.channels[l - 1], n->work));
+        if (grads) {
+            UN_TRY(n->alloc(&w->g_a[l], sizeof(float) * c * C, w->work));
+            UN_TRY(n->alloc(&w->g_d[l], sizeof(float) * c * C, w->work));
+            if (l > 0) UN_TRY(n->alloc(&w->g_p[l], sizeof(float) * c * n->cfg.channels[l - 1], w->work));
+        }
         // widest per-cell tensor of this level: a decoder input, a pooled
         // input or the padded network input
         int cin_max = n->cfg.channels[l] + (l + 1 < L ? n->cfg.channels[l + 1] : 0);
@@ -439,11 +455,13 @@ int ensure_work(pf_unet *n, int nb, int nx, int ny, int nz)
         const size_t need = (size_t)c * cin_max;
         if (need > big) big = need;
     }
-    UN_TRY(n->alloc(&n->gz, sizeof(__nv_bfloat16) * big, n->work));
-    UN_TRY(n->alloc(&n->gin, sizeof(__nv_bfloat16) * big, n->work));
-    UN_TRY(n->alloc(&n->y, sizeof(float) * c0 * D, n->work));
-    UN_TRY(n->alloc(&n->gy, sizeof(float) * c0 * D, n->work));
-    UN_TRY(n->alloc(&n->gd0, sizeof(float) * c0 * n->cfg.channels[0], n->work));
+    UN_TRY(n->alloc(&w->y, sizeof(float) * c0 * D, w->work));
+    if (grads) {
+        UN_TRY(n->alloc(&w->gz, sizeof(__nv_bfloat16) * big, w->work));
+        UN_TRY(n->alloc(&w->gin, sizeof(__nv_bfloat16) * big, w->work));
+        UN_TRY(n->alloc(&w->gy, sizeof(float) * c0 * D, w->work));
+        UN_TRY(n->alloc(&w->gd0, sizeof(float) * c0 * n->cfg.channels[0], w->work));
+    }
     return PF_OK;
 }
 
@@ -466,122 +484,122 @@ ConvArgs conv_args(const __nv_bfloat16 *in0, int C0, const __nv_bfloat16 *in1, i
 }
 
 template <int D>
-int forward_t(pf_unet *n, const float *in, cudaStream_t s)
+int forward_t(pf_unet *n, UWork *w, const float *in, cudaStream_t s)
 {
     const int L = n->cfg.levels;
-    const long long c0 = level_cells(n, 0) * n->wnb;
-    k_pack_input<<<blocks_for(c0 * 16), 256, 0, s>>>(c0, n->cfg.cin, in, n->x0);
+    const long long c0 = level_cells(n, w, 0) * w->wnb;
+    k_pack_input<<<blocks_for(c0 * 16), 256, 0, s>>>(c0, n->cfg.cin, in, w->x0);
     int k = 0;
     for (int l = 0; l < L; l++) {
-        const Dims d = level_dims(n, l);
-        const long long tiles = level_tiles(n, l);
-        const __nv_bfloat16 *src = l == 0 ? n->x0 : n->pool[l];
+        const Dims d = level_dims(n, w, l);
+        const long long tiles = level_tiles(n, w, l);
+        const __nv_bfloat16 *src = l == 0 ? w->x0 : w->pool[l];
         if (l > 0) {
-            const Dims dp = level_dims(n, l - 1);
-            const long long m = level_cells(n, l) * n->wnb * n->cfg.channels[l - 1];
-            k_pool<D><<<blocks_for(m), 256, 0, s>>>(dp, n->cfg.channels[l - 1], n->enc2[l - 1], n->pool[l]);
+            const Dims dp = level_dims(n, w, l - 1);
+            const long long m = level_cells(n, w, l) * w->wnb * n->cfg.channels[l - 1];
+            k_pool<D><<<blocks_for(m), 256, 0, s>>>(dp, n->cfg.channels[l - 1], w->enc2[l - 1], w->pool[l]);
         }
         ConvLayer &A = n->layers[k], &B = n->layers[k + 1];
-        UN_TRY(launch_conv<D>(A.co, conv_args(src, A.cip, nullptr, 0, A.wf, n->params + A.boff, n->enc1[l], 1, 0, d), tiles, s));
-        UN_TRY(launch_conv<D>(B.co, conv_args(n->enc1[l], B.cip, nullptr, 0, B.wf, n->params + B.boff, n->enc2[l], 1, 0, d), tiles, s));
+        UN_TRY(launch_conv<D>(A.co, conv_args(src, A.cip, nullptr, 0, A.wf, n->params + A.boff, w->enc1[l], 1, 0, d), tiles, s));
+        UN_TRY(launch_conv<D>(B.co, conv_args(w->enc1[l], B.cip, nullptr, 0, B.wf, n->params + B.boff, w->enc2[l], 1, 0, d), tiles, s));
         k += 2;
     }
     for (int l = L - 2; l >= 0; l--) {
-        const Dims d = level_dims(n, l);
-        const long long tiles = level_tiles(n, l);
-        const __nv_bfloat16 *coarse = l == L - 2 ? n->enc2[L - 1] : n->dec2[l + 1];
+        const Dims d = level_dims(n, w, l);
+        const long long tiles = level_tiles(n, w, l);
+        const __nv_bfloat16 *coarse = l == L - 2 ? w->enc2[L - 1] : w->dec2[l + 1];
         ConvLayer &A = n->layers[k], &B = n->layers[k + 1];
         const int C0 = n->cfg.channels[l], C1 = n->cfg.channels[l + 1];
-        UN_TRY(launch_conv<D>(A.co, conv_args(n->enc2[l], C0, coarse, C1, A.wf, n->params + A.boff, n->dec1[l], 1, 0, d), tiles, s));
-        UN_TRY(launch_conv<D>(B.co, conv_args(n->dec1[l], B.cip, nullptr, 0, B.wf, n->params + B.boff, n->dec2[l], 1, 0, d), tiles, s));
+        UN_TRY(launch_conv<D>(A.co, conv_args(w->enc2[l], C0, coarse, C1, A.wf, n->params + A.boff, w->dec1[l], 1, 0, d), tiles, s));
+        UN_TRY(launch_conv<D>(B.co, conv_args(w->dec1[l], B.cip, nullptr, 0, B.wf, n->params + B.boff, w->dec2[l], 1, 0, d), tiles, s));
         k += 2;
     }
     const ConvLayer &O = n->layers[k];
-    const __nv_bfloat16 *d0 = L > 1 ? n->dec2[0] : n->enc2[0];
-    k_out_fwd<<<blocks_for(c0), 256, 0, s>>>(c0, O.ci, O.co, d0, n->params + O.woff, n->params + O.boff, n->y);
+    const __nv_bfloat16 *d0 = L > 1 ? w->dec2[0] : w->enc2[0];
+    k_out_fwd<<<blocks_for(c0), 256, 0, s>>>(c0, O.ci, O.co, d0, n->params + O.woff, n->params + O.boff, w->y);
     return n->cuda(cudaGetLastError(), "forward");
 }
 
 // backward of one 3^D convolution with ReLU at its output: g (at the output,
-// FP32 or BF16) -> gz; weight and bias gradients; input gradient in n->gin
+// FP32 or BF16) -> gz; weight and bias gradients; input gradient in w->gin
 // (BF16, Cin channels) unless skip_input.
 template <int D, typename G>
-int conv_backward(pf_unet *n, const ConvLayer &c, const G *g, const __nv_bfloat16 *out,
+int conv_backward(pf_unet *n, UWork *w, const ConvLayer &c, const G *g, const __nv_bfloat16 *out,
                   const __nv_bfloat16 *in0, int C0, const __nv_bfloat16 *in1, int C1, int l, bool skip_input,
                   cudaStream_t s)
 {
-    const Dims d = level_dims(n, l);
-    const long long cells = level_cells(n, l) * n->wnb;
-    const long long tiles = level_tiles(n, l);
-    k_relu_mask<G><<<blocks_for(cells * c.co), 256, 0, s>>>(cells * c.co, g, out, n->gz);
-    WGradArgs w;
-    w.in0 = in0; w.in1 = in1; w.C0 = C0; w.C1 = C1; w.gz = n->gz; w.gw = c.gk; w.dim = d; w.ntiles = tiles;
-    UN_TRY(launch_wgrad<D>(c.co, w, c.cip, s));
-    k_bias_grad<<<blocks_for(cells * c.co, 1024), 256, 0, s>>>(cells, c.co, n->gz, n->grad + c.boff);
+    const Dims d = level_dims(n, w, l);
+    const long long cells = level_cells(n, w, l) * w->wnb;
+    const long long tiles = level_tiles(n, w, l);
+    k_relu_mask<G><<<blocks_for(cells * c.co), 256, 0, s>>>(cells * c.co, g, out, w->gz);
+    WGradArgs wa;
+    wa.in0 = in0; wa.in1 = in1; wa.C0 = C0; wa.C1 = C1; wa.gz = w->gz; wa.gw = c.gk; wa.dim = d; wa.ntiles = tiles;
+    UN_TRY(launch_wgrad<D>(c.co, wa, c.cip, s));
+    k_bias_grad<<<blocks_for(cells * c.co, 1024), 256, 0, s>>>(cells, c.co, w->gz, n->grad + c.boff);
     if (!skip_input)
-        UN_TRY(launch_conv<D>(c.cip, conv_args(n->gz, c.co, nullptr, 0, c.wb, nullptr, n->gin, 0, 1, d), tiles, s));
+        UN_TRY(launch_conv<D>(c.cip, conv_args(w->gz, c.co, nullptr, 0, c.wb, nullptr, w->gin, 0, 1, d), tiles, s));
     return PF_OK;
 }
 
 template <int D>
-int backward_t(pf_unet *n, const float *target, double *loss, cudaStream_t s)
+int backward_t(pf_unet *n, UWork *w, const float *target, double *loss, cudaStream_t s)
 {
     const int L = n->cfg.levels;
-    const long long c0 = level_cells(n, 0) * n->wnb;
+    const long long c0 = level_cells(n, w, 0) * w->wnb;
     const int nblk = blocks_for(c0 * D);
-    k_loss<<<nblk, 256, 0, s>>>(c0 * D, n->y, target, n->gy, 1.0 / (double)(c0 * D), n->part);
+    k_loss<<<nblk, 256, 0, s>>>(c0 * D, w->y, target, w->gy, 1.0 / (double)(c0 * D), n->part);
     // zero gradients
     UN_TRY(n->cuda(cudaMemsetAsync(n->grad, 0, sizeof(float) * n->nparam, s), "zero"));
     for (ConvLayer &c : n->layers)
         if (c.gk) UN_TRY(n->cuda(cudaMemsetAsync(c.gk, 0, sizeof(float) * c.taps * c.co * c.cip, s), "zero"));
     for (int l = 0; l < L; l++) {
-        UN_TRY(n->cuda(cudaMemsetAsync(n->g_a[l], 0, sizeof(float) * level_cells(n, l) * n->wnb * n->cfg.channels[l], s), "zero"));
+        UN_TRY(n->cuda(cudaMemsetAsync(w->g_a[l], 0, sizeof(float) * level_cells(n, w, l) * w->wnb * n->cfg.channels[l], s), "zero"));
         if (l > 0)
-            UN_TRY(n->cuda(cudaMemsetAsync(n->g_p[l], 0, sizeof(float) * level_cells(n, l) * n->wnb * n->cfg.channels[l - 1], s), "zero"));
+            UN_TRY(n->cuda(cudaMemsetAsync(w->g_p[l], 0, sizeof(float) * level_cells(n, w, l) * w->wnb * n->cfg.channels[l - 1], s), "zero"));
     }
     // output layer
     int k = (int)n->layers.size() - 1;
     const ConvLayer &O = n->layers[k];
-    const __nv_bfloat16 *d0 = L > 1 ? n->dec2[0] : n->enc2[0];
+    const __nv_bfloat16 *d0 = L > 1 ? w->dec2[0] : w->enc2[0];
     k_out_bwd<<<blocks_for(c0, 256) < 304 ? blocks_for(c0, 256) : 304, 256, sizeof(float) * (O.co * O.ci + O.co), s>>>(
-        c0, O.ci, O.co, d0, n->params + O.woff, n->gy, L > 1 ? n->g_d[0] : n->g_a[0], n->grad + O.woff, n->grad + O.boff);
+        c0, O.ci, O.co, d0, n->params + O.woff, w->gy, L > 1 ? w->g_d[0] : w->g_a[0], n->grad + O.woff, n->grad + O.boff);
     k--;
     // decoder, level 0 first
     for (int l = 0; l <= L - 2; l++) {
         const ConvLayer &B = n->layers[k], &A = n->layers[k - 1];
         k -= 2;
         const int C0 = n->cfg.channels[l], C1 = n->cfg.channels[l + 1];
-        const __nv_bfloat16 *coarse = l == L - 2 ? n->enc2[L - 1] : n->dec2[l + 1];
+        const __nv_bfloat16 *coarse = l == L - 2 ? w->enc2[L - 1] : w->dec2[l + 1];
         // second conv: output dec2[l], input dec1[l]
-        UN_TRY((conv_backward<D, float>(n, B, n->g_d[l], n->dec2[l], n->dec1[l], B.cip, nullptr, 0, l, false, s)));
+        UN_TRY((conv_backward<D, float>(n, w, B, w->g_d[l], w->dec2[l], w->dec1[l], B.cip, nullptr, 0, l, false, s)));
         // first conv: output dec1[l] (gradient = gin of the second, BF16), input concat(enc2[l], up2(coarse))
         // gin is overwritten by this call's own input gradient, so mask it into gz first
-        UN_TRY((conv_backward<D, __nv_bfloat16>(n, A, n->gin, n->dec1[l], n->enc2[l], C0, coarse, C1, l, false, s)));
-        const long long cells = level_cells(n, l) * n->wnb;
-        k_acc_skip<<<blocks_for(cells * C0), 256, 0, s>>>(cells, C0, C0 + C1, n->gin, n->g_a[l]);
+        UN_TRY((conv_backward<D, __nv_bfloat16>(n, w, A, w->gin, w->dec1[l], w->enc2[l], C0, coarse, C1, l, false, s)));
+        const long long cells = level_cells(n, w, l) * w->wnb;
+        k_acc_skip<<<blocks_for(cells * C0), 256, 0, s>>>(cells, C0, C0 + C1, w->gin, w->g_a[l]);
         // up2 backward into the coarser level's gradient (written, not added:
         // g_d[l+1], or g_a[L-1] for the bottom, has no other contribution)
-        float *gcoarse = l == L - 2 ? n->g_a[L - 1] : n->g_d[l + 1];
-        const Dims d = level_dims(n, l);
-        const long long hc = level_cells(n, l + 1) * n->wnb;
-        k_up_bwd<D><<<blocks_for(hc * C1), 256, 0, s>>>(d, C0, C1, n->gin, gcoarse);
+        float *gcoarse = l == L - 2 ? w->g_a[L - 1] : w->g_d[l + 1];
+        const Dims d = level_dims(n, w, l);
+        const long long hc = level_cells(n, w, l + 1) * w->wnb;
+        k_up_bwd<D><<<blocks_for(hc * C1), 256, 0, s>>>(d, C0, C1, w->gin, gcoarse);
     }
     // encoder, deepest level first
     for (int l = L - 1; l >= 0; l--) {
         const ConvLayer &B = n->layers[k], &A = n->layers[k - 1];
         k -= 2;
-        const __nv_bfloat16 *src = l == 0 ? n->x0 : n->pool[l];
+        const __nv_bfloat16 *src = l == 0 ? w->x0 : w->pool[l];
         const int Cs = l == 0 ? 16 : n->cfg.channels[l - 1];
-        UN_TRY((conv_backward<D, float>(n, B, n->g_a[l], n->enc2[l], n->enc1[l], B.cip, nullptr, 0, l, false, s)));
-        UN_TRY((conv_backward<D, __nv_bfloat16>(n, A, n->gin, n->enc1[l], src, Cs, nullptr, 0, l, l == 0, s)));
+        UN_TRY((conv_backward<D, float>(n, w, B, w->g_a[l], w->enc2[l], w->enc1[l], B.cip, nullptr, 0, l, false, s)));
+        UN_TRY((conv_backward<D, __nv_bfloat16>(n, w, A, w->gin, w->enc1[l], src, Cs, nullptr, 0, l, l == 0, s)));
         if (l > 0) {
             // gin = gradient at pool[l]; average-pooling backward into g_a[l-1]
-            const long long hc = level_cells(n, l) * n->wnb;
+            const long long hc = level_cells(n, w, l) * w->wnb;
             const int Cp = n->cfg.channels[l - 1];
             // convert gin (BF16, Cp channels) to FP32 g_p[l], then distribute
-            k_acc_skip<<<blocks_for(hc * Cp), 256, 0, s>>>(hc, Cp, Cp, n->gin, n->g_p[l]);
-            const Dims dc = level_dims(n, l - 1);
-            k_pool_bwd<D><<<blocks_for(level_cells(n, l - 1) * n->wnb * Cp), 256, 0, s>>>(dc, Cp, n->g_p[l], n->g_a[l - 1]);
+            k_acc_skip<<<blocks_for(hc * Cp), 256, 0, s>>>(hc, Cp, Cp, w->gin, w->g_p[l]);
+            const Dims dc = level_dims(n, w, l - 1);
+            k_pool_bwd<D><<<blocks_for(level_cells(n, w, l - 1) * w->wnb * Cp), 256, 0, s>>>(dc, Cp, w->g_p[l], w->g_a[l - 1]);
         }
     }
     // kernel-layout weight gradients into the master layout
@@ -603,13 +621,31 @@ int backward_t(pf_unet *n, const float *target, double *loss, cudaStream_t s)
 // ---------------------------------------------------------------------------
 // Internal entry points used by the field library (learned warm start)
 // ---------------------------------------------------------------------------
-int unet_forward_internal(pf_unet *n, const float *in, float *out, int nb, int nx, int ny, int nz, cudaStream_t s)
+UWork *unet_work_create(pf_unet *n, int nb, int nx, int ny, int nz)
 {
-    UN_TRY(check_dims(n, nb, nx, ny, nz));
-    UN_TRY(ensure_work(n, nb, nx, ny, nz));
-    UN_TRY(n->cfg.ndim == 2 ? forward_t<2>(n, in, s) : forward_t<3>(n, in, s));
-    const long long c0 = level_cells(n, 0) * nb;
-    return n->cuda(cudaMemcpyAsync(out, n->y, sizeof(float) * c0 * n->cfg.ndim, cudaMemcpyDeviceToDevice, s), "output");
+    if (check_dims(n, nb, nx, ny, nz) != PF_OK) return nullptr;
+    UWork *w = new (std::nothrow) UWork();
+    if (!w) return nullptr;
+    if (ensure_work(n, w, nb, nx, ny, nz, false) != PF_OK) {
+        w->release();
+        delete w;
+        return nullptr;
+    }
+    return w;
+}
+
+void unet_work_destroy(UWork *w)
+{
+    if (!w) return;
+    w->release();
+    delete w;
+}
+
+int unet_forward_work(pf_unet *n, UWork *w, const float *in, const float **out, cudaStream_t s)
+{
+    UN_TRY(n->cfg.ndim == 2 ? forward_t<2>(n, w, in, s) : forward_t<3>(n, w, in, s));
+    *out = w->y;
+    return PF_OK;
 }
 
 int unet_ndim(const pf_unet *n) { return n->cfg.ndim; }
@@ -716,7 +752,12 @@ int pf_unet_forward(pf_unet *n, const float *in, float *out, int nb, int nx, int
 {
     if (!n || !in || !out) return PF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    UN_TRY(unet_forward_internal(n, in, out, nb, nx, ny, nz, s));
+    UWork *w = &n->train;
+    UN_TRY(check_dims(n, nb, nx, ny, nz));
+    UN_TRY(ensure_work(n, w, nb, nx, ny, nz, false));
+    UN_TRY(n->cfg.ndim == 2 ? forward_t<2>(n, w, in, s) : forward_t<3>(n, w, in, s));
+    const long long c0 = level_cells(n, w, 0) * nb;
+    UN_TRY(n->cuda(cudaMemcpyAsync(out, w->y, sizeof(float) * c0 * n->cfg.ndim, cudaMemcpyDeviceToDevice, s), "output"));
     return n->cuda(cudaStreamSynchronize(s), "forward");
 }
 
@@ -726,9 +767,10 @@ int pf_unet_loss_grad(pf_unet *n, const float *in, const float *target, int nb, 
     if (!n || !in || !target || !loss) return PF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     UN_TRY(check_dims(n, nb, nx, ny, nz));
-    UN_TRY(ensure_work(n, nb, nx, ny, nz));
-    UN_TRY(n->cfg.ndim == 2 ? forward_t<2>(n, in, s) : forward_t<3>(n, in, s));
-    UN_TRY(n->cfg.ndim == 2 ? backward_t<2>(n, target, loss, s) : backward_t<3>(n, target, loss, s));
+    UWork *w = &n->train;
+    UN_TRY(ensure_work(n, w, nb, nx, ny, nz, true));
+    UN_TRY(n->cfg.ndim == 2 ? forward_t<2>(n, w, in, s) : forward_t<3>(n, w, in, s));
+    UN_TRY(n->cfg.ndim == 2 ? backward_t<2>(n, w, target, loss, s) : backward_t<3>(n, w, target, loss, s));
     if (grad_host)
         UN_TRY(n->cuda(cudaMemcpy(grad_host, n->grad, sizeof(float) * n->nparam, cudaMemcpyDeviceToHost), "grad"));
     return PF_OK;
@@ -756,7 +798,7 @@ void pf_unet_destroy(pf_unet *n)
 {
     if (!n) return;
     cudaDeviceSynchronize();
-    for (void *p : n->work) cudaFree(p);
+    n->train.release();
     for (void *p : n->allocs) cudaFree(p);
     delete n;
 }

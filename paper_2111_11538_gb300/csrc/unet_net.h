@@ -4,10 +4,16 @@
 #include <cuda_runtime.h>
 
 struct pf_unet;
+struct UWork;
 
-// y = net(x) on stream s; x: nb * cells * cin FP32, y: nb * cells * ndim FP32
-// (device).  Returns a pf.h status; unet_error() gives the text.
-int unet_forward_internal(pf_unet *n, const float *in, float *out, int nb, int nx, int ny, int nz, cudaStream_t s);
+// Inference workspace for nb samples of nx * ny * nz cells (nullptr if the
+// grid does not suit the network or memory is short).  Its buffers never
+// move, so launches that read them may be captured into a CUDA graph.
+UWork *unet_work_create(pf_unet *n, int nb, int nx, int ny, int nz);
+void unet_work_destroy(UWork *w);
+// y = net(x) on stream s; x: nb * cells * cin FP32 (device); *out points at
+// the workspace's nb * cells * ndim FP32 result.  Returns a pf.h status.
+int unet_forward_work(pf_unet *n, UWork *w, const float *in, const float **out, cudaStream_t s);
 int unet_ndim(const pf_unet *n);
 int unet_cin(const pf_unet *n);
 int unet_check_grid(pf_unet *n, int nx, int ny, int nz);

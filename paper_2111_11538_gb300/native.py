@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOTCONV, PF_ENONFINITE, PF_ETIMEOUT, PF_ESTATE = range(8)
 PF_FP64, PF_MIXED = 0, 1
-PF_WS_ZERO, PF_WS_PREV = 0, 1
+PF_WS_ZERO, PF_WS_PREV, PF_WS_LEARNED = 0, 1, 2
 PF_HOST, PF_DEVICE = 0, 1
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_ENOTCONV",
@@ -58,8 +58,8 @@ class pf_diag(ctypes.Structure):
                 ("steps", ctypes.c_longlong), ("dt", ctypes.c_double), ("status", ctypes.c_int)]
 
 
-PF_K_SETUP, PF_K_CG, PF_K_RETURN, PF_K_UPDATE, PF_K_NCLASS = range(5)
-KERNEL_CLASSES = ["setup", "cg", "return", "update"]
+PF_K_SETUP, PF_K_CG, PF_K_RETURN, PF_K_UPDATE, PF_K_WARM, PF_K_NCLASS = range(6)
+KERNEL_CLASSES = ["setup", "cg", "return", "update", "warm"]
 
 
 class pf_profile(ctypes.Structure):
@@ -77,7 +77,7 @@ class pf_unet_config(ctypes.Structure):
 SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_diagnostics",
            "pf_free_energy", "pf_dt_stable", "pf_profile_enable", "pf_profile_read",
            "pf_batch_create", "pf_batch_size", "pf_batch_set_fields", "pf_batch_get_fields",
-           "pf_batch_get_diagnostics",
+           "pf_batch_get_diagnostics", "pf_attach_unet", "pf_selftest_wait",
            "pf_device_bytes", "pf_last_error", "pf_destroy",
            "pf_fields_update_static", "pf_static_last_error",
            "pf_unet_create", "pf_unet_param_count", "pf_unet_set_params", "pf_unet_get_params",
@@ -166,6 +166,10 @@ def lib():
         l.pf_batch_get_fields.restype = ctypes.c_int
         l.pf_batch_get_diagnostics.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(pf_diag)]
         l.pf_batch_get_diagnostics.restype = ctypes.c_int
+        l.pf_selftest_wait.argtypes = [ctypes.c_longlong]
+        l.pf_selftest_wait.restype = ctypes.c_int
+        l.pf_attach_unet.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        l.pf_attach_unet.restype = ctypes.c_int
         l.pf_device_bytes.argtypes = [ctypes.c_void_p]
         l.pf_device_bytes.restype = ctypes.c_longlong
         l.pf_last_error.argtypes = [ctypes.c_void_p]
@@ -271,6 +275,14 @@ def pf_batch_get_diagnostics(h, i):
     d = pf_diag()
     rc = lib().pf_batch_get_diagnostics(h, int(i), ctypes.byref(d))
     return rc, d
+
+
+def pf_selftest_wait(spin_limit):
+    return lib().pf_selftest_wait(int(spin_limit))
+
+
+def pf_attach_unet(h, net):
+    return lib().pf_attach_unet(h, net)
 
 
 def pf_device_bytes(h):

@@ -199,3 +199,19 @@ def test_device_pointers_match_host():
     gb = b.get_fields()
     for k in ("phi_f", "xO", "xH", "xW", "u"):
         assert np.array_equal(ga[k], gb[k]), k
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A device wait on a word nothing updates gives up after its poll limit
+    and reports PF_ETIMEOUT; the CUDA context stays usable."""
+    import time
+    t0 = time.time()
+    assert native.pf_selftest_wait(1 << 16) == native.PF_ETIMEOUT
+    assert time.time() - t0 < 30
+    assert native.pf_selftest_wait(0) == native.PF_EINVAL
+    shape = (32, 32)
+    sim = Simulation(shape, workloads.params(mechanics=0), precision="fp64")
+    sim.set_fields(inputs.core_shell(shape, 10.0, 3.0))
+    sim.step(2)
+    assert sim.diagnostics()["steps"] == 2
+    sim.close()
