@@ -58,9 +58,21 @@ int pf_unet_get_params(pf_unet *net, float *host);
 /* out = net(in) for nb samples of nx * ny * nz cells (device arrays). */
 int pf_unet_forward(pf_unet *net, const float *in, float *out, int nb, int nx, int ny, int nz, void *cudaStream);
 
-/* Mean-square loss of net(in) against target and its gradient with respect
- * to the parameters, kept for pf_unet_adam_step; *loss (host) receives the
- * loss, grad_host (nullable) a copy of the gradient. */
+/* Training loss (e = net(in) - target, n = cells * ndim over the batch):
+ *   PF_UNET_LOSS_MSE  (default)  (1/n) sum |e|^2
+ *   PF_UNET_LOSS_GRAD            (1/n) sum_p w_p sum_d |e(p + e_d) - e(p)|^2,
+ *     periodic forward differences, w_p = floor + (1 - floor)(1 - in[p, weight_channel])
+ *     (with the gas weight as channel: the error of the displacement
+ *     gradient where the material is stiff, a stand-in for the energy norm
+ *     the PCG reduces; blind to rigid translations).
+ * PF_EINVAL for an unknown kind, a channel outside 0..cin-1 or floor
+ * outside [0, 1]. */
+enum { PF_UNET_LOSS_MSE = 0, PF_UNET_LOSS_GRAD = 1 };
+int pf_unet_set_loss(pf_unet *net, int kind, int weight_channel, double floor);
+
+/* The training loss of net(in) against target and its gradient with
+ * respect to the parameters, kept for pf_unet_adam_step; *loss (host)
+ * receives the loss, grad_host (nullable) a copy of the gradient. */
 int pf_unet_loss_grad(pf_unet *net, const float *in, const float *target, int nb, int nx, int ny, int nz,
                       double *loss, float *grad_host, void *cudaStream);
 

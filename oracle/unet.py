@@ -27,7 +27,13 @@ dec_{L-2}a, dec_{L-2}b, ..., dec_0a, dec_0b, out: the weights W[c_out][c_in]
 [taps] (taps row-major over (dz,) dy, dx, each in 0..2, tap offset = index-1)
 followed by the bias b[c_out].
 
-Loss: mean over cells and output channels of (y - target)^2.
+Loss, either of
+  "mse":  mean over cells and output channels of (y - target)^2;
+  "grad": (1/(cells * C_out)) sum over cells p, axes d and channels c of
+          w_p (e_c(p + e_d) - e_c(p))^2, e = y - target, periodic forward
+          differences, w_p = floor + (1 - floor)(1 - x_k(p)) with x_k an input
+          channel (the gas weight: a stiffness weight, so that the loss
+          follows the strain error where the material is stiff).
 
 Everything here is written from the definitions above with numpy; a
 convolution is a sum over taps of np.roll-shifted inputs contracted with the
@@ -185,14 +191,31 @@ def forward(theta, x, ndim, channels, cout=None, keep=False):
     return y
 
 
-def loss_and_grad(theta, x, target, ndim, channels, cout=None):
-    """Mean-square loss of net(x) against target and its gradient (flat)."""
+def output_loss(y, target, kind="mse", weights=None):
+    """Loss and its gradient with respect to the network output y (C, *S)."""
+    n = y.size
+    e = y - target
+    if kind == "mse":
+        return float(np.sum(e * e) / n), 2.0 * e / n
+    ndim = y.ndim - 1
+    loss = 0.0
+    g = np.zeros_like(y)
+    for ax in range(1, ndim + 1):
+        de = np.roll(e, -1, axis=ax) - e                  # e(p + e_d) - e(p)
+        wde = weights[None] * de
+        loss += float(np.sum(wde * de))
+        # d/d e(q) of w_p de(p)^2: +2 w_{q-1} de(q-1) - 2 w_q de(q)
+        g += 2.0 * (np.roll(wde, 1, axis=ax) - wde)
+    return loss / n, g / n
+
+
+def loss_and_grad(theta, x, target, ndim, channels, cout=None, kind="mse", weight_channel=1, floor=0.01):
+    """Loss of net(x) against target (see the module docstring) and its
+    gradient with respect to the parameters (flat)."""
     y, (P, tape, d0) = forward(theta, x, ndim, channels, cout, keep=True)
     L = len(channels)
-    n = y.size
-    diff = y - target
-    loss = float(np.sum(diff * diff) / n)
-    gy = 2.0 * diff / n
+    wts = floor + (1.0 - floor) * (1.0 - x[weight_channel]) if kind == "grad" else None
+    loss, gy = output_loss(y, target, kind, wts)
     grads = [None] * len(P)
     k = len(P) - 1
     gd, gW, gb = conv_backward(d0, P[k][0], gy)

@@ -36,7 +36,7 @@ struct PCGArgs {
     const T *sig[6];
     T *x[3], *p[3];
     T *r[2][3], *w[2][3], *s[2][3];
-    T *diag;
+    T *dinv;                       // inverse of the Jacobi diagonal, written by the set-up
     T *u[3];                       // refinement mode: FP32 displacement written at the end
     double *x64[3];                // refinement mode: FP64 solution
     int refine;                    // 1: FP64 outer residual around the FP32 iteration
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                 if (refine) {
                     double b[D], ax[D], dgn, so[NV], deo[NV], lo, mo;
                     node_setup<T, double, double, D>(P, n, A.lam, A.mu, A.sig, A.x64, xe64, use_x, b, ax, dgn, so, deo, lo, mo);
-                    A.diag[n] = (T)dgn;
+                    A.dinv[n] = (T)(1.0 / dgn);
 #pragma unroll
                     for (int d = 0; d < D; d++) { bv[d] = b[d]; rv[d] = b[d] - ax[d]; }
                     acc[2].add(lo); acc[3].add(mo);
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                 } else {
                     T b[D], ax[D], dgn, so[NV], deo[NV], lo, mo;
                     node_setup<T, T, T, D>(P, n, A.lam, A.mu, A.sig, A.x, xeT, use_x, b, ax, dgn, so, deo, lo, mo);
-                    A.diag[n] = dgn;
+                    A.dinv[n] = T(1) / dgn;
 #pragma unroll
                     for (int d = 0; d < D; d++) { bv[d] = (double)b[d]; rv[d] = (double)(b[d] - ax[d]); }
                     acc[2].add((double)lo); acc[3].add((double)mo);
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                     if (h < HN) {
                         const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
                         const int g = hidx<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz, small);
-                        R.dg[k] = __ldcg(A.diag + g);
+                        R.dg[k] = __ldcg(A.dinv + g);
 #pragma unroll
                         for (int d = 0; d < D; d++) {
                             R.r[k][d] = __ldcg(A.r[cur][d] + g);
@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                 const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
                 if (gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz)) {
                     const int n = gx + P.nx * (gy + (D == 3 ? P.ny * gz : 0));
-                    R.dgo = __ldcg(A.diag + n);
+                    R.dgo = __ldcg(A.dinv + n);
 #pragma unroll
                     for (int d = 0; d < D; d++) {
                         R.ro[d] = __ldcg(A.r[cur][d] + n);
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                 for (int k = 0; k < HS; k++) {
                     const int h = threadIdx.x + 256 * k;
                     if (h < HN) {
-                        const T inv = T(1) / R.dg[k];
+                        const T inv = R.dg[k];
 #pragma unroll
                         for (int d = 0; d < D; d++) {
                             T rv = R.r[k][d];
@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                     for (int d = 0; d < D; d++) un[d] = su[d * HN + hn];
                     T rn[D];
                     if (!first) {
-                        const T inv = T(1) / dgo;
+                        const T inv = dgo;
 #pragma unroll
                         for (int d = 0; d < D; d++) {
                             const T ri = ro[d];
@@ -685,12 +685,12 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
 #pragma unroll
                     for (int d = 0; d < D; d++) {
                         A.w[nxt][d][n] = q[d];
-                        acc[0].addprod(rn[d], un[d]);
-                        acc[1].addprod(q[d], un[d]);
-                        acc[2].addprod(rn[d], rn[d]);
+                        acc[0].fma_plain(rn[d], un[d]);
+                        acc[1].fma_plain(q[d], un[d]);
+                        acc[2].fma_plain(rn[d], rn[d]);
                     }
 #pragma unroll
-                    for (int vv = 0; vv < NV; vv++) acc[3 + vv].add(se[vv]);
+                    for (int vv = 0; vv < NV; vv++) acc[3 + vv].add_plain(se[vv]);
                 }
                 __syncthreads();
             }

@@ -99,6 +99,8 @@ template <> struct Acc<double> {
     double s = 0.0;
     __device__ __forceinline__ void add(double x) { s += x; }
     __device__ __forceinline__ void addprod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ void add_plain(double x) { s += x; }
+    __device__ __forceinline__ void fma_plain(double a, double b) { s = fma(a, b, s); }
     __device__ __forceinline__ double value() const { return s; }
 };
 template <> struct Acc<float> {
@@ -117,6 +119,10 @@ template <> struct Acc<float> {
         add(p);
         c += e;
     }
+    // uncompensated: for the few terms one thread sums before the
+    // compensated block and grid reductions take over
+    __device__ __forceinline__ void add_plain(float x) { s += x; }
+    __device__ __forceinline__ void fma_plain(float a, float b) { s = fmaf(a, b, s); }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 

@@ -337,7 +337,7 @@ PCGArgs<T, D> pcg_args(pf_handle *m)
     }
     A.refine = m->refine ? 1 : 0;
     A.eta = 1e-3;
-    A.diag = (T *)m->diag;
+    A.dinv = (T *)m->diag;
     A.partials = m->partials;
     A.result = m->result;
     A.bar_count = m->sync; A.bar_gen = m->sync + SYNC_GEN;

@@ -108,6 +108,53 @@ __global__ void k_loss(long long n, const float *y, const float *t, float *gy, d
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
+// Stiffness-weighted gradient loss: per cell q the forward differences
+// de_d(q) = e(q + e_d) - e(q) (e = y - t, periodic within the sample),
+// loss += w_q sum_d |de_d(q)|^2, w_q = floor + (1 - floor)(1 - in[q, wch]);
+// gy(q) = 2 inv_n sum_d [w_{q-e_d} de_d(q - e_d) - w_q de_d(q)].
+template <int D>
+__global__ void k_loss_grad(Dims dm, int C, const float *y, const float *t, const float *in, int cin, int wch,
+                            float floor_w, float *gy, double inv_n, double *part)
+{
+    const int nx = dm.nx, ny = dm.ny, nz = D == 3 ? dm.nz : 1;
+    const long long cells = (long long)nx * ny * nz;
+    const long long n = cells * dm.nb;
+    double s = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const long long b = q / cells;
+        const long long r = q - b * cells;
+        const int x = (int)(r % nx), yy = (int)((r / nx) % ny), z = (int)(r / ((long long)nx * ny));
+        auto at = [&](int xi, int yi, int zi) -> long long {
+            xi = wrapc(xi, nx); yi = wrapc(yi, ny); zi = D == 3 ? wrapc(zi, nz) : 0;
+            return b * cells + xi + (long long)nx * (yi + (long long)ny * zi);
+        };
+        auto wt = [&](long long p) { return floor_w + (1.f - floor_w) * (1.f - in[p * cin + wch]); };
+        const float wq = wt(q);
+        for (int c = 0; c < C; c++) {
+            const float eq = y[q * C + c] - t[q * C + c];
+            float g = 0.f;
+            for (int d = 0; d < D; d++) {
+                const long long pp = at(x + (d == 0), yy + (d == 1), z + (d == 2));
+                const long long pm = at(x - (d == 0), yy - (d == 1), z - (d == 2));
+                const float ep = y[pp * C + c] - t[pp * C + c];
+                const float em = y[pm * C + c] - t[pm * C + c];
+                const float dq = ep - eq, dm1 = eq - em;
+                s += (double)wq * (double)dq * (double)dq;
+                g += wt(pm) * dm1 - wq * dq;
+            }
+            gy[q * C + c] = (float)(2.0 * inv_n) * g;
+        }
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
 // output-layer backward: g_d[p, c] = sum_o W[o, c] gy[p, o]; gW[o, c] += sum_p gy[p, o] d[p, c]; gb[o] += sum_p gy
 __global__ void k_out_bwd(long long n, int C, int CO, const __nv_bfloat16 *d, const float *W, const float *gy,
                           float *gd, float *gW, float *gb)
@@ -283,6 +330,9 @@ struct pf_unet {
     double *part = nullptr;         // loss partials
     std::vector<void *> allocs;
     UWork train;                    // workspace of pf_unet_forward / pf_unet_loss_grad
+    int loss_kind = 0;              // PF_UNET_LOSS_MSE / PF_UNET_LOSS_GRAD
+    int loss_wch = 1;
+    float loss_floor = 0.01f;
 
     int fail(int code, const char *fmt, ...)
     {
@@ -542,12 +592,17 @@ int conv_backward(pf_unet *n, UWork *w, const ConvLayer &c, const G *g, const __
 }
 
 template <int D>
-int backward_t(pf_unet *n, UWork *w, const float *target, double *loss, cudaStream_t s)
+int backward_t(pf_unet *n, UWork *w, const float *in, const float *target, double *loss, cudaStream_t s)
 {
     const int L = n->cfg.levels;
     const long long c0 = level_cells(n, w, 0) * w->wnb;
     const int nblk = blocks_for(c0 * D);
-    k_loss<<<nblk, 256, 0, s>>>(c0 * D, w->y, target, w->gy, 1.0 / (double)(c0 * D), n->part);
+    if (n->loss_kind == PF_UNET_LOSS_GRAD)
+        k_loss_grad<D><<<blocks_for(c0), 256, 0, s>>>(level_dims(n, w, 0), D, w->y, target, in, n->cfg.cin, n->loss_wch,
+                                                       n->loss_floor, w->gy, 1.0 / (double)(c0 * D), n->part);
+    else
+        k_loss<<<nblk, 256, 0, s>>>(c0 * D, w->y, target, w->gy, 1.0 / (double)(c0 * D), n->part);
+    const int nparts = n->loss_kind == PF_UNET_LOSS_GRAD ? blocks_for(c0) : nblk;
     // zero gradients
     UN_TRY(n->cuda(cudaMemsetAsync(n->grad, 0, sizeof(float) * n->nparam, s), "zero"));
     for (ConvLayer &c : n->layers)
@@ -607,8 +662,8 @@ int backward_t(pf_unet *n, UWork *w, const float *target, double *loss, cudaStre
         if (c.taps == 1) continue;
         k_wgrad_to_master<<<blocks_for((long long)c.co * c.ci * c.taps), 256, 0, s>>>(c.co, c.ci, c.cip, c.taps, c.gk, n->grad + c.woff);
     }
-    std::vector<double> part(nblk);
-    UN_TRY(n->cuda(cudaMemcpyAsync(part.data(), n->part, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s), "loss"));
+    std::vector<double> part(nparts);
+    UN_TRY(n->cuda(cudaMemcpyAsync(part.data(), n->part, sizeof(double) * nparts, cudaMemcpyDeviceToHost, s), "loss"));
     UN_TRY(n->cuda(cudaStreamSynchronize(s), "backward"));
     double sum = 0.0;
     for (double v : part) sum += v;
@@ -731,6 +786,18 @@ int pf_unet_create(const pf_unet_config *cfg, pf_unet **out)
 
 long long pf_unet_param_count(const pf_unet *n) { return n ? n->nparam : 0; }
 
+int pf_unet_set_loss(pf_unet *n, int kind, int weight_channel, double floor)
+{
+    if (!n) return PF_EINVAL;
+    if (kind != PF_UNET_LOSS_MSE && kind != PF_UNET_LOSS_GRAD) return n->fail(PF_EINVAL, "unknown loss kind %d", kind);
+    if (weight_channel < 0 || weight_channel >= n->cfg.cin) return n->fail(PF_EINVAL, "weight channel out of range");
+    if (!(floor >= 0.0 && floor <= 1.0)) return n->fail(PF_EINVAL, "floor must be in [0, 1]");
+    n->loss_kind = kind;
+    n->loss_wch = weight_channel;
+    n->loss_floor = (float)floor;
+    return PF_OK;
+}
+
 int pf_unet_set_params(pf_unet *n, const float *host)
 {
     if (!n || !host) return PF_EINVAL;
@@ -770,7 +837,7 @@ int pf_unet_loss_grad(pf_unet *n, const float *in, const float *target, int nb, 
     UWork *w = &n->train;
     UN_TRY(ensure_work(n, w, nb, nx, ny, nz, true));
     UN_TRY(n->cfg.ndim == 2 ? forward_t<2>(n, w, in, s) : forward_t<3>(n, w, in, s));
-    UN_TRY(n->cfg.ndim == 2 ? backward_t<2>(n, w, target, loss, s) : backward_t<3>(n, w, target, loss, s));
+    UN_TRY(n->cfg.ndim == 2 ? backward_t<2>(n, w, in, target, loss, s) : backward_t<3>(n, w, in, target, loss, s));
     if (grad_host)
         UN_TRY(n->cuda(cudaMemcpy(grad_host, n->grad, sizeof(float) * n->nparam, cudaMemcpyDeviceToHost), "grad"));
     return PF_OK;

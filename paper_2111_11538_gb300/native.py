@@ -80,7 +80,7 @@ SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_dia
            "pf_batch_get_diagnostics", "pf_attach_unet", "pf_selftest_wait",
            "pf_device_bytes", "pf_last_error", "pf_destroy",
            "pf_fields_update_static", "pf_static_last_error",
-           "pf_unet_create", "pf_unet_param_count", "pf_unet_set_params", "pf_unet_get_params",
+           "pf_unet_create", "pf_unet_param_count", "pf_unet_set_loss", "pf_unet_set_params", "pf_unet_get_params",
            "pf_unet_forward", "pf_unet_loss_grad", "pf_unet_adam_step", "pf_unet_last_error",
            "pf_unet_destroy"]
 PF_STATIC_MAX_CELLS = 65536
@@ -184,6 +184,8 @@ def lib():
         l.pf_unet_create.restype = ctypes.c_int
         l.pf_unet_param_count.argtypes = [ctypes.c_void_p]
         l.pf_unet_param_count.restype = ctypes.c_longlong
+        l.pf_unet_set_loss.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        l.pf_unet_set_loss.restype = ctypes.c_int
         l.pf_unet_set_params.argtypes = [ctypes.c_void_p, _FP]
         l.pf_unet_set_params.restype = ctypes.c_int
         l.pf_unet_get_params.argtypes = [ctypes.c_void_p, _FP]
@@ -317,6 +319,13 @@ def pf_unet_create(cfg):
 
 def pf_unet_param_count(h):
     return lib().pf_unet_param_count(h)
+
+
+PF_UNET_LOSS_MSE, PF_UNET_LOSS_GRAD = 0, 1
+
+
+def pf_unet_set_loss(h, kind, weight_channel=1, floor=0.01):
+    return lib().pf_unet_set_loss(h, int(kind), int(weight_channel), float(floor))
 
 
 def pf_unet_set_params(h, host):

@@ -94,6 +94,12 @@ class WarmStartNet:
         self._check(rc)
         return (loss, g) if want_grad else loss
 
+    def set_loss(self, kind="mse", weight_channel=1, floor=0.01):
+        """Training loss: "mse" on the output, or "grad" -- the stiffness-
+        weighted error of the output's forward differences (include/pf_unet.h)."""
+        k = {"mse": native.PF_UNET_LOSS_MSE, "grad": native.PF_UNET_LOSS_GRAD}[kind]
+        self._check(native.pf_unet_set_loss(self.h, k, weight_channel, floor))
+
     def adam_step(self, lr):
         import torch
         self._check(native.pf_unet_adam_step(self.h, lr, torch.cuda.current_stream().cuda_stream))
@@ -296,6 +302,7 @@ def main(argv=None):
     ap.add_argument("--instances-256", type=int, default=16)
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--loss", default="grad", choices=["mse", "grad"])
     a = ap.parse_args(argv)
     t0 = time.time()
     X, T = generate_pairs(a.instances, (128, 128), seed=a.seed)
@@ -303,10 +310,11 @@ def main(argv=None):
     Xh, Th = generate_pairs(8, (128, 128), seed=a.seed + 100)
     t1 = time.time()
     net = init(2, DEFAULT_CHANNELS, seed=a.seed)
+    net.set_loss(a.loss)
     hist = train(net, [X, X2], [T, T2], a.steps, batch=8, lr=2e-3, seed=a.seed)
     t2 = time.time()
     save(net, a.out)
-    info = {"pairs": int(len(X) + len(X2)), "pair_seconds": t1 - t0, "train_steps": a.steps,
+    info = {"loss": a.loss, "pairs": int(len(X) + len(X2)), "pair_seconds": t1 - t0, "train_steps": a.steps,
             "train_seconds": t2 - t1, "loss_first": hist[0], "loss_last50": float(np.mean(hist[-50:])),
             "heldout_rate_error": rate_error(net, Xh, Th), "heldout_pairs": int(len(Xh))}
     print(json.dumps(info))

@@ -63,16 +63,18 @@ def test_forward_matches_reference(ndim, shape, channels):
     net.close()
 
 
+@pytest.mark.parametrize("kind", ["mse", "grad"])
 @pytest.mark.parametrize("ndim,shape,channels", [CASES[0], CASES[2]])
-def test_gradient_matches_reference(ndim, shape, channels):
+def test_gradient_matches_reference(ndim, shape, channels, kind):
     import torch
     net, theta = _net(ndim, channels, seed=21)
+    net.set_loss(kind, weight_channel=1, floor=0.05)
     x, t = _data(shape, ndim, 2, seed=22)
     loss, g = net.loss_grad(torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda"), want_grad=True)
     # the batch loss is the mean over samples of the per-sample means
     lr_, gr = 0.0, np.zeros_like(theta)
     for xb, tb in zip(_to_ref(x), _to_ref(t)):
-        l, gb = ref.loss_and_grad(theta, xb, tb, ndim, list(channels))
+        l, gb = ref.loss_and_grad(theta, xb, tb, ndim, list(channels), kind=kind, weight_channel=1, floor=0.05)
         lr_ += l / x.shape[0]
         gr += gb / x.shape[0]
     assert abs(loss - lr_) < 2e-2 * lr_

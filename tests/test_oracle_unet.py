@@ -41,22 +41,25 @@ def test_conv_matches_brute_force(shape, k):
     assert np.allclose(unet.conv(x, W, b), _brute_conv(x, W, b), rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("kind", ["mse", "grad"])
 @pytest.mark.parametrize("ndim,shape,channels", [(2, (8, 8), [3, 4]), (2, (8, 12), [2, 3, 4]), (3, (4, 4, 4), [2, 3])])
-def test_gradient_matches_central_differences(ndim, shape, channels):
+def test_gradient_matches_central_differences(ndim, shape, channels, kind):
     rng = np.random.default_rng(1)
     cin = 3
     theta = unet.init_params(ndim, cin, channels, seed=2)
     theta += 0.05 * rng.standard_normal(theta.size)     # non-zero biases too
     x = rng.standard_normal((cin,) + shape)
+    x[1] = rng.uniform(0.0, 1.0, shape)          # the weight channel is a gas weight
     tgt = rng.standard_normal((ndim,) + shape)
-    loss, g = unet.loss_and_grad(theta, x, tgt, ndim, channels)
+    f = lambda th: unet.loss_and_grad(th, x, tgt, ndim, channels, kind=kind)
+    loss, g = f(theta)
     assert g.shape == theta.shape
     h = 1e-6
     for i in rng.choice(theta.size, 40, replace=False):
         tp, tm = theta.copy(), theta.copy()
         tp[i] += h
         tm[i] -= h
-        fd = (unet.loss_and_grad(tp, x, tgt, ndim, channels)[0] - unet.loss_and_grad(tm, x, tgt, ndim, channels)[0]) / (2 * h)
+        fd = (f(tp)[0] - f(tm)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
 
 
@@ -111,3 +114,19 @@ def test_adam_first_step_closed_form():
     t1, m, v = unet.adam(theta, g, np.zeros(3), np.zeros(3), 1, lr=0.01)
     # bias-corrected first moment g, second g^2: step lr * g / (|g| + eps)
     assert np.allclose(t1, theta - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+
+
+def test_gradient_loss_ignores_translation_and_weights_stiff_cells():
+    rng = np.random.default_rng(8)
+    y = rng.standard_normal((2, 6, 8))
+    w = rng.uniform(0.0, 1.0, (6, 8))
+    # a rigid translation of the output costs nothing
+    l0, _ = unet.output_loss(y, y + np.array([0.3, -1.2])[:, None, None], "grad", w)
+    assert abs(l0) < 1e-25
+    # a single-cell error e at q costs w_q-weighted squares of its differences:
+    # sum_d [w_{q-1} e^2 + w_q e^2] / n
+    t = y.copy()
+    t[0, 2, 3] += 1.0
+    l1, _ = unet.output_loss(y, t, "grad", w)
+    want = (w[2, 2] + w[2, 3] + w[1, 3] + w[2, 3]) / y.size
+    assert np.isclose(l1, want, rtol=1e-12)
