@@ -68,25 +68,19 @@ __device__ bool reduce_barrier(AccT (&acc)[K], double *partials, double *result,
     else block_reduce_store<K>(acc, partials + (size_t)bid * PSTRIDE);
     if (threadIdx.x == 0) {
         s_ok = 1;
-        volatile unsigned int *vgen = gen;
-        s_gen = *vgen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(count, 1u);
+        s_gen = ld_relaxed_gpu(gen);
+        const unsigned int arrived = atom_add_acq_rel_gpu(count, 1u);
         s_last = (arrived == (unsigned int)nbk - 1) ? 1 : 0;
     }
     __syncthreads();
     if (s_last && pairs) {
-        __threadfence();
         last_block_pairs<K>(partials, nbk, result);
         if (threadIdx.x == 0) {
-            __threadfence();
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
+            *count = 0u;
+            red_add_release_gpu(gen, 1u);
         }
     } else if (s_last) {
         if (threadIdx.x < 32) {
-            __threadfence();
             const int lane = threadIdx.x;
 #pragma unroll
             for (int k = 0; k < K; k++) {
@@ -96,15 +90,12 @@ __device__ bool reduce_barrier(AccT (&acc)[K], double *partials, double *result,
                 if (lane == 0) result[k] = sacc;
             }
             if (lane == 0) {
-                __threadfence();
-                atomicExch(count, 0u);
-                __threadfence();
-                atomicAdd(gen, 1u);
+                *count = 0u;
+                red_add_release_gpu(gen, 1u);
             }
         }
     } else if (threadIdx.x == 0) {
         if (!wait_generation(gen, s_gen, err, SPIN_LIMIT)) s_ok = 0;
-        __threadfence();
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -294,22 +294,51 @@ __device__ void last_block_sums(const double *partials, int nb, double *result)
     block_sum_store<K>(v, result);
 }
 
+// GPU-scope synchronisation primitives of the grid barrier: the arriving
+// thread's acq_rel add publishes its block's partial sums and, for the last
+// arrival, acquires every other block's; the last block's release add of the
+// generation word publishes the totals; waiters acquire it.  (Each is one
+// instruction; the fence-based protocol it replaces needed a full
+// __threadfence around every atomic.)
+__device__ __forceinline__ unsigned int ld_relaxed_gpu(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int *p, unsigned int v)
+{
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void red_add_release_gpu(unsigned int *p, unsigned int v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
 // Bounded wait of one thread for a generation word to move past g: at most
-// `limit` polls ~100 ns apart; on expiry PF_ETIMEOUT (6) goes to *err and
-// false is returned, so the kernel can leave with the context intact.  The
-// grid barrier of the PCG and its self-test (pf_selftest_wait) use it.
+// `limit` polls ~32 ns apart (plus the load latency); on expiry PF_ETIMEOUT
+// (6) goes to *err and false is returned, so the kernel can leave with the
+// context intact.  The grid barrier of the PCG and its self-test
+// (pf_selftest_wait) use it.
 constexpr long long SPIN_LIMIT = 1LL << 24;
 
 __device__ __forceinline__ bool wait_generation(const unsigned int *gen, unsigned int g, int *err, long long limit)
 {
-    const volatile unsigned int *vgen = gen;
     long long spins = 0;
-    while (*vgen == g) {
+    while (ld_acquire_gpu(gen) == g) {
         if (++spins > limit) {
             atomicExch(err, 6);
             return false;
         }
-        __nanosleep(100);
+        __nanosleep(32);
     }
     return true;
 }
