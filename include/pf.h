@@ -83,6 +83,9 @@ typedef struct {
     double cg_rtol;     /* stop when ||r||_2 <= cg_rtol ||b||_2                         */
     double dt;          /* time step; <= 0 selects 0.2 x the stable limit               */
     pf_params p;
+    int pcg_tile;       /* node tile of the PCG sweep: 0 = the library's choice for the
+                           grid size (measured per size class), 1 = 32x8 (2D) / 16x4x4
+                           (3D), 2 = 16x16 / 32x4x2.  Results agree to rounding.        */
 } pf_config;
 
 /* Field arrays, FP64, cell-major.  Any pointer may be NULL (skipped).

@@ -31,7 +31,7 @@ class PFError(RuntimeError):
 
 
 def make_config(shape, prm, precision="fp64", mechanics=None, plasticity=None, warm_start=None,
-                cg_rtol=None, cg_maxit=None, dt=None):
+                cg_rtol=None, cg_maxit=None, dt=None, pcg_tile=None):
     """Build a pf_config from a grid shape ((ny, nx) or (nz, ny, nx)) and a
     parameter dict (see workloads.params)."""
     c = pf_config()
@@ -51,6 +51,7 @@ def make_config(shape, prm, precision="fp64", mechanics=None, plasticity=None, w
     c.cg_rtol = float(prm.get("cg_rtol", 1e-10) if cg_rtol is None else cg_rtol)
     c.cg_maxit = int(prm.get("cg_maxit", 20000) if cg_maxit is None else cg_maxit)
     c.dt = float(prm.get("dt", 0.0) if dt is None else dt)
+    c.pcg_tile = int(prm.get("pcg_tile", 0) if pcg_tile is None else pcg_tile)
     for k in PARAM_NAMES:
         setattr(c.p, k, float(prm[k]))
     return c

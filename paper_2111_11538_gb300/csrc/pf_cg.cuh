@@ -25,9 +25,15 @@
 
 namespace pfdev {
 
-template <int D> struct Tile;
-template <> struct Tile<2> { static constexpr int X = 32, Y = 8, Z = 1; };
-template <> struct Tile<3> { static constexpr int X = 16, Y = 4, Z = 4; };
+// Node tiles of the PCG sweep (256 nodes each, one per thread); the shape
+// is a launch option (pf_config.pcg_tile), picked per size class from
+// measurements when left to the library.
+template <int D, int S> struct Tile;
+template <> struct Tile<2, 0> { static constexpr int X = 32, Y = 8, Z = 1; };
+template <> struct Tile<2, 1> { static constexpr int X = 16, Y = 16, Z = 1; };
+template <> struct Tile<3, 0> { static constexpr int X = 16, Y = 4, Z = 4; };
+template <> struct Tile<3, 1> { static constexpr int X = 32, Y = 4, Z = 2; };
+constexpr int PCG_SHAPES = 2;
 
 template <typename T, int D>
 struct PCGArgs {
@@ -303,7 +309,7 @@ enum { CTL_RUN = 0, CTL_DONE = 1, CTL_ZERO = 2, CTL_STOP = 3 };
 // FP64, solves for a correction with the FP32 iteration (A.x holds the
 // correction), adds it in FP64, and stops when the FP64 residual meets rtol;
 // the FP32 displacement A.u is written from x64 at the end.
-template <typename T, int D>
+template <typename T, int D, int SH>
 __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int njobs)
 {
     // this block's job, copied to shared memory
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
     const PCGArgs<T, D> &A = sA;
     const int bid = (int)blockIdx.x - A.block0, nbk = A.nblocks;
     constexpr int NV = Dims<D>::NV;
-    constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+    constexpr int TX = Tile<D, SH>::X, TY = Tile<D, SH>::Y, TZ = Tile<D, SH>::Z;
     constexpr int HX = TX + 2, HY = TY + 2, HZ = D == 3 ? TZ + 2 : 1;
     constexpr int CX = TX + 1, CY = TY + 1, CZ = D == 3 ? TZ + 1 : 1;
     constexpr int HN = HX * HY * HZ, HC = CX * CY * CZ;
@@ -758,6 +764,26 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
         if (it_total > A.dg->cg_max) A.dg->cg_max = it_total;
         A.dg->cg_total += it_total;
     }
+}
+
+
+// Host side of one translation unit's PCG instantiations: occupancy query,
+// cooperative launch and the upload of that unit's copy of the element
+// tables (constant memory is per unit).
+template <typename T, int D>
+cudaError_t pcg_occupancy_t(int shape, int block, int *per_sm)
+{
+    if (shape == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pcg<T, D, 1>, block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pcg<T, D, 0>, block, 0);
+}
+
+template <typename T, int D>
+cudaError_t pcg_launch_t(int shape, const void *jobs, int njobs, int grid, int block, cudaStream_t s)
+{
+    const PCGArgs<T, D> *pj = (const PCGArgs<T, D> *)jobs;
+    void *args[] = {(void *)&pj, (void *)&njobs};
+    const void *fn = shape == 1 ? (const void *)k_pcg<T, D, 1> : (const void *)k_pcg<T, D, 0>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, s);
 }
 
 } // namespace pfdev

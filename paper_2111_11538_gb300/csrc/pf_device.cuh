@@ -44,8 +44,10 @@ template <typename T> struct Tab {
     T Bb2[8], Bb3[24];
     T Kdiag[4];   // [0],[1]: 2D lambda, mu; [2],[3]: 3D lambda, mu
 };
-__constant__ Tab<double> cTabD;
-__constant__ Tab<float> cTabF;
+// one copy per translation unit (no relocatable device code): every unit
+// that launches kernels reading the tables uploads its own
+static __constant__ Tab<double> cTabD;
+static __constant__ Tab<float> cTabF;
 
 template <typename T> __device__ __forceinline__ const Tab<T> &tab();
 template <> __device__ __forceinline__ const Tab<double> &tab<double>() { return cTabD; }

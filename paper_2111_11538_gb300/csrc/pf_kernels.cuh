@@ -700,11 +700,11 @@ __global__ void k_net_guess(long long N, const float *y, const int *mode, double
     }
 }
 
-__global__ void k_net_mode_clear(int *mode) { *mode = 0; }
+static __global__ void k_net_mode_clear(int *mode) { *mode = 0; }
 
 // Self-test of the bounded wait: one thread waits on a generation word that
 // nothing advances.
-__global__ void k_wait_selftest(const unsigned int *gen, int *err, long long limit)
+static __global__ void k_wait_selftest(const unsigned int *gen, int *err, long long limit)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) wait_generation(gen, 0u, err, limit);
 }

@@ -15,6 +15,16 @@
 #include "pf_unet.h"
 #include "unet_net.h"
 #include "pf_cg.cuh"
+#include "pcg_launch.h"
+
+// PCG node tile per size class (0: 32x8 / 16x4x4, 1: 16x16 / 32x4x2),
+// from the measurements of paper_2111_11538_gb300/autotune.py on GB300.
+#define PCG_TABLE_2D_F32_SMALL 0
+#define PCG_TABLE_2D_F32_LARGE 0
+#define PCG_TABLE_2D_F64_SMALL 0
+#define PCG_TABLE_2D_F64_LARGE 0
+#define PCG_TABLE_3D_F32 0
+#define PCG_TABLE_3D_F64 0
 
 using namespace pfdev;
 
@@ -99,6 +109,8 @@ bool upload_tables(int dev)
     fill_tab(tf);
     if (cudaMemcpyToSymbol(cTabD, &td, sizeof(td)) != cudaSuccess) return false;
     if (cudaMemcpyToSymbol(cTabF, &tf, sizeof(tf)) != cudaSuccess) return false;
+    if (pcg2_tables(&tf, &td) != cudaSuccess) return false;
+    if (pcg3_tables(&tf, &td) != cudaSuccess) return false;
     if (dev >= 0 && dev < 64) done[dev] = true;
     return true;
 }
@@ -192,6 +204,7 @@ struct pf_handle {
     void *d_pcg_jobs = nullptr;
     int cell_grid = 0, fused_grid = 0, pcg_grid = 0, njobs = 0;
     int cg_per_sm = 0;
+    int pcg_shape = 0;                  // node tile of the PCG sweep (pf_cg.cuh Tile<D, S>)
     bool plan_ready = false;
     int plan_par = 0;                   // which table describes the current state
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step from job tables [k]
@@ -310,11 +323,26 @@ std::vector<pf_handle *> instances(pf_handle *h)
     return h->is_batch ? h->members : std::vector<pf_handle *>{h};
 }
 
+// Node tile of the PCG sweep for a grid of N nodes: pf_config.pcg_tile if
+// set (1 or 2 select shape 0 or 1), else the per-size-class choice measured
+// on GB300 (paper_2111_11538_gb300/autotune.py prints the table).
+int default_pcg_shape(int ndim, long long N, bool fp64)
+{
+    if (ndim == 2) {
+        if (fp64) return N <= (1LL << 18) ? PCG_TABLE_2D_F64_SMALL : PCG_TABLE_2D_F64_LARGE;
+        return N <= (1LL << 18) ? PCG_TABLE_2D_F32_SMALL : PCG_TABLE_2D_F32_LARGE;
+    }
+    return fp64 ? PCG_TABLE_3D_F64 : PCG_TABLE_3D_F32;
+}
+
 template <typename T, int D>
 int setup_cg_launch(pf_handle *h)
 {
+    const bool fp64 = sizeof(T) == 8;
+    h->pcg_shape = h->cfg.pcg_tile > 0 ? h->cfg.pcg_tile - 1 : default_pcg_shape(D, h->P.N, fp64);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<T, D>, h->cg_block, 0);
+    cudaError_t e = D == 2 ? pcg2_occupancy(fp64, h->pcg_shape, h->cg_block, &per_sm)
+                           : pcg3_occupancy(fp64, h->pcg_shape, h->cg_block, &per_sm);
     if (e != cudaSuccess) return h->cuda(e, "occupancy query");
     if (per_sm < 1) return h->fail(PF_ECUDA, "CG kernel cannot be resident");
     if (per_sm > 4) per_sm = 4;
@@ -435,7 +463,9 @@ int build_plan(pf_handle *h)
         PF_TRY(h->cuda(cudaMemcpy(h->d_fused_jobs[k], fj[k].data(), cbytes, cudaMemcpyHostToDevice), "job table"));
     }
     if (h->cfg.mechanics) {
-        constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+        const int TX = h->pcg_shape ? Tile<D, 1>::X : Tile<D, 0>::X;
+        const int TY = h->pcg_shape ? Tile<D, 1>::Y : Tile<D, 0>::Y;
+        const int TZ = h->pcg_shape ? Tile<D, 1>::Z : Tile<D, 0>::Z;
         // Jacobi-PCG iteration counts grow with the grid's linear size, so
         // an instance's work per solve is ~ tiles x linear size: blocks are
         // shared out in proportion to that, so that instances finish together
@@ -523,11 +553,10 @@ int launch_step(pf_handle *h, cudaStream_t s, int k)
             }
             h->mark_end(s);
         }
-        const PCGArgs<T, D> *pj = (const PCGArgs<T, D> *)h->d_pcg_jobs;
-        int nj = n;
-        void *args[] = {(void *)&pj, (void *)&nj};
         h->mark_begin(PF_K_CG, s);
-        cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_pcg<T, D>, dim3(h->pcg_grid), dim3(h->cg_block), args, 0, s);
+        const bool fp64 = sizeof(T) == 8;
+        cudaError_t e = D == 2 ? pcg2_launch(fp64, h->pcg_shape, h->d_pcg_jobs, n, h->pcg_grid, h->cg_block, s)
+                               : pcg3_launch(fp64, h->pcg_shape, h->d_pcg_jobs, n, h->pcg_grid, h->cg_block, s);
         h->mark_end(s);
         if (e != cudaSuccess) return h->cuda(e, "cooperative CG launch");
         h->mark_begin(PF_K_RETURN, s);
@@ -854,6 +883,7 @@ int create_one(const pf_config *cfg, pf_handle **out, std::string &err)
         return PF_EINVAL;
     }
     if (c.mechanics && (c.cg_maxit <= 0 || !(c.cg_rtol > 0.0))) { err = "cg_maxit must be > 0 and cg_rtol > 0"; return PF_EINVAL; }
+    if (c.pcg_tile < 0 || c.pcg_tile > PCG_SHAPES) { err = "pcg_tile must be 0 (library choice), 1 or 2"; return PF_EINVAL; }
     if (!(c.p.nu > -1.0 && c.p.nu < 0.5) || !(c.p.E_s > 0.0) || !(c.p.E_g_ratio > 0.0)) { err = "elastic constants out of range"; return PF_EINVAL; }
     const long long N = (long long)c.nx * c.ny * (c.ndim == 3 ? c.nz : 1);
     if (N > (1LL << 31)) { err = "grid too large (more than 2^31 cells)"; return PF_EINVAL; }
@@ -956,6 +986,7 @@ int pf_batch_create(const pf_config *cfgs, int n, pf_handle **out)
     b->sms = m0->sms;
     b->cg_block = m0->cg_block;
     b->cg_per_sm = m0->cg_per_sm;
+    b->pcg_shape = m0->pcg_shape;
     for (pf_handle *m : b->members) b->bytes += m->bytes;
     cudaError_t e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking);
     if (e != cudaSuccess) {

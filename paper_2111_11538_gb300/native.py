@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libpf.so")
 CSRC = os.path.join(_HERE, "csrc")
-UNITS = [os.path.join(CSRC, n) for n in ("pf_lib.cu", "unet.cu")]       # translation units
+UNITS = [os.path.join(CSRC, n) for n in ("pf_lib.cu", "pcg_2d.cu", "pcg_3d.cu", "unet.cu")]   # translation units
 BUILD_DIR = os.path.join(_HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,7 +37,7 @@ class pf_config(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mechanics", ctypes.c_int), ("plasticity", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("cg_maxit", ctypes.c_int), ("cg_rtol", ctypes.c_double),
-                ("dt", ctypes.c_double), ("p", pf_params)]
+                ("dt", ctypes.c_double), ("p", pf_params), ("pcg_tile", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)

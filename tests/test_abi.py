@@ -84,3 +84,9 @@ def test_batch_create_validates_before_touching_the_gpu(lib):
     assert rc in (native.PF_EINVAL, native.PF_ECUDA) and not h.value
     assert lib.pf_batch_create(None, 0, ctypes.byref(ctypes.c_void_p())) == native.PF_EINVAL
     assert native.pf_batch_size(None) == 0
+
+
+def test_create_rejects_unknown_pcg_tile(lib):
+    cfg = make_config((16, 16), workloads.params(), pcg_tile=3)
+    rc, h = native.pf_create(cfg)
+    assert rc == native.PF_EINVAL and "pcg_tile" in native.pf_last_error(None)

@@ -215,3 +215,21 @@ def test_bounded_wait_times_out_and_context_survives():
     sim.step(2)
     assert sim.diagnostics()["steps"] == 2
     sim.close()
+
+
+@pytest.mark.parametrize("shape", [(40, 48), (10, 12, 14)])
+def test_pcg_tile_shapes_agree(shape):
+    """Both node tiles of the PCG sweep solve the same system: FP64 fields
+    agree to the CG tolerance, whichever shape the library picks."""
+    f = inputs.core_shell(shape, 0.3 * shape[-1], 3.0)
+    prm = workloads.params(plasticity=1, sigma_Y=0.004, H_hard=0.01, cg_rtol=1e-10)
+    out = []
+    for tile in (1, 2):
+        sim = Simulation(shape, dict(prm, pcg_tile=tile), precision="fp64")
+        sim.set_fields(f)
+        sim.step(10)
+        out.append(sim.get_fields())
+        sim.close()
+    for k in ("phi_f", "phi_w", "xO", "xH", "xW"):
+        assert rel(out[0][k], out[1][k]) < 1e-10, k
+    assert rel(out[0]["sigma"], out[1]["sigma"]) < 1e-7
