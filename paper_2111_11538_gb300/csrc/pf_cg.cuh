@@ -352,9 +352,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
     struct State {
         double XE[6];      // mean strain of x (plain) / of the correction (refine)
         double E64[6];     // FP64 mean strain of the solution (refine)
-        double DiagE[6], RE[6], UE[6], PE[6], SE[6], WE[6];
+        double DiagE[6], invDiagE[6], RE[6], UE[6], PE[6], SE[6], WE[6];
         double Sl, Sm, bnorm, rho_final, target, prev_res;
         double gamma, delta, gamma_prev, alpha_prev, alpha, beta;
+        double inv_gamma, inv_gamma_prev, inv_alpha, inv_alpha_prev;   // FP64 divisions are slow here
         int it, it_total, conv;
     };
     __shared__ State S;
@@ -369,6 +370,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
         Sl = Sm = bnorm = rho_final = target = 0.0;
         gamma = delta = alpha = beta = 0.0;
         gamma_prev = alpha_prev = 1.0;
+        S.inv_gamma = S.inv_gamma_prev = S.inv_alpha = S.inv_alpha_prev = 1.0;
         it = 0;
         it_total = 0;
         if (A.warm)
@@ -436,13 +438,14 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                     for (int w = 0; w < NV; w++) unit[w] = (w == vv) ? 1.0 : 0.0;
                     dmat_mul<D>(Sl, Sm, unit, s6);
                     DiagE[vv] = s6[vv];
+                    S.invDiagE[vv] = 1.0 / s6[vv];
                 }
                 dmat_mul<D>(Sl, Sm, refine ? E64 : XE, AXE);
                 double bbt = tot[0], rho = tot[1];
                 for (int vv = 0; vv < NV; vv++) {
                     const double BE = tot[4 + vv] + (vv < D ? (double)N * (-P.prestress) : 0.0);
                     RE[vv] = BE - (use_x ? tot[10 + vv] + AXE[vv] : 0.0);
-                    UE[vv] = RE[vv] / DiagE[vv];
+                    UE[vv] = RE[vv] * S.invDiagE[vv];
                     bbt += BE * BE;
                     rho += RE[vv] * RE[vv];
                     PE[vv] = 0.0;
@@ -462,6 +465,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                 // mode what an FP32 iteration can deliver on this correction
                 target = refine ? fmax(0.5 * A.rtol * bnorm, A.eta * sqrt(rho)) : A.rtol * bnorm;
                 gamma = 0.0; delta = 0.0; gamma_prev = 1.0; alpha_prev = 1.0; alpha = 0.0; beta = 0.0;
+                S.inv_gamma = S.inv_gamma_prev = S.inv_alpha = S.inv_alpha_prev = 1.0;
                 it = 0;
                 s_ctl = ctl;
             }
@@ -490,14 +494,19 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
         while (true) {
             if (lead) {
                 if (!first) {
-                    beta = (it == 0) ? 0.0 : gamma / gamma_prev;
-                    alpha = (it == 0) ? gamma / delta : gamma / (delta - beta * gamma / alpha_prev);
+                    // beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev):
+                    // one division here (1/alpha = den / gamma reuses 1/gamma)
+                    // and one for 1/gamma after the reduction
+                    beta = (it == 0) ? 0.0 : gamma * S.inv_gamma_prev;
+                    const double den = (it == 0) ? delta : delta - beta * gamma * S.inv_alpha_prev;
+                    alpha = gamma / den;
+                    S.inv_alpha = den * S.inv_gamma;
                     for (int vv = 0; vv < NV; vv++) {
                         PE[vv] = UE[vv] + beta * PE[vv];
                         SE[vv] = WE[vv] + beta * SE[vv];
                         XE[vv] += alpha * PE[vv];
                         RE[vv] -= alpha * SE[vv];
-                        UE[vv] = RE[vv] / DiagE[vv];
+                        UE[vv] = RE[vv] * S.invDiagE[vv];
                     }
                 }
                 s_ta = (T)alpha;
@@ -708,15 +717,19 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                 if (was_first) {
                     gamma = gnew;
                     delta = dnew;
+                    S.inv_gamma = 1.0 / gnew;
                 } else {
                     it++;
                     rho_final = rnew;
-                    if (sqrt(rnew) <= target) ctl = CTL_DONE;
+                    if (rnew <= target * target) ctl = CTL_DONE;      // ||r|| <= target without a square root
                     else if (it_total + it >= A.maxit) ctl = CTL_STOP;
                     gamma_prev = gamma;
                     alpha_prev = alpha;
+                    S.inv_gamma_prev = S.inv_gamma;
+                    S.inv_alpha_prev = S.inv_alpha;
                     gamma = gnew;
                     delta = dnew;
+                    S.inv_gamma = 1.0 / gnew;
                 }
                 s_ctl = ctl;
             }
