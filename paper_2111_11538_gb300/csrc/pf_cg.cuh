@@ -199,6 +199,73 @@ __device__ __forceinline__ void node_force2(int a, const TC *s, const TC *fh, TC
     f[1] = by * s[1] + bx * s[2] + g * fh[1];
 }
 
+// 3D Q1 hex with constant moduli, exact form of its stiffness (the
+// counterpart of the 2D decomposition): per displacement component the
+// trilinear field of a unit cell is its mean, its average gradient G and the
+// modes h1 = xi eta, h2 = eta zeta, h3 = zeta xi, h4 = xi eta zeta (centred
+// coordinates).  2x2x2 Gauss integration of the strain energy splits into
+// Bbar^T D eps(G) and a quadratic form in the twelve h coefficients whose
+// gradient (with respect to h) gives the hourglass forces; the cross terms
+// integrate to zero.  cell_force3 returns, in c[20]: the average stress
+// (Voigt xx yy zz yz xz xy, without the mean strain) in c[0..5] and the
+// forces g[k][comp] = dE/dh_k,comp in c[6 + 3k + comp]; c[18..19] pad.
+template <typename TC>
+__device__ __forceinline__ void cell_force3(TC l, TC m, const TC (&ue)[8][3], TC (&c)[20])
+{
+    TC G[3][3], h[4][3];     // G[comp][dir], h[mode][comp]
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        // node b = bx + 2 by + 4 bz; pairs along x
+        const TC e00 = ue[0][k] + ue[1][k], d00 = ue[1][k] - ue[0][k];
+        const TC e01 = ue[2][k] + ue[3][k], d01 = ue[3][k] - ue[2][k];
+        const TC e10 = ue[4][k] + ue[5][k], d10 = ue[5][k] - ue[4][k];
+        const TC e11 = ue[6][k] + ue[7][k], d11 = ue[7][k] - ue[6][k];
+        G[k][0] = TC(0.25) * ((d00 + d01) + (d10 + d11));
+        G[k][1] = TC(0.25) * ((e01 + e11) - (e00 + e10));
+        G[k][2] = TC(0.25) * ((e10 + e11) - (e00 + e01));
+        h[0][k] = TC(0.5) * ((d01 + d11) - (d00 + d10));     // sx sy
+        h[1][k] = TC(0.5) * ((e11 - e10) - (e01 - e00));     // sy sz
+        h[2][k] = TC(0.5) * ((d10 + d11) - (d00 + d01));     // sz sx
+        h[3][k] = (d11 - d10) - (d01 - d00);                 // sx sy sz
+    }
+    const TC tr = G[0][0] + G[1][1] + G[2][2];
+    c[0] = l * tr + TC(2) * m * G[0][0];
+    c[1] = l * tr + TC(2) * m * G[1][1];
+    c[2] = l * tr + TC(2) * m * G[2][2];
+    c[3] = m * (G[1][2] + G[2][1]);
+    c[4] = m * (G[0][2] + G[2][0]);
+    c[5] = m * (G[0][1] + G[1][0]);
+    const TC A = h[0][1] + h[2][2], B = h[0][0] + h[1][2], C = h[2][0] + h[1][1];
+    const TC Pq = h[1][0] + h[2][1], Q = h[2][1] + h[0][2], R = h[0][2] + h[1][0];
+    const TC c12 = TC(1.0 / 12.0), m3 = TC(3) * m, c144 = (l + TC(4) * m) * TC(1.0 / 144.0);
+    c[6] = (l * B + m3 * h[0][0]) * c12;       // mode 1, x
+    c[7] = (l * A + m3 * h[0][1]) * c12;       // mode 1, y
+    c[8] = m * (Q + R) * c12;                  // mode 1, z
+    c[9] = m * (Pq + R) * c12;                 // mode 2, x
+    c[10] = (l * C + m3 * h[1][1]) * c12;      // mode 2, y
+    c[11] = (l * B + m3 * h[1][2]) * c12;      // mode 2, z
+    c[12] = (l * C + m3 * h[2][0]) * c12;      // mode 3, x
+    c[13] = m * (Pq + Q) * c12;                // mode 3, y
+    c[14] = (l * A + m3 * h[2][2]) * c12;      // mode 3, z
+    c[15] = c144 * h[3][0];
+    c[16] = c144 * h[3][1];
+    c[17] = c144 * h[3][2];
+    c[18] = TC(0);
+    c[19] = TC(0);
+}
+
+// force on the node at corner (ax, ay, az) of a 3D cell from its average
+// stress s (mean strain included) and hourglass forces g = c + 6
+template <typename TC>
+__device__ __forceinline__ void node_force3(int ax, int ay, int az, const TC *s, const TC *g, TC (&f)[3])
+{
+    const TC sx = ax ? TC(1) : TC(-1), sy = ay ? TC(1) : TC(-1), sz = az ? TC(1) : TC(-1);
+    const TC w1 = TC(0.5) * sx * sy, w2 = TC(0.5) * sy * sz, w3 = TC(0.5) * sz * sx, w4 = sx * sy * sz;
+    f[0] = TC(0.25) * (sx * s[0] + sy * s[5] + sz * s[4]) + w1 * g[0] + w2 * g[3] + w3 * g[6] + w4 * g[9];
+    f[1] = TC(0.25) * (sy * s[1] + sx * s[5] + sz * s[3]) + w1 * g[1] + w2 * g[4] + w3 * g[7] + w4 * g[10];
+    f[2] = TC(0.25) * (sz * s[2] + sy * s[3] + sx * s[4]) + w1 * g[2] + w2 * g[5] + w3 * g[8] + w4 * g[11];
+}
+
 // Per-node part of the solve's set-up: right-hand side b = sum_e Bbar^T sig*,
 // Jacobi diagonal, A x (element tables + mean-strain coupling XE) and the own
 // cell's quantities.  TC is the arithmetic type, TV the type of x.
@@ -331,7 +398,13 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
     constexpr int MAX_OUTER = 24;
     __shared__ T su[D * HN];
     __shared__ T sl[HC], sm[HC];
-    __shared__ T scell[D == 2 ? 5 * HC : 1];     // 2D: per-cell stress and hourglass forces
+    // per-cell stress and hourglass forces: 2D 5 values per cell; 3D FP32 on
+    // the 16x4x4 tile 20 (five float4); other 3D variants use the
+    // element-matrix path and need none
+    constexpr bool CELL3 = D == 3 && sizeof(T) == 4 && SH == 0;
+    __shared__ __align__(16) T scell2[D == 2 ? 5 * HC : 1];
+    extern __shared__ __align__(16) unsigned char pcg_dyn[];   // CELL3: 20 * HC floats (pcg_dyn_smem)
+    T *scell = CELL3 ? reinterpret_cast<T *>(pcg_dyn) : scell2;
     __shared__ T s_ta, s_tb, s_ue[6], s_xe[6];
     __shared__ int s_ctl;
 
@@ -611,6 +684,31 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                 // issue the next tile's loads; they complete while this one computes
                 if (tile + nbk < ntiles) load_raw(tile + nbk, R);
                 __syncthreads();
+                if constexpr (CELL3) {
+                    // per halo cell: average stress (mean strain UE included)
+                    // and the twelve hourglass forces, shared by its 8 nodes
+                    for (int h = threadIdx.x; h < HC; h += blockDim.x) {
+                        const int cx = h % CX, cy = (h / CX) % CY, cz = h / (CX * CY);
+                        T uc[8][3];
+#pragma unroll
+                        for (int b = 0; b < 8; b++) {
+                            const int hn = (cx + (b & 1)) + HX * ((cy + ((b >> 1) & 1)) + HY * (cz + (b >> 2)));
+                            uc[b][0] = su[hn];
+                            uc[b][1] = su[HN + hn];
+                            uc[b][2] = su[2 * HN + hn];
+                        }
+                        const T l = sl[h], m = sm[h];
+                        T c[20], sx[6];
+                        cell_force3<T>(l, m, uc, c);
+                        voigt_stress<T, 3>(l, m, ue, sx);
+#pragma unroll
+                        for (int v = 0; v < 6; v++) c[v] += sx[v];
+                        float4 *dst = reinterpret_cast<float4 *>(scell + 20 * h);
+#pragma unroll
+                        for (int q4 = 0; q4 < 5; q4++) dst[q4] = make_float4(c[4 * q4], c[4 * q4 + 1], c[4 * q4 + 2], c[4 * q4 + 3]);
+                    }
+                    __syncthreads();
+                }
                 if constexpr (D == 2) {
                     // per halo cell: average stress (mean strain UE included)
                     // and hourglass forces, shared by the cell's four nodes
@@ -683,6 +781,32 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                         se[0] = scell[c0] - sx[0];
                         se[1] = scell[HC + c0] - sx[1];
                         se[2] = scell[2 * HC + c0] - sx[2];
+                    } else if constexpr (CELL3) {
+                        q[0] = q[1] = q[2] = T(0);
+#pragma unroll
+                        for (int a = 0; a < 8; a++) {
+                            const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+                            const int cl = (lx - ax) + CX * ((ly - ay) + CY * (lz - az));
+                            const float4 *src = reinterpret_cast<const float4 *>(scell + 20 * cl);
+                            T c[20];
+#pragma unroll
+                            for (int q4 = 0; q4 < 5; q4++) {
+                                const float4 v = src[q4];
+                                c[4 * q4] = v.x; c[4 * q4 + 1] = v.y; c[4 * q4 + 2] = v.z; c[4 * q4 + 3] = v.w;
+                            }
+                            T f[3];
+                            node_force3<T>(ax, ay, az, c, c + 6, f);
+                            q[0] += f[0];
+                            q[1] += f[1];
+                            q[2] += f[2];
+                            if (a == 0) {
+                                // own cell's average stress without the mean strain
+                                T sx[6];
+                                voigt_stress<T, 3>(sl[cl], sm[cl], ue, sx);
+#pragma unroll
+                                for (int v = 0; v < 6; v++) se[v] = c[v] - sx[v];
+                            }
+                        }
                     } else {
                         T eo[NV], lo, mo;
                         apply_tile<T, D, HX, HY, CX, CY>(su, sl, sm, HN, lx, ly, lz, ue, q, eo, lo, mo);
@@ -782,12 +906,26 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
 
 // Host side of one translation unit's PCG instantiations: occupancy query,
 // cooperative launch and the upload of that unit's copy of the element
-// tables (constant memory is per unit).
+// tables (constant memory is per unit).  Dynamic shared memory: the 3D FP32
+// cell buffer of the 16x4x4 tile.
+template <typename T, int D>
+size_t pcg_dyn_smem(int shape)
+{
+    if (D != 3 || sizeof(T) != 4 || shape != 0) return 0;
+    constexpr int HC = (Tile<3, 0>::X + 1) * (Tile<3, 0>::Y + 1) * (Tile<3, 0>::Z + 1);
+    return sizeof(float) * 20 * HC;
+}
+
 template <typename T, int D>
 cudaError_t pcg_occupancy_t(int shape, int block, int *per_sm)
 {
-    if (shape == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pcg<T, D, 1>, block, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pcg<T, D, 0>, block, 0);
+    const void *fn = shape == 1 ? (const void *)k_pcg<T, D, 1> : (const void *)k_pcg<T, D, 0>;
+    const size_t dyn = pcg_dyn_smem<T, D>(shape);
+    if (dyn) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, block, dyn);
 }
 
 template <typename T, int D>
@@ -796,7 +934,7 @@ cudaError_t pcg_launch_t(int shape, const void *jobs, int njobs, int grid, int b
     const PCGArgs<T, D> *pj = (const PCGArgs<T, D> *)jobs;
     void *args[] = {(void *)&pj, (void *)&njobs};
     const void *fn = shape == 1 ? (const void *)k_pcg<T, D, 1> : (const void *)k_pcg<T, D, 0>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, pcg_dyn_smem<T, D>(shape), s);
 }
 
 } // namespace pfdev
