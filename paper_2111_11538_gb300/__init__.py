@@ -110,18 +110,26 @@ def _in_fields(fields, where, N, ndim):
     return f, keep
 
 
-def _out_fields(keys, shape):
-    """pf_fields pointing at fresh numpy arrays for the requested keys."""
+def _out_fields(keys, shape, out=None):
+    """pf_fields pointing at arrays for the requested keys: the caller's
+    (float64, C-contiguous, of the field's shape; pinned host memory makes
+    the copies direct) where `out` has them, fresh numpy arrays otherwise."""
     ndim = len(shape)
     npl = 4 if ndim == 2 else 6
     nv = 3 if ndim == 2 else 6
     shp = {"u": shape + (ndim,), "eps_p": shape + (npl,), "sigma": shape + (npl,), "Ebar": (nv,)}
     f = pf_fields()
-    out = {}
+    res = {}
     for k in keys:
-        out[k] = np.zeros(shp.get(k, shape))
-        setattr(f, _NAMES[k], _dptr(out[k]))
-    return f, out
+        want = shp.get(k, shape)
+        a = out.get(k) if out is not None else None
+        if a is None:
+            a = np.zeros(want)
+        elif a.dtype != np.float64 or not a.flags.c_contiguous or a.size != int(np.prod(want)):
+            raise ValueError("out[%r] must be a C-contiguous float64 array of %d values" % (k, int(np.prod(want))))
+        res[k] = a
+        setattr(f, _NAMES[k], _dptr(a))
+    return f, res
 
 
 class Simulation:
@@ -162,10 +170,12 @@ class Simulation:
             self._check(rc)
         return rc
 
-    def get_fields(self, keys=FIELD_KEYS):
-        f, out = _out_fields(keys, self.shape)
+    def get_fields(self, keys=FIELD_KEYS, out=None):
+        """Fields as numpy arrays; with `out` (a dict of preallocated arrays,
+        e.g. pinned host memory) the copies land there."""
+        f, res = _out_fields(keys, self.shape, out)
         self._check(native.pf_get_fields(self.h, f, PF_HOST))
-        return out
+        return res
 
     def diagnostics(self):
         rc, d = native.pf_get_diagnostics(self.h)
@@ -259,10 +269,10 @@ class Batch:
             self._check(rc)
         return rc
 
-    def get_fields(self, i, keys=FIELD_KEYS):
-        f, out = _out_fields(keys, self.shapes[i])
+    def get_fields(self, i, keys=FIELD_KEYS, out=None):
+        f, res = _out_fields(keys, self.shapes[i], out)
         self._check(native.pf_batch_get_fields(self.h, i, f, PF_HOST))
-        return out
+        return res
 
     def diagnostics(self, i):
         rc, d = native.pf_batch_get_diagnostics(self.h, i)

@@ -252,3 +252,22 @@ def test_pcg_3d_cell_path_matches_matrix_path():
     for k in ("phi_f", "phi_w", "xO", "xH", "xW"):
         assert rel(out[0][k], out[1][k]) < 1e-6, (k, rel(out[0][k], out[1][k]))
     assert rel(out[0]["sigma"], out[1]["sigma"]) < 1e-4
+
+
+def test_get_fields_into_caller_arrays():
+    """get_fields(out=...) fills the caller's arrays (the end-to-end bench
+    passes pinned host memory) with what a plain get_fields returns."""
+    shape = (24, 20)
+    sim = Simulation(shape, workloads.params(plasticity=1), precision="mixed")
+    sim.set_fields(inputs.core_shell(shape, 7.0, 2.0))
+    sim.step(3)
+    keys = ("phi_f", "xO", "u", "eps_p", "Ebar")
+    ref = sim.get_fields(keys=keys)
+    out = {k: np.full_like(v, -7.0) for k, v in ref.items()}
+    got = sim.get_fields(keys=keys, out=out)
+    for k in keys:
+        assert got[k] is out[k]
+        assert np.array_equal(out[k], ref[k]), k
+    with pytest.raises(ValueError):
+        sim.get_fields(keys=("phi_f",), out={"phi_f": np.zeros(3)})
+    sim.close()
