@@ -85,7 +85,7 @@ typedef struct {
     pf_params p;
     int pcg_tile;       /* node tile of the PCG sweep: 0 = the library's choice for the
                            grid size (measured per size class), 1 = 32x8 (2D) / 16x4x4
-                           (3D), 2 = 16x16 / 32x4x2.  Results agree to rounding.        */
+                           (3D), 2 = 32x16 / 32x4x2.  Results agree to rounding.        */
 } pf_config;
 
 /* Field arrays, FP64, cell-major.  Any pointer may be NULL (skipped).

@@ -25,12 +25,14 @@
 
 namespace pfdev {
 
-// Node tiles of the PCG sweep (256 nodes each, one per thread); the shape
-// is a launch option (pf_config.pcg_tile), picked per size class from
-// measurements when left to the library.
+// Node tiles of the PCG sweep (one node per thread: the block has X*Y*Z
+// threads); the shape is a launch option (pf_config.pcg_tile), picked per
+// size class from measurements when left to the library.  The 32x16 tile
+// runs one 512-thread block per SM: fewer blocks in each grid reduction and
+// a smaller idle tail in the halo passes than two 256-thread blocks.
 template <int D, int S> struct Tile;
 template <> struct Tile<2, 0> { static constexpr int X = 32, Y = 8, Z = 1; };
-template <> struct Tile<2, 1> { static constexpr int X = 16, Y = 16, Z = 1; };
+template <> struct Tile<2, 1> { static constexpr int X = 32, Y = 16, Z = 1; };
 template <> struct Tile<3, 0> { static constexpr int X = 16, Y = 4, Z = 4; };
 template <> struct Tile<3, 1> { static constexpr int X = 32, Y = 4, Z = 2; };
 constexpr int PCG_SHAPES = 2;
@@ -376,8 +378,11 @@ enum { CTL_RUN = 0, CTL_DONE = 1, CTL_ZERO = 2, CTL_STOP = 3 };
 // FP64, solves for a correction with the FP32 iteration (A.x holds the
 // correction), adds it in FP64, and stops when the FP64 residual meets rtol;
 // the FP32 displacement A.u is written from x64 at the end.
+template <int D, int S>
+constexpr int tile_threads() { return Tile<D, S>::X * Tile<D, S>::Y * Tile<D, S>::Z; }
+
 template <typename T, int D, int SH>
-__global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int njobs)
+__global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, SH>()) k_pcg(const PCGArgs<T, D> *jobs, int njobs)
 {
     // this block's job, copied to shared memory
     __shared__ PCGArgs<T, D> sA;
@@ -597,7 +602,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
             // tile's halo (r, w, s, diag), cells (lam, mu) and own node are
             // issued before the current tile is staged and computed, so their
             // latency overlaps that work.
-            constexpr int HS = (HN + 255) / 256, CS = (HC + 255) / 256;
+            constexpr int NT = TX * TY * TZ;       // threads = tile nodes
+            constexpr int HS = (HN + NT - 1) / NT, CS = (HC + NT - 1) / NT;
             struct Raw {
                 T r[HS][D], w[HS][D], s[HS][D], dg[HS];
                 T l[CS], m[CS];
@@ -608,7 +614,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                 const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
 #pragma unroll
                 for (int k = 0; k < HS; k++) {
-                    const int h = threadIdx.x + 256 * k;
+                    const int h = threadIdx.x + NT * k;
                     if (h < HN) {
                         const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
                         const int g = hidx<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz, small);
@@ -625,7 +631,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                 }
 #pragma unroll
                 for (int k = 0; k < CS; k++) {
-                    const int h = threadIdx.x + 256 * k;
+                    const int h = threadIdx.x + NT * k;
                     if (h < HC) {
                         const int lx = h % CX, ly = (h / CX) % CY, lz = D == 3 ? h / (CX * CY) : 0;
                         const int g = hidx<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz, small);
@@ -658,7 +664,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                 // on the halo nodes, lam / mu on the halo cells
 #pragma unroll
                 for (int k = 0; k < HS; k++) {
-                    const int h = threadIdx.x + 256 * k;
+                    const int h = threadIdx.x + NT * k;
                     if (h < HN) {
                         const T inv = R.dg[k];
 #pragma unroll
@@ -671,7 +677,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg(const PCGArgs<T, D> *jobs, int n
                 }
 #pragma unroll
                 for (int k = 0; k < CS; k++) {
-                    const int h = threadIdx.x + 256 * k;
+                    const int h = threadIdx.x + NT * k;
                     if (h < HC) {
                         sl[h] = R.l[k];
                         sm[h] = R.m[k];

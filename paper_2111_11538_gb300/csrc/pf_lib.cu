@@ -17,11 +17,11 @@
 #include "pf_cg.cuh"
 #include "pcg_launch.h"
 
-// PCG node tile per size class (0: 32x8 / 16x4x4, 1: 16x16 / 32x4x2),
+// PCG node tile per size class (0: 32x8 / 16x4x4, 1: 32x16 / 32x4x2),
 // from the measurements of paper_2111_11538_gb300/autotune.py on GB300.
 #define PCG_TABLE_2D_F32_SMALL 0
 #define PCG_TABLE_2D_F32_LARGE 0
-#define PCG_TABLE_2D_F64_SMALL 0
+#define PCG_TABLE_2D_F64_SMALL 1
 #define PCG_TABLE_2D_F64_LARGE 0
 #define PCG_TABLE_3D_F32 0
 #define PCG_TABLE_3D_F64 0
@@ -340,6 +340,7 @@ int setup_cg_launch(pf_handle *h)
 {
     const bool fp64 = sizeof(T) == 8;
     h->pcg_shape = h->cfg.pcg_tile > 0 ? h->cfg.pcg_tile - 1 : default_pcg_shape(D, h->P.N, fp64);
+    h->cg_block = h->pcg_shape ? tile_threads<D, 1>() : tile_threads<D, 0>();     // one thread per tile node
     int per_sm = 0;
     cudaError_t e = D == 2 ? pcg2_occupancy(fp64, h->pcg_shape, h->cg_block, &per_sm)
                            : pcg3_occupancy(fp64, h->pcg_shape, h->cg_block, &per_sm);
