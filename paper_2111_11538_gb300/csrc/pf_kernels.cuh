@@ -57,6 +57,7 @@ struct CellJob {
     unsigned int *counter;   // last-block counter of the update
     Diag *dg;
     int block0, nblocks;
+    int strip_rows;          // unused by the current kernels
 };
 
 // Job of this block: the last job whose first block is <= blockIdx.x (jobs
@@ -640,6 +641,228 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && D == 2) ? 3 : 2) k_fus
         __threadfence();
         __shared__ double tot[6];
         last_block_sums<6>(partials, (int)nbk, tot);
+        if (threadIdx.x == 0) {
+            Diag *dg = sJ.dg;
+            dg->sumO = tot[0]; dg->sumH = tot[1]; dg->sumW = tot[2];
+            dg->removedW += tot[3];
+            dg->suppliedH += tot[4];
+            if (tot[5] > 0.0 && dg->status == 0) dg->status = 5;
+            *counter = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1 in 2D by column strips (k_fused_cm): the same arithmetic as k_fused,
+// without shared memory.  Warp w of the job walks strips of 32 lanes x
+// strip_rows rows; lane L holds column x0 - 1 + L (x0 = 30 * strip column),
+// so lanes 1..30 are the strip's output columns and lanes 0 and 31 its halo.
+// Every lane evaluates mu_O, M_O and the diffusivities of its own column in
+// a three-row register window (x_O at the lane's left/right from shuffles,
+// from an extra load at lanes 0 and 31); the update of row j takes its
+// vertical neighbours from the window and its horizontal ones by shuffle.
+// Raw fields are loaded two rows ahead of their use.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CmRaw {
+    T th, pg, xo, xh, xw;
+};
+
+template <typename T>
+__device__ __forceinline__ void cm_load(const FieldPtrs<T, 2> &F, unsigned g, CmRaw<T> &R)
+{
+    R.th = F.theta[g];
+    R.pg = F.phig[g];
+    R.xo = F.xO[g];
+    R.xh = F.xH[g];
+    R.xw = F.xW[g];
+}
+
+template <typename T>
+struct CmDer {
+    T mu, M, DH, DW;
+};
+
+// mu_O, M_O, D_H, D_H2O of a cell from its theta, phi_g, x_O and the
+// Laplacian of x_O (Sec. 2.2, 3.2; R4)
+template <typename T>
+__device__ __forceinline__ void cm_derive(const CellConst<T> &K, T th, T pg, T x, T lap, CmDer<T> &Dv)
+{
+    T Wf, Ww, Wg;
+    phase_weights(th, pg, Wf, Ww, Wg);
+    const T m1 = Wf * f_fe1(x) + Ww * f_wu1(x) + Wg * f_ga1(x);
+    const T m2 = Wf * f_fe2(x) + Ww * f_wu2(x) + Wg * f_ga2(x);
+    Dv.mu = K.c * m1 - K.kappa * lap;
+    const T DO = (T(1) - Wg) * K.DOs + Wg * K.DOg;
+    const T den = K.c * m2;
+    Dv.M = den != T(0) ? fast_div(DO, den) : T(0);
+    Dv.DH = (T(1) - Wg) * K.DHs + Wg * K.DHg;
+    Dv.DW = (T(1) - Wg) * K.DWs + Wg * K.DWg;
+}
+
+template <typename T>
+__device__ __forceinline__ T up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <typename T>
+__device__ __forceinline__ T dn1(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fused_cm(const __grid_constant__ JobSet<CellJob<T, 2>> js)
+{
+    __shared__ __align__(16) CellJob<T, 2> sJ;
+    {
+        const CellJob<T, 2> *J_ = my_job(js);
+        const int *src = (const int *)J_;
+        int *dst = (int *)&sJ;
+        for (int w = threadIdx.x; w < (int)(sizeof(CellJob<T, 2>) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    const FieldPtrs<T, 2> &F = sJ.F;       // pointers and constants are read from the
+    const CellConst<T> &K = sJ.K;          // job's shared-memory copy where used
+    const int nx = sJ.P.nx, ny = sJ.P.ny;
+    const int bid = (int)blockIdx.x - sJ.block0, nbk = sJ.nblocks;
+    const int lane = threadIdx.x & 31;
+    const int gw = bid * (blockDim.x >> 5) + (threadIdx.x >> 5), W = nbk * (blockDim.x >> 5);
+    // the (strip column, row) space is cut into W equal contiguous chunks,
+    // one per warp; a chunk that crosses a strip column is two segments
+    const int nsx = (nx + 29) / 30;
+    const long long total = (long long)nsx * ny;
+    const long long per = (total + W - 1) / W;
+    long long u = (long long)gw * per;
+    const long long uend = u + per < total ? u + per : total;
+    Acc<T> acc[5];
+    bool bad = false;
+    while (u < uend) {
+        const int sxi = (int)(u / ny), j0 = (int)(u % ny);
+        const int j1 = (int)((ny - j0) < (uend - u) ? ny : j0 + (uend - u));
+        u += j1 - j0;
+        const int x0 = sxi * 30;
+        const int craw = x0 - 1 + lane;
+        const int c = craw < 0 ? craw + nx : (craw >= nx ? craw - nx : craw);
+        const int cw = c % nx;                                   // grids narrower than a strip wrap again
+        const bool out = lane >= 1 && lane <= 30 && craw < nx;   // this lane writes its column
+        int cext = lane == 0 ? cw - 1 : cw + 1;                  // x_O beyond the halo lanes
+        cext = cext < 0 ? cext + nx : (cext >= nx ? cext - nx : cext);
+        auto row = [&](int j) {
+            int r = j < 0 ? j + ny : (j >= ny ? j - ny : j);
+            if ((unsigned)r >= (unsigned)ny) r = ((j % ny) + ny) % ny;   // grids of a few rows
+            return r;
+        };
+        auto at = [&](int col, int j) { return (unsigned)col + (unsigned)nx * (unsigned)row(j); };
+        // window: raw rows j-1 .. j+2, derived rows j-1, j
+        CmRaw<T> rm, r0, r1, r2;
+        T xe0, xe1, xe2;          // x_O beyond the halo lane, rows j, j+1, j+2 (lanes 0 and 31)
+        CmDer<T> dm, d0;
+        {
+            const T xo_m2 = F.xO[at(cw, j0 - 2)];
+            T xe_m1 = T(0);
+            cm_load(F, at(cw, j0 - 1), rm);
+            cm_load(F, at(cw, j0), r0);
+            cm_load(F, at(cw, j0 + 1), r1);
+            cm_load(F, at(cw, j0 + 2), r2);
+            if (lane == 0 || lane == 31) {
+                xe_m1 = F.xO[at(cext, j0 - 1)];
+                xe0 = F.xO[at(cext, j0)];
+                xe1 = F.xO[at(cext, j0 + 1)];
+                xe2 = F.xO[at(cext, j0 + 2)];
+            } else {
+                xe0 = xe1 = xe2 = T(0);
+            }
+            // derived of rows j0-1 and j0: Laplacians of x_O
+            T l, r;
+            l = up1(rm.xo); r = dn1(rm.xo);
+            if (lane == 0) l = xe_m1;
+            if (lane == 31) r = xe_m1;
+            cm_derive(K, rm.th, rm.pg, rm.xo, l + r + xo_m2 + r0.xo - T(4) * rm.xo, dm);
+            l = up1(r0.xo); r = dn1(r0.xo);
+            if (lane == 0) l = xe0;
+            if (lane == 31) r = xe0;
+            cm_derive(K, r0.th, r0.pg, r0.xo, l + r + rm.xo + r1.xo - T(4) * r0.xo, d0);
+        }
+        for (int j = j0; j < j1; j++) {
+            // raw values two rows ahead, and this row's per-cell inputs
+            CmRaw<T> r3;
+            T xe3 = T(0);
+            cm_load(F, at(cw, j + 3), r3);
+            if (lane == 0 || lane == 31) xe3 = F.xO[at(cext, j + 3)];
+            const unsigned g = at(cw, j);
+            T tE = T(0), s2 = T(0), mob = T(0);
+            unsigned char msk = 0;
+            if (out) { tE = F.trE[g]; s2 = F.devE2[g]; mob = F.mob[g]; msk = F.mask[g]; }
+            // derived of row j+1
+            CmDer<T> d1;
+            {
+                T l = up1(r1.xo), r = dn1(r1.xo);
+                if (lane == 0) l = xe1;
+                if (lane == 31) r = xe1;
+                cm_derive(K, r1.th, r1.pg, r1.xo, l + r + r0.xo + r2.xo - T(4) * r1.xo, d1);
+            }
+            // horizontal neighbours of row j
+            const T thl = up1(r0.th), thr = dn1(r0.th);
+            const T mul = up1(d0.mu), mur = dn1(d0.mu), Ml = up1(d0.M), Mr = dn1(d0.M);
+            const T DHl = up1(d0.DH), DHr = dn1(d0.DH), DWl = up1(d0.DW), DWr = dn1(d0.DW);
+            const T xhl = up1(r0.xh), xhr = dn1(r0.xh), xwl = up1(r0.xw), xwr = dn1(r0.xw);
+            if (out) {
+                const T th = r0.th, pg = r0.pg, xo = r0.xo, xh = r0.xh, xw = r0.xw;
+                const T mu0 = d0.mu, M0 = d0.M, DH0 = d0.DH, DW0 = d0.DW;
+                const T half = T(0.5);
+                const T lapt = (thl - th) + (thr - th) + (rm.th - th) + (r1.th - th);
+                const T dO = half * (M0 + Ml) * (mul - mu0) + half * (M0 + Mr) * (mur - mu0)
+                           + half * (M0 + dm.M) * (dm.mu - mu0) + half * (M0 + d1.M) * (d1.mu - mu0);
+                const T dH = half * (DH0 + DHl) * (xhl - xh) + half * (DH0 + DHr) * (xhr - xh)
+                           + half * (DH0 + dm.DH) * (rm.xh - xh) + half * (DH0 + d1.DH) * (r1.xh - xh);
+                const T dW = half * (DW0 + DWl) * (xwl - xw) + half * (DW0 + DWr) * (xwr - xw)
+                           + half * (DW0 + dm.DW) * (rm.xw - xw) + half * (DW0 + d1.DW) * (r1.xw - xw);
+                const T hg0 = hfun(pg);
+                const T hpt = hder(th);
+                const T sol = T(1) - hg0;
+                const T Af = K.c * f_fe(xo) + half * K.Ks * tE * tE + K.Gs * s2;
+                const T Aw = K.c * f_wu(xo) + half * K.Ks * tE * tE + K.Gs * s2;
+                const T Kmix = sol * K.Ks + hg0 * K.Kg;
+                const T force = sol * hpt * (Af - Aw) + K.w2 * mder(th) - K.eig3 * sol * hpt * Kmix * tE;
+                const T rate = K.Lh * mob * (force - K.eps2 * lapt);
+                T rr = mfun(pg) * K.kf * xo * xh;
+                if (xw >= T(1)) rr = T(0);
+                const T nth = th + K.dt * rate;
+                const T nxo = xo + K.dt * (dO - rr);
+                T nxh = xh + K.dt * (dH - T(2) * rr);
+                T nxw = xw + K.dt * (dW + rr);
+                if (msk) {
+                    acc[3].add(nxw);
+                    acc[4].add(K.xHbc - nxh);
+                    nxh = K.xHbc;
+                    nxw = T(0);
+                }
+                F.theta_o[g] = nth;
+                F.xO_o[g] = nxo;
+                F.xH_o[g] = nxh;
+                F.xW_o[g] = nxw;
+                acc[0].add(nxo); acc[1].add(nxh); acc[2].add(nxw);
+                bad |= !isfinite(nth + nxo + nxh + nxw);
+            }
+            // shift the window one row up
+            rm = r0; r0 = r1; r1 = r2; r2 = r3;
+            xe0 = xe1; xe1 = xe2; xe2 = xe3;
+            dm = d0; d0 = d1;
+        }
+    }
+    Acc<T> acc6[6];
+#pragma unroll
+    for (int q = 0; q < 5; q++) acc6[q] = acc[q];
+    acc6[5].add(T(bad ? 1 : 0));
+    double *partials = sJ.partials;
+    unsigned int *counter = sJ.counter;
+    block_reduce_store<6>(acc6, partials + (size_t)bid * PSTRIDE);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int tk = atomicAdd(counter, 1u);
+        last = (tk == (unsigned int)nbk - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        __shared__ double tot[6];
+        last_block_sums<6>(partials, nbk, tot);
         if (threadIdx.x == 0) {
             Diag *dg = sJ.dg;
             dg->sumO = tot[0]; dg->sumH = tot[1]; dg->sumW = tot[2];

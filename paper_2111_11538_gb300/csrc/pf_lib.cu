@@ -400,8 +400,12 @@ int prepare_fused(pf_handle *h)
 template <typename T, int D>
 void launch_fused(int grid, const JobSet<CellJob<T, D>> &js, cudaStream_t s)
 {
-    using S = FusedShape<D>;
-    k_fused<T, D, S::X, S::Y, S::Z><<<grid, 256, fused_smem<T, D>(), s>>>(js);
+    if constexpr (D == 2) {
+        k_fused_cm<T><<<grid, 256, 0, s>>>(js);      // column strips, no shared-memory tile
+    } else {
+        using S = FusedShape<D>;
+        k_fused<T, D, S::X, S::Y, S::Z><<<grid, 256, fused_smem<T, D>(), s>>>(js);
+    }
 }
 
 // Build the job tables of every instance: cell kernels get ~N/256 blocks per
@@ -446,8 +450,17 @@ int build_plan(pf_handle *h)
     int f0 = 0;
     for (int i = 0; i < n; i++) {
         const Params &P = I[i]->P;
-        const long long nt = (long long)((P.nx + FX - 1) / FX) * ((P.ny + FY - 1) / FY) * (D == 3 ? (P.nz + FZ - 1) / FZ : 1);
-        const int nb = (int)std::min<long long>(nt, (long long)h->sms * 8);
+        long long nt = (long long)((P.nx + FX - 1) / FX) * ((P.ny + FY - 1) / FY) * (D == 3 ? (P.nz + FZ - 1) / FZ : 1);
+        long long cap = (long long)h->sms * 8;
+        if (D == 2) {
+            // column strips (k_fused_cm, 30 output columns each, 3 blocks of
+            // 8 warps per SM): at most one wave of resident blocks, and at
+            // least ~16 rows per warp so the window start-up stays small
+            const long long rows = (long long)((P.nx + 29) / 30) * P.ny;
+            nt = (rows + 8 * 16 - 1) / (8 * 16);
+            cap = (long long)h->sms * 3;
+        }
+        const int nb = (int)std::max<long long>(1, std::min<long long>(nt, cap));
         for (int k = 0; k < 2; k++) { fj[k][i].block0 = f0; fj[k][i].nblocks = nb; }
         f0 += nb;
     }
