@@ -455,9 +455,9 @@ int build_plan(pf_handle *h)
         if (D == 2) {
             // column strips (k_fused_cm, 30 output columns each, 3 blocks of
             // 8 warps per SM): at most one wave of resident blocks, and at
-            // least ~16 rows per warp so the window start-up stays small
+            // least ~8 rows per warp so the window start-up stays small
             const long long rows = (long long)((P.nx + 29) / 30) * P.ny;
-            nt = (rows + 8 * 16 - 1) / (8 * 16);
+            nt = (rows + 8 * 8 - 1) / (8 * 8);
             cap = (long long)h->sms * 3;
         }
         const int nb = (int)std::max<long long>(1, std::min<long long>(nt, cap));
