@@ -52,6 +52,7 @@ enum {
 enum { PF_FP64 = 0, PF_MIXED = 1 };            /* device storage / arithmetic */
 enum { PF_WS_ZERO = 0, PF_WS_PREV = 1, PF_WS_LEARNED = 2 };   /* CG initial guess */
 enum { PF_HOST = 0, PF_DEVICE = 1 };           /* where caller arrays live    */
+enum { PF_PC_AUTO = 0, PF_PC_JACOBI = 1, PF_PC_MG = 2 };   /* CG preconditioner      */
 
 /* Nondimensional model parameters (energy in units of the solid Young's
  * modulus, length in cells, time in 1/(L E_s)); see Sec. 3 / Table 1. */
@@ -86,6 +87,12 @@ typedef struct {
     int pcg_tile;       /* node tile of the PCG sweep: 0 = the library's choice for the
                            grid size (measured per size class), 1 = 32x8 (2D) / 16x4x4
                            (3D), 2 = 32x16 / 32x4x2.  Results agree to rounding.        */
+    int precond;        /* CG preconditioner: PF_PC_AUTO (the library's choice),
+                           PF_PC_JACOBI (diagonal), or PF_PC_MG (2D only: one geometric
+                           multigrid V-cycle per iteration, Chebyshev-smoothed, on grids
+                           halved while both sizes stay even and the coarse grid keeps
+                           >= 8 nodes per axis).  Both solve to the same cg_rtol;
+                           iteration counts differ.                                    */
 } pf_config;
 
 /* Field arrays, FP64, cell-major.  Any pointer may be NULL (skipped).

@@ -16,7 +16,8 @@ import ctypes
 import numpy as np
 
 from . import native
-from .native import (PF_DEVICE, PF_FP64, PF_HOST, PF_MIXED, PF_OK, PF_WS_LEARNED, PF_WS_PREV, PF_WS_ZERO,
+from .native import (PF_DEVICE, PF_FP64, PF_HOST, PF_MIXED, PF_OK, PF_PC_AUTO, PF_PC_JACOBI, PF_PC_MG,
+                     PF_WS_LEARNED, PF_WS_PREV, PF_WS_ZERO,
                      STATUS_NAMES, pf_config, pf_diag, pf_fields, pf_params)
 
 __all__ = ["Simulation", "Batch", "PFError", "make_config", "native"]
@@ -31,7 +32,7 @@ class PFError(RuntimeError):
 
 
 def make_config(shape, prm, precision="fp64", mechanics=None, plasticity=None, warm_start=None,
-                cg_rtol=None, cg_maxit=None, dt=None, pcg_tile=None):
+                cg_rtol=None, cg_maxit=None, dt=None, pcg_tile=None, precond=None):
     """Build a pf_config from a grid shape ((ny, nx) or (nz, ny, nx)) and a
     parameter dict (see workloads.params)."""
     c = pf_config()
@@ -52,6 +53,8 @@ def make_config(shape, prm, precision="fp64", mechanics=None, plasticity=None, w
     c.cg_maxit = int(prm.get("cg_maxit", 20000) if cg_maxit is None else cg_maxit)
     c.dt = float(prm.get("dt", 0.0) if dt is None else dt)
     c.pcg_tile = int(prm.get("pcg_tile", 0) if pcg_tile is None else pcg_tile)
+    pc = prm.get("precond", "auto") if precond is None else precond
+    c.precond = {"auto": PF_PC_AUTO, "jacobi": PF_PC_JACOBI, "mg": PF_PC_MG}.get(pc, pc)
     for k in PARAM_NAMES:
         setattr(c.p, k, float(prm[k]))
     return c

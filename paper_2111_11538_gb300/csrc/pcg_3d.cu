@@ -5,15 +5,15 @@
 
 using namespace pfdev;
 
-cudaError_t pcg3_occupancy(bool fp64, int shape, int block, int *per_sm)
+cudaError_t pcg3_occupancy(bool fp64, int shape, bool mg, int block, int *per_sm)
 {
-    return fp64 ? pcg_occupancy_t<double, 3>(shape, block, per_sm) : pcg_occupancy_t<float, 3>(shape, block, per_sm);
+    return fp64 ? pcg_occupancy_t<double, 3>(shape, mg, block, per_sm) : pcg_occupancy_t<float, 3>(shape, mg, block, per_sm);
 }
 
-cudaError_t pcg3_launch(bool fp64, int shape, const void *jobs, int njobs, int grid, int block, cudaStream_t s)
+cudaError_t pcg3_launch(bool fp64, int shape, bool mg, const void *jobs, int njobs, int grid, int block, cudaStream_t s)
 {
-    return fp64 ? pcg_launch_t<double, 3>(shape, jobs, njobs, grid, block, s)
-                : pcg_launch_t<float, 3>(shape, jobs, njobs, grid, block, s);
+    return fp64 ? pcg_launch_t<double, 3>(shape, mg, jobs, njobs, grid, block, s)
+                : pcg_launch_t<float, 3>(shape, mg, jobs, njobs, grid, block, s);
 }
 
 cudaError_t pcg3_tables(const void *tabF, const void *tabD)

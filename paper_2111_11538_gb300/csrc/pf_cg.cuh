@@ -37,6 +37,8 @@ template <> struct Tile<3, 0> { static constexpr int X = 16, Y = 4, Z = 4; };
 template <> struct Tile<3, 1> { static constexpr int X = 32, Y = 4, Z = 2; };
 constexpr int PCG_SHAPES = 2;
 
+template <typename T> struct MGHier;
+
 template <typename T, int D>
 struct PCGArgs {
     Params P;
@@ -58,6 +60,7 @@ struct PCGArgs {
     int maxit;
     int warm;
     int block0, nblocks;           // this job's blocks in the launch
+    const MGHier<T> *mg;           // multigrid hierarchy (2D, k_pcg<..., MG = true> only)
 };
 
 // Grid barrier that also reduces K per-block values in a fixed order: the
@@ -369,8 +372,61 @@ __device__ __forceinline__ int hidx(const Params &P, int x, int y, int z, bool s
     return x + P.nx * y;
 }
 
+// FP64 state of the iteration, in shared memory and touched only by thread 0
+// (so it costs the other threads no registers).
+struct PCGState {
+    double XE[6];      // mean strain of x (plain) / of the correction (refine)
+    double E64[6];     // FP64 mean strain of the solution (refine)
+    double DiagE[6], invDiagE[6], RE[6], UE[6], PE[6], SE[6], WE[6];
+    double Sl, Sm, bnorm, rho_final, target, prev_res;
+    double gamma, delta, gamma_prev, alpha_prev, alpha, beta;
+    double inv_gamma, inv_gamma_prev, inv_alpha, inv_alpha_prev;   // FP64 divisions are slow here
+    int it, it_total, conv;
+};
+
+// Scalar part of one CG update, thread 0 only: beta and alpha from gamma and
+// delta (one division here, 1/alpha = den / gamma reusing 1/gamma, and one
+// for 1/gamma after the reduction), then the mean-strain dofs' p, s, x, r
+// and their Jacobi-preconditioned u.
+template <int NV>
+__device__ __forceinline__ void cg_scalar_update(PCGState &S)
+{
+    S.beta = (S.it == 0) ? 0.0 : S.gamma * S.inv_gamma_prev;
+    const double den = (S.it == 0) ? S.delta : S.delta - S.beta * S.gamma * S.inv_alpha_prev;
+    S.alpha = S.gamma / den;
+    S.inv_alpha = den * S.inv_gamma;
+    for (int vv = 0; vv < NV; vv++) {
+        S.PE[vv] = S.UE[vv] + S.beta * S.PE[vv];
+        S.SE[vv] = S.WE[vv] + S.beta * S.SE[vv];
+        S.XE[vv] += S.alpha * S.PE[vv];
+        S.RE[vv] -= S.alpha * S.SE[vv];
+        S.UE[vv] = S.RE[vv] * S.invDiagE[vv];
+    }
+}
+
+// Thread 0 after the reduction of gamma and delta: shift the previous
+// iteration's values (not on the first sweep of a pass).
+__device__ __forceinline__ void cg_take_gamma_delta(PCGState &S, double gnew, double dnew, bool first)
+{
+    if (!first) {
+        S.gamma_prev = S.gamma;
+        S.alpha_prev = S.alpha;
+        S.inv_gamma_prev = S.inv_gamma;
+        S.inv_alpha_prev = S.inv_alpha;
+    }
+    S.gamma = gnew;
+    S.delta = dnew;
+    S.inv_gamma = 1.0 / gnew;
+}
+
 // Control words broadcast by thread 0.
 enum { CTL_RUN = 0, CTL_DONE = 1, CTL_ZERO = 2, CTL_STOP = 3 };
+
+}  // namespace pfdev
+
+#include "pf_mg.cuh"
+
+namespace pfdev {
 
 // The solve.  Plain mode (refine = 0): x = A.x (the displacement itself).
 // Refinement mode (FP32 storage): the solution is kept in FP64 (A.x64 and the
@@ -381,9 +437,10 @@ enum { CTL_RUN = 0, CTL_DONE = 1, CTL_ZERO = 2, CTL_STOP = 3 };
 template <int D, int S>
 constexpr int tile_threads() { return Tile<D, S>::X * Tile<D, S>::Y * Tile<D, S>::Z; }
 
-template <typename T, int D, int SH>
+template <typename T, int D, int SH, bool MG>
 __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, SH>()) k_pcg(const PCGArgs<T, D> *jobs, int njobs)
 {
+    static_assert(!MG || D == 2, "the multigrid preconditioner is 2D");
     // this block's job, copied to shared memory
     __shared__ PCGArgs<T, D> sA;
     {
@@ -408,7 +465,7 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
     // element-matrix path and need none
     constexpr bool CELL3 = D == 3 && sizeof(T) == 4 && SH == 0;
     __shared__ __align__(16) T scell2[D == 2 ? 5 * HC : 1];
-    extern __shared__ __align__(16) unsigned char pcg_dyn[];   // CELL3: 20 * HC floats (pcg_dyn_smem)
+    extern __shared__ __align__(16) unsigned char pcg_dyn[];   // CELL3: 20 * HC floats; MG: block-run levels
     T *scell = CELL3 ? reinterpret_cast<T *>(pcg_dyn) : scell2;
     __shared__ T s_ta, s_tb, s_ue[6], s_xe[6];
     __shared__ int s_ctl;
@@ -425,18 +482,7 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
     const bool lead = threadIdx.x == 0;
     const bool small = P.nx < TX + 2 || P.ny < TY + 2 || (D == 3 && P.nz < TZ + 2);
 
-    // FP64 state of the iteration, in shared memory and touched only by
-    // thread 0 (so it costs the other threads no registers).
-    struct State {
-        double XE[6];      // mean strain of x (plain) / of the correction (refine)
-        double E64[6];     // FP64 mean strain of the solution (refine)
-        double DiagE[6], invDiagE[6], RE[6], UE[6], PE[6], SE[6], WE[6];
-        double Sl, Sm, bnorm, rho_final, target, prev_res;
-        double gamma, delta, gamma_prev, alpha_prev, alpha, beta;
-        double inv_gamma, inv_gamma_prev, inv_alpha, inv_alpha_prev;   // FP64 divisions are slow here
-        int it, it_total, conv;
-    };
-    __shared__ State S;
+    __shared__ PCGState S;
     double *XE = S.XE, *E64 = S.E64, *DiagE = S.DiagE, *RE = S.RE, *UE = S.UE, *PE = S.PE, *SE = S.SE, *WE = S.WE;
     double &Sl = S.Sl, &Sm = S.Sm, &bnorm = S.bnorm, &rho_final = S.rho_final, &target = S.target;
     double &gamma = S.gamma, &delta = S.delta, &gamma_prev = S.gamma_prev, &alpha_prev = S.alpha_prev;
@@ -453,6 +499,14 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
         it_total = 0;
         if (A.warm)
             for (int v = 0; v < NV; v++) (refine ? E64 : XE)[v] = A.sc->E[v];
+    }
+
+    // MG: the hierarchy descriptor (read only during the launch) stays in
+    // global memory; the coarse levels' moduli are rebuilt for this solve
+    // the block-run levels' arrays: dynamic shared memory (pcg_dyn_smem)
+    T *sblk = reinterpret_cast<T *>(pcg_dyn);
+    if constexpr (MG) {
+        if (!mg_setup<T>(*A.mg, sblk, A.bar_count, A.bar_gen, err, bid, nbk)) return;
     }
 
     for (int outer = 0; outer < (refine ? MAX_OUTER : 1); outer++) {
@@ -567,309 +621,290 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
         if (ctl0 == CTL_STOP) { conv = false; break; }
 
         // ---------------- sweeps: the first builds w_0, then iterations -----
-        bool first = true;
-        int cur = 0;
-        while (true) {
-            if (lead) {
-                if (!first) {
-                    // beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev):
-                    // one division here (1/alpha = den / gamma reuses 1/gamma)
-                    // and one for 1/gamma after the reduction
-                    beta = (it == 0) ? 0.0 : gamma * S.inv_gamma_prev;
-                    const double den = (it == 0) ? delta : delta - beta * gamma * S.inv_alpha_prev;
-                    alpha = gamma / den;
-                    S.inv_alpha = den * S.inv_gamma;
-                    for (int vv = 0; vv < NV; vv++) {
-                        PE[vv] = UE[vv] + beta * PE[vv];
-                        SE[vv] = WE[vv] + beta * SE[vv];
-                        XE[vv] += alpha * PE[vv];
-                        RE[vv] -= alpha * SE[vv];
-                        UE[vv] = RE[vv] * S.invDiagE[vv];
-                    }
+        if constexpr (MG) {
+            const int rc = mg_pass<T, TX, TY>(A, *A.mg, S, su, sl, sm, scell, sblk, s_ta, s_tb, s_ue, s_ctl, bid, nbk, err);
+            if (rc < 0) return;
+            if (lead) conv = rc == CTL_DONE;
+        } else {
+            bool first = true;
+            int cur = 0;
+            while (true) {
+                if (lead) {
+                    if (!first) cg_scalar_update<NV>(S);
+                    s_ta = (T)alpha;
+                    s_tb = (T)beta;
+                    for (int vv = 0; vv < NV; vv++) s_ue[vv] = (T)UE[vv];
                 }
-                s_ta = (T)alpha;
-                s_tb = (T)beta;
-                for (int vv = 0; vv < NV; vv++) s_ue[vv] = (T)UE[vv];
-            }
-            __syncthreads();
-            const T ta = s_ta, tb = s_tb;
-            T ue[NV];
-#pragma unroll
-            for (int vv = 0; vv < NV; vv++) ue[vv] = s_ue[vv];
-            const int nxt = first ? cur : 1 - cur;
-            Acc<T> acc[3 + NV];      // gamma, delta, ||r||^2, mean-strain row
-            // Register double buffering across tiles: the loads of the next
-            // tile's halo (r, w, s, diag), cells (lam, mu) and own node are
-            // issued before the current tile is staged and computed, so their
-            // latency overlaps that work.
-            constexpr int NT = TX * TY * TZ;       // threads = tile nodes
-            constexpr int HS = (HN + NT - 1) / NT, CS = (HC + NT - 1) / NT;
-            struct Raw {
-                T r[HS][D], w[HS][D], s[HS][D], dg[HS];
-                T l[CS], m[CS];
-                T ro[D], wo[D], so[D], xo[D], po[D], dgo;
-            };
-            auto load_raw = [&](int tile, Raw &R) {
-                const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
-                const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
-#pragma unroll
-                for (int k = 0; k < HS; k++) {
-                    const int h = threadIdx.x + NT * k;
-                    if (h < HN) {
-                        const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
-                        const int g = hidx<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz, small);
-                        R.dg[k] = __ldcg(A.dinv + g);
-#pragma unroll
+                __syncthreads();
+                const T ta = s_ta, tb = s_tb;
+                T ue[NV];
+    #pragma unroll
+                for (int vv = 0; vv < NV; vv++) ue[vv] = s_ue[vv];
+                const int nxt = first ? cur : 1 - cur;
+                Acc<T> acc[3 + NV];      // gamma, delta, ||r||^2, mean-strain row
+                // Register double buffering across tiles: the loads of the next
+                // tile's halo (r, w, s, diag), cells (lam, mu) and own node are
+                // issued before the current tile is staged and computed, so their
+                // latency overlaps that work.
+                constexpr int NT = TX * TY * TZ;       // threads = tile nodes
+                constexpr int HS = (HN + NT - 1) / NT, CS = (HC + NT - 1) / NT;
+                struct Raw {
+                    T r[HS][D], w[HS][D], s[HS][D], dg[HS];
+                    T l[CS], m[CS];
+                    T ro[D], wo[D], so[D], xo[D], po[D], dgo;
+                };
+                auto load_raw = [&](int tile, Raw &R) {
+                    const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
+                    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+    #pragma unroll
+                    for (int k = 0; k < HS; k++) {
+                        const int h = threadIdx.x + NT * k;
+                        if (h < HN) {
+                            const int lx = h % HX, ly = (h / HX) % HY, lz = D == 3 ? h / (HX * HY) : 0;
+                            const int g = hidx<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz, small);
+                            R.dg[k] = __ldcg(A.dinv + g);
+    #pragma unroll
+                            for (int d = 0; d < D; d++) {
+                                R.r[k][d] = __ldcg(A.r[cur][d] + g);
+                                if (!first) {
+                                    R.w[k][d] = __ldcg(A.w[cur][d] + g);
+                                    R.s[k][d] = __ldcg(A.s[cur][d] + g);
+                                }
+                            }
+                        }
+                    }
+    #pragma unroll
+                    for (int k = 0; k < CS; k++) {
+                        const int h = threadIdx.x + NT * k;
+                        if (h < HC) {
+                            const int lx = h % CX, ly = (h / CX) % CY, lz = D == 3 ? h / (CX * CY) : 0;
+                            const int g = hidx<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz, small);
+                            R.l[k] = __ldg(A.lam + g);
+                            R.m[k] = __ldg(A.mu + g);
+                        }
+                    }
+                    const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+                    if (gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz)) {
+                        const int n = gx + P.nx * (gy + (D == 3 ? P.ny * gz : 0));
+                        R.dgo = __ldcg(A.dinv + n);
+    #pragma unroll
                         for (int d = 0; d < D; d++) {
-                            R.r[k][d] = __ldcg(A.r[cur][d] + g);
+                            R.ro[d] = __ldcg(A.r[cur][d] + n);
                             if (!first) {
-                                R.w[k][d] = __ldcg(A.w[cur][d] + g);
-                                R.s[k][d] = __ldcg(A.s[cur][d] + g);
+                                R.wo[d] = __ldcg(A.w[cur][d] + n);
+                                R.so[d] = __ldcg(A.s[cur][d] + n);
+                                R.xo[d] = A.x[d][n];
+                                R.po[d] = A.p[d][n];
                             }
                         }
                     }
-                }
-#pragma unroll
-                for (int k = 0; k < CS; k++) {
-                    const int h = threadIdx.x + NT * k;
-                    if (h < HC) {
-                        const int lx = h % CX, ly = (h / CX) % CY, lz = D == 3 ? h / (CX * CY) : 0;
-                        const int g = hidx<D>(P, x0 - 1 + lx, y0 - 1 + ly, z0 - 1 + lz, small);
-                        R.l[k] = __ldg(A.lam + g);
-                        R.m[k] = __ldg(A.mu + g);
-                    }
-                }
-                const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-                if (gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz)) {
-                    const int n = gx + P.nx * (gy + (D == 3 ? P.ny * gz : 0));
-                    R.dgo = __ldcg(A.dinv + n);
-#pragma unroll
-                    for (int d = 0; d < D; d++) {
-                        R.ro[d] = __ldcg(A.r[cur][d] + n);
-                        if (!first) {
-                            R.wo[d] = __ldcg(A.w[cur][d] + n);
-                            R.so[d] = __ldcg(A.s[cur][d] + n);
-                            R.xo[d] = A.x[d][n];
-                            R.po[d] = A.p[d][n];
+                };
+                Raw R;
+                if (bid < ntiles) load_raw(bid, R);
+                for (int tile = bid; tile < ntiles; tile += nbk) {
+                    const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
+                    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+                    // stage this tile: u_{i+1} = (r_i - alpha (w_i + beta s_{i-1})) / diag
+                    // on the halo nodes, lam / mu on the halo cells
+    #pragma unroll
+                    for (int k = 0; k < HS; k++) {
+                        const int h = threadIdx.x + NT * k;
+                        if (h < HN) {
+                            const T inv = R.dg[k];
+    #pragma unroll
+                            for (int d = 0; d < D; d++) {
+                                T rv = R.r[k][d];
+                                if (!first) rv -= ta * (R.w[k][d] + tb * R.s[k][d]);
+                                su[d * HN + h] = rv * inv;
+                            }
                         }
                     }
-                }
-            };
-            Raw R;
-            if (bid < ntiles) load_raw(bid, R);
-            for (int tile = bid; tile < ntiles; tile += nbk) {
-                const int bx = tile % ntx, by = (tile / ntx) % nty, bz = D == 3 ? tile / (ntx * nty) : 0;
-                const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
-                // stage this tile: u_{i+1} = (r_i - alpha (w_i + beta s_{i-1})) / diag
-                // on the halo nodes, lam / mu on the halo cells
-#pragma unroll
-                for (int k = 0; k < HS; k++) {
-                    const int h = threadIdx.x + NT * k;
-                    if (h < HN) {
-                        const T inv = R.dg[k];
-#pragma unroll
-                        for (int d = 0; d < D; d++) {
-                            T rv = R.r[k][d];
-                            if (!first) rv -= ta * (R.w[k][d] + tb * R.s[k][d]);
-                            su[d * HN + h] = rv * inv;
+    #pragma unroll
+                    for (int k = 0; k < CS; k++) {
+                        const int h = threadIdx.x + NT * k;
+                        if (h < HC) {
+                            sl[h] = R.l[k];
+                            sm[h] = R.m[k];
                         }
                     }
-                }
-#pragma unroll
-                for (int k = 0; k < CS; k++) {
-                    const int h = threadIdx.x + NT * k;
-                    if (h < HC) {
-                        sl[h] = R.l[k];
-                        sm[h] = R.m[k];
-                    }
-                }
-                T ro[D], wo[D], so[D], xo[D], po[D];
-                const T dgo = R.dgo;
-#pragma unroll
-                for (int d = 0; d < D; d++) { ro[d] = R.ro[d]; wo[d] = R.wo[d]; so[d] = R.so[d]; xo[d] = R.xo[d]; po[d] = R.po[d]; }
-                // issue the next tile's loads; they complete while this one computes
-                if (tile + nbk < ntiles) load_raw(tile + nbk, R);
-                __syncthreads();
-                if constexpr (CELL3) {
-                    // per halo cell: average stress (mean strain UE included)
-                    // and the twelve hourglass forces, shared by its 8 nodes
-                    for (int h = threadIdx.x; h < HC; h += blockDim.x) {
-                        const int cx = h % CX, cy = (h / CX) % CY, cz = h / (CX * CY);
-                        T uc[8][3];
-#pragma unroll
-                        for (int b = 0; b < 8; b++) {
-                            const int hn = (cx + (b & 1)) + HX * ((cy + ((b >> 1) & 1)) + HY * (cz + (b >> 2)));
-                            uc[b][0] = su[hn];
-                            uc[b][1] = su[HN + hn];
-                            uc[b][2] = su[2 * HN + hn];
-                        }
-                        const T l = sl[h], m = sm[h];
-                        T c[20], sx[6];
-                        cell_force3<T>(l, m, uc, c);
-                        voigt_stress<T, 3>(l, m, ue, sx);
-#pragma unroll
-                        for (int v = 0; v < 6; v++) c[v] += sx[v];
-                        float4 *dst = reinterpret_cast<float4 *>(scell + 20 * h);
-#pragma unroll
-                        for (int q4 = 0; q4 < 5; q4++) dst[q4] = make_float4(c[4 * q4], c[4 * q4 + 1], c[4 * q4 + 2], c[4 * q4 + 3]);
-                    }
+                    T ro[D], wo[D], so[D], xo[D], po[D];
+                    const T dgo = R.dgo;
+    #pragma unroll
+                    for (int d = 0; d < D; d++) { ro[d] = R.ro[d]; wo[d] = R.wo[d]; so[d] = R.so[d]; xo[d] = R.xo[d]; po[d] = R.po[d]; }
+                    // issue the next tile's loads; they complete while this one computes
+                    if (tile + nbk < ntiles) load_raw(tile + nbk, R);
                     __syncthreads();
-                }
-                if constexpr (D == 2) {
-                    // per halo cell: average stress (mean strain UE included)
-                    // and hourglass forces, shared by the cell's four nodes
-                    for (int h = threadIdx.x; h < HC; h += blockDim.x) {
-                        const int cx = h % CX, cy = h / CX;
-                        T uc[4][2];
-#pragma unroll
-                        for (int b = 0; b < 4; b++) {
-                            const int hn = (cx + (b & 1)) + HX * (cy + (b >> 1));
-                            uc[b][0] = su[hn];
-                            uc[b][1] = su[HN + hn];
+                    if constexpr (CELL3) {
+                        // per halo cell: average stress (mean strain UE included)
+                        // and the twelve hourglass forces, shared by its 8 nodes
+                        for (int h = threadIdx.x; h < HC; h += blockDim.x) {
+                            const int cx = h % CX, cy = (h / CX) % CY, cz = h / (CX * CY);
+                            T uc[8][3];
+    #pragma unroll
+                            for (int b = 0; b < 8; b++) {
+                                const int hn = (cx + (b & 1)) + HX * ((cy + ((b >> 1) & 1)) + HY * (cz + (b >> 2)));
+                                uc[b][0] = su[hn];
+                                uc[b][1] = su[HN + hn];
+                                uc[b][2] = su[2 * HN + hn];
+                            }
+                            const T l = sl[h], m = sm[h];
+                            T c[20], sx[6];
+                            cell_force3<T>(l, m, uc, c);
+                            voigt_stress<T, 3>(l, m, ue, sx);
+    #pragma unroll
+                            for (int v = 0; v < 6; v++) c[v] += sx[v];
+                            float4 *dst = reinterpret_cast<float4 *>(scell + 20 * h);
+    #pragma unroll
+                            for (int q4 = 0; q4 < 5; q4++) dst[q4] = make_float4(c[4 * q4], c[4 * q4 + 1], c[4 * q4 + 2], c[4 * q4 + 3]);
                         }
-                        const T l = sl[h], m = sm[h];
-                        T s3[3], fh[2], sx[3];
-                        cell_force2<T>(l, m, uc, s3, fh);
-                        voigt_stress<T, 2>(l, m, ue, sx);
-                        scell[h] = s3[0] + sx[0];
-                        scell[HC + h] = s3[1] + sx[1];
-                        scell[2 * HC + h] = s3[2] + sx[2];
-                        scell[3 * HC + h] = fh[0];
-                        scell[4 * HC + h] = fh[1];
+                        __syncthreads();
                     }
-                    __syncthreads();
-                }
-                const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-                const bool active = gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz);
-                if (active) {
-                    const int n = gx + P.nx * (gy + (D == 3 ? P.ny * gz : 0));
-                    const int lx = tx + 1, ly = ty + 1, lz = D == 3 ? tz + 1 : 0;
-                    const int hn = lx + HX * (ly + HY * lz);
-                    T un[D];
-#pragma unroll
-                    for (int d = 0; d < D; d++) un[d] = su[d * HN + hn];
-                    T rn[D];
-                    if (!first) {
-                        const T inv = dgo;
-#pragma unroll
-                        for (int d = 0; d < D; d++) {
-                            const T ri = ro[d];
-                            const T si = wo[d] + tb * so[d];
-                            const T pi = ri * inv + tb * po[d];
-                            A.p[d][n] = pi;
-                            A.x[d][n] = xo[d] + ta * pi;
-                            A.s[nxt][d][n] = si;
-                            rn[d] = ri - ta * si;
-                            A.r[nxt][d][n] = rn[d];
-                        }
-                    } else {
-#pragma unroll
-                        for (int d = 0; d < D; d++) rn[d] = ro[d];
-                    }
-                    T q[D], se[NV];
                     if constexpr (D == 2) {
-                        q[0] = T(0);
-                        q[1] = T(0);
-#pragma unroll
-                        for (int a = 0; a < 4; a++) {
-                            const int cl = (lx - (a & 1)) + CX * (ly - (a >> 1));
-                            const T s3[3] = {scell[cl], scell[HC + cl], scell[2 * HC + cl]};
-                            const T fh[2] = {scell[3 * HC + cl], scell[4 * HC + cl]};
-                            T f[2];
-                            node_force2<T>(a, s3, fh, f);
-                            q[0] += f[0];
-                            q[1] += f[1];
-                        }
-                        // own cell's average stress without the mean strain
-                        const int c0 = lx + CX * ly;
-                        T sx[3];
-                        voigt_stress<T, 2>(sl[c0], sm[c0], ue, sx);
-                        se[0] = scell[c0] - sx[0];
-                        se[1] = scell[HC + c0] - sx[1];
-                        se[2] = scell[2 * HC + c0] - sx[2];
-                    } else if constexpr (CELL3) {
-                        q[0] = q[1] = q[2] = T(0);
-#pragma unroll
-                        for (int a = 0; a < 8; a++) {
-                            const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
-                            const int cl = (lx - ax) + CX * ((ly - ay) + CY * (lz - az));
-                            const float4 *src = reinterpret_cast<const float4 *>(scell + 20 * cl);
-                            T c[20];
-#pragma unroll
-                            for (int q4 = 0; q4 < 5; q4++) {
-                                const float4 v = src[q4];
-                                c[4 * q4] = v.x; c[4 * q4 + 1] = v.y; c[4 * q4 + 2] = v.z; c[4 * q4 + 3] = v.w;
+                        // per halo cell: average stress (mean strain UE included)
+                        // and hourglass forces, shared by the cell's four nodes
+                        for (int h = threadIdx.x; h < HC; h += blockDim.x) {
+                            const int cx = h % CX, cy = h / CX;
+                            T uc[4][2];
+    #pragma unroll
+                            for (int b = 0; b < 4; b++) {
+                                const int hn = (cx + (b & 1)) + HX * (cy + (b >> 1));
+                                uc[b][0] = su[hn];
+                                uc[b][1] = su[HN + hn];
                             }
-                            T f[3];
-                            node_force3<T>(ax, ay, az, c, c + 6, f);
-                            q[0] += f[0];
-                            q[1] += f[1];
-                            q[2] += f[2];
-                            if (a == 0) {
-                                // own cell's average stress without the mean strain
-                                T sx[6];
-                                voigt_stress<T, 3>(sl[cl], sm[cl], ue, sx);
-#pragma unroll
-                                for (int v = 0; v < 6; v++) se[v] = c[v] - sx[v];
-                            }
+                            const T l = sl[h], m = sm[h];
+                            T s3[3], fh[2], sx[3];
+                            cell_force2<T>(l, m, uc, s3, fh);
+                            voigt_stress<T, 2>(l, m, ue, sx);
+                            scell[h] = s3[0] + sx[0];
+                            scell[HC + h] = s3[1] + sx[1];
+                            scell[2 * HC + h] = s3[2] + sx[2];
+                            scell[3 * HC + h] = fh[0];
+                            scell[4 * HC + h] = fh[1];
                         }
-                    } else {
-                        T eo[NV], lo, mo;
-                        apply_tile<T, D, HX, HY, CX, CY>(su, sl, sm, HN, lx, ly, lz, ue, q, eo, lo, mo);
-                        voigt_stress<T, D>(lo, mo, eo, se);
+                        __syncthreads();
                     }
-#pragma unroll
-                    for (int d = 0; d < D; d++) {
-                        A.w[nxt][d][n] = q[d];
-                        acc[0].fma_plain(rn[d], un[d]);
-                        acc[1].fma_plain(q[d], un[d]);
-                        acc[2].fma_plain(rn[d], rn[d]);
+                    const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+                    const bool active = gx < P.nx && gy < P.ny && (D == 2 || gz < P.nz);
+                    if (active) {
+                        const int n = gx + P.nx * (gy + (D == 3 ? P.ny * gz : 0));
+                        const int lx = tx + 1, ly = ty + 1, lz = D == 3 ? tz + 1 : 0;
+                        const int hn = lx + HX * (ly + HY * lz);
+                        T un[D];
+    #pragma unroll
+                        for (int d = 0; d < D; d++) un[d] = su[d * HN + hn];
+                        T rn[D];
+                        if (!first) {
+                            const T inv = dgo;
+    #pragma unroll
+                            for (int d = 0; d < D; d++) {
+                                const T ri = ro[d];
+                                const T si = wo[d] + tb * so[d];
+                                const T pi = ri * inv + tb * po[d];
+                                A.p[d][n] = pi;
+                                A.x[d][n] = xo[d] + ta * pi;
+                                A.s[nxt][d][n] = si;
+                                rn[d] = ri - ta * si;
+                                A.r[nxt][d][n] = rn[d];
+                            }
+                        } else {
+    #pragma unroll
+                            for (int d = 0; d < D; d++) rn[d] = ro[d];
+                        }
+                        T q[D], se[NV];
+                        if constexpr (D == 2) {
+                            q[0] = T(0);
+                            q[1] = T(0);
+    #pragma unroll
+                            for (int a = 0; a < 4; a++) {
+                                const int cl = (lx - (a & 1)) + CX * (ly - (a >> 1));
+                                const T s3[3] = {scell[cl], scell[HC + cl], scell[2 * HC + cl]};
+                                const T fh[2] = {scell[3 * HC + cl], scell[4 * HC + cl]};
+                                T f[2];
+                                node_force2<T>(a, s3, fh, f);
+                                q[0] += f[0];
+                                q[1] += f[1];
+                            }
+                            // own cell's average stress without the mean strain
+                            const int c0 = lx + CX * ly;
+                            T sx[3];
+                            voigt_stress<T, 2>(sl[c0], sm[c0], ue, sx);
+                            se[0] = scell[c0] - sx[0];
+                            se[1] = scell[HC + c0] - sx[1];
+                            se[2] = scell[2 * HC + c0] - sx[2];
+                        } else if constexpr (CELL3) {
+                            q[0] = q[1] = q[2] = T(0);
+    #pragma unroll
+                            for (int a = 0; a < 8; a++) {
+                                const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+                                const int cl = (lx - ax) + CX * ((ly - ay) + CY * (lz - az));
+                                const float4 *src = reinterpret_cast<const float4 *>(scell + 20 * cl);
+                                T c[20];
+    #pragma unroll
+                                for (int q4 = 0; q4 < 5; q4++) {
+                                    const float4 v = src[q4];
+                                    c[4 * q4] = v.x; c[4 * q4 + 1] = v.y; c[4 * q4 + 2] = v.z; c[4 * q4 + 3] = v.w;
+                                }
+                                T f[3];
+                                node_force3<T>(ax, ay, az, c, c + 6, f);
+                                q[0] += f[0];
+                                q[1] += f[1];
+                                q[2] += f[2];
+                                if (a == 0) {
+                                    // own cell's average stress without the mean strain
+                                    T sx[6];
+                                    voigt_stress<T, 3>(sl[cl], sm[cl], ue, sx);
+    #pragma unroll
+                                    for (int v = 0; v < 6; v++) se[v] = c[v] - sx[v];
+                                }
+                            }
+                        } else {
+                            T eo[NV], lo, mo;
+                            apply_tile<T, D, HX, HY, CX, CY>(su, sl, sm, HN, lx, ly, lz, ue, q, eo, lo, mo);
+                            voigt_stress<T, D>(lo, mo, eo, se);
+                        }
+    #pragma unroll
+                        for (int d = 0; d < D; d++) {
+                            A.w[nxt][d][n] = q[d];
+                            acc[0].fma_plain(rn[d], un[d]);
+                            acc[1].fma_plain(q[d], un[d]);
+                            acc[2].fma_plain(rn[d], rn[d]);
+                        }
+    #pragma unroll
+                        for (int vv = 0; vv < NV; vv++) acc[3 + vv].add_plain(se[vv]);
                     }
-#pragma unroll
-                    for (int vv = 0; vv < NV; vv++) acc[3 + vv].add_plain(se[vv]);
+                    __syncthreads();
+                }
+                double tt[3 + NV];
+                if (!reduce_barrier<Acc<T>, 3 + NV>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tt, bid, nbk)) return;
+                const bool was_first = first;
+                if (lead) {
+                    double s6[6];
+                    dmat_mul<D>(Sl, Sm, UE, s6);
+                    for (int vv = 0; vv < NV; vv++) WE[vv] = tt[3 + vv] + s6[vv];
+                    double gnew = tt[0], dnew = tt[1], rnew = tt[2];
+                    for (int vv = 0; vv < NV; vv++) {
+                        gnew += RE[vv] * UE[vv];
+                        dnew += WE[vv] * UE[vv];
+                        rnew += RE[vv] * RE[vv];
+                    }
+                    int ctl = CTL_RUN;
+                    if (!was_first) {
+                        it++;
+                        rho_final = rnew;
+                        if (rnew <= target * target) ctl = CTL_DONE;      // ||r|| <= target without a square root
+                        else if (it_total + it >= A.maxit) ctl = CTL_STOP;
+                    }
+                    cg_take_gamma_delta(S, gnew, dnew, was_first);
+                    s_ctl = ctl;
                 }
                 __syncthreads();
-            }
-            double tt[3 + NV];
-            if (!reduce_barrier<Acc<T>, 3 + NV>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tt, bid, nbk)) return;
-            const bool was_first = first;
-            if (lead) {
-                double s6[6];
-                dmat_mul<D>(Sl, Sm, UE, s6);
-                for (int vv = 0; vv < NV; vv++) WE[vv] = tt[3 + vv] + s6[vv];
-                double gnew = tt[0], dnew = tt[1], rnew = tt[2];
-                for (int vv = 0; vv < NV; vv++) {
-                    gnew += RE[vv] * UE[vv];
-                    dnew += WE[vv] * UE[vv];
-                    rnew += RE[vv] * RE[vv];
+                const int ctl = s_ctl;
+                first = false;
+                if (!was_first) cur = nxt;
+                if (ctl == CTL_DONE || ctl == CTL_STOP) {
+                    if (lead) conv = (ctl == CTL_DONE);
+                    break;
                 }
-                int ctl = CTL_RUN;
-                if (was_first) {
-                    gamma = gnew;
-                    delta = dnew;
-                    S.inv_gamma = 1.0 / gnew;
-                } else {
-                    it++;
-                    rho_final = rnew;
-                    if (rnew <= target * target) ctl = CTL_DONE;      // ||r|| <= target without a square root
-                    else if (it_total + it >= A.maxit) ctl = CTL_STOP;
-                    gamma_prev = gamma;
-                    alpha_prev = alpha;
-                    S.inv_gamma_prev = S.inv_gamma;
-                    S.inv_alpha_prev = S.inv_alpha;
-                    gamma = gnew;
-                    delta = dnew;
-                    S.inv_gamma = 1.0 / gnew;
-                }
-                s_ctl = ctl;
-            }
-            __syncthreads();
-            const int ctl = s_ctl;
-            first = false;
-            if (!was_first) cur = nxt;
-            if (ctl == CTL_DONE || ctl == CTL_STOP) {
-                if (lead) conv = (ctl == CTL_DONE);
-                break;
             }
         }
         if (lead) it_total += it;
@@ -913,20 +948,33 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
 // Host side of one translation unit's PCG instantiations: occupancy query,
 // cooperative launch and the upload of that unit's copy of the element
 // tables (constant memory is per unit).  Dynamic shared memory: the 3D FP32
-// cell buffer of the 16x4x4 tile.
+// cell buffer of the 16x4x4 tile; with MG, the arrays of the block-run
+// levels (the bound for any hierarchy, so one attribute serves all).
 template <typename T, int D>
-size_t pcg_dyn_smem(int shape)
+size_t pcg_dyn_smem(int shape, bool mg)
 {
+    if (D == 2 && mg) return sizeof(T) * (size_t)mg_block_words_cap(mg_block_nodes<T>());
     if (D != 3 || sizeof(T) != 4 || shape != 0) return 0;
     constexpr int HC = (Tile<3, 0>::X + 1) * (Tile<3, 0>::Y + 1) * (Tile<3, 0>::Z + 1);
     return sizeof(float) * 20 * HC;
 }
 
+// the kernel variant of a tile shape, with or without the multigrid
+// preconditioner (2D only)
 template <typename T, int D>
-cudaError_t pcg_occupancy_t(int shape, int block, int *per_sm)
+const void *pcg_kernel(int shape, bool mg)
 {
-    const void *fn = shape == 1 ? (const void *)k_pcg<T, D, 1> : (const void *)k_pcg<T, D, 0>;
-    const size_t dyn = pcg_dyn_smem<T, D>(shape);
+    if constexpr (D == 2) {
+        if (mg) return shape == 1 ? (const void *)k_pcg<T, D, 1, true> : (const void *)k_pcg<T, D, 0, true>;
+    }
+    return shape == 1 ? (const void *)k_pcg<T, D, 1, false> : (const void *)k_pcg<T, D, 0, false>;
+}
+
+template <typename T, int D>
+cudaError_t pcg_occupancy_t(int shape, bool mg, int block, int *per_sm)
+{
+    const void *fn = pcg_kernel<T, D>(shape, mg);
+    const size_t dyn = pcg_dyn_smem<T, D>(shape, mg);
     if (dyn) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
@@ -935,12 +983,12 @@ cudaError_t pcg_occupancy_t(int shape, int block, int *per_sm)
 }
 
 template <typename T, int D>
-cudaError_t pcg_launch_t(int shape, const void *jobs, int njobs, int grid, int block, cudaStream_t s)
+cudaError_t pcg_launch_t(int shape, bool mg, const void *jobs, int njobs, int grid, int block, cudaStream_t s)
 {
     const PCGArgs<T, D> *pj = (const PCGArgs<T, D> *)jobs;
     void *args[] = {(void *)&pj, (void *)&njobs};
-    const void *fn = shape == 1 ? (const void *)k_pcg<T, D, 1> : (const void *)k_pcg<T, D, 0>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, pcg_dyn_smem<T, D>(shape), s);
+    return cudaLaunchCooperativeKernel(pcg_kernel<T, D>(shape, mg), dim3(grid), dim3(block), args,
+                                       pcg_dyn_smem<T, D>(shape, mg), s);
 }
 
 } // namespace pfdev

@@ -205,6 +205,8 @@ struct pf_handle {
     int cell_grid = 0, fused_grid = 0, pcg_grid = 0, njobs = 0;
     int cg_per_sm = 0;
     int pcg_shape = 0;                  // node tile of the PCG sweep (pf_cg.cuh Tile<D, S>)
+    bool mg = false;                    // multigrid-preconditioned CG (pf_mg.cuh)
+    void *d_mg = nullptr;               // device MGHier<T> of this instance
     bool plan_ready = false;
     int plan_par = 0;                   // which table describes the current state
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step from job tables [k]
@@ -335,15 +337,126 @@ int default_pcg_shape(int ndim, long long N, bool fp64)
     return fp64 ? PCG_TABLE_3D_F64 : PCG_TABLE_3D_F32;
 }
 
+// Largest eigenvalue of diag(K_e)^-1 K_e for the 2D element with Poisson
+// ratio nu (power iteration on the symmetric scaling D^-1/2 K_e D^-1/2).
+// Summing x_e^T K_e x_e <= w x_e^T diag(K_e) x_e over the cells bounds the
+// largest eigenvalue of D^-1 A by w for any cell moduli with this ratio.
+double element_bound(double nu)
+{
+    std::vector<double> Kl, Km, Bb;
+    element_tables(2, Kl, Km, Bb);
+    const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 0.5 / (1.0 + nu);
+    double K[64], s[8], v[8], w[8];
+    for (int i = 0; i < 64; i++) K[i] = lam * Kl[i] + mu * Km[i];
+    for (int i = 0; i < 8; i++) { s[i] = 1.0 / std::sqrt(K[i * 9]); v[i] = 1.0 + 0.1 * i; }
+    double ray = 0.0;
+    for (int it = 0; it < 2000; it++) {
+        double nv = 0.0, vw = 0.0;
+        for (int i = 0; i < 8; i++) {
+            double a = 0.0;
+            for (int j = 0; j < 8; j++) a += s[i] * K[i * 8 + j] * s[j] * v[j];
+            w[i] = a;
+        }
+        for (int i = 0; i < 8; i++) { vw += v[i] * w[i]; nv += w[i] * w[i]; }
+        double vv = 0.0;
+        for (int i = 0; i < 8; i++) vv += v[i] * v[i];
+        ray = vw / vv;
+        nv = 1.0 / std::sqrt(nv);
+        for (int i = 0; i < 8; i++) v[i] = w[i] * nv;
+    }
+    return ray;
+}
+
+// Multigrid hierarchy of one 2D instance (pf_mg.cuh): coarsen while both
+// sizes stay even and the coarse grid keeps >= 8 nodes per axis; levels of
+// at most mg_block_nodes<T>() nodes are run by one block in shared memory;
+// Chebyshev coefficients over [b/30, b] with b 2% above the element bound.
+// The device descriptor is written once (the arrays never move).  The
+// kernel wants deg >= 2 and csteps >= 3 (their last sweep is a Chebyshev
+// step, whose epilogue applies the final pointwise step).
+constexpr int MG_DEG = 2, MG_CSTEPS = 8;
+static_assert(MG_DEG >= 2 && MG_CSTEPS >= 3 && MG_CSTEPS < MG_MAX_STEPS, "multigrid step counts");
+
+template <typename T>
+int build_mg(pf_handle *h)
+{
+    MGHier<T> H;
+    memset(&H, 0, sizeof(H));
+    int nx = h->P.nx, ny = h->P.ny, L = 1;
+    while (L < MG_MAX_LEVELS && nx % 2 == 0 && ny % 2 == 0 && nx >= 16 && ny >= 16) {
+        nx /= 2;
+        ny /= 2;
+        L++;
+    }
+    H.L = L;
+    H.Lg = L;
+    H.deg = MG_DEG;
+    H.csteps = MG_CSTEPS;
+    nx = h->P.nx;
+    ny = h->P.ny;
+    for (int k = 0; k < L; k++) {
+        MGLevel<T> &V = H.lv[k];
+        V.nx = nx;
+        V.ny = ny;
+        const size_t b = sizeof(T) * (size_t)nx * (size_t)ny;
+        if (k == 0) {
+            V.lam = (T *)h->lam;
+            V.mu = (T *)h->mu;
+            V.dinv = (T *)h->diag;
+        } else if (H.Lg == L && (long long)nx * ny <= mg_block_nodes<T>()) {
+            H.Lg = k;
+        }
+        // block-run levels keep their arrays in shared memory; the top one
+        // still publishes its correction (xpost) for the grid level above
+        const bool blk = k > 0 && H.Lg <= k;
+        if (k > 0 && !blk) {
+            PF_TRY(h->alloc(&V.lam, b));
+            PF_TRY(h->alloc(&V.mu, b));
+            PF_TRY(h->alloc(&V.dinv, b));
+            for (int c = 0; c < 2; c++) PF_TRY(h->alloc(&V.f[c], b));
+        }
+        for (int c = 0; c < 2; c++) {
+            PF_TRY(h->alloc(&V.xpost[c], b));
+            if (blk) continue;
+            PF_TRY(h->alloc(&V.xpre[c], b));
+            for (int q = 0; q < 2; q++) {
+                PF_TRY(h->alloc(&V.r[q][c], b));
+                PF_TRY(h->alloc(&V.d[q][c], b));
+            }
+        }
+        nx /= 2;
+        ny /= 2;
+    }
+    // Chebyshev iteration on [bmin, bmax]: d_0 = D^-1 r_0 / theta,
+    // rho_j = 1 / (2 sigma - rho_{j-1}), d_j = rho_j rho_{j-1} d_{j-1} + 2 rho_j / delta D^-1 r_j
+    const double bmax = 1.02 * element_bound(h->cfg.p.nu), bmin = bmax / 30.0;
+    const double theta = 0.5 * (bmax + bmin), delta = 0.5 * (bmax - bmin), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    H.c1[0] = T(0);
+    H.c2[0] = (T)(1.0 / theta);
+    for (int j = 1; j < MG_MAX_STEPS; j++) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        H.c1[j] = (T)(rn * rho);
+        H.c2[j] = (T)(2.0 * rn / delta);
+        rho = rn;
+    }
+    if (!h->d_mg) PF_TRY(h->alloc(&h->d_mg, sizeof(H)));
+    return h->cuda(cudaMemcpy(h->d_mg, &H, sizeof(H), cudaMemcpyHostToDevice), "multigrid descriptor");
+}
+
 template <typename T, int D>
 int setup_cg_launch(pf_handle *h)
 {
     const bool fp64 = sizeof(T) == 8;
     h->pcg_shape = h->cfg.pcg_tile > 0 ? h->cfg.pcg_tile - 1 : default_pcg_shape(D, h->P.N, fp64);
     h->cg_block = h->pcg_shape ? tile_threads<D, 1>() : tile_threads<D, 0>();     // one thread per tile node
+    h->mg = D == 2 && h->cfg.precond == PF_PC_MG;
+    if constexpr (D == 2) {
+        if (h->mg) PF_TRY(build_mg<T>(h));
+    }
     int per_sm = 0;
-    cudaError_t e = D == 2 ? pcg2_occupancy(fp64, h->pcg_shape, h->cg_block, &per_sm)
-                           : pcg3_occupancy(fp64, h->pcg_shape, h->cg_block, &per_sm);
+    cudaError_t e = D == 2 ? pcg2_occupancy(fp64, h->pcg_shape, h->mg, h->cg_block, &per_sm)
+                           : pcg3_occupancy(fp64, h->pcg_shape, h->mg, h->cg_block, &per_sm);
     if (e != cudaSuccess) return h->cuda(e, "occupancy query");
     if (per_sm < 1) return h->fail(PF_ECUDA, "CG kernel cannot be resident");
     if (per_sm > 4) per_sm = 4;
@@ -373,6 +486,7 @@ PCGArgs<T, D> pcg_args(pf_handle *m)
     A.sc = m->sc; A.dg = m->dg;
     A.rtol = m->cfg.cg_rtol; A.maxit = m->cfg.cg_maxit;
     A.warm = m->cfg.warm_start != PF_WS_ZERO ? 1 : 0;
+    A.mg = (const MGHier<T> *)m->d_mg;
     return A;
 }
 
@@ -569,8 +683,8 @@ int launch_step(pf_handle *h, cudaStream_t s, int k)
         }
         h->mark_begin(PF_K_CG, s);
         const bool fp64 = sizeof(T) == 8;
-        cudaError_t e = D == 2 ? pcg2_launch(fp64, h->pcg_shape, h->d_pcg_jobs, n, h->pcg_grid, h->cg_block, s)
-                               : pcg3_launch(fp64, h->pcg_shape, h->d_pcg_jobs, n, h->pcg_grid, h->cg_block, s);
+        cudaError_t e = D == 2 ? pcg2_launch(fp64, h->pcg_shape, h->mg, h->d_pcg_jobs, n, h->pcg_grid, h->cg_block, s)
+                               : pcg3_launch(fp64, h->pcg_shape, h->mg, h->d_pcg_jobs, n, h->pcg_grid, h->cg_block, s);
         h->mark_end(s);
         if (e != cudaSuccess) return h->cuda(e, "cooperative CG launch");
         h->mark_begin(PF_K_RETURN, s);
@@ -898,6 +1012,11 @@ int create_one(const pf_config *cfg, pf_handle **out, std::string &err)
     }
     if (c.mechanics && (c.cg_maxit <= 0 || !(c.cg_rtol > 0.0))) { err = "cg_maxit must be > 0 and cg_rtol > 0"; return PF_EINVAL; }
     if (c.pcg_tile < 0 || c.pcg_tile > PCG_SHAPES) { err = "pcg_tile must be 0 (library choice), 1 or 2"; return PF_EINVAL; }
+    if (c.precond != PF_PC_AUTO && c.precond != PF_PC_JACOBI && c.precond != PF_PC_MG) {
+        err = "precond must be PF_PC_AUTO, PF_PC_JACOBI or PF_PC_MG";
+        return PF_EINVAL;
+    }
+    if (c.precond == PF_PC_MG && c.ndim != 2) { err = "precond PF_PC_MG is 2D only"; return PF_EINVAL; }
     if (!(c.p.nu > -1.0 && c.p.nu < 0.5) || !(c.p.E_s > 0.0) || !(c.p.E_g_ratio > 0.0)) { err = "elastic constants out of range"; return PF_EINVAL; }
     const long long N = (long long)c.nx * c.ny * (c.ndim == 3 ? c.nz : 1);
     if (N > (1LL << 31)) { err = "grid too large (more than 2^31 cells)"; return PF_EINVAL; }
@@ -968,8 +1087,8 @@ int pf_batch_create(const pf_config *cfgs, int n, pf_handle **out)
     if (!cfgs || n < 1) { g_create_error = "cfgs is NULL or n < 1"; return PF_EINVAL; }
     for (int i = 1; i < n; i++) {
         if (cfgs[i].ndim != cfgs[0].ndim || cfgs[i].precision != cfgs[0].precision
-            || (cfgs[i].mechanics != 0) != (cfgs[0].mechanics != 0)) {
-            g_create_error = "batch instances must share ndim, precision and mechanics";
+            || (cfgs[i].mechanics != 0) != (cfgs[0].mechanics != 0) || cfgs[i].precond != cfgs[0].precond) {
+            g_create_error = "batch instances must share ndim, precision, mechanics and precond";
             return PF_EINVAL;
         }
     }
@@ -1001,6 +1120,7 @@ int pf_batch_create(const pf_config *cfgs, int n, pf_handle **out)
     b->cg_block = m0->cg_block;
     b->cg_per_sm = m0->cg_per_sm;
     b->pcg_shape = m0->pcg_shape;
+    b->mg = m0->mg;
     for (pf_handle *m : b->members) b->bytes += m->bytes;
     cudaError_t e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking);
     if (e != cudaSuccess) {

@@ -21,6 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOTCONV, PF_ENONFINITE, PF_ETIMEOUT, PF_ESTATE = range(8)
 PF_FP64, PF_MIXED = 0, 1
 PF_WS_ZERO, PF_WS_PREV, PF_WS_LEARNED = 0, 1, 2
+PF_PC_AUTO, PF_PC_JACOBI, PF_PC_MG = 0, 1, 2
 PF_HOST, PF_DEVICE = 0, 1
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_ENOTCONV",
@@ -37,7 +38,8 @@ class pf_config(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mechanics", ctypes.c_int), ("plasticity", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("cg_maxit", ctypes.c_int), ("cg_rtol", ctypes.c_double),
-                ("dt", ctypes.c_double), ("p", pf_params), ("pcg_tile", ctypes.c_int)]
+                ("dt", ctypes.c_double), ("p", pf_params), ("pcg_tile", ctypes.c_int),
+                ("precond", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)

@@ -90,3 +90,12 @@ def test_create_rejects_unknown_pcg_tile(lib):
     cfg = make_config((16, 16), workloads.params(), pcg_tile=3)
     rc, h = native.pf_create(cfg)
     assert rc == native.PF_EINVAL and "pcg_tile" in native.pf_last_error(None)
+
+
+def test_create_rejects_bad_precond(lib):
+    cfg = make_config((16, 16), workloads.params(), precond=3)
+    rc, h = native.pf_create(cfg)
+    assert rc == native.PF_EINVAL and "precond" in native.pf_last_error(None)
+    cfg = make_config((8, 8, 8), workloads.params(), precond="mg")
+    rc, h = native.pf_create(cfg)
+    assert rc == native.PF_EINVAL and "2D only" in native.pf_last_error(None)
