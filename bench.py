@@ -102,6 +102,7 @@ class ClockSampler:
 
 
 WORKLOAD = "coreshell512"
+PRECOND = "auto"
 
 
 def workload_fields():
@@ -113,7 +114,7 @@ def workload_params(precision):
     from paper_2111_11538_gb300 import workloads
     # both forms solve to the workload's CG residual: the mixed form reaches
     # it through FP64 iterative refinement around its FP32 iteration
-    return dict(workloads.WORKLOADS[WORKLOAD]["params"])
+    return dict(workloads.WORKLOADS[WORKLOAD]["params"], precond=PRECOND)
 
 
 def run_gpu(precision, steps, warmup, fields, profile=True, warm=None, net=None):
@@ -193,7 +194,7 @@ def run_batch(precision, steps, warmup, count=64, seed=4, profile=True, rank=0, 
     mine = sharding.shard([sharding.instance_cost((d["n"], d["n"])) for d in desc], world)[rank]
     desc = [desc[i] for i in mine]
     count = len(desc)
-    base = workloads.WORKLOADS["batch64"]["params"]
+    base = dict(workloads.WORKLOADS["batch64"]["params"], precond=PRECOND)
     shapes = [(d["n"], d["n"]) for d in desc]
     prms = [dict(base, prestress=d["prestress"]) for d in desc]
     b = Batch(shapes, prms, precision=precision)
@@ -342,9 +343,12 @@ def main():
                          "print a short line")
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"],
                     help="profiling aid: run one method only and print a short line")
+    ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "mg"],
+                    help="CG preconditioner (auto: the library's choice for the grid)")
     args = ap.parse_args()
-    global WORKLOAD
+    global WORKLOAD, PRECOND
     WORKLOAD = args.workload
+    PRECOND = args.precond
     if args.warmup < 3:
         args.warmup = 3
 

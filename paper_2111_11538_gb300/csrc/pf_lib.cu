@@ -371,26 +371,45 @@ double element_bound(double nu)
 // sizes stay even and the coarse grid keeps >= 8 nodes per axis; levels of
 // at most mg_block_nodes<T>() nodes are run by one block in shared memory;
 // Chebyshev coefficients over [b/30, b] with b 2% above the element bound.
-// The device descriptor is written once (the arrays never move).  The
-// kernel wants deg >= 2 and csteps >= 3 (their last sweep is a Chebyshev
-// step, whose epilogue applies the final pointwise step).
-constexpr int MG_DEG = 2, MG_CSTEPS = 8;
-static_assert(MG_DEG >= 2 && MG_CSTEPS >= 3 && MG_CSTEPS < MG_MAX_STEPS, "multigrid step counts");
+// The device descriptor is written once (the arrays never move).
+// Smoothing steps per level: one on the finest (its sweeps are the
+// expensive ones, and a second step there does not lower the iteration
+// count), two on the other grid levels, three on the block-run levels
+// (cheap: shared memory, no grid barrier); the coarsest solve takes
+// MG_CSTEPS (>= 3: its last sweep is then a Chebyshev step, whose epilogue
+// applies the final pointwise step).
+constexpr int MG_DEG_FINE = 1, MG_DEG_GRID = 2, MG_DEG_BLOCK = 3, MG_CSTEPS = 8;
+static_assert(MG_CSTEPS >= 3 && MG_CSTEPS < MG_MAX_STEPS && MG_DEG_BLOCK + 1 < MG_MAX_STEPS, "multigrid step counts");
+
+// Levels of the multigrid hierarchy of an nx x ny grid.
+int mg_levels(int nx, int ny)
+{
+    int L = 1;
+    while (L < MG_MAX_LEVELS && nx % 2 == 0 && ny % 2 == 0 && nx >= 16 && ny >= 16) {
+        nx /= 2;
+        ny /= 2;
+        L++;
+    }
+    return L;
+}
+
+// PF_PC_AUTO: multigrid for 2D grids with at least three levels (sizes
+// divisible by 4 and >= 32), where it needs a small fraction of Jacobi's
+// iterations and, measured on GB300, less time; Jacobi otherwise.
+bool auto_mg(const pf_config &c)
+{
+    return c.ndim == 2 && c.mechanics && mg_levels(c.nx, c.ny) >= 3;
+}
 
 template <typename T>
 int build_mg(pf_handle *h)
 {
     MGHier<T> H;
     memset(&H, 0, sizeof(H));
-    int nx = h->P.nx, ny = h->P.ny, L = 1;
-    while (L < MG_MAX_LEVELS && nx % 2 == 0 && ny % 2 == 0 && nx >= 16 && ny >= 16) {
-        nx /= 2;
-        ny /= 2;
-        L++;
-    }
+    int nx = h->P.nx, ny = h->P.ny;
+    const int L = mg_levels(nx, ny);
     H.L = L;
     H.Lg = L;
-    H.deg = MG_DEG;
     H.csteps = MG_CSTEPS;
     nx = h->P.nx;
     ny = h->P.ny;
@@ -427,6 +446,7 @@ int build_mg(pf_handle *h)
         nx /= 2;
         ny /= 2;
     }
+    for (int k = 0; k < L; k++) H.deg[k] = k == 0 ? MG_DEG_FINE : (k < H.Lg ? MG_DEG_GRID : MG_DEG_BLOCK);
     // Chebyshev iteration on [bmin, bmax]: d_0 = D^-1 r_0 / theta,
     // rho_j = 1 / (2 sigma - rho_{j-1}), d_j = rho_j rho_{j-1} d_{j-1} + 2 rho_j / delta D^-1 r_j
     const double bmax = 1.02 * element_bound(h->cfg.p.nu), bmin = bmax / 30.0;
@@ -448,9 +468,11 @@ template <typename T, int D>
 int setup_cg_launch(pf_handle *h)
 {
     const bool fp64 = sizeof(T) == 8;
-    h->pcg_shape = h->cfg.pcg_tile > 0 ? h->cfg.pcg_tile - 1 : default_pcg_shape(D, h->P.N, fp64);
+    h->mg = D == 2 && (h->cfg.precond == PF_PC_MG || (h->cfg.precond == PF_PC_AUTO && auto_mg(h->cfg)));
+    // the V-cycle's coarse grid levels have few tiles: the 32x16 tile (one
+    // 512-thread block per SM) halves the blocks in each of their barriers
+    h->pcg_shape = h->cfg.pcg_tile > 0 ? h->cfg.pcg_tile - 1 : (h->mg ? 1 : default_pcg_shape(D, h->P.N, fp64));
     h->cg_block = h->pcg_shape ? tile_threads<D, 1>() : tile_threads<D, 0>();     // one thread per tile node
-    h->mg = D == 2 && h->cfg.precond == PF_PC_MG;
     if constexpr (D == 2) {
         if (h->mg) PF_TRY(build_mg<T>(h));
     }
@@ -595,8 +617,9 @@ int build_plan(pf_handle *h)
         const int TY = h->pcg_shape ? Tile<D, 1>::Y : Tile<D, 0>::Y;
         const int TZ = h->pcg_shape ? Tile<D, 1>::Z : Tile<D, 0>::Z;
         // Jacobi-PCG iteration counts grow with the grid's linear size, so
-        // an instance's work per solve is ~ tiles x linear size: blocks are
-        // shared out in proportion to that, so that instances finish together
+        // an instance's work per solve is ~ tiles x linear size (MG: ~ tiles):
+        // blocks are shared out in proportion to that, so that instances
+        // finish together
         std::vector<long long> tiles(n);
         std::vector<double> work(n);
         double wtot = 0.0;
@@ -604,7 +627,7 @@ int build_plan(pf_handle *h)
             const Params &P = I[i]->P;
             tiles[i] = (long long)((P.nx + TX - 1) / TX) * ((P.ny + TY - 1) / TY) * (D == 3 ? (P.nz + TZ - 1) / TZ : 1);
             const double lin = (double)std::max(P.nx, std::max(P.ny, D == 3 ? P.nz : 1));
-            work[i] = (double)tiles[i] * lin;
+            work[i] = (double)tiles[i] * (I[i]->mg ? 1.0 : lin);     // MG: iterations ~ independent of size
             wtot += work[i];
         }
         const long long cap = (long long)h->cg_per_sm * h->sms;
@@ -1092,6 +1115,10 @@ int pf_batch_create(const pf_config *cfgs, int n, pf_handle **out)
             return PF_EINVAL;
         }
     }
+    // PF_PC_AUTO picks one preconditioner for the whole batch (one kernel
+    // serves all instances): multigrid only if every instance qualifies
+    bool all_mg = true;
+    for (int i = 0; i < n; i++) all_mg = all_mg && auto_mg(cfgs[i]);
     pf_handle *b = new (std::nothrow) pf_handle();
     if (!b) { g_create_error = "host allocation failed"; return PF_ENOMEM; }
     b->is_batch = true;
@@ -1099,7 +1126,9 @@ int pf_batch_create(const pf_config *cfgs, int n, pf_handle **out)
     for (int i = 0; i < n; i++) {
         pf_handle *m = nullptr;
         std::string err;
-        int rc = create_one(&cfgs[i], &m, err);
+        pf_config ci = cfgs[i];
+        if (ci.precond == PF_PC_AUTO) ci.precond = all_mg ? PF_PC_MG : PF_PC_JACOBI;
+        int rc = create_one(&ci, &m, err);
         if (rc != PF_OK) {
             char buf[64];
             snprintf(buf, sizeof(buf), "instance %d: ", i);

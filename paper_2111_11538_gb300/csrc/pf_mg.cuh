@@ -44,7 +44,7 @@ struct MGHier {
     int L;                         // levels
     int Lg;                        // levels [0, Lg) run on the whole grid, [Lg, L) by the job's first
                                    // block in shared memory (mg_block_words)
-    int deg;                       // Chebyshev steps of each pre- and post-smoothing
+    int deg[MG_MAX_LEVELS];        // Chebyshev steps of each pre- and post-smoothing, per level
     int csteps;                    // Chebyshev steps of the coarsest solve (>= 2)
     T c1[MG_MAX_STEPS], c2[MG_MAX_STEPS];   // d_j = c1[j] d_{j-1} + c2[j] D^-1 r_j  (c1[0] = 0)
     MGLevel<T> lv[MG_MAX_LEVELS];
@@ -359,7 +359,7 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
 {
     constexpr int NV = 3;
     const bool lead = threadIdx.x == 0;
-    const int L = H.L, Lgw = H.Lg < H.L ? H.Lg : H.L, deg = H.deg, cs = H.csteps;
+    const int L = H.L, Lgw = H.Lg < H.L ? H.Lg : H.L, cs = H.csteps;
     const MGLevel<T> &L0 = H.lv[0];
     unsigned int *bc = A.bar_count, *bg = A.bar_gen;
 
@@ -403,7 +403,7 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
     // residual after its pre-smoothing, at node (gx, gy) of level k
     auto restrict_g = [&](int k, int gx, int gy, T (&f)[2]) {
         const MGLevel<T> &F = H.lv[k - 1];
-        const int pf = deg & 1;
+        const int pf = H.deg[k - 1] & 1;
         f[0] = T(0);
         f[1] = T(0);
 #pragma unroll
@@ -445,8 +445,9 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
             });
     };
     // first post-smoothing sweep of grid level k: x = x_pre + P e_{k+1}
-    // (e: level k+1's final correction), r = f - A x
-    auto post_first = [&](int k, int par, int cur) {
+    // (e: level k+1's final correction), r = f - A x; last (one-step
+    // smoothing): apply that step, x + c2[0] D^-1 r, as the final correction
+    auto post_first = [&](int k, int par, int cur, bool last) {
         const MGLevel<T> &V = H.lv[k];
         const MGLevel<T> &C = H.lv[k + 1];
         mg_sweep<T, TX, TY, false>(
@@ -467,22 +468,28 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
                 }
             },
             [&](int n, const T (&v)[2], const T (&q)[2], const T (&)[3]) {
+                const T di = last ? H.c2[0] * __ldcg(V.dinv + n) : T(0);
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    V.xpost[c][n] = v[c];
                     const T f = k == 0 ? __ldcg(A.r[cur][c] + n) : __ldcg(V.f[c] + n);
-                    V.r[1 - par][c][n] = f - q[c];
+                    if (last) {
+                        V.xpost[c][n] = v[c] + di * (f - q[c]);
+                    } else {
+                        V.xpost[c][n] = v[c];
+                        V.r[1 - par][c][n] = f - q[c];
+                    }
                 }
             });
     };
-    // post-smoothing of grid level k (deg >= 2: the last sweep is a Chebyshev step)
+    // post-smoothing of grid level k
     auto post = [&](int k, int cur) {
-        int par = deg & 1;
-        post_first(k, par, cur);
+        const int dk = H.deg[k];
+        int par = dk & 1;
+        post_first(k, par, cur, dk == 1);
         if (!grid_sync(bc, bg, err, nbk)) return false;
         par ^= 1;
-        for (int j = 0; j + 1 < deg; j++) {
-            cheb(k, j, par, true, j + 2 == deg);
+        for (int j = 0; j + 1 < dk; j++) {
+            cheb(k, j, par, true, j + 2 == dk);
             if (!grid_sync(bc, bg, err, nbk)) return false;
             par ^= 1;
         }
@@ -494,7 +501,7 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
         if (!grid_sync(bc, bg, err, nbk)) return false;
         int par = 1;
         const bool co = k == L - 1;
-        const int nk = co ? cs - 1 : deg;
+        const int nk = co ? cs - 1 : H.deg[k];
         for (int j = 1; j < nk; j++) {
             cheb(k, j, par, false, co && j + 1 == nk);
             if (!grid_sync(bc, bg, err, nbk)) return false;
@@ -575,10 +582,11 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
                 }
             });
         const bool co = k == L - 1;
-        const int nk = co ? cs - 1 : deg;
+        const int nk = co ? cs - 1 : H.deg[k];
         for (int j = 1; j < nk; j++) bcheb(k, j, co && j + 1 == nk);
     };
     auto bpost = [&](int k) {
+        const int dk = H.deg[k];
         const BLevel<T> B = blevel<T>(sblk, H, k);
         const BLevel<T> C = blevel<T>(sblk, H, k + 1);
         blk_sweep<T>(
@@ -598,13 +606,15 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
                 }
             },
             [&](int i, const T (&v)[2], const T (&q)[2]) {
+                const T di = H.c2[0] * B.dinv[i];
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    B.x[c][i] = v[c];
-                    B.r[c][i] = B.f[c][i] - q[c];
+                    const T rn = B.f[c][i] - q[c];
+                    B.x[c][i] = dk == 1 ? v[c] + di * rn : v[c];
+                    B.r[c][i] = rn;
                 }
             });
-        for (int j = 0; j + 1 < deg; j++) bcheb(k, j, j + 2 == deg);
+        for (int j = 0; j + 1 < dk; j++) bcheb(k, j, j + 2 == dk);
     };
 
     int cur = 0;
@@ -684,7 +694,7 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
         // ---- rest of the V-cycle
         {
             int par = 1;
-            const int n0 = L == 1 ? cs - 1 : deg;
+            const int n0 = L == 1 ? cs - 1 : H.deg[0];
             for (int j = 1; j < n0; j++) {
                 cheb(0, j, par, false, L == 1 && j + 1 == n0);
                 if (!grid_sync(bc, bg, err, nbk)) return -1;
