@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
     // the block-run levels' arrays: dynamic shared memory (pcg_dyn_smem)
     T *sblk = reinterpret_cast<T *>(pcg_dyn);
     if constexpr (MG) {
-        if (!mg_setup<T>(*A.mg, sblk, A.bar_count, A.bar_gen, err, bid, nbk)) return;
+        if (!mg_setup<T>(*A.mg, A.bar_count, A.bar_gen, err, bid, nbk)) return;
     }
 
     for (int outer = 0; outer < (refine ? MAX_OUTER : 1); outer++) {
@@ -525,6 +525,11 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
                 xeT[v] = s_xe[v];
             }
             Acc<double> acc[16];
+            if constexpr (MG) {
+                // 2D multigrid variant: the tiled FP64 set-up (cells once per
+                // tile) in the dynamic shared memory
+                setup_tiled<T, TX, TY>(A, use_x, refine, xe64, reinterpret_cast<double *>(pcg_dyn), acc, bid, nbk);
+            } else
             for (long long n = t0; n < N; n += st) {
                 double bv[D], rv[D];
                 if (refine) {
@@ -949,11 +954,18 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
 // cooperative launch and the upload of that unit's copy of the element
 // tables (constant memory is per unit).  Dynamic shared memory: the 3D FP32
 // cell buffer of the 16x4x4 tile; with MG, the arrays of the block-run
-// levels (the bound for any hierarchy, so one attribute serves all).
+// levels (the bound for any hierarchy, so one attribute serves all), which
+// the FP64 set-up sweep uses as scratch before them.
 template <typename T, int D>
 size_t pcg_dyn_smem(int shape, bool mg)
 {
-    if (D == 2 && mg) return sizeof(T) * (size_t)mg_block_words_cap(mg_block_nodes<T>());
+    if (D == 2 && mg) {
+        // the block-run levels' arrays, or the set-up sweep's FP64 scratch
+        const size_t blk = sizeof(T) * (size_t)mg_block_words_cap(mg_block_nodes<T>());
+        const size_t stp = sizeof(double) * (size_t)(shape == 1 ? setup_tiled_doubles<Tile<2, 1>::X, Tile<2, 1>::Y>()
+                                                                : setup_tiled_doubles<Tile<2, 0>::X, Tile<2, 0>::Y>());
+        return blk > stp ? blk : stp;
+    }
     if (D != 3 || sizeof(T) != 4 || shape != 0) return 0;
     constexpr int HC = (Tile<3, 0>::X + 1) * (Tile<3, 0>::Y + 1) * (Tile<3, 0>::Z + 1);
     return sizeof(float) * 20 * HC;

@@ -321,11 +321,10 @@ __device__ void mg_coarsen_blk(const T *fl, const T *fm, int fnx, bool global, c
 }
 
 // Hierarchy set-up at the start of a solve (the cell moduli change every
-// step): grid levels below Lg with a barrier after each, then the job's
-// first block fills the shared arrays of the rest.  Returns false if a
-// barrier timed out.
+// step): the grid levels below Lg, with a barrier after each.  Returns false
+// if a barrier timed out.
 template <typename T>
-__device__ bool mg_setup(const MGHier<T> &H, T *sblk, unsigned int *bc, unsigned int *bg, int *err, int bid, int nbk)
+__device__ bool mg_setup(const MGHier<T> &H, unsigned int *bc, unsigned int *bg, int *err, int bid, int nbk)
 {
     const int Lgw = H.Lg < H.L ? H.Lg : H.L;
     const long long t0 = bid * (long long)blockDim.x + threadIdx.x, st = (long long)nbk * blockDim.x;
@@ -333,8 +332,17 @@ __device__ bool mg_setup(const MGHier<T> &H, T *sblk, unsigned int *bc, unsigned
         mg_coarsen<T>(H.lv[k - 1], H.lv[k], t0, st);
         if (!grid_sync(bc, bg, err, nbk)) return false;
     }
-    if (bid == 0)
-        for (int k = Lgw; k < H.L; k++) {
+    return true;
+}
+
+// The shared arrays of the block-run levels, filled by the job's first
+// block at the start of every CG pass (the residual sweep before it uses
+// the same shared memory as scratch).
+template <typename T>
+__device__ void mg_setup_block(const MGHier<T> &H, T *sblk)
+{
+    const int Lgw = H.Lg < H.L ? H.Lg : H.L;
+    for (int k = Lgw; k < H.L; k++) {
             const BLevel<T> C = blevel<T>(sblk, H, k);
             if (k == Lgw) {
                 mg_coarsen_blk<T>(H.lv[k - 1].lam, H.lv[k - 1].mu, H.lv[k - 1].nx, true, C);
@@ -342,8 +350,112 @@ __device__ bool mg_setup(const MGHier<T> &H, T *sblk, unsigned int *bc, unsigned
                 const BLevel<T> F = blevel<T>(sblk, H, k - 1);
                 mg_coarsen_blk<T>(F.lam, F.mu, F.nx, false, C);
             }
+    }
+}
+
+// Shared memory (in doubles) of setup_tiled for a TX x TY tile: the FP64
+// operand on the tile halo and five values per halo cell.
+template <int TX, int TY>
+__host__ __device__ constexpr int setup_tiled_doubles() { return 2 * (TX + 2) * (TY + 2) + 5 * (TX + 1) * (TY + 1); }
+
+// The set-up sweep of one CG pass, 2D, over node tiles: right-hand side
+// b = sum_e Bbar^T sig*, Jacobi diagonal, r = b - A x (x: the FP64 solution
+// in refinement mode, else the displacement; mean strain xe) with the
+// operator applied in FP64 from per-cell average stress and hourglass forces
+// computed once per tile (dscr: setup_tiled_doubles<TX, TY>() doubles of
+// shared memory), and the per-node sums of the mean-strain rows: acc[0]
+// ||b||^2, [1] ||r||^2, [2] sum lam, [3] sum mu, [4..6] sum sig*, [10..12]
+// sum of the own cells' stress of x without the mean strain.  Also clears
+// p, s and (when x is not used or in refinement mode) the iterate.
+template <typename T, int TX, int TY>
+__device__ void setup_tiled(const PCGArgs<T, 2> &A, bool use_x, bool refine, const double *xe, double *dscr,
+                            Acc<double> (&acc)[16], int bid, int nbk)
+{
+    const Params &P = A.P;
+    constexpr int HX = TX + 2, HY = TY + 2, CX = TX + 1, CY = TY + 1, HN = HX * HY, HC = CX * CY, NT = TX * TY;
+    double *hu = dscr, *hc = dscr + 2 * HN;
+    const int nx = P.nx, ny = P.ny;
+    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntiles = ntx * nty;
+    const bool small = nx < HX || ny < HY;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    for (int tile = bid; tile < ntiles; tile += nbk) {
+        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+        if (use_x) {
+            for (int h = threadIdx.x; h < HN; h += NT) {
+                const int g = mg_wrap(x0 - 1 + h % HX, nx, small) + nx * mg_wrap(y0 - 1 + h / HX, ny, small);
+                hu[h] = refine ? __ldcg(A.x64[0] + g) : (double)A.x[0][g];
+                hu[HN + h] = refine ? __ldcg(A.x64[1] + g) : (double)A.x[1][g];
+            }
+            __syncthreads();
+            for (int h = threadIdx.x; h < HC; h += NT) {
+                const int cx = h % CX, cy = h / CX;
+                const int g = mg_wrap(x0 - 1 + cx, nx, small) + nx * mg_wrap(y0 - 1 + cy, ny, small);
+                double uc[4][2];
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    const int hn = (cx + (b & 1)) + HX * (cy + (b >> 1));
+                    uc[b][0] = hu[hn];
+                    uc[b][1] = hu[HN + hn];
+                }
+                const double l = (double)A.lam[g], m = (double)A.mu[g];
+                double s3[3], fh[2], sx[3];
+                cell_force2<double>(l, m, uc, s3, fh);
+                voigt_stress<double, 2>(l, m, xe, sx);
+                hc[h] = s3[0] + sx[0];
+                hc[HC + h] = s3[1] + sx[1];
+                hc[2 * HC + h] = s3[2] + sx[2];
+                hc[3 * HC + h] = fh[0];
+                hc[4 * HC + h] = fh[1];
+            }
+            __syncthreads();
         }
-    return true;
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx < nx && gy < ny) {
+            const int n = gx + nx * gy, lx = tx + 1, ly = ty + 1;
+            double b[2], ax[2] = {0.0, 0.0}, dgn, so[3], deo[3] = {0.0, 0.0, 0.0}, lo, mo, unused[2], unused3[3];
+            node_setup<T, double, double, 2>(P, n, A.lam, A.mu, A.sig, A.x64, xe, false, b, unused, dgn, so, unused3, lo,
+                                             mo);
+            if (use_x) {
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    const int cl = (lx - (a & 1)) + CX * (ly - (a >> 1));
+                    const double s3[3] = {hc[cl], hc[HC + cl], hc[2 * HC + cl]};
+                    const double fh[2] = {hc[3 * HC + cl], hc[4 * HC + cl]};
+                    double f[2];
+                    node_force2<double>(a, s3, fh, f);
+                    ax[0] += f[0];
+                    ax[1] += f[1];
+                }
+                // the own cell's stress of x without the mean strain
+                const int c0 = lx + CX * ly;
+                double sx[3];
+                voigt_stress<double, 2>(lo, mo, xe, sx);
+                deo[0] = hc[c0] - sx[0];
+                deo[1] = hc[HC + c0] - sx[1];
+                deo[2] = hc[2 * HC + c0] - sx[2];
+            }
+            A.dinv[n] = (T)(1.0 / dgn);
+            acc[2].add(lo);
+            acc[3].add(mo);
+#pragma unroll
+            for (int v = 0; v < 3; v++) {
+                acc[4 + v].add(so[v]);
+                acc[10 + v].add(deo[v]);
+            }
+#pragma unroll
+            for (int d = 0; d < 2; d++) {
+                const double rv = b[d] - ax[d];
+                if (refine && !use_x) A.x64[d][n] = 0.0;
+                if (refine || !use_x) A.x[d][n] = T(0);
+                A.p[d][n] = T(0);
+                A.s[0][d][n] = T(0);
+                A.r[0][d][n] = (T)rv;
+                acc[0].addprod(b[d], b[d]);
+                acc[1].addprod(rv, rv);
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // One pass of MG-preconditioned CG (the Chronopoulos-Gear form of the
@@ -616,6 +728,8 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
             });
         for (int j = 0; j + 1 < dk; j++) bcheb(k, j, j + 2 == dk);
     };
+
+    if (bid == 0 && Lgw < L) mg_setup_block<T>(H, sblk);
 
     int cur = 0;
     bool first = true;
