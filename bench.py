@@ -34,6 +34,22 @@ L2_BYTES = 129 * 1024 * 1024
 # set-up (eigenstress, Lame, warm start read; residual and diagonal written).
 CG_ITER_WORDS = {2: 16, 3: 24}
 CG_INIT_WORDS = {2: 10, 3: 15}
+# The same for the multigrid-preconditioned solve (2D), per finest-level node
+# and V-cycle iteration: finest level 29 words (CG update fused into the
+# first smoothing sweep: r, w, s, u, p, x, diag, lam, mu read; p, x, s, r and
+# the smoother's x, r, d written) + 9.5 (post-smoothing) + 8 (w = A u); each
+# coarse grid level 54.5 words per coarse node (restriction, two Chebyshev
+# steps before and after the coarse correction), 1/4 of the nodes per
+# level, so ~18 over levels 1-3; the shared-memory levels move no DRAM.
+# Set-up: one FP64 residual pass (x64, lam, mu, eigenstress read; diag, r,
+# p, s, x written) and one refinement update per launch (more passes run at
+# tight tolerances, so the figure is a lower bound).
+MG_ITER_WORDS = 64
+MG_INIT_WORDS = 28
+# DRAM bytes per k_pcg launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# from one ncu capture of the current kernel on this workload
+# (profiles/k_pcg_mg_coreshell512_mixed.md); None where not captured.
+PCG_TRAFFIC = {"mg": 9.71e6 + 1.06e6, "jacobi": None}
 # Algorithmic bytes per cell of the fused explicit update (k_fused): theta,
 # phi_g, x_O, x_H, x_H2O, tr eps_e, |dev eps_e|^2, mobility read, the 1-byte
 # supply mask read, theta, x_O, x_H, x_H2O written.
@@ -147,6 +163,9 @@ def run_gpu(precision, steps, warmup, fields, profile=True, warm=None, net=None)
         total_ms += a.elapsed_time(b)
     prof = sim.profile_read() if profile else None
     diag = sim.diagnostics()
+    if prof is not None:
+        prof["precond"] = "mg" if diag["precond"] == 2 else "jacobi"
+        prof["mg_levels"] = diag["mg_levels"]
     out = sim.get_fields(keys=("phi_f", "phi_w", "xO", "xH", "xW", "sigma"))
     sim.close()
     return total_ms, prof, diag, out
@@ -355,6 +374,7 @@ def main():
     ws, rank, local = dist_setup()
     cfg = {"workload": "coreshell512_j2: 2D core-shell 512x512, radius 160, shell 32, J2 plasticity "
                        "sigma_Y=0.01E H=0.001E, CG warm start from previous step",
+           "precond": args.precond + (" (library choice: multigrid V-cycle for this grid)" if args.precond == "auto" else ""),
            "cells": 512 * 512, "l2": "flushed before every timed step (512 MB write)",
            "parallelism": "replicas" if ws > 1 else "single"}
 
@@ -446,8 +466,9 @@ def main():
 
     hbm, peak_kind = _load_peaks()
     nd = 2
-    b_iter = CG_ITER_WORDS[nd] * 4 * N
-    b_init = CG_INIT_WORDS[nd] * 4 * N
+    mg = prof.get("precond") == "mg"
+    b_iter = (MG_ITER_WORDS if mg else CG_ITER_WORDS[nd]) * 4 * N
+    b_init = (MG_INIT_WORDS if mg else CG_INIT_WORDS[nd]) * 4 * N
     cg_launches = prof["count"]["cg"]
     cg_ms = prof["ms"]["cg"]
     iters_timed = prof["cg_iters"]          # CG iterations of the timed solves
@@ -482,11 +503,15 @@ def main():
                        "kernel_ms": prof64["ms"]},
         "speedup_vs_fp64_plain": None,
         "error_vs_fp64": err,
-        "cg": {"rtol": workload_params("mixed")["cg_rtol"], "mixed": "FP32 Chronopoulos-Gear PCG passes inside FP64 iterative refinement", "iters_timed": iters_timed,
+        "cg": {"rtol": workload_params("mixed")["cg_rtol"],
+               "mixed": "FP32 Chronopoulos-Gear PCG passes inside FP64 iterative refinement",
+               "precond": prof.get("precond"), "mg_levels": prof.get("mg_levels"), "iters_timed": iters_timed,
                "iters_per_step": iters_timed / args.steps if args.steps else None},
         "kernel_ms": prof["ms"], "kernel_count": prof["count"],
-        "roofline": {"kernel": "k_pcg (persistent PCG)", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "traffic": None,
+        "roofline": {"kernel": "k_pcg (persistent PCG, %s)" % ("multigrid V-cycle" if mg else "Jacobi"),
+                     "bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
+                     "traffic": PCG_TRAFFIC["mg" if mg else "jacobi"],
                      "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
                      "algorithmic_bytes_per_launch": cg_bytes_per_launch},
         "roofline_stencil": stencil,

@@ -127,6 +127,8 @@ typedef struct {
     long long steps;                /* steps taken since pf_set_fields             */
     double dt;                      /* time step in use                            */
     int status;                     /* sticky status of the last pf_step call      */
+    int precond;                    /* preconditioner in use: PF_PC_JACOBI or PF_PC_MG */
+    int mg_levels;                  /* levels of the multigrid hierarchy (0: Jacobi)   */
 } pf_diag;
 
 typedef struct pf_handle pf_handle;

@@ -1302,6 +1302,8 @@ int pf_get_diagnostics(pf_handle *h, pf_diag *out)
     out->steps = h->steps;
     out->dt = h->P.dt;
     out->status = dg.status ? dg.status : sc.status;
+    out->precond = h->mg ? PF_PC_MG : PF_PC_JACOBI;
+    out->mg_levels = h->mg ? mg_levels(h->P.nx, h->P.ny) : 0;
     return PF_OK;
 }
 
