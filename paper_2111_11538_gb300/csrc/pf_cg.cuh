@@ -600,7 +600,15 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
                 S.prev_res = sqrt(rho);
                 // target of this pass: the requested tolerance, or in refinement
                 // mode what an FP32 iteration can deliver on this correction
-                target = refine ? fmax(0.5 * A.rtol * bnorm, A.eta * sqrt(rho)) : A.rtol * bnorm;
+                // (eta); when the final tolerance is within a factor 10 of that,
+                // the pass aims for it directly, which saves a pass that would
+                // otherwise start just above the tolerance
+                if (refine) {
+                    const double fin = 0.5 * A.rtol * bnorm, pass = A.eta * sqrt(rho);
+                    target = fin >= 0.1 * pass ? fin : pass;
+                } else {
+                    target = A.rtol * bnorm;
+                }
                 gamma = 0.0; delta = 0.0; gamma_prev = 1.0; alpha_prev = 1.0; alpha = 0.0; beta = 0.0;
                 S.inv_gamma = S.inv_gamma_prev = S.inv_alpha = S.inv_alpha_prev = 1.0;
                 it = 0;
@@ -955,16 +963,19 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
 // tables (constant memory is per unit).  Dynamic shared memory: the 3D FP32
 // cell buffer of the 16x4x4 tile; with MG, the arrays of the block-run
 // levels (the bound for any hierarchy, so one attribute serves all), which
-// the FP64 set-up sweep uses as scratch before them.
+// the FP64 set-up sweep uses as scratch before them, and the fused
+// two-step smoothing sweep's scratch.
 template <typename T, int D>
 size_t pcg_dyn_smem(int shape, bool mg)
 {
     if (D == 2 && mg) {
-        // the block-run levels' arrays, or the set-up sweep's FP64 scratch
-        const size_t blk = sizeof(T) * (size_t)mg_block_words_cap(mg_block_nodes<T>());
-        const size_t stp = sizeof(double) * (size_t)(shape == 1 ? setup_tiled_doubles<Tile<2, 1>::X, Tile<2, 1>::Y>()
-                                                                : setup_tiled_doubles<Tile<2, 0>::X, Tile<2, 0>::Y>());
-        return blk > stp ? blk : stp;
+        // the block-run levels' arrays (or, before them in each pass, the
+        // set-up sweep's FP64 scratch), then the fused two-step sweep's scratch
+        if (shape == 1)
+            return mg_pair_offset<T, Tile<2, 1>::X, Tile<2, 1>::Y>() +
+                   sizeof(T) * (size_t)sweep2_words<Tile<2, 1>::X, Tile<2, 1>::Y>();
+        return mg_pair_offset<T, Tile<2, 0>::X, Tile<2, 0>::Y>() +
+               sizeof(T) * (size_t)sweep2_words<Tile<2, 0>::X, Tile<2, 0>::Y>();
     }
     if (D != 3 || sizeof(T) != 4 || shape != 0) return 0;
     constexpr int HC = (Tile<3, 0>::X + 1) * (Tile<3, 0>::Y + 1) * (Tile<3, 0>::Z + 1);

@@ -270,6 +270,113 @@ __device__ __forceinline__ void blk_sweep(const BLevel<T> &B, T *scr, int nmax, 
     __syncthreads();
 }
 
+// Shared memory (words of T) of mg_sweep2 for a TX x TY tile: two operands
+// on the width-2 halo, the intermediate residual and second operand on the
+// width-1 halo, and five values per cell of the width-2 halo.
+template <int TX, int TY>
+__host__ __device__ constexpr int sweep2_words()
+{
+    return 4 * (TX + 4) * (TY + 4) + 4 * (TX + 2) * (TY + 2) + 5 * (TX + 3) * (TY + 3);
+}
+
+// Two consecutive operator products on each tile with no grid barrier
+// between them (the ring of halo nodes both need is recomputed by the
+// neighbouring tiles): val(gx, gy, v0, a0) gives the first operand v0 and an
+// auxiliary a0 on the width-2 halo; mid(g, v0, a0, q0, r1, v1) forms, on the
+// width-1 halo, from v0, a0 and q0 = A v0, an intermediate r1 and the second
+// operand v1; epi(n, v0, a0, r1, v1, q1) gets q1 = A v1 at every own node.
+// Scratch: sweep2_words<TX, TY>() words of shared memory at scr.
+template <typename T, int TX, int TY, class Val, class Mid, class Epi>
+__device__ __forceinline__ void mg_sweep2(int nx, int ny, const T *lam, const T *mu, int bid, int nbk, T *scr, Val &&val,
+                                          Mid &&mid, Epi &&epi)
+{
+    constexpr int AX = TX + 4, AY = TY + 4, AN = AX * AY;     // width-2 halo nodes
+    constexpr int BX = TX + 2, BY = TY + 2, BN = BX * BY;     // width-1 halo nodes
+    constexpr int CX = TX + 3, CY = TY + 3, CN = CX * CY;     // cells of the width-2 halo
+    constexpr int DX = TX + 1, DN = (TX + 1) * (TY + 1);      // cells of the width-1 halo
+    constexpr int NT = TX * TY;
+    T *v0 = scr, *a0 = scr + 2 * AN, *r1 = scr + 4 * AN, *v1 = r1 + 2 * BN, *cf = v1 + 2 * BN;
+    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntiles = ntx * nty;
+    const bool small = nx < AX || ny < AY;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    auto cells = [&](const T *u, int ux, int un, int ncx, int ncell, int ox, int oy) {
+        // cells with lower-left node (cx, cy) of the operand grid u (row
+        // length ux, un nodes per component), global origin (ox, oy)
+        for (int h = threadIdx.x; h < ncell; h += NT) {
+            const int cx = h % ncx, cy = h / ncx;
+            const int g = mg_wrap(ox + cx, nx, small) + nx * mg_wrap(oy + cy, ny, small);
+            T uc[4][2];
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const int hn = (cx + (b & 1)) + ux * (cy + (b >> 1));
+                uc[b][0] = u[hn];
+                uc[b][1] = u[un + hn];
+            }
+            T s3[3], fh[2];
+            cell_force2<T>(__ldcg(lam + g), __ldcg(mu + g), uc, s3, fh);
+            cf[h] = s3[0];
+            cf[CN + h] = s3[1];
+            cf[2 * CN + h] = s3[2];
+            cf[3 * CN + h] = fh[0];
+            cf[4 * CN + h] = fh[1];
+        }
+    };
+    auto force = [&](int lx, int ly, int ncx, T (&q)[2]) {
+        // q at the node whose lower-left cell is (lx, ly) in cell coordinates
+        q[0] = T(0);
+        q[1] = T(0);
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            const int cl = (lx - (a & 1)) + ncx * (ly - (a >> 1));
+            const T s3[3] = {cf[cl], cf[CN + cl], cf[2 * CN + cl]};
+            const T fh[2] = {cf[3 * CN + cl], cf[4 * CN + cl]};
+            T f[2];
+            node_force2<T>(a, s3, fh, f);
+            q[0] += f[0];
+            q[1] += f[1];
+        }
+    };
+    for (int tile = bid; tile < ntiles; tile += nbk) {
+        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+        for (int h = threadIdx.x; h < AN; h += NT) {
+            T v[2], a[2];
+            val(mg_wrap(x0 - 2 + h % AX, nx, small), mg_wrap(y0 - 2 + h / AX, ny, small), v, a);
+            v0[h] = v[0];
+            v0[AN + h] = v[1];
+            a0[h] = a[0];
+            a0[AN + h] = a[1];
+        }
+        __syncthreads();
+        cells(v0, AX, AN, CX, CN, x0 - 2, y0 - 2);
+        __syncthreads();
+        for (int h = threadIdx.x; h < BN; h += NT) {
+            const int mx = h % BX, my = h / BX, ah = (mx + 1) + AX * (my + 1);
+            T q[2];
+            force(mx + 1, my + 1, CX, q);
+            const T vv[2] = {v0[ah], v0[AN + ah]}, aa[2] = {a0[ah], a0[AN + ah]};
+            T rr[2], ww[2];
+            mid(mg_wrap(x0 - 1 + mx, nx, small) + nx * mg_wrap(y0 - 1 + my, ny, small), vv, aa, q, rr, ww);
+            r1[h] = rr[0];
+            r1[BN + h] = rr[1];
+            v1[h] = ww[0];
+            v1[BN + h] = ww[1];
+        }
+        __syncthreads();
+        cells(v1, BX, BN, DX, DN, x0 - 1, y0 - 1);
+        __syncthreads();
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx < nx && gy < ny) {
+            const int ah = (tx + 2) + AX * (ty + 2), bh = (tx + 1) + BX * (ty + 1);
+            T q[2];
+            force(tx + 1, ty + 1, DX, q);
+            const T vv[2] = {v0[ah], v0[AN + ah]}, aa[2] = {a0[ah], a0[AN + ah]};
+            const T rr[2] = {r1[bh], r1[BN + bh]}, ww[2] = {v1[bh], v1[BN + bh]};
+            epi(gx + nx * gy, vv, aa, rr, ww, q);
+        }
+        __syncthreads();
+    }
+}
+
 // Coarse level C from fine level F (both in global memory): cell moduli =
 // mean of the 2x2 fine cells, Jacobi diagonal from the four coarse cells
 // around each node.  Threads t0, t0 + st, ... take the coarse nodes.
@@ -357,6 +464,17 @@ __device__ void mg_setup_block(const MGHier<T> &H, T *sblk)
 // operand on the tile halo and five values per halo cell.
 template <int TX, int TY>
 __host__ __device__ constexpr int setup_tiled_doubles() { return 2 * (TX + 2) * (TY + 2) + 5 * (TX + 1) * (TY + 1); }
+
+// Byte offset of mg_sweep2's scratch in the dynamic shared memory: after
+// the block-run levels' arrays and the set-up sweep's scratch (which share
+// the start), rounded to 16 bytes.  The total is pcg_dyn_smem.
+template <typename T, int TX, int TY>
+__host__ __device__ constexpr size_t mg_pair_offset()
+{
+    const size_t blk = sizeof(T) * (size_t)mg_block_words_cap(mg_block_nodes<T>());
+    const size_t stp = sizeof(double) * (size_t)setup_tiled_doubles<TX, TY>();
+    return ((blk > stp ? blk : stp) + 15) / 16 * 16;
+}
 
 // The set-up sweep of one CG pass, 2D, over node tiles: right-hand side
 // b = sum_e Bbar^T sig*, Jacobi diagonal, r = b - A x (x: the FP64 solution
@@ -593,8 +711,86 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
                 }
             });
     };
+    // Two-step smoothing of a grid level k >= 1 in one fused sweep (degree 2,
+    // not the coarsest): pre-smoothing from f = R r_{k-1} (x = d_0 + d_1,
+    // r_2 and d_1 into buffer 0, which the restriction to level k+1 reads),
+    // and post-smoothing from x_pre + P e_{k+1} with the final correction
+    // into xpost.
+    T *s2 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(sblk) + mg_pair_offset<T, TX, TY>());
+    auto pre2 = [&](int k) {
+        const MGLevel<T> &V = H.lv[k];
+        const T c20 = H.c2[0], c11 = H.c1[1], c21 = H.c2[1];
+        mg_sweep2<T, TX, TY>(
+            V.nx, V.ny, V.lam, V.mu, bid, nbk, s2,
+            [&](int gx, int gy, T (&v)[2], T (&a)[2]) {
+                restrict_g(k, gx, gy, a);
+                const T di = c20 * __ldcg(V.dinv + gx + V.nx * gy);
+                v[0] = di * a[0];
+                v[1] = di * a[1];
+            },
+            [&](int g, const T (&v)[2], const T (&a)[2], const T (&q)[2], T (&r)[2], T (&w)[2]) {
+                const T di = c21 * __ldcg(V.dinv + g);
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    r[c] = a[c] - q[c];
+                    w[c] = c11 * v[c] + di * r[c];
+                }
+            },
+            [&](int n, const T (&v)[2], const T (&a)[2], const T (&r)[2], const T (&w)[2], const T (&q)[2]) {
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    V.f[c][n] = a[c];
+                    V.xpre[c][n] = v[c] + w[c];
+                    V.r[0][c][n] = r[c] - q[c];
+                    V.d[0][c][n] = w[c];
+                }
+            });
+    };
+    auto post2 = [&](int k) {
+        const MGLevel<T> &V = H.lv[k];
+        const MGLevel<T> &C = H.lv[k + 1];
+        const T c20 = H.c2[0], c11 = H.c1[1], c21 = H.c2[1];
+        mg_sweep2<T, TX, TY>(
+            V.nx, V.ny, V.lam, V.mu, bid, nbk, s2,
+            [&](int gx, int gy, T (&v)[2], T (&a)[2]) {
+                const int g = gx + V.nx * gy;
+                const int ox = gx & 1, oy = gy & 1, ix = gx >> 1, iy = gy >> 1;
+                const T wgt = (ox && oy) ? T(0.25) : ((ox || oy) ? T(0.5) : T(1));
+                const int ix1 = ox ? (ix + 1 == C.nx ? 0 : ix + 1) : ix, iy1 = oy ? (iy + 1 == C.ny ? 0 : iy + 1) : iy;
+                const int c00 = ix + C.nx * iy, c10 = ix1 + C.nx * iy, c01 = ix + C.nx * iy1, c11i = ix1 + C.nx * iy1;
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    T e = __ldcg(C.xpost[c] + c00);
+                    if (ox) e += __ldcg(C.xpost[c] + c10);
+                    if (oy) e += __ldcg(C.xpost[c] + c01);
+                    if (ox && oy) e += __ldcg(C.xpost[c] + c11i);
+                    v[c] = __ldcg(V.xpre[c] + g) + wgt * e;
+                    a[c] = __ldcg(V.f[c] + g);
+                }
+            },
+            [&](int g, const T (&v)[2], const T (&a)[2], const T (&q)[2], T (&r)[2], T (&w)[2]) {
+                const T di = c20 * __ldcg(V.dinv + g);
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    r[c] = a[c] - q[c];
+                    w[c] = di * r[c];
+                }
+            },
+            [&](int n, const T (&v)[2], const T (&)[2], const T (&r)[2], const T (&w)[2], const T (&q)[2]) {
+                const T di = c21 * __ldcg(V.dinv + n);
+#pragma unroll
+                for (int c = 0; c < 2; c++) V.xpost[c][n] = v[c] + w[c] + (c11 * w[c] + di * (r[c] - q[c]));
+            });
+    };
+    // the fused form serves grid levels with two-step smoothing
+    auto fused = [&](int k) { return k >= 1 && k < L - 1 && H.deg[k] == 2; };
+
     // post-smoothing of grid level k
     auto post = [&](int k, int cur) {
+        if (fused(k)) {
+            post2(k);
+            return grid_sync(bc, bg, err, nbk);
+        }
         const int dk = H.deg[k];
         int par = dk & 1;
         post_first(k, par, cur, dk == 1);
@@ -609,6 +805,10 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
     };
     // pre-smoothing (or the coarsest solve, csteps >= 3) of grid level k >= 1
     auto pre = [&](int k) {
+        if (fused(k)) {
+            pre2(k);
+            return grid_sync(bc, bg, err, nbk);
+        }
         pre_first(k);
         if (!grid_sync(bc, bg, err, nbk)) return false;
         int par = 1;
