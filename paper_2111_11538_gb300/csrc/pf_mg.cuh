@@ -284,11 +284,13 @@ __host__ __device__ constexpr int sweep2_words()
 // neighbouring tiles): val(gx, gy, v0, a0) gives the first operand v0 and an
 // auxiliary a0 on the width-2 halo; mid(g, v0, a0, q0, r1, v1) forms, on the
 // width-1 halo, from v0, a0 and q0 = A v0, an intermediate r1 and the second
-// operand v1; epi(n, v0, a0, r1, v1, q1) gets q1 = A v1 at every own node.
+// operand v1; epi(n, v0, a0, r1, v1, q1, se) gets q1 = A v1 at every own
+// node.  E2: the second product adds the mean strain ue to every cell's
+// stress and se is the own cell's stress of v1 without it (else zero).
 // Scratch: sweep2_words<TX, TY>() words of shared memory at scr.
-template <typename T, int TX, int TY, class Val, class Mid, class Epi>
-__device__ __forceinline__ void mg_sweep2(int nx, int ny, const T *lam, const T *mu, int bid, int nbk, T *scr, Val &&val,
-                                          Mid &&mid, Epi &&epi)
+template <typename T, int TX, int TY, bool E2, class Val, class Mid, class Epi>
+__device__ __forceinline__ void mg_sweep2(int nx, int ny, const T *lam, const T *mu, int bid, int nbk, T *scr,
+                                          const T *ue, Val &&val, Mid &&mid, Epi &&epi)
 {
     constexpr int AX = TX + 4, AY = TY + 4, AN = AX * AY;     // width-2 halo nodes
     constexpr int BX = TX + 2, BY = TY + 2, BN = BX * BY;     // width-1 halo nodes
@@ -299,7 +301,7 @@ __device__ __forceinline__ void mg_sweep2(int nx, int ny, const T *lam, const T 
     const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntiles = ntx * nty;
     const bool small = nx < AX || ny < AY;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    auto cells = [&](const T *u, int ux, int un, int ncx, int ncell, int ox, int oy) {
+    auto cells = [&](const T *u, int ux, int un, int ncx, int ncell, int ox, int oy, bool withE) {
         // cells with lower-left node (cx, cy) of the operand grid u (row
         // length ux, un nodes per component), global origin (ox, oy)
         for (int h = threadIdx.x; h < ncell; h += NT) {
@@ -313,7 +315,14 @@ __device__ __forceinline__ void mg_sweep2(int nx, int ny, const T *lam, const T 
                 uc[b][1] = u[un + hn];
             }
             T s3[3], fh[2];
-            cell_force2<T>(__ldcg(lam + g), __ldcg(mu + g), uc, s3, fh);
+            const T l = __ldcg(lam + g), m = __ldcg(mu + g);
+            cell_force2<T>(l, m, uc, s3, fh);
+            if (E2 && withE) {
+                T sx[3];
+                voigt_stress<T, 2>(l, m, ue, sx);
+#pragma unroll
+                for (int v = 0; v < 3; v++) s3[v] += sx[v];
+            }
             cf[h] = s3[0];
             cf[CN + h] = s3[1];
             cf[2 * CN + h] = s3[2];
@@ -347,7 +356,7 @@ __device__ __forceinline__ void mg_sweep2(int nx, int ny, const T *lam, const T 
             a0[AN + h] = a[1];
         }
         __syncthreads();
-        cells(v0, AX, AN, CX, CN, x0 - 2, y0 - 2);
+        cells(v0, AX, AN, CX, CN, x0 - 2, y0 - 2, false);
         __syncthreads();
         for (int h = threadIdx.x; h < BN; h += NT) {
             const int mx = h % BX, my = h / BX, ah = (mx + 1) + AX * (my + 1);
@@ -362,7 +371,7 @@ __device__ __forceinline__ void mg_sweep2(int nx, int ny, const T *lam, const T 
             v1[BN + h] = ww[1];
         }
         __syncthreads();
-        cells(v1, BX, BN, DX, DN, x0 - 1, y0 - 1);
+        cells(v1, BX, BN, DX, DN, x0 - 1, y0 - 1, true);
         __syncthreads();
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx < nx && gy < ny) {
@@ -371,7 +380,17 @@ __device__ __forceinline__ void mg_sweep2(int nx, int ny, const T *lam, const T 
             force(tx + 1, ty + 1, DX, q);
             const T vv[2] = {v0[ah], v0[AN + ah]}, aa[2] = {a0[ah], a0[AN + ah]};
             const T rr[2] = {r1[bh], r1[BN + bh]}, ww[2] = {v1[bh], v1[BN + bh]};
-            epi(gx + nx * gy, vv, aa, rr, ww, q);
+            const int n = gx + nx * gy;
+            T se[3] = {T(0), T(0), T(0)};
+            if constexpr (E2) {
+                const int c0 = (tx + 1) + DX * (ty + 1);
+                T sx[3];
+                voigt_stress<T, 2>(__ldcg(lam + n), __ldcg(mu + n), ue, sx);
+                se[0] = cf[c0] - sx[0];
+                se[1] = cf[CN + c0] - sx[1];
+                se[2] = cf[2 * CN + c0] - sx[2];
+            }
+            epi(n, vv, aa, rr, ww, q, se);
         }
         __syncthreads();
     }
@@ -720,8 +739,8 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
     auto pre2 = [&](int k) {
         const MGLevel<T> &V = H.lv[k];
         const T c20 = H.c2[0], c11 = H.c1[1], c21 = H.c2[1];
-        mg_sweep2<T, TX, TY>(
-            V.nx, V.ny, V.lam, V.mu, bid, nbk, s2,
+        mg_sweep2<T, TX, TY, false>(
+            V.nx, V.ny, V.lam, V.mu, bid, nbk, s2, nullptr,
             [&](int gx, int gy, T (&v)[2], T (&a)[2]) {
                 restrict_g(k, gx, gy, a);
                 const T di = c20 * __ldcg(V.dinv + gx + V.nx * gy);
@@ -736,7 +755,8 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
                     w[c] = c11 * v[c] + di * r[c];
                 }
             },
-            [&](int n, const T (&v)[2], const T (&a)[2], const T (&r)[2], const T (&w)[2], const T (&q)[2]) {
+            [&](int n, const T (&v)[2], const T (&a)[2], const T (&r)[2], const T (&w)[2], const T (&q)[2],
+                const T (&)[3]) {
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
                     V.f[c][n] = a[c];
@@ -750,8 +770,8 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
         const MGLevel<T> &V = H.lv[k];
         const MGLevel<T> &C = H.lv[k + 1];
         const T c20 = H.c2[0], c11 = H.c1[1], c21 = H.c2[1];
-        mg_sweep2<T, TX, TY>(
-            V.nx, V.ny, V.lam, V.mu, bid, nbk, s2,
+        mg_sweep2<T, TX, TY, false>(
+            V.nx, V.ny, V.lam, V.mu, bid, nbk, s2, nullptr,
             [&](int gx, int gy, T (&v)[2], T (&a)[2]) {
                 const int g = gx + V.nx * gy;
                 const int ox = gx & 1, oy = gy & 1, ix = gx >> 1, iy = gy >> 1;
@@ -776,7 +796,8 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
                     w[c] = di * r[c];
                 }
             },
-            [&](int n, const T (&v)[2], const T (&)[2], const T (&r)[2], const T (&w)[2], const T (&q)[2]) {
+            [&](int n, const T (&v)[2], const T (&)[2], const T (&r)[2], const T (&w)[2], const T (&q)[2],
+                const T (&)[3]) {
                 const T di = c21 * __ldcg(V.dinv + n);
 #pragma unroll
                 for (int c = 0; c < 2; c++) V.xpost[c][n] = v[c] + w[c] + (c11 * w[c] + di * (r[c] - q[c]));
@@ -1030,28 +1051,76 @@ __device__ int mg_pass(const PCGArgs<T, 2> &A, const MGHier<T> &H, PCGState &S, 
             }
             if (!grid_sync(bc, bg, err, nbk)) return -1;
         }
-        for (int k = (Lgw < L - 1 ? Lgw : L - 1) - 1; k >= 0; k--)
+        // the finest level's one-step post-smoothing fuses with the next sweep
+        const bool fuse0 = L > 1 && H.deg[0] == 1;
+        for (int k = (Lgw < L - 1 ? Lgw : L - 1) - 1; k >= (fuse0 ? 1 : 0); k--)
             if (!post(k, cur)) return -1;
 
         // ---- u = V-cycle result, w = A u (+ mean strain), gamma, delta, mean-strain row
         Acc<T> acc[2 + NV];
-        mg_sweep<T, TX, TY, true>(
-            L0.nx, L0.ny, L0.lam, L0.mu, bid, nbk, su, sl, sm, scell, s_ue,
-            [&](int gx, int gy, T (&v)[2]) {
-                const int g = gx + L0.nx * gy;
-                v[0] = __ldcg(L0.xpost[0] + g);
-                v[1] = __ldcg(L0.xpost[1] + g);
-            },
-            [&](int n, const T (&v)[2], const T (&q)[2], const T (&se)[3]) {
+        if (fuse0) {
+            // x = x_pre + P e_1, r = f - A x (f: the CG residual), u = x + c2[0] D^-1 r
+            // on the width-1 ring, then w = A u on the tile
+            const MGLevel<T> &C = H.lv[1];
+            const T c20 = H.c2[0];
+            mg_sweep2<T, TX, TY, true>(
+                L0.nx, L0.ny, L0.lam, L0.mu, bid, nbk,
+                reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(sblk) + mg_pair_offset<T, TX, TY>()), s_ue,
+                [&](int gx, int gy, T (&v)[2], T (&a)[2]) {
+                    const int g = gx + L0.nx * gy;
+                    const int ox = gx & 1, oy = gy & 1, ix = gx >> 1, iy = gy >> 1;
+                    const T wgt = (ox && oy) ? T(0.25) : ((ox || oy) ? T(0.5) : T(1));
+                    const int ix1 = ox ? (ix + 1 == C.nx ? 0 : ix + 1) : ix, iy1 = oy ? (iy + 1 == C.ny ? 0 : iy + 1) : iy;
+                    const int c00 = ix + C.nx * iy, c10 = ix1 + C.nx * iy, c01 = ix + C.nx * iy1, c11 = ix1 + C.nx * iy1;
 #pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    A.w[cur][c][n] = q[c];
-                    acc[0].fma_plain(__ldcg(A.r[cur][c] + n), v[c]);
-                    acc[1].fma_plain(q[c], v[c]);
-                }
+                    for (int c = 0; c < 2; c++) {
+                        T e = __ldcg(C.xpost[c] + c00);
+                        if (ox) e += __ldcg(C.xpost[c] + c10);
+                        if (oy) e += __ldcg(C.xpost[c] + c01);
+                        if (ox && oy) e += __ldcg(C.xpost[c] + c11);
+                        v[c] = __ldcg(L0.xpre[c] + g) + wgt * e;
+                        a[c] = __ldcg(A.r[cur][c] + g);
+                    }
+                },
+                [&](int g, const T (&v)[2], const T (&a)[2], const T (&q)[2], T (&r)[2], T (&w)[2]) {
+                    const T di = c20 * __ldcg(L0.dinv + g);
 #pragma unroll
-                for (int vv = 0; vv < NV; vv++) acc[2 + vv].add_plain(se[vv]);
-            });
+                    for (int c = 0; c < 2; c++) {
+                        r[c] = a[c] - q[c];
+                        w[c] = v[c] + di * r[c];
+                    }
+                },
+                [&](int n, const T (&)[2], const T (&a)[2], const T (&)[2], const T (&u)[2], const T (&q)[2],
+                    const T (&se)[3]) {
+#pragma unroll
+                    for (int c = 0; c < 2; c++) {
+                        L0.xpost[c][n] = u[c];
+                        A.w[cur][c][n] = q[c];
+                        acc[0].fma_plain(a[c], u[c]);
+                        acc[1].fma_plain(q[c], u[c]);
+                    }
+#pragma unroll
+                    for (int vv = 0; vv < NV; vv++) acc[2 + vv].add_plain(se[vv]);
+                });
+        } else {
+            mg_sweep<T, TX, TY, true>(
+                L0.nx, L0.ny, L0.lam, L0.mu, bid, nbk, su, sl, sm, scell, s_ue,
+                [&](int gx, int gy, T (&v)[2]) {
+                    const int g = gx + L0.nx * gy;
+                    v[0] = __ldcg(L0.xpost[0] + g);
+                    v[1] = __ldcg(L0.xpost[1] + g);
+                },
+                [&](int n, const T (&v)[2], const T (&q)[2], const T (&se)[3]) {
+#pragma unroll
+                    for (int c = 0; c < 2; c++) {
+                        A.w[cur][c][n] = q[c];
+                        acc[0].fma_plain(__ldcg(A.r[cur][c] + n), v[c]);
+                        acc[1].fma_plain(q[c], v[c]);
+                    }
+#pragma unroll
+                    for (int vv = 0; vv < NV; vv++) acc[2 + vv].add_plain(se[vv]);
+                });
+        }
         double tt[2 + NV];
         if (!reduce_barrier<Acc<T>, 2 + NV>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tt, bid, nbk)) return -1;
         if (lead) {
