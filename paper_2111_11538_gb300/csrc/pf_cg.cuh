@@ -600,12 +600,12 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
                 S.prev_res = sqrt(rho);
                 // target of this pass: the requested tolerance, or in refinement
                 // mode what an FP32 iteration can deliver on this correction
-                // (eta); when the final tolerance is within a factor 10 of that,
+                // (eta); when the final tolerance is within a factor 100 of that,
                 // the pass aims for it directly, which saves a pass that would
                 // otherwise start just above the tolerance
                 if (refine) {
                     const double fin = 0.5 * A.rtol * bnorm, pass = A.eta * sqrt(rho);
-                    target = fin >= 0.1 * pass ? fin : pass;
+                    target = fin >= 0.01 * pass ? fin : pass;
                 } else {
                     target = A.rtol * bnorm;
                 }
