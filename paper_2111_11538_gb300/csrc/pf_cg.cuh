@@ -61,6 +61,8 @@ struct PCGArgs {
     int warm;
     int block0, nblocks;           // this job's blocks in the launch
     const MGHier<T> *mg;           // multigrid hierarchy (2D, k_pcg<..., MG = true> only)
+    double *b64[3];                // MG refinement mode: the FP64 right-hand side, kept from the
+                                   // first pass for the later ones
 };
 
 // Grid barrier that also reduces K per-block values in a fixed order: the
@@ -381,6 +383,7 @@ struct PCGState {
     double Sl, Sm, bnorm, rho_final, target, prev_res;
     double gamma, delta, gamma_prev, alpha_prev, alpha, beta;
     double inv_gamma, inv_gamma_prev, inv_alpha, inv_alpha_prev;   // FP64 divisions are slow here
+    double tot0[10];   // first pass's set-up sums [0, 10) (fixed during a solve; MG refinement reuses them)
     int it, it_total, conv;
 };
 
@@ -527,8 +530,10 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
             Acc<double> acc[16];
             if constexpr (MG) {
                 // 2D multigrid variant: the tiled FP64 set-up (cells once per
-                // tile) in the dynamic shared memory
-                setup_tiled<T, TX, TY>(A, use_x, refine, xe64, reinterpret_cast<double *>(pcg_dyn), acc, bid, nbk);
+                // tile) in the dynamic shared memory; later refinement passes
+                // only form the residual
+                setup_tiled<T, TX, TY>(A, use_x, refine, refine && outer > 0, xe64,
+                                       reinterpret_cast<double *>(pcg_dyn), acc, bid, nbk);
             } else
             for (long long n = t0; n < N; n += st) {
                 double bv[D], rv[D];
@@ -567,6 +572,15 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
             double tot[16];
             if (!reduce_barrier<Acc<double>, 16>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tot, bid, nbk)) return;
             if (lead) {
+                // a residual-only pass reuses the first pass's sums of b, the
+                // moduli and the eigenstress
+                if (MG && refine) {
+                    if (outer == 0)
+                        for (int k = 0; k < 10; k++) S.tot0[k] = tot[k];
+                    else
+                        for (int k = 0; k < 10; k++)
+                            if (k != 1) tot[k] = S.tot0[k];
+                }
                 // scalars of the mean-strain dofs
                 Sl = tot[2];
                 Sm = tot[3];

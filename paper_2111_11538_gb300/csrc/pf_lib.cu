@@ -206,6 +206,7 @@ struct pf_handle {
     int cg_per_sm = 0;
     int pcg_shape = 0;                  // node tile of the PCG sweep (pf_cg.cuh Tile<D, S>)
     bool mg = false;                    // multigrid-preconditioned CG (pf_mg.cuh)
+    double *b64[3] = {};                // MG mixed method: FP64 right-hand side kept across passes
     void *d_mg = nullptr;               // device MGHier<T> of this instance
     bool plan_ready = false;
     int plan_par = 0;                   // which table describes the current state
@@ -460,6 +461,9 @@ int build_mg(pf_handle *h)
         H.c2[j] = (T)(2.0 * rn / delta);
         rho = rn;
     }
+    // mixed method: the first refinement pass keeps b (FP64) for the later ones
+    if (h->refine)
+        for (int c = 0; c < 2; c++) PF_TRY(h->alloc(&h->b64[c], sizeof(double) * (size_t)h->P.N));
     if (!h->d_mg) PF_TRY(h->alloc(&h->d_mg, sizeof(H)));
     return h->cuda(cudaMemcpy(h->d_mg, &H, sizeof(H), cudaMemcpyHostToDevice), "multigrid descriptor");
 }
@@ -509,6 +513,7 @@ PCGArgs<T, D> pcg_args(pf_handle *m)
     A.rtol = m->cfg.cg_rtol; A.maxit = m->cfg.cg_maxit;
     A.warm = m->cfg.warm_start != PF_WS_ZERO ? 1 : 0;
     A.mg = (const MGHier<T> *)m->d_mg;
+    for (int d = 0; d < 3; d++) A.b64[d] = m->b64[d];
     return A;
 }
 

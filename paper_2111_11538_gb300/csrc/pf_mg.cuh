@@ -503,10 +503,13 @@ __host__ __device__ constexpr size_t mg_pair_offset()
 // shared memory), and the per-node sums of the mean-strain rows: acc[0]
 // ||b||^2, [1] ||r||^2, [2] sum lam, [3] sum mu, [4..6] sum sig*, [10..12]
 // sum of the own cells' stress of x without the mean strain.  Also clears
-// p, s and (when x is not used or in refinement mode) the iterate.
+// p, s and (when x is not used or in refinement mode) the iterate.  In
+// refinement mode the first pass keeps b in A.b64; a residual-only pass
+// (resid) reads it there and skips everything that does not change during
+// a solve (b, the diagonal, sums [0] and [2, 10)).
 template <typename T, int TX, int TY>
-__device__ void setup_tiled(const PCGArgs<T, 2> &A, bool use_x, bool refine, const double *xe, double *dscr,
-                            Acc<double> (&acc)[16], int bid, int nbk)
+__device__ void setup_tiled(const PCGArgs<T, 2> &A, bool use_x, bool refine, bool resid, const double *xe,
+                            double *dscr, Acc<double> (&acc)[16], int bid, int nbk)
 {
     const Params &P = A.P;
     constexpr int HX = TX + 2, HY = TY + 2, CX = TX + 1, CY = TY + 1, HN = HX * HY, HC = CX * CY, NT = TX * TY;
@@ -549,9 +552,20 @@ __device__ void setup_tiled(const PCGArgs<T, 2> &A, bool use_x, bool refine, con
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx < nx && gy < ny) {
             const int n = gx + nx * gy, lx = tx + 1, ly = ty + 1;
-            double b[2], ax[2] = {0.0, 0.0}, dgn, so[3], deo[3] = {0.0, 0.0, 0.0}, lo, mo, unused[2], unused3[3];
-            node_setup<T, double, double, 2>(P, n, A.lam, A.mu, A.sig, A.x64, xe, false, b, unused, dgn, so, unused3, lo,
-                                             mo);
+            double b[2], ax[2] = {0.0, 0.0}, dgn = 1.0, so[3], deo[3] = {0.0, 0.0, 0.0}, lo, mo, unused[2], unused3[3];
+            if (resid) {
+                b[0] = __ldcg(A.b64[0] + n);
+                b[1] = __ldcg(A.b64[1] + n);
+                lo = (double)A.lam[n];
+                mo = (double)A.mu[n];
+            } else {
+                node_setup<T, double, double, 2>(P, n, A.lam, A.mu, A.sig, A.x64, xe, false, b, unused, dgn, so, unused3,
+                                                 lo, mo);
+                if (refine) {
+                    A.b64[0][n] = b[0];
+                    A.b64[1][n] = b[1];
+                }
+            }
             if (use_x) {
 #pragma unroll
                 for (int a = 0; a < 4; a++) {
@@ -571,14 +585,15 @@ __device__ void setup_tiled(const PCGArgs<T, 2> &A, bool use_x, bool refine, con
                 deo[1] = hc[HC + c0] - sx[1];
                 deo[2] = hc[2 * HC + c0] - sx[2];
             }
-            A.dinv[n] = (T)(1.0 / dgn);
-            acc[2].add(lo);
-            acc[3].add(mo);
+            if (!resid) {
+                A.dinv[n] = (T)(1.0 / dgn);
+                acc[2].add(lo);
+                acc[3].add(mo);
 #pragma unroll
-            for (int v = 0; v < 3; v++) {
-                acc[4 + v].add(so[v]);
-                acc[10 + v].add(deo[v]);
+                for (int v = 0; v < 3; v++) acc[4 + v].add(so[v]);
             }
+#pragma unroll
+            for (int v = 0; v < 3; v++) acc[10 + v].add(deo[v]);
 #pragma unroll
             for (int d = 0; d < 2; d++) {
                 const double rv = b[d] - ax[d];
@@ -587,7 +602,7 @@ __device__ void setup_tiled(const PCGArgs<T, 2> &A, bool use_x, bool refine, con
                 A.p[d][n] = T(0);
                 A.s[0][d][n] = T(0);
                 A.r[0][d][n] = (T)rv;
-                acc[0].addprod(b[d], b[d]);
+                if (!resid) acc[0].addprod(b[d], b[d]);
                 acc[1].addprod(rv, rv);
             }
         }
