@@ -88,13 +88,13 @@ typedef struct {
                            grid size (measured per size class), 1 = 32x8 (2D) / 16x4x4
                            (3D), 2 = 32x16 / 32x4x2.  Results agree to rounding.        */
     int precond;        /* CG preconditioner: PF_PC_AUTO (the library's choice: PF_PC_MG
-                           for 2D grids whose sizes are divisible by 4 and >= 32, else
+                           for grids whose sizes are all divisible by 4 and >= 32, else
                            Jacobi; one choice for a whole batch), PF_PC_JACOBI
-                           (diagonal), or PF_PC_MG (2D only: one geometric
-                           multigrid V-cycle per iteration, Chebyshev-smoothed, on grids
-                           halved while both sizes stay even and the coarse grid keeps
-                           >= 8 nodes per axis).  Both solve to the same cg_rtol;
-                           iteration counts differ.                                    */
+                           (diagonal), or PF_PC_MG (one geometric multigrid V-cycle per
+                           iteration, Chebyshev-smoothed, on grids halved while all
+                           sizes stay even and the coarse grid keeps >= 8 nodes per
+                           axis).  Both solve to the same cg_rtol; iteration counts
+                           differ.                                                     */
 } pf_config;
 
 /* Field arrays, FP64, cell-major.  Any pointer may be NULL (skipped).

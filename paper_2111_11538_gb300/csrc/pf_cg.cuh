@@ -428,6 +428,7 @@ enum { CTL_RUN = 0, CTL_DONE = 1, CTL_ZERO = 2, CTL_STOP = 3 };
 }  // namespace pfdev
 
 #include "pf_mg.cuh"
+#include "pf_mg3.cuh"
 
 namespace pfdev {
 
@@ -443,7 +444,6 @@ constexpr int tile_threads() { return Tile<D, S>::X * Tile<D, S>::Y * Tile<D, S>
 template <typename T, int D, int SH, bool MG>
 __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, SH>()) k_pcg(const PCGArgs<T, D> *jobs, int njobs)
 {
-    static_assert(!MG || D == 2, "the multigrid preconditioner is 2D");
     // this block's job, copied to shared memory
     __shared__ PCGArgs<T, D> sA;
     {
@@ -508,8 +508,10 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
     // global memory; the coarse levels' moduli are rebuilt for this solve
     // the block-run levels' arrays: dynamic shared memory (pcg_dyn_smem)
     T *sblk = reinterpret_cast<T *>(pcg_dyn);
-    if constexpr (MG) {
+    if constexpr (MG && D == 2) {
         if (!mg_setup<T>(*A.mg, A.bar_count, A.bar_gen, err, bid, nbk)) return;
+    } else if constexpr (MG) {
+        if (!mg_setup3<T>(*A.mg, A.bar_count, A.bar_gen, err, bid, nbk)) return;
     }
 
     for (int outer = 0; outer < (refine ? MAX_OUTER : 1); outer++) {
@@ -528,7 +530,7 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
                 xeT[v] = s_xe[v];
             }
             Acc<double> acc[16];
-            if constexpr (MG) {
+            if constexpr (MG && D == 2) {
                 // 2D multigrid variant: the tiled FP64 set-up (cells once per
                 // tile) in the dynamic shared memory; later refinement passes
                 // only form the residual
@@ -574,7 +576,7 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
             if (lead) {
                 // a residual-only pass reuses the first pass's sums of b, the
                 // moduli and the eigenstress
-                if (MG && refine) {
+                if (MG && D == 2 && refine) {
                     if (outer == 0)
                         for (int k = 0; k < 10; k++) S.tot0[k] = tot[k];
                     else
@@ -649,7 +651,12 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
 
         // ---------------- sweeps: the first builds w_0, then iterations -----
         if constexpr (MG) {
-            const int rc = mg_pass<T, TX, TY>(A, *A.mg, S, su, sl, sm, scell, sblk, s_ta, s_tb, s_ue, s_ctl, bid, nbk, err);
+            int rc;
+            if constexpr (D == 2)
+                rc = mg_pass<T, TX, TY>(A, *A.mg, S, su, sl, sm, scell, sblk, s_ta, s_tb, s_ue, s_ctl, bid, nbk, err);
+            else
+                rc = mg_pass3<T, TX, TY, TZ>(A, *A.mg, S, su, sl, sm, reinterpret_cast<T *>(pcg_dyn), s_ta, s_tb, s_ue,
+                                             s_ctl, bid, nbk, err);
             if (rc < 0) return;
             if (lead) conv = rc == CTL_DONE;
         } else {
@@ -991,6 +998,12 @@ size_t pcg_dyn_smem(int shape, bool mg)
         return mg_pair_offset<T, Tile<2, 0>::X, Tile<2, 0>::Y>() +
                sizeof(T) * (size_t)sweep2_words<Tile<2, 0>::X, Tile<2, 0>::Y>();
     }
+    if (D == 3 && mg) {
+        // the 3D V-cycle's per-cell stress and hourglass forces (mg_sweep3)
+        const int hc = shape == 1 ? (Tile<3, 1>::X + 1) * (Tile<3, 1>::Y + 1) * (Tile<3, 1>::Z + 1)
+                                  : (Tile<3, 0>::X + 1) * (Tile<3, 0>::Y + 1) * (Tile<3, 0>::Z + 1);
+        return sizeof(T) * 20 * (size_t)hc;
+    }
     if (D != 3 || sizeof(T) != 4 || shape != 0) return 0;
     constexpr int HC = (Tile<3, 0>::X + 1) * (Tile<3, 0>::Y + 1) * (Tile<3, 0>::Z + 1);
     return sizeof(float) * 20 * HC;
@@ -1001,9 +1014,7 @@ size_t pcg_dyn_smem(int shape, bool mg)
 template <typename T, int D>
 const void *pcg_kernel(int shape, bool mg)
 {
-    if constexpr (D == 2) {
-        if (mg) return shape == 1 ? (const void *)k_pcg<T, D, 1, true> : (const void *)k_pcg<T, D, 0, true>;
-    }
+    if (mg) return shape == 1 ? (const void *)k_pcg<T, D, 1, true> : (const void *)k_pcg<T, D, 0, true>;
     return shape == 1 ? (const void *)k_pcg<T, D, 1, false> : (const void *)k_pcg<T, D, 0, false>;
 }
 

@@ -29,14 +29,14 @@ constexpr int MG_MAX_STEPS = 16;
 
 template <typename T>
 struct MGLevel {
-    int nx, ny;                    // nodes (= cells) per axis, periodic
+    int nx, ny, nz;                // nodes (= cells) per axis, periodic (nz = 1 in 2D)
     T *lam, *mu;                   // cell moduli (level 0: the solve's own, read only)
     T *dinv;                       // inverse Jacobi diagonal (level 0: the solve's own)
-    T *f[2];                       // right-hand side (levels >= 1; level 0 uses the CG residual)
-    T *xpre[2];                    // iterate of the pre-smoothing (coarsest: of its solve)
-    T *xpost[2];                   // iterate of the post-smoothing; the level's final correction
+    T *f[3];                       // right-hand side (levels >= 1; level 0 uses the CG residual)
+    T *xpre[3];                    // iterate of the pre-smoothing (coarsest: of its solve)
+    T *xpost[3];                   // iterate of the post-smoothing; the level's final correction
                                    // when it is done (finest level: u = M r)
-    T *r[2][2], *d[2][2];          // [buffer][component]: residual, Chebyshev direction
+    T *r[2][3], *d[2][3];          // [buffer][component]: residual, Chebyshev direction
 };
 
 template <typename T>

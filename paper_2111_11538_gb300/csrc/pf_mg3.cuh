@@ -1,0 +1,431 @@
+// Geometric multigrid preconditioner of the 3D solve: the V-cycle of
+// pf_mg.cuh on periodic Q1 hex grids.  Each coarse level halves all three
+// sizes; a coarse cell's moduli are the mean of its 2x2x2 fine cells times 2
+// (the unit-cell element tables are used on every level, and a hex element's
+// stiffness grows linearly with its edge, so that the rediscretised coarse
+// operator matches the fine one under trilinear prolongation); restriction
+// is the transpose of trilinear prolongation (27 fine nodes per coarse
+// node).  The Chebyshev bound is the largest eigenvalue of diag(K_e)^-1 K_e
+// of the 3D element.  All levels run on the whole grid, one tiled sweep of
+// the operator (the exact cell decomposition of cell_force3 / node_force3)
+// and one grid barrier per Chebyshev step; the CG update and the last step
+// of each smoothing are folded into neighbouring sweeps as in 2D.
+#pragma once
+
+namespace pfdev {
+
+// One 3D sweep over node tiles TX x TY x TZ: val(gx, gy, gz, v) gives the
+// operand at any node of the tile and its halo, epi(n, v, q, se) receives at
+// each own node q = A v and (WITH_E) the own cell's average stress without
+// the mean strain ue (which is added to every cell's stress for q).  su:
+// 3 * HN halo nodes, sl / sm: HC halo cells (static shared memory of the
+// PCG kernel); scell: 20 * HC values (the dynamic shared memory).
+template <typename T, int TX, int TY, int TZ, bool WITH_E, class Val, class Epi>
+__device__ __forceinline__ void mg_sweep3(int nx, int ny, int nz, const T *lam, const T *mu, int bid, int nbk, T *su,
+                                          T *sl, T *sm, T *scell, const T *ue, Val &&val, Epi &&epi)
+{
+    constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HN = HX * HY * HZ;
+    constexpr int CX = TX + 1, CY = TY + 1, CZ = TZ + 1, HC = CX * CY * CZ, NT = TX * TY * TZ;
+    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntz = (nz + TZ - 1) / TZ;
+    const int ntiles = ntx * nty * ntz;
+    const bool small = nx < HX || ny < HY || nz < HZ;
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    for (int tile = bid; tile < ntiles; tile += nbk) {
+        const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY, z0 = (tile / (ntx * nty)) * TZ;
+        for (int h = threadIdx.x; h < HN; h += NT) {
+            const int lx = h % HX, ly = (h / HX) % HY, lz = h / (HX * HY);
+            T v[3];
+            val(mg_wrap(x0 - 1 + lx, nx, small), mg_wrap(y0 - 1 + ly, ny, small), mg_wrap(z0 - 1 + lz, nz, small), v);
+            su[h] = v[0];
+            su[HN + h] = v[1];
+            su[2 * HN + h] = v[2];
+        }
+        for (int h = threadIdx.x; h < HC; h += NT) {
+            const int lx = h % CX, ly = (h / CX) % CY, lz = h / (CX * CY);
+            const int g = mg_wrap(x0 - 1 + lx, nx, small) +
+                          nx * (mg_wrap(y0 - 1 + ly, ny, small) + ny * mg_wrap(z0 - 1 + lz, nz, small));
+            sl[h] = __ldcg(lam + g);
+            sm[h] = __ldcg(mu + g);
+        }
+        __syncthreads();
+        for (int h = threadIdx.x; h < HC; h += NT) {
+            const int cx = h % CX, cy = (h / CX) % CY, cz = h / (CX * CY);
+            T uc[8][3];
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const int hn = (cx + (b & 1)) + HX * ((cy + ((b >> 1) & 1)) + HY * (cz + (b >> 2)));
+                uc[b][0] = su[hn];
+                uc[b][1] = su[HN + hn];
+                uc[b][2] = su[2 * HN + hn];
+            }
+            const T l = sl[h], m = sm[h];
+            T c[20];
+            cell_force3<T>(l, m, uc, c);
+            if constexpr (WITH_E) {
+                T sx[6];
+                voigt_stress<T, 3>(l, m, ue, sx);
+#pragma unroll
+                for (int v = 0; v < 6; v++) c[v] += sx[v];
+            }
+#pragma unroll
+            for (int v = 0; v < 18; v++) scell[v * HC + h] = c[v];
+        }
+        __syncthreads();
+        const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+        if (gx < nx && gy < ny && gz < nz) {
+            const int lx = tx + 1, ly = ty + 1, lz = tz + 1, hn = lx + HX * (ly + HY * lz);
+            const T un[3] = {su[hn], su[HN + hn], su[2 * HN + hn]};
+            T q[3] = {T(0), T(0), T(0)}, se[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+                const int cl = (lx - ax) + CX * ((ly - ay) + CY * (lz - az));
+                T c[18];
+#pragma unroll
+                for (int v = 0; v < 18; v++) c[v] = scell[v * HC + cl];
+                T f[3];
+                node_force3<T>(ax, ay, az, c, c + 6, f);
+                q[0] += f[0];
+                q[1] += f[1];
+                q[2] += f[2];
+            }
+            if constexpr (WITH_E) {
+                const int c0 = lx + CX * (ly + CY * lz);
+                T sx[6];
+                voigt_stress<T, 3>(sl[c0], sm[c0], ue, sx);
+#pragma unroll
+                for (int v = 0; v < 6; v++) se[v] = scell[v * HC + c0] - sx[v];
+            }
+            epi(gx + nx * (gy + ny * gz), un, q, se);
+        }
+        __syncthreads();
+    }
+}
+
+// Coarse 3D level C from F (global memory): cell moduli = 2 x the mean of
+// the 2x2x2 fine cells, Jacobi diagonal from the eight coarse cells around
+// each node.  Threads t0, t0 + st, ... take the coarse nodes.
+template <typename T>
+__device__ void mg_coarsen3(const MGLevel<T> &F, const MGLevel<T> &C, long long t0, long long st)
+{
+    const long long n = (long long)C.nx * C.ny * C.nz;
+    auto avg = [&](const T *a, int cx, int cy, int cz) {
+        const long long i = 2 * cx + (long long)F.nx * (2 * cy + (long long)F.ny * (2 * cz));
+        const long long sy = F.nx, sz = (long long)F.nx * F.ny;
+        const T lo = (__ldcg(a + i) + __ldcg(a + i + 1)) + (__ldcg(a + i + sy) + __ldcg(a + i + sy + 1));
+        const T hi = (__ldcg(a + i + sz) + __ldcg(a + i + sz + 1)) + (__ldcg(a + i + sz + sy) + __ldcg(a + i + sz + sy + 1));
+        return T(0.25) * (lo + hi);      // 2 x the mean of eight
+    };
+    for (long long i = t0; i < n; i += st) {
+        const int cx = (int)(i % C.nx), cy = (int)((i / C.nx) % C.ny), cz = (int)(i / ((long long)C.nx * C.ny));
+        C.lam[i] = avg(F.lam, cx, cy, cz);
+        C.mu[i] = avg(F.mu, cx, cy, cz);
+        T dg = T(0);
+#pragma unroll
+        for (int a = 0; a < 8; a++) {
+            const int ex = wrap(cx - (a & 1), C.nx), ey = wrap(cy - ((a >> 1) & 1), C.ny), ez = wrap(cz - (a >> 2), C.nz);
+            dg += avg(F.lam, ex, ey, ez) * KdL<T, 3>() + avg(F.mu, ex, ey, ez) * KdM<T, 3>();
+        }
+        C.dinv[i] = T(1) / dg;
+    }
+}
+
+// Set-up of the 3D hierarchy at the start of a solve (grid levels, a barrier
+// after each).  Returns false if a barrier timed out.
+template <typename T>
+__device__ bool mg_setup3(const MGHier<T> &H, unsigned int *bc, unsigned int *bg, int *err, int bid, int nbk)
+{
+    const long long t0 = bid * (long long)blockDim.x + threadIdx.x, st = (long long)nbk * blockDim.x;
+    for (int k = 1; k < H.L; k++) {
+        mg_coarsen3<T>(H.lv[k - 1], H.lv[k], t0, st);
+        if (!grid_sync(bc, bg, err, nbk)) return false;
+    }
+    return true;
+}
+
+// One pass of MG-preconditioned CG in 3D: as mg_pass (pf_mg.cuh), every
+// level on the whole grid.  scell: 20 * HC values of dynamic shared memory.
+// Returns CTL_DONE or CTL_STOP, or -1 when a barrier timed out.
+template <typename T, int TX, int TY, int TZ>
+__device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S, T *su, T *sl, T *sm, T *scell,
+                        T &s_ta, T &s_tb, T *s_ue, int &s_ctl, int bid, int nbk, int *err)
+{
+    constexpr int NV = 6;
+    const bool lead = threadIdx.x == 0;
+    const int L = H.L, cs = H.csteps;
+    const MGLevel<T> &L0 = H.lv[0];
+    unsigned int *bc = A.bar_count, *bg = A.bar_gen;
+    auto sync = [&]() { return grid_sync(bc, bg, err, nbk); };
+    auto lin3 = [](const MGLevel<T> &V, int x, int y, int z) { return x + V.nx * (y + V.ny * z); };
+
+    // Chebyshev step j on level k (buffer par -> 1 - par); last: also apply
+    // step j + 1 and leave the final correction in xpost
+    auto cheb = [&](int k, int j, int par, bool post, bool last) {
+        const MGLevel<T> &V = H.lv[k];
+        T *const *X = post ? V.xpost : V.xpre;
+        const T c1 = H.c1[j], c2 = H.c2[j], n1 = H.c1[j + 1], n2 = H.c2[j + 1];
+        mg_sweep3<T, TX, TY, TZ, false>(
+            V.nx, V.ny, V.nz, V.lam, V.mu, bid, nbk, su, sl, sm, scell, nullptr,
+            [&](int gx, int gy, int gz, T (&v)[3]) {
+                const int g = lin3(V, gx, gy, gz);
+                const T di = c2 * __ldcg(V.dinv + g);
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    T a = di * __ldcg(V.r[par][c] + g);
+                    if (j > 0) a += c1 * __ldcg(V.d[par][c] + g);
+                    v[c] = a;
+                }
+            },
+            [&](int n, const T (&v)[3], const T (&q)[3], const T (&)[6]) {
+                const T di = last ? n2 * __ldcg(V.dinv + n) : T(0);
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const T x = __ldcg(X[c] + n) + v[c];
+                    const T rn = __ldcg(V.r[par][c] + n) - q[c];
+                    if (last) {
+                        V.xpost[c][n] = x + (n1 * v[c] + di * rn);
+                    } else {
+                        X[c][n] = x;
+                        V.r[1 - par][c][n] = rn;
+                        V.d[1 - par][c][n] = v[c];
+                    }
+                }
+            });
+    };
+    // restriction (transpose of trilinear prolongation) of level k-1's
+    // residual after its pre-smoothing, at node (gx, gy, gz) of level k
+    auto restrict3 = [&](int k, int gx, int gy, int gz, T (&f)[3]) {
+        const MGLevel<T> &F = H.lv[k - 1];
+        const int pf = H.deg[k - 1] & 1;
+        f[0] = f[1] = f[2] = T(0);
+        for (int cz = -1; cz <= 1; cz++) {
+            const int fz = wrap(2 * gz + cz, F.nz);
+            const T wz = cz == 0 ? T(1) : T(0.5);
+            for (int cy = -1; cy <= 1; cy++) {
+                const int fy = wrap(2 * gy + cy, F.ny);
+                const T wy = wz * (cy == 0 ? T(1) : T(0.5));
+#pragma unroll
+                for (int cx = -1; cx <= 1; cx++) {
+                    const int i = lin3(F, wrap(2 * gx + cx, F.nx), fy, fz);
+                    const T w = wy * (cx == 0 ? T(1) : T(0.5));
+#pragma unroll
+                    for (int c = 0; c < 3; c++) f[c] += w * __ldcg(F.r[pf][c] + i);
+                }
+            }
+        }
+    };
+    // first pre-smoothing sweep of level k >= 1: f = R r_{k-1}, x = d_0
+    auto pre_first = [&](int k) {
+        const MGLevel<T> &V = H.lv[k];
+        const T c2 = H.c2[0];
+        mg_sweep3<T, TX, TY, TZ, false>(
+            V.nx, V.ny, V.nz, V.lam, V.mu, bid, nbk, su, sl, sm, scell, nullptr,
+            [&](int gx, int gy, int gz, T (&v)[3]) {
+                T f[3];
+                restrict3(k, gx, gy, gz, f);
+                const T di = c2 * __ldcg(V.dinv + lin3(V, gx, gy, gz));
+#pragma unroll
+                for (int c = 0; c < 3; c++) v[c] = di * f[c];
+            },
+            [&](int n, const T (&v)[3], const T (&q)[3], const T (&)[6]) {
+                const int gx = n % V.nx, gy = (n / V.nx) % V.ny, gz = n / (V.nx * V.ny);
+                T f[3];
+                restrict3(k, gx, gy, gz, f);
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    V.f[c][n] = f[c];
+                    V.xpre[c][n] = v[c];
+                    V.r[1][c][n] = f[c] - q[c];
+                    V.d[1][c][n] = v[c];
+                }
+            });
+    };
+    // first post-smoothing sweep of level k: x = x_pre + P e_{k+1}, r = f - A x;
+    // last (one-step smoothing): x + c2[0] D^-1 r is the final correction
+    auto post_first = [&](int k, int par, int cur, bool last) {
+        const MGLevel<T> &V = H.lv[k];
+        const MGLevel<T> &C = H.lv[k + 1];
+        mg_sweep3<T, TX, TY, TZ, false>(
+            V.nx, V.ny, V.nz, V.lam, V.mu, bid, nbk, su, sl, sm, scell, nullptr,
+            [&](int gx, int gy, int gz, T (&v)[3]) {
+                const int g = lin3(V, gx, gy, gz);
+                const int o[3] = {gx & 1, gy & 1, gz & 1}, ic[3] = {gx >> 1, gy >> 1, gz >> 1};
+                const int nc[3] = {C.nx, C.ny, C.nz};
+                int i1[3];
+#pragma unroll
+                for (int a = 0; a < 3; a++) i1[a] = o[a] ? (ic[a] + 1 == nc[a] ? 0 : ic[a] + 1) : ic[a];
+                const T w = T(1) / T((1 + o[0]) * (1 + o[1]) * (1 + o[2]));
+                T e[3] = {T(0), T(0), T(0)};
+                for (int bz = 0; bz <= o[2]; bz++)
+                    for (int by = 0; by <= o[1]; by++)
+                        for (int bx = 0; bx <= o[0]; bx++) {
+                            const int ci = lin3(C, bx ? i1[0] : ic[0], by ? i1[1] : ic[1], bz ? i1[2] : ic[2]);
+#pragma unroll
+                            for (int c = 0; c < 3; c++) e[c] += __ldcg(C.xpost[c] + ci);
+                        }
+#pragma unroll
+                for (int c = 0; c < 3; c++) v[c] = __ldcg(V.xpre[c] + g) + w * e[c];
+            },
+            [&](int n, const T (&v)[3], const T (&q)[3], const T (&)[6]) {
+                const T di = last ? H.c2[0] * __ldcg(V.dinv + n) : T(0);
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const T f = k == 0 ? __ldcg(A.r[cur][c] + n) : __ldcg(V.f[c] + n);
+                    if (last) {
+                        V.xpost[c][n] = v[c] + di * (f - q[c]);
+                    } else {
+                        V.xpost[c][n] = v[c];
+                        V.r[1 - par][c][n] = f - q[c];
+                    }
+                }
+            });
+    };
+    auto post = [&](int k, int cur) {
+        const int dk = H.deg[k];
+        int par = dk & 1;
+        post_first(k, par, cur, dk == 1);
+        if (!sync()) return false;
+        par ^= 1;
+        for (int j = 0; j + 1 < dk; j++) {
+            cheb(k, j, par, true, j + 2 == dk);
+            if (!sync()) return false;
+            par ^= 1;
+        }
+        return true;
+    };
+    auto pre = [&](int k) {
+        pre_first(k);
+        if (!sync()) return false;
+        int par = 1;
+        const bool co = k == L - 1;
+        const int nk = co ? cs - 1 : H.deg[k];
+        for (int j = 1; j < nk; j++) {
+            cheb(k, j, par, false, co && j + 1 == nk);
+            if (!sync()) return false;
+            par ^= 1;
+        }
+        return true;
+    };
+
+    int cur = 0;
+    bool first = true;
+    while (true) {
+        if (lead) {
+            if (!first) cg_scalar_update<NV>(S);
+            s_ta = (T)S.alpha;
+            s_tb = (T)S.beta;
+            for (int vv = 0; vv < NV; vv++) s_ue[vv] = (T)S.UE[vv];
+        }
+        __syncthreads();
+        const T ta = s_ta, tb = s_tb;
+        const int nxt = first ? cur : 1 - cur;
+
+        // ---- finest level, first pre-smoothing sweep (+ the CG update)
+        Acc<T> racc[1];
+        {
+            const T c2 = H.c2[0];
+            mg_sweep3<T, TX, TY, TZ, false>(
+                L0.nx, L0.ny, L0.nz, L0.lam, L0.mu, bid, nbk, su, sl, sm, scell, nullptr,
+                [&](int gx, int gy, int gz, T (&v)[3]) {
+                    const int g = lin3(L0, gx, gy, gz);
+                    const T di = c2 * __ldcg(L0.dinv + g);
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        T rv = __ldcg(A.r[cur][c] + g);
+                        if (!first) rv -= ta * (__ldcg(A.w[cur][c] + g) + tb * __ldcg(A.s[cur][c] + g));
+                        v[c] = di * rv;
+                    }
+                },
+                [&](int n, const T (&v)[3], const T (&q)[3], const T (&)[6]) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        T f = __ldcg(A.r[cur][c] + n);
+                        if (!first) {
+                            const T si = __ldcg(A.w[cur][c] + n) + tb * __ldcg(A.s[cur][c] + n);
+                            const T pi = __ldcg(L0.xpost[c] + n) + tb * A.p[c][n];
+                            A.p[c][n] = pi;
+                            A.x[c][n] = A.x[c][n] + ta * pi;
+                            A.s[nxt][c][n] = si;
+                            f = f - ta * si;
+                            A.r[nxt][c][n] = f;
+                            racc[0].fma_plain(f, f);
+                        }
+                        L0.xpre[c][n] = v[c];
+                        L0.r[1][c][n] = f - q[c];
+                        L0.d[1][c][n] = v[c];
+                    }
+                });
+        }
+        if (!first) {
+            double tr[1];
+            if (!reduce_barrier<Acc<T>, 1>(racc, A.partials, A.result, A.bar_count, A.bar_gen, err, tr, bid, nbk)) return -1;
+            if (lead) {
+                double rnew = tr[0];
+                for (int vv = 0; vv < NV; vv++) rnew += S.RE[vv] * S.RE[vv];
+                S.it++;
+                S.rho_final = rnew;
+                int ctl = CTL_RUN;
+                if (rnew <= S.target * S.target) ctl = CTL_DONE;
+                else if (S.it_total + S.it >= A.maxit) ctl = CTL_STOP;
+                s_ctl = ctl;
+            }
+            __syncthreads();
+            cur = nxt;
+            const int ctl = s_ctl;
+            if (ctl != CTL_RUN) return ctl;
+        } else if (!sync()) {
+            return -1;
+        }
+
+        // ---- rest of the V-cycle
+        {
+            int par = 1;
+            const int n0 = L == 1 ? cs - 1 : H.deg[0];
+            for (int j = 1; j < n0; j++) {
+                cheb(0, j, par, false, L == 1 && j + 1 == n0);
+                if (!sync()) return -1;
+                par ^= 1;
+            }
+        }
+        for (int k = 1; k < L; k++)
+            if (!pre(k)) return -1;
+        for (int k = L - 2; k >= 0; k--)
+            if (!post(k, cur)) return -1;
+
+        // ---- u = V-cycle result, w = A u (+ mean strain), gamma, delta, mean-strain row
+        Acc<T> acc[2 + NV];
+        mg_sweep3<T, TX, TY, TZ, true>(
+            L0.nx, L0.ny, L0.nz, L0.lam, L0.mu, bid, nbk, su, sl, sm, scell, s_ue,
+            [&](int gx, int gy, int gz, T (&v)[3]) {
+                const int g = lin3(L0, gx, gy, gz);
+#pragma unroll
+                for (int c = 0; c < 3; c++) v[c] = __ldcg(L0.xpost[c] + g);
+            },
+            [&](int n, const T (&v)[3], const T (&q)[3], const T (&se)[6]) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    A.w[cur][c][n] = q[c];
+                    acc[0].fma_plain(__ldcg(A.r[cur][c] + n), v[c]);
+                    acc[1].fma_plain(q[c], v[c]);
+                }
+#pragma unroll
+                for (int vv = 0; vv < NV; vv++) acc[2 + vv].add_plain(se[vv]);
+            });
+        double tt[2 + NV];
+        if (!reduce_barrier<Acc<T>, 2 + NV>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tt, bid, nbk)) return -1;
+        if (lead) {
+            double s6[6];
+            dmat_mul<3>(S.Sl, S.Sm, S.UE, s6);
+            for (int vv = 0; vv < NV; vv++) S.WE[vv] = tt[2 + vv] + s6[vv];
+            double gnew = tt[0], dnew = tt[1];
+            for (int vv = 0; vv < NV; vv++) {
+                gnew += S.RE[vv] * S.UE[vv];
+                dnew += S.WE[vv] * S.UE[vv];
+            }
+            cg_take_gamma_delta(S, gnew, dnew, first);
+        }
+        first = false;
+    }
+}
+
+}  // namespace pfdev

@@ -12,7 +12,10 @@ iterations.
   here), so after a few steps the fields agree to 1e-8 (FP64, rtol 1e-10)
   or 1e-5 (mixed, rtol 1e-8), the stress to 1e3 times that;
 * a cold-start solve at 128x128 takes at most a fifth of Jacobi's iterations;
-* batches and CUDA-graph replay behave as with Jacobi.
+* batches and CUDA-graph replay behave as with Jacobi;
+* 3D (every level on the whole grid): against the oracle at 16^3 with the
+  tolerances of the 3D Jacobi parity test (1e-10 fields, 1e-8 stress), and
+  against Jacobi on 3-, 2- and 1-level hierarchies in both storage types.
 """
 import os
 
@@ -129,3 +132,33 @@ def test_mg_graph_replay_equals_eager():
         sim.close()
     for k in KEYS + ("u", "sigma", "eps_p"):
         assert np.array_equal(out[0][k], out[1][k]), (k, rel(out[1][k], out[0][k]))
+
+
+def test_mg3_fp64_against_oracle(orc):
+    shape = (16, 16, 16)
+    f = inputs.core_shell(shape, 5.0, 2.0, delta=1.5)
+    prm = workloads.params(plasticity=1, sigma_Y=0.004, H_hard=0.01, cg_rtol=1e-12)
+    g, d = _run(shape, prm, f, 6, "fp64", "mg")
+    assert d["precond"] == native.PF_PC_MG and d["mg_levels"] == 2
+    s = orc.Sim(f, prm)
+    s.step(6)
+    ref = {"phi_f": s.phi_f, "phi_w": s.phi_w, "xO": s.f["xO"], "xH": s.f["xH"], "xW": s.f["xW"]}
+    for k in KEYS:
+        assert rel(g[k], ref[k]) < 1e-10, (k, rel(g[k], ref[k]))
+    assert rel(g["sigma"], s.f["sigma"]) < 1e-8
+
+
+@pytest.mark.parametrize("shape,levels", [((32, 32, 32), 3), ((16, 24, 32), 2), ((9, 10, 12), 1)])
+@pytest.mark.parametrize("precision,rtol,tol", [("fp64", 1e-10, 1e-8), ("mixed", 1e-8, 1e-5)])
+def test_mg3_matches_jacobi(shape, levels, precision, rtol, tol):
+    f = inputs.core_shell(shape, 0.3 * min(shape), 0.1 * min(shape) + 1.0, delta=1.5)
+    prm = workloads.params(plasticity=1, sigma_Y=0.004, H_hard=0.01, cg_rtol=rtol, prestress=0.01)
+    gj, dj = _run(shape, prm, f, 4, precision, "jacobi")
+    gm, dm = _run(shape, prm, f, 4, precision, "mg")
+    assert dm["mg_levels"] == levels and dj["precond"] == native.PF_PC_JACOBI
+    for k in KEYS:
+        assert rel(gm[k], gj[k]) < tol, (k, rel(gm[k], gj[k]))
+    assert rel(gm["sigma"], gj["sigma"]) < 1e3 * tol, rel(gm["sigma"], gj["sigma"])
+    assert rel(gm["Ebar"], gj["Ebar"]) < 1e3 * tol
+    if levels > 1:
+        assert dm["cg_iters_total"] < dj["cg_iters_total"], (dm["cg_iters_total"], dj["cg_iters_total"])
