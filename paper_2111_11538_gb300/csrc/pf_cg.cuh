@@ -330,26 +330,19 @@ __device__ __forceinline__ void node_setup(const Params &P, long long n, const T
                 ax[0] += f[0];
                 ax[1] += f[1];
             } else {
+                // the exact hex decomposition: average stress (plus the mean
+                // strain) and hourglass forces of the cell, force on this node
+                TC c[20], sx[6], f[3];
+                cell_force3<TC>(l, m, ue, c);
+                if (a == 0)
 #pragma unroll
-                for (int co = 0; co < D; co++) {
-                    TC acc = TC(0);
+                    for (int v = 0; v < 6; v++) de_own[v] = c[v];
+                voigt_stress<TC, 3>(l, m, XE, sx);
 #pragma unroll
-                    for (int bn = 0; bn < NN; bn++)
+                for (int v = 0; v < 6; v++) c[v] += sx[v];
+                node_force3<TC>(ox, oy, oz, c, c + 6, f);
 #pragma unroll
-                        for (int cc = 0; cc < D; cc++)
-                            acc += (l * Kl<TC, D>(a * D + co, bn * D + cc) + m * Km<TC, D>(a * D + co, bn * D + cc)) * ue[bn][cc];
-                    ax[co] += acc;
-                }
-                TC se[NV];
-                voigt_stress<TC, D>(l, m, XE, se);
-                bbar_t<TC, D>(a, se, bt);
-#pragma unroll
-                for (int d = 0; d < D; d++) ax[d] += bt[d];
-                if (a == 0) {
-                    TC eb[NV];
-                    avg_strain<TC, D>(ue, eb);
-                    voigt_stress<TC, D>(l, m, eb, de_own);
-                }
+                for (int d = 0; d < 3; d++) ax[d] += f[d];
             }
         }
     }
