@@ -529,6 +529,10 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
                 // only form the residual
                 setup_tiled<T, TX, TY>(A, use_x, refine, refine && outer > 0, xe64,
                                        reinterpret_cast<double *>(pcg_dyn), acc, bid, nbk);
+            } else if constexpr (MG) {
+                // 3D multigrid variant: the same in 3D
+                setup_tiled3<T, TX, TY, TZ>(A, use_x, refine, refine && outer > 0, xe64,
+                                            reinterpret_cast<double *>(pcg_dyn), acc, bid, nbk);
             } else
             for (long long n = t0; n < N; n += st) {
                 double bv[D], rv[D];
@@ -569,7 +573,7 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
             if (lead) {
                 // a residual-only pass reuses the first pass's sums of b, the
                 // moduli and the eigenstress
-                if (MG && D == 2 && refine) {
+                if (MG && refine) {
                     if (outer == 0)
                         for (int k = 0; k < 10; k++) S.tot0[k] = tot[k];
                     else
@@ -992,10 +996,15 @@ size_t pcg_dyn_smem(int shape, bool mg)
                sizeof(T) * (size_t)sweep2_words<Tile<2, 0>::X, Tile<2, 0>::Y>();
     }
     if (D == 3 && mg) {
-        // the 3D V-cycle's per-cell stress and hourglass forces (mg_sweep3)
+        // the 3D V-cycle's per-cell stress and hourglass forces (mg_sweep3),
+        // or the set-up sweep's FP64 scratch (setup_tiled3)
         const int hc = shape == 1 ? (Tile<3, 1>::X + 1) * (Tile<3, 1>::Y + 1) * (Tile<3, 1>::Z + 1)
                                   : (Tile<3, 0>::X + 1) * (Tile<3, 0>::Y + 1) * (Tile<3, 0>::Z + 1);
-        return sizeof(T) * 20 * (size_t)hc;
+        const size_t cells = sizeof(T) * 20 * (size_t)hc;
+        const size_t stp = sizeof(double) * (size_t)(shape == 1
+            ? setup_tiled3_doubles<Tile<3, 1>::X, Tile<3, 1>::Y, Tile<3, 1>::Z>()
+            : setup_tiled3_doubles<Tile<3, 0>::X, Tile<3, 0>::Y, Tile<3, 0>::Z>());
+        return cells > stp ? cells : stp;
     }
     if (D != 3 || sizeof(T) != 4 || shape != 0) return 0;
     constexpr int HC = (Tile<3, 0>::X + 1) * (Tile<3, 0>::Y + 1) * (Tile<3, 0>::Z + 1);

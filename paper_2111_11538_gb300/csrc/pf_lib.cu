@@ -477,9 +477,9 @@ int build_mg(pf_handle *h)
         H.c2[j] = (T)(2.0 * rn / delta);
         rho = rn;
     }
-    // 2D mixed method: the first refinement pass keeps b (FP64) for the later ones
-    if (D == 2 && h->refine)
-        for (int c = 0; c < 2; c++) PF_TRY(h->alloc(&h->b64[c], sizeof(double) * (size_t)h->P.N));
+    // mixed method: the first refinement pass keeps b (FP64) for the later ones
+    if (h->refine)
+        for (int c = 0; c < D; c++) PF_TRY(h->alloc(&h->b64[c], sizeof(double) * (size_t)h->P.N));
     if (!h->d_mg) PF_TRY(h->alloc(&h->d_mg, sizeof(H)));
     return h->cuda(cudaMemcpy(h->d_mg, &H, sizeof(H), cudaMemcpyHostToDevice), "multigrid descriptor");
 }

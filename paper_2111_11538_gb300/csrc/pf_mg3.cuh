@@ -130,6 +130,127 @@ __device__ void mg_coarsen3(const MGLevel<T> &F, const MGLevel<T> &C, long long 
     }
 }
 
+// Shared memory (in doubles) of setup_tiled3 for a TX x TY x TZ tile: the
+// FP64 operand on the halo and 18 values per halo cell.
+template <int TX, int TY, int TZ>
+__host__ __device__ constexpr int setup_tiled3_doubles()
+{
+    return 3 * (TX + 2) * (TY + 2) * (TZ + 2) + 18 * (TX + 1) * (TY + 1) * (TZ + 1);
+}
+
+// The set-up sweep of one CG pass in 3D (setup_tiled in 2D): b, the Jacobi
+// diagonal, r = b - A x with the operator applied in FP64 from per-cell
+// stress and hourglass forces computed once per tile, and the sums of the
+// mean-strain rows (acc[0] ||b||^2, [1] ||r||^2, [2] sum lam, [3] sum mu,
+// [4..9] sum sig*, [10..15] the own cells' stress of x without the mean
+// strain).  resid: a later refinement pass, which reads b from A.b64 and
+// skips what does not change during a solve.
+template <typename T, int TX, int TY, int TZ>
+__device__ void setup_tiled3(const PCGArgs<T, 3> &A, bool use_x, bool refine, bool resid, const double *xe,
+                             double *dscr, Acc<double> (&acc)[16], int bid, int nbk)
+{
+    const Params &P = A.P;
+    constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HN = HX * HY * HZ;
+    constexpr int CX = TX + 1, CY = TY + 1, CZ = TZ + 1, HC = CX * CY * CZ, NT = TX * TY * TZ;
+    double *hu = dscr, *hc = dscr + 3 * HN;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntz = (nz + TZ - 1) / TZ;
+    const int ntiles = ntx * nty * ntz;
+    const bool small = nx < HX || ny < HY || nz < HZ;
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    auto gidx = [&](int x, int y, int z) {
+        return mg_wrap(x, nx, small) + nx * (mg_wrap(y, ny, small) + ny * mg_wrap(z, nz, small));
+    };
+    for (int tile = bid; tile < ntiles; tile += nbk) {
+        const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY, z0 = (tile / (ntx * nty)) * TZ;
+        if (use_x) {
+            for (int h = threadIdx.x; h < HN; h += NT) {
+                const int g = gidx(x0 - 1 + h % HX, y0 - 1 + (h / HX) % HY, z0 - 1 + h / (HX * HY));
+#pragma unroll
+                for (int c = 0; c < 3; c++) hu[c * HN + h] = refine ? __ldcg(A.x64[c] + g) : (double)A.x[c][g];
+            }
+            __syncthreads();
+            for (int h = threadIdx.x; h < HC; h += NT) {
+                const int cx = h % CX, cy = (h / CX) % CY, cz = h / (CX * CY);
+                const int g = gidx(x0 - 1 + cx, y0 - 1 + cy, z0 - 1 + cz);
+                double uc[8][3];
+#pragma unroll
+                for (int b = 0; b < 8; b++) {
+                    const int hn = (cx + (b & 1)) + HX * ((cy + ((b >> 1) & 1)) + HY * (cz + (b >> 2)));
+#pragma unroll
+                    for (int c = 0; c < 3; c++) uc[b][c] = hu[c * HN + hn];
+                }
+                const double l = (double)A.lam[g], m = (double)A.mu[g];
+                double cf[20], sx[6];
+                cell_force3<double>(l, m, uc, cf);
+                voigt_stress<double, 3>(l, m, xe, sx);
+#pragma unroll
+                for (int v = 0; v < 6; v++) cf[v] += sx[v];
+#pragma unroll
+                for (int v = 0; v < 18; v++) hc[v * HC + h] = cf[v];
+            }
+            __syncthreads();
+        }
+        const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+        if (gx < nx && gy < ny && gz < nz) {
+            const int n = gx + nx * (gy + ny * gz), lx = tx + 1, ly = ty + 1, lz = tz + 1;
+            double b[3], ax[3] = {0.0, 0.0, 0.0}, dgn = 1.0, so[6], deo[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, lo, mo;
+            if (resid) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) b[c] = __ldcg(A.b64[c] + n);
+                lo = (double)A.lam[n];
+                mo = (double)A.mu[n];
+            } else {
+                double unused[3], unused6[6];
+                node_setup<T, double, double, 3>(P, n, A.lam, A.mu, A.sig, A.x64, xe, false, b, unused, dgn, so, unused6,
+                                                 lo, mo);
+                if (refine)
+#pragma unroll
+                    for (int c = 0; c < 3; c++) A.b64[c][n] = b[c];
+            }
+            if (use_x) {
+#pragma unroll
+                for (int a = 0; a < 8; a++) {
+                    const int ax_ = a & 1, ay_ = (a >> 1) & 1, az_ = a >> 2;
+                    const int cl = (lx - ax_) + CX * ((ly - ay_) + CY * (lz - az_));
+                    double cf[18], f[3];
+#pragma unroll
+                    for (int v = 0; v < 18; v++) cf[v] = hc[v * HC + cl];
+                    node_force3<double>(ax_, ay_, az_, cf, cf + 6, f);
+#pragma unroll
+                    for (int c = 0; c < 3; c++) ax[c] += f[c];
+                }
+                const int c0 = lx + CX * (ly + CY * lz);
+                double sx[6];
+                voigt_stress<double, 3>(lo, mo, xe, sx);
+#pragma unroll
+                for (int v = 0; v < 6; v++) deo[v] = hc[v * HC + c0] - sx[v];
+            }
+            if (!resid) {
+                A.dinv[n] = (T)(1.0 / dgn);
+                acc[2].add(lo);
+                acc[3].add(mo);
+#pragma unroll
+                for (int v = 0; v < 6; v++) acc[4 + v].add(so[v]);
+            }
+#pragma unroll
+            for (int v = 0; v < 6; v++) acc[10 + v].add(deo[v]);
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const double rv = b[d] - ax[d];
+                if (refine && !use_x) A.x64[d][n] = 0.0;
+                if (refine || !use_x) A.x[d][n] = T(0);
+                A.p[d][n] = T(0);
+                A.s[0][d][n] = T(0);
+                A.r[0][d][n] = (T)rv;
+                if (!resid) acc[0].addprod(b[d], b[d]);
+                acc[1].addprod(rv, rv);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Set-up of the 3D hierarchy at the start of a solve (grid levels, a barrier
 // after each).  Returns false if a barrier timed out.
 template <typename T>

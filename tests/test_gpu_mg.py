@@ -162,3 +162,21 @@ def test_mg3_matches_jacobi(shape, levels, precision, rtol, tol):
     assert rel(gm["Ebar"], gj["Ebar"]) < 1e3 * tol
     if levels > 1:
         assert dm["cg_iters_total"] < dj["cg_iters_total"], (dm["cg_iters_total"], dj["cg_iters_total"])
+
+
+def test_mg3_batch_matches_single():
+    shapes = [(32, 32, 32), (16, 32, 48)]
+    fields = [inputs.core_shell(shapes[0], 9.0, 3.0, delta=1.5), inputs.core_shell(shapes[1], 6.0, 2.0, delta=1.5)]
+    prm = workloads.params(plasticity=1, sigma_Y=0.004, H_hard=0.01, cg_rtol=1e-10, precond="mg")
+    b = Batch(shapes, prm, precision="fp64")
+    for i, f in enumerate(fields):
+        b.set_fields(i, f)
+    b.step(4)
+    for i, (s, f) in enumerate(zip(shapes, fields)):
+        ref, d = _run(s, prm, f, 4, "fp64", "mg")
+        got = b.get_fields(i)
+        assert b.diagnostics(i)["mg_levels"] == d["mg_levels"] >= 2
+        for k in KEYS:
+            assert rel(got[k], ref[k]) < 1e-10, (i, k, rel(got[k], ref[k]))
+        assert rel(got["sigma"], ref["sigma"]) < 1e-7
+    b.close()
