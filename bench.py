@@ -119,11 +119,12 @@ class ClockSampler:
 
 WORKLOAD = "coreshell512"
 PRECOND = "auto"
+SHAPE = None        # grid override for the short profiling lines (--shape)
 
 
 def workload_fields():
     from paper_2111_11538_gb300 import workloads
-    return workloads.build_fields(WORKLOAD)
+    return workloads.build_fields(WORKLOAD, shape=SHAPE)
 
 
 def workload_params(precision):
@@ -364,10 +365,17 @@ def main():
                     help="profiling aid: run one method only and print a short line")
     ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "mg"],
                     help="CG preconditioner (auto: the library's choice for the grid)")
+    ap.add_argument("--shape", default=None,
+                    help="profiling aid with --only: the workload's geometry on another grid, "
+                         "e.g. 128,128,128 (nz,ny,nx)")
     args = ap.parse_args()
-    global WORKLOAD, PRECOND
+    global WORKLOAD, PRECOND, SHAPE
     WORKLOAD = args.workload
     PRECOND = args.precond
+    if args.shape:
+        if args.only == "both":
+            ap.error("--shape needs --only (the headline line is measured on the workload's own grid)")
+        SHAPE = tuple(int(v) for v in args.shape.split(","))
     if args.warmup < 3:
         args.warmup = 3
 
@@ -433,9 +441,11 @@ def main():
     if args.only != "both":
         ms1, prof1, diag1, _ = run_gpu(args.only, args.steps, args.warmup, fields)
         if rank == 0:
-            print(json.dumps({"workload": WORKLOAD, "method": args.only, "cells": N, "steps": args.steps,
+            print(json.dumps({"workload": WORKLOAD, "shape": list(fields["phi_f"].shape), "method": args.only,
+                              "cells": N, "steps": args.steps,
                               "ms_per_step": ms1 / args.steps, "value": N * args.steps / (ms1 / 1e3),
-                              "kernel_ms": prof1["ms"], "cg_iters": prof1["cg_iters"]}))
+                              "kernel_ms": prof1["ms"], "cg_iters": prof1["cg_iters"],
+                              "precond": prof1.get("precond"), "mg_levels": prof1.get("mg_levels")}))
         return
 
     # plain FP64 method (reported beside the chosen form)
