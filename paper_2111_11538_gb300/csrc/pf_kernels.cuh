@@ -925,6 +925,46 @@ __global__ void k_net_guess(long long N, const float *y, const int *mode, double
 
 static __global__ void k_net_mode_clear(int *mode) { *mode = 0; }
 
+// Extrapolated initial guess of the solve (PF_WS_EXTRAP): with x_n the last
+// solution and h = x_{n-1} the one before it, the guess is 2 x_n - x_{n-1}
+// (linear in time); h then takes x_n.  *count (reset by pf_set_fields) is
+// the number of guesses formed since: the first two only record (the state
+// set by the caller is not a solution of a previous step).  In the mixed
+// method the FP64 copy x64 is the solve's initial guess and u follows it.
+template <typename T, int D>
+__global__ void k_extrap(long long N, const int *count, T *u0, T *u1, T *u2, double *x0, double *x1, double *x2,
+                         double *h0, double *h1, double *h2)
+{
+    const bool ext = *count >= 2;
+    T *u[3] = {u0, u1, u2};
+    double *x[3] = {x0, x1, x2}, *hh[3] = {h0, h1, h2};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < D; d++) {
+            const double xn = x[d] ? x[d][c] : (double)u[d][c];
+            if (ext) {
+                const double g = 2.0 * xn - hh[d][c];
+                if (x[d]) x[d][c] = g;
+                u[d][c] = (T)g;
+            }
+            hh[d][c] = xn;
+        }
+    }
+}
+
+// The mean strain's part of the extrapolated guess, and the count.
+static __global__ void k_extrap_tail(int *count, double *E, double *Eh, int nv)
+{
+    if (threadIdx.x != 0) return;
+    const bool ext = *count >= 2;
+    for (int v = 0; v < nv; v++) {
+        const double en = E[v];
+        if (ext) E[v] = 2.0 * en - Eh[v];
+        Eh[v] = en;
+    }
+    if (*count < 2) *count = *count + 1;
+}
+
 // Self-test of the bounded wait: one thread waits on a generation word that
 // nothing advances.
 static __global__ void k_wait_selftest(const unsigned int *gen, int *err, long long limit)

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +17,9 @@
 #include "unet_net.h"
 #include "pf_cg.cuh"
 #include "pcg_launch.h"
+
+// k_extrap_tail addresses the mean strain as the start of Scalars
+static_assert(offsetof(pfdev::Scalars, E) == 0, "Scalars::E must be the first member");
 
 // PCG node tile per size class (0: 32x8 / 16x4x4, 1: 32x16 / 32x4x2),
 // from the measurements of paper_2111_11538_gb300/autotune.py on GB300.
@@ -220,6 +224,11 @@ struct pf_handle {
     float *net_in = nullptr;            // N x 4 network inputs
     float *net_prev = nullptr;          // N previous ferrite weight
     int *net_mode = nullptr;            // 1: first step after pf_set_fields (no guess), 0: guess
+    // extrapolated warm start (PF_WS_EXTRAP): the previous solution (FP64),
+    // the previous mean strain, and the number of guesses since set_fields
+    double *ext_hist[3] = {};
+    double *ext_E = nullptr;
+    int *ext_count = nullptr;
     std::vector<void *> net_allocs;
 
     // profiling: event pairs around each launch while enabled
@@ -717,6 +726,20 @@ int launch_step(pf_handle *h, cudaStream_t s, int k)
         h->mark_begin(PF_K_SETUP, s);
         k_setup<T, D><<<h->cell_grid, 256, 0, s>>>(cj);
         h->mark_end(s);
+        if (h->cfg.warm_start == PF_WS_EXTRAP) {
+            h->mark_begin(PF_K_WARM, s);
+            for (pf_handle *m : instances(h)) {
+                const long long N = m->P.N;
+                T *u[3] = {(T *)m->u[0], (T *)m->u[1], (T *)m->u[2]};
+                double *x[3] = {m->refine ? m->x64[0] : nullptr, m->refine ? m->x64[1] : nullptr,
+                                m->refine ? m->x64[2] : nullptr};
+                k_extrap<T, D><<<grid_for(m, N), 256, 0, s>>>(N, m->ext_count, u[0], u[1], u[2], x[0], x[1], x[2],
+                                                             m->ext_hist[0], m->ext_hist[1], m->ext_hist[2]);
+                k_extrap_tail<<<1, 32, 0, s>>>(m->ext_count, reinterpret_cast<double *>(m->sc), m->ext_E,
+                                               D == 2 ? 3 : 6);       // Scalars::E is the first member
+            }
+            h->mark_end(s);
+        }
         if (h->cfg.warm_start == PF_WS_LEARNED) {
             h->mark_begin(PF_K_WARM, s);
             for (pf_handle *m : instances(h)) {
@@ -901,6 +924,7 @@ int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
         static const int first = 1;
         PF_TRY(h->cuda(cudaMemcpyAsync(h->net_mode, &first, sizeof(int), cudaMemcpyHostToDevice, s), "net mode"));
     }
+    if (h->ext_count) PF_TRY(h->cuda(cudaMemsetAsync(h->ext_count, 0, sizeof(int), s), "extrapolation count"));
     return h->cuda(cudaGetLastError(), "set_fields kernels");
 #undef PF_SRC
 }
@@ -993,6 +1017,12 @@ int alloc_fields(pf_handle *h)
         }
         PF_TRY(h->alloc(&h->result, sizeof(double) * 32));
         PF_TRY(h->alloc(&h->diag, b));
+        if (h->cfg.warm_start == PF_WS_EXTRAP) {
+            for (int d = 0; d < D; d++) PF_TRY(h->alloc(&h->ext_hist[d], sizeof(double) * (size_t)N));
+            PF_TRY(h->alloc(&h->ext_E, sizeof(double) * 6));
+            PF_TRY(h->alloc(&h->ext_count, sizeof(int)));
+            PF_TRY(h->cuda(cudaMemset(h->ext_count, 0, sizeof(int)), "extrapolation count"));
+        }
         if (!h->fp64) {
             h->refine = true;
             for (int d = 0; d < D; d++) {
@@ -1050,7 +1080,8 @@ int create_one(const pf_config *cfg, pf_handle **out, std::string &err)
     if (c.ndim != 2 && c.ndim != 3) { err = "ndim must be 2 or 3"; return PF_EINVAL; }
     if (c.nx < 2 || c.ny < 2 || (c.ndim == 3 && c.nz < 2)) { err = "grid sizes must be >= 2"; return PF_EINVAL; }
     if (c.precision != PF_FP64 && c.precision != PF_MIXED) { err = "precision must be PF_FP64 or PF_MIXED"; return PF_EINVAL; }
-    if (c.warm_start != PF_WS_ZERO && c.warm_start != PF_WS_PREV && c.warm_start != PF_WS_LEARNED) {
+    if (c.warm_start != PF_WS_ZERO && c.warm_start != PF_WS_PREV && c.warm_start != PF_WS_LEARNED &&
+        c.warm_start != PF_WS_EXTRAP) {
         err = "warm_start must be PF_WS_ZERO, PF_WS_PREV or PF_WS_LEARNED";
         return PF_EINVAL;
     }

@@ -67,3 +67,27 @@ def test_trained_network_predicts_the_displacement_rate():
     assert np.mean(hist[-50:]) < 0.5 * np.mean(hist[:50])
     err = ws.rate_error(net, Xh, Th)
     assert err < 0.8, err
+
+
+@pytest.mark.parametrize("precision,rtol,tol", [("fp64", 1e-10, 1e-9), ("mixed", 1e-8, 1e-5)])
+def test_extrapolated_guess(precision, rtol, tol):
+    """PF_WS_EXTRAP (2 u_n - u_{n-1} from the third step on) solves to the
+    same tolerance as the previous-step guess, and once the history exists
+    its solves need fewer iterations."""
+    shape = (64, 64)
+    f = inputs.core_shell(shape, 20.0, 4.0)
+    prm = workloads.params(plasticity=1, sigma_Y=0.004, H_hard=0.01, cg_rtol=rtol, prestress=0.01)
+    out = {}
+    for warm in ("prev", "extrap"):
+        sim = Simulation(shape, dict(prm, warm_start=warm), precision=precision)
+        sim.set_fields(f)
+        sim.step(8)
+        its0 = sim.diagnostics()["cg_iters_total"]
+        sim.step(12)
+        out[warm] = (sim.get_fields(), sim.diagnostics()["cg_iters_total"] - its0)
+        sim.close()
+    (gp, ip), (ge, ie) = out["prev"], out["extrap"]
+    for k in ("phi_f", "phi_w", "xO", "xH", "xW"):
+        assert rel(ge[k], gp[k]) < tol, (k, rel(ge[k], gp[k]))
+    assert rel(ge["sigma"], gp["sigma"]) < 1e3 * tol
+    assert ie < ip, (ie, ip)
