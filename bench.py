@@ -219,6 +219,8 @@ def run_batch(precision, steps, warmup, count=64, seed=4, profile=True, rank=0, 
     desc = [desc[i] for i in mine]
     count = len(desc)
     base = dict(workloads.WORKLOADS["batch64"]["params"], precond=PRECOND)
+    if WARM:
+        base["warm_start"] = WARM
     shapes = [(d["n"], d["n"]) for d in desc]
     prms = [dict(base, prestress=d["prestress"]) for d in desc]
     b = Batch(shapes, prms, precision=precision)

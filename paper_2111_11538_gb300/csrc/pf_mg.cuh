@@ -479,6 +479,99 @@ __device__ void mg_setup_block(const MGHier<T> &H, T *sblk)
     }
 }
 
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two
+// FP32 numbers (~48 significant bits).  Sums use Knuth's TwoSum, products
+// the FMA form of TwoProduct; results are renormalised with the fast
+// two-sum (|a| >= |b|).  The mixed method's refinement residual b - A x is
+// formed this way: FP64 runs at a small fraction of the FP32 rate here.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_quick(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b)
+{
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF df_from(double x)
+{
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_val(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const DF s = df_two_sum(a.hi, b.hi), t = df_two_sum(a.lo, b.lo);
+    const DF u = df_quick(s.hi, s.lo + t.hi);
+    return df_quick(u.hi, u.lo + t.lo);
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+// exact scaling by a power of two
+__device__ __forceinline__ DF df_scale(DF a, float p2) { return {a.hi * p2, a.lo * p2}; }
+__device__ __forceinline__ DF df_mul_f(DF a, float b)
+{
+    const float p = a.hi * b;
+    const float e = fmaf(a.hi, b, -p);
+    return df_quick(p, fmaf(a.lo, b, e));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p);
+    return df_quick(p, e + fmaf(a.hi, b.lo, a.lo * b.hi));
+}
+
+// plane-strain stress of a Voigt strain e (engineering shear) in
+// double-float: l tr e + 2 m e on the normals, m e on the shear
+__device__ __forceinline__ void voigt2_df(float l, float m, const DF (&e)[3], DF (&s)[3])
+{
+    const float m2 = 2.0f * m;                 // exact
+    const DF tr = df_add(e[0], e[1]);
+    s[0] = df_add(df_mul_f(tr, l), df_mul_f(e[0], m2));
+    s[1] = df_add(df_mul_f(tr, l), df_mul_f(e[1], m2));
+    s[2] = df_mul_f(e[2], m);
+}
+
+// cell_force2 in double-float: average stress of the cell's displacement
+// plus the mean-strain stress, hourglass forces (l, m: the FP32 moduli)
+__device__ __forceinline__ void cell_force2_df(float l, float m, const DF (&ue)[4][2], const DF (&xe)[3], DF (&s)[3],
+                                               DF (&fh)[2], DF (&s_own)[3])
+{
+    const DF Gxu = df_scale(df_add(df_sub(ue[1][0], ue[0][0]), df_sub(ue[3][0], ue[2][0])), 0.5f);
+    const DF Gyu = df_scale(df_add(df_sub(ue[2][0], ue[0][0]), df_sub(ue[3][0], ue[1][0])), 0.5f);
+    const DF Gxv = df_scale(df_add(df_sub(ue[1][1], ue[0][1]), df_sub(ue[3][1], ue[2][1])), 0.5f);
+    const DF Gyv = df_scale(df_add(df_sub(ue[2][1], ue[0][1]), df_sub(ue[3][1], ue[1][1])), 0.5f);
+    const DF hu = df_sub(df_sub(ue[0][0], ue[1][0]), df_sub(ue[2][0], ue[3][0]));
+    const DF hv = df_sub(df_sub(ue[0][1], ue[1][1]), df_sub(ue[2][1], ue[3][1]));
+    const DF G[3] = {Gxu, Gyv, df_add(Gyu, Gxv)};   // Voigt strain, engineering shear
+    voigt2_df(l, m, G, s_own);
+    DF sx[3];
+    voigt2_df(l, m, xe, sx);
+#pragma unroll
+    for (int v = 0; v < 3; v++) s[v] = df_add(s_own[v], sx[v]);
+    // (l + 3 m) / 12, with l + 3 m exact as a double-float
+    const float p3 = 3.0f * m;
+    const DF l3m = df_add(DF{l, 0.0f}, DF{p3, fmaf(3.0f, m, -p3)});
+    const DF c = df_mul(l3m, df_from(1.0 / 12.0));
+    fh[0] = df_mul(c, hu);
+    fh[1] = df_mul(c, hv);
+}
+
+// node_force2 in double-float
+__device__ __forceinline__ void node_force2_df(int a, const DF (&s)[3], const DF (&fh)[2], DF (&f)[2])
+{
+    const float bx = (a & 1) ? 0.5f : -0.5f, by = (a >> 1) ? 0.5f : -0.5f;
+    const bool gp = (a == 0 || a == 3);
+    const DF g0 = gp ? fh[0] : df_neg(fh[0]), g1 = gp ? fh[1] : df_neg(fh[1]);
+    f[0] = df_add(df_add(df_scale(s[0], bx), df_scale(s[2], by)), g0);
+    f[1] = df_add(df_add(df_scale(s[1], by), df_scale(s[2], bx)), g1);
+}
+
 // Shared memory (in doubles) of setup_tiled for a TX x TY tile: the FP64
 // operand on the tile halo and five values per halo cell.
 template <int TX, int TY>
@@ -502,7 +595,8 @@ __host__ __device__ constexpr size_t mg_pair_offset()
 // computed once per tile (dscr: setup_tiled_doubles<TX, TY>() doubles of
 // shared memory), and the per-node sums of the mean-strain rows: acc[0]
 // ||b||^2, [1] ||r||^2, [2] sum lam, [3] sum mu, [4..6] sum sig*, [10..12]
-// sum of the own cells' stress of x without the mean strain.  Also clears
+// sum of the own cells' stress of x without the mean strain; in the mixed
+// method the operator part is evaluated in double-float.  Also clears
 // p, s and (when x is not used or in refinement mode) the iterate.  In
 // refinement mode the first pass keeps b in A.b64; a residual-only pass
 // (resid) reads it there and skips everything that does not change during
@@ -518,9 +612,39 @@ __device__ void setup_tiled(const PCGArgs<T, 2> &A, bool use_x, bool refine, boo
     const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntiles = ntx * nty;
     const bool small = nx < HX || ny < HY;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    // the mixed method's refinement residual: double-float instead of FP64
+    const bool dfp = refine && sizeof(T) == 4;
+    DF *du = reinterpret_cast<DF *>(dscr), *dc = du + 2 * HN;      // same bytes as hu, hc
+    const DF xed[3] = {df_from(xe[0]), df_from(xe[1]), df_from(xe[2])};
     for (int tile = bid; tile < ntiles; tile += nbk) {
         const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-        if (use_x) {
+        if (use_x && dfp) {
+            for (int h = threadIdx.x; h < HN; h += NT) {
+                const int g = mg_wrap(x0 - 1 + h % HX, nx, small) + nx * mg_wrap(y0 - 1 + h / HX, ny, small);
+                du[h] = df_from(__ldcg(A.x64[0] + g));
+                du[HN + h] = df_from(__ldcg(A.x64[1] + g));
+            }
+            __syncthreads();
+            for (int h = threadIdx.x; h < HC; h += NT) {
+                const int cx = h % CX, cy = h / CX;
+                const int g = mg_wrap(x0 - 1 + cx, nx, small) + nx * mg_wrap(y0 - 1 + cy, ny, small);
+                DF uc[4][2];
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    const int hn = (cx + (b & 1)) + HX * (cy + (b >> 1));
+                    uc[b][0] = du[hn];
+                    uc[b][1] = du[HN + hn];
+                }
+                DF s3[3], fh[2], own[3];
+                cell_force2_df((float)A.lam[g], (float)A.mu[g], uc, xed, s3, fh, own);
+                dc[h] = s3[0];
+                dc[HC + h] = s3[1];
+                dc[2 * HC + h] = s3[2];
+                dc[3 * HC + h] = fh[0];
+                dc[4 * HC + h] = fh[1];
+            }
+            __syncthreads();
+        } else if (use_x) {
             for (int h = threadIdx.x; h < HN; h += NT) {
                 const int g = mg_wrap(x0 - 1 + h % HX, nx, small) + nx * mg_wrap(y0 - 1 + h / HX, ny, small);
                 hu[h] = refine ? __ldcg(A.x64[0] + g) : (double)A.x[0][g];
@@ -566,7 +690,28 @@ __device__ void setup_tiled(const PCGArgs<T, 2> &A, bool use_x, bool refine, boo
                     A.b64[1][n] = b[1];
                 }
             }
-            if (use_x) {
+            double rv2[2] = {b[0], b[1]};
+            if (use_x && dfp) {
+                DF axd[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    const int cl = (lx - (a & 1)) + CX * (ly - (a >> 1));
+                    const DF s3[3] = {dc[cl], dc[HC + cl], dc[2 * HC + cl]};
+                    const DF fh[2] = {dc[3 * HC + cl], dc[4 * HC + cl]};
+                    DF f[2];
+                    node_force2_df(a, s3, fh, f);
+                    axd[0] = df_add(axd[0], f[0]);
+                    axd[1] = df_add(axd[1], f[1]);
+                }
+#pragma unroll
+                for (int d = 0; d < 2; d++) rv2[d] = df_val(df_sub(df_from(b[d]), axd[d]));
+                // the own cell's stress of x without the mean strain
+                const int c0 = lx + CX * ly;
+                DF sx[3];
+                voigt2_df((float)lo, (float)mo, xed, sx);
+#pragma unroll
+                for (int v = 0; v < 3; v++) deo[v] = df_val(df_sub(dc[v * HC + c0], sx[v]));
+            } else if (use_x) {
 #pragma unroll
                 for (int a = 0; a < 4; a++) {
                     const int cl = (lx - (a & 1)) + CX * (ly - (a >> 1));
@@ -584,6 +729,8 @@ __device__ void setup_tiled(const PCGArgs<T, 2> &A, bool use_x, bool refine, boo
                 deo[0] = hc[c0] - sx[0];
                 deo[1] = hc[HC + c0] - sx[1];
                 deo[2] = hc[2 * HC + c0] - sx[2];
+                rv2[0] = b[0] - ax[0];
+                rv2[1] = b[1] - ax[1];
             }
             if (!resid) {
                 A.dinv[n] = (T)(1.0 / dgn);
@@ -596,7 +743,7 @@ __device__ void setup_tiled(const PCGArgs<T, 2> &A, bool use_x, bool refine, boo
             for (int v = 0; v < 3; v++) acc[10 + v].add(deo[v]);
 #pragma unroll
             for (int d = 0; d < 2; d++) {
-                const double rv = b[d] - ax[d];
+                const double rv = rv2[d];
                 if (refine && !use_x) A.x64[d][n] = 0.0;
                 if (refine || !use_x) A.x[d][n] = T(0);
                 A.p[d][n] = T(0);
