@@ -120,7 +120,7 @@ class ClockSampler:
 WORKLOAD = "coreshell512"
 PRECOND = "auto"
 SHAPE = None        # grid override for the short profiling lines (--shape)
-WARM = "extrap"     # CG initial guess (--warm-start): 2 u_n - u_{n-1} by default
+WARM = None         # CG initial guess (--warm-start); default: the workload's "warm_start", else "extrap"
 
 
 def workload_fields():
@@ -133,9 +133,13 @@ def workload_params(precision):
     # both forms solve to the workload's CG residual: the mixed form reaches
     # it through FP64 iterative refinement around its FP32 iteration
     p = dict(workloads.WORKLOADS[WORKLOAD]["params"], precond=PRECOND)
-    if WARM:
-        p["warm_start"] = WARM
+    p["warm_start"] = warm_mode()
     return p
+
+
+def warm_mode():
+    from paper_2111_11538_gb300 import workloads
+    return WARM or workloads.WORKLOADS[WORKLOAD].get("warm_start", "extrap")
 
 
 def run_gpu(precision, steps, warmup, fields, profile=True, warm=None, net=None):
@@ -218,9 +222,7 @@ def run_batch(precision, steps, warmup, count=64, seed=4, profile=True, rank=0, 
     mine = sharding.shard([sharding.instance_cost((d["n"], d["n"])) for d in desc], world)[rank]
     desc = [desc[i] for i in mine]
     count = len(desc)
-    base = dict(workloads.WORKLOADS["batch64"]["params"], precond=PRECOND)
-    if WARM:
-        base["warm_start"] = WARM
+    base = dict(workloads.WORKLOADS["batch64"]["params"], precond=PRECOND, warm_start=warm_mode())
     shapes = [(d["n"], d["n"]) for d in desc]
     prms = [dict(base, prestress=d["prestress"]) for d in desc]
     b = Batch(shapes, prms, precision=precision)
@@ -268,7 +270,7 @@ def learned_warm_start(steps, warmup, fields, prev_ms, prev_iters):
     N = fields["phi_f"].size
     net.close()
     return {"value": N * steps / (ms / 1e3), "unit": "cell-steps/s", "ms_per_step": ms / steps,
-            "cg_iters_per_step": prof["cg_iters"] / steps, "default_guess": WARM, "default_guess_cg_iters_per_step": prev_iters / steps,
+            "cg_iters_per_step": prof["cg_iters"] / steps, "default_guess": warm_mode(), "default_guess_cg_iters_per_step": prev_iters / steps,
             "default_guess_ms_per_step": prev_ms / steps, "network_ms": prof["ms"]["warm"] / max(1, prof["count"]["warm"]),
             "training": info}
 
@@ -372,9 +374,9 @@ def main():
                     help="profiling aid: run one method only and print a short line")
     ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "mg"],
                     help="CG preconditioner (auto: the library's choice for the grid)")
-    ap.add_argument("--warm-start", default="extrap", choices=["zero", "prev", "extrap"],
-                    help="CG initial guess: linear extrapolation from the two previous solutions "
-                         "(default), the previous solution, or zero")
+    ap.add_argument("--warm-start", default=None, choices=["zero", "prev", "extrap", "extrap2"],
+                    help="CG initial guess: extrapolation from the previous solutions (first or "
+                         "second order), the previous solution, or zero; default: the workload's choice")
     ap.add_argument("--shape", default=None,
                     help="profiling aid with --only: the workload's geometry on another grid, "
                          "e.g. 128,128,128 (nz,ny,nx)")
@@ -394,7 +396,8 @@ def main():
     cfg = {"workload": "coreshell512_j2: 2D core-shell 512x512, radius 160, shell 32, J2 plasticity "
                        "sigma_Y=0.01E H=0.001E",
            "warm_start": {"extrap": "2 u_n - u_(n-1) (previous solution for the first two steps)",
-                          "prev": "previous solution", "zero": "zero"}[args.warm_start],
+                          "extrap2": "3 u_n - 3 u_(n-1) + u_(n-2) (lower orders for the first three steps)",
+                          "prev": "previous solution", "zero": "zero"}[warm_mode()],
            "precond": args.precond + (" (library choice: multigrid V-cycle for this grid)" if args.precond == "auto" else ""),
            "cells": 512 * 512, "l2": "flushed before every timed step (512 MB write)",
            "parallelism": "replicas" if ws > 1 else "single"}

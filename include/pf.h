@@ -50,7 +50,7 @@ enum {
 };
 
 enum { PF_FP64 = 0, PF_MIXED = 1 };            /* device storage / arithmetic */
-enum { PF_WS_ZERO = 0, PF_WS_PREV = 1, PF_WS_LEARNED = 2, PF_WS_EXTRAP = 3 };   /* CG initial guess */
+enum { PF_WS_ZERO = 0, PF_WS_PREV = 1, PF_WS_LEARNED = 2, PF_WS_EXTRAP = 3, PF_WS_EXTRAP2 = 4 };   /* CG guess */
 enum { PF_HOST = 0, PF_DEVICE = 1 };           /* where caller arrays live    */
 enum { PF_PC_AUTO = 0, PF_PC_JACOBI = 1, PF_PC_MG = 2 };   /* CG preconditioner      */
 
@@ -79,9 +79,11 @@ typedef struct {
     int precision;      /* PF_FP64 or PF_MIXED                                          */
     int mechanics;      /* 0: skip the solve (coupling terms zero)                      */
     int plasticity;     /* 0: elastic, 1: J2 radial return                              */
-    int warm_start;     /* PF_WS_ZERO, PF_WS_PREV, PF_WS_LEARNED (see pf_attach_unet) or
-                           PF_WS_EXTRAP: 2 u_n - u_{n-1} (u and the mean strain), from
-                           the third step after pf_set_fields on (before: PF_WS_PREV)  */
+    int warm_start;     /* PF_WS_ZERO, PF_WS_PREV, PF_WS_LEARNED (see pf_attach_unet),
+                           PF_WS_EXTRAP: 2 u_n - u_{n-1} (u and the mean strain) from the
+                           third step after pf_set_fields on (before: PF_WS_PREV), or
+                           PF_WS_EXTRAP2: 3 u_n - 3 u_{n-1} + u_{n-2} from the fourth
+                           step on (before: the lower orders)                          */
     int cg_maxit;       /* CG iteration cap per step (> 0)                              */
     double cg_rtol;     /* stop when ||r||_2 <= cg_rtol ||b||_2                         */
     double dt;          /* time step; <= 0 selects 0.2 x the stable limit               */

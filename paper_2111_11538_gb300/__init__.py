@@ -17,7 +17,7 @@ import numpy as np
 
 from . import native
 from .native import (PF_DEVICE, PF_FP64, PF_HOST, PF_MIXED, PF_OK, PF_PC_AUTO, PF_PC_JACOBI, PF_PC_MG,
-                     PF_WS_EXTRAP, PF_WS_LEARNED, PF_WS_PREV, PF_WS_ZERO,
+                     PF_WS_EXTRAP, PF_WS_EXTRAP2, PF_WS_LEARNED, PF_WS_PREV, PF_WS_ZERO,
                      STATUS_NAMES, pf_config, pf_diag, pf_fields, pf_params)
 
 __all__ = ["Simulation", "Batch", "PFError", "make_config", "native"]
@@ -49,7 +49,7 @@ def make_config(shape, prm, precision="fp64", mechanics=None, plasticity=None, w
     c.plasticity = int(prm.get("plasticity", 0) if plasticity is None else plasticity)
     ws = prm.get("warm_start", 1) if warm_start is None else warm_start
     c.warm_start = {"zero": PF_WS_ZERO, "prev": PF_WS_PREV, "learned": PF_WS_LEARNED,
-                    "extrap": PF_WS_EXTRAP}.get(ws, ws)
+                    "extrap": PF_WS_EXTRAP, "extrap2": PF_WS_EXTRAP2}.get(ws, ws)
     c.cg_rtol = float(prm.get("cg_rtol", 1e-10) if cg_rtol is None else cg_rtol)
     c.cg_maxit = int(prm.get("cg_maxit", 20000) if cg_maxit is None else cg_maxit)
     c.dt = float(prm.get("dt", 0.0) if dt is None else dt)

@@ -925,44 +925,54 @@ __global__ void k_net_guess(long long N, const float *y, const int *mode, double
 
 static __global__ void k_net_mode_clear(int *mode) { *mode = 0; }
 
-// Extrapolated initial guess of the solve (PF_WS_EXTRAP): with x_n the last
-// solution and h = x_{n-1} the one before it, the guess is 2 x_n - x_{n-1}
-// (linear in time); h then takes x_n.  *count (reset by pf_set_fields) is
-// the number of guesses formed since: the first two only record (the state
-// set by the caller is not a solution of a previous step).  In the mixed
-// method the FP64 copy x64 is the solve's initial guess and u follows it.
+// Extrapolated initial guess of the solve (PF_WS_EXTRAP, order 1;
+// PF_WS_EXTRAP2, order 2): with x_n the last solution and h0 = x_{n-1},
+// h1 = x_{n-2} the ones before it, the guess is 2 x_n - x_{n-1} (linear in
+// time) or 3 x_n - 3 x_{n-1} + x_{n-2} (quadratic); the history then shifts
+// by one.  *count (reset by pf_set_fields) is the number of guesses formed
+// since: the state set by the caller is not a solution of a previous step,
+// so a guess of order k needs count >= k + 1, and lower orders are used
+// while the history fills.  In the mixed method the FP64 copy x64 is the
+// solve's initial guess and u follows it.  h1 may be null (order 1).
 template <typename T, int D>
-__global__ void k_extrap(long long N, const int *count, T *u0, T *u1, T *u2, double *x0, double *x1, double *x2,
-                         double *h0, double *h1, double *h2)
+__global__ void k_extrap(long long N, const int *count, int order, T *u0, T *u1, T *u2, double *x0, double *x1,
+                         double *x2, double *h00, double *h01, double *h02, double *h10, double *h11, double *h12)
 {
-    const bool ext = *count >= 2;
+    const int cnt = *count;
+    const int ord = order >= 2 && cnt >= 3 ? 2 : (cnt >= 2 ? 1 : 0);
     T *u[3] = {u0, u1, u2};
-    double *x[3] = {x0, x1, x2}, *hh[3] = {h0, h1, h2};
+    double *x[3] = {x0, x1, x2}, *h0[3] = {h00, h01, h02}, *h1[3] = {h10, h11, h12};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int d = 0; d < D; d++) {
             const double xn = x[d] ? x[d][c] : (double)u[d][c];
-            if (ext) {
-                const double g = 2.0 * xn - hh[d][c];
+            const double x1v = h0[d][c];
+            if (ord > 0) {
+                const double g = ord == 2 ? 3.0 * (xn - x1v) + h1[d][c] : 2.0 * xn - x1v;
                 if (x[d]) x[d][c] = g;
                 u[d][c] = (T)g;
             }
-            hh[d][c] = xn;
+            if (h1[d]) h1[d][c] = x1v;
+            h0[d][c] = xn;
         }
     }
 }
 
-// The mean strain's part of the extrapolated guess, and the count.
-static __global__ void k_extrap_tail(int *count, double *E, double *Eh, int nv)
+// The mean strain's part of the extrapolated guess (Eh: [0, 6) the
+// previous, [6, 12) the one before), and the count.
+static __global__ void k_extrap_tail(int *count, int order, double *E, double *Eh, int nv)
 {
     if (threadIdx.x != 0) return;
-    const bool ext = *count >= 2;
+    const int cnt = *count;
+    const int ord = order >= 2 && cnt >= 3 ? 2 : (cnt >= 2 ? 1 : 0);
     for (int v = 0; v < nv; v++) {
-        const double en = E[v];
-        if (ext) E[v] = 2.0 * en - Eh[v];
+        const double en = E[v], e1 = Eh[v];
+        if (ord == 2) E[v] = 3.0 * (en - e1) + Eh[6 + v];
+        else if (ord == 1) E[v] = 2.0 * en - e1;
+        Eh[6 + v] = e1;
         Eh[v] = en;
     }
-    if (*count < 2) *count = *count + 1;
+    if (cnt < 3) *count = cnt + 1;
 }
 
 // Self-test of the bounded wait: one thread waits on a generation word that

@@ -226,7 +226,7 @@ struct pf_handle {
     int *net_mode = nullptr;            // 1: first step after pf_set_fields (no guess), 0: guess
     // extrapolated warm start (PF_WS_EXTRAP): the previous solution (FP64),
     // the previous mean strain, and the number of guesses since set_fields
-    double *ext_hist[3] = {};
+    double *ext_hist[2][3] = {};       // [0]: x_{n-1}, [1]: x_{n-2} (order 2 only)
     double *ext_E = nullptr;
     int *ext_count = nullptr;
     std::vector<void *> net_allocs;
@@ -726,16 +726,18 @@ int launch_step(pf_handle *h, cudaStream_t s, int k)
         h->mark_begin(PF_K_SETUP, s);
         k_setup<T, D><<<h->cell_grid, 256, 0, s>>>(cj);
         h->mark_end(s);
-        if (h->cfg.warm_start == PF_WS_EXTRAP) {
+        if (h->cfg.warm_start == PF_WS_EXTRAP || h->cfg.warm_start == PF_WS_EXTRAP2) {
+            const int order = h->cfg.warm_start == PF_WS_EXTRAP2 ? 2 : 1;
             h->mark_begin(PF_K_WARM, s);
             for (pf_handle *m : instances(h)) {
                 const long long N = m->P.N;
                 T *u[3] = {(T *)m->u[0], (T *)m->u[1], (T *)m->u[2]};
                 double *x[3] = {m->refine ? m->x64[0] : nullptr, m->refine ? m->x64[1] : nullptr,
                                 m->refine ? m->x64[2] : nullptr};
-                k_extrap<T, D><<<grid_for(m, N), 256, 0, s>>>(N, m->ext_count, u[0], u[1], u[2], x[0], x[1], x[2],
-                                                             m->ext_hist[0], m->ext_hist[1], m->ext_hist[2]);
-                k_extrap_tail<<<1, 32, 0, s>>>(m->ext_count, reinterpret_cast<double *>(m->sc), m->ext_E,
+                double *const *h0 = m->ext_hist[0], *const *h1 = m->ext_hist[1];
+                k_extrap<T, D><<<grid_for(m, N), 256, 0, s>>>(N, m->ext_count, order, u[0], u[1], u[2], x[0], x[1],
+                                                             x[2], h0[0], h0[1], h0[2], h1[0], h1[1], h1[2]);
+                k_extrap_tail<<<1, 32, 0, s>>>(m->ext_count, order, reinterpret_cast<double *>(m->sc), m->ext_E,
                                                D == 2 ? 3 : 6);       // Scalars::E is the first member
             }
             h->mark_end(s);
@@ -1017,9 +1019,11 @@ int alloc_fields(pf_handle *h)
         }
         PF_TRY(h->alloc(&h->result, sizeof(double) * 32));
         PF_TRY(h->alloc(&h->diag, b));
-        if (h->cfg.warm_start == PF_WS_EXTRAP) {
-            for (int d = 0; d < D; d++) PF_TRY(h->alloc(&h->ext_hist[d], sizeof(double) * (size_t)N));
-            PF_TRY(h->alloc(&h->ext_E, sizeof(double) * 6));
+        if (h->cfg.warm_start == PF_WS_EXTRAP || h->cfg.warm_start == PF_WS_EXTRAP2) {
+            const int nh = h->cfg.warm_start == PF_WS_EXTRAP2 ? 2 : 1;
+            for (int k = 0; k < nh; k++)
+                for (int d = 0; d < D; d++) PF_TRY(h->alloc(&h->ext_hist[k][d], sizeof(double) * (size_t)N));
+            PF_TRY(h->alloc(&h->ext_E, sizeof(double) * 12));
             PF_TRY(h->alloc(&h->ext_count, sizeof(int)));
             PF_TRY(h->cuda(cudaMemset(h->ext_count, 0, sizeof(int)), "extrapolation count"));
         }
@@ -1081,7 +1085,7 @@ int create_one(const pf_config *cfg, pf_handle **out, std::string &err)
     if (c.nx < 2 || c.ny < 2 || (c.ndim == 3 && c.nz < 2)) { err = "grid sizes must be >= 2"; return PF_EINVAL; }
     if (c.precision != PF_FP64 && c.precision != PF_MIXED) { err = "precision must be PF_FP64 or PF_MIXED"; return PF_EINVAL; }
     if (c.warm_start != PF_WS_ZERO && c.warm_start != PF_WS_PREV && c.warm_start != PF_WS_LEARNED &&
-        c.warm_start != PF_WS_EXTRAP) {
+        c.warm_start != PF_WS_EXTRAP && c.warm_start != PF_WS_EXTRAP2) {
         err = "warm_start must be PF_WS_ZERO, PF_WS_PREV or PF_WS_LEARNED";
         return PF_EINVAL;
     }

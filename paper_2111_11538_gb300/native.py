@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOTCONV, PF_ENONFINITE, PF_ETIMEOUT, PF_ESTATE = range(8)
 PF_FP64, PF_MIXED = 0, 1
-PF_WS_ZERO, PF_WS_PREV, PF_WS_LEARNED, PF_WS_EXTRAP = 0, 1, 2, 3
+PF_WS_ZERO, PF_WS_PREV, PF_WS_LEARNED, PF_WS_EXTRAP, PF_WS_EXTRAP2 = 0, 1, 2, 3, 4
 PF_PC_AUTO, PF_PC_JACOBI, PF_PC_MG = 0, 1, 2
 PF_HOST, PF_DEVICE = 0, 1
 

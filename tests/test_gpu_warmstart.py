@@ -69,16 +69,18 @@ def test_trained_network_predicts_the_displacement_rate():
     assert err < 0.8, err
 
 
+@pytest.mark.parametrize("mode", ["extrap", "extrap2"])
 @pytest.mark.parametrize("precision,rtol,tol", [("fp64", 1e-10, 1e-9), ("mixed", 1e-8, 1e-5)])
-def test_extrapolated_guess(precision, rtol, tol):
-    """PF_WS_EXTRAP (2 u_n - u_{n-1} from the third step on) solves to the
+def test_extrapolated_guess(mode, precision, rtol, tol):
+    """PF_WS_EXTRAP (2 u_n - u_{n-1} from the third step on) and
+    PF_WS_EXTRAP2 (3 u_n - 3 u_{n-1} + u_{n-2} from the fourth) solve to the
     same tolerance as the previous-step guess, and once the history exists
-    its solves need fewer iterations."""
+    their solves need fewer iterations."""
     shape = (64, 64)
     f = inputs.core_shell(shape, 20.0, 4.0)
     prm = workloads.params(plasticity=1, sigma_Y=0.004, H_hard=0.01, cg_rtol=rtol, prestress=0.01)
     out = {}
-    for warm in ("prev", "extrap"):
+    for warm in ("prev", mode):
         sim = Simulation(shape, dict(prm, warm_start=warm), precision=precision)
         sim.set_fields(f)
         sim.step(8)
@@ -86,7 +88,7 @@ def test_extrapolated_guess(precision, rtol, tol):
         sim.step(12)
         out[warm] = (sim.get_fields(), sim.diagnostics()["cg_iters_total"] - its0)
         sim.close()
-    (gp, ip), (ge, ie) = out["prev"], out["extrap"]
+    (gp, ip), (ge, ie) = out["prev"], out[mode]
     for k in ("phi_f", "phi_w", "xO", "xH", "xW"):
         assert rel(ge[k], gp[k]) < tol, (k, rel(ge[k], gp[k]))
     assert rel(ge["sigma"], gp["sigma"]) < 1e3 * tol
