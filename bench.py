@@ -49,7 +49,7 @@ MG_INIT_WORDS = 28
 # DRAM bytes per k_pcg launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of the current kernel on this workload
 # (profiles/k_pcg_mg_coreshell512_mixed.md); None where not captured.
-PCG_TRAFFIC = {"mg": 10.05e6 + 1.31e6, "jacobi": None}
+PCG_TRAFFIC = {"mg": 10.05e6 + 1.32e6, "jacobi": None}
 # Algorithmic bytes per cell of the fused explicit update (k_fused): theta,
 # phi_g, x_O, x_H, x_H2O, tr eps_e, |dev eps_e|^2, mobility read, the 1-byte
 # supply mask read, theta, x_O, x_H, x_H2O written.

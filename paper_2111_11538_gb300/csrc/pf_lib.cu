@@ -384,11 +384,11 @@ double element_bound(double nu, int d)
 // The device descriptor is written once (the arrays never move).
 // Smoothing steps per level: one on the finest (its sweeps are the
 // expensive ones, and a second step there does not lower the iteration
-// count), two on the other grid levels, three on the block-run levels
-// (cheap: shared memory, no grid barrier); the coarsest solve takes
-// MG_CSTEPS (>= 3: its last sweep is then a Chebyshev step, whose epilogue
-// applies the final pointwise step).
-constexpr int MG_DEG_FINE = 1, MG_DEG_GRID = 2, MG_DEG_BLOCK = 3, MG_CSTEPS = 8;
+// count), two on the other levels (measured on GB300 at 512^2: three on the
+// shared-memory levels made a step slower, 1.30 vs 1.14 ms); the coarsest
+// solve takes MG_CSTEPS (>= 3: its last sweep is then a Chebyshev step,
+// whose epilogue applies the final pointwise step; 6 was no faster).
+constexpr int MG_DEG_FINE = 1, MG_DEG_GRID = 2, MG_DEG_BLOCK = 2, MG_CSTEPS = 8;
 static_assert(MG_CSTEPS >= 3 && MG_CSTEPS < MG_MAX_STEPS && MG_DEG_BLOCK + 1 < MG_MAX_STEPS, "multigrid step counts");
 
 // Levels of the multigrid hierarchy of an nx x ny grid.
