@@ -178,3 +178,48 @@ def test_dt_stable_bench_set(orc):
     # diffusion binds: dx^2 / (2 d D_max) with D_max = 1
     assert abs(orc.dt_stable((16, 16), prm) - 0.25) < 1e-15
     assert abs(orc.dt_stable((8, 8, 8), prm) - 1.0 / 6.0) < 1e-15
+
+
+def _strained_energy(orc, x, E, omega, xf, xw):
+    """The one-dimensional strain-coupled ferrite/wuestite energy of Sec. 4.2.2:
+    a quadratic elastic term (1/2) E Omega^2 x^2 plus f_f below x_f, f_w above
+    x_w, and the two blended by h((x - x_f)/(x_w - x_f)) between them."""
+    if x <= xf:
+        chem = orc.f(0, x)
+    elif x <= xw:
+        t = orc.h((x - xf) / (xw - xf))
+        chem = orc.f(0, x) * (1.0 - t) + orc.f(1, x) * t
+    else:
+        chem = orc.f(1, x)
+    return 0.5 * E * omega * omega * x * x + chem
+
+
+def _minima(orc, E, omega, xf=0.01, xw=0.571):
+    xs = np.linspace(0.0, 1.0, 4001)
+    y = np.array([_strained_energy(orc, x, E, omega, xf, xw) for x in xs])
+    inner = np.nonzero((y[1:-1] < y[:-2]) & (y[1:-1] < y[2:]))[0] + 1
+    return xs[inner]
+
+
+def test_volume_change_turns_double_well_into_single_well(orc):
+    """Sec. 4.2.2 and Sec. 5: the strain-coupled energy keeps two wells for
+    volume changes up to about 25 % and has one well above that (40 % and
+    60 % are named).  With the printed polynomials, h and the printed
+    (x_f, x_w) = (0.01, 0.571) this holds for E = 2200 in units of
+    R theta / V_mol; the literal 220 GPa / 0.661 GPa = 333 keeps two wells
+    up to 60 %, so the paper's figure is read as plotted with the larger
+    value.  A reversed blend or a wrong power of Omega moves the threshold."""
+    for omega in (0.0, 0.1, 0.2, 0.25):
+        mins = _minima(orc, 2200.0, omega)
+        assert len(mins) == 2, (omega, mins)
+        # one well on the ferrite side, one on the wuestite side
+        assert mins[0] < 0.15 and mins[1] > 0.4
+    for omega in (0.3, 0.4, 0.6):
+        mins = _minima(orc, 2200.0, omega)
+        assert len(mins) == 1 and mins[0] < 0.1, (omega, mins)
+    # the literal modulus does not reproduce the single well
+    assert len(_minima(orc, 333.0, 0.6)) == 2
+    # without strain the wuestite-side well is the minimum of the printed
+    # quadratic f_w (above x_w, so unblended): x = 213.460 / (2 * 173.263)
+    m0 = _minima(orc, 2200.0, 0.0)
+    assert abs(m0[1] - 213.460 / (2 * 173.263)) < 2.5e-4
