@@ -181,7 +181,7 @@ def test_dt_stable_bench_set(orc):
 
 
 def _strained_energy(orc, x, E, omega, xf, xw):
-    """The one-dimensional strain-coupled ferrite/wuestite energy of Sec. 4.2.2:
+    """The one-dimensional strain-coupled ferrite/wuestite energy of Sec. 4.2.1:
     a quadratic elastic term (1/2) E Omega^2 x^2 plus f_f below x_f, f_w above
     x_w, and the two blended by h((x - x_f)/(x_w - x_f)) between them."""
     if x <= xf:
@@ -202,7 +202,7 @@ def _minima(orc, E, omega, xf=0.01, xw=0.571):
 
 
 def test_volume_change_turns_double_well_into_single_well(orc):
-    """Sec. 4.2.2 and Sec. 5: the strain-coupled energy keeps two wells for
+    """Sec. 4.2.1 and Sec. 5: the strain-coupled energy keeps two wells for
     volume changes up to about 25 % and has one well above that (40 % and
     60 % are named).  With the printed polynomials, h and the printed
     (x_f, x_w) = (0.01, 0.571) this holds for E = 2200 in units of
