@@ -341,3 +341,41 @@ def test_j2_plane_strain_plastic_strain_trace_free(orc):
     ep = s.f["eps_p"].reshape(-1, 4)
     assert s.f["alpha"].max() > 0.0
     assert np.abs(ep[:, 0] + ep[:, 1] + ep[:, 2]).max() < 1e-15
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_j2_uniaxial_strain_ramp(orc, ndim):
+    """Monotonic uniaxial strain (eps_xx = e, every other component held at
+    zero; in 2D plane strain supplies eps_zz = 0): the mean stress stays the
+    elastic K e, the plastic strain is deviatoric along (2, -1, -1)/sqrt(6),
+    and after yield the von Mises stress sqrt(3/2)|s| = sigma_xx - sigma_yy
+    equals sigma_Y + H alpha (Sec. 2.3 J2 relations, small-strain form).
+    Shear alone never exercises the trace split; this path does."""
+    sy, H = 0.01, 0.05
+    prm = workloads.params(plasticity=1, sigma_Y=sy, H_hard=H, eig0=0.0)
+    shape = (2,) * ndim
+    f = {"phi_f": np.zeros(shape), "phi_w": np.ones(shape), "xO": np.zeros(shape),
+         "xH": np.zeros(shape), "xW": np.zeros(shape)}
+    s = orc.Sim(f, prm)
+    E, nu = 1.0, 0.3
+    K, G = E / (3 * (1 - 2 * nu)), E / (2 * (1 + nu))
+    r23 = np.sqrt(2.0 / 3.0)
+    npl = 4 if ndim == 2 else 6
+    for e in np.linspace(0.0, 0.05, 26):
+        s.f["Ebar"][:] = 0.0
+        s.f["Ebar"][0] = e
+        orc.return_map(s)
+        a = max(0.0, (2 * G * e * r23 - r23 * sy) / (2 * G + r23 * H))
+        assert abs(s.f["alpha"].ravel()[0] - a) < 1e-13
+        sig = s.f["sigma"].reshape(-1, npl)[0]
+        sxx, syy, szz = sig[0], sig[1], sig[2]
+        assert abs((sxx + syy + szz) / 3.0 - K * e) < 1e-13
+        assert abs(sxx - (K * e + 2 * G * (2.0 * e / 3.0 - 2.0 * a / np.sqrt(6.0)))) < 1e-13
+        assert abs(syy - szz) < 1e-14
+        ep = s.f["eps_p"].reshape(-1, npl)[0]
+        assert abs(ep[0] - 2.0 * a / np.sqrt(6.0)) < 1e-14
+        assert abs(ep[1] + a / np.sqrt(6.0)) < 1e-14 and abs(ep[2] + a / np.sqrt(6.0)) < 1e-14
+        if a > 0.0:
+            assert abs((sxx - syy) - (sy + H * a)) < 1e-13
+        else:
+            assert sxx - syy <= sy + 1e-15
