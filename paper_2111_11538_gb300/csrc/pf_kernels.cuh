@@ -654,8 +654,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && D == 2) ? 3 : 2) k_fus
 
 // ---------------------------------------------------------------------------
 // K1 in 2D by column strips (k_fused_cm): the same arithmetic as k_fused,
-// without shared memory.  Warp w of the job walks strips of 32 lanes x
-// strip_rows rows; lane L holds column x0 - 1 + L (x0 = 30 * strip column),
+// without shared memory.  Each warp walks one strip of 32 lanes over a
+// block's range of rows; lane L holds column x0 - 1 + L (x0 = 30 * strip column),
 // so lanes 1..30 are the strip's output columns and lanes 0 and 31 its halo.
 // Every lane evaluates mu_O, M_O and the diffusivities of its own column in
 // a three-row register window (x_O at the lane's left/right from shuffles,
@@ -721,20 +721,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fused_cm(const 
     const int nx = sJ.P.nx, ny = sJ.P.ny;
     const int bid = (int)blockIdx.x - sJ.block0, nbk = sJ.nblocks;
     const int lane = threadIdx.x & 31;
-    const int gw = bid * (blockDim.x >> 5) + (threadIdx.x >> 5), W = nbk * (blockDim.x >> 5);
-    // the (strip column, row) space is cut into W equal contiguous chunks,
-    // one per warp; a chunk that crosses a strip column is two segments
+    const int WB = blockDim.x >> 5, wib = threadIdx.x >> 5;
+    // strips are grouped WB at a time (one per warp of a block: adjacent
+    // strips share the 128-byte lines of their boundary columns, and the
+    // warps of one block read them together); the (group, row) space is
+    // cut into equal contiguous chunks, one per block, and a chunk that
+    // crosses a group is two segments
     const int nsx = (nx + 29) / 30;
-    const long long total = (long long)nsx * ny;
-    const long long per = (total + W - 1) / W;
-    long long u = (long long)gw * per;
+    const int ngx = (nsx + WB - 1) / WB;
+    const long long total = (long long)ngx * ny;
+    const long long per = (total + nbk - 1) / nbk;
+    long long u = (long long)bid * per;
     const long long uend = u + per < total ? u + per : total;
     Acc<T> acc[5];
     bool bad = false;
     while (u < uend) {
-        const int sxi = (int)(u / ny), j0 = (int)(u % ny);
+        const int gxi = (int)(u / ny), j0 = (int)(u % ny);
         const int j1 = (int)((ny - j0) < (uend - u) ? ny : j0 + (uend - u));
         u += j1 - j0;
+        const int sxi = gxi * WB + wib;
+        if (sxi >= nsx) continue;                                // warp-uniform
         const int x0 = sxi * 30;
         const int craw = x0 - 1 + lane;
         const int c = craw < 0 ? craw + nx : (craw >= nx ? craw - nx : craw);

@@ -619,11 +619,12 @@ int build_plan(pf_handle *h)
         long long nt = (long long)((P.nx + FX - 1) / FX) * ((P.ny + FY - 1) / FY) * (D == 3 ? (P.nz + FZ - 1) / FZ : 1);
         long long cap = (long long)h->sms * 8;
         if (D == 2) {
-            // column strips (k_fused_cm, 30 output columns each, 3 blocks of
-            // 8 warps per SM): at most one wave of resident blocks, and at
-            // least ~8 rows per warp so the window start-up stays small
-            const long long rows = (long long)((P.nx + 29) / 30) * P.ny;
-            nt = (rows + 8 * 8 - 1) / (8 * 8);
+            // column strips (k_fused_cm, 30 output columns each, groups of
+            // 8 strips per block of 8 warps, 3 blocks per SM): at most one
+            // wave of resident blocks, and at least ~8 rows per block so the
+            // window start-up stays small
+            const long long rows = (long long)(((P.nx + 29) / 30 + 7) / 8) * P.ny;
+            nt = (rows + 7) / 8;
             cap = (long long)h->sms * 3;
         }
         const int nb = (int)std::max<long long>(1, std::min<long long>(nt, cap));
