@@ -58,6 +58,15 @@
  *       stopped on ||r||_2 <= rtol ||b||_2.
  *   R8  Dirichlet cells: after each step x_H := xH_bc and x_H2O := 0, the
  *       removed water and the supplied hydrogen being counted.
+ *
+ * Pins (tests/test_oracle_*.py, no GPU): the printed CALPHAD coefficients,
+ * derivative identities, the common tangent, the strain-coupled well count,
+ * the tanh interface, exact discrete diffusion (DFT), elasticity against an
+ * independent Fourier solve and the Eshelby disk / sphere, free-energy
+ * decrease, the O + H2O and H + 2 H2O balances, the lever rule, and J2
+ * closed forms in shear and uniaxial strain.  The fully coupled step as a
+ * whole has no closed form: beyond those pins its parity is unpinned, and
+ * this file is the contract.
  */
 #include <math.h>
 #include <stdlib.h>
