@@ -7,8 +7,9 @@
  * requested step:
  *   1. mechanics: small-strain elasticity with the transformation eigenstrain
  *      (Sec. 2.2, eq. RulFloDefLocAlt, linearised) and the plastic strain,
- *      solved for the periodic displacement and the mean strain by a
- *      Jacobi-preconditioned CG on Q1 voxel elements (Sec. 2.4, div P = 0);
+ *      solved for the periodic displacement and the mean strain by CG on
+ *      Q1 voxel elements (Sec. 2.4, div P = 0), preconditioned by a
+ *      geometric-multigrid V-cycle or the Jacobi diagonal (precond below);
  *   2. per-cell stress and J2 radial return (Sec. 2.3, eq. PlaTwoJ;
  *      Sec. 2.4, eq. RulFloPla);
  *   3. explicit Euler update of the solid order parameter and of the oxygen,

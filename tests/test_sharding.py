@@ -14,9 +14,9 @@ import torch.multiprocessing as mp
 from paper_2111_11538_gb300 import inputs, sharding
 
 
-def _costs():
+def _costs(precond="mg"):
     desc = inputs.batch_instances(64, 4)
-    return [sharding.instance_cost((d["n"], d["n"])) for d in desc]
+    return [sharding.instance_cost((d["n"], d["n"]), precond) for d in desc]
 
 
 def _worker(rank, world, port, q):
@@ -52,8 +52,9 @@ def test_two_ranks_shard_the_batch():
     assert max(works) <= 1.1 * (sum(works) / 2)   # balanced
 
 
-def test_shard_properties():
-    costs = _costs()
+@pytest.mark.parametrize("precond", ["mg", "jacobi"])
+def test_shard_properties(precond):
+    costs = _costs(precond)
     for world in (1, 3, 8):
         parts = sharding.shard(costs, world)
         assert sorted(i for p in parts for i in p) == list(range(64))
@@ -61,3 +62,5 @@ def test_shard_properties():
         assert max(loads) <= max(costs) + sum(costs) / world
     with pytest.raises(ValueError):
         sharding.shard(costs, 0)
+    with pytest.raises(ValueError):
+        sharding.instance_cost((8, 8), "cg")
