@@ -61,7 +61,8 @@
  *
  * Pins (tests/test_oracle_*.py, no GPU): the printed CALPHAD coefficients,
  * derivative identities, the common tangent, the strain-coupled well count,
- * the tanh interface, exact discrete diffusion (DFT), elasticity against an
+ * the tanh interface, exact discrete diffusion (DFT) of hydrogen and, in one
+ * phase, of oxygen with its gradient-energy term, elasticity against an
  * independent Fourier solve and the Eshelby disk / sphere, free-energy
  * decrease, the O + H2O and H + 2 H2O balances, the lever rule, and J2
  * closed forms in shear and uniaxial strain.  The fully coupled step as a

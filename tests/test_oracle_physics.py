@@ -379,3 +379,43 @@ def test_j2_uniaxial_strain_ramp(orc, ndim):
             assert abs((sxx - syy) - (sy + H * a)) < 1e-13
         else:
             assert sxx - syy <= sy + 1e-15
+
+
+@pytest.mark.parametrize("phase,shape", [("wuestite", (40, 48)), ("gas", (40, 48)), ("wuestite", (10, 12, 14))])
+def test_oxygen_single_phase_exact(orc, phase, shape):
+    """In one phase with a quadratic chemical energy (wuestite: 173.263 x^2
+    + ..., gas: 1000 x^2, Sec. 3.1) the oxygen relation with the un-reduced
+    flux j_O = -M_O grad mu_O, mu_O = c f'(x_O) - kappa_O Lap x_O and
+    M_O = D_O / (c f'') (R3) is linear: x_t = D_O Lap x - (D_O kappa_O /
+    (2 a c)) Lap^2 x.  Explicit Euler then scales every DFT mode by
+    (1 - dt (D_O lambda + D_O kappa_O lambda^2 / (2 a c)))^n exactly.  A
+    dropped gradient-energy term, a mobility without the 1/f'' factor or
+    a sign error in either fails this."""
+    a = {"wuestite": 173.263, "gas": 1000.0}[phase]
+    kappa = 0.5
+    rng = np.random.default_rng(7)
+    if phase == "wuestite":
+        pf, pw = np.zeros(shape), np.ones(shape)
+    else:
+        pf, pw = np.zeros(shape), np.zeros(shape)
+    x0 = 0.3 + 0.02 * rng.standard_normal(shape)
+    f = {"phi_f": pf, "phi_w": pw, "xO": x0.copy(), "xH": np.zeros(shape), "xW": np.zeros(shape),
+         "mask": np.zeros(shape, np.uint8)}
+    prm = workloads.params(k_for=0.0, mechanics=0, kappa_O=kappa, D_O_s=0.05, D_O_g=0.5)
+    s = orc.Sim(f, prm)
+    D = prm["D_O_s"] if phase == "wuestite" else prm["D_O_g"]
+    c = prm["c_chem"]
+    n = 300
+    s.step(n)
+    k = [2 * np.pi * np.fft.fftfreq(m) for m in shape]
+    lam = sum(2.0 - 2.0 * np.cos(g) for g in np.meshgrid(*k, indexing="ij"))
+    amp = 1.0 - s.dt * (D * lam + D * kappa * lam ** 2 / (2.0 * a * c))
+    assert np.abs(amp[lam > 0]).max() < 1.0          # the oracle's dt is stable here
+    # the gradient-energy term is not negligible at the shortest wavelengths
+    assert (kappa * lam.max() / (2.0 * a * c)) > 0.1
+    ref = np.real(np.fft.ifftn(np.fft.fftn(x0) * amp ** n))
+    assert np.abs(s.f["xO"] - ref).max() < 1e-12
+    # the solid order parameter does not move in a single phase
+    assert np.abs(s.phi_f).max() == 0.0
+    # the field moved by far more than the tolerance, so the pin is not vacuous
+    assert np.abs(s.f["xO"] - x0).max() > 1e-3
