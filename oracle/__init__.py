@@ -77,6 +77,8 @@ def lib():
         l.or_mechanics.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(State)]
         l.or_fields_update.restype = None
         l.or_fields_update.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(State)]
+        l.or_rates.restype = None
+        l.or_rates.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(State), _DP]
         l.or_return_map.restype = None
         l.or_return_map.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(State)]
         l.or_free_energy.restype = ctypes.c_double
@@ -195,6 +197,12 @@ class Sim:
 
     def fields_update(self):
         lib().or_fields_update(ctypes.byref(self.p), ctypes.byref(self.s))
+
+    def rates(self):
+        """d/dt of (theta, x_O, x_H, x_H2O) at the current fields, shape (4, N)."""
+        out = np.zeros(4 * self.N)
+        lib().or_rates(ctypes.byref(self.p), ctypes.byref(self.s), _dp(out))
+        return out.reshape(4, self.N)
 
     def free_energy(self):
         return lib().or_free_energy(ctypes.byref(self.p), ctypes.byref(self.s))

@@ -724,14 +724,13 @@ double or_local_energy(const or_params *p, double th, double pg, double xO, doub
 }
 
 /*
- * Explicit Euler update of (theta, x_O, x_H, x_H2O) by the field relations
- * (FieRelDRI) with the coupling scalars already in s->trE / devE2, followed by
- * the Dirichlet reset (R8).
+ * Right-hand sides of the field relations (FieRelDRI) at the current state,
+ * with the coupling scalars already in s->trE / devE2: rate[0..N) = d theta/dt,
+ * rate[N..2N) = d x_O/dt, rate[2N..3N) = d x_H/dt, rate[3N..4N) = d x_H2O/dt.
  */
-void or_fields_update(const or_params *p, or_state *s)
+void or_rates(const or_params *p, const or_state *s, double *rate)
 {
     long N = ncell(p);
-    double dt = p->dt;
     double *lt = malloc(sizeof(double) * N), *lx = malloc(sizeof(double) * N);
     double *mu = malloc(sizeof(double) * N), *MO = malloc(sizeof(double) * N);
     double *DH = malloc(sizeof(double) * N), *DW = malloc(sizeof(double) * N);
@@ -761,16 +760,32 @@ void or_fields_update(const or_params *p, or_state *s)
         double th = s->theta[c], pg = s->phig[c];
         /* delta psi / delta theta = local force - 2 eps Lap(theta) */
         double dpsi = theta_force(p, th, pg, s->xO[c], s->trE[c], s->devE2[c]) - 2.0 * p->eps_phi * lt[c];
-        double rate = -0.5 * p->L * s->mob[c] * dpsi;
         double r = or_m(pg) * p->k_for * s->xO[c] * s->xH[c];   /* (EmpModRea), (forward-k) */
         if (s->xW[c] >= 1.0) r = 0.0;                            /* Sec. 4.3 */
-        s->theta[c] = th + dt * rate;
-        double nxo = s->xO[c] + dt * (dxo[c] - r);
-        double nxh = s->xH[c] + dt * (dxh[c] - 2.0 * r);
-        double nxw = s->xW[c] + dt * (dxw[c] + r);
-        s->xO[c] = nxo;
-        s->xH[c] = nxh;
-        s->xW[c] = nxw;
+        rate[c] = -0.5 * p->L * s->mob[c] * dpsi;
+        rate[N + c] = dxo[c] - r;
+        rate[2 * N + c] = dxh[c] - 2.0 * r;
+        rate[3 * N + c] = dxw[c] + r;
+    }
+    free(lt); free(lx); free(mu); free(MO); free(DH); free(DW); free(dxo); free(dxh); free(dxw);
+}
+
+/*
+ * Explicit Euler update of (theta, x_O, x_H, x_H2O) by the field relations
+ * (FieRelDRI) with the coupling scalars already in s->trE / devE2, followed by
+ * the Dirichlet reset (R8).
+ */
+void or_fields_update(const or_params *p, or_state *s)
+{
+    long N = ncell(p);
+    double dt = p->dt;
+    double *rate = malloc(sizeof(double) * 4 * N);
+    or_rates(p, s, rate);
+    for (long c = 0; c < N; c++) {
+        s->theta[c] = s->theta[c] + dt * rate[c];
+        s->xO[c] = s->xO[c] + dt * rate[N + c];
+        s->xH[c] = s->xH[c] + dt * rate[2 * N + c];
+        s->xW[c] = s->xW[c] + dt * rate[3 * N + c];
     }
     for (long c = 0; c < N; c++) {
         if (s->mask && s->mask[c]) {
@@ -780,7 +795,7 @@ void or_fields_update(const or_params *p, or_state *s)
             s->xW[c] = 0.0;
         }
     }
-    free(lt); free(lx); free(mu); free(MO); free(DH); free(DW); free(dxo); free(dxh); free(dxw);
+    free(rate);
 }
 
 /* One or more full coupled steps (R6).  Returns the last CG iteration count. */
