@@ -28,8 +28,11 @@ where the paper leaves the details to its finite-element package:
 
 Newton's method with the Jacobian built column by column from central
 differences of R and a dense linear solve; it stops when the largest
-residual entry is at most ``tol``.  Dense means small grids only
-(4N x 4N, N cells).
+residual entry is at most ``tol``, or when an update moves no entry by more
+than ``tol`` relative to the largest field value (the residual has then
+reached its rounding floor: at the paper's diffusivities dt R carries
+terms ~1e5 times the fields).  Dense means small grids only (4N x 4N,
+N cells).
 
 Pins (tests/test_oracle_implicit.py): exact DFT solutions in the linear
 cases (hydrogen diffusion, single-phase oxygen with its gradient-energy
@@ -74,8 +77,9 @@ def _jacobian(sim, y, dt, fixed):
 def be_step(sim, dt, tol=1e-13, maxit=30):
     """Advance an ``oracle.Sim`` by one backward-Euler step of length dt.
 
-    Returns the number of Newton iterations.  Raises RuntimeError if the
-    residual does not fall below ``tol`` within ``maxit`` iterations.
+    Returns the number of Newton iterations.  Raises RuntimeError (and
+    leaves the fields at y_n) if neither stopping rule holds within
+    ``maxit`` iterations.
     """
     sim.mechanics()                                   # S1: at y_n
     N = sim.N
@@ -94,15 +98,18 @@ def be_step(sim, dt, tol=1e-13, maxit=30):
 
     y = y0.copy()
     y[fixed] = held[fixed]
+    moved = np.inf
     for it in range(maxit + 1):
         F = residual(y)
-        if np.abs(F).max() <= tol:
+        if np.abs(F).max() <= tol or moved <= tol * max(1.0, np.abs(y).max()):
             break
         if it == maxit:
             _set_state(sim, y0)
             raise RuntimeError("backward-Euler Newton iteration did not converge "
                                "(residual %.3e)" % np.abs(F).max())
-        y = y - np.linalg.solve(_jacobian(sim, y, dt, fixed), F)
+        delta = np.linalg.solve(_jacobian(sim, y, dt, fixed), F)
+        y = y - delta
+        moved = np.abs(delta).max()
     R = _rates(sim, y)                                # S3: balances of the held cells
     w_free = y0[3 * N:] + dt * R[3 * N:]
     h_free = y0[2 * N:3 * N] + dt * R[2 * N:3 * N]

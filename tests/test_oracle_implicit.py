@@ -176,3 +176,26 @@ def test_be_allen_cahn_energy_decreases_at_large_steps(orc, be):
     se = orc.Sim(f, prm, dt=dt)
     se.step(8)
     assert se.f["theta"].min() < -1e-3 or se.f["theta"].max() > 1.0 + 1e-3
+
+
+def test_be_paper_scaled_parameters(orc, be):
+    """With the diffusivities and reaction rate of the paper's Table 1
+    (workloads.paper_params) explicit Euler needs dt ~ 7.5e-8 (gas
+    diffusion); backward Euler takes steps of 0.05 and 0.5, six to seven
+    orders larger, and keeps both balances with the supply cells."""
+    prm = workloads.paper_params(cg_rtol=1e-10)
+    f = _coreshell((14, 14))
+    s = orc.Sim(f, prm)
+    assert abs(s.dt - 0.2 / (2 * 2 * prm["D_O_g"])) < 1e-3 * s.dt
+    a0 = s.sums()
+    for dt in (0.05, 0.05, 0.5):
+        be.be_step(s, dt)
+    a1 = s.sums()
+    o0, o1 = a0[0] + a0[2], a1[0] + a1[2] + s.removedW
+    h0 = a0[1] + 2 * a0[2]
+    h1 = a1[1] + 2 * a1[2] + 2 * s.removedW - s.suppliedH
+    assert abs(o1 - o0) < 1e-12 * o0
+    assert abs(h1 - h0) < 1e-11 * h0
+    for k in ("theta", "xO", "xH", "xW"):
+        assert np.isfinite(s.f[k]).all()
+    assert s.f["xH"].min() > -1e-9 and a1[2] > 0.0
