@@ -1,0 +1,183 @@
+"""Finite-strain elastic equilibrium with the transformation deformation
+(test infrastructure).
+
+Only tests/, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py`` may
+import this module; it shares no code with the CUDA library.
+
+Sec. 2.2 of the paper: the residual deformation F_R = F_T F_P with
+F_T = d_T^(1/3) I and d_T = 1 - h(phi_f) Omega_f (RulFloDefLocAlt); the
+elastic energy per reference volume psi_ela = d_T sum_a h(phi_a) phi_a(F_E)
+with F_E = (grad chi) F_R^-1 (DenEneFreElaPha, DenEneFreBulEla); and the
+neo-Hooke phase energy phi_a(F_E) = K_a/4 (J_E^2 - 1 - 2 ln J_E)
++ G_a/2 (|uni F_E|^2 - 3), uni A = A / det(A)^(1/3) (DenEneFreIntElaPha).
+Mechanical equilibrium Div P = 0 (Sec. 2.4, FieRelDRI) is the stationarity
+of the total elastic energy.
+
+Readings (listed in the design notes as F1-F6):
+  F1  Elastic part only: F_P = I (the multiplicative J2 flow comes later).
+  F2  P = d psi_ela / d(grad chi), the derivative of the printed energy,
+      whose linearisation at F = I has K_a and G_a as the bulk and shear
+      moduli that Table 1 names.  The printed first Piola stress (StsRelMod)
+      is twice this derivative; the energy is taken as the authority.
+  F3  h(phi_a) -> the phase weights W_a of R2; d_T = 1 - W_f Omega.
+  F4  2D is plane strain: F_33 = 1.
+  F5  grad chi = Fbar + grad u on the periodic box; the mean deformation
+      gradient Fbar is symmetric (no macroscopic rotation), and the
+      symmetric part of the mean first Piola stress equals -prestress I.
+  F6  Q1 voxel elements, 2 x 2 Gauss points, nodes at cell corners (node
+      i + nx j is the corner shared by cells (i-1..i, j-1..j)); the rigid
+      translation is fixed by u = 0 at node 0.
+The solution is found by Newton's method on the residual (analytic P,
+Jacobian by central differences, dense solve), with the transformation
+applied in ``nload`` equal increments of Omega; it stops when the largest
+residual entry is at most ``tol``.  Small grids only.
+
+Pins (tests/test_oracle_finite_strain.py): P against central differences of
+the energy, frame indifference, the small-strain moduli, the homogeneous
+transformation and uniaxial-stress states against one-dimensional closed
+forms, the small-strain oracle as Omega -> 0.
+"""
+import numpy as np
+
+_GA, _GB = 0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)
+
+
+def h(x):
+    return x ** 3 * (6.0 * x * x - 15.0 * x + 10.0)
+
+
+def weights(theta, phig):
+    """W_f, W_w, W_g of R2 (each the shape of theta)."""
+    hg, ht = h(phig), h(theta)
+    return (1.0 - hg) * ht, (1.0 - hg) * (1.0 - ht), hg
+
+
+def psi(F, K, G, dT):
+    """Elastic energy per reference volume at deformation gradient F
+    (..., 3, 3), mixture moduli K, G (sum of W_a K_a, W_a G_a) and d_T."""
+    s = dT ** (-1.0 / 3.0)
+    FE = s[..., None, None] * F if np.ndim(s) else s * F
+    JE = np.linalg.det(FE)
+    I1 = np.einsum("...ij,...ij->...", FE, FE)
+    return dT * (0.25 * K * (JE * JE - 1.0 - 2.0 * np.log(JE)) + 0.5 * G * (JE ** (-2.0 / 3.0) * I1 - 3.0))
+
+
+def piola(F, K, G, dT):
+    """First Piola stress d psi / d F (F2), same shapes as psi."""
+    s = np.asarray(dT ** (-1.0 / 3.0))
+    FE = s[..., None, None] * F
+    JE = np.linalg.det(FE)
+    I1 = np.einsum("...ij,...ij->...", FE, FE)
+    FEiT = np.swapaxes(np.linalg.inv(FE), -1, -2)
+    dphi = (0.5 * K * (JE * JE - 1.0))[..., None, None] * FEiT \
+        + (G * JE ** (-2.0 / 3.0))[..., None, None] * (FE - (I1 / 3.0)[..., None, None] * FEiT)
+    return (dT * s)[..., None, None] * dphi
+
+
+def _shape_grads():
+    """dN[g, a, k]: derivative along x_k of local shape function a at Gauss
+    point g (bit 0 of a and g: x offset, bit 1: y offset)."""
+    dN = np.zeros((4, 4, 2))
+    for g in range(4):
+        xi = [_GB if (g >> l) & 1 else _GA for l in range(2)]
+        for a in range(4):
+            for k in range(2):
+                v = 1.0
+                for l in range(2):
+                    bit = (a >> l) & 1
+                    if l == k:
+                        v *= 1.0 if bit else -1.0
+                    else:
+                        v *= xi[l] if bit else 1.0 - xi[l]
+                dN[g, a, k] = v
+    return dN
+
+
+class Problem:
+    """Periodic 2D plane-strain box: cell fields theta, phig (ny, nx), phase
+    moduli from (E_s, nu, E_g_ratio) as in the small-strain oracle, and the
+    prescribed symmetric part of the mean first Piola stress: -prestress I,
+    or ``pbar`` (2 x 2, symmetric) when given."""
+
+    def __init__(self, theta, phig, prm, omega, prestress=0.0, pbar=None):
+        self.shape = theta.shape
+        ny, nx = self.shape
+        self.N = nx * ny
+        Wf, Ww, Wg = weights(np.asarray(theta, float).ravel(), np.asarray(phig, float).ravel())
+        nu = prm["nu"]
+        Es, Eg = prm["E_s"], prm["E_s"] * prm["E_g_ratio"]
+        Ks, Gs = Es / (3 * (1 - 2 * nu)), Es / (2 * (1 + nu))
+        Kg, Gg = Eg / (3 * (1 - 2 * nu)), Eg / (2 * (1 + nu))
+        self.K = (Wf + Ww) * Ks + Wg * Kg
+        self.G = (Wf + Ww) * Gs + Wg * Gg
+        self.Wf = Wf
+        self.omega = omega
+        self.pbar = -prestress * np.eye(2) if pbar is None else np.asarray(pbar, float)
+        self.dN = _shape_grads()
+        j, i = np.divmod(np.arange(self.N), nx)
+        self.nodes = np.stack([((i + (a & 1)) % nx) + nx * ((j + ((a >> 1) & 1)) % ny) for a in range(4)], axis=1)
+
+    def dT(self, omega):
+        return 1.0 - self.Wf * omega
+
+    def unpack(self, z):
+        u = np.zeros((self.N, 2))
+        u[1:] = z[:-3].reshape(-1, 2)
+        a, b, c = z[-3:]
+        return u, np.array([[a, c], [c, b]])
+
+    def gradients(self, z):
+        """Deformation gradients (N, 4, 3, 3) at every cell's Gauss points."""
+        u, Fb = self.unpack(z)
+        ue = u[self.nodes]                                   # (N, 4 nodes, 2)
+        F2 = Fb[None, None] + np.einsum("eai,gak->egik", ue, self.dN)
+        F = np.zeros(F2.shape[:2] + (3, 3))
+        F[..., :2, :2] = F2
+        F[..., 2, 2] = 1.0
+        return F
+
+    def energy(self, z, omega):
+        F = self.gradients(z)
+        e = psi(F, self.K[:, None], self.G[:, None], self.dT(omega)[:, None])
+        _, Fb = self.unpack(z)
+        return 0.25 * e.sum() - self.N * np.sum(self.pbar * Fb)
+
+    def residual(self, z, omega):
+        """Gradient of the total energy with respect to z."""
+        F = self.gradients(z)
+        P = piola(F, self.K[:, None], self.G[:, None], self.dT(omega)[:, None])[..., :2, :2]
+        fa = 0.25 * np.einsum("egik,gak->eai", P, self.dN)    # per element node
+        fu = np.zeros((self.N, 2))
+        np.add.at(fu, self.nodes.ravel(), fa.reshape(-1, 2))
+        Ps = 0.25 * P.sum(axis=(0, 1)) - self.N * self.pbar
+        return np.concatenate([fu[1:].ravel(), [Ps[0, 0], Ps[1, 1], Ps[0, 1] + Ps[1, 0]]])
+
+    def solve(self, tol=1e-11, nload=4, maxit=40, z0=None):
+        """Equilibrium at self.omega; returns z (see unpack)."""
+        n = 2 * (self.N - 1) + 3
+        z = np.zeros(n) if z0 is None else z0.copy()
+        if z0 is None:
+            z[-3:] = (1.0, 1.0, 0.0)
+        for step in range(1, nload + 1):
+            om = self.omega * step / nload
+            for it in range(maxit + 1):
+                r = self.residual(z, om)
+                if np.abs(r).max() <= tol:
+                    break
+                if it == maxit:
+                    raise RuntimeError("finite-strain Newton did not converge (residual %.3e)" % np.abs(r).max())
+                J = np.empty((n, n))
+                for j in range(n):
+                    hj = 1e-6
+                    zp = z.copy()
+                    zp[j] += hj
+                    zm = z.copy()
+                    zm[j] -= hj
+                    J[:, j] = (self.residual(zp, om) - self.residual(zm, om)) / (2.0 * hj)
+                z = z - np.linalg.solve(J, r)
+        return z
+
+    def mean_piola(self, z):
+        F = self.gradients(z)
+        P = piola(F, self.K[:, None], self.G[:, None], self.dT(self.omega)[:, None])
+        return P.mean(axis=(0, 1))

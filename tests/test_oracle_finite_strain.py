@@ -1,0 +1,175 @@
+"""Pins of the finite-strain elastic oracle (oracle/finite_strain.py).
+
+Sec. 2.2 of the paper defines the neo-Hooke energy of the elastic part of
+the deformation and the transformation stretch d_T^(1/3).  The tests fix
+the oracle by: the stress as the derivative of that energy (central
+differences), frame indifference, the small-strain moduli K and G at F = I,
+homogeneous states (transformation under plane strain, uniaxial mean
+stress) against one-dimensional energy minimisations done independently of
+the finite-element solver, the small-strain oracle as the volume change
+goes to zero, and the mean-stress condition of the periodic box.
+"""
+import numpy as np
+import pytest
+from scipy.optimize import brentq, fsolve
+
+from paper_2111_11538_gb300 import inputs, workloads
+
+
+@pytest.fixture(scope="module")
+def fs(orc):
+    from oracle import finite_strain
+    return finite_strain
+
+
+def _rot(rng):
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))
+    return q if np.linalg.det(q) > 0 else -q
+
+
+def test_piola_is_the_energy_derivative(fs):
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        F = np.eye(3) + 0.25 * rng.standard_normal((3, 3))
+        K, G, dT = 0.5 + rng.random(), 0.2 + rng.random(), 0.6 + 0.4 * rng.random()
+        P = fs.piola(F[None], np.array([K]), np.array([G]), np.array([dT]))[0]
+        e = 1e-6
+        for i in range(3):
+            for j in range(3):
+                Fp, Fm = F.copy(), F.copy()
+                Fp[i, j] += e
+                Fm[i, j] -= e
+                fd = (fs.psi(Fp[None], K, G, np.array([dT]))[0] - fs.psi(Fm[None], K, G, np.array([dT]))[0]) / (2 * e)
+                assert abs(fd - P[i, j]) < 1e-8 * max(1.0, abs(P[i, j]))
+
+
+def test_frame_indifference(fs):
+    """psi(Q F) = psi(F) and P(Q F) = Q P(F) for rotations Q."""
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        F = np.eye(3) + 0.3 * rng.standard_normal((3, 3))
+        if np.linalg.det(F) <= 0:
+            continue
+        Q = _rot(rng)
+        args = (np.array([1.1]), np.array([0.45]), np.array([0.7]))
+        assert abs(fs.psi((Q @ F)[None], *args)[0] - fs.psi(F[None], *args)[0]) < 1e-12
+        assert np.abs(fs.piola((Q @ F)[None], *args)[0] - Q @ fs.piola(F[None], *args)[0]).max() < 1e-12
+
+
+def test_small_strain_moduli(fs):
+    """At F = I + eps H (d_T = 1): P = K tr(e) I + 2 G dev(e) + O(eps^2),
+    e = sym(eps H), i.e. K and G are the bulk and shear moduli (F2)."""
+    rng = np.random.default_rng(2)
+    K, G = 0.83, 0.38
+    for eps in (1e-3, 1e-4):
+        H = rng.standard_normal((3, 3))
+        e = eps * 0.5 * (H + H.T)
+        lin = K * np.trace(e) * np.eye(3) + 2 * G * (e - np.trace(e) / 3 * np.eye(3))
+        P = fs.piola((np.eye(3) + eps * H)[None], np.array([K]), np.array([G]), np.array([1.0]))[0]
+        assert np.abs(P - lin).max() < 10 * eps * np.abs(lin).max()
+    # the stress-free state of a cell is its transformation stretch
+    dT = 0.6
+    P = fs.piola((dT ** (1 / 3) * np.eye(3))[None], np.array([K]), np.array([G]), np.array([dT]))[0]
+    assert np.abs(P).max() < 1e-15
+
+
+def _energy_stretches(l1, l2, K, G, dT):
+    """Energy of F = diag(l1, l2, 1) written with principal stretches."""
+    s = dT ** (-1 / 3)
+    JE = s ** 3 * l1 * l2
+    I1 = s * s * (l1 * l1 + l2 * l2 + 1.0)
+    return dT * (0.25 * K * (JE ** 2 - 1 - 2 * np.log(JE)) + 0.5 * G * (JE ** (-2 / 3) * I1 - 3))
+
+
+def test_uniform_transformation_plane_strain(fs):
+    """Uniform ferrite with Omega = 0.4, no mean stress: the box contracts
+    uniformly in plane to the minimiser of the one-dimensional energy
+    psi(diag(l, l, 1)) (plane strain keeps F_33 = 1, so the state is not
+    stress-free)."""
+    prm = workloads.params()
+    pr = fs.Problem(np.ones((6, 6)), np.zeros((6, 6)), prm, 0.4)
+    z = pr.solve()
+    u, Fb = pr.unpack(z)
+    K, G = pr.K[0], pr.G[0]
+    dT = 0.6
+    e = 1e-6
+    lam = brentq(lambda l: (_energy_stretches(l + e, l + e, K, G, dT) - _energy_stretches(l - e, l - e, K, G, dT)) / (2 * e),
+                 0.6, 1.0, xtol=1e-14)
+    assert abs(Fb[0, 0] - lam) < 1e-9 and abs(Fb[1, 1] - lam) < 1e-9 and abs(Fb[0, 1]) < 1e-12
+    assert np.abs(u).max() < 1e-12
+    assert lam < 0.6 ** (1 / 3)          # more in-plane contraction than the free 3D stretch
+
+
+def test_uniaxial_mean_stress(fs):
+    """Homogeneous wuestite under a mean first Piola stress diag(p, 0):
+    F = diag(l1, l2, 1) with dpsi/dl1 = p, dpsi/dl2 = 0."""
+    prm = workloads.params()
+    p = 0.05
+    pr = fs.Problem(np.zeros((5, 6)), np.zeros((5, 6)), prm, 0.0, pbar=np.diag([p, 0.0]))
+    z = pr.solve(nload=1)
+    _, Fb = pr.unpack(z)
+    K, G = pr.K[0], pr.G[0]
+    e = 1e-6
+
+    def eqs(v):
+        l1, l2 = v
+        d1 = (_energy_stretches(l1 + e, l2, K, G, 1.0) - _energy_stretches(l1 - e, l2, K, G, 1.0)) / (2 * e)
+        d2 = (_energy_stretches(l1, l2 + e, K, G, 1.0) - _energy_stretches(l1, l2 - e, K, G, 1.0)) / (2 * e)
+        return [d1 - p, d2]
+
+    l1, l2 = fsolve(eqs, [1.05, 0.98], xtol=1e-14)
+    assert abs(Fb[0, 0] - l1) < 1e-8 and abs(Fb[1, 1] - l2) < 1e-8 and abs(Fb[0, 1]) < 1e-12
+    assert l1 > 1.0 and l2 < 1.0
+
+
+def _inclusion(n=10, radius=3.0):
+    x = np.arange(n) + 0.5 - n / 2
+    gy, gx = np.meshgrid(x, x, indexing="ij")
+    r = np.sqrt(gx ** 2 + gy ** 2)
+    return 0.5 * (1 - np.tanh((r - radius) / 1.5))        # ferrite disk in wuestite
+
+
+def test_small_strain_limit(orc, fs):
+    """As Omega -> 0 the finite-strain solution of a ferrite disk in wuestite
+    approaches the small-strain oracle with eigenstrain -Omega/3 W_f: the
+    relative difference of the displacement is O(Omega)."""
+    th = _inclusion()
+    rel = []
+    for om in (0.02, 0.01):
+        pr = fs.Problem(th, np.zeros_like(th), workloads.params(), om)
+        z = pr.solve(nload=1)
+        u, Fb = pr.unpack(z)
+        prm = workloads.params(eig0=-om / 3.0, plasticity=0, cg_rtol=1e-13, cg_maxit=100000)
+        f = {"phi_f": th, "phi_w": 1.0 - th, "xO": np.zeros_like(th), "xH": np.zeros_like(th),
+             "xW": np.zeros_like(th)}
+        s = orc.Sim(f, prm)
+        s.mechanics()
+        us = s.f["u"].reshape(-1, 2)
+        du = (u - u.mean(0)) - (us - us.mean(0))
+        rel.append(np.abs(du).max() / np.abs(us - us.mean(0)).max())
+        E = s.f["Ebar"]
+        assert abs((Fb[0, 0] - 1) - E[0]) < 0.01 * abs(E[0]) and abs((Fb[1, 1] - 1) - E[1]) < 0.01 * abs(E[1])
+    assert rel[0] < 0.05
+    assert 1.7 < rel[0] / rel[1] < 2.3, rel
+
+
+def test_core_shell_mean_stress_and_equilibrium(fs):
+    """Core-shell with gas and the full 40 % volume change: the residual
+    vanishes, the whole mean first Piola stress vanishes (its skew part is
+    not imposed: it follows from frame indifference with Fbar symmetric),
+    and the solution is a local minimum of the total energy."""
+    f = inputs.core_shell((8, 8), 2.5, 1.0, delta=1.0)
+    from oracle import split_phases
+    th, pg = split_phases(f["phi_f"], f["phi_w"])
+    pr = fs.Problem(th, pg, workloads.params(), 0.4)
+    z = pr.solve(nload=6)
+    assert np.abs(pr.residual(z, 0.4)).max() < 1e-11
+    assert np.abs(pr.mean_piola(z)[:2, :2]).max() < 1e-12
+    E0 = pr.energy(z, 0.4)
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        dz = 1e-4 * rng.standard_normal(z.size)
+        assert pr.energy(z + dz, 0.4) > E0
+    _, Fb = pr.unpack(z)
+    assert Fb[0, 0] < 1.0 and Fb[1, 1] < 1.0          # the shrinking shell pulls the box in
