@@ -27,6 +27,12 @@ Readings (listed in the design notes as F1-F6):
   F6  Q1 voxel elements, 2 x 2 Gauss points, nodes at cell corners (node
       i + nx j is the corner shared by cells (i-1..i, j-1..j)); the rigid
       translation is fixed by u = 0 at node 0.
+  F7  The plastic flow dF_P/dt = L_P F_P (RulFloPla) is integrated by
+      backward Euler with the exponential map, which keeps F_P isochoric
+      (Sec. 2.2), with the flow direction taken at the end of the step;
+      the Mandel stress follows F2 (half the printed StsRelMod form).
+      ``return_map`` is the per-point update; the equilibrium solve above
+      is still elastic (F1).
 The solution is found by Newton's method on the residual (analytic P,
 Jacobian by central differences, dense solve), with the transformation
 applied in ``nload`` equal increments of Omega; it stops when the largest
@@ -35,7 +41,10 @@ residual entry is at most ``tol``.  Small grids only.
 Pins (tests/test_oracle_finite_strain.py): P against central differences of
 the energy, frame indifference, the small-strain moduli, the homogeneous
 transformation and uniaxial-stress states against one-dimensional closed
-forms, the small-strain oracle as Omega -> 0.
+forms, the small-strain oracle as Omega -> 0; for the return map: det F_P = 1,
+the yield condition after a plastic step, elastic unloading, objectivity,
+the small-strain radial return as the strain vanishes, first-order
+convergence along a shear path.
 """
 import numpy as np
 
@@ -181,3 +190,68 @@ class Problem:
         F = self.gradients(z)
         P = piola(F, self.K[:, None], self.G[:, None], self.dT(self.omega)[:, None])
         return P.mean(axis=(0, 1))
+
+
+def mandel(C, K, G, dT):
+    """Mandel stress of the elastic right Cauchy-Green tensor C (3 x 3):
+    d_T (K/2 (det C - 1) I + G dev uni C), the F2 reading of (StsRelMod)."""
+    J2 = np.linalg.det(C)
+    u = C * J2 ** (-1.0 / 3.0)
+    return dT * (0.5 * K * (J2 - 1.0) * np.eye(3) + G * (u - np.trace(u) / 3.0 * np.eye(3)))
+
+
+def return_map(F, FP, epsP, K, G, dT, sigma_Y, H):
+    """Multiplicative J2 update of one point (Sec. 2.3 PlaTwoJ; Sec. 2.4
+    RulFloPla) for the total deformation gradient F (3 x 3), the plastic
+    deformation FP and accumulated plastic strain epsP at the start of the
+    step.  Backward Euler with the exponential map (reading F7):
+        FP_new = exp(dl N) FP,  N = dev M_new / |dev M_new|,
+        |dev M_new| = sqrt(2/3) (sigma_Y + H (epsP + dl)),  dl >= 0,
+    which keeps det FP = 1.  With isotropic elasticity the update is
+    coaxial with the trial C_E, so it is solved in its principal frame:
+    elastic log stretches e = e_trial - dl n(e) and the yield condition,
+    four equations by Newton with central-difference derivatives.
+    Returns (FP_new, epsP_new, dl, M_new)."""
+    s = dT ** (-1.0 / 3.0)
+    FE = s * F @ np.linalg.inv(FP)
+    C = FE.T @ FE
+    M = mandel(C, K, G, dT)
+    dev = M - np.trace(M) / 3.0 * np.eye(3)
+    ry = np.sqrt(2.0 / 3.0)
+    if np.linalg.norm(dev) - ry * (sigma_Y + H * epsP) <= 0.0:
+        return FP.copy(), epsP, 0.0, M
+    c, V = np.linalg.eigh(C)
+    etr = 0.5 * np.log(c)
+
+    def mand(e):
+        cc = np.exp(2.0 * e)
+        return np.diag(mandel(np.diag(cc), K, G, dT))
+
+    def eqs(v):
+        e, dl = v[:3], v[3]
+        m = mand(e)
+        dm = m - m.mean()
+        nm = np.linalg.norm(dm)
+        return np.concatenate([e - etr + dl * dm / nm, [nm - ry * (sigma_Y + H * (epsP + dl))]])
+
+    v = np.concatenate([etr, [0.0]])
+    for _ in range(60):
+        r = eqs(v)
+        if np.abs(r).max() <= 1e-14 * max(1.0, np.abs(mand(v[:3])).max()):
+            break
+        J = np.empty((4, 4))
+        for j in range(4):
+            h = 1e-7
+            vp, vm = v.copy(), v.copy()
+            vp[j] += h
+            vm[j] -= h
+            J[:, j] = (eqs(vp) - eqs(vm)) / (2.0 * h)
+        v = v - np.linalg.solve(J, r)
+    else:
+        raise RuntimeError("finite-strain return map did not converge")
+    e, dl = v[:3], v[3]
+    m = mand(e)
+    n = (m - m.mean()) / np.linalg.norm(m - m.mean())
+    FPn = V @ np.diag(np.exp(dl * n)) @ V.T @ FP
+    Mn = V @ np.diag(m) @ V.T
+    return FPn, epsP + dl, dl, Mn

@@ -173,3 +173,88 @@ def test_core_shell_mean_stress_and_equilibrium(fs):
         assert pr.energy(z + dz, 0.4) > E0
     _, Fb = pr.unpack(z)
     assert Fb[0, 0] < 1.0 and Fb[1, 1] < 1.0          # the shrinking shell pulls the box in
+
+
+_KS, _GS = 1.0 / (3 * 0.4), 1.0 / 2.6            # E = 1, nu = 0.3
+
+
+def _ydev(M):
+    return np.linalg.norm(M - np.trace(M) / 3.0 * np.eye(3))
+
+
+def test_return_map_isochoric_consistent_and_unloads_elastically(fs):
+    """After a plastic step det F_P = 1 (F_P isochoric, Sec. 2.2), the
+    Mandel stress sits on the yield surface |dev M| = sqrt(2/3)(sigma_Y +
+    H eps_P) with dl > 0 (PlaTwoJ); a step back inside the surface is
+    elastic and leaves F_P and eps_P unchanged."""
+    rng = np.random.default_rng(6)
+    sy, H = 0.01, 0.05
+    FP, ep = np.eye(3), 0.0
+    for _ in range(4):
+        F = np.eye(3) + 0.06 * rng.standard_normal((3, 3))
+        FP1, ep1, dl, M = fs.return_map(F, FP, ep, _KS, _GS, 0.8, sy, H)
+        assert abs(np.linalg.det(FP1) - 1.0) < 1e-13
+        if dl > 0.0:
+            assert abs(_ydev(M) - np.sqrt(2 / 3) * (sy + H * ep1)) < 1e-13
+            assert ep1 > ep
+        FP, ep = FP1, ep1
+    assert ep > 0.0
+    # unloading: the elastic state at the current F_P is stress-free up to d_T
+    F0 = 0.8 ** (1 / 3) * FP
+    FP2, ep2, dl2, M2 = fs.return_map(F0, FP, ep, _KS, _GS, 0.8, sy, H)
+    assert dl2 == 0.0 and ep2 == ep and np.array_equal(FP2, FP) and np.abs(M2).max() < 1e-14
+
+
+@pytest.mark.parametrize("kind", ["shear", "uniaxial"])
+def test_return_map_small_strain_limit(fs, kind):
+    """For small strains from F_P = I the multiplier approaches the
+    small-strain radial return dl = (2G |dev e| - sqrt(2/3) sigma_Y) /
+    (2G + sqrt(2/3) H); the relative difference vanishes with the strain."""
+    sy, H = 0.001, 0.05
+    errs = []
+    for g in (0.01, 0.005):
+        F = np.eye(3)
+        if kind == "shear":
+            F[0, 1] = g
+            de = g / np.sqrt(2.0)
+        else:
+            F[0, 0] = 1.0 + g
+            de = g * np.sqrt(2.0 / 3.0)
+        _, _, dl, _ = fs.return_map(F, np.eye(3), 0.0, _KS, _GS, 1.0, sy, H)
+        ref = (2 * _GS * de - np.sqrt(2 / 3) * sy) / (2 * _GS + np.sqrt(2 / 3) * H)
+        errs.append(abs(dl - ref) / ref)
+    assert errs[0] < 0.02 and errs[1] < errs[0] / 1.6, errs
+
+
+def test_return_map_is_objective(fs):
+    """A rotation superposed on the current configuration (F -> Q F) leaves
+    the plastic deformation, eps_P and the Mandel stress unchanged."""
+    rng = np.random.default_rng(8)
+    F = np.eye(3) + 0.08 * rng.standard_normal((3, 3))
+    a = fs.return_map(F, np.eye(3), 0.0, _KS, _GS, 0.9, 0.005, 0.02)
+    Q = _rot(rng)
+    b = fs.return_map(Q @ F, np.eye(3), 0.0, _KS, _GS, 0.9, 0.005, 0.02)
+    assert a[2] > 0.0 and abs(a[2] - b[2]) < 1e-13
+    assert np.abs(a[0] - b[0]).max() < 1e-12 and np.abs(a[3] - b[3]).max() < 1e-12
+
+
+def test_return_map_monotonic_shear_path(fs):
+    """Simple shear to gamma = 0.2 in increments: eps_P grows monotonically
+    on the hardening line, det F_P stays 1, and halving the increments
+    changes the end state by a first-order amount."""
+    sy, H = 0.005, 0.02
+    ends = []
+    for n in (20, 40, 80):
+        FP, ep = np.eye(3), 0.0
+        for k in range(1, n + 1):
+            F = np.eye(3)
+            F[0, 1] = 0.2 * k / n
+            FP, ep1, dl, M = fs.return_map(F, FP, ep, _KS, _GS, 1.0, sy, H)
+            assert ep1 >= ep and abs(np.linalg.det(FP) - 1.0) < 1e-12
+            if dl > 0.0:
+                assert abs(_ydev(M) - np.sqrt(2 / 3) * (sy + H * ep1)) < 1e-13
+            ep = ep1
+        ends.append(ep)
+    assert ends[0] > 0.1
+    d1, d2 = abs(ends[0] - ends[1]), abs(ends[1] - ends[2])
+    assert d2 < d1 and 1.5 < d1 / d2 < 2.6, (ends, d1 / d2)
