@@ -14,7 +14,8 @@ Mechanical equilibrium Div P = 0 (Sec. 2.4, FieRelDRI) is the stationarity
 of the total elastic energy.
 
 Readings (listed in the design notes as F1-F6):
-  F1  Elastic part only: F_P = I (the multiplicative J2 flow comes later).
+  F1  The equilibrium is solved for a given plastic deformation F_P per
+      cell (identity unless a plastic step has run, F8).
   F2  P = d psi_ela / d(grad chi), the derivative of the printed energy,
       whose linearisation at F = I has K_a and G_a as the bulk and shear
       moduli that Table 1 names.  The printed first Piola stress (StsRelMod)
@@ -31,8 +32,11 @@ Readings (listed in the design notes as F1-F6):
       backward Euler with the exponential map, which keeps F_P isochoric
       (Sec. 2.2), with the flow direction taken at the end of the step;
       the Mandel stress follows F2 (half the printed StsRelMod form).
-      ``return_map`` is the per-point update; the equilibrium solve above
-      is still elastic (F1).
+      ``return_map`` is the per-point update.
+  F8  Plasticity is staggered as the small-strain step (R6): the
+      equilibrium is solved with the plastic deformation of the step's
+      start, then each cell takes one update on its cell-centre
+      deformation (``Problem.mechanics_step``).
 The solution is found by Newton's method on the residual (analytic P,
 Jacobian by central differences, dense solve), with the transformation
 applied in ``nload`` equal increments of Omega; it stops when the largest
@@ -61,25 +65,33 @@ def weights(theta, phig):
     return (1.0 - hg) * ht, (1.0 - hg) * (1.0 - ht), hg
 
 
-def psi(F, K, G, dT):
+def psi(F, K, G, dT, FPinv=None):
     """Elastic energy per reference volume at deformation gradient F
-    (..., 3, 3), mixture moduli K, G (sum of W_a K_a, W_a G_a) and d_T."""
+    (..., 3, 3), mixture moduli K, G (sum of W_a K_a, W_a G_a), d_T and the
+    inverse plastic deformation (identity when None)."""
     s = dT ** (-1.0 / 3.0)
     FE = s[..., None, None] * F if np.ndim(s) else s * F
+    if FPinv is not None:
+        FE = FE @ FPinv
     JE = np.linalg.det(FE)
     I1 = np.einsum("...ij,...ij->...", FE, FE)
     return dT * (0.25 * K * (JE * JE - 1.0 - 2.0 * np.log(JE)) + 0.5 * G * (JE ** (-2.0 / 3.0) * I1 - 3.0))
 
 
-def piola(F, K, G, dT):
-    """First Piola stress d psi / d F (F2), same shapes as psi."""
+def piola(F, K, G, dT, FPinv=None):
+    """First Piola stress d psi / d F (F2), same shapes as psi:
+    d_T s (d phi / d F_E) F_P^-T with F_E = s F F_P^-1, s = d_T^(-1/3)."""
     s = np.asarray(dT ** (-1.0 / 3.0))
     FE = s[..., None, None] * F
+    if FPinv is not None:
+        FE = FE @ FPinv
     JE = np.linalg.det(FE)
     I1 = np.einsum("...ij,...ij->...", FE, FE)
     FEiT = np.swapaxes(np.linalg.inv(FE), -1, -2)
     dphi = (0.5 * K * (JE * JE - 1.0))[..., None, None] * FEiT \
         + (G * JE ** (-2.0 / 3.0))[..., None, None] * (FE - (I1 / 3.0)[..., None, None] * FEiT)
+    if FPinv is not None:
+        dphi = dphi @ np.swapaxes(FPinv, -1, -2)
     return (dT * s)[..., None, None] * dphi
 
 
@@ -123,6 +135,9 @@ class Problem:
         self.omega = omega
         self.pbar = -prestress * np.eye(2) if pbar is None else np.asarray(pbar, float)
         self.dN = _shape_grads()
+        self.FP = np.tile(np.eye(3), (self.N, 1, 1))      # per cell (F7, F8)
+        self.epsP = np.zeros(self.N)
+        self.sigma_Y, self.H = prm["sigma_Y"], prm["H_hard"]
         j, i = np.divmod(np.arange(self.N), nx)
         self.nodes = np.stack([((i + (a & 1)) % nx) + nx * ((j + ((a >> 1) & 1)) % ny) for a in range(4)], axis=1)
 
@@ -145,16 +160,19 @@ class Problem:
         F[..., 2, 2] = 1.0
         return F
 
+    def _fpinv(self):
+        return np.linalg.inv(self.FP)[:, None]
+
     def energy(self, z, omega):
         F = self.gradients(z)
-        e = psi(F, self.K[:, None], self.G[:, None], self.dT(omega)[:, None])
+        e = psi(F, self.K[:, None], self.G[:, None], self.dT(omega)[:, None], self._fpinv())
         _, Fb = self.unpack(z)
         return 0.25 * e.sum() - self.N * np.sum(self.pbar * Fb)
 
     def residual(self, z, omega):
         """Gradient of the total energy with respect to z."""
         F = self.gradients(z)
-        P = piola(F, self.K[:, None], self.G[:, None], self.dT(omega)[:, None])[..., :2, :2]
+        P = piola(F, self.K[:, None], self.G[:, None], self.dT(omega)[:, None], self._fpinv())[..., :2, :2]
         fa = 0.25 * np.einsum("egik,gak->eai", P, self.dN)    # per element node
         fu = np.zeros((self.N, 2))
         np.add.at(fu, self.nodes.ravel(), fa.reshape(-1, 2))
@@ -188,8 +206,31 @@ class Problem:
 
     def mean_piola(self, z):
         F = self.gradients(z)
-        P = piola(F, self.K[:, None], self.G[:, None], self.dT(self.omega)[:, None])
+        P = piola(F, self.K[:, None], self.G[:, None], self.dT(self.omega)[:, None], self._fpinv())
         return P.mean(axis=(0, 1))
+
+    def centre_gradients(self, z):
+        """Deformation gradient (N, 3, 3) at every cell centre."""
+        u, Fb = self.unpack(z)
+        dNc = np.array([[-0.5, -0.5], [0.5, -0.5], [-0.5, 0.5], [0.5, 0.5]])   # dN_a/dx_k at (1/2, 1/2)
+        F2 = Fb[None] + np.einsum("eai,ak->eik", u[self.nodes], dNc)
+        F = np.zeros((self.N, 3, 3))
+        F[:, :2, :2] = F2
+        F[:, 2, 2] = 1.0
+        return F
+
+    def mechanics_step(self, z0=None, nload=1, tol=1e-11):
+        """One staggered mechanics step (reading F8, as R6 for small strain):
+        the equilibrium with the plastic deformation of the step's start,
+        then one multiplicative J2 update per cell on the cell-centre
+        deformation.  Returns z."""
+        z = self.solve(tol=tol, nload=nload, z0=z0)
+        F = self.centre_gradients(z)
+        dT = self.dT(self.omega)
+        for c in range(self.N):
+            self.FP[c], self.epsP[c], _, _ = return_map(F[c], self.FP[c], self.epsP[c], self.K[c], self.G[c],
+                                                        dT[c], self.sigma_Y, self.H)
+        return z
 
 
 def mandel(C, K, G, dT):

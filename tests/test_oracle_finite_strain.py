@@ -258,3 +258,31 @@ def test_return_map_monotonic_shear_path(fs):
     assert ends[0] > 0.1
     d1, d2 = abs(ends[0] - ends[1]), abs(ends[1] - ends[2])
     assert d2 < d1 and 1.5 < d1 / d2 < 2.6, (ends, d1 / d2)
+
+
+def test_plastic_step_small_strain_limit(orc, fs):
+    """One staggered elasto-plastic mechanics step (F8) of a ferrite disk in
+    wuestite approaches the small-strain oracle's step (R6, eigenstrain
+    -Omega/3 W_f, the same yield stress relative to Omega): the accumulated
+    plastic strain and log F_P against eps_p differ by O(Omega)."""
+    from scipy.linalg import logm
+    th = _inclusion()
+    rel = []
+    for om in (0.02, 0.01):
+        sy, H = 1e-2 * om, 0.01
+        pr = fs.Problem(th, np.zeros_like(th), workloads.params(sigma_Y=sy, H_hard=H), om)
+        pr.mechanics_step()
+        s = orc.Sim({"phi_f": th, "phi_w": 1.0 - th, "xO": np.zeros_like(th), "xH": np.zeros_like(th),
+                     "xW": np.zeros_like(th)},
+                    workloads.params(eig0=-om / 3.0, plasticity=1, sigma_Y=sy, H_hard=H, cg_rtol=1e-13,
+                                     cg_maxit=100000))
+        s.mechanics()
+        a = s.f["alpha"].ravel()
+        ep = s.f["eps_p"].reshape(-1, 4)
+        lp = np.array([np.real(logm(F)) for F in pr.FP])
+        assert (a > 0).all() and (pr.epsP > 0).all()            # every cell yielded in both
+        assert np.abs(np.linalg.det(pr.FP) - 1.0).max() < 1e-12
+        rel.append(max(np.abs(pr.epsP - a).max() / a.max(),
+                       np.abs(lp[:, 0, 0] - ep[:, 0]).max() / np.abs(ep).max(),
+                       np.abs(lp[:, 0, 1] - ep[:, 3]).max() / np.abs(ep).max()))
+    assert rel[0] < 0.02 and 1.7 < rel[0] / rel[1] < 2.3, rel
