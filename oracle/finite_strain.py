@@ -37,6 +37,11 @@ Readings (listed in the design notes as F1-F6):
       equilibrium is solved with the plastic deformation of the step's
       start, then each cell takes one update on its cell-centre
       deformation (``Problem.mechanics_step``).
+  F9  The elastic part of the order parameter's driving force is
+      d psi_ela / d theta at fixed deformation and F_P, evaluated at each
+      cell's centre deformation after the step's plastic update (as the
+      small-strain coupling scalars, R6); ``CoupledSim`` is the explicit
+      step with that force.
 The solution is found by Newton's method on the residual (analytic P,
 Jacobian by central differences, dense solve), with the transformation
 applied in ``nload`` equal increments of Omega; it stops when the largest
@@ -124,22 +129,30 @@ class Problem:
         self.shape = theta.shape
         ny, nx = self.shape
         self.N = nx * ny
-        Wf, Ww, Wg = weights(np.asarray(theta, float).ravel(), np.asarray(phig, float).ravel())
         nu = prm["nu"]
         Es, Eg = prm["E_s"], prm["E_s"] * prm["E_g_ratio"]
-        Ks, Gs = Es / (3 * (1 - 2 * nu)), Es / (2 * (1 + nu))
-        Kg, Gg = Eg / (3 * (1 - 2 * nu)), Eg / (2 * (1 + nu))
-        self.K = (Wf + Ww) * Ks + Wg * Kg
-        self.G = (Wf + Ww) * Gs + Wg * Gg
-        self.Wf = Wf
+        self.Ks, self.Gs = Es / (3 * (1 - 2 * nu)), Es / (2 * (1 + nu))
+        self.Kg, self.Gg = Eg / (3 * (1 - 2 * nu)), Eg / (2 * (1 + nu))
+        self.set_phases(theta, phig)
         self.omega = omega
         self.pbar = -prestress * np.eye(2) if pbar is None else np.asarray(pbar, float)
         self.dN = _shape_grads()
         self.FP = np.tile(np.eye(3), (self.N, 1, 1))      # per cell (F7, F8)
         self.epsP = np.zeros(self.N)
         self.sigma_Y, self.H = prm["sigma_Y"], prm["H_hard"]
+        self.plastic = bool(prm.get("plasticity", 0))
         j, i = np.divmod(np.arange(self.N), nx)
         self.nodes = np.stack([((i + (a & 1)) % nx) + nx * ((j + ((a >> 1) & 1)) % ny) for a in range(4)], axis=1)
+
+    def moduli(self, theta, phig):
+        """Mixture K, G and the ferrite weight W_f of cells (F3)."""
+        Wf, Ww, Wg = weights(theta, phig)
+        return (Wf + Ww) * self.Ks + Wg * self.Kg, (Wf + Ww) * self.Gs + Wg * self.Gg, Wf
+
+    def set_phases(self, theta, phig):
+        self.theta = np.asarray(theta, float).ravel().copy()
+        self.phig = np.asarray(phig, float).ravel().copy()
+        self.K, self.G, self.Wf = self.moduli(self.theta, self.phig)
 
     def dT(self, omega):
         return 1.0 - self.Wf * omega
@@ -222,9 +235,11 @@ class Problem:
     def mechanics_step(self, z0=None, nload=1, tol=1e-11):
         """One staggered mechanics step (reading F8, as R6 for small strain):
         the equilibrium with the plastic deformation of the step's start,
-        then one multiplicative J2 update per cell on the cell-centre
-        deformation.  Returns z."""
+        then, with plasticity on, one multiplicative J2 update per cell on
+        the cell-centre deformation.  Returns z."""
         z = self.solve(tol=tol, nload=nload, z0=z0)
+        if not self.plastic:
+            return z
         F = self.centre_gradients(z)
         dT = self.dT(self.omega)
         for c in range(self.N):
@@ -296,3 +311,59 @@ def return_map(F, FP, epsP, K, G, dT, sigma_Y, H):
     FPn = V @ np.diag(np.exp(dl * n)) @ V.T @ FP
     Mn = V @ np.diag(m) @ V.T
     return FPn, epsP + dl, dl, Mn
+
+
+def elastic_force(pr, z, h=1e-6):
+    """d psi_ela / d theta of every cell at fixed deformation and F_P
+    (reading F9: at the cell-centre deformation, like the small-strain
+    coupling scalars), by central differences of the cell's energy
+    d_T(W_f) sum_a W_a phi_a(F_E) in theta."""
+    F = pr.centre_gradients(z)
+    FPinv = np.linalg.inv(pr.FP)
+
+    def e(th):
+        K, G, Wf = pr.moduli(th, pr.phig)
+        return psi(F, K, G, 1.0 - Wf * pr.omega, FPinv)
+
+    return (e(pr.theta + h) - e(pr.theta - h)) / (2.0 * h)
+
+
+class CoupledSim:
+    """Explicit coupled step with finite-strain mechanics (reading F9): the
+    staggered elasto-plastic mechanics step of ``Problem`` at the current
+    order parameter, then the explicit Euler update of the oracle
+    (``oracle.Sim``: transport, reaction, chemical and double-well forces
+    with its small-strain coupling scalars set to zero) with the elastic
+    part of the theta force taken from the finite-strain energy, then the
+    supply-cell reset of R8.  2D only."""
+
+    def __init__(self, fields, prm, omega, prestress=0.0, nload=4):
+        import oracle
+        self.sim = oracle.Sim(fields, dict(prm, mechanics=0))
+        self.prm = prm
+        sh = self.sim.shape
+        self.pr = Problem(self.sim.f["theta"].reshape(sh), self.sim.f["phig"].reshape(sh), prm, omega,
+                          prestress=prestress)
+        self.z = None
+        self.nload = nload
+
+    def step(self, n=1):
+        s, pr = self.sim, self.pr
+        for _ in range(n):
+            pr.set_phases(s.f["theta"], s.f["phig"])
+            self.z = pr.mechanics_step(z0=self.z, nload=self.nload if self.z is None else 1)
+            fel = elastic_force(pr, self.z).reshape(s.shape)
+            s.f["trE"][:] = 0.0
+            s.f["devE2"][:] = 0.0
+            R = s.rates()
+            dt = s.dt
+            rth = R[0].reshape(s.shape) - 0.5 * self.prm["L"] * s.f["mob"] * fel
+            s.f["theta"][:] = s.f["theta"] + dt * rth
+            for i, k in ((1, "xO"), (2, "xH"), (3, "xW")):
+                s.f[k][:] = s.f[k] + dt * R[i].reshape(s.shape)
+            xH, xW = s.f["xH"].reshape(-1), s.f["xW"].reshape(-1)
+            for c in np.nonzero(s.f["mask"].reshape(-1))[0]:       # R8, cell order
+                s.s.removedW += float(xW[c])
+                s.s.suppliedH += float(s.p.xH_bc - xH[c])
+                xH[c] = s.p.xH_bc
+                xW[c] = 0.0

@@ -270,7 +270,7 @@ def test_plastic_step_small_strain_limit(orc, fs):
     rel = []
     for om in (0.02, 0.01):
         sy, H = 1e-2 * om, 0.01
-        pr = fs.Problem(th, np.zeros_like(th), workloads.params(sigma_Y=sy, H_hard=H), om)
+        pr = fs.Problem(th, np.zeros_like(th), workloads.params(plasticity=1, sigma_Y=sy, H_hard=H), om)
         pr.mechanics_step()
         s = orc.Sim({"phi_f": th, "phi_w": 1.0 - th, "xO": np.zeros_like(th), "xH": np.zeros_like(th),
                      "xW": np.zeros_like(th)},
@@ -286,3 +286,49 @@ def test_plastic_step_small_strain_limit(orc, fs):
                        np.abs(lp[:, 0, 0] - ep[:, 0]).max() / np.abs(ep).max(),
                        np.abs(lp[:, 0, 1] - ep[:, 3]).max() / np.abs(ep).max()))
     assert rel[0] < 0.02 and 1.7 < rel[0] / rel[1] < 2.3, rel
+
+
+def test_elastic_driving_force_small_strain_limit(orc, fs):
+    """The finite-strain elastic force on the order parameter (F9) of a
+    ferrite disk approaches the elastic part of the small-strain oracle's
+    force (its eigenstrain -Omega/3 W_f and coupling scalars) with a
+    relative difference O(Omega)."""
+    th = _inclusion()
+    rel = []
+    for om in (0.02, 0.01):
+        pr = fs.Problem(th, np.zeros_like(th), workloads.params(), om)
+        z = pr.mechanics_step()
+        fel = fs.elastic_force(pr, z)
+        s = orc.Sim({"phi_f": th, "phi_w": 1.0 - th, "xO": np.zeros_like(th), "xH": np.zeros_like(th),
+                     "xW": np.zeros_like(th)},
+                    workloads.params(eig0=-om / 3.0, cg_rtol=1e-13, cg_maxit=100000))
+        s.mechanics()
+        t, s2 = s.f["trE"].ravel(), s.f["devE2"].ravel()
+        ths, pgs, xo = s.f["theta"].ravel(), s.f["phig"].ravel(), s.f["xO"].ravel()
+        small = np.array([orc.theta_force(s.p, ths[c], pgs[c], xo[c], t[c], s2[c])
+                          - orc.theta_force(s.p, ths[c], pgs[c], xo[c], 0.0, 0.0)
+                          for c in range(s.N)])
+        rel.append(np.abs(fel - small).max() / np.abs(small).max())
+    assert rel[0] < 0.05 and 1.7 < rel[0] / rel[1] < 2.3, rel
+
+
+def test_coupled_step_without_volume_change_is_the_oracle_step(orc, fs):
+    """With Omega = 0 and no prestress the finite-strain mechanics is
+    stress-free, so the coupled step equals the oracle's step with
+    mechanics off, bitwise, including the supply-cell counters."""
+    f = inputs.core_shell((12, 12), 3.0, 1.2, delta=1.5)
+    assert f["mask"].any()
+    prm = workloads.params(plasticity=1)
+    c = fs.CoupledSim(f, prm, 0.0)
+    o = orc.Sim(f, dict(prm, mechanics=0))
+    c.step(3)
+    o.step(3)
+    for k in ("theta", "xO", "xH", "xW"):
+        assert np.array_equal(c.sim.f[k], o.f[k])
+    assert c.sim.removedW == o.removedW and c.sim.suppliedH == o.suppliedH
+    # with the volume change the mechanics moves the order parameter
+    c4 = fs.CoupledSim(f, prm, 0.4)
+    c4.step(1)
+    o1 = orc.Sim(f, dict(prm, mechanics=0))
+    o1.step(1)
+    assert np.abs(c4.sim.f["theta"] - o1.f["theta"]).max() > 1e-4
