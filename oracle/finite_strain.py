@@ -21,12 +21,12 @@ Readings (listed in the design notes as F1-F6):
       moduli that Table 1 names.  The printed first Piola stress (StsRelMod)
       is twice this derivative; the energy is taken as the authority.
   F3  h(phi_a) -> the phase weights W_a of R2; d_T = 1 - W_f Omega.
-  F4  2D is plane strain: F_33 = 1.
+  F4  2D is plane strain: F_33 = 1; 3D grids use 8-node hexahedra.
   F5  grad chi = Fbar + grad u on the periodic box; the mean deformation
       gradient Fbar is symmetric (no macroscopic rotation), and the
       symmetric part of the mean first Piola stress equals -prestress I.
-  F6  Q1 voxel elements, 2 x 2 Gauss points, nodes at cell corners (node
-      i + nx j is the corner shared by cells (i-1..i, j-1..j)); the rigid
+  F6  Q1 voxel elements, 2^d Gauss points, nodes at cell corners (node
+      i + nx (j + ny k) is the lower corner of cell (i, j, k)); the rigid
       translation is fixed by u = 0 at node 0.
   F7  The plastic flow dF_P/dt = L_P F_P (RulFloPla) is integrated by
       backward Euler with the exponential map, which keeps F_P isochoric
@@ -50,7 +50,8 @@ residual entry is at most ``tol``.  Small grids only.
 Pins (tests/test_oracle_finite_strain.py): P against central differences of
 the energy, frame indifference, the small-strain moduli, the homogeneous
 transformation and uniaxial-stress states against one-dimensional closed
-forms, the small-strain oracle as Omega -> 0; for the return map: det F_P = 1,
+forms (in 3D the transformation is exactly stress-free), the small-strain
+oracle as Omega -> 0 in 2D and 3D; for the return map: det F_P = 1,
 the yield condition after a plastic step, elastic unloading, objectivity,
 the small-strain radial return as the strain vanishes, first-order
 convergence along a shear path.
@@ -100,16 +101,15 @@ def piola(F, K, G, dT, FPinv=None):
     return (dT * s)[..., None, None] * dphi
 
 
-def _shape_grads():
-    """dN[g, a, k]: derivative along x_k of local shape function a at Gauss
-    point g (bit 0 of a and g: x offset, bit 1: y offset)."""
-    dN = np.zeros((4, 4, 2))
-    for g in range(4):
-        xi = [_GB if (g >> l) & 1 else _GA for l in range(2)]
-        for a in range(4):
-            for k in range(2):
+def _shape_grads(d, points):
+    """dN[g, a, k]: derivative along x_k of local shape function a (bit l of
+    a: offset along axis l) at each local point g of ``points`` (G, d)."""
+    dN = np.zeros((len(points), 1 << d, d))
+    for g, xi in enumerate(points):
+        for a in range(1 << d):
+            for k in range(d):
                 v = 1.0
-                for l in range(2):
+                for l in range(d):
                     bit = (a >> l) & 1
                     if l == k:
                         v *= 1.0 if bit else -1.0
@@ -119,30 +119,51 @@ def _shape_grads():
     return dN
 
 
+def _gauss(d):
+    return [[_GB if (g >> l) & 1 else _GA for l in range(d)] for g in range(1 << d)]
+
+
 class Problem:
-    """Periodic 2D plane-strain box: cell fields theta, phig (ny, nx), phase
-    moduli from (E_s, nu, E_g_ratio) as in the small-strain oracle, and the
-    prescribed symmetric part of the mean first Piola stress: -prestress I,
-    or ``pbar`` (2 x 2, symmetric) when given."""
+    """Periodic box in 2D (plane strain, cell fields (ny, nx)) or 3D (cell
+    fields (nz, ny, nx)): theta and phig per cell, phase moduli from (E_s,
+    nu, E_g_ratio) as in the small-strain oracle, and the prescribed
+    symmetric part of the mean first Piola stress: -prestress I, or
+    ``pbar`` (d x d, symmetric) when given."""
 
     def __init__(self, theta, phig, prm, omega, prestress=0.0, pbar=None):
         self.shape = theta.shape
-        ny, nx = self.shape
-        self.N = nx * ny
+        self.d = d = len(self.shape)
+        self.N = int(np.prod(self.shape))
         nu = prm["nu"]
         Es, Eg = prm["E_s"], prm["E_s"] * prm["E_g_ratio"]
         self.Ks, self.Gs = Es / (3 * (1 - 2 * nu)), Es / (2 * (1 + nu))
         self.Kg, self.Gg = Eg / (3 * (1 - 2 * nu)), Eg / (2 * (1 + nu))
         self.set_phases(theta, phig)
         self.omega = omega
-        self.pbar = -prestress * np.eye(2) if pbar is None else np.asarray(pbar, float)
-        self.dN = _shape_grads()
+        self.pbar = -prestress * np.eye(d) if pbar is None else np.asarray(pbar, float)
+        self.dN = _shape_grads(d, _gauss(d))
+        self.dNc = _shape_grads(d, [[0.5] * d])[0]
+        self.w = 1.0 / (1 << d)
+        # symmetric components of Fbar in z: the diagonal, then (1,2), (0,2), (0,1) in 3D / (0,1) in 2D
+        self.sym = [(i, i) for i in range(d)] + ([(1, 2), (0, 2), (0, 1)] if d == 3 else [(0, 1)])
         self.FP = np.tile(np.eye(3), (self.N, 1, 1))      # per cell (F7, F8)
         self.epsP = np.zeros(self.N)
         self.sigma_Y, self.H = prm["sigma_Y"], prm["H_hard"]
         self.plastic = bool(prm.get("plasticity", 0))
-        j, i = np.divmod(np.arange(self.N), nx)
-        self.nodes = np.stack([((i + (a & 1)) % nx) + nx * ((j + ((a >> 1) & 1)) % ny) for a in range(4)], axis=1)
+        dims = self.shape[::-1]                           # nx, ny (, nz)
+        cell = np.arange(self.N)
+        coord = []
+        for n in dims:
+            cell, r = np.divmod(cell, n)
+            coord.append(r)
+        nodes = []
+        for a in range(1 << d):
+            idx, stride = 0, 1
+            for l, n in enumerate(dims):
+                idx = idx + stride * ((coord[l] + ((a >> l) & 1)) % n)
+                stride *= n
+            nodes.append(idx)
+        self.nodes = np.stack(nodes, axis=1)
 
     def moduli(self, theta, phig):
         """Mixture K, G and the ferrite weight W_f of cells (F3)."""
@@ -157,21 +178,30 @@ class Problem:
     def dT(self, omega):
         return 1.0 - self.Wf * omega
 
+    def nz(self):
+        """Number of unknowns: the fluctuation without node 0, then Fbar."""
+        return self.d * (self.N - 1) + len(self.sym)
+
     def unpack(self, z):
-        u = np.zeros((self.N, 2))
-        u[1:] = z[:-3].reshape(-1, 2)
-        a, b, c = z[-3:]
-        return u, np.array([[a, c], [c, b]])
+        d, m = self.d, len(self.sym)
+        u = np.zeros((self.N, d))
+        u[1:] = z[:-m].reshape(-1, d)
+        Fb = np.zeros((d, d))
+        for v, (i, j) in zip(z[-m:], self.sym):
+            Fb[i, j] = Fb[j, i] = v
+        return u, Fb
+
+    def _embed(self, Fd):
+        F = np.zeros(Fd.shape[:-2] + (3, 3))
+        F[..., :self.d, :self.d] = Fd
+        if self.d == 2:
+            F[..., 2, 2] = 1.0                            # F4
+        return F
 
     def gradients(self, z):
-        """Deformation gradients (N, 4, 3, 3) at every cell's Gauss points."""
+        """Deformation gradients (N, 2^d, 3, 3) at every cell's Gauss points."""
         u, Fb = self.unpack(z)
-        ue = u[self.nodes]                                   # (N, 4 nodes, 2)
-        F2 = Fb[None, None] + np.einsum("eai,gak->egik", ue, self.dN)
-        F = np.zeros(F2.shape[:2] + (3, 3))
-        F[..., :2, :2] = F2
-        F[..., 2, 2] = 1.0
-        return F
+        return self._embed(Fb[None, None] + np.einsum("eai,gak->egik", u[self.nodes], self.dN))
 
     def _fpinv(self):
         return np.linalg.inv(self.FP)[:, None]
@@ -180,24 +210,29 @@ class Problem:
         F = self.gradients(z)
         e = psi(F, self.K[:, None], self.G[:, None], self.dT(omega)[:, None], self._fpinv())
         _, Fb = self.unpack(z)
-        return 0.25 * e.sum() - self.N * np.sum(self.pbar * Fb)
+        return self.w * e.sum() - self.N * np.sum(self.pbar * Fb)
 
     def residual(self, z, omega):
         """Gradient of the total energy with respect to z."""
+        d = self.d
         F = self.gradients(z)
-        P = piola(F, self.K[:, None], self.G[:, None], self.dT(omega)[:, None], self._fpinv())[..., :2, :2]
-        fa = 0.25 * np.einsum("egik,gak->eai", P, self.dN)    # per element node
-        fu = np.zeros((self.N, 2))
-        np.add.at(fu, self.nodes.ravel(), fa.reshape(-1, 2))
-        Ps = 0.25 * P.sum(axis=(0, 1)) - self.N * self.pbar
-        return np.concatenate([fu[1:].ravel(), [Ps[0, 0], Ps[1, 1], Ps[0, 1] + Ps[1, 0]]])
+        P = piola(F, self.K[:, None], self.G[:, None], self.dT(omega)[:, None], self._fpinv())[..., :d, :d]
+        fa = self.w * np.einsum("egik,gak->eai", P, self.dN)   # per element node
+        fu = np.zeros((self.N, d))
+        np.add.at(fu, self.nodes.ravel(), fa.reshape(-1, d))
+        Ps = self.w * P.sum(axis=(0, 1)) - self.N * self.pbar
+        rF = [Ps[i, i] if i == j else Ps[i, j] + Ps[j, i] for i, j in self.sym]
+        return np.concatenate([fu[1:].ravel(), rF])
 
     def solve(self, tol=1e-11, nload=4, maxit=40, z0=None):
         """Equilibrium at self.omega; returns z (see unpack)."""
-        n = 2 * (self.N - 1) + 3
-        z = np.zeros(n) if z0 is None else z0.copy()
+        n = self.nz()
         if z0 is None:
-            z[-3:] = (1.0, 1.0, 0.0)
+            z = np.zeros(n)
+            m = n - len(self.sym)
+            z[m:m + self.d] = 1.0                          # Fbar = I
+        else:
+            z = z0.copy()
         for step in range(1, nload + 1):
             om = self.omega * step / nload
             for it in range(maxit + 1):
@@ -225,12 +260,7 @@ class Problem:
     def centre_gradients(self, z):
         """Deformation gradient (N, 3, 3) at every cell centre."""
         u, Fb = self.unpack(z)
-        dNc = np.array([[-0.5, -0.5], [0.5, -0.5], [-0.5, 0.5], [0.5, 0.5]])   # dN_a/dx_k at (1/2, 1/2)
-        F2 = Fb[None] + np.einsum("eai,ak->eik", u[self.nodes], dNc)
-        F = np.zeros((self.N, 3, 3))
-        F[:, :2, :2] = F2
-        F[:, 2, 2] = 1.0
-        return F
+        return self._embed(Fb[None] + np.einsum("eai,ak->eik", u[self.nodes], self.dNc))
 
     def mechanics_step(self, z0=None, nload=1, tol=1e-11):
         """One staggered mechanics step (reading F8, as R6 for small strain):
@@ -335,7 +365,7 @@ class CoupledSim:
     (``oracle.Sim``: transport, reaction, chemical and double-well forces
     with its small-strain coupling scalars set to zero) with the elastic
     part of the theta force taken from the finite-strain energy, then the
-    supply-cell reset of R8.  2D only."""
+    supply-cell reset of R8.  2D or 3D."""
 
     def __init__(self, fields, prm, omega, prestress=0.0, nload=4):
         import oracle

@@ -332,3 +332,40 @@ def test_coupled_step_without_volume_change_is_the_oracle_step(orc, fs):
     o1 = orc.Sim(f, dict(prm, mechanics=0))
     o1.step(1)
     assert np.abs(c4.sim.f["theta"] - o1.f["theta"]).max() > 1e-4
+
+
+def test_3d_uniform_transformation_is_stress_free(fs):
+    """In 3D nothing constrains the transformation: uniform ferrite with
+    Omega = 0.4 and no mean stress deforms by exactly F = d_T^(1/3) I, where
+    F_E = I and every stress vanishes."""
+    pr = fs.Problem(np.ones((3, 4, 5)), np.zeros((3, 4, 5)), workloads.params(), 0.4)
+    z = pr.solve()
+    u, Fb = pr.unpack(z)
+    assert np.abs(Fb - 0.6 ** (1 / 3) * np.eye(3)).max() < 1e-12
+    assert np.abs(u).max() < 1e-12
+    assert np.abs(pr.mean_piola(z)).max() < 1e-12
+
+
+def test_3d_small_strain_limit(orc, fs):
+    """3D: a ferrite ball in wuestite approaches the small-strain oracle
+    (eigenstrain -Omega/3 W_f) with a relative displacement difference
+    O(Omega); the mean strains agree to the same order."""
+    n = 4
+    x = np.arange(n) + 0.5 - n / 2
+    gz, gy, gx = np.meshgrid(x, x, x, indexing="ij")
+    th = 0.5 * (1 - np.tanh((np.sqrt(gx ** 2 + gy ** 2 + gz ** 2) - 1.2) / 1.0))
+    rel = []
+    for om in (0.02, 0.01):
+        pr = fs.Problem(th, np.zeros_like(th), workloads.params(), om)
+        u, Fb = pr.unpack(pr.solve(nload=1))
+        s = orc.Sim({"phi_f": th, "phi_w": 1.0 - th, "xO": np.zeros_like(th), "xH": np.zeros_like(th),
+                     "xW": np.zeros_like(th)},
+                    workloads.params(eig0=-om / 3.0, cg_rtol=1e-13, cg_maxit=100000))
+        s.mechanics()
+        us = s.f["u"].reshape(-1, 3)
+        du = (u - u.mean(0)) - (us - us.mean(0))
+        rel.append(np.abs(du).max() / np.abs(us - us.mean(0)).max())
+        E = s.f["Ebar"]
+        for k in range(3):
+            assert abs((Fb[k, k] - 1) - E[k]) < 0.02 * abs(E[k])
+    assert rel[0] < 0.05 and 1.7 < rel[0] / rel[1] < 2.3, rel
