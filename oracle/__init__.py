@@ -4,6 +4,10 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It compiles ``oracle.c`` with the host
 C compiler into ``oracle/_build/liboracle.so`` and wraps it with ctypes.  It
 shares no code with the CUDA library.
+
+Submodules: ``implicit`` (backward-Euler time step of the field relations)
+and ``finite_strain`` (neo-Hooke mechanics with the transformation stretch
+and multiplicative J2, and the coupled explicit step that uses it).
 """
 import ctypes
 import os
