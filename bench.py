@@ -538,6 +538,9 @@ def main():
                      "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
                      "traffic": PCG_TRAFFIC["mg" if mg else "jacobi"],
+                     "traffic_launch": ("ncu, first timed step's solve (cold L2, 3 refinement passes, ~15 "
+                                        "V-cycles); the solve's working set stays in L2, so its DRAM bytes "
+                                        "are first-touch and do not grow with the V-cycle count"),
                      "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
                      "algorithmic_bytes_per_launch": cg_bytes_per_launch},
         "roofline_stencil": stencil,
