@@ -369,3 +369,34 @@ def test_3d_small_strain_limit(orc, fs):
         for k in range(3):
             assert abs((Fb[k, k] - 1) - E[k]) < 0.02 * abs(E[k])
     assert rel[0] < 0.05 and 1.7 < rel[0] / rel[1] < 2.3, rel
+
+
+def test_3d_plastic_step_small_strain_limit(orc, fs):
+    """3D: one staggered elasto-plastic step of a ferrite ball approaches
+    the small-strain oracle's plastic step at O(Omega), in the accumulated
+    plastic strain and in every component of log F_P against eps_p
+    (xx, yy, zz, yz, xz, xy)."""
+    from scipy.linalg import logm
+    n = 4
+    x = np.arange(n) + 0.5 - n / 2
+    gz, gy, gx = np.meshgrid(x, x, x, indexing="ij")
+    th = 0.5 * (1 - np.tanh((np.sqrt(gx ** 2 + gy ** 2 + gz ** 2) - 1.2) / 1.0))
+    comps = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    rel = []
+    for om in (0.02, 0.01):
+        sy, H = 1e-2 * om, 0.01
+        pr = fs.Problem(th, np.zeros_like(th), workloads.params(plasticity=1, sigma_Y=sy, H_hard=H), om)
+        pr.mechanics_step()
+        s = orc.Sim({"phi_f": th, "phi_w": 1.0 - th, "xO": np.zeros_like(th), "xH": np.zeros_like(th),
+                     "xW": np.zeros_like(th)},
+                    workloads.params(eig0=-om / 3.0, plasticity=1, sigma_Y=sy, H_hard=H, cg_rtol=1e-13,
+                                     cg_maxit=100000))
+        s.mechanics()
+        a = s.f["alpha"].ravel()
+        ep = s.f["eps_p"].reshape(-1, 6)
+        lp = np.array([np.real(logm(F)) for F in pr.FP])
+        assert (a > 0).all() and (pr.epsP > 0).all()
+        r = [np.abs(pr.epsP - a).max() / a.max()]
+        r += [np.abs(lp[:, i, j] - ep[:, k]).max() / np.abs(ep).max() for k, (i, j) in enumerate(comps)]
+        rel.append(max(r))
+    assert rel[0] < 0.02 and 1.7 < rel[0] / rel[1] < 2.3, rel
