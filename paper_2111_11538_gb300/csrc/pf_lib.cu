@@ -611,7 +611,8 @@ int build_plan(pf_handle *h)
     }
     h->cell_grid = b0;
     h->njobs = n;
-    // the fused update walks tiles: up to 8 blocks per SM per instance
+    // blocks of the fused update per instance: 3D walks halo tiles (up to 8
+    // blocks per SM), 2D walks column strips (below)
     std::vector<CellJob<T, D>> fj[2] = {cj[0], cj[1]};
     int f0 = 0;
     for (int i = 0; i < n; i++) {
