@@ -99,3 +99,36 @@ def test_create_rejects_bad_precond(lib):
     cfg = make_config((8, 8, 8), workloads.params(), precond=-1)
     rc, h = native.pf_create(cfg)
     assert rc == native.PF_EINVAL and "precond" in native.pf_last_error(None)
+
+
+def _c_layout(structs):
+    """sizeof and offsetof of every field, as the C compiler lays out the
+    structs of include/*.h (compiled here with gcc, plain C)."""
+    import subprocess
+    import tempfile
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pf.h"', '#include "pf_unet.h"',
+             'int main(void) {']
+    for name, cls in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines.append('return 0; }')
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        subprocess.check_call(["gcc", "-std=c11", "-I" + INCLUDE, "-o", exe, src])
+        out = subprocess.check_output([exe], text=True)
+    return dict((k, int(v)) for k, v in (l.split() for l in out.splitlines()))
+
+
+def test_ctypes_structs_match_the_c_layout():
+    """The Python binding's ctypes records have the field names, order,
+    offsets and sizes of the C structs in the headers."""
+    structs = [("pf_params", native.pf_params), ("pf_config", native.pf_config), ("pf_fields", native.pf_fields),
+               ("pf_diag", native.pf_diag), ("pf_profile", native.pf_profile),
+               ("pf_unet_config", native.pf_unet_config)]
+    c = _c_layout(structs)
+    for name, cls in structs:
+        assert c[name] == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert c["%s.%s" % (name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
