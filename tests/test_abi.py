@@ -132,3 +132,24 @@ def test_ctypes_structs_match_the_c_layout():
         assert c[name] == ctypes.sizeof(cls), name
         for f in cls._fields_:
             assert c["%s.%s" % (name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
+
+
+def test_enum_constants_match_the_headers():
+    """Every PF_* integer constant of the binding has the header's value."""
+    import subprocess
+    import tempfile
+    names = [n for n in dir(native) if n.startswith("PF_") and isinstance(getattr(native, n), int)]
+    txt = "".join(open(os.path.join(INCLUDE, f)).read() for f in sorted(os.listdir(INCLUDE)) if f.endswith(".h"))
+    names = [n for n in names if re.search(r"\b%s\b" % n, txt)]
+    assert len(names) >= 25
+    lines = ['#include <stdio.h>', '#include "pf.h"', '#include "pf_unet.h"', 'int main(void) {']
+    lines += ['printf("%s %%lld\\n", (long long)(%s));' % (n, n) for n in names]
+    lines.append('return 0; }')
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "enums.c"), os.path.join(d, "enums")
+        open(src, "w").write("\n".join(lines))
+        subprocess.check_call(["gcc", "-std=c11", "-I" + INCLUDE, "-o", exe, src])
+        out = subprocess.check_output([exe], text=True)
+    for line in out.splitlines():
+        k, v = line.split()
+        assert getattr(native, k) == int(v), k
