@@ -134,6 +134,9 @@ typedef struct {
     int status;                     /* sticky status of the last pf_step call      */
     int precond;                    /* preconditioner in use: PF_PC_JACOBI or PF_PC_MG */
     int mg_levels;                  /* levels of the multigrid hierarchy (0: Jacobi)   */
+    double reduction_rate;          /* rate of the reduction degree over the last step,
+                                       -(sum_O,n - sum_O,n-1) / (sum_O_init dt)
+                                       (Sec. 4.2.1); 0 before the first step        */
 } pf_diag;
 
 typedef struct pf_handle pf_handle;

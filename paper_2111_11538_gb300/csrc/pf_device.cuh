@@ -80,6 +80,7 @@ struct Diag {
     int cg_last, cg_max;
     int status;
     int pad;
+    double sumO_prev;       // sum of x_O before the last update (reduction rate)
 };
 
 // ---------------------------------------------------------------------------

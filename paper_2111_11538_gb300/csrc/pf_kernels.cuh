@@ -368,6 +368,7 @@ __global__ void __launch_bounds__(256) k_update(const __grid_constant__ JobSet<C
         __shared__ double tot[6];
         last_block_sums<6>(partials, (int)nbk, tot);
         if (threadIdx.x == 0) {
+            dg->sumO_prev = dg->sumO;
             dg->sumO = tot[0]; dg->sumH = tot[1]; dg->sumW = tot[2];
             dg->removedW += tot[3];
             dg->suppliedH += tot[4];
@@ -643,6 +644,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && D == 2) ? 3 : 2) k_fus
         last_block_sums<6>(partials, (int)nbk, tot);
         if (threadIdx.x == 0) {
             Diag *dg = sJ.dg;
+            dg->sumO_prev = dg->sumO;
             dg->sumO = tot[0]; dg->sumH = tot[1]; dg->sumW = tot[2];
             dg->removedW += tot[3];
             dg->suppliedH += tot[4];
@@ -871,6 +873,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fused_cm(const 
         last_block_sums<6>(partials, nbk, tot);
         if (threadIdx.x == 0) {
             Diag *dg = sJ.dg;
+            dg->sumO_prev = dg->sumO;
             dg->sumO = tot[0]; dg->sumH = tot[1]; dg->sumW = tot[2];
             dg->removedW += tot[3];
             dg->suppliedH += tot[4];

@@ -1352,6 +1352,10 @@ int pf_get_diagnostics(pf_handle *h, pf_diag *out)
     out->removed_H2O = dg.removedW; out->supplied_H = dg.suppliedH;
     out->sum_O_init = h->sumO0;
     out->reduction_degree = h->sumO0 != 0.0 && h->steps > 0 ? 1.0 - dg.sumO / h->sumO0 : 0.0;
+    // reduction rate of the last step, -(sum x_O,n - sum x_O,n-1) / (sum x_O,init dt)
+    // (Sec. 4.2.1); before the first update the previous sum is the initial one
+    const double prevO = h->steps == 1 ? h->sumO0 : dg.sumO_prev;
+    out->reduction_rate = h->sumO0 != 0.0 && h->steps > 0 ? (prevO - dg.sumO) / (h->sumO0 * h->P.dt) : 0.0;
     out->cg_rel_residual = sc.relres;
     out->cg_iters_last = dg.cg_last;
     out->cg_iters_max = dg.cg_max;

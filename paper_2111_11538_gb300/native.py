@@ -58,7 +58,8 @@ class pf_diag(ctypes.Structure):
                 ("cg_rel_residual", ctypes.c_double), ("cg_iters_last", ctypes.c_int),
                 ("cg_iters_max", ctypes.c_int), ("cg_iters_total", ctypes.c_longlong),
                 ("steps", ctypes.c_longlong), ("dt", ctypes.c_double), ("status", ctypes.c_int),
-                ("precond", ctypes.c_int), ("mg_levels", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("mg_levels", ctypes.c_int),
+                ("reduction_rate", ctypes.c_double)]
 
 
 PF_K_SETUP, PF_K_CG, PF_K_RETURN, PF_K_UPDATE, PF_K_WARM, PF_K_NCLASS = range(6)

@@ -133,6 +133,33 @@ def test_mass_balance_fp64_sums():
     assert 0 < d["reduction_degree"] < 1
 
 
+def test_reduction_rate_telescopes():
+    """The reduction rate of Sec. 4.2.1 is the change of the reduction
+    degree over the last step divided by dt, so its sum times dt telescopes
+    to the reduction degree; a call of several steps reports its last step's
+    rate (the same as stepping one at a time)."""
+    shape = (32, 32)
+    f = inputs.core_shell(shape, 10.0, 3.0)
+    prm = workloads.params(cg_rtol=1e-8)
+    a = Simulation(shape, prm, precision="fp64")
+    a.set_fields(f)
+    assert a.diagnostics()["reduction_rate"] == 0.0
+    acc, prev = 0.0, 0.0
+    for _ in range(9):
+        a.step(1)
+        d = a.diagnostics()
+        assert d["reduction_rate"] > 0.0
+        assert abs(d["reduction_rate"] * d["dt"] - (d["reduction_degree"] - prev)) < 1e-13
+        acc += d["reduction_rate"] * d["dt"]
+        prev = d["reduction_degree"]
+    assert abs(acc - d["reduction_degree"]) < 1e-13
+    b = Simulation(shape, prm, precision="fp64")
+    b.set_fields(f)
+    b.step(6)
+    b.step(3)
+    assert b.diagnostics()["reduction_rate"] == d["reduction_rate"]
+
+
 def test_status_not_converged():
     shape = (32, 32)
     f = inputs.core_shell(shape, 10.0, 3.0)
