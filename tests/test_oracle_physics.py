@@ -50,6 +50,26 @@ def test_tanh_interface(orc, delta):
     assert np.abs(1.0 - s.phi_f - s.phi_w).max() < 1e-13
 
 
+def _interface_error(orc, delta):
+    w = 1.2379e-3
+    eps = 0.5 * delta ** 2 * w
+    nx = int(16 * delta)
+    prm = workloads.params(c_chem=0.0, k_for=0.0, mechanics=0, eps_phi=eps, w=w, **NOFLUX)
+    x = np.arange(nx) + 0.5
+    a, b = nx / 4.0, 3.0 * nx / 4.0
+    s = orc.Sim(_strip(1.0 - ((x > a) & (x < b)).astype(float)), prm)
+    s.step(int(12 * delta ** 2 / (prm["L"] * eps) / s.dt))
+    sel = np.abs(x - a) < 4 * delta
+    return np.abs(s.phi_f[0][sel] - 0.5 * (1.0 + np.tanh((x[sel] - a) / delta))).max()
+
+
+def test_tanh_interface_second_order(orc):
+    """The relaxed discrete interface converges to the tanh profile at second
+    order in dx / delta: halving dx / delta divides the error by ~4."""
+    e = [_interface_error(orc, d) for d in (2.0, 4.0, 8.0)]
+    assert all(3.5 < e[i] / e[i + 1] < 4.5 for i in range(2)), e
+
+
 def _dft_heat(u0, D, dt, n):
     """Exact discrete solution of explicit Euler for u_t = D Lap_h u, periodic."""
     k = [2 * np.pi * np.fft.fftfreq(m) for m in u0.shape]
