@@ -199,3 +199,20 @@ def test_be_paper_scaled_parameters(orc, be):
     for k in ("theta", "xO", "xH", "xW"):
         assert np.isfinite(s.f[k]).all()
     assert s.f["xH"].min() > -1e-9 and a1[2] > 0.0
+
+
+def test_be_3d_coupled_balances_with_plasticity(orc, be):
+    """3D core-shell with mechanics, J2 plasticity, reaction and supply
+    cells: backward-Euler steps keep both balances to roundoff."""
+    f = inputs.core_shell((6, 6, 6), 1.5, 0.7, delta=0.8)
+    assert f["mask"].any()
+    s = orc.Sim(f, workloads.params(cg_rtol=1e-10, plasticity=1, sigma_Y=0.002, H_hard=0.01))
+    a0 = s.sums()
+    for _ in range(2):
+        be.be_step(s, 2.0 * s.dt)
+    a1 = s.sums()
+    o0, o1 = a0[0] + a0[2], a1[0] + a1[2] + s.removedW
+    h0 = a0[1] + 2 * a0[2]
+    h1 = a1[1] + 2 * a1[2] + 2 * s.removedW - s.suppliedH
+    assert abs(o1 - o0) < 1e-12 * o0 and abs(h1 - h0) < 1e-12 * h0
+    assert s.f["alpha"].max() > 0.0 and a1[2] > 0.0
