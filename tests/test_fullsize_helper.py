@@ -1,0 +1,48 @@
+"""The full-size step checks (tests/fullsize_local.py) applied to the
+oracle's own steps: they must find nothing on the whole grid or on a
+periodic sub-box, find a change planted in one interior cell, and the
+oracle's solve must pass the residual check."""
+import numpy as np
+import pytest
+
+from fullsize_local import oracle_state, solve_residual, step_errors
+from paper_2111_11538_gb300 import inputs, workloads
+
+
+def _run(orc, shape, prm, f):
+    s = orc.Sim(f, prm)
+    s.step(3)
+    before = oracle_state(s)
+    s.step(1)
+    return before, oracle_state(s)
+
+
+@pytest.mark.parametrize("shape", [(24, 28), (10, 11, 12)])
+def test_step_checks_on_oracle_steps(orc, shape):
+    if len(shape) == 2:
+        f = inputs.core_shell(shape, 7.0, 2.5, delta=1.5)
+    else:
+        f = inputs.core_shell(shape, 3.0, 1.2, delta=1.0)
+    prm = workloads.params(plasticity=1, sigma_Y=0.002, H_hard=0.01, cg_rtol=1e-12)
+    before, after = _run(orc, shape, prm, f)
+    assert after["alpha"].max() > 0.0
+    whole = step_errors(orc, prm, before, after, f)
+    assert max(whole.values()) < 1e-12, whole
+    m = 9
+    origin = tuple(n // 3 for n in shape)
+    box = step_errors(orc, prm, before, after, f, origin=origin, m=m)
+    assert max(box.values()) < 1e-12, box
+    # the same box across the periodic seam
+    seam = step_errors(orc, prm, before, after, f, origin=tuple(n - 4 for n in shape), m=m)
+    assert max(seam.values()) < 1e-12, seam
+    if len(shape) == 2:
+        assert solve_residual(orc, prm, before, after, f) < 2e-12
+    # a change in one interior cell of the box is found
+    planted = {k: v.copy() for k, v in after.items()}
+    c = tuple(o + 4 for o in origin)
+    planted["xO"][c] += 1e-6
+    assert step_errors(orc, prm, before, planted, f, origin=origin, m=m)["xO"] > 1e-7
+    if len(shape) == 2:
+        planted = {k: v.copy() for k, v in after.items()}
+        planted["u"][c] += 1e-3
+        assert solve_residual(orc, prm, before, planted, f) > 1e-6
