@@ -52,14 +52,24 @@ def step_errors(orc, prm, before, after, static, origin=None, m=None):
     ref = {"alpha": s.f["alpha"].copy(), "eps_p": s.f["eps_p"].copy(), "sigma": s.f["sigma"].copy()}
     s.fields_update()
     ref.update({"phi_f": s.phi_f, "phi_w": s.phi_w, "xO": s.f["xO"], "xH": s.f["xH"], "xW": s.f["xW"]})
+    # The exported phi_f, phi_w do not carry the order parameter of cells
+    # with no solid (phi_g = 1); its value there enters the Laplacian of
+    # the neighbours, so the phase outputs are compared away from such cells.
+    gas = (f["phi_f"] + f["phi_w"]) == 0.0
+    near_gas = gas.copy()
+    for ax in range(nd):
+        near_gas |= np.roll(gas, 1, axis=ax) | np.roll(gas, -1, axis=ax)
     errs = {}
     for k in OUT_KEYS:
         g = cut(after[k])[inner]
         r = ref[k][inner]
+        if k in ("phi_f", "phi_w"):
+            keep = ~near_gas[inner]
+            g, r = g[keep], r[keep]
         # relative to the output's magnitude, floored at 1e-6 so that a field
         # still near zero (early water, elastic plastic strain) is held to an
         # absolute bound
-        errs[k] = float(np.abs(g - r).max() / max(np.abs(r).max(), 1e-6))
+        errs[k] = float(np.abs(g - r).max() / max(np.abs(r).max(), 1e-6)) if g.size else 0.0
     return errs
 
 
