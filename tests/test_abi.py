@@ -4,7 +4,6 @@ import ctypes
 import os
 import re
 
-import numpy as np
 import pytest
 
 from paper_2111_11538_gb300 import make_config, native, workloads
