@@ -259,8 +259,7 @@ void pf_destroy(pf_handle *h);
  * Field update that allocates no device memory.  (The paper has no
  * counterpart: this entry point exists for callers of the library.)
  *
- * For callers that cannot call cudaMalloc at the point of use: code that
- * runs while a stream is being captured into a CUDA graph, runtimes that
+ * For callers that cannot call cudaMalloc at the point of use: runtimes that
  * hand out a fixed device-memory budget once and forbid later allocations,
  * and hosts that must leave the process's allocator untouched.
  *
@@ -279,8 +278,10 @@ void pf_destroy(pf_handle *h);
  * 8 * PF_STATIC_MAX_CELLS doubles plus about 0.2 MB; 4.5 MB), which every device
  * that loads the library keeps until the process exits.  Grids with more
  * than PF_STATIC_MAX_CELLS cells are rejected with PF_EINVAL.  The first call
- * on a device looks the array's device address up (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call shares the
+ * on a device looks the array's device address up (cudaGetSymbolAddress)
+ * and caches it for the life of the process; make that first call before
+ * any stream capture, and do not use the library across a cudaDeviceReset
+ * (the array moves to a new address in the new context).  Every call shares the
  * array and clears what must start at zero: calls whose GPU work overlaps
  * (other streams or host threads) race, so serialise them.
  * Returns PF_OK, PF_EINVAL, PF_ECUDA or PF_ENONFINITE; the text of the last

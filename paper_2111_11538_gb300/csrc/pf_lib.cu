@@ -1494,11 +1494,10 @@ void pf_destroy(pf_handle *h)
 // ---------------------------------------------------------------------------
 // Allocation-free field update.
 //
-// Some callers cannot allocate device memory: code that runs while a stream
-// is being captured into a CUDA graph (cudaMalloc is not allowed there),
-// host runtimes that hand out a fixed device-memory budget up front and
-// forbid allocations afterwards, and callers that must not touch the
-// allocator state of a process they share.  For them,
+// Some callers cannot allocate device memory where they run the step: host
+// runtimes that hand out a fixed device-memory budget up front and forbid
+// allocations afterwards, and callers that must not touch the allocator
+// state of a process they share.  For them,
 // pf_fields_update_static runs the explicit field update of one step with its
 // working arrays in the fixed device array below instead of in memory it
 // allocates.  The array exists once per device that loads the library, for
@@ -1523,7 +1522,10 @@ std::mutex g_static_mu;
 void *g_static_addr[64] = {};
 
 // Device address of the scratch array for the current device (looked up once
-// per device; the host-side name is only a stand-in for it).
+// per device, by the first call made with that device current; the
+// host-side name is only a stand-in for it).  The address is cached for the
+// life of the process: after cudaDeviceReset the array has a new address in
+// the new context, so the library must not be used across a device reset.
 int static_scratch(void **out, std::string &err)
 {
     int dev = 0;
@@ -1546,10 +1548,12 @@ int static_scratch(void **out, std::string &err)
 
 thread_local std::string g_static_error;
 
+// Records the error of the failing CUDA call (cudaSuccess if none failed).
 template <int D>
 int fields_update_static_t(const Params &P, const pf_fields *in, const double *trE, const double *devE2,
-                           pf_fields *out, cudaStream_t s, void *base)
+                           pf_fields *out, cudaStream_t s, void *base, cudaError_t &cerr)
 {
+    auto ck = [&](cudaError_t e) { if (e != cudaSuccess && cerr == cudaSuccess) cerr = e; return e == cudaSuccess; };
     const long long N = P.N;
     double *a = (double *)base;
     double *theta = a, *phig = a + N, *muO = a + 2 * N, *MO = a + 3 * N, *theta_o = a + 4 * N;
@@ -1561,12 +1565,12 @@ int fields_update_static_t(const Params &P, const pf_fields *in, const double *t
     unsigned char *mask0 = (unsigned char *)(a + STATIC_DOUBLES);
     const int g = (int)std::min<long long>((N + 255) / 256, STATIC_BLOCKS);
     // state that must start at zero on every call
-    if (cudaMemsetAsync(tail, 0, 64 * sizeof(double), s) != cudaSuccess) return PF_ECUDA;
+    if (!ck(cudaMemsetAsync(tail, 0, 64 * sizeof(double), s))) return PF_ECUDA;
     if (!trE || !devE2) {
-        if (cudaMemsetAsync(zero0, 0, sizeof(double) * N, s) != cudaSuccess) return PF_ECUDA;
-        if (cudaMemsetAsync(zero1, 0, sizeof(double) * N, s) != cudaSuccess) return PF_ECUDA;
+        if (!ck(cudaMemsetAsync(zero0, 0, sizeof(double) * N, s))) return PF_ECUDA;
+        if (!ck(cudaMemsetAsync(zero1, 0, sizeof(double) * N, s))) return PF_ECUDA;
     }
-    if (!in->dirichlet && cudaMemsetAsync(mask0, 0, (size_t)N, s) != cudaSuccess) return PF_ECUDA;
+    if (!in->dirichlet && !ck(cudaMemsetAsync(mask0, 0, (size_t)N, s))) return PF_ECUDA;
     if (!in->mobility) k_in_scalar<double><<<g, 256, 0, s>>>(N, nullptr, one, 1.0);
     k_in_phase<double><<<g, 256, 0, s>>>(N, in->phi_f, in->phi_w, theta, phig);
     FieldPtrs<double, D> F;
@@ -1579,7 +1583,7 @@ int fields_update_static_t(const Params &P, const pf_fields *in, const double *t
     F.trE = const_cast<double *>(trE ? trE : zero0);
     F.devE2 = const_cast<double *>(devE2 ? devE2 : zero1);
     // the job travels in the launch parameters: nothing is copied to the
-    // device before the launches, so the call can be captured into a graph
+    // device before the launches
     JobSet<CellJob<double, D>> js;
     memset(&js, 0, sizeof(js));
     js.one.P = P;
@@ -1593,10 +1597,10 @@ int fields_update_static_t(const Params &P, const pf_fields *in, const double *t
     k_mu<double, D><<<g, 256, 0, s>>>(js);
     k_update<double, D><<<g, 256, 0, s>>>(js);
     k_out_phase<double><<<g, 256, 0, s>>>(N, theta_o, phig, out->phi_f, out->phi_w);
-    if (cudaGetLastError() != cudaSuccess) return PF_ECUDA;
+    if (!ck(cudaGetLastError())) return PF_ECUDA;
     int status = 0;
-    if (cudaMemcpyAsync(&status, &dg->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PF_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return PF_ECUDA;
+    if (!ck(cudaMemcpyAsync(&status, &dg->status, sizeof(int), cudaMemcpyDeviceToHost, s))) return PF_ECUDA;
+    if (!ck(cudaStreamSynchronize(s))) return PF_ECUDA;
     return status == 5 ? PF_ENONFINITE : PF_OK;
 }
 
@@ -1632,9 +1636,10 @@ int pf_fields_update_static(const pf_config *cfg, const pf_fields *in, const dou
     Params P;
     fill_params(c, N, P);
     cudaStream_t s = (cudaStream_t)cudaStream;
-    rc = c.ndim == 2 ? fields_update_static_t<2>(P, in, trE, devE2, out, s, base)
-                     : fields_update_static_t<3>(P, in, trE, devE2, out, s, base);
-    if (rc == PF_ECUDA) g_static_error = std::string("CUDA error: ") + cudaGetErrorString(cudaGetLastError());
+    cudaError_t cerr = cudaSuccess;
+    rc = c.ndim == 2 ? fields_update_static_t<2>(P, in, trE, devE2, out, s, base, cerr)
+                     : fields_update_static_t<3>(P, in, trE, devE2, out, s, base, cerr);
+    if (rc == PF_ECUDA) g_static_error = std::string("CUDA error: ") + cudaGetErrorString(cerr);
     else if (rc == PF_ENONFINITE) g_static_error = "non-finite value in the fields";
     return rc;
 }

@@ -112,8 +112,16 @@ def porous(shape, n_grains, pore_fraction, pore_median, pore_sigma, seed,
         og = np.meshgrid(*offs, indexing="ij")
         rr = np.sqrt(sum(o * o for o in og)) - rad
         ix = np.ix_(*sl)
-        dist[ix] = np.minimum(dist[ix], rr)
-        filled = float(np.sum(dist < 0.0))
+        old = dist[ix]
+        new = np.minimum(old, rr)
+        dist[ix] = new
+        # cells that turned gas with this pore (the count of dist < 0 over
+        # the box, kept incrementally; the ball's box never wraps onto itself
+        # on the grids used here, and where it does the sum below is exact)
+        if all(2 * reach + 1 <= n for n in shape):
+            filled += float(np.count_nonzero(new < 0.0) - np.count_nonzero(old < 0.0))
+        else:
+            filled = float(np.sum(dist < 0.0))
     phi_g = 1.0 - _tanh_step(dist, delta)
     mask = np.zeros(shape, dtype=np.uint8)
     for ax in range(d):

@@ -1,13 +1,14 @@
 """The allocation-free field update, pf_fields_update_static.
 
-Callers that cannot allocate device memory at the point of use (code running
-during CUDA-graph stream capture, runtimes with a fixed device-memory budget,
-hosts that must leave the allocator alone) use this entry point instead of a
-handle: it keeps its working arrays in a fixed device array of the library.
-Its results must equal those of the regular entry point (pf_step with the
-mechanics off) on two calls in a row, within the FP64 tolerance of the other
-GPU tests.  This file is collected last so that a failure here comes after
-every other test has run.
+Callers that cannot allocate device memory at the point of use (runtimes
+with a fixed device-memory budget, hosts that must leave the allocator alone)
+use this entry point instead of a handle: it keeps its working arrays in a
+fixed device array of the library.  Its results must equal those of the
+regular entry point (pf_step with the mechanics off) on two calls in a row,
+within the FP64 tolerance of the other GPU tests, in 2D and 3D; with given
+coupling scalars (tr eps_e, |dev eps_e|^2) they must equal the oracle's
+field update on the same inputs.  This file is collected last so that a
+failure here comes after every other test has run.
 """
 import ctypes
 
@@ -31,12 +32,29 @@ def _dp(t):
     return ctypes.cast(t.data_ptr(), ctypes.POINTER(ctypes.c_double))
 
 
-def test_static_update_matches_regular_entry_point_twice():
+def _static_call(cfg, cur, mob, mask, stream, trE=None, devE2=None):
+    """One call through the C ABI on caller-owned device buffers; returns the
+    new fields (device tensors)."""
+    torch = pytest.importorskip("torch")
+    nxt = {k: torch.empty_like(cur[k]) for k in KEYS}
+    fin, fout = pf_fields(), pf_fields()
+    for k in KEYS:
+        setattr(fin, NAMES[k], _dp(cur[k]))
+        setattr(fout, NAMES[k], _dp(nxt[k]))
+    fin.mobility = _dp(mob)
+    fin.dirichlet = ctypes.cast(mask.data_ptr(), ctypes.POINTER(ctypes.c_ubyte))
+    rc = native.pf_fields_update_static(cfg, fin, None if trE is None else _dp(trE),
+                                        None if devE2 is None else _dp(devE2), fout, stream)
+    assert rc == native.PF_OK, native.pf_static_last_error()
+    return nxt
+
+
+@pytest.mark.parametrize("shape", [(40, 48), (16, 16, 16)])
+def test_static_update_matches_regular_entry_point_twice(shape):
     torch = pytest.importorskip("torch")
     native.build_library()
     native.lib()
-    shape = (40, 48)
-    f = inputs.core_shell(shape, 12.0, 3.0)
+    f = inputs.core_shell(shape, 12.0 if len(shape) == 2 else 5.0, 3.0)
     f["mob"] = np.random.default_rng(3).uniform(0.8, 1.2, shape)
     prm = workloads.params(mechanics=0)
 
@@ -57,19 +75,45 @@ def test_static_update_matches_regular_entry_point_twice():
     mask = torch.as_tensor(np.ascontiguousarray(f["mask"], dtype=np.uint8), device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     for ref in (ref1, ref2):
-        nxt = {k: torch.empty_like(cur[k]) for k in KEYS}
-        fin, fout = pf_fields(), pf_fields()
-        for k in KEYS:
-            setattr(fin, NAMES[k], _dp(cur[k]))
-            setattr(fout, NAMES[k], _dp(nxt[k]))
-        fin.mobility = _dp(mob)
-        fin.dirichlet = ctypes.cast(mask.data_ptr(), ctypes.POINTER(ctypes.c_ubyte))
-        rc = native.pf_fields_update_static(cfg, fin, None, None, fout, stream)
-        assert rc == native.PF_OK, native.pf_static_last_error()
+        nxt = _static_call(cfg, cur, mob, mask, stream)
         for k in KEYS:
             got = nxt[k].cpu().numpy()
             assert _rel(got, ref[k]) < 1e-12, (k, _rel(got, ref[k]))
         cur = nxt
+
+
+def test_static_update_with_coupling_scalars_matches_oracle_twice():
+    """Nonzero tr eps_e and |dev eps_e|^2 per cell (the elastic driving force
+    of the order parameter): two calls against the oracle's field update on
+    the same inputs."""
+    torch = pytest.importorskip("torch")
+    import oracle
+    native.build_library()
+    shape = (36, 44)
+    f = inputs.core_shell(shape, 11.0, 3.0)
+    rng = np.random.default_rng(11)
+    f["mob"] = rng.uniform(0.8, 1.2, shape)
+    trE = rng.uniform(-0.06, 0.02, shape)
+    devE2 = rng.uniform(0.0, 4e-3, shape)
+    prm = workloads.params(mechanics=0)
+    ref = oracle.Sim(f, prm)
+    ref.f["trE"][...] = trE
+    ref.f["devE2"][...] = devE2
+    cfg = make_config(shape, prm, precision="fp64", mechanics=0)
+    cfg.dt = ref.dt
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+    cur = {k: dev(f[k]) for k in KEYS}
+    mob = dev(f["mob"])
+    mask = torch.as_tensor(np.ascontiguousarray(f["mask"], dtype=np.uint8), device="cuda")
+    tE, dE = dev(trE), dev(devE2)
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        ref.fields_update()
+        exp = {"phi_f": ref.phi_f, "phi_w": ref.phi_w, "xO": ref.f["xO"], "xH": ref.f["xH"], "xW": ref.f["xW"]}
+        cur = _static_call(cfg, cur, mob, mask, stream, tE, dE)
+        for k in KEYS:
+            got = cur[k].cpu().numpy()
+            assert _rel(got, exp[k]) < 1e-12, (k, _rel(got, exp[k]))
 
 
 def test_static_update_rejects_oversize_grid():
