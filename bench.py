@@ -1,13 +1,16 @@
 """Benchmark of the coupled phase-field step on GB300.
 
-Workload (default): 2D core-shell, 512 x 512 cells, radius 160, iron shell 32,
-J2 plasticity (sigma_Y = 0.01 E, H = 0.001 E), CG warm-started from the
-previous step.  One "step" is the whole hot path: mechanics right-hand side,
-PCG solve, J2 return, field update.  The chosen form (FP32 fields and
-operator, FP64-grade reductions) gives ``value``; the plain FP64 method is
-measured beside it on the same GPU.
+Workload (default): 3D porous microstructure, 256 x 256 x 256 cells (~500
+Voronoi grains, pore fraction 0.15, lognormal pore radii with median 6 cells
+and sigma 0.4, two supply layers on every face), J2 plasticity (sigma_Y =
+0.01 E, H = 0.001 E), CG residual 1e-8.  One "step" is the whole hot path:
+mechanics right-hand side, initial guess, PCG solve, J2 return, field
+update.  The chosen form (FP32 fields and operator, FP64-grade reductions,
+FP64 iterative refinement of the solve) gives ``value``; the plain FP64
+method is measured beside it on the same GPU and the same input.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload porous256cube|coreshell512|porous2048|batch64|stencil]
 
 Under torchrun (N > 1) every rank advances its own replica of the workload
 (the single-grid step does not shard; see the design notes) and ``value`` is
@@ -29,31 +32,34 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-steps/s, coupled PF+diffusion+mechanics, at stated FP64 error; % HBM peak"
 L2_BYTES = 129 * 1024 * 1024
 
-# Algorithmic bytes per node per PCG iteration (x, r, p read and written once,
-# diag and the two Lame parameters read once) and per node of the solve's
-# set-up (eigenstress, Lame, warm start read; residual and diagonal written).
+# Algorithmic bytes per node and PCG iteration (the minimum traffic of one
+# Jacobi-preconditioned iteration: x, r, p read and written, w / s and the
+# diagonal and the two Lame parameters read): 2D 16 words, 3D 24 words.
 CG_ITER_WORDS = {2: 16, 3: 24}
 CG_INIT_WORDS = {2: 10, 3: 15}
-# The same for the multigrid-preconditioned solve (2D), per finest-level node
-# and V-cycle iteration: finest level 29 words (CG update fused into the
-# first smoothing sweep: r, w, s, u, p, x, diag, lam, mu read; p, x, s, r and
-# the smoother's x, r, d written) + 9.5 (post-smoothing) + 8 (w = A u); each
-# coarse grid level 54.5 words per coarse node (restriction, two Chebyshev
-# steps before and after the coarse correction), 1/4 of the nodes per
-# level, so ~18 over levels 1-3; the shared-memory levels move no DRAM.
-# Set-up: one FP64 residual pass (x64, lam, mu, eigenstress read; diag, r,
-# p, s, x written) and one refinement update per launch (more passes run at
-# tight tolerances, so the figure is a lower bound).
-MG_ITER_WORDS = 64
-MG_INIT_WORDS = 28
+# The compulsory traffic of one multigrid-preconditioned iteration (a V-cycle)
+# per finest-level node, in FP32 words (model, reported beside the figure
+# above).  2D: finest level 29 (CG update fused into the first smoothing
+# sweep) + 9.5 (post-smoothing) + 8 (w = A u); coarse grid levels ~18;
+# shared-memory levels none.  3D (three components per vector): first sweep
+# 46 (r, w, s, p, x, xpost and dinv, lam, mu read; p, x, s, r, xpre, r1, d1
+# written), post-smoothing sweep 19 (xpre, r, xpost-correction, dinv, lam,
+# mu read; xpost written), w = A u 17 (xpost, r, lam, mu read; w written),
+# every coarse level 1/8 of the nodes with four sweeps of ~20 words: ~11.
+MG_ITER_WORDS = {2: 64, 3: 93}
+MG_INIT_WORDS = {2: 28, 3: 40}
 # DRAM bytes per k_pcg launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# from one ncu capture of the current kernel on this workload
-# (profiles/k_pcg_mg_coreshell512_mixed.md); None where not captured.
-PCG_TRAFFIC = {"mg": 10.05e6 + 1.32e6, "jacobi": None}
+# from one ncu capture of the current kernel on the named workload, per
+# finest node and V-cycle (so that it scales with the launch's iterations);
+# None where the current kernel has not been captured.
+PCG_TRAFFIC_PER_NODE_ITER = {"porous256cube": None}
 # Algorithmic bytes per cell of the fused explicit update (k_fused): theta,
 # phi_g, x_O, x_H, x_H2O, tr eps_e, |dev eps_e|^2, mobility read, the 1-byte
 # supply mask read, theta, x_O, x_H, x_H2O written.
 FUSED_BYTES = {"mixed": 8 * 4 + 1 + 4 * 4, "fp64": 8 * 8 + 1 + 4 * 8}
+# ncu DRAM bytes per cell of the fused update, mechanics off, None where the
+# current kernel has not been captured
+FUSED_TRAFFIC_PER_CELL = {2: None, 3: None}
 
 
 def _load_peaks():
@@ -117,36 +123,57 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-WORKLOAD = "coreshell512"
+WORKLOAD = "porous256cube"
 PRECOND = "auto"
 SHAPE = None        # grid override for the short profiling lines (--shape)
 WARM = None         # CG initial guess (--warm-start); default: the workload's "warm_start", else "extrap"
 
+DESCR = {
+    "porous256cube": "porous256cube_j2: 3D porous 256x256x256, ~500 Voronoi grains, pore fraction 0.15, "
+                     "lognormal pore radii (median 6, sigma 0.4), supply layers on every face, J2 plasticity "
+                     "sigma_Y=0.01E H=0.001E, CG rtol 1e-8",
+    "coreshell512": "coreshell512_j2: 2D core-shell 512x512, radius 160, shell 32, J2 plasticity "
+                    "sigma_Y=0.01E H=0.001E, CG rtol 1e-8",
+    "porous2048": "porous2048: 2D porous 2048x2048, ~200 Voronoi grains, pore fraction 0.2, lognormal pore radii "
+                  "(median 12, sigma 0.5), elastic, CG rtol 1e-8",
+    "coreshell64": "coreshell64: 2D core-shell 64x64, radius 20, shell 4, elastic, CG rtol 1e-10",
+}
+WARM_TEXT = {"extrap": "2 u_n - u_(n-1) (previous solution for the first two steps)",
+             "extrap2": "3 u_n - 3 u_(n-1) + u_(n-2) (lower orders for the first three steps)",
+             "prev": "previous solution", "zero": "zero", "learned": "learned (U-Net)"}
 
-def workload_fields():
+
+def workload_fields(name=None):
+    """Seeded initial fields of a workload: the bench's own (on the --shape
+    grid if given), or another workload on its own grid."""
     from paper_2111_11538_gb300 import workloads
-    return workloads.build_fields(WORKLOAD, shape=SHAPE)
+    if name is None:
+        return workloads.build_fields(WORKLOAD, shape=SHAPE)
+    return workloads.build_fields(name)
 
 
-def workload_params(precision):
+def workload_params(precision, name=None):
     from paper_2111_11538_gb300 import workloads
     # both forms solve to the workload's CG residual: the mixed form reaches
     # it through FP64 iterative refinement around its FP32 iteration
-    p = dict(workloads.WORKLOADS[WORKLOAD]["params"], precond=PRECOND)
-    p["warm_start"] = warm_mode()
+    p = dict(workloads.WORKLOADS[name or WORKLOAD]["params"], precond=PRECOND)
+    p["warm_start"] = warm_mode(name)
     return p
 
 
-def warm_mode():
+def warm_mode(name=None):
     from paper_2111_11538_gb300 import workloads
-    return WARM or workloads.WORKLOADS[WORKLOAD].get("warm_start", "extrap")
+    return WARM or workloads.WORKLOADS[name or WORKLOAD].get("warm_start", "extrap")
 
 
-def run_gpu(precision, steps, warmup, fields, profile=True, warm=None, net=None):
+def run_gpu(precision, steps, warmup, fields, profile=True, warm=None, net=None, name=None, prm=None,
+            keys=("phi_f", "phi_w", "xO", "xH", "xW", "sigma")):
+    """Advance `fields` for warmup + steps steps, timing the last `steps`
+    with CUDA events on the launch stream (the L2 flushed before each)."""
     import torch
     from paper_2111_11538_gb300 import Simulation
     shape = fields["phi_f"].shape
-    prm = workload_params(precision)
+    prm = dict(prm) if prm is not None else workload_params(precision, name)
     if warm is not None:
         prm["warm_start"] = warm
     sim = Simulation(shape, prm, precision=precision)
@@ -175,8 +202,9 @@ def run_gpu(precision, steps, warmup, fields, profile=True, warm=None, net=None)
     if prof is not None:
         prof["precond"] = "mg" if diag["precond"] == 2 else "jacobi"
         prof["mg_levels"] = diag["mg_levels"]
-    out = sim.get_fields(keys=("phi_f", "phi_w", "xO", "xH", "xW", "sigma"))
+    out = sim.get_fields(keys=keys) if keys else None
     sim.close()
+    del flush
     return total_ms, prof, diag, out
 
 
@@ -222,7 +250,8 @@ def run_batch(precision, steps, warmup, count=64, seed=4, profile=True, rank=0, 
     mine = sharding.shard([sharding.instance_cost((d["n"], d["n"])) for d in desc], world)[rank]
     desc = [desc[i] for i in mine]
     count = len(desc)
-    base = dict(workloads.WORKLOADS["batch64"]["params"], precond=PRECOND, warm_start=warm_mode())
+    base = dict(workloads.WORKLOADS["batch64"]["params"], precond=PRECOND,
+                warm_start=WARM or workloads.WORKLOADS["batch64"].get("warm_start", "extrap"))
     shapes = [(d["n"], d["n"]) for d in desc]
     prms = [dict(base, prestress=d["prestress"]) for d in desc]
     b = Batch(shapes, prms, precision=precision)
@@ -254,36 +283,38 @@ def run_batch(precision, steps, warmup, count=64, seed=4, profile=True, rank=0, 
 WARMSTART_WEIGHTS = os.path.join(ROOT, "paper_2111_11538_gb300", "data", "warmstart2d.npz")
 
 
-def learned_warm_start(steps, warmup, fields, prev_ms, prev_iters):
+def learned_warm_start(steps, warmup, fields, prev_ms, prev_iters, name):
     """The chosen form with the learned warm start (the trained 2D network
     shipped with the package) beside the default guess of the timed run
-    (the "default_guess_*" keys; WARM names it), same steps."""
+    (the "default_guess_*" keys), same steps."""
+    if len(fields["phi_f"].shape) != 2:
+        return {"status": "no trained 3D network ships with the package; the 2D network is reported on "
+                          "the 512x512 core-shell line"}
     if not os.path.exists(WARMSTART_WEIGHTS):
         return {"status": "no trained network at paper_2111_11538_gb300/data/warmstart2d.npz"}
-    import json as _json
     from paper_2111_11538_gb300 import warmstart
     net = warmstart.load(WARMSTART_WEIGHTS)
-    ms, prof, diag, _ = run_gpu("mixed", steps, warmup, fields, warm="learned", net=net)
+    ms, prof, diag, _ = run_gpu("mixed", steps, warmup, fields, warm="learned", net=net, name=name, keys=())
     info = {}
     if os.path.exists(WARMSTART_WEIGHTS + ".json"):
-        info = _json.load(open(WARMSTART_WEIGHTS + ".json"))
+        info = json.load(open(WARMSTART_WEIGHTS + ".json"))
     N = fields["phi_f"].size
     net.close()
     return {"value": N * steps / (ms / 1e3), "unit": "cell-steps/s", "ms_per_step": ms / steps,
-            "cg_iters_per_step": prof["cg_iters"] / steps, "default_guess": warm_mode(), "default_guess_cg_iters_per_step": prev_iters / steps,
-            "default_guess_ms_per_step": prev_ms / steps, "network_ms": prof["ms"]["warm"] / max(1, prof["count"]["warm"]),
-            "training": info}
+            "cg_iters_per_step": prof["cg_iters"] / steps, "default_guess": warm_mode(name),
+            "default_guess_cg_iters_per_step": prev_iters / steps,
+            "default_guess_ms_per_step": prev_ms / steps,
+            "network_ms": prof["ms"]["warm"] / max(1, prof["count"]["warm"]), "training": info}
 
 
-def stencil_roofline(steps=20, warmup=3, n=2048):
+def stencil_roofline(fields, name, steps=20, warmup=3):
     """Achieved HBM bandwidth of the fused explicit update alone: the
-    2048 x 2048 porous microstructure (inputs 4x larger than L2) stepped with
-    the mechanics off, so that every launch is k_fused; per-launch CUDA
-    events on the launch stream."""
+    workload's microstructure stepped with the mechanics off, so that every
+    launch is k_fused; per-launch CUDA events on the launch stream."""
     from paper_2111_11538_gb300 import Simulation, workloads
-    f = workloads.build_fields("porous2048", shape=(n, n))
-    sim = Simulation((n, n), workloads.params(mechanics=0), precision="mixed")
-    sim.set_fields(f)
+    shape = fields["phi_f"].shape
+    sim = Simulation(shape, workloads.params(mechanics=0), precision="mixed")
+    sim.set_fields(fields)
     sim.step(warmup)
     sim.profile(True)
     sim.step(steps)
@@ -292,33 +323,53 @@ def stencil_roofline(steps=20, warmup=3, n=2048):
     launches = prof["count"]["update"]
     ms = prof["ms"]["update"] / launches
     hbm, kind = _load_peaks()
-    algo = FUSED_BYTES["mixed"] * n * n
+    N = int(np.prod(shape))
+    algo = FUSED_BYTES["mixed"] * N
     gbs = algo / (ms / 1e3) / 1e9
-    return {"kernel": "k_fused (mu_O + explicit update)", "workload": "porous 2048x2048, mechanics off",
+    nd = len(shape)
+    tr = FUSED_TRAFFIC_PER_CELL.get(nd)
+    return {"kernel": "k_fused (mu_O + explicit update, %dD)" % nd,
+            "workload": "%s, %s cells, mechanics off" % (name, "x".join(str(v) for v in shape[::-1])),
             "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-            "traffic": None, "peak_kind": kind, "algorithmic_bytes_per_launch": algo,
-            "us_per_launch": ms * 1e3, "launches": launches}
+            "traffic": tr * N if tr else None, "peak_kind": kind + " (hbm_gbs, burst copy)",
+            "algorithmic_bytes_per_launch": algo, "us_per_launch": ms * 1e3, "launches": launches}
 
 
-def cpu_baseline(seconds=12.0):
-    """The FP64 oracle on the host (single thread) over a bounded sample of the
-    workload: the same core-shell geometry and parameters on a 128 x 128 grid
-    (radius and shell scaled by 1/4), two untimed steps, then timed steps
-    until about `seconds` have passed."""
+def oracle_sample(fields, n=20):
+    """The 256^3 workload's own fields cropped to their n^3 corner (the corner
+    holds the supply layers of three faces; the crop is periodic like the
+    whole box), for the oracle's CPU timing."""
+    return {k: np.ascontiguousarray(v[:n, :n, :n]) for k, v in fields.items()}
+
+
+def time_oracle(fields, prm, warmup, steps=None, seconds=None):
+    """Single-threaded FP64 oracle steps on the host: `warmup` untimed steps,
+    then `steps` timed steps (or timed steps until `seconds` have passed)."""
     import oracle
-    from paper_2111_11538_gb300 import workloads
-    f = workloads.build_fields("coreshell512", shape=(128, 128))
-    s = oracle.Sim(f, workloads.WORKLOADS["coreshell512"]["params"])
-    s.step(2)
-    n = 0
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
+    s = oracle.Sim(fields, prm)
+    for _ in range(warmup):
         s.step(1)
+    n, its = 0, []
+    t0 = time.perf_counter()
+    while (steps is not None and n < steps) or (steps is None and time.perf_counter() - t0 < seconds):
+        its.append(s.step(1))
         n += 1
     dt = time.perf_counter() - t0
-    return {"value": 128 * 128 * n / dt, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "128x128 core-shell (workload geometry scaled 1/4, same parameters), %d timed "
-                      "steps after 2 untimed, single-threaded FP64 C" % n}
+    return fields["phi_f"].size * n / dt, n, dt, its
+
+
+def cpu_baseline(crop, seconds=12.0):
+    """The FP64 oracle on the host (single thread) over a bounded sample of the
+    workload: its own fields cropped to the 20^3 corner, one untimed step,
+    then timed steps until about `seconds` have passed."""
+    from paper_2111_11538_gb300 import workloads
+    prm = workloads.WORKLOADS[WORKLOAD]["params"]
+    v, n, dt, its = time_oracle(crop, prm, 1, seconds=seconds)
+    edge = crop["phi_f"].shape[0]
+    return {"value": v, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d^3 corner of the 256^3 porous workload's own fields (periodic crop, same parameters, "
+                      "J2, CG rtol 1e-8), %d timed steps after 1 untimed, single-threaded FP64 C; the oracle's "
+                      "Jacobi PCG took %s iterations per step on the crop" % (edge, n, its)}
 
 
 def dist_setup():
@@ -359,17 +410,76 @@ def barrier(ws):
         dist.barrier()
 
 
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def pcg_roofline(prof, N, nd, steps, name):
+    """k_pcg against the HBM roofline: achieved = (24 words per node and
+    iteration in 3D, 16 in 2D: the minimum traffic of one PCG iteration)
+    x N x the launch's iterations / the launch's event time, beside the
+    multigrid V-cycle's own compulsory traffic (model)."""
+    hbm, peak_kind = _load_peaks()
+    mg = prof.get("precond") == "mg"
+    launches = prof["count"]["cg"]
+    cg_ms = prof["ms"]["cg"]
+    iters = prof["cg_iters"]
+    if not launches or cg_ms <= 0:
+        return None
+    us_launch = cg_ms / launches * 1e3
+    it_launch = iters / launches
+    algo = CG_ITER_WORDS[nd] * 4 * N * it_launch
+    achieved = algo / (us_launch / 1e6) / 1e9
+    model = (MG_ITER_WORDS[nd] if mg else CG_ITER_WORDS[nd]) * 4 * N * it_launch + \
+            (MG_INIT_WORDS[nd] if mg else CG_INIT_WORDS[nd]) * 4 * N
+    tr = PCG_TRAFFIC_PER_NODE_ITER.get(name)
+    return {"kernel": "k_pcg (persistent PCG, %s, %dD)" % ("multigrid V-cycle" if mg else "Jacobi", nd),
+            "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": tr * N * it_launch if tr else None,
+            "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
+            "unit_bytes": "%d B per node and PCG iteration x %d nodes x %.2f iterations per launch"
+                          % (CG_ITER_WORDS[nd] * 4, N, it_launch),
+            "algorithmic_bytes_per_launch": algo, "us_per_launch": us_launch, "iters_per_launch": it_launch,
+            "vcycle_model_bytes_per_launch": model, "vcycle_model_frac": model / (us_launch / 1e6) / 1e9 / hbm}
+
+
+def short_line(name, steps, warmup):
+    """Another workload on its own grid, the chosen form beside the plain FP64
+    method (short runs), for the extra keys of the headline line."""
+    f = workload_fields(name)
+    if f is None:
+        return None
+    N = f["phi_f"].size
+    ms, prof, diag, out = run_gpu("mixed", steps, warmup, f, name=name)
+    s64 = max(2, steps // 4)
+    ms64, prof64, _, out64 = run_gpu("fp64", s64, warmup + steps - s64, f, name=name)
+    line = {"workload": DESCR.get(name, name), "cells": N, "steps": steps, "warmup": warmup,
+            "value": N * steps / (ms / 1e3), "unit": "cell-steps/s", "ms_per_step": ms / steps,
+            "cg_iters_per_step": prof["cg_iters"] / steps, "warm_start": WARM_TEXT.get(warm_mode(name)),
+            "fp64_plain": {"value": N * s64 / (ms64 / 1e3), "ms_per_step": ms64 / s64,
+                           "cg_iters_per_step": prof64["cg_iters"] / s64},
+            "error_vs_fp64": {k: relerr(out[k], out64[k]) for k in out},
+            "kernel_ms": prof["ms"]}
+    line["speedup_vs_fp64_plain"] = line["value"] / line["fp64_plain"]["value"]
+    line["roofline"] = pcg_roofline(prof, N, len(f["phi_f"].shape), steps, name)
+    if len(f["phi_f"].shape) == 2:
+        line["learned_warm_start"] = learned_warm_start(steps, warmup, f, ms, prof["cg_iters"], name)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="coreshell512",
-                    help="coreshell512 (default, the headline); porous2048, coreshell64 or batch64 "
-                         "print a short line")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads' keys")
+    ap.add_argument("--workload", default="porous256cube",
+                    help="porous256cube (default, the headline); coreshell512, porous2048, coreshell64, "
+                         "batch64 or stencil print a short line")
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"],
                     help="profiling aid: run one method only and print a short line")
     ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "mg"],
@@ -393,33 +503,26 @@ def main():
         args.warmup = 3
 
     ws, rank, local = dist_setup()
-    cfg = {"workload": "coreshell512_j2: 2D core-shell 512x512, radius 160, shell 32, J2 plasticity "
-                       "sigma_Y=0.01E H=0.001E",
-           "warm_start": {"extrap": "2 u_n - u_(n-1) (previous solution for the first two steps)",
-                          "extrap2": "3 u_n - 3 u_(n-1) + u_(n-2) (lower orders for the first three steps)",
-                          "prev": "previous solution", "zero": "zero"}[warm_mode()],
+    cfg = {"workload": DESCR.get(WORKLOAD, WORKLOAD),
+           "warm_start": WARM_TEXT.get(warm_mode()) if WORKLOAD in DESCR else None,
            "precond": args.precond + (" (library choice: multigrid V-cycle for this grid)" if args.precond == "auto" else ""),
-           "cells": 512 * 512, "l2": "flushed before every timed step (512 MB write)",
+           "l2": "flushed before every timed step (256 MB write); the 256^3 working set (~2 GB) exceeds L2",
            "parallelism": "replicas" if ws > 1 else "single"}
 
     if args.impl == "reference":
+        # the reference arm: the FP64 oracle on the host cores, on a bounded
+        # sample of the same workload (there is no reference implementation
+        # to install: the paper publishes no code)
         if rank != 0:
             return
         import oracle
         oracle.build()
-        f = None
         from paper_2111_11538_gb300 import workloads
-        f = workloads.build_fields("coreshell512", shape=(128, 128))
-        s = oracle.Sim(f, workloads.WORKLOADS["coreshell512"]["params"])
-        for _ in range(args.warmup):
-            s.step(1)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            s.step(1)
-        dt = time.perf_counter() - t0
-        v = 128 * 128 * args.steps / dt
-        sample = ("each step: one oracle step of the workload geometry scaled to 128x128 "
-                  "(radius 40, shell 8, same parameters), single-threaded FP64 C")
+        crop = oracle_sample(workload_fields("porous256cube"), 20)
+        v, n, dt, its = time_oracle(crop, workloads.WORKLOADS["porous256cube"]["params"], args.warmup,
+                                    steps=args.steps)
+        sample = ("each step: one oracle step of the 20^3 corner of the 256^3 porous workload's own fields "
+                  "(periodic crop, same parameters, J2, CG rtol 1e-8), single-threaded FP64 C")
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-steps/s",
                           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
@@ -435,7 +538,10 @@ def main():
     from paper_2111_11538_gb300 import native
     native.build_library()
     if WORKLOAD == "stencil":
-        print(json.dumps(stencil_roofline(steps=args.steps, warmup=args.warmup)))
+        out = [stencil_roofline(workload_fields("porous256cube"), "porous256cube", args.steps,
+                                args.warmup),
+               stencil_roofline(workload_fields("porous2048"), "porous2048", args.steps, args.warmup)]
+        print(json.dumps(out))
         return
     if WORKLOAD == "batch64":
         meth = "mixed" if args.only == "both" else args.only
@@ -454,21 +560,27 @@ def main():
         return
     fields = workload_fields()
     N = fields["phi_f"].size
+    nd = len(fields["phi_f"].shape)
     if args.only != "both":
-        ms1, prof1, diag1, _ = run_gpu(args.only, args.steps, args.warmup, fields)
+        ms1, prof1, diag1, _ = run_gpu(args.only, args.steps, args.warmup, fields, keys=())
         if rank == 0:
             print(json.dumps({"workload": WORKLOAD, "shape": list(fields["phi_f"].shape), "method": args.only,
                               "cells": N, "steps": args.steps,
                               "ms_per_step": ms1 / args.steps, "value": N * args.steps / (ms1 / 1e3),
                               "kernel_ms": prof1["ms"], "cg_iters": prof1["cg_iters"],
-                              "precond": prof1.get("precond"), "mg_levels": prof1.get("mg_levels")}))
+                              "precond": prof1.get("precond"), "mg_levels": prof1.get("mg_levels"),
+                              "roofline": pcg_roofline(prof1, N, nd, args.steps, WORKLOAD)}))
         return
 
-    # plain FP64 method (reported beside the chosen form)
+    # plain FP64 method on the same input (reported beside the chosen form);
+    # its state after fp64_warm + steps64 steps is the reference of the
+    # chosen form's per-field error
+    steps64 = max(2, args.fp64_steps)
+    warm64 = 3
     barrier(ws)
-    ms64, prof64, diag64, out64 = run_gpu("fp64", max(3, args.steps // 4), args.warmup, fields)
-    steps64 = max(3, args.steps // 4)
+    ms64, prof64, diag64, out64 = run_gpu("fp64", steps64, warm64, fields)
 
+    # the chosen form, timed (clocks sampled during the timed region)
     barrier(ws)
     torch.cuda.synchronize()
     clk = ClockSampler(local)
@@ -481,39 +593,35 @@ def main():
     value = N * args.steps * ws / (ms_max / 1e3)
 
     # per-field error of the chosen form against the plain FP64 method after
-    # the same steps (the FP64 path is held to the oracle by the parity tests)
-    def relerr(a, b):
-        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-    err = {}
-    # rerun FP64 for exactly the mixed step count so the states line up
-    ms64b, _, _, ref = run_gpu("fp64", args.steps, args.warmup, fields, profile=False)
-    for k in ("phi_f", "phi_w", "xO", "xH", "xW", "sigma"):
-        err[k] = relerr(out[k], ref[k])
+    # the same number of steps (the FP64 path is held to the oracle by the
+    # parity tests)
+    if args.steps + args.warmup == steps64 + warm64:
+        outm = out
+    else:
+        _, _, _, outm = run_gpu("mixed", steps64, warm64, fields, profile=False)
+    err = {k: relerr(outm[k], out64[k]) for k in out64}
+    del out, outm, out64
 
-    hbm, peak_kind = _load_peaks()
-    nd = 2
-    mg = prof.get("precond") == "mg"
-    b_iter = (MG_ITER_WORDS if mg else CG_ITER_WORDS[nd]) * 4 * N
-    b_init = (MG_INIT_WORDS if mg else CG_INIT_WORDS[nd]) * 4 * N
-    cg_launches = prof["count"]["cg"]
-    cg_ms = prof["ms"]["cg"]
-    iters_timed = prof["cg_iters"]          # CG iterations of the timed solves
-    achieved = None
-    cg_bytes_per_launch = None
-    if cg_launches and cg_ms > 0:
-        bytes_total = b_iter * iters_timed + b_init * cg_launches
-        cg_bytes_per_launch = bytes_total / cg_launches
-        achieved = cg_bytes_per_launch / (cg_ms / cg_launches / 1e3) / 1e9
-
-    stencil = stencil_roofline()
-    learned = learned_warm_start(args.steps, args.warmup, fields, ms, prof["cg_iters"])
+    roof = pcg_roofline(prof, N, nd, args.steps, WORKLOAD)
+    stencil = stencil_roofline(fields, WORKLOAD, steps=20, warmup=3)
     e2e_dt, h2d, d2h = run_e2e("mixed", args.e2e_steps, fields)
     e2e_val = N * args.e2e_steps * ws / reduce_max(e2e_dt, ws)
+
+    extra = {}
+    if not args.no_extra and ws == 1:
+        try:
+            extra["coreshell512"] = short_line("coreshell512", 20, 5)
+        except Exception as e:  # noqa: BLE001
+            extra["coreshell512"] = {"error": str(e)[:200]}
+        try:
+            extra["roofline_stencil_2d"] = stencil_roofline(workload_fields("porous2048"), "porous2048")
+        except Exception as e:  # noqa: BLE001
+            extra["roofline_stencil_2d"] = {"error": str(e)[:200]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         try:
-            cpu = cpu_baseline()
+            cpu = cpu_baseline(oracle_sample(fields, 20))
         except Exception as e:  # noqa: BLE001
             cpu = {"value": None, "error": str(e)[:200]}
 
@@ -523,33 +631,32 @@ def main():
         "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 fields+operator, f64 reductions", "data": "synthetic", "config": cfg,
+        "dtype": "f32 fields+operator, f64 reductions and f64 refinement of the solve "
+                 "(error vs plain f64 in error_vs_fp64)",
+        "data": "synthetic", "config": dict(cfg, cells=N),
         "fp64_plain": {"value": N * steps64 * ws / (reduce_max(ms64, ws) / 1e3), "unit": "cell-steps/s",
-                       "ms_per_step": ms64 / steps64, "cg_iters_per_step": prof64["cg_iters"] / steps64,
-                       "kernel_ms": prof64["ms"]},
+                       "steps": steps64, "warmup": warm64, "ms_per_step": ms64 / steps64,
+                       "cg_iters_per_step": prof64["cg_iters"] / steps64, "kernel_ms": prof64["ms"]},
         "speedup_vs_fp64_plain": None,
-        "error_vs_fp64": err,
+        "error_vs_fp64": dict(err, after_steps=steps64 + warm64),
         "cg": {"rtol": workload_params("mixed")["cg_rtol"],
                "mixed": "FP32 Chronopoulos-Gear PCG passes inside FP64 iterative refinement",
-               "precond": prof.get("precond"), "mg_levels": prof.get("mg_levels"), "iters_timed": iters_timed,
-               "iters_per_step": iters_timed / args.steps if args.steps else None},
+               "precond": prof.get("precond"), "mg_levels": prof.get("mg_levels"),
+               "iters_timed": prof["cg_iters"], "iters_per_step": prof["cg_iters"] / args.steps},
         "kernel_ms": prof["ms"], "kernel_count": prof["count"],
-        "roofline": {"kernel": "k_pcg (persistent PCG, %s)" % ("multigrid V-cycle" if mg else "Jacobi"),
-                     "bound": "hbm", "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
-                     "traffic": PCG_TRAFFIC["mg" if mg else "jacobi"],
-                     "traffic_launch": ("ncu, first timed step's solve (cold L2, 3 refinement passes, ~15 "
-                                        "V-cycles); the solve's working set stays in L2, so its DRAM bytes "
-                                        "are first-touch and do not grow with the V-cycle count"),
-                     "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
-                     "algorithmic_bytes_per_launch": cg_bytes_per_launch},
+        "roofline": roof,
         "roofline_stencil": stencil,
-        "learned_warm_start": learned,
-        "e2e": {"value": e2e_val, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "learned_warm_start": learned_warm_start(0, 0, fields, 0, 0, WORKLOAD),
+        "e2e": {"value": e2e_val, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": args.e2e_steps,
+                "note": "pf_set_fields / pf_step / pf_get_fields with pinned host buffers every step; each "
+                        "set_fields restarts the extrapolated guess, so these steps start from the previous "
+                        "solution"},
         "gpu_launches": prof["launches"],
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    line.update(extra)
     line["speedup_vs_fp64_plain"] = value / line["fp64_plain"]["value"] if line["fp64_plain"]["value"] else None
     print(json.dumps(line))
 
