@@ -454,8 +454,11 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
     constexpr int CX = TX + 1, CY = TY + 1, CZ = D == 3 ? TZ + 1 : 1;
     constexpr int HN = HX * HY * HZ, HC = CX * CY * CZ;
     constexpr int MAX_OUTER = 24;
-    __shared__ T su[D * HN];
-    __shared__ T sl[HC], sm[HC];
+    // the node and cell tiles of the plain sweep (the 3D multigrid variant
+    // keeps its tiles in the dynamic shared memory)
+    constexpr bool Z3 = MG && D == 3;
+    __shared__ T su[Z3 ? 1 : D * HN];
+    __shared__ T sl[Z3 ? 1 : HC], sm[Z3 ? 1 : HC];
     // per-cell stress and hourglass forces: 2D 5 values per cell; 3D FP32 on
     // the 16x4x4 tile 20 (five float4); other 3D variants use the
     // element-matrix path and need none
@@ -652,8 +655,7 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
             if constexpr (D == 2)
                 rc = mg_pass<T, TX, TY>(A, *A.mg, S, su, sl, sm, scell, sblk, s_ta, s_tb, s_ue, s_ctl, bid, nbk, err);
             else
-                rc = mg_pass3<T, TX, TY, TZ>(A, *A.mg, S, su, sl, sm, reinterpret_cast<T *>(pcg_dyn), s_ta, s_tb, s_ue,
-                                             s_ctl, bid, nbk, err);
+                rc = mg_pass3<T>(A, *A.mg, S, reinterpret_cast<T *>(pcg_dyn), s_ta, s_tb, s_ue, s_ctl, bid, nbk, err);
             if (rc < 0) return;
             if (lead) conv = rc == CTL_DONE;
         } else {
@@ -996,11 +998,9 @@ size_t pcg_dyn_smem(int shape, bool mg)
                sizeof(T) * (size_t)sweep2_words<Tile<2, 0>::X, Tile<2, 0>::Y>();
     }
     if (D == 3 && mg) {
-        // the 3D V-cycle's per-cell stress and hourglass forces (mg_sweep3),
-        // or the set-up sweep's FP64 scratch (setup_tiled3)
-        const int hc = shape == 1 ? (Tile<3, 1>::X + 1) * (Tile<3, 1>::Y + 1) * (Tile<3, 1>::Z + 1)
-                                  : (Tile<3, 0>::X + 1) * (Tile<3, 0>::Y + 1) * (Tile<3, 0>::Z + 1);
-        const size_t cells = sizeof(T) * 20 * (size_t)hc;
+        // the 3D V-cycle's node planes and corner forces (mg_sweep3z), or the
+        // set-up sweep's FP64 scratch (setup_tiled3)
+        const size_t cells = sizeof(T) * (size_t)mg_sweep3z_words<T>();
         const size_t stp = sizeof(double) * (size_t)(shape == 1
             ? setup_tiled3_doubles<Tile<3, 1>::X, Tile<3, 1>::Y, Tile<3, 1>::Z>()
             : setup_tiled3_doubles<Tile<3, 0>::X, Tile<3, 0>::Y, Tile<3, 0>::Z>());

@@ -14,91 +14,200 @@
 
 namespace pfdev {
 
-// One 3D sweep over node tiles TX x TY x TZ: val(gx, gy, gz, v) gives the
-// operand at any node of the tile and its halo, epi(n, v, q, se) receives at
-// each own node q = A v and (WITH_E) the own cell's average stress without
-// the mean strain ue (which is added to every cell's stress for q).  su:
-// 3 * HN halo nodes, sl / sm: HC halo cells (static shared memory of the
-// PCG kernel); scell: 20 * HC values (the dynamic shared memory).
-template <typename T, int TX, int TY, int TZ, bool WITH_E, class Val, class Epi>
-__device__ __forceinline__ void mg_sweep3(int nx, int ny, int nz, const T *lam, const T *mu, int bid, int nbk, T *su,
-                                          T *sl, T *sm, T *scell, const T *ue, Val &&val, Epi &&epi)
+// Shared-memory storage of 3-vectors: FP32 as one float4 per entry (one
+// 128-bit access), FP64 as three planes of n doubles.  WORDS values of T per
+// entry.
+template <typename T> struct V3S;
+template <> struct V3S<float> {
+    static constexpr int WORDS = 4;
+    __device__ static __forceinline__ void st(float *b, int, int i, const float (&v)[3])
+    {
+        reinterpret_cast<float4 *>(b)[i] = make_float4(v[0], v[1], v[2], 0.f);
+    }
+    __device__ static __forceinline__ void ld(const float *b, int, int i, float (&v)[3])
+    {
+        const float4 a = reinterpret_cast<const float4 *>(b)[i];
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = a.z;
+    }
+};
+template <> struct V3S<double> {
+    static constexpr int WORDS = 3;
+    __device__ static __forceinline__ void st(double *b, int n, int i, const double (&v)[3])
+    {
+        b[i] = v[0];
+        b[n + i] = v[1];
+        b[2 * n + i] = v[2];
+    }
+    __device__ static __forceinline__ void ld(const double *b, int n, int i, double (&v)[3])
+    {
+        v[0] = b[i];
+        v[1] = b[n + i];
+        v[2] = b[2 * n + i];
+    }
+};
+
+// Forces of a 3D cell on its eight corner nodes, f[a][comp] with
+// a = ax + 2 ay + 4 az, from its average stress s (mean strain included) and
+// hourglass forces g (cell_force3).  This is node_force3 at every corner,
+// factored: per component the corner value is a sum of the terms sx, sy, sz,
+// sx sy, sy sz, sz sx and sx sy sz (s_i = +1 at the upper corner along axis
+// i, -1 at the lower) with the coefficients below, and the eight sign
+// patterns are formed by sums and differences.
+template <typename TC>
+__device__ __forceinline__ void corner_forces3(const TC *s, const TC *g, TC (&f)[8][3])
 {
-    constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HN = HX * HY * HZ;
-    constexpr int CX = TX + 1, CY = TY + 1, CZ = TZ + 1, HC = CX * CY * CZ, NT = TX * TY * TZ;
-    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntz = (nz + TZ - 1) / TZ;
-    const int ntiles = ntx * nty * ntz;
-    const bool small = nx < HX || ny < HY || nz < HZ;
-    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
-    for (int tile = bid; tile < ntiles; tile += nbk) {
-        const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY, z0 = (tile / (ntx * nty)) * TZ;
-        for (int h = threadIdx.x; h < HN; h += NT) {
-            const int lx = h % HX, ly = (h / HX) % HY, lz = h / (HX * HY);
-            T v[3];
-            val(mg_wrap(x0 - 1 + lx, nx, small), mg_wrap(y0 - 1 + ly, ny, small), mg_wrap(z0 - 1 + lz, nz, small), v);
-            su[h] = v[0];
-            su[HN + h] = v[1];
-            su[2 * HN + h] = v[2];
+    constexpr int SXI[3] = {0, 5, 4}, SYI[3] = {5, 1, 3}, SZI[3] = {4, 3, 2};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const TC ax = TC(0.25) * s[SXI[k]], ay = TC(0.25) * s[SYI[k]], az = TC(0.25) * s[SZI[k]];
+        const TC axy = TC(0.5) * g[k], ayz = TC(0.5) * g[3 + k], azx = TC(0.5) * g[6 + k], axyz = g[9 + k];
+        const TC p1 = ay + ayz, p2 = ay - ayz, o1 = ax + azx, o2 = ax - azx, q1 = axy + axyz, q2 = axy - axyz;
+        // (sy, sz) = (+, +), (-, +), (+, -), (-, -): even part E, odd part O in sx
+        const TC Epp = p1 + az, Emp = az - p1, Epm = p2 - az, Emm = -(p2 + az);
+        const TC Opp = o1 + q1, Omp = o1 - q1, Opm = o2 + q2, Omm = o2 - q2;
+        f[7][k] = Epp + Opp;  f[6][k] = Epp - Opp;     // ay = 1, az = 1
+        f[5][k] = Emp + Omp;  f[4][k] = Emp - Omp;     // ay = 0, az = 1
+        f[3][k] = Epm + Opm;  f[2][k] = Epm - Opm;     // ay = 1, az = 0
+        f[1][k] = Emm + Omm;  f[0][k] = Emm - Omm;     // ay = 0, az = 0
+    }
+}
+
+// Tile of the z-marching 3D sweep: TX x TY nodes per plane, one thread each.
+constexpr int MGZ_TX = 32, MGZ_TY = 8;
+
+// Shared memory (values of T) of mg_sweep3z: two node planes and the eight
+// corner forces of one cell plane, with their halos.
+template <typename T>
+__host__ __device__ constexpr int mg_sweep3z_words()
+{
+    return V3S<T>::WORDS * (2 * (MGZ_TX + 2) * (MGZ_TY + 2) + 8 * (MGZ_TX + 1) * (MGZ_TY + 1));
+}
+
+// z-chunk of the 3D sweep on an nx x ny x nz level with nbk blocks: the
+// candidate that minimises (work items per block, rounded up) x (planes per
+// item + 1), ties to the longer chunk.
+__device__ __forceinline__ int mg_zchunk(int nx, int ny, int nz, int nbk)
+{
+    const int ixy = ((nx + MGZ_TX - 1) / MGZ_TX) * ((ny + MGZ_TY - 1) / MGZ_TY);
+    constexpr int cand[12] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+    int best = nz;
+    long long bcost = (long long)((ixy + nbk - 1) / nbk) * (nz + 1);
+    for (int i = 0; i < 12; i++) {
+        const int zc = cand[i];
+        if (zc >= nz) break;
+        const long long items = (long long)ixy * ((nz + zc - 1) / zc);
+        const long long cost = ((items + nbk - 1) / nbk) * (zc + 1);
+        if (cost <= bcost) {
+            bcost = cost;
+            best = zc;
         }
-        for (int h = threadIdx.x; h < HC; h += NT) {
-            const int lx = h % CX, ly = (h / CX) % CY, lz = h / (CX * CY);
-            const int g = mg_wrap(x0 - 1 + lx, nx, small) +
-                          nx * (mg_wrap(y0 - 1 + ly, ny, small) + ny * mg_wrap(z0 - 1 + lz, nz, small));
-            sl[h] = __ldcg(lam + g);
-            sm[h] = __ldcg(mu + g);
+    }
+    return best;
+}
+
+// One 3D sweep of the level's Q1 operator, marching along z.  A work item is
+// a TX x TY column of node tiles over zc planes.  Per cell plane zp: the node
+// plane zp + 1 (with its one-node halo in x and y) is staged by val(gx, gy,
+// gz, v), every cell of the plane (with the halo cells at x0 - 1, y0 - 1)
+// computes its average stress and hourglass forces once (cell_force3) and
+// its forces on its eight corners (corner_forces3), and each own node of
+// plane zp adds its bottom-corner forces to the top-corner forces left by
+// plane zp - 1: q = A v is complete and epi(n, v, q) receives it.  WITH_E:
+// the mean strain ue enters every cell's stress, and cell_e(c) receives the
+// stress of every own cell without it (c[0..5]).  smem: mg_sweep3z_words<T>()
+// values; two block barriers per plane.
+template <typename T, bool WITH_E, class Val, class Epi, class CellE>
+__device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const T *lam, const T *mu, int bid,
+                                           int nbk, T *smem, const T *ue, Val &&val, Epi &&epi, CellE &&cell_e)
+{
+    constexpr int TX = MGZ_TX, TY = MGZ_TY;
+    constexpr int NX = TX + 2, NY = TY + 2, NP = NX * NY;
+    constexpr int CX = TX + 1, CY = TY + 1, NC = CX * CY, NT = TX * TY;
+    constexpr int W = V3S<T>::WORDS;
+    T *const np0 = smem, *const np1 = smem + W * NP, *const cf = smem + 2 * W * NP;
+    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, nzc = (nz + zc - 1) / zc;
+    const int items = ntx * nty * nzc;
+    const bool small = nx < NX || ny < NY;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    for (int item = bid; item < items; item += nbk) {
+        const int x0 = (item % ntx) * TX, y0 = ((item / ntx) % nty) * TY, z0 = (item / (ntx * nty)) * zc;
+        const int z1 = min(z0 + zc, nz);
+        const int gx = x0 + tx, gy = y0 + ty;
+        const bool own = gx < nx && gy < ny;
+        auto stage = [&](int z, T *buf) {
+            const int zw = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+            for (int h = threadIdx.x; h < NP; h += NT) {
+                const int lx = h % NX, ly = h / NX;
+                T v[3];
+                val(mg_wrap(x0 - 1 + lx, nx, small), mg_wrap(y0 - 1 + ly, ny, small), zw, v);
+                V3S<T>::st(buf, NP, h, v);
+            }
+        };
+        stage(z0 - 1, ((z0 - 1) & 1) ? np1 : np0);
+        T qt[3] = {T(0), T(0), T(0)};     // top-corner forces of the previous cell plane on the own node
+        for (int zp = z0 - 1; zp < z1; zp++) {
+            T *const nlo = (zp & 1) ? np1 : np0;
+            T *const nhi = (zp & 1) ? np0 : np1;
+            stage(zp + 1, nhi);
+            __syncthreads();
+            const int zw = zp < 0 ? zp + nz : zp;
+            const bool inner = zp >= z0;
+            for (int h = threadIdx.x; h < NC; h += NT) {
+                const int cx = h % CX, cy = h / CX;
+                const int g = mg_wrap(x0 - 1 + cx, nx, small) + nx * (mg_wrap(y0 - 1 + cy, ny, small) + ny * zw);
+                const T l = __ldcg(lam + g), m = __ldcg(mu + g);
+                T uc[8][3];
+#pragma unroll
+                for (int b = 0; b < 8; b++) V3S<T>::ld((b >> 2) ? nhi : nlo, NP, (cx + (b & 1)) + NX * (cy + ((b >> 1) & 1)), uc[b]);
+                T c[20];
+                cell_force3<T>(l, m, uc, c);
+                if constexpr (WITH_E) {
+                    if (inner && cx >= 1 && cy >= 1 && x0 + cx - 1 < nx && y0 + cy - 1 < ny) cell_e(c);
+                    T sx[6];
+                    voigt_stress<T, 3>(l, m, ue, sx);
+#pragma unroll
+                    for (int v = 0; v < 6; v++) c[v] += sx[v];
+                }
+                T f[8][3];
+                corner_forces3<T>(c, c + 6, f);
+#pragma unroll
+                for (int a = 0; a < 8; a++) V3S<T>::st(cf + a * W * NC, NC, h, f[a]);
+            }
+            T un[3];
+            if (own && inner) V3S<T>::ld(nlo, NP, (tx + 1) + NX * (ty + 1), un);
+            __syncthreads();
+            if (own) {
+                // cells around the node in this plane: (tx, ty) is its lower-left
+                // neighbour (the node is that cell's corner ax = ay = 1)
+                const int c11 = tx + CX * ty, c01 = c11 + 1, c10 = c11 + CX, c00 = c10 + 1;
+                T fb[3], ft[3], v[3];
+                V3S<T>::ld(cf + 3 * W * NC, NC, c11, fb);
+                V3S<T>::ld(cf + 7 * W * NC, NC, c11, ft);
+#pragma unroll
+                for (int k = 0; k < 3; k++) { fb[k] += qt[k]; }
+                V3S<T>::ld(cf + 2 * W * NC, NC, c01, v);
+#pragma unroll
+                for (int k = 0; k < 3; k++) fb[k] += v[k];
+                V3S<T>::ld(cf + 6 * W * NC, NC, c01, v);
+#pragma unroll
+                for (int k = 0; k < 3; k++) ft[k] += v[k];
+                V3S<T>::ld(cf + 1 * W * NC, NC, c10, v);
+#pragma unroll
+                for (int k = 0; k < 3; k++) fb[k] += v[k];
+                V3S<T>::ld(cf + 5 * W * NC, NC, c10, v);
+#pragma unroll
+                for (int k = 0; k < 3; k++) ft[k] += v[k];
+                V3S<T>::ld(cf + 0 * W * NC, NC, c00, v);
+#pragma unroll
+                for (int k = 0; k < 3; k++) fb[k] += v[k];
+                V3S<T>::ld(cf + 4 * W * NC, NC, c00, v);
+#pragma unroll
+                for (int k = 0; k < 3; k++) { ft[k] += v[k]; qt[k] = ft[k]; }
+                if (inner) epi(gx + nx * (gy + ny * zp), un, fb);
+            }
         }
-        __syncthreads();
-        for (int h = threadIdx.x; h < HC; h += NT) {
-            const int cx = h % CX, cy = (h / CX) % CY, cz = h / (CX * CY);
-            T uc[8][3];
-#pragma unroll
-            for (int b = 0; b < 8; b++) {
-                const int hn = (cx + (b & 1)) + HX * ((cy + ((b >> 1) & 1)) + HY * (cz + (b >> 2)));
-                uc[b][0] = su[hn];
-                uc[b][1] = su[HN + hn];
-                uc[b][2] = su[2 * HN + hn];
-            }
-            const T l = sl[h], m = sm[h];
-            T c[20];
-            cell_force3<T>(l, m, uc, c);
-            if constexpr (WITH_E) {
-                T sx[6];
-                voigt_stress<T, 3>(l, m, ue, sx);
-#pragma unroll
-                for (int v = 0; v < 6; v++) c[v] += sx[v];
-            }
-#pragma unroll
-            for (int v = 0; v < 18; v++) scell[v * HC + h] = c[v];
-        }
-        __syncthreads();
-        const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-        if (gx < nx && gy < ny && gz < nz) {
-            const int lx = tx + 1, ly = ty + 1, lz = tz + 1, hn = lx + HX * (ly + HY * lz);
-            const T un[3] = {su[hn], su[HN + hn], su[2 * HN + hn]};
-            T q[3] = {T(0), T(0), T(0)}, se[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-#pragma unroll
-            for (int a = 0; a < 8; a++) {
-                const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
-                const int cl = (lx - ax) + CX * ((ly - ay) + CY * (lz - az));
-                T c[18];
-#pragma unroll
-                for (int v = 0; v < 18; v++) c[v] = scell[v * HC + cl];
-                T f[3];
-                node_force3<T>(ax, ay, az, c, c + 6, f);
-                q[0] += f[0];
-                q[1] += f[1];
-                q[2] += f[2];
-            }
-            if constexpr (WITH_E) {
-                const int c0 = lx + CX * (ly + CY * lz);
-                T sx[6];
-                voigt_stress<T, 3>(sl[c0], sm[c0], ue, sx);
-#pragma unroll
-                for (int v = 0; v < 6; v++) se[v] = scell[v * HC + c0] - sx[v];
-            }
-            epi(gx + nx * (gy + ny * gz), un, q, se);
-        }
-        __syncthreads();
     }
 }
 
@@ -267,9 +376,9 @@ __device__ bool mg_setup3(const MGHier<T> &H, unsigned int *bc, unsigned int *bg
 // One pass of MG-preconditioned CG in 3D: as mg_pass (pf_mg.cuh), every
 // level on the whole grid.  scell: 20 * HC values of dynamic shared memory.
 // Returns CTL_DONE or CTL_STOP, or -1 when a barrier timed out.
-template <typename T, int TX, int TY, int TZ>
-__device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S, T *su, T *sl, T *sm, T *scell,
-                        T &s_ta, T &s_tb, T *s_ue, int &s_ctl, int bid, int nbk, int *err)
+template <typename T>
+__device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S, T *smem, T &s_ta, T &s_tb,
+                        T *s_ue, int &s_ctl, int bid, int nbk, int *err)
 {
     constexpr int NV = 6;
     const bool lead = threadIdx.x == 0;
@@ -278,6 +387,16 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
     unsigned int *bc = A.bar_count, *bg = A.bar_gen;
     auto sync = [&]() { return grid_sync(bc, bg, err, nbk); };
     auto lin3 = [](const MGLevel<T> &V, int x, int y, int z) { return x + V.nx * (y + V.ny * z); };
+    // z-chunk of every level's sweeps for this job's blocks
+    __shared__ int s_zc[MG_MAX_LEVELS];
+    if (lead)
+        for (int k = 0; k < L; k++) s_zc[k] = mg_zchunk(H.lv[k].nx, H.lv[k].ny, H.lv[k].nz, nbk);
+    __syncthreads();
+    auto none = [](const T *) {};
+    auto sweep = [&](int k, auto &&val, auto &&epi) {
+        const MGLevel<T> &V = H.lv[k];
+        mg_sweep3z<T, false>(V.nx, V.ny, V.nz, s_zc[k], V.lam, V.mu, bid, nbk, smem, nullptr, val, epi, none);
+    };
 
     // Chebyshev step j on level k (buffer par -> 1 - par); last: also apply
     // step j + 1 and leave the final correction in xpost
@@ -285,8 +404,7 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
         const MGLevel<T> &V = H.lv[k];
         T *const *X = post ? V.xpost : V.xpre;
         const T c1 = H.c1[j], c2 = H.c2[j], n1 = H.c1[j + 1], n2 = H.c2[j + 1];
-        mg_sweep3<T, TX, TY, TZ, false>(
-            V.nx, V.ny, V.nz, V.lam, V.mu, bid, nbk, su, sl, sm, scell, nullptr,
+        sweep(k,
             [&](int gx, int gy, int gz, T (&v)[3]) {
                 const int g = lin3(V, gx, gy, gz);
                 const T di = c2 * __ldcg(V.dinv + g);
@@ -297,7 +415,7 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                     v[c] = a;
                 }
             },
-            [&](int n, const T (&v)[3], const T (&q)[3], const T (&)[6]) {
+            [&](int n, const T (&v)[3], const T (&q)[3]) {
                 const T di = last ? n2 * __ldcg(V.dinv + n) : T(0);
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
@@ -339,8 +457,7 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
     auto pre_first = [&](int k) {
         const MGLevel<T> &V = H.lv[k];
         const T c2 = H.c2[0];
-        mg_sweep3<T, TX, TY, TZ, false>(
-            V.nx, V.ny, V.nz, V.lam, V.mu, bid, nbk, su, sl, sm, scell, nullptr,
+        sweep(k,
             [&](int gx, int gy, int gz, T (&v)[3]) {
                 T f[3];
                 restrict3(k, gx, gy, gz, f);
@@ -348,7 +465,7 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
 #pragma unroll
                 for (int c = 0; c < 3; c++) v[c] = di * f[c];
             },
-            [&](int n, const T (&v)[3], const T (&q)[3], const T (&)[6]) {
+            [&](int n, const T (&v)[3], const T (&q)[3]) {
                 const int gx = n % V.nx, gy = (n / V.nx) % V.ny, gz = n / (V.nx * V.ny);
                 T f[3];
                 restrict3(k, gx, gy, gz, f);
@@ -366,8 +483,7 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
     auto post_first = [&](int k, int par, int cur, bool last) {
         const MGLevel<T> &V = H.lv[k];
         const MGLevel<T> &C = H.lv[k + 1];
-        mg_sweep3<T, TX, TY, TZ, false>(
-            V.nx, V.ny, V.nz, V.lam, V.mu, bid, nbk, su, sl, sm, scell, nullptr,
+        sweep(k,
             [&](int gx, int gy, int gz, T (&v)[3]) {
                 const int g = lin3(V, gx, gy, gz);
                 const int o[3] = {gx & 1, gy & 1, gz & 1}, ic[3] = {gx >> 1, gy >> 1, gz >> 1};
@@ -387,7 +503,7 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
 #pragma unroll
                 for (int c = 0; c < 3; c++) v[c] = __ldcg(V.xpre[c] + g) + w * e[c];
             },
-            [&](int n, const T (&v)[3], const T (&q)[3], const T (&)[6]) {
+            [&](int n, const T (&v)[3], const T (&q)[3]) {
                 const T di = last ? H.c2[0] * __ldcg(V.dinv + n) : T(0);
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
@@ -445,8 +561,7 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
         Acc<T> racc[1];
         {
             const T c2 = H.c2[0];
-            mg_sweep3<T, TX, TY, TZ, false>(
-                L0.nx, L0.ny, L0.nz, L0.lam, L0.mu, bid, nbk, su, sl, sm, scell, nullptr,
+            sweep(0,
                 [&](int gx, int gy, int gz, T (&v)[3]) {
                     const int g = lin3(L0, gx, gy, gz);
                     const T di = c2 * __ldcg(L0.dinv + g);
@@ -457,7 +572,7 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                         v[c] = di * rv;
                     }
                 },
-                [&](int n, const T (&v)[3], const T (&q)[3], const T (&)[6]) {
+                [&](int n, const T (&v)[3], const T (&q)[3]) {
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
                         T f = __ldcg(A.r[cur][c] + n);
@@ -515,20 +630,22 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
 
         // ---- u = V-cycle result, w = A u (+ mean strain), gamma, delta, mean-strain row
         Acc<T> acc[2 + NV];
-        mg_sweep3<T, TX, TY, TZ, true>(
-            L0.nx, L0.ny, L0.nz, L0.lam, L0.mu, bid, nbk, su, sl, sm, scell, s_ue,
+        mg_sweep3z<T, true>(
+            L0.nx, L0.ny, L0.nz, s_zc[0], L0.lam, L0.mu, bid, nbk, smem, s_ue,
             [&](int gx, int gy, int gz, T (&v)[3]) {
                 const int g = lin3(L0, gx, gy, gz);
 #pragma unroll
                 for (int c = 0; c < 3; c++) v[c] = __ldcg(L0.xpost[c] + g);
             },
-            [&](int n, const T (&v)[3], const T (&q)[3], const T (&se)[6]) {
+            [&](int n, const T (&v)[3], const T (&q)[3]) {
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
                     A.w[cur][c][n] = q[c];
                     acc[0].fma_plain(__ldcg(A.r[cur][c] + n), v[c]);
                     acc[1].fma_plain(q[c], v[c]);
                 }
+            },
+            [&](const T *se) {
 #pragma unroll
                 for (int vv = 0; vv < NV; vv++) acc[2 + vv].add_plain(se[vv]);
             });

@@ -148,6 +148,26 @@ def test_mg3_fp64_against_oracle(orc):
     assert rel(g["sigma"], s.f["sigma"]) < 1e-8
 
 
+def test_mg3_mixed_against_oracle(orc):
+    """The configuration the 3D bench times, on a grid the oracle finishes:
+    mixed precision (FP32 V-cycles inside FP64 refinement), multigrid with
+    three levels (32^3 -> 16^3 -> 8^3), J2 plasticity, the extrapolated
+    guess, CG rtol 1e-8, a porous input with supply layers; against the
+    oracle's FP64 Jacobi solves at the same rtol: 1e-4 on the fields, 1e-3
+    on the stress."""
+    shape = (32, 32, 32)
+    f = inputs.porous(shape, 20, 0.15, 3.0, 0.4, 31)
+    prm = workloads.params(plasticity=1, cg_rtol=1e-8)
+    g, d = _run(shape, dict(prm, warm_start="extrap"), f, 3, "mixed", "mg")
+    assert d["precond"] == native.PF_PC_MG and d["mg_levels"] == 3
+    s = orc.Sim(f, prm)
+    s.step(3)
+    ref = {"phi_f": s.phi_f, "phi_w": s.phi_w, "xO": s.f["xO"], "xH": s.f["xH"], "xW": s.f["xW"]}
+    for k in KEYS:
+        assert rel(g[k], ref[k]) < 1e-4, (k, rel(g[k], ref[k]))
+    assert rel(g["sigma"], s.f["sigma"]) < 1e-3, rel(g["sigma"], s.f["sigma"])
+
+
 @pytest.mark.parametrize("shape,levels", [((32, 32, 32), 3), ((16, 24, 32), 2), ((9, 10, 12), 1)])
 @pytest.mark.parametrize("precision,rtol,tol", [("fp64", 1e-10, 1e-8), ("mixed", 1e-8, 1e-5)])
 def test_mg3_matches_jacobi(shape, levels, precision, rtol, tol):
