@@ -223,7 +223,7 @@ def run_e2e(precision, steps, fields):
     state = {k: pinned(v, np.uint8 if k == "mask" else np.float64) for k, v in fields.items()}
     sim.set_fields(state)
     sim.step(2)
-    keys = ("phi_f", "phi_w", "xO", "xH", "xW", "u", "Ebar", "eps_p", "alpha")
+    keys = ("phi_f", "phi_w", "xO", "xH", "xW", "theta", "phig", "u", "Ebar", "eps_p", "alpha")
     cur = sim.get_fields(keys=keys)
     state.update({k: pinned(v) for k, v in cur.items()})
     h2d = sum(v.nbytes for v in state.values())

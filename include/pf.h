@@ -17,8 +17,16 @@
  *      (Sec. 2.4, eq. FieRelDRI; Sec. 2.3.1, eqs. EmpModRea, forward-k),
  *      then the reset of the supply (Dirichlet) cells (Sec. 4.3).
  * Gas fraction phi_g = 1 - phi_f - phi_w is held fixed; the solid is split by
- * theta = phi_f / (phi_f + phi_w) (the library's reading of Sec. 2.2 and
- * Sec. 2.4, see the repository's design notes).
+ * the order parameter theta = phi_f / (phi_f + phi_w), which evolves.  This
+ * is the library's reading of Sec. 2.2 and Sec. 2.4: the paper's two
+ * Allen-Cahn relations for phi_f and phi_w, taken literally with phi_g
+ * dependent and the absolute CALPHAD energies, create gas inside ferrite /
+ * wuestite interfaces at the rate L h'(phi) (psi_f + psi_w); with phi_g held
+ * and the weights W_f = (1 - h(phi_g)) h(theta), W_w = (1 - h(phi_g))
+ * (1 - h(theta)), W_g = h(phi_g) in place of h(phi_a), every two-phase
+ * interface keeps the paper's energies and the theta relation on a ferrite /
+ * wuestite interface is the paper's phi_f relation minus its phi_w relation,
+ * over two.
  *
  * Conventions
  *   - Grids are periodic, dx = 1, row-major with x fastest: index
@@ -112,12 +120,23 @@ typedef struct {
  *   sigma   : output only, N*4 / N*6 like eps_p (from the last step's return map)
  *   mobility: input only, N factor on L (grain scatter)
  *   dirichlet: input only, N bytes, 1 = supply cell
+ *   theta   : N, the evolving solid order parameter, and
+ *   phi_g   : N, the gas fraction the library holds fixed (the fields of
+ *             Sec. 2.4 as the library advances them: theta, phi_g, x_O,
+ *             x_H, x_H2O).  On output their values; on input, if given, they
+ *             replace phi_f / (phi_f + phi_w) and 1 - phi_f - phi_w, which
+ *             round, and which cannot recover theta in cells without solid
+ *             (phi_g = 1), where theta still evolves and enters its
+ *             neighbours' Laplacian.  A pf_get_fields of every field
+ *             followed by pf_set_fields (plus mobility and dirichlet)
+ *             restores the state exactly in FP64.
  * With PF_DEVICE every pointer is device memory holding the same FP64 layout. */
 typedef struct {
     double *phi_f, *phi_w, *x_O, *x_H, *x_H2O;
     double *u, *Ebar, *eps_p, *alpha, *sigma;
     double *mobility;
     unsigned char *dirichlet;
+    double *theta, *phi_g;
 } pf_fields;
 
 typedef struct {
@@ -141,14 +160,22 @@ typedef struct {
 
 typedef struct pf_handle pf_handle;
 
-/* Allocate device state for one grid.  Validates cfg (PF_EINVAL), chooses dt
+/* Allocate device state for one grid: the fields of the model (Sec. 2.4:
+ * order parameter, gas fraction, the three species fractions; Sec. 2.3: the
+ * plastic strain and hardening variable; the displacement of div P = 0) and
+ * the solver's work arrays.  Validates cfg (PF_EINVAL), chooses dt
  * (pf_dt_stable x 0.2 when cfg->dt <= 0), allocates (PF_ENOMEM).  *out is set
  * to NULL on failure. */
 int pf_create(const pf_config *cfg, pf_handle **out);
 
-/* Copy fields in.  phi_f, phi_w, x_O, x_H, x_H2O are required; the rest
- * default to: u = 0, Ebar = 0, eps_p = 0, alpha = 0, mobility = 1,
- * dirichlet = 0.  Resets the step counter and the diagnostics. */
+/* Copy in the state that the field relations of Sec. 2.4 evolve (the
+ * initial conditions of Sec. 4: phases, species fractions, and the
+ * mechanical state).  phi_f, phi_w, x_O, x_H, x_H2O are required; the rest
+ * default to: theta = phi_f / (phi_f + phi_w) (0 without solid),
+ * phi_g = 1 - phi_f - phi_w, u = 0,
+ * Ebar = 0, eps_p = 0, alpha = 0, mobility = 1, dirichlet = 0.  Resets the
+ * step counter, the diagnostics and the extrapolation history of the CG
+ * guess. */
 int pf_set_fields(pf_handle *h, const pf_fields *f, int where);
 
 /* Advance nsteps >= 0 steps on cudaStream (NULL: the handle's own stream),
@@ -160,8 +187,10 @@ int pf_set_fields(pf_handle *h, const pf_fields *f, int where);
  * capture fails); the results are the same either way. */
 int pf_step(pf_handle *h, int nsteps, void *cudaStream);
 
-/* Copy fields out into caller arrays (FP64).  sigma is the stress of the last
- * return map.  mobility / dirichlet are ignored. */
+/* Copy the current state (the fields of Sec. 2.4 and the mechanical state)
+ * out into caller arrays (FP64); NULL members are skipped.  sigma is the
+ * stress of the last return map (Sec. 2.3).  mobility / dirichlet are
+ * ignored. */
 int pf_get_fields(pf_handle *h, pf_fields *out, int where);
 
 int pf_get_diagnostics(pf_handle *h, pf_diag *out);

@@ -165,7 +165,7 @@ class Sim:
         self.f = {}
         th, pg = split_phases(fields["phi_f"], fields["phi_w"])
         self.f["theta"] = np.ascontiguousarray(fields.get("theta", th), dtype=np.float64).copy()
-        self.f["phig"] = np.ascontiguousarray(pg, dtype=np.float64).copy()
+        self.f["phig"] = np.ascontiguousarray(fields.get("phig", pg), dtype=np.float64).copy()
         for k in ("xO", "xH", "xW"):
             self.f[k] = np.ascontiguousarray(fields[k], dtype=np.float64).copy()
         self.f["mob"] = np.ascontiguousarray(fields.get("mob", np.ones(self.shape)), dtype=np.float64).copy()

@@ -65,10 +65,10 @@ def _dptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
 
 
-FIELD_KEYS = ("phi_f", "phi_w", "xO", "xH", "xW", "u", "Ebar", "eps_p", "alpha", "sigma")
+FIELD_KEYS = ("phi_f", "phi_w", "xO", "xH", "xW", "u", "Ebar", "eps_p", "alpha", "sigma", "theta", "phig")
 _NAMES = {"phi_f": "phi_f", "phi_w": "phi_w", "xO": "x_O", "xH": "x_H", "xW": "x_H2O",
           "u": "u", "Ebar": "Ebar", "eps_p": "eps_p", "alpha": "alpha", "sigma": "sigma",
-          "mob": "mobility"}
+          "mob": "mobility", "theta": "theta", "phig": "phi_g"}
 
 
 def _in_fields(fields, where, N, ndim):
@@ -81,7 +81,7 @@ def _in_fields(fields, where, N, ndim):
     nv = 3 if ndim == 2 else 6
     if where == "host":
         sizes = {"u": N * ndim, "eps_p": N * npl, "Ebar": nv}
-        for key in ("phi_f", "phi_w", "xO", "xH", "xW", "alpha", "mob", "u", "eps_p", "Ebar"):
+        for key in ("phi_f", "phi_w", "xO", "xH", "xW", "alpha", "mob", "u", "eps_p", "Ebar", "theta", "phig"):
             v = fields.get(key)
             if v is None:
                 continue
@@ -98,7 +98,7 @@ def _in_fields(fields, where, N, ndim):
             keep.append(a)
             f.dirichlet = a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
     elif where == "device":
-        for key in ("phi_f", "phi_w", "xO", "xH", "xW", "alpha", "mob", "u", "eps_p", "Ebar"):
+        for key in ("phi_f", "phi_w", "xO", "xH", "xW", "alpha", "mob", "u", "eps_p", "Ebar", "theta", "phig"):
             t = fields.get(key)
             if t is not None:
                 t = t.contiguous()

@@ -297,6 +297,32 @@ __device__ void last_block_sums(const double *partials, int nb, double *result)
     block_sum_store<K>(v, result);
 }
 
+// Asynchronous global -> shared copies of one element (cp.async): the
+// thread goes on while the copy is in flight; commit groups the copies
+// issued since the last commit, wait<n> blocks until at most n of the
+// thread's groups are still pending (its own copies are then visible to
+// it; other threads see them after a block barrier).
+template <typename T>
+__device__ __forceinline__ void cp_async(T *smem, const T *gmem)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// 16-byte copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+
 // GPU-scope synchronisation primitives of the grid barrier: the arriving
 // thread's acq_rel add publishes its block's partial sums and, for the last
 // arrival, acquires every other block's; the last block's release add of the

@@ -57,7 +57,7 @@ struct CellJob {
     unsigned int *counter;   // last-block counter of the update
     Diag *dg;
     int block0, nblocks;
-    int strip_rows;          // unused by the current kernels
+    int strip_rows;          // k_fusedz: planes per chunk along the marching axis
 };
 
 // Job of this block: the last job whose first block is <= blockIdx.x (jobs
@@ -852,6 +852,346 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fused_cm(const 
             xe0 = xe1; xe1 = xe2; xe2 = xe3;
             dm = d0; d0 = d1;
         }
+    }
+    Acc<T> acc6[6];
+#pragma unroll
+    for (int q = 0; q < 5; q++) acc6[q] = acc[q];
+    acc6[5].add(T(bad ? 1 : 0));
+    double *partials = sJ.partials;
+    unsigned int *counter = sJ.counter;
+    block_reduce_store<6>(acc6, partials + (size_t)bid * PSTRIDE);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int tk = atomicAdd(counter, 1u);
+        last = (tk == (unsigned int)nbk - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        __shared__ double tot[6];
+        last_block_sums<6>(partials, nbk, tot);
+        if (threadIdx.x == 0) {
+            Diag *dg = sJ.dg;
+            dg->sumO_prev = dg->sumO;
+            dg->sumO = tot[0]; dg->sumH = tot[1]; dg->sumW = tot[2];
+            dg->removedW += tot[3];
+            dg->suppliedH += tot[4];
+            if (tot[5] > 0.0 && dg->status == 0) dg->status = 5;
+            *counter = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1 marching along the slowest axis (k_fusedz): the same arithmetic as
+// k_fused, with the grid cut into planes (3D: 32 x 8 cells of an x-y plane,
+// marching along z; 2D: 256-cell row segments, marching along y).  A block
+// walks a chunk of planes of one tile column: x_O with a halo of two cells
+// in the plane and theta, phi_g, x_H, x_H2O with a halo of one are copied
+// into ring buffers of planes by asynchronous copies (cp.async) issued one
+// plane ahead, so that their latency overlaps the work on the current
+// plane; mu_O, M_O, D_H, D_H2O are evaluated one plane ahead of the update
+// (the cross-plane neighbours come from the rings), and the plane's own
+// cells are updated.  Every field is read from HBM once per step plus the
+// in-plane halo (L2 hits) and the chunk's first planes.
+// ---------------------------------------------------------------------------
+template <int D>
+struct FusedZ {
+    static constexpr int TX = D == 3 ? 32 : 256, TY = D == 3 ? 8 : 1;
+    // shared-memory rows are RS values wide with the tile's first column at
+    // CO (16-byte aligned), so that the row interior is copied in 16-byte
+    // pieces; x_O keeps two halo columns each side, the other fields one
+    static constexpr int RS = TX + 8, CO = 4;
+    static constexpr int EY = D == 3 ? TY + 2 : 1, GY = D == 3 ? TY + 4 : 1;   // rows: halo 1 / halo 2
+    static constexpr int E = EY * RS, G = GY * RS;                             // values per plane
+    static constexpr int EX = TX + 2;                                          // halo-1 cells per row
+    static constexpr int NE = EX * EY;                                         // halo-1 cells per plane
+    // ring depths (planes): x_O and the raw fields hold the planes being
+    // read (update m - 1 .. m + 1 and the derived plane m + 1) plus the one
+    // in flight; mu, M, D_H, D_H2O three planes
+    static constexpr int RO = 5, RE = 5, RM = 3;
+    static constexpr int WORDS = RO * G + 4 * RE * E + 4 * RM * E;
+    static constexpr int NT = 256;
+    static_assert(TX * TY == NT, "one own cell per thread");
+    // copy tasks per plane on the aligned path: x_O rows of TX / 4 16-byte
+    // pieces plus four halo values, raw-field rows of TX / 4 pieces plus two
+    static constexpr int VW = TX / 4;
+    static constexpr int TO = GY * (VW + 4), TE = EY * (VW + 2);
+    static_assert(TO + TE <= NT, "one copy task per thread and plane");
+    static constexpr int DPT = (NE + NT - 1) / NT;                             // derived cells per thread
+};
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fusedz(const __grid_constant__ JobSet<CellJob<T, D>> js)
+{
+    using Z = FusedZ<D>;
+    constexpr int TX = Z::TX, TY = Z::TY, RS = Z::RS, CO = Z::CO, E = Z::E, G = Z::G, NT = Z::NT;
+    constexpr int EX = Z::EX, NE = Z::NE, VW = Z::VW, DPT = Z::DPT;
+    constexpr int XR = D == 3 ? 1 : 0;          // x_O row of raw-field row r is r + XR
+    extern __shared__ __align__(16) unsigned char fsz_raw[];
+    T *const sXO = (T *)fsz_raw;                                   // [RO][G]
+    T *const sTh = sXO + Z::RO * G, *const sPg = sTh + Z::RE * E;  // [RE][E] each
+    T *const sXH = sPg + Z::RE * E, *const sXW = sXH + Z::RE * E;
+    T *const sMu = sXW + Z::RE * E, *const sM = sMu + Z::RM * E;   // [RM][E] each
+    T *const sDH = sM + Z::RM * E, *const sDW = sDH + Z::RM * E;
+
+    __shared__ __align__(16) CellJob<T, D> sJ;
+    {
+        const CellJob<T, D> *J_ = my_job(js);
+        const int *src = (const int *)J_;
+        int *dst = (int *)&sJ;
+        for (int w = threadIdx.x; w < (int)(sizeof(CellJob<T, D>) / sizeof(int)); w += NT) dst[w] = src[w];
+    }
+    __syncthreads();
+    const Params &P = sJ.P;
+    const FieldPtrs<T, D> &F = sJ.F;
+    const int bid = (int)blockIdx.x - sJ.block0, nbk = sJ.nblocks;
+    const int nx = P.nx, ny = P.ny, nm = D == 3 ? P.nz : P.ny;     // nm: planes along the marching axis
+    const unsigned ps = D == 3 ? (unsigned)nx * (unsigned)ny : (unsigned)nx;   // cells per plane (grids < 2^31 cells)
+    const int ntx = (nx + TX - 1) / TX, nty = D == 3 ? (ny + TY - 1) / TY : 1;
+    const int zc = sJ.strip_rows, nch = (nm + zc - 1) / zc;
+    const int items = ntx * nty * nch;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    auto slot5 = [](int m) { return (m + 10) % 5; };              // m >= -3
+    auto slot3 = [](int m) { return (m + 3) % 3; };                // m >= -2
+    // this thread's derived cells (halo-1 cells of a plane): shared-memory
+    // index in a raw-field plane; the x_O plane's is RS * XR further
+    int dix[DPT];
+#pragma unroll
+    for (int u = 0; u < DPT; u++) {
+        const int l = threadIdx.x + u * NT;
+        dix[u] = l < NE ? (l / EX) * RS + (l % EX) + CO - 1 : -1;
+    }
+    const int eown = (D == 3 ? (ty + 1) * RS : 0) + tx + CO;     // own cell in a raw-field plane
+    Acc<T> acc[5];           // sum x_O, x_H, x_H2O, removed water, supplied H
+    bool bad = false;
+
+    for (int item = bid; item < items; item += nbk) {
+        const int x0 = (item % ntx) * TX, y0 = D == 3 ? ((item / ntx) % nty) * TY : 0;
+        const int m0 = (item / (ntx * nty)) * zc, m1 = min(m0 + zc, nm);
+        // in-plane offset of a (possibly out-of-range) position
+        auto off = [&](int x, int y) -> unsigned {
+            return (unsigned)pwrap(x, nx) + (D == 3 ? (unsigned)nx * (unsigned)pwrap(y, ny) : 0u);
+        };
+        // aligned path: the tile's columns lie inside the grid and rows start
+        // on 16-byte boundaries; this thread's copy task of every plane
+        const bool vec = (nx % 4) == 0 && x0 + TX <= nx;
+        int task = -1;               // 0: x_O piece / value, 1: raw-field piece / value
+        bool piece = false;
+        unsigned toff = 0;           // in-plane source offset
+        int tdst = 0;                // shared-memory offset within a plane
+        if (vec) {
+            const int t = threadIdx.x;
+            if (t >= Z::TE && t < Z::TE + Z::TO) {
+                task = 0;
+                const int r = (t - Z::TE) / (VW + 4), k = (t - Z::TE) % (VW + 4);
+                const int col = k < VW ? CO + 4 * k : (k - VW < 2 ? CO - 2 + (k - VW) : CO + TX + (k - VW - 2));
+                piece = k < VW;
+                toff = off(x0 - CO + col, y0 - 2 + r);
+                tdst = r * RS + col;
+            } else if (t < Z::TE) {
+                task = 1;
+                const int t2 = t, r = t2 / (VW + 2), k = t2 % (VW + 2);
+                const int col = k < VW ? CO + 4 * k : (k == VW ? CO - 1 : CO + TX);
+                piece = k < VW;
+                toff = off(x0 - CO + col, y0 - 1 + r);
+                tdst = r * RS + col;
+            }
+        }
+        auto issue_o = [&](int m) {
+            const unsigned pb = ps * (unsigned)pwrap(m, nm);
+            T *dst = sXO + slot5(m) * G;
+            if (vec) {
+                if (task == 0) {
+                    if (piece) {
+                        if constexpr (sizeof(T) == 4) cp_async16(dst + tdst, F.xO + (pb + toff));
+                        else { cp_async16(dst + tdst, F.xO + (pb + toff)); cp_async16(dst + tdst + 2, F.xO + (pb + toff + 2)); }
+                    } else {
+                        cp_async(dst + tdst, F.xO + (pb + toff));
+                    }
+                }
+                return;
+            }
+            for (int l = threadIdx.x; l < (TX + 4) * Z::GY; l += NT) {
+                const int c = l % (TX + 4), r = l / (TX + 4);
+                cp_async(dst + r * RS + c + CO - 2, F.xO + (pb + off(x0 - 2 + c, y0 - 2 + r)));
+            }
+        };
+        auto issue_e = [&](int m) {
+            const unsigned pb = ps * (unsigned)pwrap(m, nm);
+            const int so = slot5(m) * E;
+            if (vec) {
+                if (task == 1) {
+                    const unsigned g = pb + toff;
+                    const int d = so + tdst;
+                    if (piece) {
+                        if constexpr (sizeof(T) == 4) {
+                            cp_async16(sTh + d, F.theta + g); cp_async16(sPg + d, F.phig + g);
+                            cp_async16(sXH + d, F.xH + g); cp_async16(sXW + d, F.xW + g);
+                        } else {
+                            cp_async16(sTh + d, F.theta + g); cp_async16(sPg + d, F.phig + g);
+                            cp_async16(sXH + d, F.xH + g); cp_async16(sXW + d, F.xW + g);
+                            cp_async16(sTh + d + 2, F.theta + g + 2); cp_async16(sPg + d + 2, F.phig + g + 2);
+                            cp_async16(sXH + d + 2, F.xH + g + 2); cp_async16(sXW + d + 2, F.xW + g + 2);
+                        }
+                    } else {
+                        cp_async(sTh + d, F.theta + g); cp_async(sPg + d, F.phig + g);
+                        cp_async(sXH + d, F.xH + g); cp_async(sXW + d, F.xW + g);
+                    }
+                }
+                return;
+            }
+            for (int l = threadIdx.x; l < NE; l += NT) {
+                const int c = l % EX, r = l / EX;
+                const unsigned g = pb + off(x0 - 1 + c, y0 - 1 + r);
+                const int d = so + r * RS + c + CO - 1;
+                cp_async(sTh + d, F.theta + g);
+                cp_async(sPg + d, F.phig + g);
+                cp_async(sXH + d, F.xH + g);
+                cp_async(sXW + d, F.xW + g);
+            }
+        };
+        // mu_O, M_O (Sec. 2.2, 3.2) and the species diffusivities (R4) of
+        // plane m, own cells plus one halo cell in the plane
+        auto derive = [&](int m) {
+            const CellConst<T> &K = sJ.K;
+            const T *xo = sXO + slot5(m) * G, *xlo = sXO + slot5(m - 1) * G, *xhi = sXO + slot5(m + 1) * G;
+            const int se = slot5(m) * E, sm = slot3(m) * E;
+#pragma unroll
+            for (int u = 0; u < DPT; u++) {
+                const int l = dix[u];
+                if (l < 0) continue;
+                const int q = l + RS * XR;
+                const T x = xo[q];
+                T lap;
+                if constexpr (D == 3) {
+                    lap = xo[q - 1] + xo[q + 1] + xo[q - RS] + xo[q + RS] - T(2 * D) * x;
+                    lap += xlo[q] + xhi[q];
+                } else {
+                    lap = xo[q - 1] + xo[q + 1] + xlo[q] + xhi[q] - T(2 * D) * x;
+                }
+                T Wf, Ww, Wg;
+                phase_weights(sTh[se + l], sPg[se + l], Wf, Ww, Wg);
+                const T m1_ = Wf * f_fe1(x) + Ww * f_wu1(x) + Wg * f_ga1(x);
+                const T m2_ = Wf * f_fe2(x) + Ww * f_wu2(x) + Wg * f_ga2(x);
+                sMu[sm + l] = K.c * m1_ - K.kappa * lap;
+                const T DO = (T(1) - Wg) * K.DOs + Wg * K.DOg;
+                const T den = K.c * m2_;
+                sM[sm + l] = den != T(0) ? fast_div(DO, den) : T(0);
+                sDH[sm + l] = (T(1) - Wg) * K.DHs + Wg * K.DHg;
+                sDW[sm + l] = (T(1) - Wg) * K.DWs + Wg * K.DWg;
+            }
+        };
+        const int gxo = x0 + tx, gyo = y0 + ty;
+        const bool own = gxo < nx && (D == 2 || gyo < ny);
+        const unsigned goff = (unsigned)gxo + (D == 3 ? (unsigned)nx * (unsigned)gyo : 0u);
+        // start-up: x_O planes m0 - 2 .. m0 + 1 and raw planes m0 - 1, m0 in
+        // one group, x_O m0 + 2 and raw m0 + 1 in the next (the first
+        // iteration's), then mu etc. of planes m0 - 1 and m0
+        issue_o(m0 - 2);
+        issue_o(m0 - 1);
+        issue_o(m0);
+        issue_o(m0 + 1);
+        issue_e(m0 - 1);
+        issue_e(m0);
+        cp_async_commit();
+        issue_o(m0 + 2);
+        issue_e(m0 + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        derive(m0 - 1);
+        derive(m0);
+        // per-cell inputs of the first plane
+        T tE = T(0), s2 = T(0), mob = T(0);
+        unsigned char msk = 0;
+        if (own) {
+            const unsigned g = goff + ps * (unsigned)m0;
+            tE = F.trE[g]; s2 = F.devE2[g]; mob = F.mob[g]; msk = F.mask[g];
+        }
+        for (int m = m0; m < m1; m++) {
+            // the next plane's copies go out first (group of plane m + 1 for
+            // the raw fields, m + 2 for x_O is already in flight), then this
+            // iteration waits for the group issued one iteration ago
+            if (m + 1 < m1) {
+                issue_o(m + 3);
+                issue_e(m + 2);
+            }
+            cp_async_commit();
+            cp_async_wait<1>();
+            // the next plane's per-cell inputs (registers)
+            T tEn = T(0), s2n = T(0), mobn = T(0);
+            unsigned char mskn = 0;
+            if (own && m + 1 < m1) {
+                const unsigned gn = goff + ps * (unsigned)(m + 1);
+                tEn = F.trE[gn]; s2n = F.devE2[gn]; mobn = F.mob[gn]; mskn = F.mask[gn];
+            }
+            __syncthreads();
+            derive(m + 1);
+            __syncthreads();
+            if (own) {
+                const CellConst<T> &K = sJ.K;
+                const unsigned g = goff + ps * (unsigned)m;
+                const int e = eown;
+                const int sc = slot5(m) * E, sl = slot5(m - 1) * E, sh = slot5(m + 1) * E;
+                const int mc = slot3(m) * E, ml = slot3(m - 1) * E, mh = slot3(m + 1) * E;
+                const T th = sTh[sc + e], pg = sPg[sc + e];
+                const T xo = sXO[slot5(m) * G + e + RS * XR];
+                const T xh = sXH[sc + e], xw = sXW[sc + e];
+                const T mu0 = sMu[mc + e], M0 = sM[mc + e], DH0 = sDH[mc + e], DW0 = sDW[mc + e];
+                // neighbours in the order x-, x+, y-, y+ (, z-, z+): in-plane
+                // offsets, then the planes before and after
+                int ro[2 * D], mo[2 * D];
+                ro[0] = sc + e - 1; ro[1] = sc + e + 1;
+                mo[0] = mc + e - 1; mo[1] = mc + e + 1;
+                if constexpr (D == 3) {
+                    ro[2] = sc + e - RS; ro[3] = sc + e + RS; ro[4] = sl + e; ro[5] = sh + e;
+                    mo[2] = mc + e - RS; mo[3] = mc + e + RS; mo[4] = ml + e; mo[5] = mh + e;
+                } else {
+                    ro[2] = sl + e; ro[3] = sh + e;
+                    mo[2] = ml + e; mo[3] = mh + e;
+                }
+                T lapt = T(0), dO = T(0), dH = T(0), dW = T(0);
+#pragma unroll
+                for (int qn = 0; qn < 2 * D; qn++) {
+                    const int a = ro[qn], b = mo[qn];
+                    lapt += sTh[a] - th;
+                    dO += T(0.5) * (M0 + sM[b]) * (sMu[b] - mu0);
+                    dH += T(0.5) * (DH0 + sDH[b]) * (sXH[a] - xh);
+                    dW += T(0.5) * (DW0 + sDW[b]) * (sXW[a] - xw);
+                }
+                const T hg0 = hfun(pg);
+                const T hpt = hder(th);
+                const T sol = T(1) - hg0;
+                const T Af = K.c * f_fe(xo) + T(0.5) * K.Ks * tE * tE + K.Gs * s2;
+                const T Aw = K.c * f_wu(xo) + T(0.5) * K.Ks * tE * tE + K.Gs * s2;
+                const T Kmix = sol * K.Ks + hg0 * K.Kg;
+                const T force = sol * hpt * (Af - Aw) + K.w2 * mder(th) - K.eig3 * sol * hpt * Kmix * tE;
+                const T rate = K.Lh * mob * (force - K.eps2 * lapt);
+                T rr = mfun(pg) * K.kf * xo * xh;
+                if (xw >= T(1)) rr = T(0);
+                const T nth = th + K.dt * rate;
+                const T nxo = xo + K.dt * (dO - rr);
+                T nxh = xh + K.dt * (dH - T(2) * rr);
+                T nxw = xw + K.dt * (dW + rr);
+                if (msk) {
+                    acc[3].add(nxw);
+                    acc[4].add(K.xHbc - nxh);
+                    nxh = K.xHbc;
+                    nxw = T(0);
+                }
+                F.theta_o[g] = nth;
+                F.xO_o[g] = nxo;
+                F.xH_o[g] = nxh;
+                F.xW_o[g] = nxw;
+                acc[0].add(nxo); acc[1].add(nxh); acc[2].add(nxw);
+                bad |= !isfinite(nth + nxo + nxh + nxw);
+            }
+            tE = tEn; s2 = s2n; mob = mobn; msk = mskn;
+        }
+        cp_async_wait<0>();
+        __syncthreads();       // the next item's copies reuse every ring slot
     }
     Acc<T> acc6[6];
 #pragma unroll

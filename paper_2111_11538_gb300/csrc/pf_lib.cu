@@ -208,6 +208,7 @@ struct pf_handle {
     void *d_pcg_jobs = nullptr;
     int cell_grid = 0, fused_grid = 0, pcg_grid = 0, njobs = 0;
     int cg_per_sm = 0;
+    int fused_per_sm = 0;               // resident blocks per SM of the marching update
     int pcg_shape = 0;                  // node tile of the PCG sweep (pf_cg.cuh Tile<D, S>)
     bool mg = false;                    // multigrid-preconditioned CG (pf_mg.cuh)
     double *b64[3] = {};                // MG mixed method: FP64 right-hand side kept across passes
@@ -542,36 +543,48 @@ PCGArgs<T, D> pcg_args(pf_handle *m)
     return A;
 }
 
-// Tile of the fused update (k_fused): 2D 32 x 16 cells, 3D 32 x 4 x 4.
-template <int D> struct FusedShape;
-template <> struct FusedShape<2> { static constexpr int X = 32, Y = 16, Z = 1; };
-template <> struct FusedShape<3> { static constexpr int X = 32, Y = 4, Z = 4; };
-
 template <typename T, int D>
 size_t fused_smem()
 {
-    using S = FusedShape<D>;
-    return sizeof(T) * FusedTile<D, S::X, S::Y, S::Z>::WORDS;
+    return sizeof(T) * FusedZ<D>::WORDS;
 }
 
 template <typename T, int D>
 int prepare_fused(pf_handle *h)
 {
-    using S = FusedShape<D>;
-    cudaError_t e = cudaFuncSetAttribute(k_fused<T, D, S::X, S::Y, S::Z>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_fusedz<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)fused_smem<T, D>());
+    if (e == cudaSuccess && !h->fused_per_sm)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->fused_per_sm, k_fusedz<T, D>, 256, fused_smem<T, D>());
     return h->cuda(e, "fused kernel shared memory");
 }
 
 template <typename T, int D>
 void launch_fused(int grid, const JobSet<CellJob<T, D>> &js, cudaStream_t s)
 {
-    if constexpr (D == 2) {
-        k_fused_cm<T><<<grid, 256, 0, s>>>(js);      // column strips, no shared-memory tile
-    } else {
-        using S = FusedShape<D>;
-        k_fused<T, D, S::X, S::Y, S::Z><<<grid, 256, fused_smem<T, D>(), s>>>(js);
+    k_fusedz<T, D><<<grid, 256, fused_smem<T, D>(), s>>>(js);
+}
+
+// Chunk length (planes along the marching axis) of the marching update for
+// a grid with `cols` tile columns and nm planes, and its block count: the
+// length that minimises (work items per block, rounded up) x (planes per
+// item + 3, the chunk's start-up planes), with at most cap blocks.
+int fused_chunk(long long cols, int nm, long long cap, int &nblocks)
+{
+    int best = nm;
+    long long bcost = -1;
+    for (int zc = 1; zc <= nm; zc++) {
+        const long long items = cols * ((nm + zc - 1) / zc);
+        const long long nb = std::min(items, cap);
+        const long long cost = ((items + nb - 1) / nb) * (zc + 3);
+        if (bcost < 0 || cost < bcost) {
+            bcost = cost;
+            best = zc;
+        }
     }
+    const long long items = cols * ((nm + best - 1) / best);
+    nblocks = (int)std::max<long long>(1, std::min(items, cap));
+    return best;
 }
 
 // Build the job tables of every instance: cell kernels get ~N/256 blocks per
@@ -580,7 +593,6 @@ void launch_fused(int grid, const JobSet<CellJob<T, D>> &js, cudaStream_t s)
 template <typename T, int D>
 int build_plan(pf_handle *h)
 {
-    constexpr int FX = FusedShape<D>::X, FY = FusedShape<D>::Y, FZ = FusedShape<D>::Z;
     PF_TRY((prepare_fused<T, D>(h)));
     std::vector<pf_handle *> I = instances(h);
     const int n = (int)I.size();
@@ -611,25 +623,18 @@ int build_plan(pf_handle *h)
     }
     h->cell_grid = b0;
     h->njobs = n;
-    // blocks of the fused update per instance: 3D walks halo tiles (up to 8
-    // blocks per SM), 2D walks column strips (below)
+    // blocks of the marching update per instance: one wave of resident
+    // blocks at most, each walking chunks of planes of its tile columns
     std::vector<CellJob<T, D>> fj[2] = {cj[0], cj[1]};
     int f0 = 0;
     for (int i = 0; i < n; i++) {
         const Params &P = I[i]->P;
-        long long nt = (long long)((P.nx + FX - 1) / FX) * ((P.ny + FY - 1) / FY) * (D == 3 ? (P.nz + FZ - 1) / FZ : 1);
-        long long cap = (long long)h->sms * 8;
-        if (D == 2) {
-            // column strips (k_fused_cm, 30 output columns each, groups of
-            // 8 strips per block of 8 warps, 3 blocks per SM): at most one
-            // wave of resident blocks, and at least ~8 rows per block so the
-            // window start-up stays small
-            const long long rows = (long long)(((P.nx + 29) / 30 + 7) / 8) * P.ny;
-            nt = (rows + 7) / 8;
-            cap = (long long)h->sms * 3;
-        }
-        const int nb = (int)std::max<long long>(1, std::min<long long>(nt, cap));
-        for (int k = 0; k < 2; k++) { fj[k][i].block0 = f0; fj[k][i].nblocks = nb; }
+        const long long cols = (long long)((P.nx + FusedZ<D>::TX - 1) / FusedZ<D>::TX) *
+                               (D == 3 ? (P.ny + FusedZ<D>::TY - 1) / FusedZ<D>::TY : 1);
+        const long long cap = (long long)h->sms * std::max(1, h->fused_per_sm);
+        int nb = 1;
+        const int zc = fused_chunk(cols, D == 3 ? P.nz : P.ny, cap, nb);
+        for (int k = 0; k < 2; k++) { fj[k][i].block0 = f0; fj[k][i].nblocks = nb; fj[k][i].strip_rows = zc; }
         f0 += nb;
     }
     h->fused_grid = f0;
@@ -849,6 +854,15 @@ int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
         PF_SRC(pw, f->phi_w, nb, h->stage2);
         k_in_phase<T><<<g, 256, 0, s>>>(N, pf, pw, (T *)h->theta[0], (T *)h->phig);
     }
+    if (f->theta) {
+        // the order parameter itself (exact restore, also where phi_g = 1)
+        PF_SRC(a, f->theta, nb, h->stage);
+        k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->theta[0], 0.0);
+    }
+    if (f->phi_g) {
+        PF_SRC(a, f->phi_g, nb, h->stage2);
+        k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->phig, 0.0);
+    }
     {
         PF_SRC(a, f->x_O, nb, h->stage);
         k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->xO[0], 0.0);
@@ -955,7 +969,8 @@ int get_fields_t(pf_handle *h, pf_fields *f, int where, cudaStream_t s)
         PF_TRY(h->cuda(cudaStreamSynchronize(s), "get sync"));
     }
     struct One { double *dst; const void *src; };
-    One ones[4] = {{f->x_O, h->xO[c]}, {f->x_H, h->xH[c]}, {f->x_H2O, h->xW[c]}, {f->alpha, h->alpha}};
+    One ones[6] = {{f->x_O, h->xO[c]}, {f->x_H, h->xH[c]}, {f->x_H2O, h->xW[c]}, {f->alpha, h->alpha},
+                   {f->theta, h->theta[c]}, {f->phi_g, h->phig}};
     for (auto &o : ones) {
         if (!o.dst) continue;
         k_out_scalar<T><<<g, 256, 0, s>>>(N, (const T *)o.src, out(o.dst, h->stage));

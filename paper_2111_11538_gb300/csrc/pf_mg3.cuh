@@ -75,14 +75,22 @@ __device__ __forceinline__ void corner_forces3(const TC *s, const TC *g, TC (&f)
 }
 
 // Tile of the z-marching 3D sweep: TX x TY nodes per plane, one thread each.
-constexpr int MGZ_TX = 32, MGZ_TY = 8;
+constexpr int MGZ_TX = 32, MGZ_TY = 8, MGZ_NP = (MGZ_TX + 2) * (MGZ_TY + 2);
+// Streams (arrays read at a staged node) a sweep's operand is formed from,
+// at most; and whether they are copied into shared memory one plane ahead
+// (asynchronous copies, FP32) or read when the plane is staged (FP64, whose
+// sweeps are bound by the FP64 pipe rather than by memory latency).
+constexpr int MGZ_NS = 10;
+template <typename T> struct MGZPipe { static constexpr bool on = sizeof(T) == 4; static constexpr int RB = on ? 2 : 1; };
 
-// Shared memory (values of T) of mg_sweep3z: two node planes and the eight
-// corner forces of one cell plane, with their halos.
+// Shared memory (values of T) of mg_sweep3z: two node planes, the eight
+// corner forces of one cell plane with their halos, and the staged nodes'
+// raw streams (two planes when they are copied ahead).
 template <typename T>
 __host__ __device__ constexpr int mg_sweep3z_words()
 {
-    return V3S<T>::WORDS * (2 * (MGZ_TX + 2) * (MGZ_TY + 2) + 8 * (MGZ_TX + 1) * (MGZ_TY + 1));
+    return V3S<T>::WORDS * (2 * (MGZ_TX + 2) * (MGZ_TY + 2) + 8 * (MGZ_TX + 1) * (MGZ_TY + 1)) +
+           MGZPipe<T>::RB * MGZ_NS * (MGZ_TX + 2) * (MGZ_TY + 2);
 }
 
 // z-chunk of the 3D sweep on an nx x ny x nz level with nbk blocks: the
@@ -109,55 +117,115 @@ __device__ __forceinline__ int mg_zchunk(int nx, int ny, int nz, int nbk)
 
 // One 3D sweep of the level's Q1 operator, marching along z.  A work item is
 // a TX x TY column of node tiles over zc planes.  Per cell plane zp: the node
-// plane zp + 1 (with its one-node halo in x and y) is staged by val(gx, gy,
-// gz, v), every cell of the plane (with the halo cells at x0 - 1, y0 - 1)
-// computes its average stress and hourglass forces once (cell_force3) and
-// its forces on its eight corners (corner_forces3), and each own node of
-// plane zp adds its bottom-corner forces to the top-corner forces left by
-// plane zp - 1: q = A v is complete and epi(n, v, q) receives it.  WITH_E:
-// the mean strain ue enters every cell's stress, and cell_e(c) receives the
-// stress of every own cell without it (c[0..5]).  smem: mg_sweep3z_words<T>()
-// values; two block barriers per plane.
-template <typename T, bool WITH_E, class Val, class Epi, class CellE>
+// plane zp + 1 (with its one-node halo in x and y) is formed by
+// make(raw, h, gx, gy, gz, v) from its ns raw streams src[0 .. ns) (FP32:
+// copied into shared memory one plane ahead, so that their latency overlaps
+// the previous plane's work; raw[s * NP + h] is stream s at staged node h),
+// every cell of the plane (with the halo cells at x0 - 1, y0 - 1) computes
+// its average stress and hourglass forces once (cell_force3; its moduli are
+// read one plane ahead) and its forces on its eight corners
+// (corner_forces3), and each own node of plane zp adds its bottom-corner
+// forces to the top-corner forces left by plane zp - 1: q = A v is complete
+// and epi(n, v, q) receives it.  WITH_E: the mean strain ue enters every
+// cell's stress, and cell_e(c) receives the stress of every own cell
+// without it (c[0..5]).  smem: mg_sweep3z_words<T>() values; src: ns
+// pointers (shared memory, set by the caller); two block barriers per plane.
+template <typename T, bool WITH_E, class Make, class Epi, class CellE>
 __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const T *lam, const T *mu, int bid,
-                                           int nbk, T *smem, const T *ue, Val &&val, Epi &&epi, CellE &&cell_e)
+                                           int nbk, T *smem, const T *ue, int ns, const T *const *src, Make &&make,
+                                           Epi &&epi, CellE &&cell_e)
 {
     constexpr int TX = MGZ_TX, TY = MGZ_TY;
     constexpr int NX = TX + 2, NY = TY + 2, NP = NX * NY;
     constexpr int CX = TX + 1, CY = TY + 1, NC = CX * CY, NT = TX * TY;
     constexpr int W = V3S<T>::WORDS;
+    constexpr bool PIPE = MGZPipe<T>::on;
+    constexpr int CPT = (NC + NT - 1) / NT;                 // cells per thread
     T *const np0 = smem, *const np1 = smem + W * NP, *const cf = smem + 2 * W * NP;
+    T *const rawb = cf + 8 * W * NC;                        // [RB][MGZ_NS][NP]
     const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, nzc = (nz + zc - 1) / zc;
     const int items = ntx * nty * nzc;
     const bool small = nx < NX || ny < NY;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    auto zwrap = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
     for (int item = bid; item < items; item += nbk) {
         const int x0 = (item % ntx) * TX, y0 = ((item / ntx) % nty) * TY, z0 = (item / (ntx * nty)) * zc;
         const int z1 = min(z0 + zc, nz);
         const int gx = x0 + tx, gy = y0 + ty;
         const bool own = gx < nx && gy < ny;
-        auto stage = [&](int z, T *buf) {
-            const int zw = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+        auto raw_of = [&](int z) { return rawb + (PIPE ? (z & 1) : 0) * (MGZ_NS * NP); };
+        // raw streams of node plane z: asynchronous copies (FP32) or loads
+        auto issue = [&](int z) {
+            const int zw = zwrap(z);
+            T *raw = raw_of(z);
+            for (int h = threadIdx.x; h < NP; h += NT) {
+                const int lx = h % NX, ly = h / NX;
+                const int g = mg_wrap(x0 - 1 + lx, nx, small) + nx * (mg_wrap(y0 - 1 + ly, ny, small) + ny * zw);
+                for (int q = 0; q < ns; q++) {
+                    if constexpr (PIPE) cp_async(raw + q * NP + h, src[q] + g);
+                    else raw[q * NP + h] = __ldcg(src[q] + g);
+                }
+            }
+        };
+        // node plane z formed from its raw streams (each thread forms the
+        // nodes whose streams it copied)
+        auto form = [&](int z, T *buf) {
+            const int zw = zwrap(z);
+            const T *raw = raw_of(z);
             for (int h = threadIdx.x; h < NP; h += NT) {
                 const int lx = h % NX, ly = h / NX;
                 T v[3];
-                val(mg_wrap(x0 - 1 + lx, nx, small), mg_wrap(y0 - 1 + ly, ny, small), zw, v);
+                make(raw, h, mg_wrap(x0 - 1 + lx, nx, small), mg_wrap(y0 - 1 + ly, ny, small), zw, v);
                 V3S<T>::st(buf, NP, h, v);
             }
         };
-        stage(z0 - 1, ((z0 - 1) & 1) ? np1 : np0);
+        // moduli of this thread's cells of plane z
+        auto moduli = [&](int z, T (&l)[CPT], T (&m)[CPT]) {
+            const int zw = zwrap(z);
+#pragma unroll
+            for (int u = 0; u < CPT; u++) {
+                const int h = threadIdx.x + u * NT;
+                if (h < NC) {
+                    const int cx = h % CX, cy = h / CX;
+                    const int g = mg_wrap(x0 - 1 + cx, nx, small) + nx * (mg_wrap(y0 - 1 + cy, ny, small) + ny * zw);
+                    l[u] = __ldcg(lam + g);
+                    m[u] = __ldcg(mu + g);
+                }
+            }
+        };
+        issue(z0 - 1);
+        if constexpr (PIPE) {
+            cp_async_commit();
+            issue(z0);
+            cp_async_commit();
+            cp_async_wait<1>();
+        }
+        form(z0 - 1, ((z0 - 1) & 1) ? np1 : np0);
+        T lc[CPT], mc[CPT];
+        moduli(z0 - 1, lc, mc);
         T qt[3] = {T(0), T(0), T(0)};     // top-corner forces of the previous cell plane on the own node
         for (int zp = z0 - 1; zp < z1; zp++) {
             T *const nlo = (zp & 1) ? np1 : np0;
             T *const nhi = (zp & 1) ? np0 : np1;
-            stage(zp + 1, nhi);
+            if constexpr (PIPE) {
+                // copies of plane zp + 2 go out; plane zp + 1's have landed
+                if (zp + 2 <= z1) issue(zp + 2);
+                cp_async_commit();
+                cp_async_wait<1>();
+            } else {
+                issue(zp + 1);
+            }
+            form(zp + 1, nhi);
+            T ln[CPT], mn[CPT];
+            if (zp + 1 < z1) moduli(zp + 1, ln, mn);
             __syncthreads();
-            const int zw = zp < 0 ? zp + nz : zp;
             const bool inner = zp >= z0;
-            for (int h = threadIdx.x; h < NC; h += NT) {
+#pragma unroll
+            for (int u = 0; u < CPT; u++) {
+                const int h = threadIdx.x + u * NT;
+                if (h >= NC) continue;
                 const int cx = h % CX, cy = h / CX;
-                const int g = mg_wrap(x0 - 1 + cx, nx, small) + nx * (mg_wrap(y0 - 1 + cy, ny, small) + ny * zw);
-                const T l = __ldcg(lam + g), m = __ldcg(mu + g);
+                const T l = lc[u], m = mc[u];
                 T uc[8][3];
 #pragma unroll
                 for (int b = 0; b < 8; b++) V3S<T>::ld((b >> 2) ? nhi : nlo, NP, (cx + (b & 1)) + NX * (cy + ((b >> 1) & 1)), uc[b]);
@@ -177,6 +245,10 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
             }
             T un[3];
             if (own && inner) V3S<T>::ld(nlo, NP, (tx + 1) + NX * (ty + 1), un);
+            if (zp + 1 < z1) {
+#pragma unroll
+                for (int u = 0; u < CPT; u++) { lc[u] = ln[u]; mc[u] = mn[u]; }
+            }
             __syncthreads();
             if (own) {
                 // cells around the node in this plane: (tx, ty) is its lower-left
@@ -208,6 +280,7 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
                 if (inner) epi(gx + nx * (gy + ny * zp), un, fb);
             }
         }
+        if constexpr (PIPE) cp_async_wait<0>();
     }
 }
 
@@ -393,10 +466,16 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
         for (int k = 0; k < L; k++) s_zc[k] = mg_zchunk(H.lv[k].nx, H.lv[k].ny, H.lv[k].nz, nbk);
     __syncthreads();
     auto none = [](const T *) {};
-    auto sweep = [&](int k, auto &&val, auto &&epi) {
+    // the streams of the next sweep (shared memory; every sweep is preceded
+    // by a grid or block barrier after its streams are set)
+    __shared__ const T *s_src[MGZ_NS];
+    auto sweep = [&](int k, int ns, auto &&setsrc, auto &&make, auto &&epi) {
         const MGLevel<T> &V = H.lv[k];
-        mg_sweep3z<T, false>(V.nx, V.ny, V.nz, s_zc[k], V.lam, V.mu, bid, nbk, smem, nullptr, val, epi, none);
+        if (lead) setsrc(s_src);
+        __syncthreads();
+        mg_sweep3z<T, false>(V.nx, V.ny, V.nz, s_zc[k], V.lam, V.mu, bid, nbk, smem, nullptr, ns, s_src, make, epi, none);
     };
+    constexpr int NP = MGZ_NP;
 
     // Chebyshev step j on level k (buffer par -> 1 - par); last: also apply
     // step j + 1 and leave the final correction in xpost
@@ -404,14 +483,17 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
         const MGLevel<T> &V = H.lv[k];
         T *const *X = post ? V.xpost : V.xpre;
         const T c1 = H.c1[j], c2 = H.c2[j], n1 = H.c1[j + 1], n2 = H.c2[j + 1];
-        sweep(k,
-            [&](int gx, int gy, int gz, T (&v)[3]) {
-                const int g = lin3(V, gx, gy, gz);
-                const T di = c2 * __ldcg(V.dinv + g);
+        sweep(k, j > 0 ? 7 : 4,
+            [&](const T **src) {
+                src[0] = V.dinv;
+                for (int c = 0; c < 3; c++) { src[1 + c] = V.r[par][c]; src[4 + c] = V.d[par][c]; }
+            },
+            [&](const T *raw, int h, int, int, int, T (&v)[3]) {
+                const T di = c2 * raw[h];
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    T a = di * __ldcg(V.r[par][c] + g);
-                    if (j > 0) a += c1 * __ldcg(V.d[par][c] + g);
+                    T a = di * raw[(1 + c) * NP + h];
+                    if (j > 0) a += c1 * raw[(4 + c) * NP + h];
                     v[c] = a;
                 }
             },
@@ -457,11 +539,11 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
     auto pre_first = [&](int k) {
         const MGLevel<T> &V = H.lv[k];
         const T c2 = H.c2[0];
-        sweep(k,
-            [&](int gx, int gy, int gz, T (&v)[3]) {
+        sweep(k, 1, [&](const T **src) { src[0] = V.dinv; },
+            [&](const T *raw, int h, int gx, int gy, int gz, T (&v)[3]) {
                 T f[3];
                 restrict3(k, gx, gy, gz, f);
-                const T di = c2 * __ldcg(V.dinv + lin3(V, gx, gy, gz));
+                const T di = c2 * raw[h];
 #pragma unroll
                 for (int c = 0; c < 3; c++) v[c] = di * f[c];
             },
@@ -483,9 +565,8 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
     auto post_first = [&](int k, int par, int cur, bool last) {
         const MGLevel<T> &V = H.lv[k];
         const MGLevel<T> &C = H.lv[k + 1];
-        sweep(k,
-            [&](int gx, int gy, int gz, T (&v)[3]) {
-                const int g = lin3(V, gx, gy, gz);
+        sweep(k, 3, [&](const T **src) { for (int c = 0; c < 3; c++) src[c] = V.xpre[c]; },
+            [&](const T *raw, int h, int gx, int gy, int gz, T (&v)[3]) {
                 const int o[3] = {gx & 1, gy & 1, gz & 1}, ic[3] = {gx >> 1, gy >> 1, gz >> 1};
                 const int nc[3] = {C.nx, C.ny, C.nz};
                 int i1[3];
@@ -501,7 +582,7 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                             for (int c = 0; c < 3; c++) e[c] += __ldcg(C.xpost[c] + ci);
                         }
 #pragma unroll
-                for (int c = 0; c < 3; c++) v[c] = __ldcg(V.xpre[c] + g) + w * e[c];
+                for (int c = 0; c < 3; c++) v[c] = raw[c * NP + h] + w * e[c];
             },
             [&](int n, const T (&v)[3], const T (&q)[3]) {
                 const T di = last ? H.c2[0] * __ldcg(V.dinv + n) : T(0);
@@ -561,14 +642,17 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
         Acc<T> racc[1];
         {
             const T c2 = H.c2[0];
-            sweep(0,
-                [&](int gx, int gy, int gz, T (&v)[3]) {
-                    const int g = lin3(L0, gx, gy, gz);
-                    const T di = c2 * __ldcg(L0.dinv + g);
+            sweep(0, first ? 4 : 10,
+                [&](const T **src) {
+                    src[0] = L0.dinv;
+                    for (int c = 0; c < 3; c++) { src[1 + c] = A.r[cur][c]; src[4 + c] = A.w[cur][c]; src[7 + c] = A.s[cur][c]; }
+                },
+                [&](const T *raw, int h, int, int, int, T (&v)[3]) {
+                    const T di = c2 * raw[h];
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
-                        T rv = __ldcg(A.r[cur][c] + g);
-                        if (!first) rv -= ta * (__ldcg(A.w[cur][c] + g) + tb * __ldcg(A.s[cur][c] + g));
+                        T rv = raw[(1 + c) * NP + h];
+                        if (!first) rv -= ta * (raw[(4 + c) * NP + h] + tb * raw[(7 + c) * NP + h]);
                         v[c] = di * rv;
                     }
                 },
@@ -630,12 +714,14 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
 
         // ---- u = V-cycle result, w = A u (+ mean strain), gamma, delta, mean-strain row
         Acc<T> acc[2 + NV];
+        if (lead)
+            for (int c = 0; c < 3; c++) s_src[c] = L0.xpost[c];
+        __syncthreads();
         mg_sweep3z<T, true>(
-            L0.nx, L0.ny, L0.nz, s_zc[0], L0.lam, L0.mu, bid, nbk, smem, s_ue,
-            [&](int gx, int gy, int gz, T (&v)[3]) {
-                const int g = lin3(L0, gx, gy, gz);
+            L0.nx, L0.ny, L0.nz, s_zc[0], L0.lam, L0.mu, bid, nbk, smem, s_ue, 3, s_src,
+            [&](const T *raw, int h, int, int, int, T (&v)[3]) {
 #pragma unroll
-                for (int c = 0; c < 3; c++) v[c] = __ldcg(L0.xpost[c] + g);
+                for (int c = 0; c < 3; c++) v[c] = raw[c * NP + h];
             },
             [&](int n, const T (&v)[3], const T (&q)[3]) {
 #pragma unroll

@@ -48,7 +48,8 @@ _DP = ctypes.POINTER(ctypes.c_double)
 class pf_fields(ctypes.Structure):
     _fields_ = [("phi_f", _DP), ("phi_w", _DP), ("x_O", _DP), ("x_H", _DP), ("x_H2O", _DP),
                 ("u", _DP), ("Ebar", _DP), ("eps_p", _DP), ("alpha", _DP), ("sigma", _DP),
-                ("mobility", _DP), ("dirichlet", ctypes.POINTER(ctypes.c_ubyte))]
+                ("mobility", _DP), ("dirichlet", ctypes.POINTER(ctypes.c_ubyte)), ("theta", _DP),
+                ("phi_g", _DP)]
 
 
 class pf_diag(ctypes.Structure):

@@ -108,6 +108,38 @@ def test_batch_full_size(orc):
         _balances(b.diagnostics(i), fi)
 
 
+def test_mixed_against_oracle_from_fp64_snapshot(orc):
+    """The 512^2 J2 workload in the configuration the benchmark times for it
+    (mixed method: FP32 multigrid V-cycles inside FP64 refinement to rtol
+    1e-8, the extrapolated guess) against the oracle over a short window:
+    the library's FP64 state after 12 steps is loaded into both, which then
+    take 3 steps (the mixed method's extrapolation history restarts at the
+    load, as the oracle's guess does); 1e-4 on the fields, 1e-3 on the
+    stress."""
+    name = "coreshell512"
+    f = workloads.build_fields(name)
+    shape = f["phi_f"].shape
+    sim = Simulation(shape, _lib_params(name), precision="fp64")
+    sim.set_fields(f)
+    sim.step(12)
+    snap = sim.get_fields()
+    sim.close()
+    snap["mob"], snap["mask"] = f["mob"], f["mask"]
+    mixed = Simulation(shape, _lib_params(name), precision="mixed")
+    mixed.set_fields(snap)
+    mixed.step(3)
+    g = mixed.get_fields()
+    mixed.close()
+    ref = orc.Sim(snap, workloads.WORKLOADS[name]["params"])
+    ref.step(3)
+    exp = {"phi_f": ref.phi_f, "phi_w": ref.phi_w, "xO": ref.f["xO"], "xH": ref.f["xH"], "xW": ref.f["xW"]}
+    for k in exp:
+        r = np.linalg.norm(g[k] - exp[k]) / np.linalg.norm(exp[k])
+        assert r < 1e-4, (k, r)
+    r = np.linalg.norm(g["sigma"] - ref.f["sigma"]) / np.linalg.norm(ref.f["sigma"])
+    assert r < 1e-3, r
+
+
 def test_mixed_against_fp64_headline():
     """The benchmark's mixed method stays within the mixed parity tolerance
     (1e-4 on the fields, 1e-3 on the stress) of the FP64 method on the
