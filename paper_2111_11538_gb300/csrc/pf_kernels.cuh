@@ -1106,6 +1106,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fusedz(const __
         // per-cell inputs of the first plane
         T tE = T(0), s2 = T(0), mob = T(0);
         unsigned char msk = 0;
+        T cTh[3], cXH[3], cXW[3], cMu[3], cM[3], cDH[3], cDW[3];   // own cell, planes m - 1, m, m + 1
         if (own) {
             const unsigned g = goff + ps * (unsigned)m0;
             tE = F.trE[g]; s2 = F.devE2[g]; mob = F.mob[g]; msk = F.mask[g];
@@ -1134,33 +1135,47 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fusedz(const __
                 const CellConst<T> &K = sJ.K;
                 const unsigned g = goff + ps * (unsigned)m;
                 const int e = eown;
-                const int sc = slot5(m) * E, sl = slot5(m - 1) * E, sh = slot5(m + 1) * E;
-                const int mc = slot3(m) * E, ml = slot3(m - 1) * E, mh = slot3(m + 1) * E;
-                const T th = sTh[sc + e], pg = sPg[sc + e];
-                const T xo = sXO[slot5(m) * G + e + RS * XR];
-                const T xh = sXH[sc + e], xw = sXW[sc + e];
-                const T mu0 = sMu[mc + e], M0 = sM[mc + e], DH0 = sDH[mc + e], DW0 = sDW[mc + e];
-                // neighbours in the order x-, x+, y-, y+ (, z-, z+): in-plane
-                // offsets, then the planes before and after
-                int ro[2 * D], mo[2 * D];
-                ro[0] = sc + e - 1; ro[1] = sc + e + 1;
-                mo[0] = mc + e - 1; mo[1] = mc + e + 1;
-                if constexpr (D == 3) {
-                    ro[2] = sc + e - RS; ro[3] = sc + e + RS; ro[4] = sl + e; ro[5] = sh + e;
-                    mo[2] = mc + e - RS; mo[3] = mc + e + RS; mo[4] = ml + e; mo[5] = mh + e;
-                } else {
-                    ro[2] = sl + e; ro[3] = sh + e;
-                    mo[2] = ml + e; mo[3] = mh + e;
+                const int sc = slot5(m) * E, sh = slot5(m + 1) * E;
+                const int mc = slot3(m) * E, mh = slot3(m + 1) * E;
+                // the own cell's values of the planes before and after (the
+                // cross-plane neighbours) roll through registers
+                if (m == m0) {
+                    const int sl = slot5(m - 1) * E, ml = slot3(m - 1) * E;
+                    cTh[0] = sTh[sl + e]; cXH[0] = sXH[sl + e]; cXW[0] = sXW[sl + e];
+                    cMu[0] = sMu[ml + e]; cM[0] = sM[ml + e]; cDH[0] = sDH[ml + e]; cDW[0] = sDW[ml + e];
+                    cTh[1] = sTh[sc + e]; cXH[1] = sXH[sc + e]; cXW[1] = sXW[sc + e];
+                    cMu[1] = sMu[mc + e]; cM[1] = sM[mc + e]; cDH[1] = sDH[mc + e]; cDW[1] = sDW[mc + e];
                 }
+                cTh[2] = sTh[sh + e]; cXH[2] = sXH[sh + e]; cXW[2] = sXW[sh + e];
+                cMu[2] = sMu[mh + e]; cM[2] = sM[mh + e]; cDH[2] = sDH[mh + e]; cDW[2] = sDW[mh + e];
+                const T th = cTh[1], pg = sPg[sc + e];
+                const T xo = sXO[slot5(m) * G + e + RS * XR];
+                const T xh = cXH[1], xw = cXW[1];
+                const T mu0 = cMu[1], M0 = cM[1], DH0 = cDH[1], DW0 = cDW[1];
+                // neighbours in the order x-, x+, y-, y+ (, z-, z+): in-plane
+                // ones from shared memory, then the planes before and after
+                constexpr int NI = D == 3 ? 4 : 2;      // in-plane neighbours
+                const int io[4] = {-1, 1, -RS, RS};
                 T lapt = T(0), dO = T(0), dH = T(0), dW = T(0);
 #pragma unroll
-                for (int qn = 0; qn < 2 * D; qn++) {
-                    const int a = ro[qn], b = mo[qn];
+                for (int qn = 0; qn < NI; qn++) {
+                    const int a = sc + e + io[qn], b = mc + e + io[qn];
                     lapt += sTh[a] - th;
                     dO += T(0.5) * (M0 + sM[b]) * (sMu[b] - mu0);
                     dH += T(0.5) * (DH0 + sDH[b]) * (sXH[a] - xh);
                     dW += T(0.5) * (DW0 + sDW[b]) * (sXW[a] - xw);
                 }
+#pragma unroll
+                for (int k = 0; k < 3; k += 2) {
+                    lapt += cTh[k] - th;
+                    dO += T(0.5) * (M0 + cM[k]) * (cMu[k] - mu0);
+                    dH += T(0.5) * (DH0 + cDH[k]) * (cXH[k] - xh);
+                    dW += T(0.5) * (DW0 + cDW[k]) * (cXW[k] - xw);
+                }
+                cTh[0] = cTh[1]; cXH[0] = cXH[1]; cXW[0] = cXW[1];
+                cMu[0] = cMu[1]; cM[0] = cM[1]; cDH[0] = cDH[1]; cDW[0] = cDW[1];
+                cTh[1] = cTh[2]; cXH[1] = cXH[2]; cXW[1] = cXW[2];
+                cMu[1] = cMu[2]; cM[1] = cM[2]; cDH[1] = cDH[2]; cDW[1] = cDW[2];
                 const T hg0 = hfun(pg);
                 const T hpt = hder(th);
                 const T sol = T(1) - hg0;
