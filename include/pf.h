@@ -108,6 +108,10 @@ typedef struct {
                            sizes stay even and the coarse grid keeps >= 8 nodes per
                            axis).  Both solve to the same cg_rtol; iteration counts
                            differ.                                                     */
+    int fused_chunk;    /* planes per work item of the fused field update, which marches
+                           along the slowest axis (z in 3D, y in 2D): 0 = the library's
+                           choice (a cost model whose start-up weight is measured per
+                           dimension), > 0 = that many planes.  Results are identical. */
 } pf_config;
 
 /* Field arrays, FP64, cell-major.  Any pointer may be NULL (skipped).

@@ -32,7 +32,7 @@ class PFError(RuntimeError):
 
 
 def make_config(shape, prm, precision="fp64", mechanics=None, plasticity=None, warm_start=None,
-                cg_rtol=None, cg_maxit=None, dt=None, pcg_tile=None, precond=None):
+                cg_rtol=None, cg_maxit=None, dt=None, pcg_tile=None, precond=None, fused_chunk=None):
     """Build a pf_config from a grid shape ((ny, nx) or (nz, ny, nx)) and a
     parameter dict (see workloads.params)."""
     c = pf_config()
@@ -54,6 +54,7 @@ def make_config(shape, prm, precision="fp64", mechanics=None, plasticity=None, w
     c.cg_maxit = int(prm.get("cg_maxit", 20000) if cg_maxit is None else cg_maxit)
     c.dt = float(prm.get("dt", 0.0) if dt is None else dt)
     c.pcg_tile = int(prm.get("pcg_tile", 0) if pcg_tile is None else pcg_tile)
+    c.fused_chunk = int(prm.get("fused_chunk", 0) if fused_chunk is None else fused_chunk)
     pc = prm.get("precond", "auto") if precond is None else precond
     c.precond = {"auto": PF_PC_AUTO, "jacobi": PF_PC_JACOBI, "mg": PF_PC_MG}.get(pc, pc)
     for k in PARAM_NAMES:

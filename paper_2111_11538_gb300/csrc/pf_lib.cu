@@ -21,14 +21,10 @@
 // k_extrap_tail addresses the mean strain as the start of Scalars
 static_assert(offsetof(pfdev::Scalars, E) == 0, "Scalars::E must be the first member");
 
-// PCG node tile per size class (0: 32x8 / 16x4x4, 1: 32x16 / 32x4x2),
-// from the measurements of paper_2111_11538_gb300/autotune.py on GB300.
-#define PCG_TABLE_2D_F32_SMALL 0
-#define PCG_TABLE_2D_F32_LARGE 0
-#define PCG_TABLE_2D_F64_SMALL 1
-#define PCG_TABLE_2D_F64_LARGE 0
-#define PCG_TABLE_3D_F32 0
-#define PCG_TABLE_3D_F64 0
+// Launch shapes per size class, written by paper_2111_11538_gb300/autotune.py
+// from its measurements on GB300 (PCG node tiles of the Jacobi and the 2D
+// multigrid solves, start-up weight of the marching update's chunk choice).
+#include "tuning.h"
 
 using namespace pfdev;
 
@@ -348,6 +344,14 @@ int default_pcg_shape(int ndim, long long N, bool fp64)
     return fp64 ? PCG_TABLE_3D_F64 : PCG_TABLE_3D_F32;
 }
 
+// Node tile of the 2D multigrid-preconditioned solve (its V-cycle sweeps use
+// the same tile), per size class.
+int mg2_pcg_shape(long long N, bool fp64)
+{
+    if (fp64) return N <= (1LL << 18) ? PCG_TABLE_MG2D_F64_SMALL : PCG_TABLE_MG2D_F64_LARGE;
+    return N <= (1LL << 18) ? PCG_TABLE_MG2D_F32_SMALL : PCG_TABLE_MG2D_F32_LARGE;
+}
+
 // Largest eigenvalue of diag(K_e)^-1 K_e for the d-dimensional Q1 element
 // with Poisson ratio nu (power iteration on the symmetric scaling
 // D^-1/2 K_e D^-1/2).
@@ -503,7 +507,8 @@ int setup_cg_launch(pf_handle *h)
     // tile (one 512-thread block per SM) halves the blocks in each of their
     // barriers; 3D: the 16x4x4 tile of the cell path
     h->pcg_shape = h->cfg.pcg_tile > 0 ? h->cfg.pcg_tile - 1
-                                       : (h->mg ? (D == 2 ? 1 : 0) : default_pcg_shape(D, h->P.N, fp64));
+                                       : (h->mg ? (D == 2 ? mg2_pcg_shape(h->P.N, fp64) : 0)
+                                                : default_pcg_shape(D, h->P.N, fp64));
     h->cg_block = h->pcg_shape ? tile_threads<D, 1>() : tile_threads<D, 0>();     // one thread per tile node
     if (h->mg) PF_TRY((build_mg<T, D>(h)));
     int per_sm = 0;
@@ -567,19 +572,22 @@ void launch_fused(int grid, const JobSet<CellJob<T, D>> &js, cudaStream_t s)
 
 // Chunk length (planes along the marching axis) of the marching update for
 // a grid with `cols` tile columns and nm planes, and its block count: the
-// length that minimises (work items per block, rounded up) x (planes per
-// item + 3, the chunk's start-up planes), with at most cap blocks.
-int fused_chunk(long long cols, int nm, long long cap, int &nblocks)
+// explicit length `fixed` if > 0, else the length that minimises (work items
+// per block, rounded up) x (planes per item + w), w the start-up cost of a
+// chunk in planes, with at most cap blocks.
+int fused_chunk(long long cols, int nm, long long cap, int w, int fixed, int &nblocks)
 {
-    int best = nm;
-    long long bcost = -1;
-    for (int zc = 1; zc <= nm; zc++) {
-        const long long items = cols * ((nm + zc - 1) / zc);
-        const long long nb = std::min(items, cap);
-        const long long cost = ((items + nb - 1) / nb) * (zc + 3);
-        if (bcost < 0 || cost < bcost) {
-            bcost = cost;
-            best = zc;
+    int best = fixed > 0 ? std::min(fixed, nm) : nm;
+    if (fixed <= 0) {
+        long long bcost = -1;
+        for (int zc = 1; zc <= nm; zc++) {
+            const long long items = cols * ((nm + zc - 1) / zc);
+            const long long nb = std::min(items, cap);
+            const long long cost = ((items + nb - 1) / nb) * (zc + w);
+            if (bcost < 0 || cost < bcost) {
+                bcost = cost;
+                best = zc;
+            }
         }
     }
     const long long items = cols * ((nm + best - 1) / best);
@@ -633,7 +641,8 @@ int build_plan(pf_handle *h)
                                (D == 3 ? (P.ny + FusedZ<D>::TY - 1) / FusedZ<D>::TY : 1);
         const long long cap = (long long)h->sms * std::max(1, h->fused_per_sm);
         int nb = 1;
-        const int zc = fused_chunk(cols, D == 3 ? P.nz : P.ny, cap, nb);
+        const int zc = fused_chunk(cols, D == 3 ? P.nz : P.ny, cap, D == 3 ? FUSED_STARTUP_3D : FUSED_STARTUP_2D,
+                                   I[i]->cfg.fused_chunk, nb);
         for (int k = 0; k < 2; k++) { fj[k][i].block0 = f0; fj[k][i].nblocks = nb; fj[k][i].strip_rows = zc; }
         f0 += nb;
     }
@@ -1108,6 +1117,7 @@ int create_one(const pf_config *cfg, pf_handle **out, std::string &err)
     }
     if (c.mechanics && (c.cg_maxit <= 0 || !(c.cg_rtol > 0.0))) { err = "cg_maxit must be > 0 and cg_rtol > 0"; return PF_EINVAL; }
     if (c.pcg_tile < 0 || c.pcg_tile > PCG_SHAPES) { err = "pcg_tile must be 0 (library choice), 1 or 2"; return PF_EINVAL; }
+    if (c.fused_chunk < 0) { err = "fused_chunk must be >= 0 (0: library choice)"; return PF_EINVAL; }
     if (c.precond != PF_PC_AUTO && c.precond != PF_PC_JACOBI && c.precond != PF_PC_MG) {
         err = "precond must be PF_PC_AUTO, PF_PC_JACOBI or PF_PC_MG";
         return PF_EINVAL;

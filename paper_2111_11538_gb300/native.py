@@ -39,7 +39,7 @@ class pf_config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("mechanics", ctypes.c_int), ("plasticity", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("cg_maxit", ctypes.c_int), ("cg_rtol", ctypes.c_double),
                 ("dt", ctypes.c_double), ("p", pf_params), ("pcg_tile", ctypes.c_int),
-                ("precond", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("fused_chunk", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)

@@ -16,7 +16,7 @@ OUT_KEYS = ("alpha", "eps_p", "sigma", "phi_f", "phi_w", "xO", "xH", "xW")
 def oracle_state(sim):
     """The state of an oracle.Sim in the layout of Simulation.get_fields."""
     out = {"phi_f": sim.phi_f.copy(), "phi_w": sim.phi_w.copy()}
-    for k in ("xO", "xH", "xW", "u", "Ebar", "eps_p", "alpha", "sigma"):
+    for k in ("xO", "xH", "xW", "u", "Ebar", "eps_p", "alpha", "sigma", "theta", "phig"):
         out[k] = sim.f[k].copy()
     return out
 
@@ -42,7 +42,9 @@ def step_errors(orc, prm, before, after, static, origin=None, m=None):
     else:
         cut = lambda a: _box(a, origin, m, nd)                   # noqa: E731
         inner = (slice(3, m - 3),) * nd
-    f = {k: cut(before[k]) for k in ("phi_f", "phi_w", "xO", "xH", "xW", "eps_p", "alpha")}
+    exact = "theta" in before and "phig" in before
+    keys = ("phi_f", "phi_w", "xO", "xH", "xW", "eps_p", "alpha") + (("theta", "phig") if exact else ())
+    f = {k: cut(before[k]) for k in keys}
     f["mob"] = cut(static["mob"])
     f["mask"] = cut(static["mask"])
     f["u"] = cut(after["u"])
@@ -51,19 +53,22 @@ def step_errors(orc, prm, before, after, static, origin=None, m=None):
     orc.return_map(s)
     ref = {"alpha": s.f["alpha"].copy(), "eps_p": s.f["eps_p"].copy(), "sigma": s.f["sigma"].copy()}
     s.fields_update()
-    ref.update({"phi_f": s.phi_f, "phi_w": s.phi_w, "xO": s.f["xO"], "xH": s.f["xH"], "xW": s.f["xW"]})
-    # The exported phi_f, phi_w do not carry the order parameter of cells
-    # with no solid (phi_g = 1); its value there enters the Laplacian of
-    # the neighbours, so the phase outputs are compared away from such cells.
+    ref.update({"phi_f": s.phi_f, "phi_w": s.phi_w, "xO": s.f["xO"], "xH": s.f["xH"], "xW": s.f["xW"],
+                "theta": s.f["theta"]})
+    # With the exported order parameter and gas fraction the state is exact
+    # and every cell is compared (theta too).  From phi_f, phi_w alone the
+    # order parameter of cells with no solid (phi_g = 1) is lost; its value
+    # there enters the Laplacian of the neighbours, so the phase outputs are
+    # then compared away from such cells.
     gas = (f["phi_f"] + f["phi_w"]) == 0.0
     near_gas = gas.copy()
     for ax in range(nd):
         near_gas |= np.roll(gas, 1, axis=ax) | np.roll(gas, -1, axis=ax)
     errs = {}
-    for k in OUT_KEYS:
+    for k in OUT_KEYS + (("theta",) if exact else ()):
         g = cut(after[k])[inner]
         r = ref[k][inner]
-        if k in ("phi_f", "phi_w"):
+        if k in ("phi_f", "phi_w") and not exact:
             keep = ~near_gas[inner]
             g, r = g[keep], r[keep]
         # relative to the output's magnitude, floored at 1e-6 so that a field
@@ -77,7 +82,8 @@ def solve_residual(orc, prm, before, after, static):
     """||b - A x|| / ||b|| of the step's solved displacement (`after`'s u
     and Ebar) for the operator and right-hand side the oracle builds from
     the state before the step (whole grid)."""
-    f = {k: before[k] for k in ("phi_f", "phi_w", "xO", "xH", "xW", "eps_p", "alpha")}
+    f = {k: before[k] for k in ("phi_f", "phi_w", "xO", "xH", "xW", "eps_p", "alpha", "theta", "phig")
+         if k in before}
     f["mob"] = static["mob"]
     f["mask"] = static["mask"]
     s = orc.Sim(f, prm)
