@@ -51,15 +51,20 @@ MG_INIT_WORDS = {2: 28, 3: 40}
 # DRAM bytes per k_pcg launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of the current kernel on the named workload, per
 # finest node and V-cycle (so that it scales with the launch's iterations);
-# None where the current kernel has not been captured.
-PCG_TRAFFIC_PER_NODE_ITER = {"porous256cube": None}
-# Algorithmic bytes per cell of the fused explicit update (k_fused): theta,
+# None where the current kernel has not been captured.  porous256cube: the
+# first timed solve of `bench.py --only mixed --steps 1 --warmup 4` (44
+# V-cycles), 140.43 GB read + 95.73 GB written = 319.9 B per node and V-cycle
+# (profiles/launches_porous256_mixed.md).
+PCG_TRAFFIC_PER_NODE_ITER = {"porous256cube": 319.906}
+# Algorithmic bytes per cell of the fused explicit update (k_fusedz): theta,
 # phi_g, x_O, x_H, x_H2O, tr eps_e, |dev eps_e|^2, mobility read, the 1-byte
 # supply mask read, theta, x_O, x_H, x_H2O written.
 FUSED_BYTES = {"mixed": 8 * 4 + 1 + 4 * 4, "fp64": 8 * 8 + 1 + 4 * 8}
 # ncu DRAM bytes per cell of the fused update, mechanics off, None where the
-# current kernel has not been captured
-FUSED_TRAFFIC_PER_CELL = {2: None, 3: None}
+# current kernel has not been captured.  3D: one launch on the 256^3 porous
+# input, 576.0 MB read + 244.0 MB written = 48.9 B per cell
+# (profiles/k_fusedz_porous256_mechanics_off.md).
+FUSED_TRAFFIC_PER_CELL = {2: None, 3: 48.875}
 
 
 def _load_peaks():
@@ -310,7 +315,7 @@ def learned_warm_start(steps, warmup, fields, prev_ms, prev_iters, name):
 def stencil_roofline(fields, name, steps=20, warmup=3):
     """Achieved HBM bandwidth of the fused explicit update alone: the
     workload's microstructure stepped with the mechanics off, so that every
-    launch is k_fused; per-launch CUDA events on the launch stream."""
+    launch is k_fusedz; per-launch CUDA events on the launch stream."""
     from paper_2111_11538_gb300 import Simulation, workloads
     shape = fields["phi_f"].shape
     sim = Simulation(shape, workloads.params(mechanics=0), precision="mixed")
@@ -328,7 +333,7 @@ def stencil_roofline(fields, name, steps=20, warmup=3):
     gbs = algo / (ms / 1e3) / 1e9
     nd = len(shape)
     tr = FUSED_TRAFFIC_PER_CELL.get(nd)
-    return {"kernel": "k_fused (mu_O + explicit update, %dD)" % nd,
+    return {"kernel": "k_fusedz (mu_O + explicit update, %dD)" % nd,
             "workload": "%s, %s cells, mechanics off" % (name, "x".join(str(v) for v in shape[::-1])),
             "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
             "traffic": tr * N if tr else None, "peak_kind": kind + " (hbm_gbs, burst copy)",
