@@ -533,9 +533,9 @@ __global__ void __launch_bounds__(tile_threads<D, SH>(), 512 / tile_threads<D, S
                 setup_tiled<T, TX, TY>(A, use_x, refine, refine && outer > 0, xe64,
                                        reinterpret_cast<double *>(pcg_dyn), acc, bid, nbk);
             } else if constexpr (MG) {
-                // 3D multigrid variant: the same in 3D
-                setup_tiled3<T, TX, TY, TZ>(A, use_x, refine, refine && outer > 0, xe64,
-                                            reinterpret_cast<double *>(pcg_dyn), acc, bid, nbk);
+                // 3D multigrid variant: the z-marching sweep in FP64
+                setup_march3<T>(A, use_x, refine, refine && outer > 0, xe64, reinterpret_cast<double *>(pcg_dyn), acc,
+                                bid, nbk);
             } else
             for (long long n = t0; n < N; n += st) {
                 double bv[D], rv[D];
@@ -998,12 +998,10 @@ size_t pcg_dyn_smem(int shape, bool mg)
                sizeof(T) * (size_t)sweep2_words<Tile<2, 0>::X, Tile<2, 0>::Y>();
     }
     if (D == 3 && mg) {
-        // the 3D V-cycle's node planes and corner forces (mg_sweep3z), or the
-        // set-up sweep's FP64 scratch (setup_tiled3)
+        // the 3D V-cycle's sweeps (mg_sweep3z in T), or the set-up sweep's
+        // (FP64, three raw streams)
         const size_t cells = sizeof(T) * (size_t)mg_sweep3z_words<T>();
-        const size_t stp = sizeof(double) * (size_t)(shape == 1
-            ? setup_tiled3_doubles<Tile<3, 1>::X, Tile<3, 1>::Y, Tile<3, 1>::Z>()
-            : setup_tiled3_doubles<Tile<3, 0>::X, Tile<3, 0>::Y, Tile<3, 0>::Z>());
+        const size_t stp = sizeof(double) * (size_t)mg_sweep3z_words<double>(3);
         return cells > stp ? cells : stp;
     }
     if (D != 3 || sizeof(T) != 4 || shape != 0) return 0;

@@ -321,6 +321,11 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// Bring the line holding p into the L1 cache (no register result): the
+// operands of a later load whose latency would otherwise be exposed.  Data
+// written by other blocks before a grid barrier may be cached this way: the
+// barrier's acquire makes the writes visible to loads after it.
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 
 // GPU-scope synchronisation primitives of the grid barrier: the arriving

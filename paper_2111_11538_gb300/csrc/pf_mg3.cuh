@@ -9,7 +9,12 @@
 // of the 3D element.  All levels run on the whole grid, one tiled sweep of
 // the operator (the exact cell decomposition of cell_force3 / node_force3)
 // and one grid barrier per Chebyshev step; the CG update and the last step
-// of each smoothing are folded into neighbouring sweeps as in 2D.
+// of each smoothing are folded into neighbouring sweeps as in 2D.  Data
+// written by other blocks is read only after the grid barrier that follows
+// the write (an acquire at GPU scope), so such loads may be cached in L1:
+// the epilogues' operands are prefetched into L1 when a plane's work begins,
+// and the restriction and prolongation gathers, which read each value from
+// several neighbouring nodes, go through L1.
 #pragma once
 
 namespace pfdev {
@@ -83,14 +88,14 @@ constexpr int MGZ_TX = 32, MGZ_TY = 8, MGZ_NP = (MGZ_TX + 2) * (MGZ_TY + 2);
 constexpr int MGZ_NS = 10;
 template <typename T> struct MGZPipe { static constexpr bool on = sizeof(T) == 4; static constexpr int RB = on ? 2 : 1; };
 
-// Shared memory (values of T) of mg_sweep3z: two node planes, the eight
-// corner forces of one cell plane with their halos, and the staged nodes'
-// raw streams (two planes when they are copied ahead).
+// Shared memory (values of T) of mg_sweep3z with at most ns raw streams: two
+// node planes, the eight corner forces of one cell plane with their halos,
+// and the staged nodes' raw streams (two planes when they are copied ahead).
 template <typename T>
-__host__ __device__ constexpr int mg_sweep3z_words()
+__host__ __device__ constexpr int mg_sweep3z_words(int ns = MGZ_NS)
 {
     return V3S<T>::WORDS * (2 * (MGZ_TX + 2) * (MGZ_TY + 2) + 8 * (MGZ_TX + 1) * (MGZ_TY + 1)) +
-           MGZPipe<T>::RB * MGZ_NS * (MGZ_TX + 2) * (MGZ_TY + 2);
+           MGZPipe<T>::RB * ns * (MGZ_TX + 2) * (MGZ_TY + 2);
 }
 
 // z-chunk of the 3D sweep on an nx x ny x nz level with nbk blocks: the
@@ -122,18 +127,21 @@ __device__ __forceinline__ int mg_zchunk(int nx, int ny, int nz, int nbk)
 // copied into shared memory one plane ahead, so that their latency overlaps
 // the previous plane's work; raw[s * NP + h] is stream s at staged node h),
 // every cell of the plane (with the halo cells at x0 - 1, y0 - 1) computes
-// its average stress and hourglass forces once (cell_force3; its moduli are
-// read one plane ahead) and its forces on its eight corners
+// its average stress and hourglass forces once (cell_force3; its moduli, of
+// type TM, are read one plane ahead) and its forces on its eight corners
 // (corner_forces3), and each own node of plane zp adds its bottom-corner
 // forces to the top-corner forces left by plane zp - 1: q = A v is complete
-// and epi(n, v, q) receives it.  WITH_E: the mean strain ue enters every
-// cell's stress, and cell_e(c) receives the stress of every own cell
-// without it (c[0..5]).  smem: mg_sweep3z_words<T>() values; src: ns
-// pointers (shared memory, set by the caller); two block barriers per plane.
-template <typename T, bool WITH_E, class Make, class Epi, class CellE>
-__device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const T *lam, const T *mu, int bid,
+// and epi(n, v, q) receives it.  pref(n) runs for each own node of plane zp
+// when the plane's work begins (before the node plane ahead is formed), so
+// that the epilogue's operands can be fetched early.  WITH_E: the mean strain
+// ue enters every cell's stress, and cell_e(c) receives the stress of every
+// own cell without it (c[0..5]).  smem: mg_sweep3z_words<T>(ns) values; src:
+// ns pointers (shared memory, set by the caller); two block barriers per
+// plane.
+template <typename T, bool WITH_E, class TM, class Make, class Epi, class CellE, class Pref>
+__device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const TM *lam, const TM *mu, int bid,
                                            int nbk, T *smem, const T *ue, int ns, const T *const *src, Make &&make,
-                                           Epi &&epi, CellE &&cell_e)
+                                           Epi &&epi, CellE &&cell_e, Pref &&pref)
 {
     constexpr int TX = MGZ_TX, TY = MGZ_TY;
     constexpr int NX = TX + 2, NY = TY + 2, NP = NX * NY;
@@ -188,8 +196,8 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
                 if (h < NC) {
                     const int cx = h % CX, cy = h / CX;
                     const int g = mg_wrap(x0 - 1 + cx, nx, small) + nx * (mg_wrap(y0 - 1 + cy, ny, small) + ny * zw);
-                    l[u] = __ldcg(lam + g);
-                    m[u] = __ldcg(mu + g);
+                    l[u] = (T)__ldcg(lam + g);
+                    m[u] = (T)__ldcg(mu + g);
                 }
             }
         };
@@ -207,6 +215,7 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
         for (int zp = z0 - 1; zp < z1; zp++) {
             T *const nlo = (zp & 1) ? np1 : np0;
             T *const nhi = (zp & 1) ? np0 : np1;
+            if (own && zp >= z0) pref(gx + nx * (gy + ny * zp));
             if constexpr (PIPE) {
                 // copies of plane zp + 2 go out; plane zp + 1's have landed
                 if (zp + 2 <= z1) issue(zp + 2);
@@ -312,125 +321,74 @@ __device__ void mg_coarsen3(const MGLevel<T> &F, const MGLevel<T> &C, long long 
     }
 }
 
-// Shared memory (in doubles) of setup_tiled3 for a TX x TY x TZ tile: the
-// FP64 operand on the halo and 18 values per halo cell.
-template <int TX, int TY, int TZ>
-__host__ __device__ constexpr int setup_tiled3_doubles()
-{
-    return 3 * (TX + 2) * (TY + 2) * (TZ + 2) + 18 * (TX + 1) * (TY + 1) * (TZ + 1);
-}
-
-// The set-up sweep of one CG pass in 3D (setup_tiled in 2D): b, the Jacobi
-// diagonal, r = b - A x with the operator applied in FP64 from per-cell
-// stress and hourglass forces computed once per tile, and the sums of the
-// mean-strain rows (acc[0] ||b||^2, [1] ||r||^2, [2] sum lam, [3] sum mu,
-// [4..9] sum sig*, [10..15] the own cells' stress of x without the mean
-// strain).  resid: a later refinement pass, which reads b from A.b64 and
-// skips what does not change during a solve.
-template <typename T, int TX, int TY, int TZ>
-__device__ void setup_tiled3(const PCGArgs<T, 3> &A, bool use_x, bool refine, bool resid, const double *xe,
-                             double *dscr, Acc<double> (&acc)[16], int bid, int nbk)
+// The set-up sweep of one CG pass in 3D, on the z-marching sweep in FP64
+// (cell stress and hourglass forces once per cell, corner forces gathered per
+// node): b, the Jacobi diagonal, r = b - A x and the sums of the mean-strain
+// rows (acc[0] ||b||^2, [1] ||r||^2, [2] sum lam, [3] sum mu, [4..9] sum
+// sig*, [10..15] the cells' stress of x without the mean strain).  resid: a
+// later refinement pass, which reads b from A.b64 and skips what does not
+// change during a solve.  smem: mg_sweep3z_words<double>(3) doubles.
+template <typename T>
+__device__ void setup_march3(const PCGArgs<T, 3> &A, bool use_x, bool refine, bool resid, const double *xe,
+                             double *smem, Acc<double> (&acc)[16], int bid, int nbk)
 {
     const Params &P = A.P;
-    constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HN = HX * HY * HZ;
-    constexpr int CX = TX + 1, CY = TY + 1, CZ = TZ + 1, HC = CX * CY * CZ, NT = TX * TY * TZ;
-    double *hu = dscr, *hc = dscr + 3 * HN;
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntz = (nz + TZ - 1) / TZ;
-    const int ntiles = ntx * nty * ntz;
-    const bool small = nx < HX || ny < HY || nz < HZ;
-    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
-    auto gidx = [&](int x, int y, int z) {
-        return mg_wrap(x, nx, small) + nx * (mg_wrap(y, ny, small) + ny * mg_wrap(z, nz, small));
+    auto node = [&](int n, const double (&ax)[3]) {
+        double b[3];
+        if (resid) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) b[c] = __ldcg(A.b64[c] + n);
+        } else {
+            double unused[3], so[6], unused6[6], dgn, lo, mo;
+            node_setup<T, double, double, 3>(P, n, A.lam, A.mu, A.sig, A.x64, xe, false, b, unused, dgn, so, unused6,
+                                             lo, mo);
+            if (refine)
+#pragma unroll
+                for (int c = 0; c < 3; c++) A.b64[c][n] = b[c];
+            A.dinv[n] = (T)(1.0 / dgn);
+            acc[2].add(lo);
+            acc[3].add(mo);
+#pragma unroll
+            for (int v = 0; v < 6; v++) acc[4 + v].add(so[v]);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double rv = b[d] - ax[d];
+            if (refine && !use_x) A.x64[d][n] = 0.0;
+            if (refine || !use_x) A.x[d][n] = T(0);
+            A.p[d][n] = T(0);
+            A.s[0][d][n] = T(0);
+            A.r[0][d][n] = (T)rv;
+            if (!resid) acc[0].addprod(b[d], b[d]);
+            acc[1].addprod(rv, rv);
+        }
     };
-    for (int tile = bid; tile < ntiles; tile += nbk) {
-        const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY, z0 = (tile / (ntx * nty)) * TZ;
-        if (use_x) {
-            for (int h = threadIdx.x; h < HN; h += NT) {
-                const int g = gidx(x0 - 1 + h % HX, y0 - 1 + (h / HX) % HY, z0 - 1 + h / (HX * HY));
-#pragma unroll
-                for (int c = 0; c < 3; c++) hu[c * HN + h] = refine ? __ldcg(A.x64[c] + g) : (double)A.x[c][g];
-            }
-            __syncthreads();
-            for (int h = threadIdx.x; h < HC; h += NT) {
-                const int cx = h % CX, cy = (h / CX) % CY, cz = h / (CX * CY);
-                const int g = gidx(x0 - 1 + cx, y0 - 1 + cy, z0 - 1 + cz);
-                double uc[8][3];
-#pragma unroll
-                for (int b = 0; b < 8; b++) {
-                    const int hn = (cx + (b & 1)) + HX * ((cy + ((b >> 1) & 1)) + HY * (cz + (b >> 2)));
-#pragma unroll
-                    for (int c = 0; c < 3; c++) uc[b][c] = hu[c * HN + hn];
-                }
-                const double l = (double)A.lam[g], m = (double)A.mu[g];
-                double cf[20], sx[6];
-                cell_force3<double>(l, m, uc, cf);
-                voigt_stress<double, 3>(l, m, xe, sx);
-#pragma unroll
-                for (int v = 0; v < 6; v++) cf[v] += sx[v];
-#pragma unroll
-                for (int v = 0; v < 18; v++) hc[v * HC + h] = cf[v];
-            }
-            __syncthreads();
-        }
-        const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-        if (gx < nx && gy < ny && gz < nz) {
-            const int n = gx + nx * (gy + ny * gz), lx = tx + 1, ly = ty + 1, lz = tz + 1;
-            double b[3], ax[3] = {0.0, 0.0, 0.0}, dgn = 1.0, so[6], deo[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, lo, mo;
-            if (resid) {
-#pragma unroll
-                for (int c = 0; c < 3; c++) b[c] = __ldcg(A.b64[c] + n);
-                lo = (double)A.lam[n];
-                mo = (double)A.mu[n];
-            } else {
-                double unused[3], unused6[6];
-                node_setup<T, double, double, 3>(P, n, A.lam, A.mu, A.sig, A.x64, xe, false, b, unused, dgn, so, unused6,
-                                                 lo, mo);
-                if (refine)
-#pragma unroll
-                    for (int c = 0; c < 3; c++) A.b64[c][n] = b[c];
-            }
-            if (use_x) {
-#pragma unroll
-                for (int a = 0; a < 8; a++) {
-                    const int ax_ = a & 1, ay_ = (a >> 1) & 1, az_ = a >> 2;
-                    const int cl = (lx - ax_) + CX * ((ly - ay_) + CY * (lz - az_));
-                    double cf[18], f[3];
-#pragma unroll
-                    for (int v = 0; v < 18; v++) cf[v] = hc[v * HC + cl];
-                    node_force3<double>(ax_, ay_, az_, cf, cf + 6, f);
-#pragma unroll
-                    for (int c = 0; c < 3; c++) ax[c] += f[c];
-                }
-                const int c0 = lx + CX * (ly + CY * lz);
-                double sx[6];
-                voigt_stress<double, 3>(lo, mo, xe, sx);
-#pragma unroll
-                for (int v = 0; v < 6; v++) deo[v] = hc[v * HC + c0] - sx[v];
-            }
-            if (!resid) {
-                A.dinv[n] = (T)(1.0 / dgn);
-                acc[2].add(lo);
-                acc[3].add(mo);
-#pragma unroll
-                for (int v = 0; v < 6; v++) acc[4 + v].add(so[v]);
-            }
-#pragma unroll
-            for (int v = 0; v < 6; v++) acc[10 + v].add(deo[v]);
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const double rv = b[d] - ax[d];
-                if (refine && !use_x) A.x64[d][n] = 0.0;
-                if (refine || !use_x) A.x[d][n] = T(0);
-                A.p[d][n] = T(0);
-                A.s[0][d][n] = T(0);
-                A.r[0][d][n] = (T)rv;
-                if (!resid) acc[0].addprod(b[d], b[d]);
-                acc[1].addprod(rv, rv);
-            }
-        }
-        __syncthreads();
+    if (!use_x) {
+        const long long t0 = bid * (long long)blockDim.x + threadIdx.x, st = (long long)nbk * blockDim.x;
+        const double zero[3] = {0.0, 0.0, 0.0};
+        for (long long n = t0; n < P.N; n += st) node((int)n, zero);
+        return;
     }
+    // x: the FP64 solution of the refinement, or the solution itself (FP64)
+    __shared__ const double *s_xs[3];
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; c++) {
+            if constexpr (sizeof(T) == 8) s_xs[c] = refine ? A.x64[c] : reinterpret_cast<const double *>(A.x[c]);
+            else s_xs[c] = A.x64[c];
+        }
+    __syncthreads();
+    mg_sweep3z<double, true>(
+        P.nx, P.ny, P.nz, mg_zchunk(P.nx, P.ny, P.nz, nbk), A.lam, A.mu, bid, nbk, smem, xe, 3, s_xs,
+        [&](const double *raw, int h, int, int, int, double (&v)[3]) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) v[c] = raw[c * MGZ_NP + h];
+        },
+        [&](int n, const double (&)[3], const double (&q)[3]) { node(n, q); },
+        [&](const double *c) {
+#pragma unroll
+            for (int v = 0; v < 6; v++) acc[10 + v].add(c[v]);
+        },
+        [](int) {});
 }
 
 // Set-up of the 3D hierarchy at the start of a solve (grid levels, a barrier
@@ -469,12 +427,14 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
     // the streams of the next sweep (shared memory; every sweep is preceded
     // by a grid or block barrier after its streams are set)
     __shared__ const T *s_src[MGZ_NS];
-    auto sweep = [&](int k, int ns, auto &&setsrc, auto &&make, auto &&epi) {
+    auto sweep = [&](int k, int ns, auto &&setsrc, auto &&make, auto &&epi, auto &&pref) {
         const MGLevel<T> &V = H.lv[k];
         if (lead) setsrc(s_src);
         __syncthreads();
-        mg_sweep3z<T, false>(V.nx, V.ny, V.nz, s_zc[k], V.lam, V.mu, bid, nbk, smem, nullptr, ns, s_src, make, epi, none);
+        mg_sweep3z<T, false>(V.nx, V.ny, V.nz, s_zc[k], V.lam, V.mu, bid, nbk, smem, nullptr, ns, s_src, make, epi, none,
+                             pref);
     };
+    auto nopref = [](int) {};
     constexpr int NP = MGZ_NP;
 
     // Chebyshev step j on level k (buffer par -> 1 - par); last: also apply
@@ -498,11 +458,11 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                 }
             },
             [&](int n, const T (&v)[3], const T (&q)[3]) {
-                const T di = last ? n2 * __ldcg(V.dinv + n) : T(0);
+                const T di = last ? n2 * __ldca(V.dinv + n) : T(0);
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    const T x = __ldcg(X[c] + n) + v[c];
-                    const T rn = __ldcg(V.r[par][c] + n) - q[c];
+                    const T x = __ldca(X[c] + n) + v[c];
+                    const T rn = __ldca(V.r[par][c] + n) - q[c];
                     if (last) {
                         V.xpost[c][n] = x + (n1 * v[c] + di * rn);
                     } else {
@@ -511,6 +471,11 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                         V.d[1 - par][c][n] = v[c];
                     }
                 }
+            },
+            [&](int n) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) { prefetch_l1(X[c] + n); prefetch_l1(V.r[par][c] + n); }
+                if (last) prefetch_l1(V.dinv + n);
             });
     };
     // restriction (transpose of trilinear prolongation) of level k-1's
@@ -530,7 +495,7 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                     const int i = lin3(F, wrap(2 * gx + cx, F.nx), fy, fz);
                     const T w = wy * (cx == 0 ? T(1) : T(0.5));
 #pragma unroll
-                    for (int c = 0; c < 3; c++) f[c] += w * __ldcg(F.r[pf][c] + i);
+                    for (int c = 0; c < 3; c++) f[c] += w * __ldca(F.r[pf][c] + i);
                 }
             }
         }
@@ -558,7 +523,8 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                     V.r[1][c][n] = f[c] - q[c];
                     V.d[1][c][n] = v[c];
                 }
-            });
+            },
+            nopref);
     };
     // first post-smoothing sweep of level k: x = x_pre + P e_{k+1}, r = f - A x;
     // last (one-step smoothing): x + c2[0] D^-1 r is the final correction
@@ -579,16 +545,16 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                         for (int bx = 0; bx <= o[0]; bx++) {
                             const int ci = lin3(C, bx ? i1[0] : ic[0], by ? i1[1] : ic[1], bz ? i1[2] : ic[2]);
 #pragma unroll
-                            for (int c = 0; c < 3; c++) e[c] += __ldcg(C.xpost[c] + ci);
+                            for (int c = 0; c < 3; c++) e[c] += __ldca(C.xpost[c] + ci);
                         }
 #pragma unroll
                 for (int c = 0; c < 3; c++) v[c] = raw[c * NP + h] + w * e[c];
             },
             [&](int n, const T (&v)[3], const T (&q)[3]) {
-                const T di = last ? H.c2[0] * __ldcg(V.dinv + n) : T(0);
+                const T di = last ? H.c2[0] * __ldca(V.dinv + n) : T(0);
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    const T f = k == 0 ? __ldcg(A.r[cur][c] + n) : __ldcg(V.f[c] + n);
+                    const T f = k == 0 ? __ldca(A.r[cur][c] + n) : __ldca(V.f[c] + n);
                     if (last) {
                         V.xpost[c][n] = v[c] + di * (f - q[c]);
                     } else {
@@ -596,6 +562,11 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                         V.r[1 - par][c][n] = f - q[c];
                     }
                 }
+            },
+            [&](int n) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) prefetch_l1((k == 0 ? A.r[cur][c] : V.f[c]) + n);
+                if (last) prefetch_l1(V.dinv + n);
             });
     };
     auto post = [&](int k, int cur) {
@@ -659,10 +630,10 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                 [&](int n, const T (&v)[3], const T (&q)[3]) {
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
-                        T f = __ldcg(A.r[cur][c] + n);
+                        T f = __ldca(A.r[cur][c] + n);
                         if (!first) {
-                            const T si = __ldcg(A.w[cur][c] + n) + tb * __ldcg(A.s[cur][c] + n);
-                            const T pi = __ldcg(L0.xpost[c] + n) + tb * A.p[c][n];
+                            const T si = __ldca(A.w[cur][c] + n) + tb * __ldca(A.s[cur][c] + n);
+                            const T pi = __ldca(L0.xpost[c] + n) + tb * A.p[c][n];
                             A.p[c][n] = pi;
                             A.x[c][n] = A.x[c][n] + ta * pi;
                             A.s[nxt][c][n] = si;
@@ -673,6 +644,19 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                         L0.xpre[c][n] = v[c];
                         L0.r[1][c][n] = f - q[c];
                         L0.d[1][c][n] = v[c];
+                    }
+                },
+                [&](int n) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        prefetch_l1(A.r[cur][c] + n);
+                        if (!first) {
+                            prefetch_l1(A.w[cur][c] + n);
+                            prefetch_l1(A.s[cur][c] + n);
+                            prefetch_l1(L0.xpost[c] + n);
+                            prefetch_l1(A.p[c] + n);
+                            prefetch_l1(A.x[c] + n);
+                        }
                     }
                 });
         }
@@ -727,13 +711,17 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
                     A.w[cur][c][n] = q[c];
-                    acc[0].fma_plain(__ldcg(A.r[cur][c] + n), v[c]);
+                    acc[0].fma_plain(__ldca(A.r[cur][c] + n), v[c]);
                     acc[1].fma_plain(q[c], v[c]);
                 }
             },
             [&](const T *se) {
 #pragma unroll
                 for (int vv = 0; vv < NV; vv++) acc[2 + vv].add_plain(se[vv]);
+            },
+            [&](int n) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) prefetch_l1(A.r[cur][c] + n);
             });
         double tt[2 + NV];
         if (!reduce_barrier<Acc<T>, 2 + NV>(acc, A.partials, A.result, A.bar_count, A.bar_gen, err, tt, bid, nbk)) return -1;
