@@ -153,7 +153,7 @@ typedef struct {
     int cg_iters_last, cg_iters_max;/* last solve / max over the last pf_step call */
     long long cg_iters_total;       /* all solves since pf_set_fields              */
     long long steps;                /* steps taken since pf_set_fields             */
-    double dt;                      /* time step in use                            */
+    double dt;                      /* time step of the last step (pf_step: cfg dt; pf_step_implicit: its own) */
     int status;                     /* sticky status of the last pf_step call      */
     int precond;                    /* preconditioner in use: PF_PC_JACOBI or PF_PC_MG */
     int mg_levels;                  /* levels of the multigrid hierarchy (0: Jacobi)   */
@@ -190,6 +190,52 @@ int pf_set_fields(pf_handle *h, const pf_fields *f, int where);
  * the first step after pf_create / pf_set_fields (direct launches if the
  * capture fails); the results are the same either way. */
 int pf_step(pf_handle *h, int nsteps, void *cudaStream);
+
+/* Backward-Euler steps of the field relations.  The paper integrates the
+ * relations of Sec. 2.4 in time by backward Euler and solves each step by
+ * Newton's method (Sec. 2.4, closing paragraph).  One step here: the
+ * mechanics of pf_step at the current state (the solve and the J2 return,
+ * whose coupling scalars tr eps_e, |dev eps_e|^2 are then held over the
+ * step), then Newton's method on
+ *     F(y) = y - y_n - dt R(y),   y = (theta, x_O, x_H, x_H2O),
+ * R the right-hand sides of pf_step's update (the same fluxes, driving force
+ * and reaction; the reaction switch at x_H2O >= 1 evaluated at the new
+ * state), with x_H = x_H,bc and x_H2O = 0 held on supply cells at the new
+ * time level; the water removed and the hydrogen supplied there are the
+ * differences from what those cells' own relations would give, so the
+ * balances of pf_get_diagnostics hold as for explicit steps.  Newton stops
+ * when max |F| <= newton_tol, or when an update computed from a linear solve
+ * that met gmres_rtol moves no entry by more than newton_tol * max(1, max |y|).
+ * Each Newton iteration solves J delta = F by
+ * restarted GMRES, matrix-free (each product J z is the directional
+ * derivative of F along z, evaluated in forward mode), preconditioned on the right by pc_degree Chebyshev steps
+ * (Jacobi-scaled) on each field's own block: theta's gradient term and the
+ * species' diffusion with the phase-interpolated diffusivities.  Single-grid
+ * handles with precision PF_FP64 only.  Blocking.
+ * Returns PF_EINVAL (batch or mixed handle, invalid opts), PF_ESTATE (no
+ * fields), PF_ENOTCONV (Newton did not meet its stopping rule within
+ * newton_maxit: that step is not taken -- the fields stay at its start while
+ * the mechanical state has advanced -- and the call stops; or a CG solve hit
+ * cg_maxit), PF_ENONFINITE, PF_ETIMEOUT as pf_step.  stats may be NULL. */
+typedef struct {
+    double dt;          /* time step (> 0), free of the explicit limit              */
+    double newton_tol;  /* Newton stopping tolerance (> 0), see above                */
+    int newton_maxit;   /* Newton iterations per step (>= 1)                         */
+    double gmres_rtol;  /* each linear solve to ||J delta - F|| <= gmres_rtol ||F||  */
+    int gmres_restart;  /* Krylov vectors per GMRES cycle, 1 .. 60                   */
+    int gmres_maxit;    /* GMRES iterations per Newton iteration (>= 1)              */
+    int pc_degree;      /* Chebyshev steps of the block preconditioner, 0 (none) .. 64 */
+} pf_implicit_opts;
+
+typedef struct {
+    int newton_iters;          /* Newton iterations of the last step           */
+    int newton_iters_total;    /* over all steps of the call                   */
+    long long gmres_iters;     /* GMRES iterations over all steps of the call  */
+    double residual;           /* max |F| at the end of the last step          */
+} pf_implicit_stats;
+
+int pf_step_implicit(pf_handle *h, int nsteps, const pf_implicit_opts *opts, pf_implicit_stats *stats,
+                     void *cudaStream);
 
 /* Copy the current state (the fields of Sec. 2.4 and the mechanical state)
  * out into caller arrays (FP64); NULL members are skipped.  sigma is the

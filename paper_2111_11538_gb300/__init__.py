@@ -175,6 +175,20 @@ class Simulation:
             self._check(rc)
         return rc
 
+    def step_implicit(self, n, dt, newton_tol=1e-12, newton_maxit=30, gmres_rtol=1e-6, gmres_restart=60,
+                      gmres_maxit=5000, pc_degree=32, stream=None, check=True):
+        """n backward-Euler steps of length dt (pf_step_implicit); returns the
+        Newton and GMRES counts as a dict."""
+        o = native.pf_implicit_opts(dt=float(dt), newton_tol=float(newton_tol), newton_maxit=int(newton_maxit),
+                                    gmres_rtol=float(gmres_rtol), gmres_restart=int(gmres_restart),
+                                    gmres_maxit=int(gmres_maxit), pc_degree=int(pc_degree))
+        rc, st = native.pf_step_implicit(self.h, n, o, stream)
+        if check:
+            self._check(rc)
+        out = {k: getattr(st, k) for k, _ in native.pf_implicit_stats._fields_}
+        out["rc"] = rc
+        return out
+
     def get_fields(self, keys=FIELD_KEYS, out=None):
         """Fields as numpy arrays; with `out` (a dict of preallocated arrays,
         e.g. pinned host memory) the copies land there."""

@@ -17,6 +17,7 @@
 #include "unet_net.h"
 #include "pf_cg.cuh"
 #include "pcg_launch.h"
+#include "pf_implicit.cuh"
 
 // k_extrap_tail addresses the mean strain as the start of Scalars
 static_assert(offsetof(pfdev::Scalars, E) == 0, "Scalars::E must be the first member");
@@ -214,6 +215,13 @@ struct pf_handle {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step from job tables [k]
     bool graph_failed = false;
     bool use_graph = true;
+
+    // backward-Euler steps (pf_step_implicit): work arrays allocated at the
+    // first call (be_len values) and the time step of the last step taken
+    // that way (0 after explicit steps: the configured dt)
+    double *be_ws = nullptr;
+    size_t be_len = 0;
+    double dt_last = 0.0;
 
     // learned warm start (pf_attach_unet)
     pf_unet *net = nullptr;
@@ -728,10 +736,11 @@ int learned_guess(pf_handle *m, cudaStream_t s)
     return PF_OK;
 }
 
-// Queue one step of every instance; k selects the job tables (0: current
-// state, 1: one step later).
+// Queue the mechanics of one step of every instance (moduli and eigenstress,
+// the initial guess, the solve, the return map); k selects the job tables
+// (0: current state, 1: one step later).
 template <typename T, int D>
-int launch_step(pf_handle *h, cudaStream_t s, int k)
+int launch_mechanics(pf_handle *h, cudaStream_t s, int k)
 {
     JobSet<CellJob<T, D>> cj;
     memset(&cj, 0, sizeof(cj));
@@ -776,7 +785,18 @@ int launch_step(pf_handle *h, cudaStream_t s, int k)
         k_return<T, D><<<h->cell_grid, 256, 0, s>>>(cj);
         h->mark_end(s);
     }
-    JobSet<CellJob<T, D>> fj = cj;
+    return PF_OK;
+}
+
+// One explicit step from job tables [k]: the mechanics at the current state,
+// then the fused field update.
+template <typename T, int D>
+int launch_step(pf_handle *h, cudaStream_t s, int k)
+{
+    PF_TRY((launch_mechanics<T, D>(h, s, k)));
+    JobSet<CellJob<T, D>> fj;
+    memset(&fj, 0, sizeof(fj));
+    fj.njobs = h->njobs;
     fj.table = (const CellJob<T, D> *)h->d_fused_jobs[k];
     h->mark_begin(PF_K_UPDATE, s);
     launch_fused<T, D>(h->fused_grid, fj, s);
@@ -1163,6 +1183,274 @@ int create_one(const pf_config *cfg, pf_handle **out, std::string &err)
     return PF_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Backward-Euler steps of the field relations (pf_step_implicit): the
+// mechanics of the explicit step at y_n, then Newton's method on
+// F(y) = y - y_n - dt R(y) with matrix-free GMRES (pf_implicit.cuh).
+// ---------------------------------------------------------------------------
+constexpr int BE_NDOT = 256;   // blocks of the dot-product kernel
+constexpr int BE_MAX_RESTART = 60;
+// partial sums: the dot products of up to BE_MAX_RESTART + 1 vectors, or the
+// five balance sums of up to 16 blocks per SM on 152 SMs and more
+constexpr size_t BE_NPART = (size_t)BE_NDOT * 65;
+
+struct BEWork {
+    long long N, L;
+    int m;
+    double *y, *y0, *F0, *Ft, *t, *der, *z, *r, *d, *q, *dg, *x, *u, *V;
+    double *part, *hvec;
+    unsigned long long *mx;    // [0] max |F|, [2..3] max |delta|, max |y|, [4..7] Gershgorin s per block
+};
+
+int be_work(pf_handle *h, int m, BEWork &w)
+{
+    const long long N = h->P.N, L = 4 * N;
+    const size_t nvec = 14 + (size_t)(m + 1);
+    const size_t len = nvec * (size_t)L + BE_NPART + 64 + 8;
+    if (h->be_len < len) {
+        PF_TRY(h->alloc(&h->be_ws, sizeof(double) * len));
+        h->be_len = len;
+    }
+    double *p = h->be_ws;
+    w.N = N; w.L = L; w.m = m;
+    double **vec[14] = {&w.y, &w.y0, &w.F0, &w.Ft, &w.t, &w.der, &w.z, &w.r, &w.d, &w.q, &w.dg, &w.x, &w.u, &w.V};
+    for (int k = 0; k < 14; k++) { *vec[k] = p; p += L; }
+    p += (size_t)m * L;                       // V holds m + 1 vectors
+    w.part = p; p += BE_NPART;
+    w.hvec = p; p += 64;
+    w.mx = reinterpret_cast<unsigned long long *>(p);
+    return PF_OK;
+}
+
+template <int D>
+int be_steps(pf_handle *h, int nsteps, const pf_implicit_opts &o, pf_implicit_stats &st, cudaStream_t s)
+{
+    if (!h->plan_ready) PF_TRY((build_plan<double, D>(h)));
+    const int m = o.gmres_restart, K = o.pc_degree;
+    BEWork w;
+    PF_TRY(be_work(h, m, w));
+    const long long N = w.N, L = w.L;
+    const int gN = grid_for(h, N), gL = grid_for(h, L);
+    BEArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nx = h->P.nx; a.ny = h->P.ny; a.nz = D == 3 ? h->P.nz : 1; a.N = N; a.dt = o.dt;
+    a.K = cell_const<double>(h->P);
+    a.phig = (const double *)h->phig; a.mob = (const double *)h->mob;
+    a.trE = (const double *)h->trE; a.devE2 = (const double *)h->devE2; a.mask = h->mask;
+    std::vector<double> hp((size_t)BE_NDOT * (m + 1));
+    auto check = [&](const char *what) { return h->cuda(cudaGetLastError(), what); };
+    // dot products of w with nv vectors starting at V (fixed summation order)
+    auto dots = [&](const double *Vb, int nv, const double *vw, double *res) -> int {
+        k_be_dots<<<dim3(BE_NDOT, nv), 256, 0, s>>>(L, Vb, nv, vw, w.part);
+        PF_TRY(h->cuda(cudaMemcpyAsync(hp.data(), w.part, sizeof(double) * BE_NDOT * nv, cudaMemcpyDeviceToHost, s),
+                       "dot products"));
+        PF_TRY(h->cuda(cudaStreamSynchronize(s), "dot products"));
+        for (int k = 0; k < nv; k++) {
+            double t = 0.0;
+            for (int b = 0; b < BE_NDOT; b++) t += hp[(size_t)k * BE_NDOT + b];
+            res[k] = t;
+        }
+        return PF_OK;
+    };
+    auto comb = [&](const double *Vb, int nv, const double *c, double *out) -> int {
+        PF_TRY(h->cuda(cudaMemcpyAsync(w.hvec, c, sizeof(double) * nv, cudaMemcpyHostToDevice, s), "coefficients"));
+        k_be_comb<<<gL, 256, 0, s>>>(L, Vb, nv, w.hvec, out);
+        return check("combination");
+    };
+    auto read_max = [&](int k0, int n, double *out) -> int {
+        unsigned long long v[8];
+        PF_TRY(h->cuda(cudaMemcpyAsync(v, w.mx + k0, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s), "max"));
+        PF_TRY(h->cuda(cudaStreamSynchronize(s), "max"));
+        for (int k = 0; k < n; k++) {
+            const long long b = (long long)v[k];
+            memcpy(&out[k], &b, sizeof(double));
+        }
+        return PF_OK;
+    };
+    // F(yy) into out, max |F| into mx[0]
+    auto Fval = [&](const double *yy, double *out) -> int {
+        PF_TRY(h->cuda(cudaMemsetAsync(w.mx, 0, sizeof(unsigned long long), s), "max"));
+        k_be_derive<D><<<gN, 256, 0, s>>>(a, yy, w.der);
+        k_be_rates<D><<<gN, 256, 0, s>>>(a, yy, w.y0, w.der, out, 0, w.mx);
+        return check("residual");
+    };
+    // Chebyshev coefficients of the block preconditioner
+    std::vector<BECheb> cheb;
+    BECheb cinit;
+    auto precond = [&](const double *v, double *zo) -> int {
+        if (K == 0) return h->cuda(cudaMemcpyAsync(zo, v, sizeof(double) * L, cudaMemcpyDeviceToDevice, s), "copy");
+        k_be_pc_init<<<gL, 256, 0, s>>>(N, v, w.dg, zo, w.r, w.d, cinit);
+        for (int k = 0; k + 1 < K; k++) {
+            k_be_pc_apply<D><<<gN, 256, 0, s>>>(a, w.der, w.d, w.q);
+            k_be_pc_step<<<gL, 256, 0, s>>>(N, w.q, w.dg, zo, w.r, w.d, cheb[k], 0);
+        }
+        k_be_pc_step<<<gL, 256, 0, s>>>(N, w.q, w.dg, zo, w.r, w.d, cinit, 1);
+        return check("preconditioner");
+    };
+    // J zz: the directional derivative of F at y, in forward mode
+    auto jvp = [&](const double *zz, double *out) -> int {
+        k_be_jderive<D><<<gN, 256, 0, s>>>(a, w.y, zz, w.t, w.Ft);
+        k_be_jvp<D><<<gN, 256, 0, s>>>(a, w.y, zz, w.t, w.Ft, out);
+        return check("jvp");
+    };
+
+    st.newton_iters = 0;
+    for (int step = 0; step < nsteps; step++) {
+        // mechanics at y_n (staggered, as in the explicit step)
+        PF_TRY((launch_mechanics<double, D>(h, s, h->plan_par)));
+        const int c = h->cur;
+        k_be_gather<<<gN, 256, 0, s>>>(N, (const double *)h->theta[c], (const double *)h->xO[c],
+                                        (const double *)h->xH[c], (const double *)h->xW[c], w.y0);
+        k_be_init<<<gN, 256, 0, s>>>(a, w.y0, w.y);
+        // the preconditioner's blocks depend on phi_g and the mobility only
+        PF_TRY(h->cuda(cudaMemsetAsync(w.mx + 4, 0, 4 * sizeof(unsigned long long), s), "bounds"));
+        k_be_derive<D><<<gN, 256, 0, s>>>(a, w.y, w.der);
+        k_be_pc_diag<D><<<gN, 256, 0, s>>>(a, w.der, w.dg, w.mx + 4);
+        PF_TRY(check("preconditioner set-up"));
+        double sb[4];
+        PF_TRY(read_max(4, 4, sb));
+        cheb.assign(K > 0 ? K : 1, BECheb{});
+        {
+            double sig1[4], rho0[4];
+            for (int b = 0; b < 4; b++) {
+                const double del = std::max(sb[b], 1e-12);
+                sig1[b] = 1.0 / del;               // theta = 1
+                rho0[b] = 1.0 / sig1[b];
+                cinit.c1[b] = 0.0;
+                cinit.c2[b] = 1.0;                 // d_0 = D^-1 r_0 / theta
+            }
+            for (int k = 0; k + 1 < K; k++)
+                for (int b = 0; b < 4; b++) {
+                    const double del = std::max(sb[b], 1e-12);
+                    const double rho1 = 1.0 / (2.0 * sig1[b] - rho0[b]);
+                    cheb[k].c1[b] = rho1 * rho0[b];
+                    cheb[k].c2[b] = 2.0 * rho1 / del;
+                    rho0[b] = rho1;
+                }
+        }
+        PF_TRY(Fval(w.y, w.F0));
+        double fmax;
+        PF_TRY(read_max(0, 1, &fmax));
+        // the update rule counts only after a linear solve that met its
+        // target (a stalled GMRES also gives small updates)
+        double moved = INFINITY, ymax = 0.0;
+        bool solved = false;
+        int it = 0;
+        bool conv = false;
+        for (;; it++) {
+            if (fmax <= o.newton_tol || (solved && moved <= o.newton_tol * std::max(1.0, ymax))) {
+                conv = true;
+                break;
+            }
+            if (it == o.newton_maxit) break;
+            // GMRES(m) on J delta = F0, right preconditioned, from delta = 0
+            PF_TRY(h->cuda(cudaMemsetAsync(w.x, 0, sizeof(double) * L, s), "gmres"));
+            double beta;
+            PF_TRY(dots(w.F0, 1, w.F0, &beta));
+            beta = sqrt(beta);
+            const double target = o.gmres_rtol * beta;
+            int inner = 0;
+            bool first = true;
+            while (beta > target && inner < o.gmres_maxit) {
+                if (first) {
+                    k_be_axpby<<<gL, 256, 0, s>>>(L, 1.0 / beta, w.F0, 0.0, w.F0, w.V);
+                } else {
+                    // r = F0 - J x
+                    PF_TRY(jvp(w.x, w.u));
+                    k_be_axpby<<<gL, 256, 0, s>>>(L, 1.0, w.F0, -1.0, w.u, w.u);
+                    double b2;
+                    PF_TRY(dots(w.u, 1, w.u, &b2));
+                    beta = sqrt(b2);
+                    if (beta <= target) break;
+                    k_be_axpby<<<gL, 256, 0, s>>>(L, 1.0 / beta, w.u, 0.0, w.u, w.V);
+                }
+                first = false;
+                std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
+                g[0] = beta;
+                int j = 0;
+                double res = beta;
+                for (; j < m && inner < o.gmres_maxit;) {
+                    double *vj = w.V + (size_t)j * L, *vn = w.V + (size_t)(j + 1) * L;
+                    PF_TRY(precond(vj, w.z));
+                    PF_TRY(jvp(w.z, vn));
+                    // classical Gram-Schmidt, twice
+                    double hc[64], h2[64], nh[64];
+                    PF_TRY(dots(w.V, j + 1, vn, hc));
+                    for (int k = 0; k <= j; k++) nh[k] = -hc[k];
+                    PF_TRY(comb(w.V, j + 1, nh, vn));
+                    PF_TRY(dots(w.V, j + 1, vn, h2));
+                    for (int k = 0; k <= j; k++) { nh[k] = -h2[k]; hc[k] += h2[k]; }
+                    PF_TRY(comb(w.V, j + 1, nh, vn));
+                    double hn;
+                    PF_TRY(dots(vn, 1, vn, &hn));
+                    hn = sqrt(hn);
+                    for (int k = 0; k <= j; k++) H[(size_t)k * m + j] = hc[k];
+                    H[(size_t)(j + 1) * m + j] = hn;
+                    if (hn > 0.0) k_be_axpby<<<gL, 256, 0, s>>>(L, 1.0 / hn, vn, 0.0, vn, vn);
+                    // Givens rotations of column j
+                    for (int k = 0; k < j; k++) {
+                        const double a0 = H[(size_t)k * m + j], a1 = H[(size_t)(k + 1) * m + j];
+                        H[(size_t)k * m + j] = cs[k] * a0 + sn[k] * a1;
+                        H[(size_t)(k + 1) * m + j] = -sn[k] * a0 + cs[k] * a1;
+                    }
+                    const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
+                    const double rr = hypot(a0, a1);
+                    cs[j] = rr > 0.0 ? a0 / rr : 1.0;
+                    sn[j] = rr > 0.0 ? a1 / rr : 0.0;
+                    H[(size_t)j * m + j] = rr;
+                    H[(size_t)(j + 1) * m + j] = 0.0;
+                    g[j + 1] = -sn[j] * g[j];
+                    g[j] = cs[j] * g[j];
+                    res = fabs(g[j + 1]);
+                    j++;
+                    inner++;
+                    if (res <= target || hn == 0.0) break;
+                }
+                // x += M^-1 V y, H y = g (upper triangular, j x j)
+                std::vector<double> yv(j, 0.0);
+                for (int k = j - 1; k >= 0; k--) {
+                    double t = g[k];
+                    for (int l = k + 1; l < j; l++) t -= H[(size_t)k * m + l] * yv[l];
+                    yv[k] = H[(size_t)k * m + k] != 0.0 ? t / H[(size_t)k * m + k] : 0.0;
+                }
+                PF_TRY(h->cuda(cudaMemsetAsync(w.u, 0, sizeof(double) * L, s), "gmres"));
+                if (j > 0) PF_TRY(comb(w.V, j, yv.data(), w.u));
+                PF_TRY(precond(w.u, w.z));
+                k_be_axpby<<<gL, 256, 0, s>>>(L, 1.0, w.x, 1.0, w.z, w.x);
+                beta = res;
+            }
+            st.gmres_iters += inner;
+            solved = beta <= target;
+            // Newton update
+            PF_TRY(h->cuda(cudaMemsetAsync(w.mx + 2, 0, 2 * sizeof(unsigned long long), s), "max"));
+            k_be_newton<<<gL, 256, 0, s>>>(L, w.x, w.y, w.mx + 2);
+            PF_TRY(check("newton update"));
+            double mm[2];
+            PF_TRY(read_max(2, 2, mm));
+            moved = mm[0];
+            ymax = mm[1];
+            PF_TRY(Fval(w.y, w.F0));
+            PF_TRY(read_max(0, 1, &fmax));
+        }
+        st.newton_iters = it;
+        st.newton_iters_total += it;
+        st.residual = fmax;
+        if (!conv) return h->fail(PF_ENOTCONV, "backward-Euler Newton iteration did not converge (max |F| %.3e)", fmax);
+        // the new fields, the balances of the step
+        k_be_rates<D><<<gN, 256, 0, s>>>(a, w.y, w.y0, w.der, w.Ft, 1, w.mx);
+        const int o_ = 1 - c;
+        const int nbf = std::min(gN, (int)(BE_NPART / 5));
+        k_be_finish<<<nbf, 256, 0, s>>>(a, w.y, w.y0, w.Ft, (double *)h->theta[o_], (double *)h->xO[o_],
+                                        (double *)h->xH[o_], (double *)h->xW[o_], w.part);
+        k_be_diag<<<1, 32, 0, s>>>(w.part, nbf, h->dg);
+        PF_TRY(check("backward-Euler step"));
+        advance(h, 1);
+        h->dt_last = o.dt;
+    }
+    return PF_OK;
+}
+
 } // namespace
 
 // ---------------------------------------------------------------------------
@@ -1290,7 +1578,9 @@ int pf_set_fields(pf_handle *h, const pf_fields *f, int where)
         return h->fail(PF_EINVAL, "phi_f, phi_w, x_O, x_H and x_H2O are required");
     if (where != PF_HOST && where != PF_DEVICE) return h->fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
     cudaStream_t s = h->own;
-    return h->fp64 ? set_fields_t<double>(h, f, where, s) : set_fields_t<float>(h, f, where, s);
+    const int rc = h->fp64 ? set_fields_t<double>(h, f, where, s) : set_fields_t<float>(h, f, where, s);
+    if (rc == PF_OK) h->dt_last = 0.0;
+    return rc;
 }
 
 int pf_step(pf_handle *h, int nsteps, void *stream)
@@ -1326,6 +1616,8 @@ int pf_step(pf_handle *h, int nsteps, void *stream)
     if (h->cfg.ndim == 2) rc = h->fp64 ? run_steps<double, 2>(h, nsteps, s) : run_steps<float, 2>(h, nsteps, s);
     else rc = h->fp64 ? run_steps<double, 3>(h, nsteps, s) : run_steps<float, 3>(h, nsteps, s);
     if (rc != PF_OK) return rc;
+    if (nsteps > 0)
+        for (pf_handle *m : instances(h)) m->dt_last = 0.0;
     std::vector<pf_handle *> I = instances(h);
     std::vector<Scalars> scs(I.size());
     std::vector<Diag> dgs(I.size());
@@ -1355,6 +1647,45 @@ int pf_step(pf_handle *h, int nsteps, void *stream)
     return PF_OK;
 }
 
+int pf_step_implicit(pf_handle *h, int nsteps, const pf_implicit_opts *opts, pf_implicit_stats *stats, void *stream)
+{
+    if (!h || !opts) return PF_EINVAL;
+    if (nsteps < 0) return h->fail(PF_EINVAL, "nsteps < 0");
+    if (h->is_batch) return h->fail(PF_EINVAL, "backward-Euler steps take a single-grid handle");
+    if (!h->fp64) return h->fail(PF_EINVAL, "backward-Euler steps need precision PF_FP64");
+    if (!h->have_fields) return h->fail(PF_ESTATE, "pf_step_implicit before the fields were set");
+    const pf_implicit_opts &o = *opts;
+    if (!(o.dt > 0.0) || !(o.newton_tol > 0.0) || o.newton_maxit < 1 || !(o.gmres_rtol > 0.0 && o.gmres_rtol < 1.0) ||
+        o.gmres_restart < 1 || o.gmres_restart > BE_MAX_RESTART || o.gmres_maxit < 1 || o.pc_degree < 0 ||
+        o.pc_degree > 64)
+        return h->fail(PF_EINVAL, "invalid pf_implicit_opts");
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->own;
+    if (h->own != s) {
+        cudaEvent_t ev;
+        PF_TRY(h->cuda(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event"));
+        cudaEventRecord(ev, h->own);
+        cudaStreamWaitEvent(s, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    PF_TRY(h->cuda(cudaMemsetAsync(&h->sc->status, 0, sizeof(int), s), "status clear"));
+    PF_TRY(h->cuda(cudaMemsetAsync(&h->dg->status, 0, sizeof(int), s), "status clear"));
+    PF_TRY(h->cuda(cudaMemsetAsync(&h->dg->cg_max, 0, sizeof(int), s), "status clear"));
+    pf_implicit_stats st;
+    memset(&st, 0, sizeof(st));
+    const int rc = h->cfg.ndim == 2 ? be_steps<2>(h, nsteps, o, st, s) : be_steps<3>(h, nsteps, o, st, s);
+    if (stats) *stats = st;
+    if (rc != PF_OK) return rc;
+    Scalars sc;
+    Diag dg;
+    PF_TRY(h->cuda(cudaMemcpyAsync(&sc, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s), "status read"));
+    PF_TRY(h->cuda(cudaMemcpyAsync(&dg, h->dg, sizeof(Diag), cudaMemcpyDeviceToHost, s), "status read"));
+    PF_TRY(h->cuda(cudaStreamSynchronize(s), "pf_step_implicit"));
+    if (sc.status == 6 || dg.status == 6) return h->fail(PF_ETIMEOUT, "a bounded device-side wait gave up");
+    if (dg.status == 5) return h->fail(PF_ENONFINITE, "non-finite value in the fields");
+    if (sc.status == 4) return h->fail(PF_ENOTCONV, "CG reached cg_maxit without meeting cg_rtol");
+    return PF_OK;
+}
+
 int pf_get_fields(pf_handle *h, pf_fields *out, int where)
 {
     if (!h || !out) return PF_EINVAL;
@@ -1380,13 +1711,15 @@ int pf_get_diagnostics(pf_handle *h, pf_diag *out)
     // reduction rate of the last step, -(sum x_O,n - sum x_O,n-1) / (sum x_O,init dt)
     // (Sec. 4.2.1); before the first update the previous sum is the initial one
     const double prevO = h->steps == 1 ? h->sumO0 : dg.sumO_prev;
-    out->reduction_rate = h->sumO0 != 0.0 && h->steps > 0 ? (prevO - dg.sumO) / (h->sumO0 * h->P.dt) : 0.0;
+    // the last step's time step: backward-Euler steps take their own
+    const double dt = h->dt_last > 0.0 ? h->dt_last : h->P.dt;
+    out->reduction_rate = h->sumO0 != 0.0 && h->steps > 0 ? (prevO - dg.sumO) / (h->sumO0 * dt) : 0.0;
     out->cg_rel_residual = sc.relres;
     out->cg_iters_last = dg.cg_last;
     out->cg_iters_max = dg.cg_max;
     out->cg_iters_total = dg.cg_total;
     out->steps = h->steps;
-    out->dt = h->P.dt;
+    out->dt = dt;
     out->status = dg.status ? dg.status : sc.status;
     out->precond = h->mg ? PF_PC_MG : PF_PC_JACOBI;
     out->mg_levels = !h->mg ? 0 : (h->cfg.ndim == 2 ? mg_levels(h->P.nx, h->P.ny) : mg_levels3(h->P.nx, h->P.ny, h->P.nz));

@@ -67,6 +67,17 @@ PF_K_SETUP, PF_K_CG, PF_K_RETURN, PF_K_UPDATE, PF_K_WARM, PF_K_NCLASS = range(6)
 KERNEL_CLASSES = ["setup", "cg", "return", "update", "warm"]
 
 
+class pf_implicit_opts(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
+                ("gmres_rtol", ctypes.c_double), ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
+                ("pc_degree", ctypes.c_int)]
+
+
+class pf_implicit_stats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("newton_iters_total", ctypes.c_int),
+                ("gmres_iters", ctypes.c_longlong), ("residual", ctypes.c_double)]
+
+
 class pf_profile(ctypes.Structure):
     _fields_ = [("enabled", ctypes.c_int), ("launches", ctypes.c_longlong),
                 ("count", ctypes.c_longlong * PF_K_NCLASS), ("ms", ctypes.c_double * PF_K_NCLASS),
@@ -79,7 +90,7 @@ class pf_unet_config(ctypes.Structure):
 
 
 # exported symbols, in the order of include/pf.h then include/pf_unet.h
-SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_get_fields", "pf_get_diagnostics",
+SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_step_implicit", "pf_get_fields", "pf_get_diagnostics",
            "pf_free_energy", "pf_dt_stable", "pf_profile_enable", "pf_profile_read",
            "pf_batch_create", "pf_batch_size", "pf_batch_set_fields", "pf_batch_get_fields",
            "pf_batch_get_diagnostics", "pf_attach_unet", "pf_selftest_wait",
@@ -149,6 +160,9 @@ def lib():
         l.pf_set_fields.restype = ctypes.c_int
         l.pf_step.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
         l.pf_step.restype = ctypes.c_int
+        l.pf_step_implicit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(pf_implicit_opts),
+                                       ctypes.POINTER(pf_implicit_stats), ctypes.c_void_p]
+        l.pf_step_implicit.restype = ctypes.c_int
         l.pf_get_fields.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_fields), ctypes.c_int]
         l.pf_get_fields.restype = ctypes.c_int
         l.pf_get_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_diag)]
@@ -227,6 +241,13 @@ def pf_set_fields(h, fields, where=PF_HOST):
 
 def pf_step(h, nsteps, stream=None):
     return lib().pf_step(h, int(nsteps), ctypes.c_void_p(stream) if stream else None)
+
+
+def pf_step_implicit(h, nsteps, opts, stream=None):
+    st = pf_implicit_stats()
+    rc = lib().pf_step_implicit(h, int(nsteps), ctypes.byref(opts), ctypes.byref(st),
+                                ctypes.c_void_p(stream) if stream else None)
+    return rc, st
 
 
 def pf_get_fields(h, fields, where=PF_HOST):

@@ -63,6 +63,7 @@ def test_create_without_gpu_fails_cleanly(lib):
 
 def test_null_handle_calls(lib):
     assert lib.pf_step(None, 1, None) == native.PF_EINVAL
+    assert lib.pf_step_implicit(None, 1, None, None, None) == native.PF_EINVAL
     assert lib.pf_set_fields(None, None, 0) == native.PF_EINVAL
     lib.pf_destroy(None)
 
@@ -125,6 +126,7 @@ def test_ctypes_structs_match_the_c_layout():
     offsets and sizes of the C structs in the headers."""
     structs = [("pf_params", native.pf_params), ("pf_config", native.pf_config), ("pf_fields", native.pf_fields),
                ("pf_diag", native.pf_diag), ("pf_profile", native.pf_profile),
+               ("pf_implicit_opts", native.pf_implicit_opts), ("pf_implicit_stats", native.pf_implicit_stats),
                ("pf_unet_config", native.pf_unet_config)]
     c = _c_layout(structs)
     for name, cls in structs:
