@@ -10,7 +10,7 @@ FP64 iterative refinement of the solve) gives ``value``; the plain FP64
 method is measured beside it on the same GPU and the same input.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload porous256cube|coreshell512|porous2048|batch64|stencil]
+                    [--workload porous256cube|coreshell512|porous2048|batch64|stencil|implicit]
 
 Under torchrun (N > 1) every rank advances its own replica of the workload
 (the single-grid step does not shard; see the design notes) and ``value`` is
@@ -469,6 +469,51 @@ def short_line(name, steps, warmup):
     return line
 
 
+def backward_euler_line(n=256, steps=3, dt=0.05, explicit_steps=20):
+    """Backward-Euler steps (pf_step_implicit, FP64) at the paper's Table 1
+    diffusivities and reaction rate (workloads.paper_params) on the n x n
+    core-shell of the 512^2 recipe, beside explicit steps of the same model
+    (the library's dt: 0.2 x the explicit limit): physical time advanced per
+    wall-clock second both ways.  Wall clock (the Newton-Krylov loop is
+    driven from the host)."""
+    import time
+    import torch
+    from paper_2111_11538_gb300 import Simulation, inputs, workloads
+    f = inputs.core_shell((n, n), 0.3125 * n, 0.0625 * n)
+    prm = workloads.paper_params(cg_rtol=1e-10)
+    sim = Simulation((n, n), prm, precision="fp64")
+    sim.set_fields(f)
+    sim.step_implicit(1, dt)                   # allocations, first solve
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    newton = gmres = 0
+    for _ in range(steps):
+        st = sim.step_implicit(1, dt)
+        newton += st["newton_iters"]
+        gmres += st["gmres_iters"]
+    t_imp = (time.perf_counter() - t0) / steps
+    d = sim.diagnostics()
+    sim.close()
+    ex = Simulation((n, n), prm, precision="fp64")
+    ex.set_fields(f)
+    ex.step(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ex.step(explicit_steps)
+    t_exp = (time.perf_counter() - t0) / explicit_steps
+    dt_e = ex.diagnostics()["dt"]
+    ex.close()
+    return {"workload": "core-shell %dx%d, paper Table 1 diffusivities and k_for (explicit limit %.2e), FP64"
+                        % (n, n, dt_e / 0.2),
+            "dt": dt, "s_per_step": t_imp, "newton_iters_per_step": newton / steps,
+            "gmres_iters_per_step": gmres / steps, "explicit_dt": dt_e, "explicit_s_per_step": t_exp,
+            "explicit_steps_per_step": dt / dt_e,
+            "physical_time_per_s": dt / t_imp, "explicit_physical_time_per_s": dt_e / t_exp,
+            "speedup_vs_explicit": (dt / t_imp) / (dt_e / t_exp),
+            "balances": {"O": d["sum_O"] + d["sum_H2O"] + d["removed_H2O"],
+                         "H": d["sum_H"] + 2 * d["sum_H2O"] + 2 * d["removed_H2O"] - d["supplied_H"]}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -481,7 +526,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads' keys")
     ap.add_argument("--workload", default="porous256cube",
                     help="porous256cube (default, the headline); coreshell512, porous2048, coreshell64, "
-                         "batch64 or stencil print a short line")
+                         "batch64, stencil or implicit (backward-Euler steps at the paper's "
+                         "diffusivities) print a short line")
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"],
                     help="profiling aid: run one method only and print a short line")
     ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "mg"],
@@ -544,6 +590,9 @@ def main():
                                 args.warmup),
                stencil_roofline(workload_fields("porous2048"), "porous2048", args.steps, args.warmup)]
         print(json.dumps(out))
+        return
+    if WORKLOAD == "implicit":
+        print(json.dumps(backward_euler_line()))
         return
     if WORKLOAD == "batch64":
         meth = "mixed" if args.only == "both" else args.only
@@ -619,6 +668,10 @@ def main():
             extra["roofline_stencil_2d"] = stencil_roofline(workload_fields("porous2048"), "porous2048")
         except Exception as e:  # noqa: BLE001
             extra["roofline_stencil_2d"] = {"error": str(e)[:200]}
+        try:
+            extra["backward_euler"] = backward_euler_line()
+        except Exception as e:  # noqa: BLE001
+            extra["backward_euler"] = {"error": str(e)[:200]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:

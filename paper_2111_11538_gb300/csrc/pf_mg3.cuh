@@ -90,12 +90,14 @@ template <typename T> struct MGZPipe { static constexpr bool on = sizeof(T) == 4
 
 // Shared memory (values of T) of mg_sweep3z with at most ns raw streams: two
 // node planes, the eight corner forces of one cell plane with their halos,
-// and the staged nodes' raw streams (two planes when they are copied ahead).
+// the staged nodes' raw streams (two planes when they are copied ahead) and,
+// when copied ahead, the cell moduli of three planes.
 template <typename T>
 __host__ __device__ constexpr int mg_sweep3z_words(int ns = MGZ_NS)
 {
     return V3S<T>::WORDS * (2 * (MGZ_TX + 2) * (MGZ_TY + 2) + 8 * (MGZ_TX + 1) * (MGZ_TY + 1)) +
-           MGZPipe<T>::RB * ns * (MGZ_TX + 2) * (MGZ_TY + 2);
+           MGZPipe<T>::RB * ns * (MGZ_TX + 2) * (MGZ_TY + 2) +
+           (MGZPipe<T>::on ? 6 * (MGZ_TX + 1) * (MGZ_TY + 1) : 0);
 }
 
 // z-chunk of the 3D sweep on an nx x ny x nz level with nbk blocks: the
@@ -128,7 +130,8 @@ __device__ __forceinline__ int mg_zchunk(int nx, int ny, int nz, int nbk)
 // the previous plane's work; raw[s * NP + h] is stream s at staged node h),
 // every cell of the plane (with the halo cells at x0 - 1, y0 - 1) computes
 // its average stress and hourglass forces once (cell_force3; its moduli, of
-// type TM, are read one plane ahead) and its forces on its eight corners
+// type TM, are copied with the raw streams two planes ahead in FP32 and read
+// one plane ahead in FP64) and its forces on its eight corners
 // (corner_forces3), and each own node of plane zp adds its bottom-corner
 // forces to the top-corner forces left by plane zp - 1: q = A v is complete
 // and epi(n, v, q) receives it.  pref(n) runs for each own node of plane zp
@@ -151,6 +154,8 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
     constexpr int CPT = (NC + NT - 1) / NT;                 // cells per thread
     T *const np0 = smem, *const np1 = smem + W * NP, *const cf = smem + 2 * W * NP;
     T *const rawb = cf + 8 * W * NC;                        // [RB][MGZ_NS][NP]
+    T *const modb = rawb + MGZPipe<T>::RB * MGZ_NS * NP;     // FP32: [3][lam, mu][NC]
+    static_assert(!PIPE || std::is_same<TM, T>::value, "copied moduli have the sweep's type");
     const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, nzc = (nz + zc - 1) / zc;
     const int items = ntx * nty * nzc;
     const bool small = nx < NX || ny < NY;
@@ -174,6 +179,21 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
                     else raw[q * NP + h] = __ldcg(src[q] + g);
                 }
             }
+            if constexpr (PIPE) {
+                // the moduli of this thread's cells of plane z (read by this
+                // thread only)
+                T *md = modb + ((z + 3) % 3) * 2 * NC;
+#pragma unroll
+                for (int u = 0; u < CPT; u++) {
+                    const int h = threadIdx.x + u * NT;
+                    if (h < NC) {
+                        const int cx = h % CX, cy = h / CX;
+                        const int g = mg_wrap(x0 - 1 + cx, nx, small) + nx * (mg_wrap(y0 - 1 + cy, ny, small) + ny * zw);
+                        cp_async(md + h, reinterpret_cast<const T *>(lam) + g);
+                        cp_async(md + NC + h, reinterpret_cast<const T *>(mu) + g);
+                    }
+                }
+            }
         };
         // node plane z formed from its raw streams (each thread forms the
         // nodes whose streams it copied)
@@ -187,7 +207,7 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
                 V3S<T>::st(buf, NP, h, v);
             }
         };
-        // moduli of this thread's cells of plane z
+        // moduli of this thread's cells of plane z (FP64: into registers)
         auto moduli = [&](int z, T (&l)[CPT], T (&m)[CPT]) {
             const int zw = zwrap(z);
 #pragma unroll
@@ -210,7 +230,7 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
         }
         form(z0 - 1, ((z0 - 1) & 1) ? np1 : np0);
         T lc[CPT], mc[CPT];
-        moduli(z0 - 1, lc, mc);
+        if constexpr (!PIPE) moduli(z0 - 1, lc, mc);
         T qt[3] = {T(0), T(0), T(0)};     // top-corner forces of the previous cell plane on the own node
         for (int zp = z0 - 1; zp < z1; zp++) {
             T *const nlo = (zp & 1) ? np1 : np0;
@@ -226,7 +246,8 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
             }
             form(zp + 1, nhi);
             T ln[CPT], mn[CPT];
-            if (zp + 1 < z1) moduli(zp + 1, ln, mn);
+            if constexpr (!PIPE)
+                if (zp + 1 < z1) moduli(zp + 1, ln, mn);
             __syncthreads();
             const bool inner = zp >= z0;
 #pragma unroll
@@ -234,7 +255,8 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
                 const int h = threadIdx.x + u * NT;
                 if (h >= NC) continue;
                 const int cx = h % CX, cy = h / CX;
-                const T l = lc[u], m = mc[u];
+                const T *md = modb + ((zp + 3) % 3) * 2 * NC;
+                const T l = PIPE ? md[h] : lc[u], m = PIPE ? md[NC + h] : mc[u];
                 T uc[8][3];
 #pragma unroll
                 for (int b = 0; b < 8; b++) V3S<T>::ld((b >> 2) ? nhi : nlo, NP, (cx + (b & 1)) + NX * (cy + ((b >> 1) & 1)), uc[b]);
@@ -254,9 +276,11 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
             }
             T un[3];
             if (own && inner) V3S<T>::ld(nlo, NP, (tx + 1) + NX * (ty + 1), un);
-            if (zp + 1 < z1) {
+            if constexpr (!PIPE) {
+                if (zp + 1 < z1) {
 #pragma unroll
-                for (int u = 0; u < CPT; u++) { lc[u] = ln[u]; mc[u] = mn[u]; }
+                    for (int u = 0; u < CPT; u++) { lc[u] = ln[u]; mc[u] = mn[u]; }
+                }
             }
             __syncthreads();
             if (own) {
@@ -609,8 +633,10 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
         const T ta = s_ta, tb = s_tb;
         const int nxt = first ? cur : 1 - cur;
 
-        // ---- finest level, first pre-smoothing sweep (+ the CG update)
+        // ---- finest level, first pre-smoothing sweep (+ the CG update); its
+        // Chebyshev direction is read only by further smoothing steps there
         Acc<T> racc[1];
+        const bool d0 = (L == 1 ? cs - 1 : H.deg[0]) > 1;
         {
             const T c2 = H.c2[0];
             sweep(0, first ? 4 : 10,
@@ -643,7 +669,7 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                         }
                         L0.xpre[c][n] = v[c];
                         L0.r[1][c][n] = f - q[c];
-                        L0.d[1][c][n] = v[c];
+                        if (d0) L0.d[1][c][n] = v[c];
                     }
                 },
                 [&](int n) {
