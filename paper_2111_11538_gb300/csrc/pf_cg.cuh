@@ -1001,7 +1001,7 @@ size_t pcg_dyn_smem(int shape, bool mg)
         // the 3D V-cycle's sweeps (mg_sweep3z in T), or the set-up sweep's
         // (FP64, three raw streams)
         const size_t cells = sizeof(T) * (size_t)mg_sweep3z_words<T>();
-        const size_t stp = sizeof(double) * (size_t)mg_sweep3z_words<double>(3);
+        const size_t stp = sizeof(double) * (size_t)mg_sweep3z_words<double, true>(3);
         return cells > stp ? cells : stp;
     }
     if (D != 3 || sizeof(T) != 4 || shape != 0) return 0;

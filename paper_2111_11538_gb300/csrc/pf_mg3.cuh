@@ -90,14 +90,14 @@ template <typename T> struct MGZPipe { static constexpr bool on = sizeof(T) == 4
 
 // Shared memory (values of T) of mg_sweep3z with at most ns raw streams: two
 // node planes, the eight corner forces of one cell plane with their halos,
-// the staged nodes' raw streams (two planes when they are copied ahead) and,
-// when copied ahead, the cell moduli of three planes.
-template <typename T>
+// the staged nodes' raw streams (two planes when they are copied ahead,
+// PIPE) and, in FP32, the cell moduli of three planes.
+template <typename T, bool PIPE = MGZPipe<T>::on>
 __host__ __device__ constexpr int mg_sweep3z_words(int ns = MGZ_NS)
 {
     return V3S<T>::WORDS * (2 * (MGZ_TX + 2) * (MGZ_TY + 2) + 8 * (MGZ_TX + 1) * (MGZ_TY + 1)) +
-           MGZPipe<T>::RB * ns * (MGZ_TX + 2) * (MGZ_TY + 2) +
-           (MGZPipe<T>::on ? 6 * (MGZ_TX + 1) * (MGZ_TY + 1) : 0);
+           (PIPE ? 2 : 1) * ns * (MGZ_TX + 2) * (MGZ_TY + 2) +
+           (PIPE && sizeof(T) == 4 ? 6 * (MGZ_TX + 1) * (MGZ_TY + 1) : 0);
 }
 
 // z-chunk of the 3D sweep on an nx x ny x nz level with nbk blocks: the
@@ -131,7 +131,9 @@ __device__ __forceinline__ int mg_zchunk(int nx, int ny, int nz, int nbk)
 // every cell of the plane (with the halo cells at x0 - 1, y0 - 1) computes
 // its average stress and hourglass forces once (cell_force3; its moduli, of
 // type TM, are copied with the raw streams two planes ahead in FP32 and read
-// one plane ahead in FP64) and its forces on its eight corners
+// one plane ahead in FP64; PIPE: the raw streams are copied into shared
+// memory one plane ahead, the default in FP32) and its forces on its eight
+// corners
 // (corner_forces3), and each own node of plane zp adds its bottom-corner
 // forces to the top-corner forces left by plane zp - 1: q = A v is complete
 // and epi(n, v, q) receives it.  pref(n) runs for each own node of plane zp
@@ -141,7 +143,8 @@ __device__ __forceinline__ int mg_zchunk(int nx, int ny, int nz, int nbk)
 // own cell without it (c[0..5]).  smem: mg_sweep3z_words<T>(ns) values; src:
 // ns pointers (shared memory, set by the caller); two block barriers per
 // plane.
-template <typename T, bool WITH_E, class TM, class Make, class Epi, class CellE, class Pref>
+template <typename T, bool WITH_E, bool PIPE_ = MGZPipe<T>::on, class TM, class Make, class Epi, class CellE,
+          class Pref>
 __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const TM *lam, const TM *mu, int bid,
                                            int nbk, T *smem, const T *ue, int ns, const T *const *src, Make &&make,
                                            Epi &&epi, CellE &&cell_e, Pref &&pref)
@@ -150,12 +153,12 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
     constexpr int NX = TX + 2, NY = TY + 2, NP = NX * NY;
     constexpr int CX = TX + 1, CY = TY + 1, NC = CX * CY, NT = TX * TY;
     constexpr int W = V3S<T>::WORDS;
-    constexpr bool PIPE = MGZPipe<T>::on;
+    constexpr bool PIPE = PIPE_, MODC = PIPE && sizeof(T) == 4;   // copied raw streams / moduli
     constexpr int CPT = (NC + NT - 1) / NT;                 // cells per thread
     T *const np0 = smem, *const np1 = smem + W * NP, *const cf = smem + 2 * W * NP;
-    T *const rawb = cf + 8 * W * NC;                        // [RB][MGZ_NS][NP]
-    T *const modb = rawb + MGZPipe<T>::RB * MGZ_NS * NP;     // FP32: [3][lam, mu][NC]
-    static_assert(!PIPE || std::is_same<TM, T>::value, "copied moduli have the sweep's type");
+    T *const rawb = cf + 8 * W * NC;                        // [PIPE ? 2 : 1][ns][NP]
+    T *const modb = rawb + 2 * MGZ_NS * NP;                  // MODC: [3][lam, mu][NC]
+    static_assert(!MODC || std::is_same<TM, T>::value, "copied moduli have the sweep's type");
     const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, nzc = (nz + zc - 1) / zc;
     const int items = ntx * nty * nzc;
     const bool small = nx < NX || ny < NY;
@@ -166,7 +169,7 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
         const int z1 = min(z0 + zc, nz);
         const int gx = x0 + tx, gy = y0 + ty;
         const bool own = gx < nx && gy < ny;
-        auto raw_of = [&](int z) { return rawb + (PIPE ? (z & 1) : 0) * (MGZ_NS * NP); };
+        auto raw_of = [&](int z) { return rawb + (PIPE ? (z & 1) : 0) * (ns * NP); };
         // raw streams of node plane z: asynchronous copies (FP32) or loads
         auto issue = [&](int z) {
             const int zw = zwrap(z);
@@ -179,7 +182,7 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
                     else raw[q * NP + h] = __ldcg(src[q] + g);
                 }
             }
-            if constexpr (PIPE) {
+            if constexpr (MODC) {
                 // the moduli of this thread's cells of plane z (read by this
                 // thread only)
                 T *md = modb + ((z + 3) % 3) * 2 * NC;
@@ -230,7 +233,7 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
         }
         form(z0 - 1, ((z0 - 1) & 1) ? np1 : np0);
         T lc[CPT], mc[CPT];
-        if constexpr (!PIPE) moduli(z0 - 1, lc, mc);
+        if constexpr (!MODC) moduli(z0 - 1, lc, mc);
         T qt[3] = {T(0), T(0), T(0)};     // top-corner forces of the previous cell plane on the own node
         for (int zp = z0 - 1; zp < z1; zp++) {
             T *const nlo = (zp & 1) ? np1 : np0;
@@ -246,7 +249,7 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
             }
             form(zp + 1, nhi);
             T ln[CPT], mn[CPT];
-            if constexpr (!PIPE)
+            if constexpr (!MODC)
                 if (zp + 1 < z1) moduli(zp + 1, ln, mn);
             __syncthreads();
             const bool inner = zp >= z0;
@@ -256,7 +259,7 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
                 if (h >= NC) continue;
                 const int cx = h % CX, cy = h / CX;
                 const T *md = modb + ((zp + 3) % 3) * 2 * NC;
-                const T l = PIPE ? md[h] : lc[u], m = PIPE ? md[NC + h] : mc[u];
+                const T l = MODC ? md[h] : lc[u], m = MODC ? md[NC + h] : mc[u];
                 T uc[8][3];
 #pragma unroll
                 for (int b = 0; b < 8; b++) V3S<T>::ld((b >> 2) ? nhi : nlo, NP, (cx + (b & 1)) + NX * (cy + ((b >> 1) & 1)), uc[b]);
@@ -276,7 +279,7 @@ __device__ __forceinline__ void mg_sweep3z(int nx, int ny, int nz, int zc, const
             }
             T un[3];
             if (own && inner) V3S<T>::ld(nlo, NP, (tx + 1) + NX * (ty + 1), un);
-            if constexpr (!PIPE) {
+            if constexpr (!MODC) {
                 if (zp + 1 < z1) {
 #pragma unroll
                     for (int u = 0; u < CPT; u++) { lc[u] = ln[u]; mc[u] = mn[u]; }
@@ -351,7 +354,9 @@ __device__ void mg_coarsen3(const MGLevel<T> &F, const MGLevel<T> &C, long long 
 // rows (acc[0] ||b||^2, [1] ||r||^2, [2] sum lam, [3] sum mu, [4..9] sum
 // sig*, [10..15] the cells' stress of x without the mean strain).  resid: a
 // later refinement pass, which reads b from A.b64 and skips what does not
-// change during a solve.  smem: mg_sweep3z_words<double>(3) doubles.
+// change during a solve.  Its three raw streams (x) are copied one plane ahead
+// like the FP32 sweeps' (8-byte asynchronous copies).  smem:
+// mg_sweep3z_words<double, true>(3) doubles.
 template <typename T>
 __device__ void setup_march3(const PCGArgs<T, 3> &A, bool use_x, bool refine, bool resid, const double *xe,
                              double *smem, Acc<double> (&acc)[16], int bid, int nbk)
@@ -401,7 +406,7 @@ __device__ void setup_march3(const PCGArgs<T, 3> &A, bool use_x, bool refine, bo
             else s_xs[c] = A.x64[c];
         }
     __syncthreads();
-    mg_sweep3z<double, true>(
+    mg_sweep3z<double, true, true>(
         P.nx, P.ny, P.nz, mg_zchunk(P.nx, P.ny, P.nz, nbk), A.lam, A.mu, bid, nbk, smem, xe, 3, s_xs,
         [&](const double *raw, int h, int, int, int, double (&v)[3]) {
 #pragma unroll
