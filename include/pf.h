@@ -237,6 +237,48 @@ typedef struct {
 int pf_step_implicit(pf_handle *h, int nsteps, const pf_implicit_opts *opts, pf_implicit_stats *stats,
                      void *cudaStream);
 
+/* Finite-strain elastic equilibrium with the transformation stretch, for
+ * given order parameter and gas fraction (Sec. 2.2: F_R = F_T F_P with
+ * F_T = d_T^(1/3) I, d_T = 1 - W_f omega (RulFloDefLocAlt); the energy
+ * d_T sum_a W_a phi_a(F_E), F_E = F F_R^-1, with the neo-Hooke phase energy
+ * phi_a = K_a/4 (J_E^2 - 1 - 2 ln J_E) + G_a/2 (J_E^(-2/3) |F_E|^2 - 3)
+ * (DenEneFreIntElaPha), K_a, G_a from cfg->p (E_s, nu, E_g_ratio); Sec. 2.4:
+ * Div P = 0), with F_P = I.  The library's readings: P is the derivative of
+ * that energy (half the printed stress); Q1 voxel elements with 2^d Gauss
+ * points on the periodic grid of cfg (2D plane strain, F_33 = 1); F = Fbar +
+ * grad u, Fbar symmetric, the symmetric part of the mean first Piola stress
+ * prescribed (pbar, d x d row-major; NULL: -cfg->p.prestress I); u = 0 at
+ * node 0.  Newton's method over opts->nload equal steps of omega, each
+ * Newton system solved by conjugate gradients on the energy's Hessian
+ * (products evaluated in forward mode) with the small-strain diagonal as
+ * preconditioner; stops when max |residual| <= opts->newton_tol.
+ *   theta, phi_g : host arrays of N cells (cell-major, x fastest)
+ *   u            : out, host, N * ndim (u[n * ndim + c], node n = lower
+ *                  corner of cell n)
+ *   Fbar         : out, host, ndim * ndim row-major
+ * Uses the current device; allocates and frees its own device memory;
+ * blocking.  Returns PF_EINVAL (arguments), PF_ENOMEM, PF_ECUDA, PF_ENOTCONV
+ * (Newton over newton_maxit in a load step; stats still filled);
+ * pf_fs_last_error() gives the text.  Not part of the explicit step. */
+typedef struct {
+    int nload;          /* load steps of omega (>= 1)                    */
+    int newton_maxit;   /* Newton iterations per load step (>= 1)        */
+    double newton_tol;  /* max |residual| at convergence (> 0)           */
+    int cg_maxit;       /* CG iterations per Newton system (>= 1)        */
+    double cg_rtol;     /* CG relative residual per Newton system (0, 1) */
+} pf_fs_opts;
+
+typedef struct {
+    int newton_iters;   /* over all load steps                           */
+    long long cg_iters; /* over all Newton systems                       */
+    double residual;    /* max |residual| at the end                     */
+} pf_fs_stats;
+
+int pf_finite_strain_solve(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
+                           const double *pbar, const pf_fs_opts *opts, double *u, double *Fbar,
+                           pf_fs_stats *stats);
+const char *pf_fs_last_error(void);
+
 /* Copy the current state (the fields of Sec. 2.4 and the mechanical state)
  * out into caller arrays (FP64); NULL members are skipped.  sigma is the
  * stress of the last return map (Sec. 2.3).  mobility / dirichlet are

@@ -1,0 +1,517 @@
+// Finite-strain elastic equilibrium with the transformation stretch on the
+// GPU (the C ABI's pf_finite_strain_solve, include/pf.h).
+//
+// Sec. 2.2 of the paper: the residual deformation F_R = F_T F_P with
+// F_T = d_T^(1/3) I, d_T = 1 - W_f Omega (RulFloDefLocAlt, with the phase
+// weights of the small-strain model); the elastic energy per reference
+// volume psi = d_T phi(F_E), F_E = F F_R^-1 = d_T^(-1/3) F (F_P = I here),
+// with the neo-Hooke energy of the phase mixture
+//     phi(F_E) = K/4 (J_E^2 - 1 - 2 ln J_E) + G/2 (J_E^(-2/3) |F_E|^2 - 3)
+// (DenEneFreIntElaPha; K, G the weighted bulk and shear moduli).  The
+// equilibrium Div P = 0 (Sec. 2.4) is the stationarity of the total energy
+// sum_cells w sum_gauss psi(F) - N pbar : Fbar over the periodic box, with
+// F = Fbar + grad u at the 2^d Gauss points of Q1 voxel elements, Fbar
+// symmetric, u = 0 at node 0; P = d psi / d F.  2D is plane strain
+// (F_33 = 1).
+//
+// Newton's method in load steps of Omega; each Newton system H delta = -r is
+// solved by conjugate gradients (H, the Hessian of the energy, is symmetric)
+// preconditioned by the diagonal of the small-strain operator; every
+// product H v is the directional derivative of the residual along v,
+// evaluated in forward mode (value, derivative) through the same cell
+// function as the residual.  FP64 throughout.  Not on the explicit step's
+// hot path: the call allocates and frees its device memory.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pf.h"
+
+namespace {
+
+thread_local std::string g_fs_error;
+
+struct FD {   // value and directional derivative
+    double v, d;
+    __host__ __device__ FD() {}
+    __host__ __device__ FD(double a) : v(a), d(0.0) {}
+    __host__ __device__ FD(double a, double b) : v(a), d(b) {}
+};
+__device__ __forceinline__ FD operator+(FD a, FD b) { return FD(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ FD operator-(FD a, FD b) { return FD(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ FD operator*(FD a, FD b) { return FD(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ FD operator/(FD a, FD b)
+{
+    const double q = a.v / b.v;
+    return FD(q, (a.d - q * b.d) / b.v);
+}
+__device__ __forceinline__ FD fd_pow(FD a, double p)
+{
+    const double q = pow(a.v, p);
+    return FD(q, p * q / a.v * a.d);
+}
+__device__ __forceinline__ double fd_pow(double a, double p) { return pow(a, p); }
+
+struct FSArgs {
+    int d, nx, ny, nz;
+    long long N;
+    const double *K, *G, *Wf;    // per cell
+    double omega;                // transformation of this load step
+};
+
+// local shape-function derivative dN/dx_k of corner a at Gauss point g
+// (bit l of a: corner offset along axis l; bit l of g: Gauss abscissa
+// 1/2 +- 1/(2 sqrt 3) along axis l)
+__device__ __forceinline__ double dshape(int d, int g, int a, int k)
+{
+    const double ga = 0.5 - 0.5 / sqrt(3.0), gb = 0.5 + 0.5 / sqrt(3.0);
+    double v = 1.0;
+    for (int l = 0; l < d; l++) {
+        const int bit = (a >> l) & 1;
+        const double xi = ((g >> l) & 1) ? gb : ga;
+        v *= l == k ? (bit ? 1.0 : -1.0) : (bit ? xi : 1.0 - xi);
+    }
+    return v;
+}
+
+__device__ __forceinline__ long long fs_node(const FSArgs &A, long long c, int a)
+{
+    const int i = (int)(c % A.nx);
+    const long long r = c / A.nx;
+    const int j = (int)(r % A.ny), k = (int)(r / A.ny);
+    const int ii = (i + (a & 1)) % A.nx, jj = (j + ((a >> 1) & 1)) % A.ny;
+    const int kk = A.d == 3 ? (k + ((a >> 2) & 1)) % A.nz : 0;
+    return ii + (long long)A.nx * (jj + (long long)A.ny * kk);
+}
+
+// first Piola stress of cell c at deformation F (3 x 3, row-major)
+template <typename S>
+__device__ void fs_piola(const FSArgs &A, long long c, const S (&F)[9], S (&P)[9])
+{
+    const double dT = 1.0 - A.Wf[c] * A.omega, s = pow(dT, -1.0 / 3.0);
+    const double K = A.K[c], G = A.G[c];
+    S Fe[9];
+    for (int q = 0; q < 9; q++) Fe[q] = S(s) * F[q];
+    // cofactor matrix: J F^-T
+    S cof[9];
+    cof[0] = Fe[4] * Fe[8] - Fe[5] * Fe[7];
+    cof[1] = Fe[5] * Fe[6] - Fe[3] * Fe[8];
+    cof[2] = Fe[3] * Fe[7] - Fe[4] * Fe[6];
+    cof[3] = Fe[2] * Fe[7] - Fe[1] * Fe[8];
+    cof[4] = Fe[0] * Fe[8] - Fe[2] * Fe[6];
+    cof[5] = Fe[1] * Fe[6] - Fe[0] * Fe[7];
+    cof[6] = Fe[1] * Fe[5] - Fe[2] * Fe[4];
+    cof[7] = Fe[2] * Fe[3] - Fe[0] * Fe[5];
+    cof[8] = Fe[0] * Fe[4] - Fe[1] * Fe[3];
+    const S J = Fe[0] * cof[0] + Fe[1] * cof[1] + Fe[2] * cof[2];
+    S I1(0.0);
+    for (int q = 0; q < 9; q++) I1 = I1 + Fe[q] * Fe[q];
+    // d phi / d F_E = K/2 (J^2 - 1) F_E^-T + G J^(-2/3) (F_E - I1/3 F_E^-T)
+    const S a1 = S(0.5 * K) * (J * J - S(1.0)) / J;          // times cof = J F^-T
+    const S jm = fd_pow(J, -2.0 / 3.0);
+    const S a2 = S(G) * jm;
+    const S a3 = a2 * I1 / (S(3.0) * J);
+    for (int q = 0; q < 9; q++) P[q] = S(dT * s) * (a1 * cof[q] + a2 * Fe[q] - a3 * cof[q]);
+}
+
+// forces of cell c on its 2^d corners (f[a * d + i]) and its weighted sum of
+// the Gauss-point stresses (pm, d x d row-major), for the state (u, Fbar)
+// given by ld_u(node, comp) and fb (3 x 3 symmetric)
+template <typename S, class LU>
+__device__ void fs_cell(const FSArgs &A, long long c, LU &&ld_u, const S (&fb)[9], S (&f)[24], S (&pm)[9])
+{
+    const int d = A.d, na = 1 << d;
+    const double w = 1.0 / na;
+    S ua[8][3];
+    for (int a = 0; a < na; a++) {
+        const long long n = fs_node(A, c, a);
+        for (int i = 0; i < d; i++) ua[a][i] = ld_u(n, i);
+    }
+    for (int q = 0; q < 24; q++) f[q] = S(0.0);
+    for (int q = 0; q < 9; q++) pm[q] = S(0.0);
+    for (int g = 0; g < na; g++) {
+        S F[9];
+        for (int q = 0; q < 9; q++) F[q] = fb[q];
+        for (int i = 0; i < d; i++)
+            for (int k = 0; k < d; k++) {
+                S t = F[3 * i + k];
+                for (int a = 0; a < na; a++) t = t + ua[a][i] * S(dshape(d, g, a, k));
+                F[3 * i + k] = t;
+            }
+        if (d == 2) {
+            F[2] = F[5] = F[6] = F[7] = S(0.0);
+            F[8] = S(1.0);
+        }
+        S P[9];
+        fs_piola(A, c, F, P);
+        for (int a = 0; a < na; a++)
+            for (int i = 0; i < d; i++) {
+                S t = f[a * d + i];
+                for (int k = 0; k < d; k++) t = t + S(w) * P[3 * i + k] * S(dshape(d, g, a, k));
+                f[a * d + i] = t;
+            }
+        for (int i = 0; i < d; i++)
+            for (int k = 0; k < d; k++) pm[3 * i + k] = pm[3 * i + k] + S(w) * P[3 * i + k];
+    }
+}
+
+// symmetric Fbar (3 x 3) from the m trailing entries of a vector
+__device__ __forceinline__ void fs_fbar(int d, const double *zf, double (&fb)[9])
+{
+    for (int q = 0; q < 9; q++) fb[q] = 0.0;
+    if (d == 3) {
+        fb[0] = zf[0]; fb[4] = zf[1]; fb[8] = zf[2];
+        fb[5] = fb[7] = zf[3]; fb[2] = fb[6] = zf[4]; fb[1] = fb[3] = zf[5];
+    } else {
+        fb[0] = zf[0]; fb[4] = zf[1]; fb[1] = fb[3] = zf[2];
+    }
+}
+
+// per cell: corner forces (value, or with v != nullptr the directional
+// derivative along v) into cf[c][a][i] and the stress sums into pc[c][9]
+__global__ void k_fs_cells(FSArgs A, const double *z, const double *v, double *cf, double *pc)
+{
+    const int d = A.d, na = 1 << d;
+    const long long N = A.N;
+    const double *zf = z + (size_t)d * N, *vf = v ? v + (size_t)d * N : nullptr;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        if (!v) {
+            double fb[9], f[24], pm[9];
+            fs_fbar(d, zf, fb);
+            fs_cell<double>(A, c, [&](long long n, int i) { return z[n * d + i]; }, fb, f, pm);
+            for (int q = 0; q < na * d; q++) cf[c * 24 + q] = f[q];
+            for (int q = 0; q < 9; q++) pc[c * 9 + q] = pm[q];
+        } else {
+            double fb0[9], fb1[9];
+            fs_fbar(d, zf, fb0);
+            fs_fbar(d, vf, fb1);
+            FD fb[9], f[24], pm[9];
+            for (int q = 0; q < 9; q++) fb[q] = FD(fb0[q], fb1[q]);
+            fs_cell<FD>(A, c, [&](long long n, int i) { return FD(z[n * d + i], v[n * d + i]); }, fb, f, pm);
+            for (int q = 0; q < na * d; q++) cf[c * 24 + q] = f[q].d;
+            for (int q = 0; q < 9; q++) pc[c * 9 + q] = pm[q].d;
+        }
+    }
+}
+
+// nodal forces: each node sums the corner forces of its 2^d cells; node 0
+// is held (zero)
+__global__ void k_fs_gather(FSArgs A, const double *cf, double *out)
+{
+    const int d = A.d, na = 1 << d;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < A.N; n += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(n % A.nx);
+        const long long r = n / A.nx;
+        const int j = (int)(r % A.ny), k = (int)(r / A.ny);
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < na; a++) {
+            const int ci = (i - (a & 1) + A.nx) % A.nx, cj = (j - ((a >> 1) & 1) + A.ny) % A.ny;
+            const int ck = d == 3 ? (k - ((a >> 2) & 1) + A.nz) % A.nz : 0;
+            const long long c = ci + (long long)A.nx * (cj + (long long)A.ny * ck);
+            for (int q = 0; q < d; q++) s[q] += cf[c * 24 + a * d + q];
+        }
+        for (int q = 0; q < d; q++) out[n * d + q] = n == 0 ? 0.0 : s[q];
+    }
+}
+
+// block partial sums of the cells' stress sums (fixed order)
+__global__ void k_fs_psum(long long N, const double *pc, double *part)
+{
+    __shared__ double sh[9][8];
+    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        for (int q = 0; q < 9; q++) s[q] += pc[c * 9 + q];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = 0; q < 9; q++) {
+        double t = s[q];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[q][wid] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[threadIdx.x][k];
+        part[blockIdx.x * 9 + threadIdx.x] = t;
+    }
+}
+
+// Jacobi diagonal of the displacement dofs from the small-strain operator
+// (lambda = K - 2G/3, mu = G) of the 2^d cells around each node
+__global__ void k_fs_diag(FSArgs A, double dl, double dm, double *dg)
+{
+    const int d = A.d, na = 1 << d;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < A.N; n += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(n % A.nx);
+        const long long r = n / A.nx;
+        const int j = (int)(r % A.ny), k = (int)(r / A.ny);
+        double s = 0.0;
+        for (int a = 0; a < na; a++) {
+            const int ci = (i - (a & 1) + A.nx) % A.nx, cj = (j - ((a >> 1) & 1) + A.ny) % A.ny;
+            const int ck = d == 3 ? (k - ((a >> 2) & 1) + A.nz) % A.nz : 0;
+            const long long c = ci + (long long)A.nx * (cj + (long long)A.ny * ck);
+            s += (A.K[c] - 2.0 * A.G[c] / 3.0) * dl + A.G[c] * dm;
+        }
+        for (int q = 0; q < d; q++) dg[n * d + q] = s;
+    }
+}
+
+__global__ void k_fs_moduli(long long N, const double *theta, const double *phig, double Ks, double Gs, double Kg,
+                            double Gg, double *K, double *G, double *Wf)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        auto h = [](double x) { return x * x * x * (x * (6.0 * x - 15.0) + 10.0); };
+        const double hg = h(phig[c]), ht = h(theta[c]);
+        const double wf = (1.0 - hg) * ht, ww = (1.0 - hg) * (1.0 - ht);
+        K[c] = (wf + ww) * Ks + hg * Kg;
+        G[c] = (wf + ww) * Gs + hg * Gg;
+        Wf[c] = wf;
+    }
+}
+
+__global__ void k_fs_dot(long long L, const double *a, const double *b, double *part)
+{
+    __shared__ double sh[8];
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L; i += (long long)gridDim.x * blockDim.x)
+        s = fma(a[i], b[i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[k];
+        part[blockIdx.x] = t;
+    }
+}
+
+// y = a x + b y on [0, L); z = x / dg elementwise with dg over [0, nd) and
+// 1 / dgf beyond (mode 1)
+__global__ void k_fs_axpby(long long L, double a, const double *x, double b, double *y)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L; i += (long long)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+__global__ void k_fs_precond(long long L, long long nd, const double *x, const double *dg, double dgf, double *z)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L; i += (long long)gridDim.x * blockDim.x)
+        z[i] = i < nd ? x[i] / dg[i] : x[i] / dgf;
+}
+
+constexpr int FS_NB = 128;     // blocks of the reductions
+
+struct FSSolver {
+    FSArgs A;
+    long long N, nd, L;
+    int m;
+    double pbar[9];
+    double *z = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *s = nullptr, *dz = nullptr, *dg = nullptr;
+    double *cf = nullptr, *pc = nullptr, *part = nullptr, *K = nullptr, *G = nullptr, *Wf = nullptr;
+    double *th = nullptr, *pg = nullptr;
+    std::vector<void *> mem;
+    std::vector<double> hp;
+    int grid = 0;
+
+    cudaError_t alloc(double **x, size_t n)
+    {
+        cudaError_t e = cudaMalloc((void **)x, sizeof(double) * (n ? n : 1));
+        if (e == cudaSuccess) mem.push_back(*x);
+        return e;
+    }
+    ~FSSolver()
+    {
+        for (void *v : mem) cudaFree(v);
+    }
+    double dot(const double *a, const double *b)
+    {
+        k_fs_dot<<<FS_NB, 256>>>(L, a, b, part);
+        cudaMemcpy(hp.data(), part, sizeof(double) * FS_NB, cudaMemcpyDeviceToHost);
+        double t = 0.0;
+        for (int k = 0; k < FS_NB; k++) t += hp[k];
+        return t;
+    }
+    // the residual (v == nullptr) or its directional derivative along v,
+    // into out (length L)
+    void apply(const double *v, double *out)
+    {
+        const int d = A.d;
+        k_fs_cells<<<grid, 128>>>(A, z, v, cf, pc);
+        k_fs_gather<<<grid, 128>>>(A, cf, out);
+        k_fs_psum<<<FS_NB, 256>>>(N, pc, part);
+        cudaMemcpy(hp.data(), part, sizeof(double) * FS_NB * 9, cudaMemcpyDeviceToHost);
+        double ps[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < FS_NB; k++)
+            for (int q = 0; q < 9; q++) ps[q] += hp[(size_t)k * 9 + q];
+        if (!v)
+            for (int q = 0; q < 9; q++) ps[q] -= (double)N * pbar[q];
+        double rf[6];
+        const int ii[6] = {0, 1, 2, 1, 0, 0}, jj[6] = {0, 1, 2, 2, 2, 1};
+        const int i2[3] = {0, 1, 0}, j2[3] = {0, 1, 1};
+        for (int k = 0; k < m; k++) {
+            const int i = d == 3 ? ii[k] : i2[k], j = d == 3 ? jj[k] : j2[k];
+            rf[k] = i == j ? ps[3 * i + i] : ps[3 * i + j] + ps[3 * j + i];
+        }
+        cudaMemcpy(out + nd, rf, sizeof(double) * m, cudaMemcpyHostToDevice);
+    }
+    double maxabs(const double *x)
+    {
+        std::vector<double> h((size_t)L);
+        cudaMemcpy(h.data(), x, sizeof(double) * L, cudaMemcpyDeviceToHost);
+        double mx = 0.0;
+        for (double v : h) mx = std::max(mx, std::fabs(v));
+        return mx;
+    }
+};
+
+int fs_fail(int code, const char *msg)
+{
+    g_fs_error = msg;
+    return code;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pf_finite_strain_solve(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
+                           const double *pbar, const pf_fs_opts *opts, double *u, double *Fbar, pf_fs_stats *stats)
+{
+    if (!cfg || !theta || !phi_g || !opts || !u || !Fbar) return fs_fail(PF_EINVAL, "null argument");
+    const int d = cfg->ndim;
+    if (d != 2 && d != 3) return fs_fail(PF_EINVAL, "ndim must be 2 or 3");
+    if (cfg->nx < 2 || cfg->ny < 2 || (d == 3 && cfg->nz < 2)) return fs_fail(PF_EINVAL, "grid sizes must be >= 2");
+    if (opts->nload < 1 || opts->newton_maxit < 1 || !(opts->newton_tol > 0.0) || opts->cg_maxit < 1 ||
+        !(opts->cg_rtol > 0.0 && opts->cg_rtol < 1.0))
+        return fs_fail(PF_EINVAL, "invalid pf_fs_opts");
+    const double nu = cfg->p.nu, Es = cfg->p.E_s, Eg = Es * cfg->p.E_g_ratio;
+    if (!(Es > 0.0) || !(nu > -1.0 && nu < 0.5)) return fs_fail(PF_EINVAL, "E_s > 0 and -1 < nu < 0.5 required");
+    FSSolver S;
+    S.N = (long long)cfg->nx * cfg->ny * (d == 3 ? cfg->nz : 1);
+    S.m = d == 3 ? 6 : 3;
+    S.nd = (long long)d * S.N;
+    S.L = S.nd + S.m;
+    S.hp.assign((size_t)FS_NB * 9, 0.0);
+    for (int q = 0; q < 9; q++) S.pbar[q] = 0.0;
+    for (int i = 0; i < d; i++)
+        for (int j = 0; j < d; j++) S.pbar[3 * i + j] = pbar ? pbar[i * d + j] : (i == j ? -cfg->p.prestress : 0.0);
+    const long long N = S.N, L = S.L;
+    double **bufs[8] = {&S.z, &S.r, &S.p, &S.q, &S.s, &S.dz, &S.dg, &S.part};
+    const size_t lens[8] = {(size_t)L, (size_t)L, (size_t)L, (size_t)L, (size_t)L, (size_t)L, (size_t)S.nd,
+                            (size_t)FS_NB * 9};
+    for (int k = 0; k < 8; k++)
+        if (S.alloc(bufs[k], lens[k]) != cudaSuccess) return fs_fail(PF_ENOMEM, "cudaMalloc failed");
+    if (S.alloc(&S.cf, (size_t)N * 24) != cudaSuccess || S.alloc(&S.pc, (size_t)N * 9) != cudaSuccess ||
+        S.alloc(&S.K, N) != cudaSuccess || S.alloc(&S.G, N) != cudaSuccess || S.alloc(&S.Wf, N) != cudaSuccess ||
+        S.alloc(&S.th, N) != cudaSuccess || S.alloc(&S.pg, N) != cudaSuccess)
+        return fs_fail(PF_ENOMEM, "cudaMalloc failed");
+    cudaMemcpy(S.th, theta, sizeof(double) * N, cudaMemcpyHostToDevice);
+    cudaMemcpy(S.pg, phi_g, sizeof(double) * N, cudaMemcpyHostToDevice);
+    S.grid = (int)std::min<long long>((N + 127) / 128, 4096);
+    const double Ks = Es / (3 * (1 - 2 * nu)), Gs = Es / (2 * (1 + nu));
+    const double Kg = Eg / (3 * (1 - 2 * nu)), Gg = Eg / (2 * (1 + nu));
+    k_fs_moduli<<<S.grid, 128>>>(N, S.th, S.pg, Ks, Gs, Kg, Gg, S.K, S.G, S.Wf);
+    S.A.d = d; S.A.nx = cfg->nx; S.A.ny = cfg->ny; S.A.nz = d == 3 ? cfg->nz : 1; S.A.N = N;
+    S.A.K = S.K; S.A.G = S.G; S.A.Wf = S.Wf; S.A.omega = 0.0;
+    // small-strain diagonals of a displacement dof per unit lambda and mu:
+    // sum over Gauss points of w (dN_i)^2 and w (|dN|^2 + dN_i^2); equal
+    // for every corner and component
+    {
+        const double ga = 0.5 - 0.5 / std::sqrt(3.0), gb = 0.5 + 0.5 / std::sqrt(3.0);
+        const int na = 1 << d;
+        double dl = 0.0, dm = 0.0;
+        for (int g = 0; g < na; g++) {
+            double dn[3];
+            for (int k = 0; k < d; k++) {
+                double v = 1.0;
+                for (int l = 0; l < d; l++) {
+                    const double xi = ((g >> l) & 1) ? gb : ga;
+                    v *= l == k ? -1.0 : 1.0 - xi;     // corner a = 0
+                }
+                dn[k] = v;
+            }
+            double n2 = 0.0;
+            for (int k = 0; k < d; k++) n2 += dn[k] * dn[k];
+            dl += dn[0] * dn[0] / na;
+            dm += (n2 + dn[0] * dn[0]) / na;
+        }
+        k_fs_diag<<<S.grid, 128>>>(S.A, dl, dm, S.dg);
+    }
+    // the mean-deformation dofs: scale of the summed moduli
+    std::vector<double> hK((size_t)N), hG((size_t)N);
+    cudaMemcpy(hK.data(), S.K, sizeof(double) * N, cudaMemcpyDeviceToHost);
+    cudaMemcpy(hG.data(), S.G, sizeof(double) * N, cudaMemcpyDeviceToHost);
+    double sK = 0.0, sG = 0.0;
+    for (long long c = 0; c < N; c++) { sK += hK[c]; sG += hG[c]; }
+    const double dgf = sK + 4.0 * sG / 3.0;
+    // start: u = 0, Fbar = I
+    std::vector<double> z0((size_t)L, 0.0);
+    for (int i = 0; i < d; i++) z0[S.nd + i] = 1.0;
+    cudaMemcpy(S.z, z0.data(), sizeof(double) * L, cudaMemcpyHostToDevice);
+    pf_fs_stats st;
+    memset(&st, 0, sizeof(st));
+    double res = 0.0;
+    for (int step = 1; step <= opts->nload; step++) {
+        S.A.omega = omega * step / opts->nload;
+        for (int it = 0;; it++) {
+            S.apply(nullptr, S.r);
+            res = S.maxabs(S.r);
+            if (res <= opts->newton_tol) break;
+            if (it == opts->newton_maxit) {
+                st.residual = res;
+                if (stats) *stats = st;
+                return fs_fail(PF_ENOTCONV, "finite-strain Newton iteration did not converge");
+            }
+            st.newton_iters++;
+            // PCG on H dz = -r from dz = 0 (r, p, q, s: residual, direction,
+            // H p, preconditioned residual)
+            cudaMemset(S.dz, 0, sizeof(double) * L);
+            k_fs_axpby<<<S.grid, 128>>>(L, -1.0, S.r, 0.0, S.r);
+            const double r0 = std::sqrt(S.dot(S.r, S.r));
+            k_fs_precond<<<S.grid, 128>>>(L, S.nd, S.r, S.dg, dgf, S.s);
+            cudaMemcpy(S.p, S.s, sizeof(double) * L, cudaMemcpyDeviceToDevice);
+            double rz = S.dot(S.r, S.s);
+            for (int k = 0; k < opts->cg_maxit; k++) {
+                S.apply(S.p, S.q);
+                const double pq = S.dot(S.p, S.q);
+                if (!(pq > 0.0)) break;                  // not positive definite along p
+                const double al = rz / pq;
+                k_fs_axpby<<<S.grid, 128>>>(L, al, S.p, 1.0, S.dz);
+                k_fs_axpby<<<S.grid, 128>>>(L, -al, S.q, 1.0, S.r);
+                st.cg_iters++;
+                if (std::sqrt(S.dot(S.r, S.r)) <= opts->cg_rtol * r0) break;
+                k_fs_precond<<<S.grid, 128>>>(L, S.nd, S.r, S.dg, dgf, S.s);
+                const double rz1 = S.dot(S.r, S.s);
+                k_fs_axpby<<<S.grid, 128>>>(L, 1.0, S.s, rz1 / rz, S.p);
+                rz = rz1;
+            }
+            k_fs_axpby<<<S.grid, 128>>>(L, 1.0, S.dz, 1.0, S.z);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fs_fail(PF_ECUDA, cudaGetErrorString(e));
+    std::vector<double> zh((size_t)L);
+    cudaMemcpy(zh.data(), S.z, sizeof(double) * L, cudaMemcpyDeviceToHost);
+    memcpy(u, zh.data(), sizeof(double) * S.nd);
+    double fb[9];
+    for (int q = 0; q < 9; q++) fb[q] = 0.0;
+    const double *zf = zh.data() + S.nd;
+    if (d == 3) {
+        fb[0] = zf[0]; fb[4] = zf[1]; fb[8] = zf[2];
+        fb[5] = fb[7] = zf[3]; fb[2] = fb[6] = zf[4]; fb[1] = fb[3] = zf[5];
+    } else {
+        fb[0] = zf[0]; fb[4] = zf[1]; fb[1] = fb[3] = zf[2];
+    }
+    for (int i = 0; i < d; i++)
+        for (int j = 0; j < d; j++) Fbar[i * d + j] = fb[3 * i + j];
+    st.residual = res;
+    if (stats) *stats = st;
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fs_fail(PF_ECUDA, cudaGetErrorString(e));
+    return PF_OK;
+}
+
+const char *pf_fs_last_error(void) { return g_fs_error.c_str(); }
+
+}  // extern "C"

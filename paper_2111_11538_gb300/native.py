@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libpf.so")
 CSRC = os.path.join(_HERE, "csrc")
-UNITS = [os.path.join(CSRC, n) for n in ("pf_lib.cu", "pcg_2d.cu", "pcg_3d.cu", "unet.cu")]   # translation units
+UNITS = [os.path.join(CSRC, n) for n in ("pf_lib.cu", "pcg_2d.cu", "pcg_3d.cu", "unet.cu", "finite.cu")]   # translation units
 BUILD_DIR = os.path.join(_HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -78,6 +78,15 @@ class pf_implicit_stats(ctypes.Structure):
                 ("gmres_iters", ctypes.c_longlong), ("residual", ctypes.c_double)]
 
 
+class pf_fs_opts(ctypes.Structure):
+    _fields_ = [("nload", ctypes.c_int), ("newton_maxit", ctypes.c_int), ("newton_tol", ctypes.c_double),
+                ("cg_maxit", ctypes.c_int), ("cg_rtol", ctypes.c_double)]
+
+
+class pf_fs_stats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("cg_iters", ctypes.c_longlong), ("residual", ctypes.c_double)]
+
+
 class pf_profile(ctypes.Structure):
     _fields_ = [("enabled", ctypes.c_int), ("launches", ctypes.c_longlong),
                 ("count", ctypes.c_longlong * PF_K_NCLASS), ("ms", ctypes.c_double * PF_K_NCLASS),
@@ -90,7 +99,8 @@ class pf_unet_config(ctypes.Structure):
 
 
 # exported symbols, in the order of include/pf.h then include/pf_unet.h
-SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_step_implicit", "pf_get_fields", "pf_get_diagnostics",
+SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_step_implicit", "pf_finite_strain_solve", "pf_fs_last_error",
+           "pf_get_fields", "pf_get_diagnostics",
            "pf_free_energy", "pf_dt_stable", "pf_profile_enable", "pf_profile_read",
            "pf_batch_create", "pf_batch_size", "pf_batch_set_fields", "pf_batch_get_fields",
            "pf_batch_get_diagnostics", "pf_attach_unet", "pf_selftest_wait",
@@ -163,6 +173,11 @@ def lib():
         l.pf_step_implicit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(pf_implicit_opts),
                                        ctypes.POINTER(pf_implicit_stats), ctypes.c_void_p]
         l.pf_step_implicit.restype = ctypes.c_int
+        l.pf_finite_strain_solve.argtypes = [ctypes.POINTER(pf_config), _DP, _DP, ctypes.c_double, _DP,
+                                             ctypes.POINTER(pf_fs_opts), _DP, _DP, ctypes.POINTER(pf_fs_stats)]
+        l.pf_finite_strain_solve.restype = ctypes.c_int
+        l.pf_fs_last_error.argtypes = []
+        l.pf_fs_last_error.restype = ctypes.c_char_p
         l.pf_get_fields.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_fields), ctypes.c_int]
         l.pf_get_fields.restype = ctypes.c_int
         l.pf_get_diagnostics.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_diag)]
@@ -248,6 +263,23 @@ def pf_step_implicit(h, nsteps, opts, stream=None):
     rc = lib().pf_step_implicit(h, int(nsteps), ctypes.byref(opts), ctypes.byref(st),
                                 ctypes.c_void_p(stream) if stream else None)
     return rc, st
+
+
+def pf_finite_strain_solve(cfg, theta, phig, omega, pbar, opts):
+    """Host arrays in, (rc, u, Fbar, stats) out (see include/pf.h)."""
+    import numpy as np
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    pg = np.ascontiguousarray(phig, dtype=np.float64)
+    d = cfg.ndim
+    u = np.zeros(th.size * d)
+    fb = np.zeros(d * d)
+    pb = None if pbar is None else np.ascontiguousarray(pbar, dtype=np.float64).ravel()
+    st = pf_fs_stats()
+    ptr = lambda a: a.ctypes.data_as(_DP)                                   # noqa: E731
+    rc = lib().pf_finite_strain_solve(ctypes.byref(cfg), ptr(th), ptr(pg), float(omega),
+                                      ptr(pb) if pb is not None else None, ctypes.byref(opts), ptr(u), ptr(fb),
+                                      ctypes.byref(st))
+    return rc, u.reshape(-1, d), fb.reshape(d, d), st
 
 
 def pf_get_fields(h, fields, where=PF_HOST):

@@ -127,6 +127,7 @@ def test_ctypes_structs_match_the_c_layout():
     structs = [("pf_params", native.pf_params), ("pf_config", native.pf_config), ("pf_fields", native.pf_fields),
                ("pf_diag", native.pf_diag), ("pf_profile", native.pf_profile),
                ("pf_implicit_opts", native.pf_implicit_opts), ("pf_implicit_stats", native.pf_implicit_stats),
+               ("pf_fs_opts", native.pf_fs_opts), ("pf_fs_stats", native.pf_fs_stats),
                ("pf_unet_config", native.pf_unet_config)]
     c = _c_layout(structs)
     for name, cls in structs:

@@ -1,0 +1,101 @@
+"""GPU finite-strain elastic equilibrium (pf_finite_strain_solve) against
+the finite-strain oracle (oracle/finite_strain.py, Problem.solve).
+
+Sec. 2.2 of the paper: neo-Hooke elasticity of F_E = F F_R^-1 with the
+transformation stretch d_T^(1/3), d_T = 1 - W_f Omega; Sec. 2.4: Div P = 0.
+Both sides discretise the same energy on the same Q1 voxel elements with
+2^d Gauss points and solve its stationarity by Newton's method over the
+same load steps to max |residual| <= 1e-11 (the oracle with a dense
+finite-difference Jacobian, the library matrix-free by conjugate
+gradients), so u and Fbar agree to the Newton tolerance times the
+problem's conditioning: 1e-8 relative to the largest displacement, 1e-10 on
+Fbar.
+"""
+import numpy as np
+import pytest
+
+from paper_2111_11538_gb300 import inputs, make_config, native, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    native.build_library()
+    native.lib()
+
+
+@pytest.fixture(scope="module")
+def fs(orc):
+    from oracle import finite_strain
+    return finite_strain
+
+
+def _opts(nload, tol=1e-11):
+    return native.pf_fs_opts(nload=nload, newton_maxit=40, newton_tol=tol, cg_maxit=20000, cg_rtol=1e-12)
+
+
+def _gpu(th, pg, prm, omega, nload, pbar=None):
+    cfg = make_config(th.shape, prm)
+    rc, u, Fb, st = native.pf_finite_strain_solve(cfg, th.ravel(), pg.ravel(), omega, pbar, _opts(nload))
+    assert rc == native.PF_OK, native.lib().pf_fs_last_error()
+    return u, Fb, st
+
+
+def _compare(fs, th, pg, prm, omega, nload, prestress=0.0, pbar=None):
+    pr = fs.Problem(th, pg, prm, omega, prestress=prestress, pbar=pbar)
+    u0, F0 = pr.unpack(pr.solve(tol=1e-11, nload=nload))
+    u, Fb, st = _gpu(th, pg, dict(prm, prestress=prestress), omega, nload, pbar)
+    scale = max(np.abs(u0).max(), 1e-12)
+    assert np.abs(u - u0).max() < 1e-8 * scale, (np.abs(u - u0).max(), scale)
+    assert np.abs(Fb - F0).max() < 1e-10, (Fb, F0)
+    assert st.residual <= 1e-11 and st.newton_iters >= nload
+    return u, Fb
+
+
+def test_finite_strain_2d_core_shell_matches_oracle(fs):
+    """Core-shell with gas cells and a 20 % volume change of ferrite,
+    prestress 0.005, four load steps (plane strain)."""
+    from oracle import split_phases
+    f = inputs.core_shell((8, 8), 2.5, 1.0, delta=1.0)
+    th, pg = split_phases(f["phi_f"], f["phi_w"])
+    u, Fb = _compare(fs, th, pg, workloads.params(), 0.2, 4, prestress=0.005)
+    assert Fb[0, 0] < 1.0 and np.abs(u).max() > 1e-3
+
+
+def test_finite_strain_2d_sheared_box_matches_oracle(fs):
+    """A prescribed mean shear stress (pbar with off-diagonal entries) on a
+    ragged 7x5 grid."""
+    rng = np.random.default_rng(3)
+    th = np.clip(0.5 + 0.5 * rng.standard_normal((5, 7)), 0.0, 1.0)
+    pg = np.zeros((5, 7))
+    pbar = np.array([[0.0, 0.004], [0.004, -0.002]])
+    _compare(fs, th, pg, workloads.params(), 0.1, 2, pbar=pbar)
+
+
+def test_finite_strain_3d_ball_matches_oracle(fs):
+    n = 4
+    x = np.arange(n) + 0.5 - n / 2
+    gz, gy, gx = np.meshgrid(x, x, x, indexing="ij")
+    th = 0.5 * (1 - np.tanh((np.sqrt(gx ** 2 + gy ** 2 + gz ** 2) - 1.2) / 1.0))
+    pg = np.zeros_like(th)
+    pg[0, 0, :] = 1.0                      # a row of gas cells
+    th[0, 0, :] = 0.0
+    _compare(fs, th, pg, workloads.params(), 0.3, 3)
+
+
+def test_finite_strain_3d_uniform_transformation_is_stress_free():
+    """In 3D nothing constrains a uniform transformation: Fbar = d_T^(1/3) I
+    exactly, u = 0 (d_T = 1 - Omega for uniform ferrite)."""
+    th = np.ones((3, 4, 5))
+    u, Fb, _ = _gpu(th, np.zeros_like(th), workloads.params(), 0.4, 2)
+    assert np.abs(Fb - 0.6 ** (1 / 3) * np.eye(3)).max() < 1e-12
+    assert np.abs(u).max() < 1e-12
+
+
+def test_finite_strain_rejects_bad_arguments():
+    th = np.ones((4, 4))
+    cfg = make_config((4, 4), workloads.params())
+    bad = native.pf_fs_opts(nload=0, newton_maxit=10, newton_tol=1e-10, cg_maxit=10, cg_rtol=1e-6)
+    rc, _, _, _ = native.pf_finite_strain_solve(cfg, th.ravel(), th.ravel() * 0, 0.1, None, bad)
+    assert rc == native.PF_EINVAL and b"pf_fs_opts" in native.lib().pf_fs_last_error()
