@@ -277,6 +277,29 @@ typedef struct {
 int pf_finite_strain_solve(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
                            const double *pbar, const pf_fs_opts *opts, double *u, double *Fbar,
                            pf_fs_stats *stats);
+
+/* One staggered finite-strain mechanics step (the library's reading of the
+ * paper's plastic flow, as for small strain): the equilibrium above with the
+ * plastic deformation FP of every cell (F_E = d_T^(-1/3) F FP^-1), then, if
+ * cfg->plasticity, one multiplicative J2 update per cell at its cell-centre
+ * deformation (Sec. 2.3 PlaTwoJ, Sec. 2.4 RulFloPla: backward Euler with the
+ * exponential map, FP_new = exp(dl N) FP, N = dev M / |dev M| at the end of
+ * the step, |dev M| = sqrt(2/3) (sigma_Y + H_hard (epsP + dl)); M the Mandel
+ * stress d_T (K/2 (det C_E - 1) I + G dev(det C_E^(-1/3) C_E)), the
+ * derivative of the energy above), which keeps det FP = 1.
+ *   FP   : in/out, host, N * 9 (3 x 3 row-major per cell; identity to start)
+ *   epsP : in/out, host, N accumulated plastic strain
+ * Other arguments and errors as pf_finite_strain_solve; PF_ENOTCONV also
+ * when a cell's update does not converge (that cell keeps its FP). */
+int pf_finite_strain_step(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
+                          const double *pbar, const pf_fs_opts *opts, double *u, double *Fbar, double *FP,
+                          double *epsP, pf_fs_stats *stats);
+
+/* The multiplicative J2 update above for n independent points (host arrays):
+ * F (n * 9 total deformation gradients), FP (n * 9, in/out), epsP (n,
+ * in/out), K, G, dT (n each: bulk and shear moduli, d_T), sigma_Y, H. */
+int pf_fs_return_map(int n, const double *F, double *FP, double *epsP, const double *K, const double *G,
+                     const double *dT, double sigma_Y, double H);
 const char *pf_fs_last_error(void);
 
 /* Copy the current state (the fields of Sec. 2.4 and the mechanical state)

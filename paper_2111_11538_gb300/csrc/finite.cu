@@ -14,6 +14,11 @@
 // symmetric, u = 0 at node 0; P = d psi / d F.  2D is plane strain
 // (F_33 = 1).
 //
+// With a plastic deformation F_P per cell, F_E = d_T^(-1/3) F F_P^-1 and
+// P = d_T^(2/3) (d phi / d F_E) F_P^-T; pf_finite_strain_step then takes one
+// multiplicative J2 update per cell at the cell-centre deformation (Sec. 2.3
+// PlaTwoJ, Sec. 2.4 RulFloPla; fs_return_map).
+//
 // Newton's method in load steps of Omega; each Newton system H delta = -r is
 // solved by conjugate gradients (H, the Hessian of the energy, is symmetric)
 // preconditioned by the diagonal of the small-strain operator; every
@@ -54,11 +59,23 @@ __device__ __forceinline__ FD fd_pow(FD a, double p)
     return FD(q, p * q / a.v * a.d);
 }
 __device__ __forceinline__ double fd_pow(double a, double p) { return pow(a, p); }
+__device__ __forceinline__ FD fd_exp(FD a)
+{
+    const double q = exp(a.v);
+    return FD(q, q * a.d);
+}
+__device__ __forceinline__ double fd_exp(double a) { return exp(a); }
+__device__ __forceinline__ FD fd_sqrt(FD a)
+{
+    const double q = sqrt(a.v);
+    return FD(q, 0.5 * a.d / q);
+}
 
 struct FSArgs {
     int d, nx, ny, nz;
     long long N;
     const double *K, *G, *Wf;    // per cell
+    const double *FPinv;         // per cell 3 x 3 row-major inverse plastic deformation, or null (identity)
     double omega;                // transformation of this load step
 };
 
@@ -93,8 +110,15 @@ __device__ void fs_piola(const FSArgs &A, long long c, const S (&F)[9], S (&P)[9
 {
     const double dT = 1.0 - A.Wf[c] * A.omega, s = pow(dT, -1.0 / 3.0);
     const double K = A.K[c], G = A.G[c];
+    const double *Fi = A.FPinv ? A.FPinv + c * 9 : nullptr;
     S Fe[9];
-    for (int q = 0; q < 9; q++) Fe[q] = S(s) * F[q];
+    if (Fi) {
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++)
+                Fe[3 * i + j] = S(s) * (F[3 * i] * S(Fi[j]) + F[3 * i + 1] * S(Fi[3 + j]) + F[3 * i + 2] * S(Fi[6 + j]));
+    } else {
+        for (int q = 0; q < 9; q++) Fe[q] = S(s) * F[q];
+    }
     // cofactor matrix: J F^-T
     S cof[9];
     cof[0] = Fe[4] * Fe[8] - Fe[5] * Fe[7];
@@ -114,7 +138,187 @@ __device__ void fs_piola(const FSArgs &A, long long c, const S (&F)[9], S (&P)[9
     const S jm = fd_pow(J, -2.0 / 3.0);
     const S a2 = S(G) * jm;
     const S a3 = a2 * I1 / (S(3.0) * J);
-    for (int q = 0; q < 9; q++) P[q] = S(dT * s) * (a1 * cof[q] + a2 * Fe[q] - a3 * cof[q]);
+    if (Fi) {
+        S D[9];
+        for (int q = 0; q < 9; q++) D[q] = a1 * cof[q] + a2 * Fe[q] - a3 * cof[q];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++)
+                P[3 * i + j] = S(dT * s) * (D[3 * i] * S(Fi[3 * j]) + D[3 * i + 1] * S(Fi[3 * j + 1]) +
+                                            D[3 * i + 2] * S(Fi[3 * j + 2]));
+    } else {
+        for (int q = 0; q < 9; q++) P[q] = S(dT * s) * (a1 * cof[q] + a2 * Fe[q] - a3 * cof[q]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Multiplicative J2 update of one point (Sec. 2.3 PlaTwoJ, Sec. 2.4
+// RulFloPla), backward Euler with the exponential map:
+//     F_P,new = exp(dl N) F_P,  N = dev M / |dev M|,
+//     |dev M| = sqrt(2/3) (sigma_Y + H (eps_P + dl)),  dl >= 0,
+// M the Mandel stress d_T (K/2 (det C - 1) I + G dev(det C^(-1/3) C)) of the
+// elastic right Cauchy-Green tensor C = F_E^T F_E (the derivative of the
+// energy above).  Isotropic elasticity keeps the update coaxial with the
+// trial C_E: in its principal frame the elastic log stretches e solve
+// e - e_trial + dl dev m / |dev m| = 0 and the yield condition, four
+// equations by Newton (Jacobian in forward mode).
+// ---------------------------------------------------------------------------
+// eigenvalues w and eigenvectors (columns of V, row-major) of a symmetric
+// 3 x 3 matrix by cyclic Jacobi rotations
+__device__ void fs_eig3(const double (&A0)[9], double (&w)[3], double (&V)[9])
+{
+    double a[9];
+    for (int q = 0; q < 9; q++) { a[q] = A0[q]; V[q] = (q % 4 == 0) ? 1.0 : 0.0; }
+    for (int sweep = 0; sweep < 30; sweep++) {
+        const double off = a[1] * a[1] + a[2] * a[2] + a[5] * a[5];
+        const double nrm = a[0] * a[0] + a[4] * a[4] + a[8] * a[8] + 2.0 * off;
+        if (off <= 1e-34 * nrm) break;
+        for (int p = 0; p < 2; p++)
+            for (int q = p + 1; q < 3; q++) {
+                const double apq = a[3 * p + q];
+                if (apq == 0.0) continue;
+                const double th = (a[3 * q + q] - a[3 * p + p]) / (2.0 * apq);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < 3; k++) {          // a = J^T a J on columns p, q
+                    const double akp = a[3 * k + p], akq = a[3 * k + q];
+                    a[3 * k + p] = c * akp - sn * akq;
+                    a[3 * k + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 3; k++) {          // rows p, q
+                    const double apk = a[3 * p + k], aqk = a[3 * q + k];
+                    a[3 * p + k] = c * apk - sn * aqk;
+                    a[3 * q + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; k++) {
+                    const double vkp = V[3 * k + p], vkq = V[3 * k + q];
+                    V[3 * k + p] = c * vkp - sn * vkq;
+                    V[3 * k + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    w[0] = a[0]; w[1] = a[4]; w[2] = a[8];
+}
+
+// principal Mandel stresses of the elastic log stretches e
+template <typename S>
+__device__ void fs_mand(const S (&e)[3], double K, double G, double dT, S (&m)[3])
+{
+    S cc[3];
+    for (int i = 0; i < 3; i++) cc[i] = fd_exp(S(2.0) * e[i]);
+    const S J2 = cc[0] * cc[1] * cc[2];
+    const S f = fd_pow(J2, -1.0 / 3.0);
+    S uu[3];
+    for (int i = 0; i < 3; i++) uu[i] = cc[i] * f;
+    const S tr = (uu[0] + uu[1] + uu[2]) / S(3.0);
+    for (int i = 0; i < 3; i++) m[i] = S(dT) * (S(0.5 * K) * (J2 - S(1.0)) + S(G) * (uu[i] - tr));
+}
+
+// residual of the four equations at (e, dl)
+template <typename S>
+__device__ void fs_rm_eqs(const S (&e)[3], S dl, const double (&etr)[3], double epsP, double K, double G, double dT,
+                          double sY, double H, S (&r)[4])
+{
+    S m[3];
+    fs_mand(e, K, G, dT, m);
+    const S mean = (m[0] + m[1] + m[2]) / S(3.0);
+    S dm[3];
+    for (int i = 0; i < 3; i++) dm[i] = m[i] - mean;
+    const S nm = fd_sqrt(dm[0] * dm[0] + dm[1] * dm[1] + dm[2] * dm[2]);
+    for (int i = 0; i < 3; i++) r[i] = e[i] - S(etr[i]) + dl * dm[i] / nm;
+    r[3] = nm - S(sqrt(2.0 / 3.0)) * (S(sY) + S(H) * (S(epsP) + dl));
+}
+
+// one point: F (deformation), FP and epsP in/out; returns 0, or 1 if the
+// Newton iteration did not converge (the point is then left elastic)
+__device__ int fs_return_map(const double (&F)[9], double (&FP)[9], double &epsP, double K, double G, double dT,
+                             double sY, double H)
+{
+    const double s = pow(dT, -1.0 / 3.0);
+    // F_P^-1 through its cofactors
+    double ci[9];
+    ci[0] = FP[4] * FP[8] - FP[5] * FP[7]; ci[1] = FP[2] * FP[7] - FP[1] * FP[8]; ci[2] = FP[1] * FP[5] - FP[2] * FP[4];
+    ci[3] = FP[5] * FP[6] - FP[3] * FP[8]; ci[4] = FP[0] * FP[8] - FP[2] * FP[6]; ci[5] = FP[2] * FP[3] - FP[0] * FP[5];
+    ci[6] = FP[3] * FP[7] - FP[4] * FP[6]; ci[7] = FP[1] * FP[6] - FP[0] * FP[7]; ci[8] = FP[0] * FP[4] - FP[1] * FP[3];
+    const double det = FP[0] * ci[0] + FP[1] * ci[3] + FP[2] * ci[6];
+    double Fe[9], C[9];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            Fe[3 * i + j] = s * (F[3 * i] * ci[j] + F[3 * i + 1] * ci[3 + j] + F[3 * i + 2] * ci[6 + j]) / det;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) C[3 * i + j] = Fe[i] * Fe[j] + Fe[3 + i] * Fe[3 + j] + Fe[6 + i] * Fe[6 + j];
+    // trial: the Mandel stress of C and the yield function
+    {
+        const double J2 = C[0] * (C[4] * C[8] - C[5] * C[7]) - C[1] * (C[3] * C[8] - C[5] * C[6]) +
+                          C[2] * (C[3] * C[7] - C[4] * C[6]);
+        const double f = pow(J2, -1.0 / 3.0), tr = (C[0] + C[4] + C[8]) * f / 3.0;
+        double dev2 = 0.0;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                const double v = dT * G * (C[3 * i + j] * f - (i == j ? tr : 0.0));
+                dev2 += v * v;
+            }
+        if (sqrt(dev2) - sqrt(2.0 / 3.0) * (sY + H * epsP) <= 0.0) return 0;
+    }
+    double c[3], V[9];
+    fs_eig3(C, c, V);
+    double etr[3], v[4];
+    for (int i = 0; i < 3; i++) { etr[i] = 0.5 * log(c[i]); v[i] = etr[i]; }
+    v[3] = 0.0;
+    bool conv = false;
+    for (int it = 0; it < 60; it++) {
+        double r[4], Jm[16];
+        for (int col = 0; col < 4; col++) {
+            FD e[3], dl = FD(v[3], col == 3 ? 1.0 : 0.0), rr[4];
+            for (int i = 0; i < 3; i++) e[i] = FD(v[i], col == i ? 1.0 : 0.0);
+            fs_rm_eqs(e, dl, etr, epsP, K, G, dT, sY, H, rr);
+            for (int i = 0; i < 4; i++) { Jm[4 * i + col] = rr[i].d; r[i] = rr[i].v; }
+        }
+        double mv[3], e0[3] = {v[0], v[1], v[2]};
+        fs_mand(e0, K, G, dT, mv);
+        const double scale = fmax(1.0, fmax(fabs(mv[0]), fmax(fabs(mv[1]), fabs(mv[2]))));
+        double rmax = 0.0;
+        for (int i = 0; i < 4; i++) rmax = fmax(rmax, fabs(r[i]));
+        if (rmax <= 1e-14 * scale) { conv = true; break; }
+        // Gaussian elimination with partial pivoting on the 4 x 4 system
+        double b[4] = {r[0], r[1], r[2], r[3]};
+        for (int k = 0; k < 4; k++) {
+            int pv = k;
+            for (int i = k + 1; i < 4; i++) if (fabs(Jm[4 * i + k]) > fabs(Jm[4 * pv + k])) pv = i;
+            if (pv != k) {
+                for (int j = 0; j < 4; j++) { const double t = Jm[4 * k + j]; Jm[4 * k + j] = Jm[4 * pv + j]; Jm[4 * pv + j] = t; }
+                const double t = b[k]; b[k] = b[pv]; b[pv] = t;
+            }
+            for (int i = k + 1; i < 4; i++) {
+                const double f = Jm[4 * i + k] / Jm[4 * k + k];
+                for (int j = k; j < 4; j++) Jm[4 * i + j] -= f * Jm[4 * k + j];
+                b[i] -= f * b[k];
+            }
+        }
+        double x[4];
+        for (int k = 3; k >= 0; k--) {
+            double t = b[k];
+            for (int j = k + 1; j < 4; j++) t -= Jm[4 * k + j] * x[j];
+            x[k] = t / Jm[4 * k + k];
+        }
+        for (int i = 0; i < 4; i++) v[i] -= x[i];
+    }
+    if (!conv) return 1;
+    double m[3], e[3] = {v[0], v[1], v[2]};
+    fs_mand(e, K, G, dT, m);
+    const double mean = (m[0] + m[1] + m[2]) / 3.0;
+    const double nm = sqrt((m[0] - mean) * (m[0] - mean) + (m[1] - mean) * (m[1] - mean) + (m[2] - mean) * (m[2] - mean));
+    double ex[3];
+    for (int i = 0; i < 3; i++) ex[i] = exp(v[3] * (m[i] - mean) / nm);
+    // exp(dl N) = V diag(ex) V^T; FP <- exp(dl N) FP
+    double E[9], FPn[9];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) E[3 * i + j] = V[3 * i] * ex[0] * V[3 * j] + V[3 * i + 1] * ex[1] * V[3 * j + 1] +
+                                                   V[3 * i + 2] * ex[2] * V[3 * j + 2];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) FPn[3 * i + j] = E[3 * i] * FP[j] + E[3 * i + 1] * FP[3 + j] + E[3 * i + 2] * FP[6 + j];
+    for (int q = 0; q < 9; q++) FP[q] = FPn[q];
+    epsP += v[3];
+    return 0;
 }
 
 // forces of cell c on its 2^d corners (f[a * d + i]) and its weighted sum of
@@ -300,6 +504,69 @@ __global__ void k_fs_precond(long long L, long long nd, const double *x, const d
         z[i] = i < nd ? x[i] / dg[i] : x[i] / dgf;
 }
 
+// per cell: the inverse of the plastic deformation (row-major 3 x 3)
+__global__ void k_fs_inv(long long N, const double *FP, double *FPinv)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const double *a = FP + c * 9;
+        double ci[9];
+        ci[0] = a[4] * a[8] - a[5] * a[7]; ci[1] = a[2] * a[7] - a[1] * a[8]; ci[2] = a[1] * a[5] - a[2] * a[4];
+        ci[3] = a[5] * a[6] - a[3] * a[8]; ci[4] = a[0] * a[8] - a[2] * a[6]; ci[5] = a[2] * a[3] - a[0] * a[5];
+        ci[6] = a[3] * a[7] - a[4] * a[6]; ci[7] = a[1] * a[6] - a[0] * a[7]; ci[8] = a[0] * a[4] - a[1] * a[3];
+        const double det = a[0] * ci[0] + a[1] * ci[3] + a[2] * ci[6];
+        for (int q = 0; q < 9; q++) FPinv[c * 9 + q] = ci[q] / det;
+    }
+}
+
+// per cell: one multiplicative J2 update at the cell-centre deformation
+// Fbar + sum_a u_a (x) grad N_a(centre); bad[0] counts points whose update
+// did not converge
+__global__ void k_fs_return_cells(FSArgs A, const double *z, double sY, double H, double *FP, double *epsP,
+                                  unsigned int *bad)
+{
+    const int d = A.d, na = 1 << d;
+    const long long N = A.N;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        double F[9];
+        fs_fbar(d, z + (size_t)d * N, F);
+        for (int i = 0; i < d; i++)
+            for (int k = 0; k < d; k++) {
+                double t = F[3 * i + k];
+                for (int a = 0; a < na; a++) {
+                    double g = 1.0;
+                    for (int l = 0; l < d; l++) g *= l == k ? (((a >> l) & 1) ? 1.0 : -1.0) : 0.5;
+                    t += z[fs_node(A, c, a) * d + i] * g;
+                }
+                F[3 * i + k] = t;
+            }
+        if (d == 2) {
+            F[2] = F[5] = F[6] = F[7] = 0.0;
+            F[8] = 1.0;
+        }
+        double fp[9];
+        for (int q = 0; q < 9; q++) fp[q] = FP[c * 9 + q];
+        double ep = epsP[c];
+        const double dT = 1.0 - A.Wf[c] * A.omega;
+        if (fs_return_map(F, fp, ep, A.K[c], A.G[c], dT, sY, H)) atomicAdd(bad, 1u);
+        for (int q = 0; q < 9; q++) FP[c * 9 + q] = fp[q];
+        epsP[c] = ep;
+    }
+}
+
+// independent points: F, FP, epsP, K, G, dT per point
+__global__ void k_fs_return_points(int n, const double *F, double *FP, double *epsP, const double *K, const double *G,
+                                   const double *dT, double sY, double H, unsigned int *bad)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        double f[9], fp[9];
+        for (int q = 0; q < 9; q++) { f[q] = F[c * 9 + q]; fp[q] = FP[c * 9 + q]; }
+        double ep = epsP[c];
+        if (fs_return_map(f, fp, ep, K[c], G[c], dT[c], sY, H)) atomicAdd(bad, 1u);
+        for (int q = 0; q < 9; q++) FP[c * 9 + q] = fp[q];
+        epsP[c] = ep;
+    }
+}
+
 constexpr int FS_NB = 128;     // blocks of the reductions
 
 struct FSSolver {
@@ -371,12 +638,11 @@ int fs_fail(int code, const char *msg)
     return code;
 }
 
-}  // namespace
-
-extern "C" {
-
-int pf_finite_strain_solve(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
-                           const double *pbar, const pf_fs_opts *opts, double *u, double *Fbar, pf_fs_stats *stats)
+// the equilibrium with the plastic deformation FP (N x 9, or null: identity)
+// and, with cfg->plasticity, FP and epsP (N) updated by one return map per
+// cell after it
+int fs_run(const pf_config *cfg, const double *theta, const double *phi_g, double omega, const double *pbar,
+           const pf_fs_opts *opts, double *u, double *Fbar, double *FP, double *epsP, pf_fs_stats *stats)
 {
     if (!cfg || !theta || !phi_g || !opts || !u || !Fbar) return fs_fail(PF_EINVAL, "null argument");
     const int d = cfg->ndim;
@@ -408,12 +674,27 @@ int pf_finite_strain_solve(const pf_config *cfg, const double *theta, const doub
         return fs_fail(PF_ENOMEM, "cudaMalloc failed");
     cudaMemcpy(S.th, theta, sizeof(double) * N, cudaMemcpyHostToDevice);
     cudaMemcpy(S.pg, phi_g, sizeof(double) * N, cudaMemcpyHostToDevice);
+    double *dFP = nullptr, *dFPinv = nullptr, *dEp = nullptr;
+    unsigned int *dbad = nullptr;
+    if (FP) {
+        if (S.alloc(&dFP, (size_t)N * 9) != cudaSuccess || S.alloc(&dFPinv, (size_t)N * 9) != cudaSuccess ||
+            S.alloc(&dEp, N) != cudaSuccess || S.alloc(reinterpret_cast<double **>(&dbad), 1) != cudaSuccess)
+            return fs_fail(PF_ENOMEM, "cudaMalloc failed");
+        cudaMemcpy(dFP, FP, sizeof(double) * N * 9, cudaMemcpyHostToDevice);
+        cudaMemcpy(dEp, epsP, sizeof(double) * N, cudaMemcpyHostToDevice);
+        cudaMemset(dbad, 0, sizeof(unsigned int));
+    }
     S.grid = (int)std::min<long long>((N + 127) / 128, 4096);
     const double Ks = Es / (3 * (1 - 2 * nu)), Gs = Es / (2 * (1 + nu));
     const double Kg = Eg / (3 * (1 - 2 * nu)), Gg = Eg / (2 * (1 + nu));
     k_fs_moduli<<<S.grid, 128>>>(N, S.th, S.pg, Ks, Gs, Kg, Gg, S.K, S.G, S.Wf);
     S.A.d = d; S.A.nx = cfg->nx; S.A.ny = cfg->ny; S.A.nz = d == 3 ? cfg->nz : 1; S.A.N = N;
     S.A.K = S.K; S.A.G = S.G; S.A.Wf = S.Wf; S.A.omega = 0.0;
+    S.A.FPinv = nullptr;
+    if (FP) {
+        k_fs_inv<<<S.grid, 128>>>(N, dFP, dFPinv);
+        S.A.FPinv = dFPinv;
+    }
     // small-strain diagonals of a displacement dof per unit lambda and mu:
     // sum over Gauss points of w (dN_i)^2 and w (|dN|^2 + dN_i^2); equal
     // for every corner and component
@@ -506,9 +787,71 @@ int pf_finite_strain_solve(const pf_config *cfg, const double *theta, const doub
     for (int i = 0; i < d; i++)
         for (int j = 0; j < d; j++) Fbar[i * d + j] = fb[3 * i + j];
     st.residual = res;
+    if (FP && cfg->plasticity) {
+        S.A.omega = omega;
+        k_fs_return_cells<<<S.grid, 64>>>(S.A, S.z, cfg->p.sigma_Y, cfg->p.H_hard, dFP, dEp, dbad);
+        unsigned int nbad = 0;
+        cudaMemcpy(&nbad, dbad, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+        cudaMemcpy(FP, dFP, sizeof(double) * N * 9, cudaMemcpyDeviceToHost);
+        cudaMemcpy(epsP, dEp, sizeof(double) * N, cudaMemcpyDeviceToHost);
+        if (nbad) {
+            if (stats) *stats = st;
+            return fs_fail(PF_ENOTCONV, "return map did not converge");
+        }
+    }
     if (stats) *stats = st;
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fs_fail(PF_ECUDA, cudaGetErrorString(e));
+    return PF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pf_finite_strain_solve(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
+                           const double *pbar, const pf_fs_opts *opts, double *u, double *Fbar, pf_fs_stats *stats)
+{
+    return fs_run(cfg, theta, phi_g, omega, pbar, opts, u, Fbar, nullptr, nullptr, stats);
+}
+
+int pf_finite_strain_step(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
+                          const double *pbar, const pf_fs_opts *opts, double *u, double *Fbar, double *FP,
+                          double *epsP, pf_fs_stats *stats)
+{
+    if (!FP || !epsP) return fs_fail(PF_EINVAL, "FP and epsP are required");
+    return fs_run(cfg, theta, phi_g, omega, pbar, opts, u, Fbar, FP, epsP, stats);
+}
+
+int pf_fs_return_map(int n, const double *F, double *FP, double *epsP, const double *K, const double *G,
+                     const double *dT, double sigma_Y, double H)
+{
+    if (n < 0 || (n > 0 && (!F || !FP || !epsP || !K || !G || !dT))) return fs_fail(PF_EINVAL, "null argument");
+    if (n == 0) return PF_OK;
+    double *b[7] = {};
+    const size_t len[7] = {(size_t)n * 9, (size_t)n * 9, (size_t)n, (size_t)n, (size_t)n, (size_t)n, 1};
+    for (int k = 0; k < 7; k++)
+        if (cudaMalloc((void **)&b[k], sizeof(double) * len[k]) != cudaSuccess) {
+            for (int j = 0; j < k; j++) cudaFree(b[j]);
+            return fs_fail(PF_ENOMEM, "cudaMalloc failed");
+        }
+    cudaMemcpy(b[0], F, sizeof(double) * n * 9, cudaMemcpyHostToDevice);
+    cudaMemcpy(b[1], FP, sizeof(double) * n * 9, cudaMemcpyHostToDevice);
+    cudaMemcpy(b[2], epsP, sizeof(double) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(b[3], K, sizeof(double) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(b[4], G, sizeof(double) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(b[5], dT, sizeof(double) * n, cudaMemcpyHostToDevice);
+    cudaMemset(b[6], 0, sizeof(double));
+    unsigned int *bad = reinterpret_cast<unsigned int *>(b[6]);
+    k_fs_return_points<<<(n + 63) / 64, 64>>>(n, b[0], b[1], b[2], b[3], b[4], b[5], sigma_Y, H, bad);
+    unsigned int nbad = 0;
+    cudaMemcpy(&nbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+    cudaMemcpy(FP, b[1], sizeof(double) * n * 9, cudaMemcpyDeviceToHost);
+    cudaMemcpy(epsP, b[2], sizeof(double) * n, cudaMemcpyDeviceToHost);
+    const cudaError_t e = cudaDeviceSynchronize();
+    for (int k = 0; k < 7; k++) cudaFree(b[k]);
+    if (e != cudaSuccess) return fs_fail(PF_ECUDA, cudaGetErrorString(e));
+    if (nbad) return fs_fail(PF_ENOTCONV, "return map did not converge");
     return PF_OK;
 }
 

@@ -99,7 +99,8 @@ class pf_unet_config(ctypes.Structure):
 
 
 # exported symbols, in the order of include/pf.h then include/pf_unet.h
-SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_step_implicit", "pf_finite_strain_solve", "pf_fs_last_error",
+SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_step_implicit", "pf_finite_strain_solve", "pf_finite_strain_step",
+           "pf_fs_return_map", "pf_fs_last_error",
            "pf_get_fields", "pf_get_diagnostics",
            "pf_free_energy", "pf_dt_stable", "pf_profile_enable", "pf_profile_read",
            "pf_batch_create", "pf_batch_size", "pf_batch_set_fields", "pf_batch_get_fields",
@@ -176,6 +177,12 @@ def lib():
         l.pf_finite_strain_solve.argtypes = [ctypes.POINTER(pf_config), _DP, _DP, ctypes.c_double, _DP,
                                              ctypes.POINTER(pf_fs_opts), _DP, _DP, ctypes.POINTER(pf_fs_stats)]
         l.pf_finite_strain_solve.restype = ctypes.c_int
+        l.pf_finite_strain_step.argtypes = [ctypes.POINTER(pf_config), _DP, _DP, ctypes.c_double, _DP,
+                                            ctypes.POINTER(pf_fs_opts), _DP, _DP, _DP, _DP,
+                                            ctypes.POINTER(pf_fs_stats)]
+        l.pf_finite_strain_step.restype = ctypes.c_int
+        l.pf_fs_return_map.argtypes = [ctypes.c_int, _DP, _DP, _DP, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double]
+        l.pf_fs_return_map.restype = ctypes.c_int
         l.pf_fs_last_error.argtypes = []
         l.pf_fs_last_error.restype = ctypes.c_char_p
         l.pf_get_fields.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_fields), ctypes.c_int]
@@ -280,6 +287,35 @@ def pf_finite_strain_solve(cfg, theta, phig, omega, pbar, opts):
                                       ptr(pb) if pb is not None else None, ctypes.byref(opts), ptr(u), ptr(fb),
                                       ctypes.byref(st))
     return rc, u.reshape(-1, d), fb.reshape(d, d), st
+
+
+def pf_finite_strain_step(cfg, theta, phig, omega, pbar, opts, FP, epsP):
+    """One staggered step; FP (N, 3, 3) and epsP (N,) are updated in place
+    (contiguous float64 arrays); returns (rc, u, Fbar, stats)."""
+    import numpy as np
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    pg = np.ascontiguousarray(phig, dtype=np.float64)
+    assert FP.dtype == np.float64 and FP.flags.c_contiguous and epsP.dtype == np.float64 and epsP.flags.c_contiguous
+    d = cfg.ndim
+    u = np.zeros(th.size * d)
+    fb = np.zeros(d * d)
+    pb = None if pbar is None else np.ascontiguousarray(pbar, dtype=np.float64).ravel()
+    st = pf_fs_stats()
+    ptr = lambda a: a.ctypes.data_as(_DP)                                   # noqa: E731
+    rc = lib().pf_finite_strain_step(ctypes.byref(cfg), ptr(th), ptr(pg), float(omega),
+                                     ptr(pb) if pb is not None else None, ctypes.byref(opts), ptr(u), ptr(fb),
+                                     ptr(FP), ptr(epsP), ctypes.byref(st))
+    return rc, u.reshape(-1, d), fb.reshape(d, d), st
+
+
+def pf_fs_return_map(F, FP, epsP, K, G, dT, sigma_Y, H):
+    """Pointwise multiplicative J2 update; FP, epsP updated in place."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (F, K, G, dT)]
+    assert FP.dtype == np.float64 and FP.flags.c_contiguous and epsP.dtype == np.float64 and epsP.flags.c_contiguous
+    ptr = lambda a: a.ctypes.data_as(_DP)                                   # noqa: E731
+    return lib().pf_fs_return_map(int(epsP.size), ptr(arrs[0]), ptr(FP), ptr(epsP), ptr(arrs[1]), ptr(arrs[2]),
+                                  ptr(arrs[3]), float(sigma_Y), float(H))
 
 
 def pf_get_fields(h, fields, where=PF_HOST):

@@ -99,3 +99,61 @@ def test_finite_strain_rejects_bad_arguments():
     bad = native.pf_fs_opts(nload=0, newton_maxit=10, newton_tol=1e-10, cg_maxit=10, cg_rtol=1e-6)
     rc, _, _, _ = native.pf_finite_strain_solve(cfg, th.ravel(), th.ravel() * 0, 0.1, None, bad)
     assert rc == native.PF_EINVAL and b"pf_fs_opts" in native.lib().pf_fs_last_error()
+
+
+def test_return_map_matches_oracle(fs):
+    """The multiplicative J2 update of independent points against the
+    oracle's return_map (Sec. 2.3 PlaTwoJ, Sec. 2.4 RulFloPla): plastic and
+    elastic points, first and second steps (FP from a previous update)."""
+    rng = np.random.default_rng(7)
+    n = 40
+    F = np.empty((n, 3, 3))
+    for i in range(n):
+        g = (0.0005 if i % 3 == 0 else 0.02) * rng.standard_normal((3, 3))
+        F[i] = np.eye(3) + g + g.T * 0.5
+    K = np.full(n, 1.0 / (3 * 0.4))
+    G = np.full(n, 1.0 / 2.6)
+    dT = 1.0 - 0.2 * rng.random(n)
+    sY, H = 0.004, 0.01
+    FP = np.tile(np.eye(3), (n, 1, 1))
+    ep = np.zeros(n)
+    ref_FP, ref_ep = FP.copy(), ep.copy()
+    for rnd in range(2):
+        for i in range(n):
+            ref_FP[i], ref_ep[i], _, _ = fs.return_map(F[i], ref_FP[i], ref_ep[i], K[i], G[i], dT[i], sY, H)
+        rc = native.pf_fs_return_map(F, FP, ep, K, G, dT, sY, H)
+        assert rc == native.PF_OK, native.lib().pf_fs_last_error()
+        assert np.abs(FP - ref_FP).max() < 1e-11, (rnd, np.abs(FP - ref_FP).max())
+        assert np.abs(ep - ref_ep).max() < 1e-11
+        if rnd == 0:
+            assert (ep > 0).sum() >= n // 2 and (ep == 0).sum() >= n // 4      # plastic and elastic points
+        F = F @ (np.eye(3) + 0.01 * np.array([[0, 1, 0], [1, 0, 0], [0, 0, 0]]))
+    assert np.abs(np.linalg.det(FP) - 1.0).max() < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (4, 4, 4)])
+def test_finite_strain_plastic_steps_match_oracle(fs, shape):
+    """Two staggered elasto-plastic mechanics steps on a core-shell (the
+    second with the plastic deformation of the first) against
+    Problem.mechanics_step."""
+    from oracle import split_phases
+    r = 0.3 * min(shape)
+    f = inputs.core_shell(shape, r, 0.15 * min(shape), delta=1.0)
+    th, pg = split_phases(f["phi_f"], f["phi_w"])
+    prm = workloads.params(plasticity=1, sigma_Y=0.002, H_hard=0.01)
+    om = 0.2
+    pr = fs.Problem(th, pg, prm, om)
+    N = th.size
+    FP = np.tile(np.eye(3), (N, 1, 1)).copy()
+    ep = np.zeros(N)
+    cfg = make_config(th.shape, prm)
+    for k in range(2):
+        u0, F0 = pr.unpack(pr.mechanics_step(nload=2))
+        rc, u, Fb, st = native.pf_finite_strain_step(cfg, th.ravel(), pg.ravel(), om, None, _opts(2), FP, ep)
+        assert rc == native.PF_OK, native.lib().pf_fs_last_error()
+        scale = max(np.abs(u0).max(), 1e-12)
+        assert np.abs(u - u0).max() < 1e-8 * scale, (k, np.abs(u - u0).max(), scale)
+        assert np.abs(Fb - F0).max() < 1e-10
+        assert np.abs(FP - pr.FP).max() < 1e-9, (k, np.abs(FP - pr.FP).max())
+        assert np.abs(ep - pr.epsP).max() < 1e-9
+    assert pr.epsP.max() > 0.0 and (ep > 0).any()
