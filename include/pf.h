@@ -300,6 +300,16 @@ int pf_finite_strain_step(const pf_config *cfg, const double *theta, const doubl
  * in/out), K, G, dT (n each: bulk and shear moduli, d_T), sigma_Y, H. */
 int pf_fs_return_map(int n, const double *F, double *FP, double *epsP, const double *K, const double *G,
                      const double *dT, double sigma_Y, double H);
+
+/* The elastic part of the order parameter's driving force per cell,
+ * d psi / d theta at fixed deformation and plastic deformation (the
+ * derivative of the energy above through W_f in d_T and through the
+ * mixture moduli), at each cell-centre deformation of the state (u, Fbar) of
+ * pf_finite_strain_solve / _step; FP may be NULL (identity).  force: out,
+ * host, N.  The coupled explicit step adds -(L/2) mob times it to theta's
+ * rate in place of the small-strain coupling. */
+int pf_fs_elastic_force(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
+                        const double *u, const double *Fbar, const double *FP, double *force);
 const char *pf_fs_last_error(void);
 
 /* Copy the current state (the fields of Sec. 2.4 and the mechanical state)

@@ -65,6 +65,7 @@ __device__ __forceinline__ FD fd_exp(FD a)
     return FD(q, q * a.d);
 }
 __device__ __forceinline__ double fd_exp(double a) { return exp(a); }
+__device__ __forceinline__ FD fd_log(FD a) { return FD(log(a.v), a.d / a.v); }
 __device__ __forceinline__ FD fd_sqrt(FD a)
 {
     const double q = sqrt(a.v);
@@ -567,6 +568,55 @@ __global__ void k_fs_return_points(int n, const double *F, double *FP, double *e
     }
 }
 
+// per cell: d psi / d theta at fixed deformation (the cell-centre
+// deformation of the state z) and plastic deformation: the elastic part of
+// the order parameter's driving force (the derivative through W_f in d_T and
+// through the mixture moduli), in forward mode along theta
+__global__ void k_fs_force(FSArgs A, const double *z, const double *theta, const double *phig, double Ks, double Gs,
+                           double Kg, double Gg, double *force)
+{
+    const int d = A.d, na = 1 << d;
+    const long long N = A.N;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        double F[9];
+        fs_fbar(d, z + (size_t)d * N, F);
+        for (int i = 0; i < d; i++)
+            for (int k = 0; k < d; k++) {
+                double t = F[3 * i + k];
+                for (int a = 0; a < na; a++) {
+                    double g = 1.0;
+                    for (int l = 0; l < d; l++) g *= l == k ? (((a >> l) & 1) ? 1.0 : -1.0) : 0.5;
+                    t += z[fs_node(A, c, a) * d + i] * g;
+                }
+                F[3 * i + k] = t;
+            }
+        if (d == 2) {
+            F[2] = F[5] = F[6] = F[7] = 0.0;
+            F[8] = 1.0;
+        }
+        const FD th(theta[c], 1.0);
+        const double hg = phig[c] * phig[c] * phig[c] * (phig[c] * (6.0 * phig[c] - 15.0) + 10.0);
+        const FD ht = th * th * th * (th * (FD(6.0) * th - FD(15.0)) + FD(10.0));
+        const FD wf = FD(1.0 - hg) * ht, ww = FD(1.0 - hg) * (FD(1.0) - ht);
+        const FD K = (wf + ww) * FD(Ks) + FD(hg * Kg), G = (wf + ww) * FD(Gs) + FD(hg * Gg);
+        const FD dT = FD(1.0) - wf * FD(A.omega), s = fd_pow(dT, -1.0 / 3.0);
+        const double *Fi = A.FPinv ? A.FPinv + c * 9 : nullptr;
+        FD Fe[9];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                const double v = Fi ? F[3 * i] * Fi[j] + F[3 * i + 1] * Fi[3 + j] + F[3 * i + 2] * Fi[6 + j] : F[3 * i + j];
+                Fe[3 * i + j] = s * FD(v);
+            }
+        const FD J = Fe[0] * (Fe[4] * Fe[8] - Fe[5] * Fe[7]) - Fe[1] * (Fe[3] * Fe[8] - Fe[5] * Fe[6]) +
+                     Fe[2] * (Fe[3] * Fe[7] - Fe[4] * Fe[6]);
+        FD I1(0.0);
+        for (int q = 0; q < 9; q++) I1 = I1 + Fe[q] * Fe[q];
+        const FD psi = dT * (FD(0.25) * K * (J * J - FD(1.0) - FD(2.0) * fd_log(J)) +
+                             FD(0.5) * G * (fd_pow(J, -2.0 / 3.0) * I1 - FD(3.0)));
+        force[c] = psi.d;
+    }
+}
+
 constexpr int FS_NB = 128;     // blocks of the reductions
 
 struct FSSolver {
@@ -821,6 +871,54 @@ int pf_finite_strain_step(const pf_config *cfg, const double *theta, const doubl
 {
     if (!FP || !epsP) return fs_fail(PF_EINVAL, "FP and epsP are required");
     return fs_run(cfg, theta, phi_g, omega, pbar, opts, u, Fbar, FP, epsP, stats);
+}
+
+int pf_fs_elastic_force(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
+                        const double *u, const double *Fbar, const double *FP, double *force)
+{
+    if (!cfg || !theta || !phi_g || !u || !Fbar || !force) return fs_fail(PF_EINVAL, "null argument");
+    const int d = cfg->ndim;
+    if (d != 2 && d != 3) return fs_fail(PF_EINVAL, "ndim must be 2 or 3");
+    if (cfg->nx < 2 || cfg->ny < 2 || (d == 3 && cfg->nz < 2)) return fs_fail(PF_EINVAL, "grid sizes must be >= 2");
+    const double nu = cfg->p.nu, Es = cfg->p.E_s, Eg = Es * cfg->p.E_g_ratio;
+    const long long N = (long long)cfg->nx * cfg->ny * (d == 3 ? cfg->nz : 1);
+    const int m = d == 3 ? 6 : 3;
+    // the state vector: u, then the symmetric components of Fbar
+    std::vector<double> z((size_t)d * N + m);
+    memcpy(z.data(), u, sizeof(double) * d * N);
+    if (d == 3) {
+        const double zf[6] = {Fbar[0], Fbar[4], Fbar[8], Fbar[5], Fbar[2], Fbar[1]};
+        memcpy(z.data() + d * N, zf, sizeof(zf));
+    } else {
+        const double zf[3] = {Fbar[0], Fbar[3], Fbar[1]};
+        memcpy(z.data() + d * N, zf, sizeof(zf));
+    }
+    FSSolver S;          // device buffers freed with it
+    double *dz, *dth, *dpg, *dF, *dFP = nullptr, *dFPinv = nullptr;
+    if (S.alloc(&dz, z.size()) != cudaSuccess || S.alloc(&dth, N) != cudaSuccess || S.alloc(&dpg, N) != cudaSuccess ||
+        S.alloc(&dF, N) != cudaSuccess)
+        return fs_fail(PF_ENOMEM, "cudaMalloc failed");
+    if (FP && (S.alloc(&dFP, (size_t)N * 9) != cudaSuccess || S.alloc(&dFPinv, (size_t)N * 9) != cudaSuccess))
+        return fs_fail(PF_ENOMEM, "cudaMalloc failed");
+    cudaMemcpy(dz, z.data(), sizeof(double) * z.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(dth, theta, sizeof(double) * N, cudaMemcpyHostToDevice);
+    cudaMemcpy(dpg, phi_g, sizeof(double) * N, cudaMemcpyHostToDevice);
+    const int grid = (int)std::min<long long>((N + 127) / 128, 4096);
+    FSArgs A;
+    memset(&A, 0, sizeof(A));
+    A.d = d; A.nx = cfg->nx; A.ny = cfg->ny; A.nz = d == 3 ? cfg->nz : 1; A.N = N; A.omega = omega;
+    if (FP) {
+        cudaMemcpy(dFP, FP, sizeof(double) * N * 9, cudaMemcpyHostToDevice);
+        k_fs_inv<<<grid, 128>>>(N, dFP, dFPinv);
+        A.FPinv = dFPinv;
+    }
+    const double Ks = Es / (3 * (1 - 2 * nu)), Gs = Es / (2 * (1 + nu));
+    const double Kg = Eg / (3 * (1 - 2 * nu)), Gg = Eg / (2 * (1 + nu));
+    k_fs_force<<<grid, 128>>>(A, dz, dth, dpg, Ks, Gs, Kg, Gg, dF);
+    cudaMemcpy(force, dF, sizeof(double) * N, cudaMemcpyDeviceToHost);
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fs_fail(PF_ECUDA, cudaGetErrorString(e));
+    return PF_OK;
 }
 
 int pf_fs_return_map(int n, const double *F, double *FP, double *epsP, const double *K, const double *G,

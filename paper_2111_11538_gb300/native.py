@@ -100,7 +100,7 @@ class pf_unet_config(ctypes.Structure):
 
 # exported symbols, in the order of include/pf.h then include/pf_unet.h
 SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_step_implicit", "pf_finite_strain_solve", "pf_finite_strain_step",
-           "pf_fs_return_map", "pf_fs_last_error",
+           "pf_fs_return_map", "pf_fs_elastic_force", "pf_fs_last_error",
            "pf_get_fields", "pf_get_diagnostics",
            "pf_free_energy", "pf_dt_stable", "pf_profile_enable", "pf_profile_read",
            "pf_batch_create", "pf_batch_size", "pf_batch_set_fields", "pf_batch_get_fields",
@@ -183,6 +183,8 @@ def lib():
         l.pf_finite_strain_step.restype = ctypes.c_int
         l.pf_fs_return_map.argtypes = [ctypes.c_int, _DP, _DP, _DP, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double]
         l.pf_fs_return_map.restype = ctypes.c_int
+        l.pf_fs_elastic_force.argtypes = [ctypes.POINTER(pf_config), _DP, _DP, ctypes.c_double, _DP, _DP, _DP, _DP]
+        l.pf_fs_elastic_force.restype = ctypes.c_int
         l.pf_fs_last_error.argtypes = []
         l.pf_fs_last_error.restype = ctypes.c_char_p
         l.pf_get_fields.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_fields), ctypes.c_int]
@@ -316,6 +318,18 @@ def pf_fs_return_map(F, FP, epsP, K, G, dT, sigma_Y, H):
     ptr = lambda a: a.ctypes.data_as(_DP)                                   # noqa: E731
     return lib().pf_fs_return_map(int(epsP.size), ptr(arrs[0]), ptr(FP), ptr(epsP), ptr(arrs[1]), ptr(arrs[2]),
                                   ptr(arrs[3]), float(sigma_Y), float(H))
+
+
+def pf_fs_elastic_force(cfg, theta, phig, omega, u, Fbar, FP=None):
+    """(rc, force per cell); host arrays."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (theta, phig, u, Fbar)]
+    fp = None if FP is None else np.ascontiguousarray(FP, dtype=np.float64).ravel()
+    out = np.zeros(arrs[0].size)
+    ptr = lambda a: a.ctypes.data_as(_DP)                                   # noqa: E731
+    rc = lib().pf_fs_elastic_force(ctypes.byref(cfg), ptr(arrs[0]), ptr(arrs[1]), float(omega), ptr(arrs[2]),
+                                   ptr(arrs[3]), ptr(fp) if fp is not None else None, ptr(out))
+    return rc, out
 
 
 def pf_get_fields(h, fields, where=PF_HOST):

@@ -157,3 +157,21 @@ def test_finite_strain_plastic_steps_match_oracle(fs, shape):
         assert np.abs(FP - pr.FP).max() < 1e-9, (k, np.abs(FP - pr.FP).max())
         assert np.abs(ep - pr.epsP).max() < 1e-9
     assert pr.epsP.max() > 0.0 and (ep > 0).any()
+
+
+def test_elastic_driving_force_matches_oracle(fs):
+    """d psi / d theta at the cell centres (the coupled step's elastic force
+    on the order parameter) after an elasto-plastic step, against the
+    oracle's central differences (step 1e-6: agreement to 1e-7 relative)."""
+    from oracle import split_phases
+    f = inputs.core_shell((8, 8), 2.5, 1.0, delta=1.0)
+    th, pg = split_phases(f["phi_f"], f["phi_w"])
+    prm = workloads.params(plasticity=1, sigma_Y=0.002, H_hard=0.01)
+    pr = fs.Problem(th, pg, prm, 0.2)
+    z = pr.mechanics_step(nload=2)
+    ref = fs.elastic_force(pr, z)
+    u, Fb = pr.unpack(z)
+    rc, g = native.pf_fs_elastic_force(make_config(th.shape, prm), th, pg, 0.2, u, Fb, pr.FP)
+    assert rc == native.PF_OK, native.lib().pf_fs_last_error()
+    assert np.abs(g - ref).max() < 1e-7 * np.abs(ref).max(), (np.abs(g - ref).max(), np.abs(ref).max())
+    assert np.abs(ref).max() > 1e-4
