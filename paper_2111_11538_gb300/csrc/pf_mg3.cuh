@@ -538,16 +538,25 @@ __device__ int mg_pass3(const PCGArgs<T, 3> &A, const MGHier<T> &H, PCGState &S,
                 T f[3];
                 restrict3(k, gx, gy, gz, f);
                 const T di = c2 * raw[h];
-#pragma unroll
-                for (int c = 0; c < 3; c++) v[c] = di * f[c];
-            },
-            [&](int n, const T (&v)[3], const T (&q)[3]) {
-                const int gx = n % V.nx, gy = (n / V.nx) % V.ny, gz = n / (V.nx * V.ny);
-                T f[3];
-                restrict3(k, gx, gy, gz, f);
+                // the tile's own nodes keep f for their epilogue (a halo
+                // plane's interior belongs to a neighbouring item, which
+                // stores the same values)
+                const int lx = h % (MGZ_TX + 2), ly = h / (MGZ_TX + 2);
+                const bool inner = lx >= 1 && lx <= MGZ_TX && ly >= 1 && ly <= MGZ_TY;
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    V.f[c][n] = f[c];
+                    v[c] = di * f[c];
+                    if (inner) V.f[c][lin3(V, gx, gy, gz)] = f[c];
+                }
+            },
+            [&](int n, const T (&v)[3], const T (&q)[3]) {
+                // f, stored by the forming of this plane (same block, before
+                // the plane's barriers)
+                T f[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++) f[c] = __ldcg(V.f[c] + n);
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
                     V.xpre[c][n] = v[c];
                     V.r[1][c][n] = f[c] - q[c];
                     V.d[1][c][n] = v[c];
