@@ -1002,6 +1002,8 @@ size_t pcg_dyn_smem(int shape, bool mg)
         // (FP64, three raw streams)
         const size_t cells = sizeof(T) * (size_t)mg_sweep3z_words<T>();
         const size_t stp = sizeof(double) * (size_t)mg_sweep3z_words<double, true>(3);
+        static_assert(sizeof(DS) == sizeof(double) && V3S<DS>::WORDS == V3S<double>::WORDS,
+                      "the double-single set-up sweep fits the FP64 one's shared memory");
         return cells > stp ? cells : stp;
     }
     if (D != 3 || sizeof(T) != 4 || shape != 0) return 0;

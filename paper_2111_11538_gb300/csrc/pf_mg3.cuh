@@ -19,9 +19,46 @@
 
 namespace pfdev {
 
+// Double-single number (hi + lo, two floats, ~48 significant bits): the
+// arithmetic of the mixed method's residual sweep, which needs about FP64
+// accuracy and gets it from the FP32 pipes (GB300 runs FP64 at 1/64 of the
+// FP32 rate).  Sums are error-free transformations (Knuth's two-sum,
+// Dekker's fast two-sum), products take their rounding error from an FMA;
+// the relative error of a sum or product is ~2^-44 of its operands, against
+// FP64's 2^-53.
+struct DS {
+    float hi, lo;
+    __host__ __device__ __forceinline__ DS() {}
+    __host__ __device__ __forceinline__ DS(int x) : hi((float)x), lo(0.f) {}
+    __host__ __device__ __forceinline__ DS(float x) : hi(x), lo(0.f) {}
+    __host__ __device__ __forceinline__ DS(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+    __host__ __device__ __forceinline__ DS(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ DS ds_fast(float a, float b)
+{
+    const float s = a + b;
+    return DS(s, b - (s - a));
+}
+__device__ __forceinline__ DS operator+(DS x, DS y)
+{
+    const float s = x.hi + y.hi, v = s - x.hi;
+    const float e = (x.hi - (s - v)) + (y.hi - v) + (x.lo + y.lo);
+    return ds_fast(s, e);
+}
+__device__ __forceinline__ DS operator-(DS x) { return DS(-x.hi, -x.lo); }
+__device__ __forceinline__ DS operator-(DS x, DS y) { return x + (-y); }
+__device__ __forceinline__ DS operator*(DS x, DS y)
+{
+    const float p = x.hi * y.hi;
+    const float e = fmaf(x.hi, y.hi, -p) + (x.hi * y.lo + x.lo * y.hi);
+    return ds_fast(p, e);
+}
+__device__ __forceinline__ DS &operator+=(DS &x, DS y) { x = x + y; return x; }
+
 // Shared-memory storage of 3-vectors: FP32 as one float4 per entry (one
-// 128-bit access), FP64 as three planes of n doubles.  WORDS values of T per
-// entry.
+// 128-bit access), FP64 and double-single as three planes of n values.
+// WORDS values of T per entry.
 template <typename T> struct V3S;
 template <> struct V3S<float> {
     static constexpr int WORDS = 4;
@@ -37,21 +74,23 @@ template <> struct V3S<float> {
         v[2] = a.z;
     }
 };
-template <> struct V3S<double> {
+template <typename T> struct V3Planes {
     static constexpr int WORDS = 3;
-    __device__ static __forceinline__ void st(double *b, int n, int i, const double (&v)[3])
+    __device__ static __forceinline__ void st(T *b, int n, int i, const T (&v)[3])
     {
         b[i] = v[0];
         b[n + i] = v[1];
         b[2 * n + i] = v[2];
     }
-    __device__ static __forceinline__ void ld(const double *b, int n, int i, double (&v)[3])
+    __device__ static __forceinline__ void ld(const T *b, int n, int i, T (&v)[3])
     {
         v[0] = b[i];
         v[1] = b[n + i];
         v[2] = b[2 * n + i];
     }
 };
+template <> struct V3S<double> : V3Planes<double> {};
+template <> struct V3S<DS> : V3Planes<DS> {};
 
 // Forces of a 3D cell on its eight corner nodes, f[a][comp] with
 // a = ax + 2 ay + 4 az, from its average stress s (mean strain included) and
@@ -355,8 +394,9 @@ __device__ void mg_coarsen3(const MGLevel<T> &F, const MGLevel<T> &C, long long 
 // sig*, [10..15] the cells' stress of x without the mean strain).  resid: a
 // later refinement pass, which reads b from A.b64 and skips what does not
 // change during a solve.  Its three raw streams (x) are copied one plane ahead
-// like the FP32 sweeps' (8-byte asynchronous copies).  smem:
-// mg_sweep3z_words<double, true>(3) doubles.
+// like the FP32 sweeps' (8-byte asynchronous copies).  The mixed method runs
+// the operator in double-single arithmetic (DS) on the FP32 pipes, the FP64
+// method in FP64.  smem: mg_sweep3z_words<double, true>(3) doubles.
 template <typename T>
 __device__ void setup_march3(const PCGArgs<T, 3> &A, bool use_x, bool refine, bool resid, const double *xe,
                              double *smem, Acc<double> (&acc)[16], int bid, int nbk)
@@ -398,26 +438,55 @@ __device__ void setup_march3(const PCGArgs<T, 3> &A, bool use_x, bool refine, bo
         for (long long n = t0; n < P.N; n += st) node((int)n, zero);
         return;
     }
-    // x: the FP64 solution of the refinement, or the solution itself (FP64)
-    __shared__ const double *s_xs[3];
-    if (threadIdx.x == 0)
-        for (int c = 0; c < 3; c++) {
-            if constexpr (sizeof(T) == 8) s_xs[c] = refine ? A.x64[c] : reinterpret_cast<const double *>(A.x[c]);
-            else s_xs[c] = A.x64[c];
+    if constexpr (sizeof(T) == 4) {
+        // mixed method: the sweep in double-single arithmetic; x64 is copied
+        // as 8-byte words and split into hi + lo when its node plane is formed
+        __shared__ DS s_xd[6];
+        __shared__ const DS *s_xsd[3];
+        if (threadIdx.x == 0) {
+            for (int v = 0; v < 6; v++) s_xd[v] = DS(xe[v]);
+            for (int c = 0; c < 3; c++) s_xsd[c] = reinterpret_cast<const DS *>(A.x64[c]);
         }
-    __syncthreads();
-    mg_sweep3z<double, true, true>(
-        P.nx, P.ny, P.nz, mg_zchunk(P.nx, P.ny, P.nz, nbk), A.lam, A.mu, bid, nbk, smem, xe, 3, s_xs,
-        [&](const double *raw, int h, int, int, int, double (&v)[3]) {
+        __syncthreads();
+        mg_sweep3z<DS, true, true>(
+            P.nx, P.ny, P.nz, mg_zchunk(P.nx, P.ny, P.nz, nbk), A.lam, A.mu, bid, nbk, reinterpret_cast<DS *>(smem),
+            s_xd, 3, s_xsd,
+            [&](const DS *raw, int h, int, int, int, DS (&v)[3]) {
 #pragma unroll
-            for (int c = 0; c < 3; c++) v[c] = raw[c * MGZ_NP + h];
-        },
-        [&](int n, const double (&)[3], const double (&q)[3]) { node(n, q); },
-        [&](const double *c) {
+                for (int c = 0; c < 3; c++) {
+                    double x;
+                    memcpy(&x, raw + c * MGZ_NP + h, sizeof(double));
+                    v[c] = DS(x);
+                }
+            },
+            [&](int n, const DS (&)[3], const DS (&q)[3]) {
+                const double qd[3] = {q[0].value(), q[1].value(), q[2].value()};
+                node(n, qd);
+            },
+            [&](const DS *c) {
 #pragma unroll
-            for (int v = 0; v < 6; v++) acc[10 + v].add(c[v]);
-        },
-        [](int) {});
+                for (int v = 0; v < 6; v++) acc[10 + v].add(c[v].value());
+            },
+            [](int) {});
+    } else {
+        // x: the solution itself (FP64 method)
+        __shared__ const double *s_xs[3];
+        if (threadIdx.x == 0)
+            for (int c = 0; c < 3; c++) s_xs[c] = refine ? A.x64[c] : reinterpret_cast<const double *>(A.x[c]);
+        __syncthreads();
+        mg_sweep3z<double, true, true>(
+            P.nx, P.ny, P.nz, mg_zchunk(P.nx, P.ny, P.nz, nbk), A.lam, A.mu, bid, nbk, smem, xe, 3, s_xs,
+            [&](const double *raw, int h, int, int, int, double (&v)[3]) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) v[c] = raw[c * MGZ_NP + h];
+            },
+            [&](int n, const double (&)[3], const double (&q)[3]) { node(n, q); },
+            [&](const double *c) {
+#pragma unroll
+                for (int v = 0; v < 6; v++) acc[10 + v].add(c[v]);
+            },
+            [](int) {});
+    }
 }
 
 // Set-up of the 3D hierarchy at the start of a solve (grid levels, a barrier
