@@ -387,6 +387,42 @@ __device__ void mg_coarsen3(const MGLevel<T> &F, const MGLevel<T> &C, long long 
     }
 }
 
+// b = sum over the 8 cells around node n of Bbar^T sig* in double-single
+// arithmetic (the unit cell's Bbar entries are +-1/4, so each product with an
+// FP32 sig* is exact in FP32), the Jacobi diagonal (FP32: it only scales the
+// preconditioner), and the own cell's sig*, lam, mu; FP32 storage.
+__device__ __forceinline__ void node_rhs_ds3(const Params &P, long long n, const float *lam, const float *mu,
+                                             const float *const *sig, double (&b)[3], double &dgn, double (&so)[6],
+                                             double &lo, double &mo)
+{
+    int i, j, k;
+    cell_coords<3>(P, n, i, j, k);
+    DS bs[3] = {DS(0), DS(0), DS(0)};
+    float dg = 0.f;
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+        const long long c = lin<3>(P, i - (a & 1), j - ((a >> 1) & 1), k - ((a >> 2) & 1));
+        const float l = lam[c], m = mu[c];
+        dg += l * KdL<float, 3>() + m * KdM<float, 3>();
+        float sv[6];
+#pragma unroll
+        for (int v = 0; v < 6; v++) sv[v] = sig[v][c];
+        const float bx = Bb<float, 3>(a, 0), by = Bb<float, 3>(a, 1), bz = Bb<float, 3>(a, 2);
+        bs[0] += (DS(bx * sv[0]) + DS(by * sv[5])) + DS(bz * sv[4]);
+        bs[1] += (DS(by * sv[1]) + DS(bx * sv[5])) + DS(bz * sv[3]);
+        bs[2] += (DS(bz * sv[2]) + DS(by * sv[3])) + DS(bx * sv[4]);
+        if (a == 0) {
+#pragma unroll
+            for (int v = 0; v < 6; v++) so[v] = sv[v];
+            lo = l;
+            mo = m;
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; d++) b[d] = bs[d].value();
+    dgn = dg;
+}
+
 // The set-up sweep of one CG pass in 3D, on the z-marching sweep in FP64
 // (cell stress and hourglass forces once per cell, corner forces gathered per
 // node): b, the Jacobi diagonal, r = b - A x and the sums of the mean-strain
@@ -408,9 +444,14 @@ __device__ void setup_march3(const PCGArgs<T, 3> &A, bool use_x, bool refine, bo
 #pragma unroll
             for (int c = 0; c < 3; c++) b[c] = __ldcg(A.b64[c] + n);
         } else {
-            double unused[3], so[6], unused6[6], dgn, lo, mo;
-            node_setup<T, double, double, 3>(P, n, A.lam, A.mu, A.sig, A.x64, xe, false, b, unused, dgn, so, unused6,
-                                             lo, mo);
+            double so[6], dgn, lo, mo;
+            if constexpr (sizeof(T) == 4) {
+                node_rhs_ds3(P, n, A.lam, A.mu, A.sig, b, dgn, so, lo, mo);
+            } else {
+                double unused[3], unused6[6];
+                node_setup<T, double, double, 3>(P, n, A.lam, A.mu, A.sig, A.x64, xe, false, b, unused, dgn, so,
+                                                 unused6, lo, mo);
+            }
             if (refine)
 #pragma unroll
                 for (int c = 0; c < 3; c++) A.b64[c][n] = b[c];
