@@ -53,9 +53,9 @@ MG_INIT_WORDS = {2: 28, 3: 40}
 # finest node and V-cycle (so that it scales with the launch's iterations);
 # None where the current kernel has not been captured.  porous256cube: the
 # first timed solve of `bench.py --only mixed --steps 1 --warmup 4` (44
-# V-cycles), 139.31 GB read + 86.03 GB written = 305.3 B per node and V-cycle
+# V-cycles), 139.35 GB read + 85.84 GB written = 305.1 B per node and V-cycle
 # (profiles/launches_porous256_mixed.md).
-PCG_TRAFFIC_PER_NODE_ITER = {"porous256cube": 305.26}
+PCG_TRAFFIC_PER_NODE_ITER = {"porous256cube": 305.05}
 # Algorithmic bytes per cell of the fused explicit update (k_fusedz): theta,
 # phi_g, x_O, x_H, x_H2O, tr eps_e, |dev eps_e|^2, mobility read, the 1-byte
 # supply mask read, theta, x_O, x_H, x_H2O written.
