@@ -310,7 +310,30 @@ int pf_fs_return_map(int n, const double *F, double *FP, double *epsP, const dou
  * rate in place of the small-strain coupling. */
 int pf_fs_elastic_force(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
                         const double *u, const double *Fbar, const double *FP, double *force);
+
+/* The same force as a small-strain coupling scalar: the solid phases share
+ * their moduli, so d psi / d theta = -Omega (1 - h(phi_g)) h'(theta)
+ * d psi / d d_T, and the field update's elastic term
+ * -3 eig0 (1 - h(phi_g)) h'(theta) K_mix tr eps_e equals it for
+ *   trE = Omega (d psi / d d_T) / (3 eig0 K_mix),
+ *   K_mix = (1 - h(phi_g)) K_s + h(phi_g) K_g
+ * (0 where K_mix = 0).  trE: out, host, N; hand it to pf_set_coupling (with
+ * devE2 = NULL) on a mechanics = 0 handle to step the fields with the
+ * finite-strain force.  PF_EINVAL also when cfg->p.eig0 == 0. */
+int pf_fs_coupling(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
+                   const double *u, const double *Fbar, const double *FP, double *trE);
 const char *pf_fs_last_error(void);
+
+/* The coupling scalars of the field update (the elastic part of the order
+ * parameter's driving force, Sec. 2.4 with the small-strain energy of
+ * Sec. 2.2: tr eps_e and |dev eps_e|^2 per cell) supplied by the caller, for
+ * handles created with mechanics = 0, whose steps then run the field update
+ * alone with these values: for example the equivalent coupling of another
+ * mechanics model (pf_fs_coupling).  trE, devE2: N values each, FP64, on the
+ * host or the device (where); NULL sets zero.  They stay until the next call
+ * or pf_set_fields (which zeroes them).  Blocking.  Returns PF_EINVAL
+ * (batch handle, where), PF_ESTATE (mechanics on, no fields), PF_ECUDA. */
+int pf_set_coupling(pf_handle *h, const double *trE, const double *devE2, int where);
 
 /* Copy the current state (the fields of Sec. 2.4 and the mechanical state)
  * out into caller arrays (FP64); NULL members are skipped.  sigma is the

@@ -20,7 +20,7 @@ from .native import (PF_DEVICE, PF_FP64, PF_HOST, PF_MIXED, PF_OK, PF_PC_AUTO, P
                      PF_WS_EXTRAP, PF_WS_EXTRAP2, PF_WS_LEARNED, PF_WS_PREV, PF_WS_ZERO,
                      STATUS_NAMES, pf_config, pf_diag, pf_fields, pf_params)
 
-__all__ = ["Simulation", "Batch", "PFError", "make_config", "native"]
+__all__ = ["Simulation", "FiniteStrainSimulation", "Batch", "PFError", "make_config", "native"]
 
 PARAM_NAMES = [f[0] for f in pf_params._fields_]
 
@@ -210,6 +210,11 @@ class Simulation:
     def dt(self):
         return self.diagnostics()["dt"]
 
+    def set_coupling(self, trE, devE2=None, where="host"):
+        """Coupling scalars of a mechanics = 0 handle's field update
+        (pf_set_coupling); None: zero."""
+        self._check(native.pf_set_coupling(self.h, trE, devE2, PF_HOST if where == "host" else PF_DEVICE))
+
     def profile(self, on=True):
         self._check(native.pf_profile_enable(self.h, on))
 
@@ -246,6 +251,66 @@ class Simulation:
 
     def __exit__(self, *a):
         self.close()
+
+
+class FiniteStrainSimulation:
+    """The explicit step coupled to finite-strain mechanics (Sec. 2.2 neo-Hooke
+    mixture with the transformation stretch, Sec. 2.3/2.4 multiplicative J2
+    flow).  Each step: the staggered finite-strain mechanics step at the
+    current order parameter (pf_finite_strain_step, F_P updated in place),
+    its elastic force on the order parameter as the equivalent small-strain
+    coupling scalar (pf_fs_coupling), then one field update of a
+    mechanics = 0 handle with that coupling (pf_set_coupling, pf_step):
+    transport, reaction, chemical and double-well forces, the supply-cell
+    reset.  FP64; the equilibrium is solved from zero over `nload` load steps
+    every step."""
+
+    def __init__(self, shape, prm, omega, prestress=0.0, pbar=None, nload=4, newton_tol=1e-11, cg_rtol=1e-12):
+        self.shape = tuple(shape)
+        self.N = int(np.prod(self.shape))
+        self.sim = Simulation(self.shape, dict(prm, mechanics=0), precision="fp64")
+        self.cfg = make_config(self.shape, dict(prm, prestress=prestress))
+        if self.cfg.p.eig0 == 0.0:
+            raise ValueError("the coupling needs a nonzero eig0 (any value: it cancels)")
+        self.omega = float(omega)
+        self.pbar = pbar
+        self.opts = native.pf_fs_opts(nload=int(nload), newton_maxit=40, newton_tol=float(newton_tol),
+                                      cg_maxit=20000, cg_rtol=float(cg_rtol))
+        self.FP = np.tile(np.eye(3), (self.N, 1, 1))
+        self.epsP = np.zeros(self.N)
+        self.u = None
+        self.Fbar = None
+        self.stats = None
+
+    def _fs(self, rc):
+        if rc != PF_OK:
+            raise PFError(rc, native.lib().pf_fs_last_error().decode())
+
+    def set_fields(self, fields):
+        self.sim.set_fields(fields)
+        self.FP[:] = np.eye(3)
+        self.epsP[:] = 0.0
+
+    def step(self, n=1):
+        for _ in range(int(n)):
+            g = self.sim.get_fields(keys=("theta", "phig"))
+            th, pg = g["theta"].ravel(), g["phig"].ravel()
+            rc, self.u, self.Fbar, self.stats = native.pf_finite_strain_step(
+                self.cfg, th, pg, self.omega, self.pbar, self.opts, self.FP, self.epsP)
+            self._fs(rc)
+            rc, tE = native.pf_fs_coupling(self.cfg, th, pg, self.omega, self.u, self.Fbar, self.FP)
+            self._fs(rc)
+            self.sim.set_coupling(tE)
+            self.sim.step(1)
+
+    def get_fields(self, keys=FIELD_KEYS):
+        return self.sim.get_fields(keys=keys)
+
+    def diagnostics(self):
+        return self.sim.diagnostics()
+
+    def close(self):
+        self.sim.close()
 
 
 class Batch:

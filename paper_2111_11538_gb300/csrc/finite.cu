@@ -572,8 +572,16 @@ __global__ void k_fs_return_points(int n, const double *F, double *FP, double *e
 // deformation of the state z) and plastic deformation: the elastic part of
 // the order parameter's driving force (the derivative through W_f in d_T and
 // through the mixture moduli), in forward mode along theta
+//
+// mode 1: instead, the small-strain coupling scalar tr eps_e that gives the
+// marching update the same force.  K and G do not depend on theta (the solid
+// phases share K_s, G_s), so d psi / d theta = -Omega (1 - h(phi_g)) h'(theta)
+// d psi / d d_T, and the update's elastic term -3 eig0 (1 - h(phi_g))
+// h'(theta) K_mix tr eps_e equals it for tr eps_e = Omega (d psi / d d_T) /
+// (3 eig0 K_mix), K_mix = (1 - h(phi_g)) K_s + h(phi_g) K_g: the derivative is
+// taken along d_T.
 __global__ void k_fs_force(FSArgs A, const double *z, const double *theta, const double *phig, double Ks, double Gs,
-                           double Kg, double Gg, double *force)
+                           double Kg, double Gg, double *force, int mode, double eig0)
 {
     const int d = A.d, na = 1 << d;
     const long long N = A.N;
@@ -594,12 +602,14 @@ __global__ void k_fs_force(FSArgs A, const double *z, const double *theta, const
             F[2] = F[5] = F[6] = F[7] = 0.0;
             F[8] = 1.0;
         }
-        const FD th(theta[c], 1.0);
+        const FD th(theta[c], mode == 0 ? 1.0 : 0.0);
         const double hg = phig[c] * phig[c] * phig[c] * (phig[c] * (6.0 * phig[c] - 15.0) + 10.0);
         const FD ht = th * th * th * (th * (FD(6.0) * th - FD(15.0)) + FD(10.0));
         const FD wf = FD(1.0 - hg) * ht, ww = FD(1.0 - hg) * (FD(1.0) - ht);
         const FD K = (wf + ww) * FD(Ks) + FD(hg * Kg), G = (wf + ww) * FD(Gs) + FD(hg * Gg);
-        const FD dT = FD(1.0) - wf * FD(A.omega), s = fd_pow(dT, -1.0 / 3.0);
+        FD dT = FD(1.0) - wf * FD(A.omega);
+        if (mode == 1) dT.d = 1.0;
+        const FD s = fd_pow(dT, -1.0 / 3.0);
         const double *Fi = A.FPinv ? A.FPinv + c * 9 : nullptr;
         FD Fe[9];
         for (int i = 0; i < 3; i++)
@@ -613,7 +623,10 @@ __global__ void k_fs_force(FSArgs A, const double *z, const double *theta, const
         for (int q = 0; q < 9; q++) I1 = I1 + Fe[q] * Fe[q];
         const FD psi = dT * (FD(0.25) * K * (J * J - FD(1.0) - FD(2.0) * fd_log(J)) +
                              FD(0.5) * G * (fd_pow(J, -2.0 / 3.0) * I1 - FD(3.0)));
-        force[c] = psi.d;
+        const double Kmix = (1.0 - hg) * Ks + hg * Kg;
+        // Kmix == 0 only in a pure gas cell with a zero gas modulus, where the
+        // solid factor (1 - h(phi_g)) of the force vanishes: no coupling.
+        force[c] = mode == 0 ? psi.d : (Kmix != 0.0 ? A.omega * psi.d / (3.0 * eig0 * Kmix) : 0.0);
     }
 }
 
@@ -691,6 +704,9 @@ int fs_fail(int code, const char *msg)
 // the equilibrium with the plastic deformation FP (N x 9, or null: identity)
 // and, with cfg->plasticity, FP and epsP (N) updated by one return map per
 // cell after it
+int fs_force(const pf_config *cfg, const double *theta, const double *phi_g, double omega, const double *u,
+             const double *Fbar, const double *FP, double *force, int mode);
+
 int fs_run(const pf_config *cfg, const double *theta, const double *phi_g, double omega, const double *pbar,
            const pf_fs_opts *opts, double *u, double *Fbar, double *FP, double *epsP, pf_fs_stats *stats)
 {
@@ -873,8 +889,25 @@ int pf_finite_strain_step(const pf_config *cfg, const double *theta, const doubl
     return fs_run(cfg, theta, phi_g, omega, pbar, opts, u, Fbar, FP, epsP, stats);
 }
 
+int pf_fs_coupling(const pf_config *cfg, const double *theta, const double *phi_g, double omega, const double *u,
+                   const double *Fbar, const double *FP, double *trE)
+{
+    if (cfg && cfg->p.eig0 == 0.0) return fs_fail(PF_EINVAL, "eig0 must be nonzero");
+    return fs_force(cfg, theta, phi_g, omega, u, Fbar, FP, trE, 1);
+}
+
 int pf_fs_elastic_force(const pf_config *cfg, const double *theta, const double *phi_g, double omega,
                         const double *u, const double *Fbar, const double *FP, double *force)
+{
+    return fs_force(cfg, theta, phi_g, omega, u, Fbar, FP, force, 0);
+}
+
+}  // extern "C"
+
+namespace {
+
+int fs_force(const pf_config *cfg, const double *theta, const double *phi_g, double omega, const double *u,
+             const double *Fbar, const double *FP, double *force, int mode)
 {
     if (!cfg || !theta || !phi_g || !u || !Fbar || !force) return fs_fail(PF_EINVAL, "null argument");
     const int d = cfg->ndim;
@@ -914,12 +947,16 @@ int pf_fs_elastic_force(const pf_config *cfg, const double *theta, const double 
     }
     const double Ks = Es / (3 * (1 - 2 * nu)), Gs = Es / (2 * (1 + nu));
     const double Kg = Eg / (3 * (1 - 2 * nu)), Gg = Eg / (2 * (1 + nu));
-    k_fs_force<<<grid, 128>>>(A, dz, dth, dpg, Ks, Gs, Kg, Gg, dF);
+    k_fs_force<<<grid, 128>>>(A, dz, dth, dpg, Ks, Gs, Kg, Gg, dF, mode, cfg->p.eig0);
     cudaMemcpy(force, dF, sizeof(double) * N, cudaMemcpyDeviceToHost);
     const cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fs_fail(PF_ECUDA, cudaGetErrorString(e));
     return PF_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int pf_fs_return_map(int n, const double *F, double *FP, double *epsP, const double *K, const double *G,
                      const double *dT, double sigma_Y, double H)

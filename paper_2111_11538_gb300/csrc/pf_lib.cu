@@ -1686,6 +1686,38 @@ int pf_step_implicit(pf_handle *h, int nsteps, const pf_implicit_opts *opts, pf_
     return PF_OK;
 }
 
+int pf_set_coupling(pf_handle *h, const double *trE, const double *devE2, int where)
+{
+    if (!h) return PF_EINVAL;
+    if (h->is_batch) return h->fail(PF_EINVAL, "pf_set_coupling takes a single-grid handle");
+    if (where != PF_HOST && where != PF_DEVICE) return h->fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    if (h->cfg.mechanics)
+        return h->fail(PF_ESTATE, "pf_set_coupling needs mechanics = 0 (the step's own solve sets the coupling)");
+    if (!h->have_fields) return h->fail(PF_ESTATE, "pf_set_coupling before the fields were set");
+    const long long N = h->P.N;
+    const size_t nb = sizeof(double) * (size_t)N;
+    const int g = grid_for(h, N);
+    cudaStream_t s = h->own;
+    const double *src[2] = {trE, devE2};
+    void *dst[2] = {h->trE, h->devE2};
+    double *stage[2] = {h->stage, h->stage2};
+    for (int k = 0; k < 2; k++) {
+        if (!src[k]) {
+            PF_TRY(h->cuda(cudaMemsetAsync(dst[k], 0, h->tsz * (size_t)N, s), "coupling"));
+            continue;
+        }
+        const double *a = src[k];
+        if (where == PF_HOST) {
+            PF_TRY(h->cuda(cudaMemcpyAsync(stage[k], src[k], nb, cudaMemcpyHostToDevice, s), "coupling"));
+            a = stage[k];
+        }
+        if (h->fp64) k_in_scalar<double><<<g, 256, 0, s>>>(N, a, (double *)dst[k], 0.0);
+        else k_in_scalar<float><<<g, 256, 0, s>>>(N, a, (float *)dst[k], 0.0);
+    }
+    PF_TRY(h->cuda(cudaGetLastError(), "coupling"));
+    return h->cuda(cudaStreamSynchronize(s), "coupling");
+}
+
 int pf_get_fields(pf_handle *h, pf_fields *out, int where)
 {
     if (!h || !out) return PF_EINVAL;

@@ -100,8 +100,8 @@ class pf_unet_config(ctypes.Structure):
 
 # exported symbols, in the order of include/pf.h then include/pf_unet.h
 SYMBOLS = ["pf_create", "pf_set_fields", "pf_step", "pf_step_implicit", "pf_finite_strain_solve", "pf_finite_strain_step",
-           "pf_fs_return_map", "pf_fs_elastic_force", "pf_fs_last_error",
-           "pf_get_fields", "pf_get_diagnostics",
+           "pf_fs_return_map", "pf_fs_elastic_force", "pf_fs_coupling", "pf_fs_last_error",
+           "pf_set_coupling", "pf_get_fields", "pf_get_diagnostics",
            "pf_free_energy", "pf_dt_stable", "pf_profile_enable", "pf_profile_read",
            "pf_batch_create", "pf_batch_size", "pf_batch_set_fields", "pf_batch_get_fields",
            "pf_batch_get_diagnostics", "pf_attach_unet", "pf_selftest_wait",
@@ -185,6 +185,10 @@ def lib():
         l.pf_fs_return_map.restype = ctypes.c_int
         l.pf_fs_elastic_force.argtypes = [ctypes.POINTER(pf_config), _DP, _DP, ctypes.c_double, _DP, _DP, _DP, _DP]
         l.pf_fs_elastic_force.restype = ctypes.c_int
+        l.pf_fs_coupling.argtypes = [ctypes.POINTER(pf_config), _DP, _DP, ctypes.c_double, _DP, _DP, _DP, _DP]
+        l.pf_fs_coupling.restype = ctypes.c_int
+        l.pf_set_coupling.argtypes = [ctypes.c_void_p, _DP, _DP, ctypes.c_int]
+        l.pf_set_coupling.restype = ctypes.c_int
         l.pf_fs_last_error.argtypes = []
         l.pf_fs_last_error.restype = ctypes.c_char_p
         l.pf_get_fields.argtypes = [ctypes.c_void_p, ctypes.POINTER(pf_fields), ctypes.c_int]
@@ -320,16 +324,33 @@ def pf_fs_return_map(F, FP, epsP, K, G, dT, sigma_Y, H):
                                   ptr(arrs[3]), float(sigma_Y), float(H))
 
 
-def pf_fs_elastic_force(cfg, theta, phig, omega, u, Fbar, FP=None):
-    """(rc, force per cell); host arrays."""
+def _fs_cellwise(fn, cfg, theta, phig, omega, u, Fbar, FP):
     import numpy as np
     arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (theta, phig, u, Fbar)]
     fp = None if FP is None else np.ascontiguousarray(FP, dtype=np.float64).ravel()
     out = np.zeros(arrs[0].size)
     ptr = lambda a: a.ctypes.data_as(_DP)                                   # noqa: E731
-    rc = lib().pf_fs_elastic_force(ctypes.byref(cfg), ptr(arrs[0]), ptr(arrs[1]), float(omega), ptr(arrs[2]),
-                                   ptr(arrs[3]), ptr(fp) if fp is not None else None, ptr(out))
+    rc = fn(ctypes.byref(cfg), ptr(arrs[0]), ptr(arrs[1]), float(omega), ptr(arrs[2]),
+            ptr(arrs[3]), ptr(fp) if fp is not None else None, ptr(out))
     return rc, out
+
+
+def pf_fs_elastic_force(cfg, theta, phig, omega, u, Fbar, FP=None):
+    """(rc, d psi / d theta per cell); host arrays."""
+    return _fs_cellwise(lib().pf_fs_elastic_force, cfg, theta, phig, omega, u, Fbar, FP)
+
+
+def pf_fs_coupling(cfg, theta, phig, omega, u, Fbar, FP=None):
+    """(rc, the equivalent small-strain coupling scalar per cell); host arrays."""
+    return _fs_cellwise(lib().pf_fs_coupling, cfg, theta, phig, omega, u, Fbar, FP)
+
+
+def pf_set_coupling(h, trE, devE2=None, where=PF_HOST):
+    """Set a mechanics-free handle's coupling scalars from FP64 arrays (None: zero)."""
+    import numpy as np
+    keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (trE, devE2)]
+    ptr = [None if a is None else a.ctypes.data_as(_DP) for a in keep]
+    return lib().pf_set_coupling(h, ptr[0], ptr[1], where)
 
 
 def pf_get_fields(h, fields, where=PF_HOST):

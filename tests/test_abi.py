@@ -65,7 +65,19 @@ def test_null_handle_calls(lib):
     assert lib.pf_step(None, 1, None) == native.PF_EINVAL
     assert lib.pf_step_implicit(None, 1, None, None, None) == native.PF_EINVAL
     assert lib.pf_set_fields(None, None, 0) == native.PF_EINVAL
+    assert lib.pf_set_coupling(None, None, None, 0) == native.PF_EINVAL
     lib.pf_destroy(None)
+
+
+def test_fs_coupling_validates_before_touching_the_gpu(lib):
+    """eig0 = 0 leaves no equivalent coupling scalar; NULL arrays are
+    argument errors (both answered before any CUDA call)."""
+    import numpy as np
+    th = np.ones((4, 4))
+    cfg = make_config((4, 4), dict(workloads.params(), eig0=0.0))
+    rc, _ = native.pf_fs_coupling(cfg, th, th * 0, 0.1, np.zeros((16, 2)), np.eye(2))
+    assert rc == native.PF_EINVAL and b"eig0" in lib.pf_fs_last_error()
+    assert lib.pf_fs_coupling(None, None, None, 0.1, None, None, None, None) == native.PF_EINVAL
 
 
 def test_batch_create_validates_before_touching_the_gpu(lib):

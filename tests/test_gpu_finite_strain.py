@@ -175,3 +175,67 @@ def test_elastic_driving_force_matches_oracle(fs):
     assert rc == native.PF_OK, native.lib().pf_fs_last_error()
     assert np.abs(g - ref).max() < 1e-7 * np.abs(ref).max(), (np.abs(g - ref).max(), np.abs(ref).max())
     assert np.abs(ref).max() > 1e-4
+
+
+def test_coupled_finite_strain_steps_match_oracle(fs):
+    """Two explicit steps coupled to elasto-plastic finite-strain mechanics
+    (FiniteStrainSimulation) against finite_strain.CoupledSim on a core-shell
+    with gas and supply cells.  The oracle adds -(L/2) mob d psi/d theta
+    (central differences, step 1e-6) to theta's rate; the library runs the
+    mechanics-free field update with the equivalent coupling scalar
+    (pf_fs_coupling, exact derivative along d_T).  The two forces differ by
+    the difference quotient's error, ~1e-8 of the force, so each field's
+    change over the steps agrees to 1e-6 of its size."""
+    from paper_2111_11538_gb300 import FiniteStrainSimulation
+    f = inputs.core_shell((8, 8), 2.5, 1.0, delta=1.0)
+    prm = workloads.params(plasticity=1, sigma_Y=0.002, H_hard=0.01)
+    ref = fs.CoupledSim(f, prm, 0.2, nload=2)
+    sim = FiniteStrainSimulation((8, 8), prm, 0.2, nload=2)
+    sim.set_fields(f)
+    keys = ("theta", "xO", "xH", "xW")
+    f0 = {k: ref.sim.f[k].copy() for k in keys}
+    for step in range(2):
+        ref.step(1)
+        sim.step(1)
+        g = sim.get_fields(keys=keys)
+        for k in keys:
+            ch = np.abs(ref.sim.f[k] - f0[k]).max()
+            assert np.abs(g[k] - ref.sim.f[k]).max() <= 1e-6 * ch + 1e-14, (step, k, np.abs(g[k] - ref.sim.f[k]).max(), ch)
+        assert np.abs(sim.FP - ref.pr.FP).max() < 1e-9, (step, np.abs(sim.FP - ref.pr.FP).max())
+        assert np.abs(sim.epsP - ref.pr.epsP).max() < 1e-9
+    assert ref.pr.epsP.max() > 0.0
+    d = sim.diagnostics()
+    assert abs(d["removed_H2O"] - ref.sim.removedW) <= 1e-9 * max(ref.sim.removedW, 1e-12)
+    # the elastic force matters: the same steps without it move theta by more
+    # than the tolerance above
+    bare = fs.CoupledSim(f, prm, 0.0, nload=1)
+    bare.step(2)
+    assert np.abs(bare.sim.f["theta"] - ref.sim.f["theta"]).max() > 1e-3 * np.abs(ref.sim.f["theta"] - f0["theta"]).max()
+    sim.close()
+
+
+def test_coupling_scalar_reproduces_the_elastic_force(fs):
+    """pf_fs_coupling against pf_fs_elastic_force: the field update's elastic
+    term -3 eig0 (1 - h(phi_g)) h'(theta) K_mix trE equals d psi / d theta."""
+    from oracle import split_phases
+    f = inputs.core_shell((8, 8), 2.5, 1.0, delta=1.0)
+    th, pg = split_phases(f["phi_f"], f["phi_w"])
+    prm = workloads.params(plasticity=1, sigma_Y=0.002, H_hard=0.01)
+    pr = fs.Problem(th, pg, prm, 0.2)
+    z = pr.mechanics_step(nload=2)
+    u, Fb = pr.unpack(z)
+    cfg = make_config(th.shape, prm)
+    rc, g = native.pf_fs_elastic_force(cfg, th, pg, 0.2, u, Fb, pr.FP)
+    assert rc == native.PF_OK
+    rc, tE = native.pf_fs_coupling(cfg, th, pg, 0.2, u, Fb, pr.FP)
+    assert rc == native.PF_OK, native.lib().pf_fs_last_error()
+    t, hg = th.ravel(), pg.ravel() ** 3 * (pg.ravel() * (6 * pg.ravel() - 15) + 10)
+    hp = 30 * t * t * (1 - t) ** 2
+    E, nu = prm["E_s"], prm["nu"]
+    Ks, Kg = E / (3 * (1 - 2 * nu)), E * prm["E_g_ratio"] / (3 * (1 - 2 * nu))
+    Kmix = (1 - hg) * Ks + hg * Kg
+    term = -3 * prm["eig0"] * (1 - hg) * hp * Kmix * tE
+    assert np.abs(term - g).max() < 1e-12 * np.abs(g).max(), (np.abs(term - g).max(), np.abs(g).max())
+    assert np.abs(g).max() > 1e-4
+    rc, _ = native.pf_fs_coupling(make_config(th.shape, dict(prm, eig0=0.0)), th, pg, 0.2, u, Fb, pr.FP)
+    assert rc == native.PF_EINVAL
