@@ -10,7 +10,7 @@ FP64 iterative refinement of the solve) gives ``value``; the plain FP64
 method is measured beside it on the same GPU and the same input.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload porous256cube|coreshell512|porous2048|batch64|stencil|implicit]
+                    [--workload porous256cube|coreshell512|porous2048|batch64|stencil|implicit|finite]
 
 Under torchrun (N > 1) every rank advances its own replica of the workload
 (the single-grid step does not shard; see the design notes) and ``value`` is
@@ -517,6 +517,58 @@ def backward_euler_line(n=256, steps=3, dt=0.05, explicit_steps=20):
                          "H": d["sum_H"] + 2 * d["sum_H2O"] + 2 * d["removed_H2O"] - d["supplied_H"]}}
 
 
+def finite_strain_line(n=64, omega=0.2, nload=2, only="both"):
+    """One staggered elasto-plastic finite-strain mechanics step
+    (pf_finite_strain_step: neo-Hooke mixture with the transformation
+    stretch, Newton-CG to max |residual| <= 1e-10, then the multiplicative J2
+    update per cell) on the n^3 core-shell with gas, with FP32 and with FP64
+    Hessian-vector products: wall time, Newton and CG counts, and the
+    product kernel's device time (CUDA events around each launch on its
+    stream, pf_fs_stats.hvp_ms).  The call allocates its own memory, so the
+    wall time includes that; the first call (untimed) loads the kernels."""
+    import time
+    import torch
+    from paper_2111_11538_gb300 import Simulation, inputs, make_config, native, workloads
+    shape = (n, n, n)
+    f = inputs.core_shell(shape, 0.3 * n, 0.15 * n, delta=1.0)
+    prm = workloads.params(plasticity=1, sigma_Y=0.002, H_hard=0.01)
+    sim = Simulation(shape, dict(prm, mechanics=0), precision="fp64")
+    sim.set_fields(f)
+    g = sim.get_fields(keys=("theta", "phig"))
+    sim.close()
+    th, pg = g["theta"].ravel(), g["phig"].ravel()
+    cfg = make_config(shape, prm)
+    N = th.size
+    out = {"workload": "finite-strain elasto-plastic step, core-shell %d^3 with gas (E_g/E_s = %.3g), Omega = %g, "
+                       "%d load steps, FP64 residual" % (n, prm["E_g_ratio"], omega, nload), "cells": N}
+    small = (8, 8, 8)
+    for name, prec in (("fp32_products", native.PF_MIXED), ("fp64_products", native.PF_FP64)):
+        if only != "both" and (prec == native.PF_MIXED) != (only == "mixed"):
+            continue
+        o = native.pf_fs_opts(nload=nload, newton_maxit=40, newton_tol=1e-10, cg_maxit=100000, cg_rtol=1e-10,
+                              precision=prec)
+        FP = np.tile(np.eye(3), (int(np.prod(small)), 1, 1))
+        native.pf_finite_strain_step(make_config(small, prm), np.full(small, 0.5), np.zeros(small), omega, None, o,
+                                     FP, np.zeros(int(np.prod(small))))
+        FP = np.tile(np.eye(3), (N, 1, 1))
+        ep = np.zeros(N)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, u, Fb, st = native.pf_finite_strain_step(cfg, th, pg, omega, None, o, FP, ep)
+        t = time.perf_counter() - t0
+        out[name] = {"rc": rc, "s_per_step": t, "newton_iters": st.newton_iters, "cg_iters": st.cg_iters,
+                     "residual": st.residual, "hvp_launches": st.hvp_launches,
+                     "hvp_ms_per_launch": st.hvp_ms / max(st.hvp_launches, 1),
+                     "hvp_share_of_wall": st.hvp_ms / 1e3 / t,
+                     "cell_products_per_s": N * st.hvp_launches / t, "plastic_cells": int((ep > 0).sum()),
+                     "max_u": float(np.abs(u).max())}
+    if only == "both":
+        a, b = out["fp32_products"], out["fp64_products"]
+        out["speedup_fp32_products"] = b["s_per_step"] / a["s_per_step"]
+        out["hvp_speedup_per_launch"] = b["hvp_ms_per_launch"] / max(a["hvp_ms_per_launch"], 1e-12)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -529,8 +581,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads' keys")
     ap.add_argument("--workload", default="porous256cube",
                     help="porous256cube (default, the headline); coreshell512, porous2048, coreshell64, "
-                         "batch64, stencil or implicit (backward-Euler steps at the paper's "
-                         "diffusivities) print a short line")
+                         "batch64, stencil, implicit (backward-Euler steps at the paper's "
+                         "diffusivities) or finite (a finite-strain elasto-plastic step, 64^3) print a "
+                         "short line")
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"],
                     help="profiling aid: run one method only and print a short line")
     ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "mg"],
@@ -547,7 +600,7 @@ def main():
     PRECOND = args.precond
     WARM = args.warm_start
     if args.shape:
-        if args.only == "both":
+        if args.only == "both" and args.workload != "finite":
             ap.error("--shape needs --only (the headline line is measured on the workload's own grid)")
         SHAPE = tuple(int(v) for v in args.shape.split(","))
     if args.warmup < 3:
@@ -596,6 +649,9 @@ def main():
         return
     if WORKLOAD == "implicit":
         print(json.dumps(backward_euler_line()))
+        return
+    if WORKLOAD == "finite":
+        print(json.dumps(finite_strain_line(n=SHAPE[0] if SHAPE else 64, only=args.only)))
         return
     if WORKLOAD == "batch64":
         meth = "mixed" if args.only == "both" else args.only

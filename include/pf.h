@@ -250,8 +250,10 @@ int pf_step_implicit(pf_handle *h, int nsteps, const pf_implicit_opts *opts, pf_
  * prescribed (pbar, d x d row-major; NULL: -cfg->p.prestress I); u = 0 at
  * node 0.  Newton's method over opts->nload equal steps of omega, each
  * Newton system solved by conjugate gradients on the energy's Hessian
- * (products evaluated in forward mode) with the small-strain diagonal as
- * preconditioner; stops when max |residual| <= opts->newton_tol.
+ * (products evaluated in forward mode, in FP64 or FP32 by opts->precision;
+ * the CG scalars stay on the device and the host reads them every 16
+ * iterations) with the small-strain diagonal as preconditioner; stops when
+ * max |residual| (FP64) <= opts->newton_tol.
  *   theta, phi_g : host arrays of N cells (cell-major, x fastest)
  *   u            : out, host, N * ndim (u[n * ndim + c], node n = lower
  *                  corner of cell n)
@@ -266,12 +268,19 @@ typedef struct {
     double newton_tol;  /* max |residual| at convergence (> 0)           */
     int cg_maxit;       /* CG iterations per Newton system (>= 1)        */
     double cg_rtol;     /* CG relative residual per Newton system (0, 1) */
+    int precision;      /* PF_FP64: Hessian-vector products in FP64;
+                           PF_MIXED: in FP32 (the residual stays FP64, so
+                           the solution is the same; CG then stops at
+                           max(cg_rtol, 1e-6), an inexact Newton step)     */
 } pf_fs_opts;
 
 typedef struct {
     int newton_iters;   /* over all load steps                           */
     long long cg_iters; /* over all Newton systems                       */
     double residual;    /* max |residual| at the end                     */
+    double hvp_ms;      /* device time of the Hessian-vector product
+                           kernel (CUDA events around each launch)       */
+    long long hvp_launches; /* its launches that did work              */
 } pf_fs_stats;
 
 int pf_finite_strain_solve(const pf_config *cfg, const double *theta, const double *phi_g, double omega,

@@ -262,10 +262,12 @@ class FiniteStrainSimulation:
     coupling scalar (pf_fs_coupling), then one field update of a
     mechanics = 0 handle with that coupling (pf_set_coupling, pf_step):
     transport, reaction, chemical and double-well forces, the supply-cell
-    reset.  FP64; the equilibrium is solved from zero over `nload` load steps
-    every step."""
+    reset.  The field update and the mechanics' residual are FP64; the
+    Hessian-vector products FP32 (precision="mixed") or FP64.  The
+    equilibrium is solved from zero over `nload` load steps every step."""
 
-    def __init__(self, shape, prm, omega, prestress=0.0, pbar=None, nload=4, newton_tol=1e-11, cg_rtol=1e-12):
+    def __init__(self, shape, prm, omega, prestress=0.0, pbar=None, nload=4, newton_tol=1e-13, cg_rtol=1e-12,
+                 precision="mixed"):
         self.shape = tuple(shape)
         self.N = int(np.prod(self.shape))
         self.sim = Simulation(self.shape, dict(prm, mechanics=0), precision="fp64")
@@ -275,7 +277,8 @@ class FiniteStrainSimulation:
         self.omega = float(omega)
         self.pbar = pbar
         self.opts = native.pf_fs_opts(nload=int(nload), newton_maxit=40, newton_tol=float(newton_tol),
-                                      cg_maxit=20000, cg_rtol=float(cg_rtol))
+                                      cg_maxit=20000, cg_rtol=float(cg_rtol),
+                                      precision=PF_MIXED if precision == "mixed" else PF_FP64)
         self.FP = np.tile(np.eye(3), (self.N, 1, 1))
         self.epsP = np.zeros(self.N)
         self.u = None

@@ -72,6 +72,34 @@ __device__ __forceinline__ FD fd_sqrt(FD a)
     return FD(q, 0.5 * a.d / q);
 }
 
+// The same pair in FP32, for the Hessian-vector products of the mixed
+// method (GB300 runs FP32 at many times its FP64 rate)
+struct FDf {
+    float v, d;
+    __host__ __device__ FDf() {}
+    __host__ __device__ FDf(double a) : v((float)a), d(0.0f) {}
+    __host__ __device__ FDf(double a, double b) : v((float)a), d((float)b) {}
+    __host__ __device__ FDf(float a) : v(a), d(0.0f) {}
+    __host__ __device__ FDf(float a, float b) : v(a), d(b) {}
+};
+__device__ __forceinline__ FDf operator+(FDf a, FDf b) { return FDf(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ FDf operator-(FDf a, FDf b) { return FDf(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ FDf operator*(FDf a, FDf b) { return FDf(a.v * b.v, fmaf(a.d, b.v, a.v * b.d)); }
+__device__ __forceinline__ FDf operator/(FDf a, FDf b)
+{
+    const float q = a.v / b.v;
+    return FDf(q, (a.d - q * b.d) / b.v);
+}
+__device__ __forceinline__ FDf fd_pow(FDf a, double p)
+{
+    const float q = powf(a.v, (float)p);
+    return FDf(q, (float)p * q / a.v * a.d);
+}
+
+// the plain real type of each scalar kind
+template <typename S> struct RealOf { typedef double type; };
+template <> struct RealOf<FDf> { typedef float type; };
+
 struct FSArgs {
     int d, nx, ny, nz;
     long long N;
@@ -80,19 +108,39 @@ struct FSArgs {
     double omega;                // transformation of this load step
 };
 
+// Gauss abscissae 1/2 -+ 1/(2 sqrt 3) of the unit interval
+constexpr double FS_GA = 0.5 - 0.5 / 1.7320508075688772935, FS_GB = 0.5 + 0.5 / 1.7320508075688772935;
+
 // local shape-function derivative dN/dx_k of corner a at Gauss point g
-// (bit l of a: corner offset along axis l; bit l of g: Gauss abscissa
-// 1/2 +- 1/(2 sqrt 3) along axis l)
-__device__ __forceinline__ double dshape(int d, int g, int a, int k)
+// (bit l of a: corner offset along axis l; bit l of g: Gauss abscissa FS_GA
+// or FS_GB along axis l), the dimension fixed at compile time: with g, a, k
+// from unrolled loops every value is a constant
+template <int D, typename R>
+__device__ __forceinline__ R dshape_c(int g, int a, int k)
 {
-    const double ga = 0.5 - 0.5 / sqrt(3.0), gb = 0.5 + 0.5 / sqrt(3.0);
-    double v = 1.0;
-    for (int l = 0; l < d; l++) {
+    R v = R(1.0);
+#pragma unroll
+    for (int l = 0; l < D; l++) {
         const int bit = (a >> l) & 1;
-        const double xi = ((g >> l) & 1) ? gb : ga;
-        v *= l == k ? (bit ? 1.0 : -1.0) : (bit ? xi : 1.0 - xi);
+        const R xi = ((g >> l) & 1) ? R(FS_GB) : R(FS_GA);
+        v *= l == k ? (bit ? R(1.0) : R(-1.0)) : (bit ? xi : R(1.0) - xi);
     }
     return v;
+}
+
+// the 2^D corner nodes of cell c (corner a: offsets bit l of a along axis
+// l), with 32-bit index arithmetic (the solver admits N < 2^31 cells)
+template <int D>
+__device__ __forceinline__ void fs_corners(const FSArgs &A, int c, int (&nd)[1 << D])
+{
+    const int nx = A.nx, ny = A.ny;
+    const int i = c % nx, r = c / nx;
+    const int j = r % ny, k = r / ny;
+    const int i1 = i + 1 == nx ? 0 : i + 1, j1 = j + 1 == ny ? 0 : j + 1;
+    const int k1 = D == 3 ? (k + 1 == A.nz ? 0 : k + 1) : 0;
+    const int row[4] = {nx * (j + ny * k), nx * (j1 + ny * k), nx * (j + ny * k1), nx * (j1 + ny * k1)};
+#pragma unroll
+    for (int a = 0; a < (1 << D); a++) nd[a] = ((a & 1) ? i1 : i) + row[(a >> 1) & 3];
 }
 
 __device__ __forceinline__ long long fs_node(const FSArgs &A, long long c, int a)
@@ -105,19 +153,33 @@ __device__ __forceinline__ long long fs_node(const FSArgs &A, long long c, int a
     return ii + (long long)A.nx * (jj + (long long)A.ny * kk);
 }
 
-// first Piola stress of cell c at deformation F (3 x 3, row-major)
+// The per-cell constants of the stress in the arithmetic type R, computed
+// once per load step (k_fs_pack): the mixture moduli, d_T = 1 - W_f omega,
+// s = d_T^(-1/3), d_T s, and the inverse plastic deformation.
+template <typename R>
+struct FSPack {
+    R K, G, dTs, s;
+    R Fi[9];
+};
+
+// first Piola stress at deformation F (3 x 3, row-major) of a cell with
+// constants pk (hasFi: F_P is not the identity)
 template <typename S>
-__device__ void fs_piola(const FSArgs &A, long long c, const S (&F)[9], S (&P)[9])
+__device__ __forceinline__ void fs_piola(const FSPack<typename RealOf<S>::type> &pk, bool hasFi, const S (&F)[9],
+                                         S (&P)[9])
 {
-    const double dT = 1.0 - A.Wf[c] * A.omega, s = pow(dT, -1.0 / 3.0);
-    const double K = A.K[c], G = A.G[c];
-    const double *Fi = A.FPinv ? A.FPinv + c * 9 : nullptr;
+    typedef typename RealOf<S>::type R;
+    const R s = pk.s, K = pk.K, G = pk.G;
     S Fe[9];
-    if (Fi) {
+    if (hasFi) {
+#pragma unroll
         for (int i = 0; i < 3; i++)
+#pragma unroll
             for (int j = 0; j < 3; j++)
-                Fe[3 * i + j] = S(s) * (F[3 * i] * S(Fi[j]) + F[3 * i + 1] * S(Fi[3 + j]) + F[3 * i + 2] * S(Fi[6 + j]));
+                Fe[3 * i + j] = S(s) * (F[3 * i] * S(pk.Fi[j]) + F[3 * i + 1] * S(pk.Fi[3 + j]) +
+                                        F[3 * i + 2] * S(pk.Fi[6 + j]));
     } else {
+#pragma unroll
         for (int q = 0; q < 9; q++) Fe[q] = S(s) * F[q];
     }
     // cofactor matrix: J F^-T
@@ -133,21 +195,26 @@ __device__ void fs_piola(const FSArgs &A, long long c, const S (&F)[9], S (&P)[9
     cof[8] = Fe[0] * Fe[4] - Fe[1] * Fe[3];
     const S J = Fe[0] * cof[0] + Fe[1] * cof[1] + Fe[2] * cof[2];
     S I1(0.0);
+#pragma unroll
     for (int q = 0; q < 9; q++) I1 = I1 + Fe[q] * Fe[q];
     // d phi / d F_E = K/2 (J^2 - 1) F_E^-T + G J^(-2/3) (F_E - I1/3 F_E^-T)
-    const S a1 = S(0.5 * K) * (J * J - S(1.0)) / J;          // times cof = J F^-T
+    const S a1 = S(R(0.5) * K) * (J * J - S(1.0)) / J;       // times cof = J F^-T
     const S jm = fd_pow(J, -2.0 / 3.0);
     const S a2 = S(G) * jm;
     const S a3 = a2 * I1 / (S(3.0) * J);
-    if (Fi) {
+    if (hasFi) {
         S D[9];
+#pragma unroll
         for (int q = 0; q < 9; q++) D[q] = a1 * cof[q] + a2 * Fe[q] - a3 * cof[q];
+#pragma unroll
         for (int i = 0; i < 3; i++)
+#pragma unroll
             for (int j = 0; j < 3; j++)
-                P[3 * i + j] = S(dT * s) * (D[3 * i] * S(Fi[3 * j]) + D[3 * i + 1] * S(Fi[3 * j + 1]) +
-                                            D[3 * i + 2] * S(Fi[3 * j + 2]));
+                P[3 * i + j] = S(pk.dTs) * (D[3 * i] * S(pk.Fi[3 * j]) + D[3 * i + 1] * S(pk.Fi[3 * j + 1]) +
+                                            D[3 * i + 2] * S(pk.Fi[3 * j + 2]));
     } else {
-        for (int q = 0; q < 9; q++) P[q] = S(dT * s) * (a1 * cof[q] + a2 * Fe[q] - a3 * cof[q]);
+#pragma unroll
+        for (int q = 0; q < 9; q++) P[q] = S(pk.dTs) * (a1 * cof[q] + a2 * Fe[q] - a3 * cof[q]);
     }
 }
 
@@ -322,125 +389,221 @@ __device__ int fs_return_map(const double (&F)[9], double (&FP)[9], double &epsP
     return 0;
 }
 
-// forces of cell c on its 2^d corners (f[a * d + i]) and its weighted sum of
-// the Gauss-point stresses (pm, d x d row-major), for the state (u, Fbar)
-// given by ld_u(node, comp) and fb (3 x 3 symmetric)
-template <typename S, class LU>
-__device__ void fs_cell(const FSArgs &A, long long c, LU &&ld_u, const S (&fb)[9], S (&f)[24], S (&pm)[9])
+// forces of cell c (constants pk) on its 2^d corners (f[a * d + i]) and
+// its weighted sum of the Gauss-point stresses (pm, d x d row-major), for
+// the state (u, Fbar) given by ld_u(node, comp) and fb (3 x 3 symmetric)
+template <int D, typename S, class LU>
+__device__ __forceinline__ void fs_cell(const FSArgs &A, long long c, const FSPack<typename RealOf<S>::type> &pk,
+                                        LU &&ld_u, const S (&fb)[9], S (&f)[24], S (&pm)[9])
 {
-    const int d = A.d, na = 1 << d;
-    const double w = 1.0 / na;
-    S ua[8][3];
+    const bool hasFi = A.FPinv != nullptr;
+    typedef typename RealOf<S>::type R;
+    constexpr int na = 1 << D;
+    constexpr double w = 1.0 / na;
+    int nodes[na];
+    fs_corners<D>(A, (int)c, nodes);
+    S ua[na][D];
+#pragma unroll
     for (int a = 0; a < na; a++) {
-        const long long n = fs_node(A, c, a);
-        for (int i = 0; i < d; i++) ua[a][i] = ld_u(n, i);
+#pragma unroll
+        for (int i = 0; i < D; i++) ua[a][i] = ld_u((long long)nodes[a], i);
     }
+#pragma unroll
     for (int q = 0; q < 24; q++) f[q] = S(0.0);
+#pragma unroll
     for (int q = 0; q < 9; q++) pm[q] = S(0.0);
+#pragma unroll
     for (int g = 0; g < na; g++) {
         S F[9];
+#pragma unroll
         for (int q = 0; q < 9; q++) F[q] = fb[q];
-        for (int i = 0; i < d; i++)
-            for (int k = 0; k < d; k++) {
+#pragma unroll
+        for (int i = 0; i < D; i++)
+#pragma unroll
+            for (int k = 0; k < D; k++) {
                 S t = F[3 * i + k];
-                for (int a = 0; a < na; a++) t = t + ua[a][i] * S(dshape(d, g, a, k));
+#pragma unroll
+                for (int a = 0; a < na; a++) t = t + ua[a][i] * S(dshape_c<D, R>(g, a, k));
                 F[3 * i + k] = t;
             }
-        if (d == 2) {
+        if (D == 2) {
             F[2] = F[5] = F[6] = F[7] = S(0.0);
             F[8] = S(1.0);
         }
         S P[9];
-        fs_piola(A, c, F, P);
+        fs_piola(pk, hasFi, F, P);
+#pragma unroll
         for (int a = 0; a < na; a++)
-            for (int i = 0; i < d; i++) {
-                S t = f[a * d + i];
-                for (int k = 0; k < d; k++) t = t + S(w) * P[3 * i + k] * S(dshape(d, g, a, k));
-                f[a * d + i] = t;
+#pragma unroll
+            for (int i = 0; i < D; i++) {
+                S t = f[a * D + i];
+#pragma unroll
+                for (int k = 0; k < D; k++) t = t + S(R(w) * dshape_c<D, R>(g, a, k)) * P[3 * i + k];
+                f[a * D + i] = t;
             }
-        for (int i = 0; i < d; i++)
-            for (int k = 0; k < d; k++) pm[3 * i + k] = pm[3 * i + k] + S(w) * P[3 * i + k];
+#pragma unroll
+        for (int i = 0; i < D; i++)
+#pragma unroll
+            for (int k = 0; k < D; k++) pm[3 * i + k] = pm[3 * i + k] + S(w) * P[3 * i + k];
     }
 }
+
+// Conjugate gradients keep every scalar on the device: the host launches
+// FS_CHUNK iterations at a time and reads this state once per chunk; after
+// convergence (done) or breakdown (stop) the remaining launches of the chunk
+// return at once.
+struct FSCG {
+    double rz;      // (r, M r)
+    double al;      // step along p
+    double beta;    // direction update
+    double tol;     // stop when |r| <= tol
+    int stop;       // (p, H p) <= 0: no positive curvature along p
+    int done;       // converged or at maxit
+    int iters, maxit;
+};
+__device__ __forceinline__ bool fs_cg_over(const FSCG *cg) { return cg && (cg->stop || cg->done); }
 
 // symmetric Fbar (3 x 3) from the m trailing entries of a vector
-__device__ __forceinline__ void fs_fbar(int d, const double *zf, double (&fb)[9])
+template <typename T, typename R>
+__device__ __forceinline__ void fs_fbar(int d, const T *zf, R (&fb)[9])
 {
-    for (int q = 0; q < 9; q++) fb[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; q++) fb[q] = R(0.0);
     if (d == 3) {
-        fb[0] = zf[0]; fb[4] = zf[1]; fb[8] = zf[2];
-        fb[5] = fb[7] = zf[3]; fb[2] = fb[6] = zf[4]; fb[1] = fb[3] = zf[5];
+        fb[0] = R(zf[0]); fb[4] = R(zf[1]); fb[8] = R(zf[2]);
+        fb[5] = fb[7] = R(zf[3]); fb[2] = fb[6] = R(zf[4]); fb[1] = fb[3] = R(zf[5]);
     } else {
-        fb[0] = zf[0]; fb[4] = zf[1]; fb[1] = fb[3] = zf[2];
+        fb[0] = R(zf[0]); fb[4] = R(zf[1]); fb[1] = fb[3] = R(zf[2]);
     }
 }
 
-// per cell: corner forces (value, or with v != nullptr the directional
-// derivative along v) into cf[c][a][i] and the stress sums into pc[c][9]
-__global__ void k_fs_cells(FSArgs A, const double *z, const double *v, double *cf, double *pc)
+// the per-cell constants of a load step (omega in A) in type R
+template <typename R>
+__global__ void k_fs_pack(FSArgs A, FSPack<R> *pk)
 {
-    const int d = A.d, na = 1 << d;
-    const long long N = A.N;
-    const double *zf = z + (size_t)d * N, *vf = v ? v + (size_t)d * N : nullptr;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        if (!v) {
-            double fb[9], f[24], pm[9];
-            fs_fbar(d, zf, fb);
-            fs_cell<double>(A, c, [&](long long n, int i) { return z[n * d + i]; }, fb, f, pm);
-            for (int q = 0; q < na * d; q++) cf[c * 24 + q] = f[q];
-            for (int q = 0; q < 9; q++) pc[c * 9 + q] = pm[q];
-        } else {
-            double fb0[9], fb1[9];
-            fs_fbar(d, zf, fb0);
-            fs_fbar(d, vf, fb1);
-            FD fb[9], f[24], pm[9];
-            for (int q = 0; q < 9; q++) fb[q] = FD(fb0[q], fb1[q]);
-            fs_cell<FD>(A, c, [&](long long n, int i) { return FD(z[n * d + i], v[n * d + i]); }, fb, f, pm);
-            for (int q = 0; q < na * d; q++) cf[c * 24 + q] = f[q].d;
-            for (int q = 0; q < 9; q++) pc[c * 9 + q] = pm[q].d;
-        }
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < A.N; c += (long long)gridDim.x * blockDim.x) {
+        const double dT = 1.0 - A.Wf[c] * A.omega, s = pow(dT, -1.0 / 3.0);
+        FSPack<R> p;
+        p.K = R(A.K[c]);
+        p.G = R(A.G[c]);
+        p.s = R(s);
+        p.dTs = R(dT * s);
+        for (int q = 0; q < 9; q++) p.Fi[q] = R(A.FPinv ? A.FPinv[c * 9 + q] : (q % 4 == 0 ? 1.0 : 0.0));
+        pk[c] = p;
     }
 }
 
-// nodal forces: each node sums the corner forces of its 2^d cells; node 0
-// is held (zero)
-__global__ void k_fs_gather(FSArgs A, const double *cf, double *out)
+// x32 = (float) x on [0, L)
+__global__ void k_fs_to32(long long L, const double *x, float *x32)
 {
-    const int d = A.d, na = 1 << d;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < A.N; n += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(n % A.nx);
-        const long long r = n / A.nx;
-        const int j = (int)(r % A.ny), k = (int)(r / A.ny);
-        double s[3] = {0.0, 0.0, 0.0};
-        for (int a = 0; a < na; a++) {
-            const int ci = (i - (a & 1) + A.nx) % A.nx, cj = (j - ((a >> 1) & 1) + A.ny) % A.ny;
-            const int ck = d == 3 ? (k - ((a >> 2) & 1) + A.nz) % A.nz : 0;
-            const long long c = ci + (long long)A.nx * (cj + (long long)A.ny * ck);
-            for (int q = 0; q < d; q++) s[q] += cf[c * 24 + a * d + q];
-        }
-        for (int q = 0; q < d; q++) out[n * d + q] = n == 0 ? 0.0 : s[q];
-    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L; i += (long long)gridDim.x * blockDim.x)
+        x32[i] = (float)x[i];
 }
 
-// block partial sums of the cells' stress sums (fixed order)
-__global__ void k_fs_psum(long long N, const double *pc, double *part)
+// block sums of nv values per thread (warp shuffles in the values' type,
+// then the warps in order in FP64), written by thread 0..nv-1 to
+// out[q * gridDim.x + blockIdx.x]; blockDim.x a multiple of 32, at most 1024
+template <int NV, typename T>
+__device__ __forceinline__ void fs_block_partials(T (&v)[NV], double *out)
 {
-    __shared__ double sh[9][8];
-    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
-        for (int q = 0; q < 9; q++) s[q] += pc[c * 9 + q];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int q = 0; q < 9; q++) {
-        double t = s[q];
+    __shared__ double sh[NV][32];
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        T t = v[q];
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) sh[q][wid] = t;
+        if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = (double)t;
     }
     __syncthreads();
-    if (threadIdx.x < 9) {
+    if (threadIdx.x < NV) {
         double t = 0.0;
         for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[threadIdx.x][k];
-        part[blockIdx.x * 9 + threadIdx.x] = t;
+        out[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = t;
     }
+}
+
+// per cell: corner forces of the state z into cf[c][a][i] (FP64, with the
+// cell constants pk) and the block partial stress sums into part9
+// (9 x gridDim.x): the residual
+template <int D>
+__global__ void k_fs_res(FSArgs A, const FSPack<double> *pk, const double *z, double *cf, double *part9)
+{
+    const long long N = A.N;
+    const double *zf = z + (size_t)D * N;
+    double fb[9], acc[9];
+    fs_fbar(D, zf, fb);
+#pragma unroll
+    for (int q = 0; q < 9; q++) acc[q] = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        double f[24], pm[9];
+        const FSPack<double> p = pk[c];
+        fs_cell<D, double>(A, c, p, [&](long long n, int i) { return z[n * D + i]; }, fb, f, pm);
+#pragma unroll
+        for (int q = 0; q < (1 << D) * D; q++) cf[c * 24 + q] = f[q];
+#pragma unroll
+        for (int q = 0; q < 9; q++) acc[q] += pm[q];
+    }
+    fs_block_partials<9>(acc, part9);
+}
+
+// the same, differentiated along v in forward mode: one Hessian-vector
+// product of the energy.  S = FD: FP64 (z, v the solver's vectors); S = FDf:
+// FP32 (z, v their FP32 copies, cf FP32)
+template <int D, typename S>
+__global__ void __launch_bounds__(128, 4)
+k_fs_hvp(FSArgs A, const FSPack<typename RealOf<S>::type> *pk, const typename RealOf<S>::type *z,
+         const typename RealOf<S>::type *v, typename RealOf<S>::type *cf, double *part9, const FSCG *cg)
+{
+    typedef typename RealOf<S>::type R;
+    if (fs_cg_over(cg)) return;
+    const long long N = A.N;
+    R fb0[9], fb1[9];
+    fs_fbar(D, z + (size_t)D * N, fb0);
+    fs_fbar(D, v + (size_t)D * N, fb1);
+    S fb[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) fb[q] = S(fb0[q], fb1[q]);
+    R acc[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) acc[q] = R(0.0);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        S f[24], pm[9];
+        const FSPack<R> p = pk[c];
+        fs_cell<D, S>(A, c, p, [&](long long n, int i) { return S(z[n * D + i], v[n * D + i]); }, fb, f, pm);
+#pragma unroll
+        for (int q = 0; q < (1 << D) * D; q++) cf[c * 24 + q] = f[q].d;
+#pragma unroll
+        for (int q = 0; q < 9; q++) acc[q] += pm[q].d;
+    }
+    fs_block_partials<9>(acc, part9);
+}
+
+// nodal forces: each node sums the corner forces of its 2^d cells (in the
+// corner forces' type); node 0 is held (zero).  With p given, also the block
+// partials of (p, out) over the displacement dofs into partdot.
+template <typename R>
+__global__ void k_fs_gather(FSArgs A, const R *cf, double *out, const double *p, double *partdot, const FSCG *cg)
+{
+    if (fs_cg_over(cg)) return;
+    const int d = A.d, na = 1 << d, nx = A.nx, ny = A.ny;
+    double dot[1] = {0.0};
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (int)A.N; n += gridDim.x * blockDim.x) {
+        const int i = n % nx, r = n / nx;
+        const int j = r % ny, k = r / ny;
+        const int i0 = i == 0 ? nx - 1 : i - 1, j0 = j == 0 ? ny - 1 : j - 1;
+        const int k0 = d == 3 ? (k == 0 ? A.nz - 1 : k - 1) : 0;
+        R s[3] = {R(0.0), R(0.0), R(0.0)};
+        for (int a = 0; a < na; a++) {
+            const int ci = (a & 1) ? i0 : i, cj = (a & 2) ? j0 : j, ck = (a & 4) ? k0 : k;
+            const size_t c = (size_t)ci + (size_t)nx * (cj + (size_t)ny * ck);
+            for (int q = 0; q < d; q++) s[q] += cf[c * 24 + a * d + q];
+        }
+        for (int q = 0; q < d; q++) {
+            const double o = n == 0 ? 0.0 : (double)s[q];
+            out[n * d + q] = o;
+            if (p) dot[0] = fma(p[n * d + q], o, dot[0]);
+        }
+    }
+    if (p) fs_block_partials<1>(dot, partdot);
 }
 
 // Jacobi diagonal of the displacement dofs from the small-strain operator
@@ -492,17 +655,164 @@ __global__ void k_fs_dot(long long L, const double *a, const double *b, double *
     }
 }
 
-// y = a x + b y on [0, L); z = x / dg elementwise with dg over [0, nd) and
-// 1 / dgf beyond (mode 1)
+// y = a x + b y on [0, L); the inverse Jacobi diagonal: 1 / dg over
+// [0, nd), 1 / dgf beyond
 __global__ void k_fs_axpby(long long L, double a, const double *x, double b, double *y)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L; i += (long long)gridDim.x * blockDim.x)
         y[i] = a * x[i] + b * y[i];
 }
-__global__ void k_fs_precond(long long L, long long nd, const double *x, const double *dg, double dgf, double *z)
+__global__ void k_fs_dginv(long long L, long long nd, const double *dg, double dgf, double *dginv)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L; i += (long long)gridDim.x * blockDim.x)
-        z[i] = i < nd ? x[i] / dg[i] : x[i] / dgf;
+        dginv[i] = 1.0 / (i < nd ? dg[i] : dgf);
+}
+
+// ---------------------------------------------------------------------------
+// The CG scalar kernels (one block of 256 threads; sums in a fixed order)
+// ---------------------------------------------------------------------------
+struct Mat9 {
+    double v[9];
+};
+
+// sums over the n partials of each of NV rows (row q at part + q * n) by
+// the block: thread t takes t, t + 256, ...; then fs_block_partials' tree
+template <int NV>
+__device__ __forceinline__ void fs_sum_rows(const double *part, int n, double (&tot)[NV])
+{
+    __shared__ double res[NV];
+    double v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; q++) v[q] = 0.0;
+    // the rows inside the loop over k: NV independent loads per step
+#pragma unroll 2
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double t[NV];
+#pragma unroll
+        for (int q = 0; q < NV; q++) t[q] = part[(size_t)q * n + k];
+#pragma unroll
+        for (int q = 0; q < NV; q++) v[q] += t[q];
+    }
+    __shared__ double sh[NV][8];
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        double t = v[q];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[threadIdx.x][k];
+        res[threadIdx.x] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; q++) tot[q] = res[q];
+}
+
+// the m mean-deformation rows from the summed stresses ps: the diagonal
+// entries, ps_ij + ps_ji off it
+__device__ __forceinline__ void fs_rows_of(int d, const double (&ps)[9], double (&rf)[6])
+{
+    const int ii[6] = {0, 1, 2, 1, 0, 0}, jj[6] = {0, 1, 2, 2, 2, 1};
+    const int i2[3] = {0, 1, 0}, j2[3] = {0, 1, 1};
+    const int m = d == 3 ? 6 : 3;
+    for (int k = 0; k < m; k++) {
+        const int i = d == 3 ? ii[k] : i2[k], j = d == 3 ? jj[k] : j2[k];
+        rf[k] = i == j ? ps[3 * i + i] : ps[3 * i + j] + ps[3 * j + i];
+    }
+}
+
+// the residual's mean-deformation rows: summed stresses minus N pbar
+__global__ void k_fs_rows(int d, int nb, const double *part9, Mat9 pbar, double Nc, double *outf)
+{
+    double ps[9];
+    fs_sum_rows<9>(part9, nb, ps);
+    if (threadIdx.x != 0) return;
+    for (int q = 0; q < 9; q++) ps[q] -= Nc * pbar.v[q];
+    double rf[6];
+    fs_rows_of(d, ps, rf);
+    for (int k = 0; k < (d == 3 ? 6 : 3); k++) outf[k] = rf[k];
+}
+
+// the product's mean-deformation rows into qf, then
+// al = rz / (p, H p) with (p, H p) = the gather's partials + the rows' part
+__global__ void k_fs_cg_alpha(int d, int nb, const double *part9, int ng, const double *partdot, const double *pf,
+                              double *qf, FSCG *cg)
+{
+    if (fs_cg_over(cg)) return;
+    double ps[9], pd[1];
+    fs_sum_rows<9>(part9, nb, ps);
+    fs_sum_rows<1>(partdot, ng, pd);
+    if (threadIdx.x != 0) return;
+    double rf[6];
+    fs_rows_of(d, ps, rf);
+    double pq = pd[0];
+    for (int k = 0; k < (d == 3 ? 6 : 3); k++) {
+        qf[k] = rf[k];
+        pq = fma(pf[k], rf[k], pq);
+    }
+    if (!(pq > 0.0)) {
+        cg->stop = 1;                 // no positive curvature along p
+        return;
+    }
+    cg->al = cg->rz / pq;
+}
+
+// dz += al p, r -= al q, s = M r (Jacobi: dginv the inverse diagonal);
+// block partials of (r, r) and (r, s) into part2 (2 x gridDim.x)
+__global__ void k_fs_cg_update(long long L, const double *dginv, const double *p, const double *q, double *dz,
+                               double *r, double *s, const FSCG *cg, double *part2)
+{
+    if (fs_cg_over(cg)) return;
+    const double al = cg->al;
+    double acc[2] = {0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L; i += (long long)gridDim.x * blockDim.x) {
+        dz[i] = fma(al, p[i], dz[i]);
+        const double ri = fma(-al, q[i], r[i]);
+        r[i] = ri;
+        const double si = ri * dginv[i];
+        s[i] = si;
+        acc[0] = fma(ri, ri, acc[0]);
+        acc[1] = fma(ri, si, acc[1]);
+    }
+    fs_block_partials<2>(acc, part2);
+}
+
+// |r| against the tolerance, then beta = (r, s)_new / (r, s)_old
+__global__ void k_fs_cg_beta(int nb, const double *part2, FSCG *cg)
+{
+    if (fs_cg_over(cg)) return;
+    double t[2];
+    fs_sum_rows<2>(part2, nb, t);
+    if (threadIdx.x != 0) return;
+    cg->iters++;
+    if (sqrt(t[0]) <= cg->tol || cg->iters >= cg->maxit) {
+        cg->done = 1;
+        return;
+    }
+    cg->beta = t[1] / cg->rz;
+    cg->rz = t[1];
+}
+
+// p = s + beta p (and its FP32 copy, if kept)
+__global__ void k_fs_cg_dir(long long L, const double *s, double *p, float *p32, const FSCG *cg)
+{
+    if (fs_cg_over(cg)) return;
+    const double b = cg->beta;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L; i += (long long)gridDim.x * blockDim.x) {
+        const double v = fma(b, p[i], s[i]);
+        p[i] = v;
+        if (p32) p32[i] = (float)v;
+    }
+}
+
+// z = x * dginv elementwise
+__global__ void k_fs_scale(long long L, const double *x, const double *dginv, double *z)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L; i += (long long)gridDim.x * blockDim.x)
+        z[i] = x[i] * dginv[i];
 }
 
 // per cell: the inverse of the plastic deformation (row-major 3 x 3)
@@ -631,6 +941,11 @@ __global__ void k_fs_force(FSArgs A, const double *z, const double *theta, const
 }
 
 constexpr int FS_NB = 128;     // blocks of the reductions
+constexpr int FS_CHUNK = 16;   // CG iterations launched between two host reads of the CG state
+// the mixed method's CG stops at a relative residual of at least this: its
+// FP32 products carry ~1e-7 relative rounding, so tighter solves buy no
+// better Newton steps (inexact Newton, the residual itself is FP64)
+constexpr double FS_MIXED_RTOL = 1e-5;
 
 struct FSSolver {
     FSArgs A;
@@ -638,21 +953,37 @@ struct FSSolver {
     int m;
     double pbar[9];
     double *z = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *s = nullptr, *dz = nullptr, *dg = nullptr;
-    double *cf = nullptr, *pc = nullptr, *part = nullptr, *K = nullptr, *G = nullptr, *Wf = nullptr;
-    double *th = nullptr, *pg = nullptr;
+    double *dginv = nullptr;             // inverse Jacobi diagonal over [0, L)
+    double *cf = nullptr;                // corner forces, N x 24 (FP32 in the mixed product)
+    double *part = nullptr;              // FS_NB partials of host-read dot products
+    double *part9 = nullptr, *partdot = nullptr;   // grid x 9 stress and grid (p, Hp) partials
+    double *part2 = nullptr;             // 2 x grid partials of (r, r), (r, s)
+    double *K = nullptr, *G = nullptr, *Wf = nullptr, *th = nullptr, *pg = nullptr;
+    FSPack<double> *pk64 = nullptr;      // cell constants of the load step
+    FSPack<float> *pk32 = nullptr;       // their FP32 copy (mixed)
+    float *z32 = nullptr, *p32 = nullptr;  // FP32 copies of z and p (mixed)
+    FSCG *cg = nullptr;                  // device CG state
     std::vector<void *> mem;
     std::vector<double> hp;
     int grid = 0;
+    int mixed = 0;                       // FP32 Hessian-vector products
+    cudaEvent_t ev[2 * FS_CHUNK];        // around each product of a chunk
+    bool have_ev = false;
+    double hvp_ms = 0.0;
+    long long hvp_launches = 0;
 
-    cudaError_t alloc(double **x, size_t n)
+    template <typename T>
+    cudaError_t alloc(T **x, size_t n)
     {
-        cudaError_t e = cudaMalloc((void **)x, sizeof(double) * (n ? n : 1));
+        cudaError_t e = cudaMalloc((void **)x, sizeof(T) * (n ? n : 1));
         if (e == cudaSuccess) mem.push_back(*x);
         return e;
     }
     ~FSSolver()
     {
         for (void *v : mem) cudaFree(v);
+        if (have_ev)
+            for (cudaEvent_t &e : ev) cudaEventDestroy(e);
     }
     double dot(const double *a, const double *b)
     {
@@ -662,28 +993,83 @@ struct FSSolver {
         for (int k = 0; k < FS_NB; k++) t += hp[k];
         return t;
     }
-    // the residual (v == nullptr) or its directional derivative along v,
-    // into out (length L)
-    void apply(const double *v, double *out)
+    // the cell constants of the current load step (A.omega)
+    void pack()
+    {
+        k_fs_pack<double><<<grid, 128>>>(A, pk64);
+        if (mixed) k_fs_pack<float><<<grid, 128>>>(A, pk32);
+    }
+    // the residual of the state z into r (FP64); no host synchronisation
+    void residual()
+    {
+        if (A.d == 3) k_fs_res<3><<<grid, 128>>>(A, pk64, z, cf, part9);
+        else k_fs_res<2><<<grid, 128>>>(A, pk64, z, cf, part9);
+        k_fs_gather<double><<<grid, 128>>>(A, cf, r, nullptr, nullptr, nullptr);
+        Mat9 pb;
+        for (int k = 0; k < 9; k++) pb.v[k] = pbar[k];
+        k_fs_rows<<<1, 256>>>(A.d, grid, part9, pb, (double)N, r + nd);
+    }
+    // q = H p (events ev0/ev1 around the product kernel), then al
+    void product(cudaEvent_t ev0, cudaEvent_t ev1)
     {
         const int d = A.d;
-        k_fs_cells<<<grid, 128>>>(A, z, v, cf, pc);
-        k_fs_gather<<<grid, 128>>>(A, cf, out);
-        k_fs_psum<<<FS_NB, 256>>>(N, pc, part);
-        cudaMemcpy(hp.data(), part, sizeof(double) * FS_NB * 9, cudaMemcpyDeviceToHost);
-        double ps[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int k = 0; k < FS_NB; k++)
-            for (int q = 0; q < 9; q++) ps[q] += hp[(size_t)k * 9 + q];
-        if (!v)
-            for (int q = 0; q < 9; q++) ps[q] -= (double)N * pbar[q];
-        double rf[6];
-        const int ii[6] = {0, 1, 2, 1, 0, 0}, jj[6] = {0, 1, 2, 2, 2, 1};
-        const int i2[3] = {0, 1, 0}, j2[3] = {0, 1, 1};
-        for (int k = 0; k < m; k++) {
-            const int i = d == 3 ? ii[k] : i2[k], j = d == 3 ? jj[k] : j2[k];
-            rf[k] = i == j ? ps[3 * i + i] : ps[3 * i + j] + ps[3 * j + i];
+        if (ev0) cudaEventRecord(ev0);
+        if (mixed) {
+            float *cf32 = reinterpret_cast<float *>(cf);
+            if (d == 3) k_fs_hvp<3, FDf><<<grid, 128>>>(A, pk32, z32, p32, cf32, part9, cg);
+            else k_fs_hvp<2, FDf><<<grid, 128>>>(A, pk32, z32, p32, cf32, part9, cg);
+            if (ev1) cudaEventRecord(ev1);
+            k_fs_gather<float><<<grid, 128>>>(A, cf32, q, p, partdot, cg);
+        } else {
+            if (d == 3) k_fs_hvp<3, FD><<<grid, 128>>>(A, pk64, z, p, cf, part9, cg);
+            else k_fs_hvp<2, FD><<<grid, 128>>>(A, pk64, z, p, cf, part9, cg);
+            if (ev1) cudaEventRecord(ev1);
+            k_fs_gather<double><<<grid, 128>>>(A, cf, q, p, partdot, cg);
         }
-        cudaMemcpy(out + nd, rf, sizeof(double) * m, cudaMemcpyHostToDevice);
+        k_fs_cg_alpha<<<1, 256>>>(d, grid, part9, grid, partdot, p + nd, q + nd, cg);
+    }
+    // PCG on H dz = -r from dz = 0 (r, p, q, s: residual, direction, H p,
+    // preconditioned residual), then z += dz; returns the iterations taken
+    int cg_solve(double rtol, int maxit)
+    {
+        cudaMemset(dz, 0, sizeof(double) * L);
+        k_fs_axpby<<<grid, 128>>>(L, -1.0, r, 0.0, r);
+        const double r0 = std::sqrt(dot(r, r));
+        k_fs_scale<<<grid, 128>>>(L, r, dginv, s);
+        cudaMemcpy(p, s, sizeof(double) * L, cudaMemcpyDeviceToDevice);
+        if (mixed) {
+            k_fs_to32<<<grid, 128>>>(L, z, z32);
+            k_fs_to32<<<grid, 128>>>(L, p, p32);
+        }
+        FSCG h;
+        memset(&h, 0, sizeof(h));
+        h.rz = dot(r, s);
+        h.tol = rtol * r0;
+        h.maxit = maxit;
+        cudaMemcpy(cg, &h, sizeof(h), cudaMemcpyHostToDevice);
+        for (;;) {
+            const int before = h.iters;
+            for (int k = 0; k < FS_CHUNK; k++) {
+                product(have_ev ? ev[2 * k] : nullptr, have_ev ? ev[2 * k + 1] : nullptr);
+                k_fs_cg_update<<<grid, 128>>>(L, dginv, p, q, dz, r, s, cg, part2);
+                k_fs_cg_beta<<<1, 256>>>(grid, part2, cg);
+                k_fs_cg_dir<<<grid, 128>>>(L, s, p, mixed ? p32 : nullptr, cg);
+            }
+            cudaMemcpy(&h, cg, sizeof(h), cudaMemcpyDeviceToHost);
+            // products that did work: one per completed iteration, and the
+            // one that found no positive curvature
+            const int ran = h.iters - before + (h.stop ? 1 : 0);
+            if (have_ev)
+                for (int k = 0; k < ran && k < FS_CHUNK; k++) {
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
+                    hvp_ms += ms;
+                }
+            hvp_launches += ran;
+            if (h.stop || h.done) break;
+        }
+        k_fs_axpby<<<grid, 128>>>(L, 1.0, dz, 1.0, z);
+        return h.iters;
     }
     double maxabs(const double *x)
     {
@@ -714,12 +1100,17 @@ int fs_run(const pf_config *cfg, const double *theta, const double *phi_g, doubl
     const int d = cfg->ndim;
     if (d != 2 && d != 3) return fs_fail(PF_EINVAL, "ndim must be 2 or 3");
     if (cfg->nx < 2 || cfg->ny < 2 || (d == 3 && cfg->nz < 2)) return fs_fail(PF_EINVAL, "grid sizes must be >= 2");
+    if ((long long)cfg->nx * cfg->ny * (d == 3 ? cfg->nz : 1) * d + 6 >= (1LL << 31))
+        return fs_fail(PF_EINVAL, "finite-strain grids hold fewer than 2^31 / ndim cells");
     if (opts->nload < 1 || opts->newton_maxit < 1 || !(opts->newton_tol > 0.0) || opts->cg_maxit < 1 ||
         !(opts->cg_rtol > 0.0 && opts->cg_rtol < 1.0))
         return fs_fail(PF_EINVAL, "invalid pf_fs_opts");
+    if (opts->precision != PF_FP64 && opts->precision != PF_MIXED)
+        return fs_fail(PF_EINVAL, "pf_fs_opts precision must be PF_FP64 or PF_MIXED");
     const double nu = cfg->p.nu, Es = cfg->p.E_s, Eg = Es * cfg->p.E_g_ratio;
     if (!(Es > 0.0) || !(nu > -1.0 && nu < 0.5)) return fs_fail(PF_EINVAL, "E_s > 0 and -1 < nu < 0.5 required");
     FSSolver S;
+    S.mixed = opts->precision == PF_MIXED;
     S.N = (long long)cfg->nx * cfg->ny * (d == 3 ? cfg->nz : 1);
     S.m = d == 3 ? 6 : 3;
     S.nd = (long long)d * S.N;
@@ -729,13 +1120,33 @@ int fs_run(const pf_config *cfg, const double *theta, const double *phi_g, doubl
     for (int i = 0; i < d; i++)
         for (int j = 0; j < d; j++) S.pbar[3 * i + j] = pbar ? pbar[i * d + j] : (i == j ? -cfg->p.prestress : 0.0);
     const long long N = S.N, L = S.L;
-    double **bufs[8] = {&S.z, &S.r, &S.p, &S.q, &S.s, &S.dz, &S.dg, &S.part};
-    const size_t lens[8] = {(size_t)L, (size_t)L, (size_t)L, (size_t)L, (size_t)L, (size_t)L, (size_t)S.nd,
-                            (size_t)FS_NB * 9};
-    for (int k = 0; k < 8; k++)
+    // one resident wave of the product kernel (4 blocks of 128 per SM): its
+    // block partials, summed in FP64 by one block, stay few
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fs_fail(PF_ECUDA, "no CUDA device");
+    S.grid = (int)std::min<long long>((N + 127) / 128, 4LL * std::max(sms, 1));
+    double **bufs[11] = {&S.z, &S.r, &S.p, &S.q, &S.s, &S.dz, &S.dg, &S.dginv, &S.part, &S.part2, &S.partdot};
+    const size_t lens[11] = {(size_t)L, (size_t)L, (size_t)L, (size_t)L, (size_t)L, (size_t)L, (size_t)S.nd,
+                             (size_t)L, (size_t)FS_NB, (size_t)S.grid * 2, (size_t)S.grid};
+    for (int k = 0; k < 11; k++)
         if (S.alloc(bufs[k], lens[k]) != cudaSuccess) return fs_fail(PF_ENOMEM, "cudaMalloc failed");
-    if (S.alloc(&S.cf, (size_t)N * 24) != cudaSuccess || S.alloc(&S.pc, (size_t)N * 9) != cudaSuccess ||
-        S.alloc(&S.K, N) != cudaSuccess || S.alloc(&S.G, N) != cudaSuccess || S.alloc(&S.Wf, N) != cudaSuccess ||
+    if (S.alloc(&S.part9, (size_t)S.grid * 9) != cudaSuccess || S.alloc(&S.cg, 1) != cudaSuccess ||
+        S.alloc(&S.pk64, (size_t)N) != cudaSuccess)
+        return fs_fail(PF_ENOMEM, "cudaMalloc failed");
+    if (S.mixed && (S.alloc(&S.pk32, (size_t)N) != cudaSuccess || S.alloc(&S.z32, (size_t)L) != cudaSuccess ||
+                    S.alloc(&S.p32, (size_t)L) != cudaSuccess))
+        return fs_fail(PF_ENOMEM, "cudaMalloc failed");
+    {
+        int ok = 0;
+        while (ok < 2 * FS_CHUNK && cudaEventCreate(&S.ev[ok]) == cudaSuccess) ok++;
+        if (ok < 2 * FS_CHUNK) {
+            for (int k = 0; k < ok; k++) cudaEventDestroy(S.ev[k]);
+            return fs_fail(PF_ECUDA, "cudaEventCreate failed");
+        }
+        S.have_ev = true;
+    }
+    if (S.alloc(&S.cf, (size_t)N * 24) != cudaSuccess || S.alloc(&S.K, N) != cudaSuccess || S.alloc(&S.G, N) != cudaSuccess || S.alloc(&S.Wf, N) != cudaSuccess ||
         S.alloc(&S.th, N) != cudaSuccess || S.alloc(&S.pg, N) != cudaSuccess)
         return fs_fail(PF_ENOMEM, "cudaMalloc failed");
     cudaMemcpy(S.th, theta, sizeof(double) * N, cudaMemcpyHostToDevice);
@@ -744,13 +1155,12 @@ int fs_run(const pf_config *cfg, const double *theta, const double *phi_g, doubl
     unsigned int *dbad = nullptr;
     if (FP) {
         if (S.alloc(&dFP, (size_t)N * 9) != cudaSuccess || S.alloc(&dFPinv, (size_t)N * 9) != cudaSuccess ||
-            S.alloc(&dEp, N) != cudaSuccess || S.alloc(reinterpret_cast<double **>(&dbad), 1) != cudaSuccess)
+            S.alloc(&dEp, N) != cudaSuccess || S.alloc(&dbad, 1) != cudaSuccess)
             return fs_fail(PF_ENOMEM, "cudaMalloc failed");
         cudaMemcpy(dFP, FP, sizeof(double) * N * 9, cudaMemcpyHostToDevice);
         cudaMemcpy(dEp, epsP, sizeof(double) * N, cudaMemcpyHostToDevice);
         cudaMemset(dbad, 0, sizeof(unsigned int));
     }
-    S.grid = (int)std::min<long long>((N + 127) / 128, 4096);
     const double Ks = Es / (3 * (1 - 2 * nu)), Gs = Es / (2 * (1 + nu));
     const double Kg = Eg / (3 * (1 - 2 * nu)), Gg = Eg / (2 * (1 + nu));
     k_fs_moduli<<<S.grid, 128>>>(N, S.th, S.pg, Ks, Gs, Kg, Gg, S.K, S.G, S.Wf);
@@ -792,6 +1202,7 @@ int fs_run(const pf_config *cfg, const double *theta, const double *phi_g, doubl
     double sK = 0.0, sG = 0.0;
     for (long long c = 0; c < N; c++) { sK += hK[c]; sG += hG[c]; }
     const double dgf = sK + 4.0 * sG / 3.0;
+    k_fs_dginv<<<S.grid, 128>>>(L, S.nd, S.dg, dgf, S.dginv);
     // start: u = 0, Fbar = I
     std::vector<double> z0((size_t)L, 0.0);
     for (int i = 0; i < d; i++) z0[S.nd + i] = 1.0;
@@ -801,39 +1212,20 @@ int fs_run(const pf_config *cfg, const double *theta, const double *phi_g, doubl
     double res = 0.0;
     for (int step = 1; step <= opts->nload; step++) {
         S.A.omega = omega * step / opts->nload;
+        S.pack();
         for (int it = 0;; it++) {
-            S.apply(nullptr, S.r);
+            S.residual();
             res = S.maxabs(S.r);
             if (res <= opts->newton_tol) break;
             if (it == opts->newton_maxit) {
                 st.residual = res;
+                st.hvp_ms = S.hvp_ms;
+                st.hvp_launches = S.hvp_launches;
                 if (stats) *stats = st;
                 return fs_fail(PF_ENOTCONV, "finite-strain Newton iteration did not converge");
             }
             st.newton_iters++;
-            // PCG on H dz = -r from dz = 0 (r, p, q, s: residual, direction,
-            // H p, preconditioned residual)
-            cudaMemset(S.dz, 0, sizeof(double) * L);
-            k_fs_axpby<<<S.grid, 128>>>(L, -1.0, S.r, 0.0, S.r);
-            const double r0 = std::sqrt(S.dot(S.r, S.r));
-            k_fs_precond<<<S.grid, 128>>>(L, S.nd, S.r, S.dg, dgf, S.s);
-            cudaMemcpy(S.p, S.s, sizeof(double) * L, cudaMemcpyDeviceToDevice);
-            double rz = S.dot(S.r, S.s);
-            for (int k = 0; k < opts->cg_maxit; k++) {
-                S.apply(S.p, S.q);
-                const double pq = S.dot(S.p, S.q);
-                if (!(pq > 0.0)) break;                  // not positive definite along p
-                const double al = rz / pq;
-                k_fs_axpby<<<S.grid, 128>>>(L, al, S.p, 1.0, S.dz);
-                k_fs_axpby<<<S.grid, 128>>>(L, -al, S.q, 1.0, S.r);
-                st.cg_iters++;
-                if (std::sqrt(S.dot(S.r, S.r)) <= opts->cg_rtol * r0) break;
-                k_fs_precond<<<S.grid, 128>>>(L, S.nd, S.r, S.dg, dgf, S.s);
-                const double rz1 = S.dot(S.r, S.s);
-                k_fs_axpby<<<S.grid, 128>>>(L, 1.0, S.s, rz1 / rz, S.p);
-                rz = rz1;
-            }
-            k_fs_axpby<<<S.grid, 128>>>(L, 1.0, S.dz, 1.0, S.z);
+            st.cg_iters += S.cg_solve(S.mixed ? std::max(opts->cg_rtol, FS_MIXED_RTOL) : opts->cg_rtol, opts->cg_maxit);
         }
     }
     cudaError_t e = cudaGetLastError();
@@ -853,6 +1245,8 @@ int fs_run(const pf_config *cfg, const double *theta, const double *phi_g, doubl
     for (int i = 0; i < d; i++)
         for (int j = 0; j < d; j++) Fbar[i * d + j] = fb[3 * i + j];
     st.residual = res;
+    st.hvp_ms = S.hvp_ms;
+    st.hvp_launches = S.hvp_launches;
     if (FP && cfg->plasticity) {
         S.A.omega = omega;
         k_fs_return_cells<<<S.grid, 64>>>(S.A, S.z, cfg->p.sigma_Y, cfg->p.H_hard, dFP, dEp, dbad);
@@ -913,6 +1307,8 @@ int fs_force(const pf_config *cfg, const double *theta, const double *phi_g, dou
     const int d = cfg->ndim;
     if (d != 2 && d != 3) return fs_fail(PF_EINVAL, "ndim must be 2 or 3");
     if (cfg->nx < 2 || cfg->ny < 2 || (d == 3 && cfg->nz < 2)) return fs_fail(PF_EINVAL, "grid sizes must be >= 2");
+    if ((long long)cfg->nx * cfg->ny * (d == 3 ? cfg->nz : 1) * d + 6 >= (1LL << 31))
+        return fs_fail(PF_EINVAL, "finite-strain grids hold fewer than 2^31 / ndim cells");
     const double nu = cfg->p.nu, Es = cfg->p.E_s, Eg = Es * cfg->p.E_g_ratio;
     const long long N = (long long)cfg->nx * cfg->ny * (d == 3 ? cfg->nz : 1);
     const int m = d == 3 ? 6 : 3;

@@ -80,11 +80,12 @@ class pf_implicit_stats(ctypes.Structure):
 
 class pf_fs_opts(ctypes.Structure):
     _fields_ = [("nload", ctypes.c_int), ("newton_maxit", ctypes.c_int), ("newton_tol", ctypes.c_double),
-                ("cg_maxit", ctypes.c_int), ("cg_rtol", ctypes.c_double)]
+                ("cg_maxit", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("precision", ctypes.c_int)]
 
 
 class pf_fs_stats(ctypes.Structure):
-    _fields_ = [("newton_iters", ctypes.c_int), ("cg_iters", ctypes.c_longlong), ("residual", ctypes.c_double)]
+    _fields_ = [("newton_iters", ctypes.c_int), ("cg_iters", ctypes.c_longlong), ("residual", ctypes.c_double),
+                ("hvp_ms", ctypes.c_double), ("hvp_launches", ctypes.c_longlong)]
 
 
 class pf_profile(ctypes.Structure):

@@ -9,7 +9,13 @@ same load steps to max |residual| <= 1e-11 (the oracle with a dense
 finite-difference Jacobian, the library matrix-free by conjugate
 gradients), so u and Fbar agree to the Newton tolerance times the
 problem's conditioning: 1e-8 relative to the largest displacement, 1e-10 on
-Fbar.
+Fbar.  The library's Hessian-vector products run in FP32 (PF_MIXED, the
+default here) or FP64; the residual is FP64 either way.  With FP32
+products Newton converges linearly (~1e-6 per step) and stops just under
+its tolerance, where the oracle's exact Newton overshoots 1e-11 by orders;
+the near-translation mode (u = 0 only at node 0) turns a 1e-11 residual
+into ~2e-9 of u, so the library side solves to 1e-13 (FP64 residuals reach
+it).
 """
 import numpy as np
 import pytest
@@ -31,21 +37,24 @@ def fs(orc):
     return finite_strain
 
 
-def _opts(nload, tol=1e-11):
-    return native.pf_fs_opts(nload=nload, newton_maxit=40, newton_tol=tol, cg_maxit=20000, cg_rtol=1e-12)
+def _opts(nload, tol=1e-13, precision=native.PF_MIXED):
+    return native.pf_fs_opts(nload=nload, newton_maxit=40, newton_tol=tol, cg_maxit=20000, cg_rtol=1e-12,
+                             precision=precision)
 
 
-def _gpu(th, pg, prm, omega, nload, pbar=None):
+def _gpu(th, pg, prm, omega, nload, pbar=None, precision=native.PF_MIXED):
     cfg = make_config(th.shape, prm)
-    rc, u, Fb, st = native.pf_finite_strain_solve(cfg, th.ravel(), pg.ravel(), omega, pbar, _opts(nload))
+    rc, u, Fb, st = native.pf_finite_strain_solve(cfg, th.ravel(), pg.ravel(), omega, pbar,
+                                                  _opts(nload, precision=precision))
     assert rc == native.PF_OK, native.lib().pf_fs_last_error()
+    assert st.hvp_launches >= st.cg_iters and st.hvp_ms > 0.0
     return u, Fb, st
 
 
-def _compare(fs, th, pg, prm, omega, nload, prestress=0.0, pbar=None):
+def _compare(fs, th, pg, prm, omega, nload, prestress=0.0, pbar=None, precision=native.PF_MIXED):
     pr = fs.Problem(th, pg, prm, omega, prestress=prestress, pbar=pbar)
     u0, F0 = pr.unpack(pr.solve(tol=1e-11, nload=nload))
-    u, Fb, st = _gpu(th, pg, dict(prm, prestress=prestress), omega, nload, pbar)
+    u, Fb, st = _gpu(th, pg, dict(prm, prestress=prestress), omega, nload, pbar, precision)
     scale = max(np.abs(u0).max(), 1e-12)
     assert np.abs(u - u0).max() < 1e-8 * scale, (np.abs(u - u0).max(), scale)
     assert np.abs(Fb - F0).max() < 1e-10, (Fb, F0)
@@ -53,13 +62,14 @@ def _compare(fs, th, pg, prm, omega, nload, prestress=0.0, pbar=None):
     return u, Fb
 
 
-def test_finite_strain_2d_core_shell_matches_oracle(fs):
+@pytest.mark.parametrize("precision", [native.PF_MIXED, native.PF_FP64])
+def test_finite_strain_2d_core_shell_matches_oracle(fs, precision):
     """Core-shell with gas cells and a 20 % volume change of ferrite,
     prestress 0.005, four load steps (plane strain)."""
     from oracle import split_phases
     f = inputs.core_shell((8, 8), 2.5, 1.0, delta=1.0)
     th, pg = split_phases(f["phi_f"], f["phi_w"])
-    u, Fb = _compare(fs, th, pg, workloads.params(), 0.2, 4, prestress=0.005)
+    u, Fb = _compare(fs, th, pg, workloads.params(), 0.2, 4, prestress=0.005, precision=precision)
     assert Fb[0, 0] < 1.0 and np.abs(u).max() > 1e-3
 
 
@@ -73,7 +83,8 @@ def test_finite_strain_2d_sheared_box_matches_oracle(fs):
     _compare(fs, th, pg, workloads.params(), 0.1, 2, pbar=pbar)
 
 
-def test_finite_strain_3d_ball_matches_oracle(fs):
+@pytest.mark.parametrize("precision", [native.PF_MIXED, native.PF_FP64])
+def test_finite_strain_3d_ball_matches_oracle(fs, precision):
     n = 4
     x = np.arange(n) + 0.5 - n / 2
     gz, gy, gx = np.meshgrid(x, x, x, indexing="ij")
@@ -81,7 +92,7 @@ def test_finite_strain_3d_ball_matches_oracle(fs):
     pg = np.zeros_like(th)
     pg[0, 0, :] = 1.0                      # a row of gas cells
     th[0, 0, :] = 0.0
-    _compare(fs, th, pg, workloads.params(), 0.3, 3)
+    _compare(fs, th, pg, workloads.params(), 0.3, 3, precision=precision)
 
 
 def test_finite_strain_3d_uniform_transformation_is_stress_free():
@@ -99,6 +110,9 @@ def test_finite_strain_rejects_bad_arguments():
     bad = native.pf_fs_opts(nload=0, newton_maxit=10, newton_tol=1e-10, cg_maxit=10, cg_rtol=1e-6)
     rc, _, _, _ = native.pf_finite_strain_solve(cfg, th.ravel(), th.ravel() * 0, 0.1, None, bad)
     assert rc == native.PF_EINVAL and b"pf_fs_opts" in native.lib().pf_fs_last_error()
+    bad = native.pf_fs_opts(nload=1, newton_maxit=10, newton_tol=1e-10, cg_maxit=10, cg_rtol=1e-6, precision=2)
+    rc, _, _, _ = native.pf_finite_strain_solve(cfg, th.ravel(), th.ravel() * 0, 0.1, None, bad)
+    assert rc == native.PF_EINVAL and b"precision" in native.lib().pf_fs_last_error()
 
 
 def test_return_map_matches_oracle(fs):
@@ -131,8 +145,9 @@ def test_return_map_matches_oracle(fs):
     assert np.abs(np.linalg.det(FP) - 1.0).max() < 1e-12
 
 
-@pytest.mark.parametrize("shape", [(8, 8), (4, 4, 4)])
-def test_finite_strain_plastic_steps_match_oracle(fs, shape):
+@pytest.mark.parametrize("shape,precision", [((8, 8), native.PF_MIXED), ((4, 4, 4), native.PF_MIXED),
+                                             ((4, 4, 4), native.PF_FP64)])
+def test_finite_strain_plastic_steps_match_oracle(fs, shape, precision):
     """Two staggered elasto-plastic mechanics steps on a core-shell (the
     second with the plastic deformation of the first) against
     Problem.mechanics_step."""
@@ -149,7 +164,8 @@ def test_finite_strain_plastic_steps_match_oracle(fs, shape):
     cfg = make_config(th.shape, prm)
     for k in range(2):
         u0, F0 = pr.unpack(pr.mechanics_step(nload=2))
-        rc, u, Fb, st = native.pf_finite_strain_step(cfg, th.ravel(), pg.ravel(), om, None, _opts(2), FP, ep)
+        rc, u, Fb, st = native.pf_finite_strain_step(cfg, th.ravel(), pg.ravel(), om, None,
+                                                     _opts(2, precision=precision), FP, ep)
         assert rc == native.PF_OK, native.lib().pf_fs_last_error()
         scale = max(np.abs(u0).max(), 1e-12)
         assert np.abs(u - u0).max() < 1e-8 * scale, (k, np.abs(u - u0).max(), scale)
