@@ -517,6 +517,19 @@ def backward_euler_line(n=256, steps=3, dt=0.05, explicit_steps=20):
                          "H": d["sum_H"] + 2 * d["sum_H2O"] + 2 * d["removed_H2O"] - d["supplied_H"]}}
 
 
+# The finite-strain Hessian-vector product kernel (k_fs_hvp<3, FDf>, FP32
+# forward mode) from one ncu capture of the current kernel on the 64^3
+# workload (profiles/k_fs_hvp_coreshell64_finite_strain.md): FP32 flops per
+# cell = 2 FFMA + FADD + FMUL thread instructions / cells, and DRAM bytes
+# per cell (the 64^3 working set sits in L2, so they are below the
+# compulsory bytes).  Its bound is the FP32 pipe: the peak is 152 SMs x 128
+# FP32 lanes x 2 flops x 2.07 GHz (the counters' FFMA peak of 128 per cycle
+# and SM; the maximum SM clock).
+FS_HVP_FLOPS_PER_CELL = 10036.4
+FS_HVP_DRAM_PER_CELL = 114.4
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def finite_strain_line(n=64, omega=0.2, nload=2, only="both"):
     """One staggered elasto-plastic finite-strain mechanics step
     (pf_finite_strain_step: neo-Hooke mixture with the transformation
@@ -562,6 +575,16 @@ def finite_strain_line(n=64, omega=0.2, nload=2, only="both"):
                      "hvp_share_of_wall": st.hvp_ms / 1e3 / t,
                      "cell_products_per_s": N * st.hvp_launches / t, "plastic_cells": int((ep > 0).sum()),
                      "max_u": float(np.abs(u).max())}
+    if "fp32_products" in out:
+        a = out["fp32_products"]
+        tf = FS_HVP_FLOPS_PER_CELL * N / (a["hvp_ms_per_launch"] * 1e-3) / 1e12
+        out["roofline"] = {"kernel": "k_fs_hvp<3, FDf> (FP32 Hessian-vector product)", "bound": "alu",
+                           "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": tf / FP32_PEAK_TFLOPS,
+                           "traffic": FS_HVP_DRAM_PER_CELL * N if n == 64 else None,
+                           "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                           "unit_flops": "%.1f FP32 flops per cell (ncu instruction counts) x %d cells per launch"
+                                         % (FS_HVP_FLOPS_PER_CELL, N)}
     if only == "both":
         a, b = out["fp32_products"], out["fp64_products"]
         out["speedup_fp32_products"] = b["s_per_step"] / a["s_per_step"]
