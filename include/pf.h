@@ -225,6 +225,10 @@ typedef struct {
     int gmres_restart;  /* Krylov vectors per GMRES cycle, 1 .. 60                   */
     int gmres_maxit;    /* GMRES iterations per Newton iteration (>= 1)              */
     int pc_degree;      /* Chebyshev steps of the block preconditioner, 0 (none) .. 64 */
+    int pc_precision;   /* the preconditioner's arithmetic: PF_FP64, or PF_MIXED (FP32
+                           coefficients and iterates, one fused kernel per Chebyshev
+                           step; grids of fewer than 2^29 cells).  GMRES, the
+                           Jacobian-vector products and F stay FP64 either way.   */
 } pf_implicit_opts;
 
 typedef struct {

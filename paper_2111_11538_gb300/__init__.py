@@ -176,12 +176,16 @@ class Simulation:
         return rc
 
     def step_implicit(self, n, dt, newton_tol=1e-12, newton_maxit=30, gmres_rtol=1e-6, gmres_restart=60,
-                      gmres_maxit=5000, pc_degree=32, stream=None, check=True):
+                      gmres_maxit=5000, pc_degree=32, pc_precision="mixed", stream=None, check=True):
         """n backward-Euler steps of length dt (pf_step_implicit); returns the
-        Newton and GMRES counts as a dict."""
+        Newton and GMRES counts as a dict.  pc_precision: the block
+        preconditioner in FP32 ("mixed") or FP64 ("fp64")."""
+        if pc_precision not in ("mixed", "fp64"):
+            raise ValueError("pc_precision must be 'mixed' or 'fp64'")
         o = native.pf_implicit_opts(dt=float(dt), newton_tol=float(newton_tol), newton_maxit=int(newton_maxit),
                                     gmres_rtol=float(gmres_rtol), gmres_restart=int(gmres_restart),
-                                    gmres_maxit=int(gmres_maxit), pc_degree=int(pc_degree))
+                                    gmres_maxit=int(gmres_maxit), pc_degree=int(pc_degree),
+                                    pc_precision=PF_MIXED if pc_precision == "mixed" else PF_FP64)
         rc, st = native.pf_step_implicit(self.h, n, o, stream)
         if check:
             self._check(rc)

@@ -13,7 +13,8 @@
 // Jacobian-vector products are directional derivatives of F evaluated in
 // forward mode (matrix-free); the linear solves are restarted GMRES
 // preconditioned by a fixed Chebyshev polynomial of each field's own
-// diffusion block (see k_be_pc_*).  FP64 throughout.
+// diffusion block (see k_be_pc_*), in FP64 or FP32 (k_be_pc32_*); FP64
+// everywhere else.
 #pragma once
 
 namespace pfdev {
@@ -348,6 +349,120 @@ __global__ void k_be_pc_step(long long N, const double *__restrict__ q, const do
             d[i] = cf.c1[b] * dd + cf.c2[b] * rr / dg[i];
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same preconditioner in FP32 (pf_implicit_opts.pc_precision =
+// PF_MIXED; GB300 runs FP32 at 64 times its FP64 rate): the blocks'
+// coefficients packed once per Newton step, one fused kernel per Chebyshev
+// step (the stencil reads the previous direction and writes the next, so no
+// q pass), the result handed back in FP64.  The Krylov vectors, the
+// Jacobian-vector products and the Newton residual stay FP64; only the
+// preconditioner, an approximate inverse by construction, rounds to FP32.
+// ---------------------------------------------------------------------------
+struct BEPc32 {
+    float *cth;        // N: the theta block's dt L eps mob_c (with its sign)
+    float *DO, *DH, *DW;   // N: the diffusivities of the three species blocks
+    float *dginv;      // 4N: inverse diagonals
+    float *z, *r, *d0, *d1;   // 4N each: iterate, residual, directions (ping-pong)
+};
+struct BECheb32 {
+    float c1[4], c2[4];
+};
+
+template <int D>
+__device__ __forceinline__ void be_neighbours32(int nx, int ny, int nz, int c, int (&nb)[2 * D])
+{
+    const int i = c % nx, r = c / nx;
+    const int j = r % ny, k = D == 3 ? r / ny : 0;
+    const int base = c - i, pl = nx * ny;
+    nb[0] = base + (i == 0 ? nx - 1 : i - 1);
+    nb[1] = base + (i == nx - 1 ? 0 : i + 1);
+    nb[2] = c + nx * ((j == 0 ? ny - 1 : j - 1) - j);
+    nb[3] = c + nx * ((j == ny - 1 ? 0 : j + 1) - j);
+    if constexpr (D == 3) {
+        nb[4] = c + pl * ((k == 0 ? nz - 1 : k - 1) - k);
+        nb[5] = c + pl * ((k == nz - 1 ? 0 : k + 1) - k);
+    }
+}
+
+// the FP32 coefficients of the four blocks (after k_be_pc_diag)
+__global__ void k_be_pc32_pack(const BEArgs a, const double *__restrict__ der, const double *__restrict__ dg,
+                               BEPc32 P)
+{
+    const int N = (int)a.N;
+    const double cth = -a.dt * a.K.Lh * a.K.eps2;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const double hc = hfun(a.phig[c]);
+        P.cth[c] = (float)(cth * a.mob[c]);
+        P.DO[c] = (float)((1.0 - hc) * a.K.DOs + hc * a.K.DOg);
+        P.DH[c] = (float)der[2 * (size_t)N + c];
+        P.DW[c] = (float)der[3 * (size_t)N + c];
+#pragma unroll
+        for (int b = 0; b < 4; b++) P.dginv[(size_t)b * N + c] = (float)(1.0 / dg[(size_t)b * N + c]);
+    }
+}
+
+// z = 0, r = v, d0 = c2 D^-1 r
+__global__ void k_be_pc32_init(int N, const double *__restrict__ v, BEPc32 P, BECheb32 cf)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const size_t i = (size_t)b * N + c;
+            const float rv = (float)v[i];
+            P.z[i] = 0.0f;
+            P.r[i] = rv;
+            P.d0[i] = cf.c2[b] * rv * P.dginv[i];
+        }
+}
+
+// one Chebyshev step: q = A din at cell c, then z += din, r -= q,
+// dout = c1 din + c2 D^-1 r
+template <int D>
+__global__ void k_be_pc32_step(int nx, int ny, int nz, int N, float dt, const unsigned char *__restrict__ mask,
+                               BEPc32 P, const float *__restrict__ din, float *__restrict__ dout, BECheb32 cf)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        int nb[2 * D];
+        be_neighbours32<D>(nx, ny, nz, c, nb);
+        const float d0c = din[c], d1c = din[N + c], d2c = din[2 * N + c], d3c = din[3 * N + c];
+        const float DOc = P.DO[c], DHc = P.DH[c], DWc = P.DW[c];
+        float lt = 0.0f, fo = 0.0f, fh = 0.0f, fw = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 2 * D; k++) {
+            const int n = nb[k];
+            lt += d0c - din[n];
+            fo += 0.5f * (DOc + P.DO[n]) * (d1c - din[N + n]);
+            fh += 0.5f * (DHc + P.DH[n]) * (d2c - din[2 * N + n]);
+            fw += 0.5f * (DWc + P.DW[n]) * (d3c - din[3 * N + n]);
+        }
+        const bool held = mask[c] != 0;
+        float q[4], dc[4] = {d0c, d1c, d2c, d3c};
+        q[0] = d0c + P.cth[c] * lt;
+        q[1] = d1c + dt * fo;
+        q[2] = held ? d2c : d2c + dt * fh;
+        q[3] = held ? d3c : d3c + dt * fw;
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const size_t i = (size_t)b * N + c;
+            P.z[i] += dc[b];
+            const float rr = P.r[i] - q[b];
+            P.r[i] = rr;
+            dout[i] = cf.c1[b] * dc[b] + cf.c2[b] * rr * P.dginv[i];
+        }
+    }
+}
+
+// the last step (z += din) into the FP64 result
+__global__ void k_be_pc32_final(int N, BEPc32 P, const float *__restrict__ din, double *__restrict__ zo)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const size_t i = (size_t)b * N + c;
+            zo[i] = (double)(P.z[i] + din[i]);
+        }
 }
 
 // ---------------------------------------------------------------------------

@@ -1201,12 +1201,13 @@ struct BEWork {
     double *y, *y0, *F0, *Ft, *t, *der, *z, *r, *d, *q, *dg, *x, *u, *V;
     double *part, *hvec;
     unsigned long long *mx;    // [0] max |F|, [2..3] max |delta|, max |y|, [4..7] Gershgorin s per block
+    BEPc32 pc32;               // the FP32 preconditioner's arrays (24 N floats)
 };
 
 int be_work(pf_handle *h, int m, BEWork &w)
 {
     const long long N = h->P.N, L = 4 * N;
-    const size_t nvec = 14 + (size_t)(m + 1);
+    const size_t nvec = 14 + (size_t)(m + 1) + 3;     // the last 3: 24 N floats of the FP32 preconditioner
     const size_t len = nvec * (size_t)L + BE_NPART + 64 + 8;
     if (h->be_len < len) {
         PF_TRY(h->alloc(&h->be_ws, sizeof(double) * len));
@@ -1217,6 +1218,12 @@ int be_work(pf_handle *h, int m, BEWork &w)
     double **vec[14] = {&w.y, &w.y0, &w.F0, &w.Ft, &w.t, &w.der, &w.z, &w.r, &w.d, &w.q, &w.dg, &w.x, &w.u, &w.V};
     for (int k = 0; k < 14; k++) { *vec[k] = p; p += L; }
     p += (size_t)m * L;                       // V holds m + 1 vectors
+    float *f = reinterpret_cast<float *>(p);
+    p += 3 * (size_t)L;
+    float **fv[9] = {&w.pc32.cth, &w.pc32.DO, &w.pc32.DH, &w.pc32.DW, &w.pc32.dginv, &w.pc32.z, &w.pc32.r,
+                     &w.pc32.d0, &w.pc32.d1};
+    const long long flen[9] = {N, N, N, N, L, L, L, L, L};
+    for (int k = 0; k < 9; k++) { *fv[k] = f; f += flen[k]; }
     w.part = p; p += BE_NPART;
     w.hvec = p; p += 64;
     w.mx = reinterpret_cast<unsigned long long *>(p);
@@ -1278,8 +1285,23 @@ int be_steps(pf_handle *h, int nsteps, const pf_implicit_opts &o, pf_implicit_st
     // Chebyshev coefficients of the block preconditioner
     std::vector<BECheb> cheb;
     BECheb cinit;
+    std::vector<BECheb32> cheb32;
+    BECheb32 cinit32;
+    const bool pc32 = o.pc_precision == PF_MIXED;
     auto precond = [&](const double *v, double *zo) -> int {
         if (K == 0) return h->cuda(cudaMemcpyAsync(zo, v, sizeof(double) * L, cudaMemcpyDeviceToDevice, s), "copy");
+        if (pc32) {
+            const int n32 = (int)N;
+            k_be_pc32_init<<<gN, 256, 0, s>>>(n32, v, w.pc32, cinit32);
+            float *din = w.pc32.d0, *dout = w.pc32.d1;
+            for (int k = 0; k + 1 < K; k++) {
+                k_be_pc32_step<D><<<gN, 256, 0, s>>>(a.nx, a.ny, a.nz, n32, (float)a.dt, a.mask, w.pc32, din, dout,
+                                                     cheb32[k]);
+                std::swap(din, dout);
+            }
+            k_be_pc32_final<<<gN, 256, 0, s>>>(n32, w.pc32, din, zo);
+            return check("preconditioner");
+        }
         k_be_pc_init<<<gL, 256, 0, s>>>(N, v, w.dg, zo, w.r, w.d, cinit);
         for (int k = 0; k + 1 < K; k++) {
             k_be_pc_apply<D><<<gN, 256, 0, s>>>(a, w.der, w.d, w.q);
@@ -1328,7 +1350,18 @@ int be_steps(pf_handle *h, int nsteps, const pf_implicit_opts &o, pf_implicit_st
                     cheb[k].c2[b] = 2.0 * rho1 / del;
                     rho0[b] = rho1;
                 }
+            cheb32.assign(cheb.size(), BECheb32{});
+            for (size_t k = 0; k < cheb.size(); k++)
+                for (int b = 0; b < 4; b++) {
+                    cheb32[k].c1[b] = (float)cheb[k].c1[b];
+                    cheb32[k].c2[b] = (float)cheb[k].c2[b];
+                }
+            for (int b = 0; b < 4; b++) {
+                cinit32.c1[b] = (float)cinit.c1[b];
+                cinit32.c2[b] = (float)cinit.c2[b];
+            }
         }
+        if (pc32 && K > 0) k_be_pc32_pack<<<gN, 256, 0, s>>>(a, w.der, w.dg, w.pc32);
         PF_TRY(Fval(w.y, w.F0));
         double fmax;
         PF_TRY(read_max(0, 1, &fmax));
@@ -1657,8 +1690,10 @@ int pf_step_implicit(pf_handle *h, int nsteps, const pf_implicit_opts *opts, pf_
     const pf_implicit_opts &o = *opts;
     if (!(o.dt > 0.0) || !(o.newton_tol > 0.0) || o.newton_maxit < 1 || !(o.gmres_rtol > 0.0 && o.gmres_rtol < 1.0) ||
         o.gmres_restart < 1 || o.gmres_restart > BE_MAX_RESTART || o.gmres_maxit < 1 || o.pc_degree < 0 ||
-        o.pc_degree > 64)
+        o.pc_degree > 64 || (o.pc_precision != PF_FP64 && o.pc_precision != PF_MIXED))
         return h->fail(PF_EINVAL, "invalid pf_implicit_opts");
+    if (o.pc_precision == PF_MIXED && 4 * h->P.N >= (1LL << 31))
+        return h->fail(PF_EINVAL, "the FP32 preconditioner takes grids of fewer than 2^29 cells");
     cudaStream_t s = stream ? (cudaStream_t)stream : h->own;
     if (h->own != s) {
         cudaEvent_t ev;

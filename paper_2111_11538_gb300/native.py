@@ -70,7 +70,7 @@ KERNEL_CLASSES = ["setup", "cg", "return", "update", "warm"]
 class pf_implicit_opts(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
                 ("gmres_rtol", ctypes.c_double), ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
-                ("pc_degree", ctypes.c_int)]
+                ("pc_degree", ctypes.c_int), ("pc_precision", ctypes.c_int)]
 
 
 class pf_implicit_stats(ctypes.Structure):

@@ -9,7 +9,9 @@ matrix-free Newton-Krylov (Jacobian-vector products in forward mode); both stop 
 or an update below 1e-12 of the largest field value), so the states agree to
 the Newton tolerance amplified by the step's conditioning: 1e-9 (relative L2)
 at the bench parameters, 1e-8 at the paper's diffusivities, where dt R
-carries terms ~1e4 times the fields.
+carries terms ~1e4 times the fields.  The library's block preconditioner
+runs in FP32 by default (pc_precision "mixed") or FP64; F is FP64 either
+way, so both meet the same bounds.
 """
 import numpy as np
 import pytest
@@ -66,13 +68,14 @@ def _balances(d, f, tol):
     assert abs(d["sum_H"] + 2 * d["sum_H2O"] + 2 * d["removed_H2O"] - d["supplied_H"] - H0) < tol * H0
 
 
-def test_backward_euler_2d_matches_oracle(orc, be):
+@pytest.mark.parametrize("pc_precision", ["mixed", "fp64"])
+def test_backward_euler_2d_matches_oracle(orc, be, pc_precision):
     """14x14 core-shell with supply cells, mechanics, reaction: three steps
     at 4x the explicit stability limit."""
     f = _coreshell()
     prm = workloads.params(cg_rtol=1e-12)
     dt = 20.0 * orc.Sim(f, prm).dt                  # Sim.dt is 0.2 x the explicit limit
-    ref, g, d, stats = _run(orc, be, f, prm, [dt] * 3)
+    ref, g, d, stats = _run(orc, be, f, prm, [dt] * 3, pc_precision=pc_precision)
     for k in KEYS:
         assert rel(g[k], ref.f[k]) < 1e-9, (k, rel(g[k], ref.f[k]))
     assert rel(g["sigma"], ref.f["sigma"]) < 1e-8
@@ -144,6 +147,10 @@ def test_backward_euler_rejects_mixed_and_bad_options():
         sim.step_implicit(1, 0.1)                     # no fields yet
     assert e.value.code == native.PF_ESTATE
     sim.set_fields(f)
+    o = native.pf_implicit_opts(dt=0.1, newton_tol=1e-12, newton_maxit=5, gmres_rtol=1e-6, gmres_restart=20,
+                                gmres_maxit=100, pc_degree=8, pc_precision=2)
+    rc, _ = native.pf_step_implicit(sim.h, 1, o)
+    assert rc == native.PF_EINVAL
     for bad in ({"dt": -1.0}, {"gmres_restart": 61}, {"pc_degree": -1}, {"gmres_rtol": 1.0}):
         kw = dict(dt=0.1)
         kw.update(bad)
