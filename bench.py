@@ -797,9 +797,9 @@ def main():
         "learned_warm_start": learned_warm_start(0, 0, fields, 0, 0, WORKLOAD),
         "e2e": {"value": e2e_val, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": args.e2e_steps,
-                "note": "pf_set_fields / pf_step / pf_get_fields with pinned host buffers every step; each "
-                        "set_fields restarts the extrapolated guess, so these steps start from the previous "
-                        "solution"},
+                "note": "pf_set_fields / pf_step / pf_get_fields of the full state with pinned host buffers "
+                        "every step (the copies take ~30 ms of a step); the solve after each round trip "
+                        "takes more V-cycles than consecutive steps do (about 54 against 31 at 256^3)"},
         "gpu_launches": prof["launches"],
         "clocks": clocks,
         "cpu_baseline": cpu,

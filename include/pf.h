@@ -178,8 +178,12 @@ int pf_create(const pf_config *cfg, pf_handle **out);
  * default to: theta = phi_f / (phi_f + phi_w) (0 without solid),
  * phi_g = 1 - phi_f - phi_w, u = 0,
  * Ebar = 0, eps_p = 0, alpha = 0, mobility = 1, dirichlet = 0.  Resets the
- * step counter, the diagnostics and the extrapolation history of the CG
- * guess. */
+ * step counter and the diagnostics.  The extrapolation history of the CG
+ * guess (PF_WS_EXTRAP, PF_WS_EXTRAP2) and, for PF_MIXED, the FP64 copy of
+ * the displacement are reset too, unless u equals, bit for bit, the
+ * handle's displacement as pf_get_fields exports it: a state round trip
+ * through the host then continues the solver's trajectory (the guess only
+ * sets where each solve starts; every solve still meets cfg->cg_rtol). */
 int pf_set_fields(pf_handle *h, const pf_fields *f, int where);
 
 /* Advance nsteps >= 0 steps on cudaStream (NULL: the handle's own stream),

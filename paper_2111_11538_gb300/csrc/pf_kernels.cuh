@@ -1363,6 +1363,33 @@ __global__ void k_in_comp(long long N, int ncomp, const double *src, T *const *d
         for (int k = 0; k < ncomp; k++) dst[k][c] = (T)(src ? src[c * ncomp + k] : 0.0);
 }
 
+// *changed = 1 if any component differs from (double) of the stored one
+template <typename T>
+__global__ void k_comp_differs(long long N, int ncomp, const double *src, const T *const *cur, int *changed)
+{
+    bool diff = false;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        for (int k = 0; k < ncomp; k++)
+            if ((src ? src[c * ncomp + k] : 0.0) != (double)cur[k][c]) diff = true;
+    if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) *changed = 1;
+}
+
+// k_in_comp, unless *changed == 0 (changed == nullptr: always)
+template <typename T>
+__global__ void k_in_comp_if(long long N, int ncomp, const double *src, T *const *dst, const int *changed)
+{
+    if (changed && *changed == 0) return;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        for (int k = 0; k < ncomp; k++) dst[k][c] = (T)(src ? src[c * ncomp + k] : 0.0);
+}
+
+// the extrapolated guess starts over unless the displacement came back
+// unchanged (changed == nullptr: always)
+static __global__ void k_ext_restart(const int *changed, int *count)
+{
+    if (!changed || *changed) *count = 0;
+}
+
 // (phi_f, phi_w) -> theta = phi_f / (phi_f + phi_w) (0 where no solid), phi_g
 template <typename T>
 __global__ void k_in_phase(long long N, const double *pf, const double *pw, T *theta, T *phig)

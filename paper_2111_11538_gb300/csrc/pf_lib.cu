@@ -234,6 +234,7 @@ struct pf_handle {
     double *ext_hist[2][3] = {};       // [0]: x_{n-1}, [1]: x_{n-2} (order 2 only)
     double *ext_E = nullptr;
     int *ext_count = nullptr;
+    int *u_changed = nullptr;          // set_fields: the displacement differs from the handle's own
     std::vector<void *> net_allocs;
 
     // profiling: event pairs around each launch while enabled
@@ -868,6 +869,9 @@ template <typename T>
 int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
 {
     const long long N = h->P.N;
+    // the state goes into the current parity's buffers: the step plan (job
+    // tables and captured graphs, laid out relative to that parity) stays
+    const int c0 = h->cur;
     const int D = h->cfg.ndim, NP = D == 2 ? 4 : 6, NV = D == 2 ? 3 : 6;
     const int g = grid_for(h, N);
     const size_t nb = sizeof(double) * (size_t)N;
@@ -881,12 +885,12 @@ int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
     {
         PF_SRC(pf, f->phi_f, nb, h->stage);
         PF_SRC(pw, f->phi_w, nb, h->stage2);
-        k_in_phase<T><<<g, 256, 0, s>>>(N, pf, pw, (T *)h->theta[0], (T *)h->phig);
+        k_in_phase<T><<<g, 256, 0, s>>>(N, pf, pw, (T *)h->theta[c0], (T *)h->phig);
     }
     if (f->theta) {
         // the order parameter itself (exact restore, also where phi_g = 1)
         PF_SRC(a, f->theta, nb, h->stage);
-        k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->theta[0], 0.0);
+        k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->theta[c0], 0.0);
     }
     if (f->phi_g) {
         PF_SRC(a, f->phi_g, nb, h->stage2);
@@ -894,13 +898,13 @@ int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
     }
     {
         PF_SRC(a, f->x_O, nb, h->stage);
-        k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->xO[0], 0.0);
+        k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->xO[c0], 0.0);
         PF_SRC(b, f->x_H, nb, h->stage2);
-        k_in_scalar<T><<<g, 256, 0, s>>>(N, b, (T *)h->xH[0], 0.0);
+        k_in_scalar<T><<<g, 256, 0, s>>>(N, b, (T *)h->xH[c0], 0.0);
     }
     {
         PF_SRC(a, f->x_H2O, nb, h->stage);
-        k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->xW[0], 0.0);
+        k_in_scalar<T><<<g, 256, 0, s>>>(N, a, (T *)h->xW[c0], 0.0);
         PF_SRC(b, f->mobility, nb, h->stage2);
         k_in_scalar<T><<<g, 256, 0, s>>>(N, b, (T *)h->mob, 1.0);
     }
@@ -914,12 +918,28 @@ int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
         for (int d = 0; d < 3; d++) tab[d] = h->u[d];
         PF_TRY(h->cuda(cudaMemcpyAsync(h->ptrtab, tab, sizeof(tab), cudaMemcpyHostToDevice, s), "pointer table"));
         PF_SRC(a, f->u, nb * D, h->stage);
-        k_in_comp<T><<<g, 256, 0, s>>>(N, D, a, (T *const *)h->ptrtab);
+        // a displacement equal to the handle's own, bit for bit as
+        // pf_get_fields exports it (a state round trip), keeps the
+        // extrapolation history and the FP64 copy of the solve
+        // (the mixed form exports its FP64 copy)
+        if (h->u_changed) {
+            PF_TRY(h->cuda(cudaMemsetAsync(h->u_changed, 0, sizeof(int), s), "round-trip flag"));
+            if (h->refine) {
+                void *t64[6] = {};
+                for (int d = 0; d < D; d++) t64[d] = h->x64[d];
+                PF_TRY(h->cuda(cudaMemcpyAsync(h->ptrtab, t64, sizeof(t64), cudaMemcpyHostToDevice, s), "pointer table"));
+                k_comp_differs<double><<<g, 256, 0, s>>>(N, D, a, (double *const *)h->ptrtab, h->u_changed);
+                PF_TRY(h->cuda(cudaMemcpyAsync(h->ptrtab, tab, sizeof(tab), cudaMemcpyHostToDevice, s), "pointer table"));
+            } else {
+                k_comp_differs<T><<<g, 256, 0, s>>>(N, D, a, (T *const *)h->ptrtab, h->u_changed);
+            }
+        }
+        k_in_comp_if<T><<<g, 256, 0, s>>>(N, D, a, (T *const *)h->ptrtab, h->u_changed);
         PF_TRY(h->cuda(cudaStreamSynchronize(s), "set_fields sync"));
         if (h->refine) {
             for (int d = 0; d < 3; d++) tab[d] = h->x64[d];
             PF_TRY(h->cuda(cudaMemcpyAsync(h->ptrtab, tab, sizeof(tab), cudaMemcpyHostToDevice, s), "pointer table"));
-            k_in_comp<double><<<g, 256, 0, s>>>(N, D, a, (double *const *)h->ptrtab);
+            k_in_comp_if<double><<<g, 256, 0, s>>>(N, D, a, (double *const *)h->ptrtab, h->u_changed);
             PF_TRY(h->cuda(cudaStreamSynchronize(s), "set_fields sync"));
         }
     }
@@ -954,24 +974,22 @@ int set_fields_t(pf_handle *h, const pf_fields *f, int where, cudaStream_t s)
     PF_TRY(h->cuda(cudaMemsetAsync(h->devE2, 0, h->tsz * (size_t)N, s), "coupling"));
     // reference oxygen content
     const int gs = grid_for(h, N);
-    k_sum<T><<<gs, 256, 0, s>>>(N, (const T *)h->xO[0], h->partials);
+    k_sum<T><<<gs, 256, 0, s>>>(N, (const T *)h->xO[c0], h->partials);
     std::vector<double> part((size_t)gs * PSTRIDE);
     PF_TRY(h->cuda(cudaMemcpyAsync(part.data(), h->partials, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s), "partials"));
     PF_TRY(h->cuda(cudaStreamSynchronize(s), "set_fields sync"));
     double s0 = 0.0;
     for (int b = 0; b < gs; b++) s0 += part[(size_t)b * PSTRIDE];
     h->sumO0 = s0;
-    h->cur = 0;
     h->steps = 0;
     h->cg_total_seen = 0;
     h->have_fields = true;
     h->sigma_valid = false;
-    h->plan_ready = false;          // the field buffers' roles changed
     if (h->net_mode) {
         static const int first = 1;
         PF_TRY(h->cuda(cudaMemcpyAsync(h->net_mode, &first, sizeof(int), cudaMemcpyHostToDevice, s), "net mode"));
     }
-    if (h->ext_count) PF_TRY(h->cuda(cudaMemsetAsync(h->ext_count, 0, sizeof(int), s), "extrapolation count"));
+    if (h->ext_count) k_ext_restart<<<1, 1, 0, s>>>(h->u_changed, h->ext_count);
     return h->cuda(cudaGetLastError(), "set_fields kernels");
 #undef PF_SRC
 }
@@ -1072,6 +1090,7 @@ int alloc_fields(pf_handle *h)
             PF_TRY(h->alloc(&h->ext_E, sizeof(double) * 12));
             PF_TRY(h->alloc(&h->ext_count, sizeof(int)));
             PF_TRY(h->cuda(cudaMemset(h->ext_count, 0, sizeof(int)), "extrapolation count"));
+            PF_TRY(h->alloc(&h->u_changed, sizeof(int)));
         }
         if (!h->fp64) {
             h->refine = true;
