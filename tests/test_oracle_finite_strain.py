@@ -334,6 +334,32 @@ def test_coupled_step_without_volume_change_is_the_oracle_step(orc, fs):
     assert np.abs(c4.sim.f["theta"] - o1.f["theta"]).max() > 1e-4
 
 
+def test_coupled_step_small_strain_limit(orc, fs):
+    """The elastic part of one coupled step (CoupledSim: the change of theta
+    that the finite-strain mechanics adds to the step without mechanics)
+    approaches the same part of one oracle step with the small-strain
+    mechanics (eigenstrain -Omega/3 W_f) as Omega -> 0: the relative
+    difference is O(Omega).  This fixes the sign and the factor -(L/2) mob
+    with which the finite-strain force enters the order parameter's rate."""
+    th = _inclusion()
+    z = np.zeros_like(th)
+    f = {"phi_f": th, "phi_w": 1.0 - th, "xO": z + 0.3, "xH": z + 0.01, "xW": z}
+    prm = workloads.params(prestress=0.0, cg_rtol=1e-13, cg_maxit=100000)
+    o0 = orc.Sim(f, dict(prm, mechanics=0))
+    o0.step(1)
+    rel = []
+    for om in (0.02, 0.01):
+        c = fs.CoupledSim(f, prm, om)
+        c.step(1)
+        s = orc.Sim(f, dict(prm, eig0=-om / 3.0))
+        s.step(1)
+        d_fin = c.sim.f["theta"] - o0.f["theta"]
+        d_small = s.f["theta"] - o0.f["theta"]
+        assert np.abs(d_small).max() > 1e-8        # far above the rounding of theta ~ 1
+        rel.append(np.abs(d_fin - d_small).max() / np.abs(d_small).max())
+    assert rel[0] < 0.05 and 1.7 < rel[0] / rel[1] < 2.3, rel
+
+
 def test_3d_uniform_transformation_is_stress_free(fs):
     """In 3D nothing constrains the transformation: uniform ferrite with
     Omega = 0.4 and no mean stress deforms by exactly F = d_T^(1/3) I, where
