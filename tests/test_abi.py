@@ -80,6 +80,28 @@ def test_fs_coupling_validates_before_touching_the_gpu(lib):
     assert lib.pf_fs_coupling(None, None, None, 0.1, None, None, None, None) == native.PF_EINVAL
 
 
+def test_finite_strain_validates_before_touching_the_gpu(lib):
+    """pf_finite_strain_solve answers bad options, precisions, grid sizes
+    and material constants with PF_EINVAL and a message before any CUDA
+    call."""
+    import numpy as np
+    th = np.ones((4, 4))
+    good = dict(nload=1, newton_maxit=5, newton_tol=1e-10, cg_maxit=10, cg_rtol=1e-6, precision=native.PF_MIXED)
+    cases = [(dict(good, nload=0), b"pf_fs_opts"), (dict(good, cg_rtol=1.0), b"pf_fs_opts"),
+             (dict(good, newton_tol=0.0), b"pf_fs_opts"), (dict(good, precision=7), b"precision")]
+    cfg = make_config((4, 4), workloads.params())
+    for o, msg in cases:
+        rc, _, _, _ = native.pf_finite_strain_solve(cfg, th, th * 0, 0.1, None, native.pf_fs_opts(**o))
+        assert rc == native.PF_EINVAL and msg in lib.pf_fs_last_error(), (o, lib.pf_fs_last_error())
+    bad = make_config((4, 4), dict(workloads.params(), nu=0.5))
+    rc, _, _, _ = native.pf_finite_strain_solve(bad, th, th * 0, 0.1, None, native.pf_fs_opts(**good))
+    assert rc == native.PF_EINVAL and b"nu" in lib.pf_fs_last_error()
+    one = make_config((4, 4), workloads.params())
+    one.nx = 1
+    rc, _, _, _ = native.pf_finite_strain_solve(one, th, th * 0, 0.1, None, native.pf_fs_opts(**good))
+    assert rc == native.PF_EINVAL and b"grid sizes" in lib.pf_fs_last_error()
+
+
 def test_batch_create_validates_before_touching_the_gpu(lib):
     prm = workloads.params()
     two = make_config((16, 16), prm)
