@@ -279,7 +279,7 @@ typedef struct {
     int precision;      /* PF_FP64: Hessian-vector products in FP64;
                            PF_MIXED: in FP32 (the residual stays FP64, so
                            the solution is the same; CG then stops at
-                           max(cg_rtol, 1e-6), an inexact Newton step)     */
+                           max(cg_rtol, 1e-5), an inexact Newton step)     */
 } pf_fs_opts;
 
 typedef struct {
